@@ -1,0 +1,153 @@
+"""ctypes wrapper around ``oracle/rng.c`` (test infrastructure only).
+
+The shared object is compiled on first use with ``gcc -O2 -ffp-contract=off``
+so every binary32 step is the exact IEEE operation written in the source.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rng.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle_rng.so")
+_lock = threading.Lock()
+_lib = None
+
+# Streams of the Philox field (counter word 3, low byte).
+STREAM_SKETCH_U = 0      # S^t, U-half (Section 3.2, eq. sketched_u)
+STREAM_SKETCH_V = 1      # S'^t, V-half (eq. sketched_v)
+STREAM_INIT_U = 2        # U^0 (Alg. 2 line 1)
+STREAM_INIT_V = 3        # V^0
+
+
+def build(force=False):
+    """Compile rng.c into _build/liboracle_rng.so (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            f32p = ctypes.POINTER(ctypes.c_float)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            L.ora_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.ora_uniform_open.argtypes = [ctypes.c_uint32]
+            L.ora_uniform_open.restype = ctypes.c_float
+            L.ora_uniform01.argtypes = [ctypes.c_uint32]
+            L.ora_uniform01.restype = ctypes.c_float
+            L.ora_lnf.argtypes = [ctypes.c_float]
+            L.ora_lnf.restype = ctypes.c_float
+            L.ora_sincos_turn.argtypes = [ctypes.c_uint32, f32p, f32p]
+            L.ora_box_muller.argtypes = [ctypes.c_uint32, ctypes.c_uint32, f32p, f32p]
+            L.ora_field_words.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                          ctypes.c_int64, ctypes.c_int64, u32p]
+            L.ora_gaussian_field.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                             ctypes.c_int64, ctypes.c_int64, ctypes.c_float, f32p]
+            L.ora_uniform_field.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                            ctypes.c_int64, ctypes.c_int64, f32p]
+            L.ora_feistel_half_bits.argtypes = [ctypes.c_int64]
+            L.ora_feistel_half_bits.restype = ctypes.c_int
+            L.ora_feistel_once.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                           ctypes.c_int, ctypes.c_uint32]
+            L.ora_feistel_once.restype = ctypes.c_uint32
+            L.ora_subsample.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                        ctypes.c_int64, ctypes.c_int64, i32p]
+            _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block: 4 counter words, 2 key words -> 4 output words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().ora_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                            _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def field_words(seed, stream, t, rows, cols):
+    out = np.empty((rows, cols), dtype=np.uint32)
+    lib().ora_field_words(seed, stream, t, rows, cols, _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def lnf(u):
+    return np.float32(lib().ora_lnf(float(np.float32(u))))
+
+
+def sincos_turn(w):
+    s = ctypes.c_float()
+    c = ctypes.c_float()
+    lib().ora_sincos_turn(int(w), ctypes.byref(s), ctypes.byref(c))
+    return np.float32(s.value), np.float32(c.value)
+
+
+def uniform_open(w):
+    return np.float32(lib().ora_uniform_open(int(w)))
+
+
+def box_muller(wa, wb):
+    a = ctypes.c_float()
+    b = ctypes.c_float()
+    lib().ora_box_muller(int(wa), int(wb), ctypes.byref(a), ctypes.byref(b))
+    return np.float32(a.value), np.float32(b.value)
+
+
+def gaussian_scale(d):
+    """1/sqrt(d) rounded once to binary32 (the scale of Section 3.4)."""
+    return np.float32(1.0 / np.sqrt(np.float64(d)))
+
+
+def gaussian_field(seed, stream, t, rows, cols, scale):
+    """rows x cols binary32 Gaussian field times ``scale`` (exact bits)."""
+    out = np.empty((rows, cols), dtype=np.float32)
+    lib().ora_gaussian_field(seed, stream, t, rows, cols, float(np.float32(scale)),
+                             _ptr(out, ctypes.c_float))
+    return out
+
+
+def uniform_field(seed, stream, t, rows, cols):
+    out = np.empty((rows, cols), dtype=np.float32)
+    lib().ora_uniform_field(seed, stream, t, rows, cols, _ptr(out, ctypes.c_float))
+    return out
+
+
+def feistel_half_bits(n):
+    return int(lib().ora_feistel_half_bits(n))
+
+
+def feistel_once(seed, side, t, h, x):
+    return int(lib().ora_feistel_once(seed, side, t, h, x))
+
+
+def subsample_indices(seed, side, t, n, d):
+    """The d sampled indices of {0..n-1}, sorted ascending (Section 3.4)."""
+    J = np.empty(d, dtype=np.int32)
+    lib().ora_subsample(seed, side, t, n, d, _ptr(J, ctypes.c_int32))
+    return np.sort(J)
+
+
+def subsample_scale(n, d):
+    """sqrt(n/d) rounded once to binary32 (makes E[S S^T] = I, Assumption 1)."""
+    return np.float32(np.sqrt(np.float64(n) / np.float64(d)))

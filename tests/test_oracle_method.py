@@ -1,0 +1,284 @@
+"""Pins of the oracle's method steps (CPU only).
+
+Each test checks the FP64 oracle against a fact fixed outside it: the
+unbiasedness of the sketched gradient (Section 3.5.1), the reduction of the
+sketched steps to textbook unsketched ones when S = I (HALS for Alg. 3 with
+mu = 0; the plain projected-gradient step), the exact identity satisfied by a
+projected step (Appendix B, eq. delta), monotone descent, coordinate-wise
+optimality of Alg. 3, row independence (eq. u_block), Lemma 1's rescaling
+invariance, library eigen-solvers and the dense/sparse error identity.
+A final group plants mistakes into a copy of the oracle and checks that the
+pins above catch them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import method, rng
+from synthdata import planted_dense
+
+
+def _problem(m=30, n=24, k=4, seed=0):
+    M, U0, V0 = planted_dense(m, n, k, seed)
+    g = np.random.default_rng(seed + 100)
+    U = g.random((m, k))
+    V = g.random((n, k))
+    return M.astype(np.float64), U, V
+
+
+# --------------------------------------------------------------------------
+# pin functions (take the oracle module so a mutated copy can be checked)
+# --------------------------------------------------------------------------
+
+def pin_unbiased_gradient(mod, kind, trials=3000):
+    """E over S of (U G - R) equals U V^T V - M V (Section 3.5.1)."""
+    M, U, V = _problem(8, 10, 3, 1)
+    acc = np.zeros_like(U)
+    for t in range(trials):
+        S = mod.Sketch(kind, 5, t, 0, M.shape[1], 4)
+        _, _, G, R = mod.sketched_terms(M, V, S)
+        acc += U @ G - R
+    mean = acc / trials
+    exact = U @ (V.T @ V) - M @ V
+    return np.max(np.abs(mean - exact)) / np.max(np.abs(exact))
+
+
+def pin_identity_pgd(mod):
+    """S = I: the sketched PGD step is the plain projected-gradient step."""
+    M, U, V = _problem()
+    S = mod.Sketch(mod.IDENTITY, 0, 0, 0, M.shape[1], M.shape[1])
+    _, _, G, R = mod.sketched_terms(M, V, S)
+    eta = 1.0 / (mod.lambda_max(G) + 0.5)
+    got = mod.pgd_update(U, G, R, eta)
+    want = method.project(U - eta * (U @ (V.T @ V) - M @ V))
+    return np.max(np.abs(got - want))
+
+
+def pin_identity_rcd_is_hals(mod):
+    """S = I, mu = 0: Alg. 3 is the textbook HALS column sweep."""
+    M, U, V = _problem()
+    S = mod.Sketch(mod.IDENTITY, 0, 0, 0, M.shape[1], M.shape[1])
+    _, _, G, R = mod.sketched_terms(M, V, S)
+    got = mod.rcd_update(U, G, R, 0.0)
+    Z = U.copy()
+    XY, YY = M @ V, V.T @ V
+    for j in range(Z.shape[1]):
+        Z[:, j] = np.maximum(Z[:, j] + (XY[:, j] - Z @ YY[:, j]) / YY[j, j], 0.0)
+    return np.max(np.abs(got - Z))
+
+
+def pin_pgd_identity(mod):
+    """(U^t - U^{t+1}) / eta = min(U^t / eta, U G - R) (Appendix B, eq. delta)."""
+    M, U, V = _problem()
+    S = mod.Sketch(mod.GAUSSIAN, 3, 2, 0, M.shape[1], 8)
+    _, _, G, R = mod.sketched_terms(M, V, S)
+    eta = 1.0 / (mod.lambda_max(G) + 1.0)
+    Un = mod.pgd_update(U, G, R, eta)
+    lhs = (U - Un) / eta
+    rhs = np.minimum(U / eta, U @ G - R)
+    return np.max(np.abs(lhs - rhs)) / np.max(np.abs(rhs))
+
+
+# --------------------------------------------------------------------------
+# pins
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE])
+def test_sketched_gradient_is_unbiased(kind):
+    assert pin_unbiased_gradient(method, kind) < 0.08
+
+
+def test_identity_sketch_reduces_to_plain_pg():
+    assert pin_identity_pgd(method) < 1e-12
+
+
+def test_identity_rcd_mu0_is_hals():
+    assert pin_identity_rcd_is_hals(method) < 1e-12
+
+
+def test_projected_step_identity():
+    assert pin_pgd_identity(method) < 1e-12
+
+
+def test_lambda_max_matches_eigvalsh():
+    M, U, V = _problem(40, 60, 6, 4)
+    for t in range(5):
+        S = method.Sketch(method.GAUSSIAN, 1, t, 0, 60, 20)
+        _, B, G, _ = method.sketched_terms(M, V, S)
+        lam = method.lambda_max(G, 32)
+        ref = np.linalg.eigvalsh(G)[-1]
+        assert abs(lam - ref) <= 1e-6 * ref
+
+
+@pytest.mark.parametrize("solver", [method.PGD, method.RCD])
+def test_identity_sketch_descends(solver):
+    """With S = I every half-step decreases ||M - U V^T||_F (step 1/(L+mu) for
+    PGD; exact coordinate minimisation plus a proximal term for RCD)."""
+    M, U, V = _problem(40, 30, 5, 2)
+    opt = method.Options(sketch=method.IDENTITY, solver=solver, alpha=0.1, beta=0.0)
+    f = np.linalg.norm(M - U @ V.T)
+    for t in range(15):
+        S = method.Sketch(method.IDENTITY, 0, t, 0, 30, 30)
+        U = method.half_step(M, V, U, S, solver, 0.1)
+        f1 = np.linalg.norm(M - U @ V.T)
+        assert f1 <= f * (1 + 1e-12)
+        S = method.Sketch(method.IDENTITY, 0, t, 1, 40, 40)
+        V = method.half_step(M.T, U, V, S, solver, 0.1)
+        f2 = np.linalg.norm(M - U @ V.T)
+        assert f2 <= f1 * (1 + 1e-12)
+        f = f2
+
+
+def test_rcd_columns_are_coordinate_minimisers():
+    """Each column from Alg. 3 minimises the 1-D proximal objective of eq. entry_sol:
+    derivative zero where positive, nonnegative where clamped at 0."""
+    M, U, V = _problem(25, 20, 4, 7)
+    S = method.Sketch(method.GAUSSIAN, 2, 1, 0, 20, 12)
+    A, B, G, R = method.sketched_terms(M, V, S)
+    mu = 0.7
+    Un = method.rcd_update(U, G, R, mu)
+    k = U.shape[1]
+    for j in range(k):
+        Zj = np.concatenate([Un[:, :j], U[:, j:]], axis=1)
+        # row-wise residual of the sketched objective with column j free
+        others = np.delete(np.arange(k), j)
+        Zo = Zj[:, others]
+        x = Un[:, j]
+        # d/dx [ ||A - x B_j - Zo B_o||^2 + mu (x - U_j)^2 ] / 2
+        grad = x * (B[j] @ B[j]) - (A - Zo @ B[others]) @ B[j] + mu * (x - U[:, j])
+        scale = np.max(np.abs(A @ B[j])) + 1.0
+        assert np.all(np.abs(grad[x > 0]) <= 1e-9 * scale)
+        assert np.all(grad[x == 0] >= -1e-9 * scale)
+
+
+def test_half_step_is_row_independent():
+    M, U, V = _problem(30, 24, 4, 9)
+    S = method.Sketch(method.GAUSSIAN, 4, 0, 0, 24, 10)
+    full = method.half_step(M, V, U, S, method.PGD, 1.0)
+    rows = np.array([0, 7, 29])
+    part = method.half_step(M, V, U, S, method.PGD, 1.0, rows=rows)
+    assert np.allclose(full[rows], part, rtol=0, atol=1e-13)
+    full = method.half_step(M, V, U, S, method.RCD, 1.0)
+    part = method.half_step(M, V, U, S, method.RCD, 1.0, rows=rows)
+    assert np.allclose(full[rows], part, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("solver", [method.PGD, method.RCD])
+@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE])
+def test_factors_stay_nonnegative(solver, kind):
+    M, U, V = _problem(30, 24, 4, 3)
+    opt = method.Options(sketch=kind, d=8, solver=solver)
+    MT = M.T.copy()
+    for t in range(10):
+        U, V = method.outer_iteration(M, MT, U, V, 0, t, opt)
+        assert U.min() >= 0 and V.min() >= 0
+
+
+def test_rescaling_invariance_lemma1():
+    M, U, V = _problem()
+    D = np.diag([0.5, 2.0, 3.0, 0.25])
+    assert abs(method.rel_error(M, U @ D, V @ np.linalg.inv(D)) - method.rel_error(M, U, V)) < 1e-13
+
+
+def test_sparse_error_expansion_equals_direct():
+    g = np.random.default_rng(0)
+    D = g.random((40, 30))
+    D[D < 0.7] = 0.0
+    U, V = g.random((40, 5)), g.random((30, 5))
+    direct = np.linalg.norm(D - U @ V.T) / np.linalg.norm(D)
+    assert abs(method.rel_error(sp.csr_matrix(D), U, V) - direct) < 1e-12
+
+
+def test_sketch_subsample_matches_dense_definition():
+    M, U, V = _problem(10, 20, 3, 0)
+    S = method.Sketch(method.SUBSAMPLE, 7, 3, 0, 20, 6)
+    Sd = S.dense()
+    assert np.allclose(S.right_multiply(M), M @ Sd, rtol=0, atol=1e-13)
+    assert np.allclose(Sd.sum(axis=0), float(S.scale))
+    assert math.isclose(float(S.scale) ** 2, 20 / 6, rel_tol=1e-6)
+
+
+def test_sketched_run_reduces_error():
+    M, U0, V0 = planted_dense(120, 90, 5, 0)
+    U, V = method.default_init(0, 120, 90, 5)
+    opt = method.Options(sketch=method.GAUSSIAN, d=30, solver=method.PGD)
+    _, _, errs = method.run(M, U, V, 0, 30, opt)
+    assert errs[-1] < 0.75 * errs[0]
+    opt = method.Options(sketch=method.SUBSAMPLE, d=30, solver=method.RCD)
+    _, _, errs = method.run(M, U, V, 0, 30, opt)
+    assert errs[-1] < 0.5 * errs[0]
+
+
+def test_default_init_is_uniform_field():
+    U, V = method.default_init(3, 17, 9, 4)
+    assert U.shape == (17, 4) and V.shape == (9, 4)
+    assert np.array_equal(U, rng.uniform_field(3, 2, 0, 17, 4))
+    assert U.min() >= 0 and U.max() < 1
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: a mutated copy of the oracle must fail at least one pin
+# --------------------------------------------------------------------------
+
+class _Mutant:
+    def __init__(self, **over):
+        self.__dict__.update({k: getattr(method, k) for k in dir(method) if not k.startswith("__")})
+        self.__dict__.update(over)
+
+
+
+def test_mutant_dropped_R_term_is_caught():
+    def bad_pgd(Z, G, R, eta, bound=None):
+        return method.project(Z - eta * (Z @ G))
+    mut = _Mutant(pgd_update=bad_pgd)
+    assert pin_pgd_identity(mut) > 1e-3 or pin_identity_pgd(mut) > 1e-3
+
+
+def test_mutant_wrong_sign_in_rcd_is_caught():
+    def bad_rcd(Z, G, R, mu, bound=None):
+        Zold, Znew = Z, Z.copy()
+        for j in range(Z.shape[1]):
+            T = mu * Zold[:, j] + R[:, j]
+            for l in range(j):
+                T = T + G[l, j] * Znew[:, l]
+            for l in range(j + 1, Z.shape[1]):
+                T = T - G[l, j] * Zold[:, l]
+            Znew[:, j] = method.project(T / (G[j, j] + mu))
+        return Znew
+    mut = _Mutant(rcd_update=bad_rcd)
+    assert pin_identity_rcd_is_hals(mut) > 1e-3
+
+
+def test_mutant_old_columns_in_rcd_is_caught():
+    """Jacobi instead of Gauss-Seidel sweep (all l use U^t)."""
+    def jacobi(Z, G, R, mu, bound=None):
+        Znew = Z.copy()
+        for j in range(Z.shape[1]):
+            T = mu * Z[:, j] + R[:, j] - Z @ G[:, j] + G[j, j] * Z[:, j]
+            Znew[:, j] = method.project(T / (G[j, j] + mu))
+        return Znew
+    mut = _Mutant(rcd_update=jacobi)
+    assert pin_identity_rcd_is_hals(mut) > 1e-3
+
+
+def test_mutant_unscaled_subsample_is_caught():
+    class BadSketch(method.Sketch):
+        def __init__(self, *a, **k):
+            super().__init__(*a, **k)
+            if self.kind == method.SUBSAMPLE:
+                self.scale = np.float32(1.0)
+    mut = _Mutant(Sketch=BadSketch)
+    assert pin_unbiased_gradient(mut, method.SUBSAMPLE, trials=1500) > 0.2
+
+
+def test_mutant_missing_gaussian_scale_is_caught():
+    """Entries N(0,1) instead of N(0,1/d) give E[S S^T] = d I."""
+    class BadSketch(method.Sketch):
+        def __init__(self, kind, seed, t, side, n, d):
+            super().__init__(kind, seed, t, side, n, d)
+            if kind == method.GAUSSIAN:
+                self.dense32 = rng.gaussian_field(seed, side, t, n, d, 1.0)
+    mut = _Mutant(Sketch=BadSketch)
+    assert pin_unbiased_gradient(mut, method.GAUSSIAN, trials=300) > 0.2
