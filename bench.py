@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of sketched ANLS (DSANLS hot path) on one GB300 per rank.
+
+Workload (default ``dense_gaussian``): the dense image-like precision study --
+planted M = U0 V0^T + |N(0, 0.01^2)| of 65,536 x 16,384 (U0, V0 ~ U[0,1) with
+70% zeros, k = 64), rank 64, Gaussian sketch d = d' = 2048, projected-gradient
+step.  A "step" is one outer iteration (U-half + V-half) replayed as a CUDA
+graph; the metric is outer iterations per second.  With N ranks each rank runs
+its own replica (independent problem, seed = rank): weak scaling, no
+collective on the data path.
+
+Also printed on the same JSON line:
+  roofline      the dominant kernel (the sketched product A = M S) timed with
+                CUDA events on the handle's stream right after the timed region
+  cpu_baseline  the FP64 oracle on a bounded row sample, extrapolated
+  e2e           the same metric through the public API with host buffers
+                (upload of M from pinned memory, one iteration, factors back)
+  clocks        nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sketched-ANLS outer iters/s and time-to-ε (rel. Frobenius err) vs plain FP32"
+UNIT = "outer_iters/s"
+
+WORKLOADS = {
+    "dense_gaussian": dict(m=65536, n=16384, k=64, d=2048, d_v=2048, sketch=0, zero_frac=0.7, noise=0.01,
+                           desc="dense 65536x16384 planted (k=64, 70% zero factors, |N(0,0.01^2)| noise), "
+                                "Gaussian sketch d=d'=2048, PGD"),
+    "dense_subsample": dict(m=65536, n=16384, k=64, d=2048, d_v=2048, sketch=1, zero_frac=0.7, noise=0.01,
+                            desc="dense 65536x16384 planted (k=64), subsampling sketch d=d'=2048, PGD"),
+    "small": dict(m=1000, n=800, k=10, d=100, d_v=100, sketch=0, zero_frac=0.0, noise=0.01,
+                  desc="planted 1000x800, k=10, Gaussian d=100, PGD"),
+}
+
+# FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.070 GHz.
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_inputs(w, seed):
+    from synthdata import planted_dense
+    M, _, _ = planted_dense(w["m"], w["n"], w["k"], seed, zero_frac=w["zero_frac"], noise=w["noise"])
+    return M
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(M, w, seed, rows_budget):
+    """Time the FP64 oracle on one outer iteration restricted to `rows_budget`
+    rows per half and extrapolate linearly in rows (the row-independent part:
+    the sketch, B = Y^T S and G are computed in full).  Returns (iters/s, desc)."""
+    from oracle import method
+    m, n, k = w["m"], w["n"], w["k"]
+    U0, V0 = method.default_init(seed, m, n, k)
+    U0 = U0.astype(np.float64)
+    V0 = V0.astype(np.float64)
+    mu = method.mu_t(1.0, 1.0, 0)
+    total = 0.0
+    for side, K, rows_all, dd in ((0, n, m, w["d"]), (1, m, n, w["d_v"])):
+        r = min(rows_all, rows_budget)
+        rows = np.arange(r)
+        t0 = time.perf_counter()
+        S = method.Sketch(w["sketch"], seed, 0, side, K, dd)
+        Y = V0 if side == 0 else U0
+        if w["sketch"] == method.GAUSSIAN:
+            B = Y.T @ S.dense32.astype(np.float64)
+        else:
+            B = (Y[S.J, :] * np.float64(S.scale)).T
+        G = B @ B.T
+        lam = method.lambda_max(G)
+        t1 = time.perf_counter()
+        X = M[rows].astype(np.float64) if side == 0 else M[:, rows].T.astype(np.float64)
+        A = S.right_multiply(X)
+        R = A @ B.T
+        Z = (U0 if side == 0 else V0)[rows]
+        method.pgd_update(Z, G, R, 1.0 / (lam + mu))
+        t2 = time.perf_counter()
+        total += (t1 - t0) + (t2 - t1) * rows_all / r
+    desc = "FP64 oracle, one outer iteration on %d rows per half, extrapolated to %dx%d" % (
+        min(rows_budget, m), m, n)
+    return 1.0 / total, desc
+
+
+def _cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args, w):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    M = make_inputs(w, 0)
+    rows = 512 if w["m"] > 10000 else w["m"]
+    for _ in range(args.warmup):
+        oracle_sample(M, w, 0, rows)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, desc = oracle_sample(M, w, 0, rows)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(statistics.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"],
+                   "d": w["d"], "d_v": w["d_v"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def _traffic(kernel_key, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        table = json.load(f)
+    ent = table.get(kernel_key, {}).get(workload)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2009_02845_gb300", "csrc", ent["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2009_02845_gb300 as pkg
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    prec = pkg.BF16 if args.precision == "bf16" else pkg.FP32
+    M = make_inputs(w, rank)
+    h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=rank, d_v=w["d_v"], solver=pkg.PGD,
+                   precision=prec, use_graph=1)
+    h.set_dense(M)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        h.step(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = pkg.kernel_launches()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        h.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = pkg.kernel_launches() - l0
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1000.0)
+    err = h.rel_error()
+
+    # dominant kernel: the sketched product of each half, timed per phase
+    phases = [h.profile_half_step(0, reps=2), h.profile_half_step(1, reps=2)]
+    peaks, peak_src = _peaks()
+    m, n, d, d_v, k = w["m"], w["n"], w["d"], w["d_v"], w["k"]
+    if w["sketch"] == 0:
+        flops = [2.0 * m * n * d, 2.0 * n * m * d_v]
+        if prec == pkg.BF16:
+            flops = [f + 2.0 * m * d * k for f in flops]  # R = A B^T is fused into the same kernel
+        prod_ms = [p["product"] for p in phases]
+        achieved = sum(flops) / (sum(prod_ms) / 1000.0) / 1e12
+        if prec == pkg.BF16:
+            bound, peak, unit, kernel_key = "tensor", peaks["bf16_tflops_sustained"], "TFLOP/s", "tc_sketch_rhs"
+            peak_note = "bf16_tflops_sustained of %s" % peak_src
+        else:
+            bound, peak, unit, kernel_key = "alu", FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "sgemm_simt"
+            peak_note = "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
+    else:
+        # subsampling: the gathered product reads d columns of M^T per half
+        bytes_ = [4.0 * (m * d + d * k) + 4.0 * m * k, 4.0 * (n * d_v + d_v * k) + 4.0 * n * k]
+        prod_ms = [p["rhs"] for p in phases]
+        achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
+        bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "sgemm_simt_gather"
+        peak_note = "hbm_gbs of %s" % peak_src
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": _traffic(kernel_key, args.workload), "kernel": kernel_key, "peak_source": peak_note,
+                "launch_ms": [round(x, 4) for x in prod_ms]}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        Mp = torch.from_numpy(M).pin_memory()
+        Uh = torch.empty((m, k), dtype=torch.float32).pin_memory()
+        Vh = torch.empty((n, k), dtype=torch.float32).pin_memory()
+        he = pkg.DSANLS(m, n, k, d, w["sketch"], seed=rank, d_v=d_v, solver=pkg.PGD, precision=prec, use_graph=1)
+
+        def e2e_step():
+            he.set_dense(Mp)
+            he.step(1)
+            he.factors()  # synchronising device->host read of U and V
+        e2e_step()
+        reps = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        he.close()
+        e2e = {"value": 1.0 / dt, "unit": UNIT, "h2d_bytes_per_step": int(M.nbytes),
+               "d2h_bytes_per_step": int((m + n) * k * 4),
+               "note": "per step: set_dense from pinned host M, 1 outer iteration, get_factors to host"}
+        del Mp
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows = 512 if m > 10000 else m
+        v, desc = oracle_sample(M, w, rank, rows)
+        cpu = {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": desc}
+
+    h.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if prec == pkg.BF16 else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "k": k, "d": d, "d_v": d_v,
+                       "precision": args.precision, "solver": "pgd", "graph": True, "replicas": ws,
+                       "l2": "inputs larger than L2 (M is %.1f GB)" % (M.nbytes / 1e9)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "phases_ms": {"U": {k_: round(v_, 4) for k_, v_ in phases[0].items()},
+                          "V": {k_: round(v_, 4) for k_, v_ in phases[1].items()}},
+            "rel_error_after": err,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense_gaussian")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * dsanls.h -- C ABI of the GB300 sketched-ANLS library (libdsanls.so).
+ *
+ * The library computes nonnegative matrix factorisations M ~ U V^T
+ * (M m x n, U m x k, V n x k, all >= 0; Section 2.1, eq. problem) with the
+ * sketched alternating nonnegative least squares method of Section 3
+ * (SANLS; the single-node body of DSANLS, Alg. 2).  One outer iteration t:
+ *
+ *   U-half: draw S^t (n x d); A = M S^t; B = V^T S^t; G = B B^T; R = A B^T;
+ *           U <- solver(U, G, R, t)           (Section 3.2, eq. sketched_u)
+ *   V-half: draw S'^t (m x d'); the same with M^T and the new U
+ *                                             (eq. sketched_v, Alg. 1 line 4)
+ *
+ * solver = projected gradient (eq. gradient_descent) or proximal coordinate
+ * descent (Alg. 3, eq. entry_sol); sketches: Gaussian N(0,1/d), column
+ * subsampling without replacement, or the identity (Section 3.4).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an int status (DSANLS_OK = 0 or a negative code
+ *    below); no C++ exception crosses the ABI.  Handle calls store a message
+ *    retrievable with dsanls_last_error().
+ *  - Matrices are row-major binary32 unless stated otherwise.
+ *  - Input arrays are copied; the caller keeps ownership of everything it
+ *    passes.  Output buffers are caller-owned.
+ *  - "on_device" = 1 means the pointer is CUDA device memory of the current
+ *    device, 0 means host memory (pageable or pinned).
+ *  - A handle is bound to the CUDA device current at dsanls_create and is
+ *    not thread-safe: use one handle per host thread.
+ *  - Work is queued on the handle's stream (dsanls_options.stream; NULL
+ *    selects a non-blocking stream created and owned by the handle).  dsanls_step returns once the work is
+ *    queued; an asynchronous failure (a CUDA error, a NaN/Inf produced by an
+ *    update) surfaces at the next synchronising call (dsanls_rel_error,
+ *    dsanls_get_factors, dsanls_sync).
+ */
+#ifndef DSANLS_H
+#define DSANLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define DSANLS_OK 0
+#define DSANLS_EINVAL (-1)    /* bad argument (size, pointer, kind, option)      */
+#define DSANLS_ENOMEM (-2)    /* device or host allocation failed               */
+#define DSANLS_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed     */
+#define DSANLS_ESTATE (-4)    /* call out of order, e.g. step before set_dense   */
+#define DSANLS_ENUMERIC (-5)  /* an update produced NaN or Inf                   */
+#define DSANLS_ETIMEOUT (-6)  /* a bounded device wait gave up                   */
+
+/* ---- sketch kinds (Section 3.4) ------------------------------------- */
+#define DSANLS_SKETCH_GAUSSIAN 0   /* i.i.d. N(0, 1/d) entries                       */
+#define DSANLS_SKETCH_SUBSAMPLE 1  /* d columns sqrt(n/d) e_i, drawn w/o replacement */
+#define DSANLS_SKETCH_IDENTITY 2   /* S = I (needs d = n and d_v = m)                */
+
+/* ---- subproblem solvers (Section 3.5) -------------------------------- */
+#define DSANLS_SOLVER_PGD 0   /* one projected gradient step, eq. gradient_descent */
+#define DSANLS_SOLVER_RCD 1   /* proximal coordinate descent, Alg. 3               */
+
+/* ---- arithmetic of the sketched products A = M S and R = A B^T -------- */
+#define DSANLS_PREC_FP32 0    /* binary32 operands and accumulation (CUDA cores)  */
+#define DSANLS_PREC_BF16 1    /* bf16 operands, fp32 accumulation (tcgen05)       */
+
+/* ---- Philox field streams (counter word 3, low byte) ------------------ */
+#define DSANLS_STREAM_SKETCH_U 0
+#define DSANLS_STREAM_SKETCH_V 1
+#define DSANLS_STREAM_INIT_U 2
+#define DSANLS_STREAM_INIT_V 3
+
+typedef struct dsanls_options {
+    int32_t solver;        /* DSANLS_SOLVER_*; default PGD                           */
+    int32_t precision;     /* DSANLS_PREC_*; default FP32                            */
+    int32_t d_v;           /* sketch size d' of the V-half; 0 = same as d            */
+    int32_t power_iters;   /* power iterations for lambda_max(G); default 32         */
+    double alpha;          /* mu_t = alpha + beta * t (eq. reg_sub); default 1       */
+    double beta;           /* default 1                                              */
+    int64_t t;             /* iteration index of the next outer iteration; default 0 */
+    int32_t bound_clamp;   /* 1: clamp entries at sqrt(2 ||M||_F) (eq. extra_con)    */
+    int32_t use_graph;     /* 1: replay each outer iteration as a CUDA graph         */
+    void *stream;          /* cudaStream_t for all work; NULL = the handle's own     */
+} dsanls_options;
+
+typedef struct dsanls_ctx *dsanls_t;
+
+/* Fill *opt with the defaults listed above. */
+int dsanls_default_options(dsanls_options *opt);
+
+/* Create a handle for an m x n problem of rank k with sketch size d for the
+ * U-half (and, unless set_options overrides d_v, for the V-half).
+ * seed keys the Philox field (S^t, S'^t, default U^0, V^0; Section 3.3's
+ * shared seed).  Requires m, n >= 1, 1 <= k <= 128, d >= 1; for SUBSAMPLE
+ * d <= n and d <= 16384; for IDENTITY d == n.  Factors start as the default
+ * Uniform[0,1) draws of streams 2 and 3.  EINVAL, ENOMEM, ECUDA. */
+int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kind,
+                  uint64_t seed, dsanls_t *out);
+
+int dsanls_get_options(dsanls_t h, dsanls_options *opt);
+/* Validates and applies options; d_v follows the same rules as d for the
+ * V-half (against m).  Changing precision to BF16 requires dense data. */
+int dsanls_set_options(dsanls_t h, const dsanls_options *opt);
+
+/* Dense M: m rows of n binary32 values, row stride ld >= n (elements).  The
+ * library keeps M and M^T in device memory (plus bf16 copies when the BF16
+ * precision is selected).  Synchronises the handle's stream. */
+int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device);
+
+/* Sparse M in CSR: rowptr[m+1] (int64, rowptr[0] = 0, nondecreasing,
+ * rowptr[m] = nnz), col[nnz] (int32 in [0,n), strictly increasing within a
+ * row), val[nnz].  The transposed CSR (CSR of M^T, n rows) may be passed in
+ * t_rowptr/t_col/t_val; if t_rowptr is NULL the library builds it on the host
+ * (host inputs only).  Synchronises the handle's stream. */
+int dsanls_set_csr(dsanls_t h, const int64_t *rowptr, const int32_t *col, const float *val,
+                   int64_t nnz, const int64_t *t_rowptr, const int32_t *t_col,
+                   const float *t_val, int32_t on_device);
+
+/* Replace U (m x k) and V (n x k), both row-major; either may be NULL to keep
+ * the current one.  Values are used as given (no projection). */
+int dsanls_set_factors(dsanls_t h, const float *U, const float *V, int32_t on_device);
+
+/* Run outer_iters outer iterations (Alg. 1/Alg. 2 loop body: U-half then
+ * V-half), advancing t by outer_iters.  Asynchronous on the stream. */
+int dsanls_step(dsanls_t h, int32_t outer_iters);
+
+/* Run only one half at the current t without advancing t: side 0 updates U
+ * (eq. sketched_u), side 1 updates V (eq. sketched_v) using the current U. */
+int dsanls_half_step(dsanls_t h, int32_t side);
+
+/* ||M - U V^T||_F / ||M||_F of the current factors (Section 5.1), FP64
+ * accumulation.  Synchronises; reports pending asynchronous errors. */
+int dsanls_rel_error(dsanls_t h, double *out);
+
+/* Copy U (m x k) and V (n x k) out; either may be NULL.  Synchronises. */
+int dsanls_get_factors(dsanls_t h, float *U, float *V, int32_t on_device);
+
+/* G (k x k, FP64, row-major) and eta of the last half-step of the given
+ * side, for inspection; either output may be NULL.  Synchronises. */
+int dsanls_get_gram(dsanls_t h, int32_t side, double *G, double *eta);
+
+/* Wait for all queued work; reports pending asynchronous errors. */
+int dsanls_sync(dsanls_t h);
+
+/* ---- profiling ---------------------------------------------------------
+ * Phases of one half-step, timed by dsanls_profile_half_step. */
+#define DSANLS_PHASE_SKETCH 0     /* draw S^t: Philox field or Feistel indices          */
+#define DSANLS_PHASE_B 1          /* B = Y^T S (eq. def_A_B)                            */
+#define DSANLS_PHASE_PRODUCT 2    /* A = X S (dense: the O(mnd) GEMM; sparse: SpMM)     */
+#define DSANLS_PHASE_RHS 3        /* R = A B^T (zero when fused into PRODUCT)           */
+#define DSANLS_PHASE_GRAM 4       /* G = B B^T in FP64                                  */
+#define DSANLS_PHASE_STEP_SIZE 5  /* lambda_max(G), mu_t, eta_t                         */
+#define DSANLS_PHASE_UPDATE 6     /* fused NNLS row update                              */
+#define DSANLS_NPHASES 7
+
+/* Run the half-step of `side` reps times (it updates the factor like
+ * dsanls_half_step) with CUDA events on the handle's stream at every phase
+ * boundary; ms[0..DSANLS_NPHASES) receives the mean milliseconds per phase.
+ * Synchronises. */
+int dsanls_profile_half_step(dsanls_t h, int32_t side, int32_t reps, double *ms);
+
+/* Cumulative number of kernel launches issued by the library in this
+ * process (a replayed CUDA graph counts each of its kernels).  No GPU work. */
+int dsanls_kernel_launches(uint64_t *out);
+
+const char *dsanls_last_error(dsanls_t h);
+void dsanls_destroy(dsanls_t h);
+
+/* ---- stateless primitives of the hot path (device pointers) ----------
+ * Each runs on `stream` (cudaStream_t, NULL = default) and returns after
+ * queuing; EINVAL on bad sizes or NULL pointers, ECUDA on launch failure. */
+
+/* Raw Philox4x32-10 words of the field: out[i*cols + j] = word (i & 3) of
+ * Philox(counter = (i >> 2, j, t mod 2^32, stream_id | (t >> 32) << 8),
+ *        key = (seed mod 2^32, seed >> 32))   (Salmon et al. 2011). */
+int dsanls_philox_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,
+                        int64_t cols, uint32_t *out, void *stream);
+
+/* Gaussian sketch entries S[i][j] = z(i, j) * scale for i < rows, j < cols,
+ * z standard normal by Box-Muller on the field words (pairs (w0,w1) give rows
+ * 4q, 4q+1, (w2,w3) rows 4q+2, 4q+3) -- the N(0, 1/d) matrix of Section 3.4
+ * with scale = 1/sqrt(d).  transposed = 0 writes S row-major (rows x cols),
+ * 1 writes S^T row-major (cols x rows). */
+int dsanls_gaussian_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,
+                          int64_t cols, float scale, int32_t transposed, float *out,
+                          void *stream);
+
+/* Uniform [0,1) field X[i][j] = (w >> 8) * 2^-24, row-major rows x cols. */
+int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,
+                         int64_t cols, float *out, void *stream);
+
+/* The d column indices of a subsampling sketch (Section 3.4: columns drawn
+ * uniformly without replacement), ascending: {pi(0), ..., pi(d-1)} for the
+ * 4-round Feistel permutation pi of {0..n-1} keyed by (seed, t, side) with
+ * cycle walking.  1 <= d <= min(n, 16384). */
+int dsanls_subsample_indices(uint64_t seed, uint32_t side, uint64_t t, int64_t n, int32_t d,
+                             int32_t *J, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSANLS_H */

@@ -1,0 +1,300 @@
+"""ctypes declarations of libdsanls and a small handle class (argument marshalling only)."""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_PKG, "libdsanls.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENUMERIC, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+GAUSSIAN, SUBSAMPLE, IDENTITY = 0, 1, 2
+PGD, RCD = 0, 1
+FP32, BF16 = 0, 1
+STREAM_SKETCH_U, STREAM_SKETCH_V, STREAM_INIT_U, STREAM_INIT_V = 0, 1, 2, 3
+
+_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE",
+          ENUMERIC: "ENUMERIC", ETIMEOUT: "ETIMEOUT"}
+
+EXPORTED_SYMBOLS = [
+    "dsanls_default_options", "dsanls_create", "dsanls_get_options", "dsanls_set_options",
+    "dsanls_set_dense", "dsanls_set_csr", "dsanls_set_factors", "dsanls_step", "dsanls_half_step",
+    "dsanls_rel_error", "dsanls_get_factors", "dsanls_get_gram", "dsanls_sync", "dsanls_last_error",
+    "dsanls_destroy", "dsanls_philox_field", "dsanls_gaussian_field", "dsanls_uniform_field",
+    "dsanls_subsample_indices", "dsanls_profile_half_step", "dsanls_kernel_launches",
+]
+NPHASES = 7
+PHASES = ["sketch", "B", "product", "rhs", "gram", "step_size", "update"]
+
+
+class DSANLSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("solver", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("d_v", ctypes.c_int32),
+        ("power_iters", ctypes.c_int32),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("t", ctypes.c_int64),
+        ("bound_clamp", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdsanls.so (ImportError if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(lib_path):
+            raise ImportError("libdsanls.so is not built; run paper_2009_02845_gb300.build.build()")
+        L = ctypes.CDLL(lib_path)
+        vp, i32, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+        dbl_p = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "dsanls_default_options": ([ctypes.POINTER(Options)], ctypes.c_int),
+            "dsanls_create": ([i64, i64, i32, i32, i32, u64, ctypes.POINTER(vp)], ctypes.c_int),
+            "dsanls_get_options": ([vp, ctypes.POINTER(Options)], ctypes.c_int),
+            "dsanls_set_options": ([vp, ctypes.POINTER(Options)], ctypes.c_int),
+            "dsanls_set_dense": ([vp, vp, i64, i32], ctypes.c_int),
+            "dsanls_set_csr": ([vp, vp, vp, vp, i64, vp, vp, vp, i32], ctypes.c_int),
+            "dsanls_set_factors": ([vp, vp, vp, i32], ctypes.c_int),
+            "dsanls_step": ([vp, i32], ctypes.c_int),
+            "dsanls_half_step": ([vp, i32], ctypes.c_int),
+            "dsanls_rel_error": ([vp, dbl_p], ctypes.c_int),
+            "dsanls_get_factors": ([vp, vp, vp, i32], ctypes.c_int),
+            "dsanls_get_gram": ([vp, i32, vp, vp], ctypes.c_int),
+            "dsanls_sync": ([vp], ctypes.c_int),
+            "dsanls_last_error": ([vp], ctypes.c_char_p),
+            "dsanls_destroy": ([vp], None),
+            "dsanls_philox_field": ([u64, u32, u64, i64, i64, vp, vp], ctypes.c_int),
+            "dsanls_gaussian_field": ([u64, u32, u64, i64, i64, ctypes.c_float, i32, vp, vp], ctypes.c_int),
+            "dsanls_uniform_field": ([u64, u32, u64, i64, i64, vp, vp], ctypes.c_int),
+            "dsanls_subsample_indices": ([u64, u32, u64, i64, i32, vp, vp], ctypes.c_int),
+            "dsanls_profile_half_step": ([vp, i32, i32, vp], ctypes.c_int),
+            "dsanls_kernel_launches": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(code, what="", handle=None):
+    if code != OK:
+        msg = what
+        if handle is not None:
+            m = lib().dsanls_last_error(handle)
+            msg = (m.decode() if m else "") or what
+        raise DSANLSError(code, msg)
+
+
+def _dev_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# stateless primitives (outputs are torch CUDA tensors)
+# ---------------------------------------------------------------------------
+
+def kernel_launches():
+    """Cumulative kernel launches issued by libdsanls in this process."""
+    v = ctypes.c_uint64()
+    _check(lib().dsanls_kernel_launches(ctypes.byref(v)), "kernel_launches")
+    return v.value
+
+
+def philox_field(seed, stream_id, t, rows, cols, device="cuda"):
+    torch = _torch()
+    out = torch.empty((rows, cols), dtype=torch.int32, device=device)
+    _check(lib().dsanls_philox_field(seed, stream_id, t, rows, cols, _dev_ptr(out), _stream_ptr()), "philox_field")
+    return out
+
+
+def gaussian_field(seed, stream_id, t, rows, cols, scale, transposed=False, device="cuda"):
+    torch = _torch()
+    shape = (cols, rows) if transposed else (rows, cols)
+    out = torch.empty(shape, dtype=torch.float32, device=device)
+    _check(lib().dsanls_gaussian_field(seed, stream_id, t, rows, cols, float(scale), int(bool(transposed)),
+                                       _dev_ptr(out), _stream_ptr()), "gaussian_field")
+    return out
+
+
+def uniform_field(seed, stream_id, t, rows, cols, device="cuda"):
+    torch = _torch()
+    out = torch.empty((rows, cols), dtype=torch.float32, device=device)
+    _check(lib().dsanls_uniform_field(seed, stream_id, t, rows, cols, _dev_ptr(out), _stream_ptr()), "uniform_field")
+    return out
+
+
+def subsample_indices(seed, side, t, n, d, device="cuda"):
+    torch = _torch()
+    out = torch.empty((d,), dtype=torch.int32, device=device)
+    _check(lib().dsanls_subsample_indices(seed, side, t, n, d, _dev_ptr(out), _stream_ptr()), "subsample_indices")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# handle
+# ---------------------------------------------------------------------------
+
+def _host_or_device(a, dtype):
+    """Returns (pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != dtype[1]:
+                raise TypeError("expected %s" % dtype[1])
+            a = a.contiguous()
+            if a.is_cuda:
+                return ctypes.c_void_p(a.data_ptr()), 1, a
+            return ctypes.c_void_p(a.data_ptr()), 0, a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a, dtype=dtype[0])
+    return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+def _dt(kind):
+    torch = _torch()
+    return {"f32": (np.float32, torch.float32), "i32": (np.int32, torch.int32), "i64": (np.int64, torch.int64)}[kind]
+
+
+class DSANLS:
+    """One factorisation problem M (m x n) ~ U V^T of rank k on the current CUDA device."""
+
+    def __init__(self, m, n, k, d, sketch=GAUSSIAN, seed=0, **options):
+        h = ctypes.c_void_p()
+        _check(lib().dsanls_create(m, n, k, d, sketch, seed, ctypes.byref(h)), "dsanls_create(%d,%d,%d,%d)" % (m, n, k, d))
+        self._h = h
+        self.m, self.n, self.k, self.d, self.sketch, self.seed = m, n, k, d, sketch, seed
+        if options:
+            self.set_options(**options)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dsanls_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- options
+    def options(self):
+        o = Options()
+        _check(lib().dsanls_get_options(self._h, ctypes.byref(o)), "get_options", self._h)
+        return o
+
+    def set_options(self, stream="current", **kw):
+        o = self.options()
+        for key, v in kw.items():
+            if not hasattr(o, key) or key == "stream":
+                raise TypeError("unknown option %r" % key)
+            setattr(o, key, v)
+        if stream == "current":
+            o.stream = _stream_ptr().value
+        elif stream is None:
+            o.stream = None
+        else:
+            o.stream = stream.cuda_stream
+        _check(lib().dsanls_set_options(self._h, ctypes.byref(o)), "set_options", self._h)
+
+    # -- data
+    def set_dense(self, M):
+        p, on_dev, keep = _host_or_device(M, _dt("f32"))
+        if tuple(keep.shape) != (self.m, self.n):
+            raise ValueError("M must be %d x %d" % (self.m, self.n))
+        _check(lib().dsanls_set_dense(self._h, p, self.n, on_dev), "set_dense", self._h)
+
+    def set_csr(self, rowptr, col, val, t_rowptr=None, t_col=None, t_val=None):
+        rp, dev, k1 = _host_or_device(rowptr, _dt("i64"))
+        cp, _, k2 = _host_or_device(col, _dt("i32"))
+        vp, _, k3 = _host_or_device(val, _dt("f32"))
+        nnz = int(k2.shape[0])
+        if t_rowptr is not None:
+            trp, _, k4 = _host_or_device(t_rowptr, _dt("i64"))
+            tcp, _, k5 = _host_or_device(t_col, _dt("i32"))
+            tvp, _, k6 = _host_or_device(t_val, _dt("f32"))
+        else:
+            trp = tcp = tvp = None
+        _check(lib().dsanls_set_csr(self._h, rp, cp, vp, nnz, trp, tcp, tvp, dev), "set_csr", self._h)
+
+    def set_factors(self, U=None, V=None):
+        up, udev, ku = _host_or_device(U, _dt("f32")) if U is not None else (None, 0, None)
+        vp, vdev, kv = _host_or_device(V, _dt("f32")) if V is not None else (None, 0, None)
+        if U is not None and V is not None and udev != vdev:
+            raise ValueError("U and V must both be host or both device arrays")
+        _check(lib().dsanls_set_factors(self._h, up, vp, udev or vdev), "set_factors", self._h)
+
+    # -- iteration
+    def step(self, iters=1):
+        _check(lib().dsanls_step(self._h, int(iters)), "step", self._h)
+
+    def half_step(self, side):
+        _check(lib().dsanls_half_step(self._h, int(side)), "half_step", self._h)
+
+    def sync(self):
+        _check(lib().dsanls_sync(self._h), "sync", self._h)
+
+    def rel_error(self):
+        v = ctypes.c_double()
+        _check(lib().dsanls_rel_error(self._h, ctypes.byref(v)), "rel_error", self._h)
+        return v.value
+
+    def factors(self, out_U=None, out_V=None):
+        """Returns (U, V) as numpy arrays, or fills the given torch CUDA tensors."""
+        if out_U is not None or out_V is not None:
+            _check(lib().dsanls_get_factors(self._h, _dev_ptr(out_U) if out_U is not None else None,
+                                            _dev_ptr(out_V) if out_V is not None else None, 1), "get_factors", self._h)
+            return out_U, out_V
+        U = np.empty((self.m, self.k), dtype=np.float32)
+        V = np.empty((self.n, self.k), dtype=np.float32)
+        _check(lib().dsanls_get_factors(self._h, U.ctypes.data_as(ctypes.c_void_p),
+                                        V.ctypes.data_as(ctypes.c_void_p), 0), "get_factors", self._h)
+        return U, V
+
+    def profile_half_step(self, side, reps=1):
+        """Mean milliseconds per phase (dict) of `reps` half-steps of `side`."""
+        ms = np.zeros(NPHASES, dtype=np.float64)
+        _check(lib().dsanls_profile_half_step(self._h, int(side), int(reps), ms.ctypes.data_as(ctypes.c_void_p)),
+               "profile_half_step", self._h)
+        return dict(zip(PHASES, ms.tolist()))
+
+    def gram(self, side):
+        G = np.empty((self.k, self.k), dtype=np.float64)
+        eta = ctypes.c_double()
+        _check(lib().dsanls_get_gram(self._h, int(side), G.ctypes.data_as(ctypes.c_void_p), ctypes.byref(eta)),
+               "get_gram", self._h)
+        return G, eta.value

@@ -1,0 +1,857 @@
+// C ABI of libdsanls: handle state, buffer management and the orchestration
+// of one outer iteration of sketched ANLS (Alg. 1 with the sketched
+// subproblems of Section 3.2; the per-node body of Alg. 2 on one GPU).
+//
+// Per half-step (side 0: U against M and V; side 1: V against M^T and U):
+//   sketch (Gaussian field / Feistel subsample / identity)  -> S or J
+//   B = Y^T S                       (eq. def_A_B, "B^t = V^T S^t")
+//   R = (X S) B^T                   (gradient term A B^T, eq. gradient_descent)
+//   G = B B^T in FP64, eta_t        (eq. gradient_descent / reg_sub)
+//   fused NNLS update of Z          (PGD step or Alg. 3 sweep)
+// The iteration index t lives in device memory so that one captured CUDA
+// graph replays every iteration unchanged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dsanls.h"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "sparse.cuh"
+#include "tc_gemm.cuh"
+
+using namespace dsanls;
+
+namespace {
+
+template <typename T>
+void dalloc(T *&p, int64_t count) {
+    if (p) {
+        cudaFree(p);
+        p = nullptr;
+    }
+    if (count <= 0) return;
+    cudaError_t e = cudaMalloc((void **)&p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        throw std::bad_alloc();
+    }
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int kp_bucket(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 64 ? 64 : 128)); }
+
+constexpr int MAX_SPLITS = 32;
+constexpr int64_t WORK_ELEMS = 320ll * 128 * 128;
+
+}  // namespace
+
+struct dsanls_ctx {
+    int device = 0;
+    int64_t m = 0, n = 0;
+    int k = 0, d = 0;
+    int sketch = 0;
+    uint64_t seed = 0;
+    dsanls_options opt{};
+    int64_t t_host = 0;
+    cudaStream_t own_stream = nullptr;
+
+    // data
+    bool has_dense = false, has_sparse = false;
+    float *M = nullptr, *MT = nullptr;
+    __nv_bfloat16 *Mb = nullptr, *MTb = nullptr;
+    int64_t nnz = 0;
+    int64_t *rp = nullptr, *trp = nullptr;
+    int32_t *ci = nullptr, *tci = nullptr;
+    float *cv = nullptr, *tcv = nullptr;
+    std::vector<int64_t> h_rp, h_trp;  // host copies of the row pointers (capacity planning)
+
+    // factors
+    float *U = nullptr, *V = nullptr;
+
+    // workspaces (sized by prepare())
+    int64_t cfg_key[6] = {-1, -1, -1, -1, -1, -1};
+    float *S = nullptr;
+    __nv_bfloat16 *Sb = nullptr;
+    int32_t *J = nullptr;
+    float *A = nullptr;
+    float *W = nullptr;
+    float *Wpart = nullptr;
+    float *R = nullptr;
+    float *Rpart = nullptr;
+    double *G64[2] = {nullptr, nullptr};
+    double *scal[2] = {nullptr, nullptr};
+    float *Gf = nullptr;
+    double *work = nullptr;
+    int64_t *t_dev = nullptr;
+    int *flag = nullptr;
+    double *dscal = nullptr;  // [0] ||M||^2, [1] residual^2, [2] cross, [3..] Gram of U, Gram of V
+    SubCsr sub;
+    float bound = 0.0f;
+
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+    uint64_t graph_launches = 0;  // kernels per captured outer iteration
+    std::string err;
+
+    cudaStream_t stream() const { return opt.stream ? (cudaStream_t)opt.stream : own_stream; }
+};
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename F>
+int guarded(dsanls_ctx *h, F &&body) {
+    try {
+        return body();
+    } catch (const CudaError &e) {
+        if (h) h->err = std::string("CUDA error: ") + cudaGetErrorString(e.err) + " (" + e.where + ")";
+        cudaGetLastError();
+        return DSANLS_ECUDA;
+    } catch (const ArgError &e) {
+        if (h) h->err = e.what;
+        return DSANLS_EINVAL;
+    } catch (const std::bad_alloc &) {
+        if (h) h->err = "out of memory";
+        return DSANLS_ENOMEM;
+    } catch (...) {
+        if (h) h->err = "unexpected internal error";
+        return DSANLS_ECUDA;
+    }
+}
+
+int fail(dsanls_ctx *h, int code, const std::string &msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+void check_sketch(int kind, int64_t K, int64_t dd, const char *what) {
+    if (dd < 1) throw ArgError{std::string(what) + " must be >= 1"};
+    if (kind == DSANLS_SKETCH_SUBSAMPLE && (dd > K || dd > 16384))
+        throw ArgError{std::string(what) + ": subsampling needs sketch size <= dimension and <= 16384"};
+    if (kind == DSANLS_SKETCH_IDENTITY && dd != K)
+        throw ArgError{std::string(what) + ": the identity sketch needs sketch size == dimension"};
+    if (dd > (1 << 30)) throw ArgError{std::string(what) + " too large"};
+}
+
+void invalidate_graph(dsanls_ctx *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_valid = false;
+}
+
+int d_v_of(const dsanls_ctx *h) { return h->opt.d_v > 0 ? h->opt.d_v : h->d; }
+
+// Sum of the `take` largest segment lengths of a CSR row pointer.
+int64_t top_lengths(const std::vector<int64_t> &ptr, int64_t take) {
+    std::vector<int64_t> len(ptr.size() - 1);
+    for (size_t i = 0; i + 1 < ptr.size(); ++i) len[i] = ptr[i + 1] - ptr[i];
+    take = std::min<int64_t>(take, (int64_t)len.size());
+    std::nth_element(len.begin(), len.begin() + (take > 0 ? take - 1 : 0), len.end(), std::greater<int64_t>());
+    int64_t s = 0;
+    for (int64_t i = 0; i < take; ++i) s += len[i];
+    return s;
+}
+
+// (Re)allocate the per-configuration workspaces.
+void prepare(dsanls_ctx *h) {
+    const int dv = d_v_of(h);
+    const int64_t key[6] = {h->sketch, h->d, dv, h->opt.precision, h->has_dense ? 1 : 0, h->has_sparse ? 1 : 0};
+    if (std::equal(key, key + 6, h->cfg_key)) return;
+    invalidate_graph(h);
+    const int64_t m = h->m, n = h->n, k = h->k;
+    const int64_t dmax = std::max<int64_t>(h->d, dv);
+    const bool gauss = h->sketch == DSANLS_SKETCH_GAUSSIAN;
+    const bool ident = h->sketch == DSANLS_SKETCH_IDENTITY;
+    const bool bf16 = h->opt.precision == DSANLS_PREC_BF16;
+    dalloc(h->S, gauss ? std::max(n * h->d, m * dv) : 0);
+    dalloc(h->Sb, (gauss && bf16) ? std::max(n * h->d, m * dv) : 0);
+    dalloc(h->J, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? dmax : 0);
+    dalloc(h->A, (gauss && !bf16) ? std::max(m * h->d, n * dv) : 0);
+    dalloc(h->W, k * (ident ? std::max(m, n) : dmax));
+    dalloc(h->Wpart, gauss ? (int64_t)MAX_SPLITS * k * dmax : 0);
+    dalloc(h->R, std::max(m, n) * k);
+    dalloc(h->Rpart, (gauss && bf16) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
+    if (h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE) {
+        const int64_t cap = std::max(top_lengths(h->h_trp, h->d), top_lengths(h->h_rp, dv));
+        const int64_t rows = std::max(m, n);
+        dalloc(h->sub.off, dmax + 1);
+        dalloc(h->sub.total, 1);
+        dalloc(h->sub.cnt, rows);
+        dalloc(h->sub.ptr, rows + 1);
+        dalloc(h->sub.bsum, ceil_div(rows, 4096) + 1);
+        dalloc(h->sub.col, std::max<int64_t>(cap, 1));
+        dalloc(h->sub.val, std::max<int64_t>(cap, 1));
+        h->sub.capacity = cap;
+    }
+    std::copy(key, key + 6, h->cfg_key);
+}
+
+// ---------------------------------------------------------------------------
+// one half-step
+// ---------------------------------------------------------------------------
+// Optional CUDA events at the phase boundaries of a half-step (profiling).
+struct PhaseEvents {
+    cudaEvent_t ev[DSANLS_NPHASES + 1];
+};
+
+inline void mark(PhaseEvents *pe, int i, cudaStream_t s) {
+    if (pe) DSANLS_CUDA(cudaEventRecord(pe->ev[i], s));
+}
+
+void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullptr) {
+    const int64_t rows = side == 0 ? h->m : h->n;
+    const int64_t K = side == 0 ? h->n : h->m;
+    const int dd = side == 0 ? h->d : d_v_of(h);
+    const int k = h->k;
+    float *Z = side == 0 ? h->U : h->V;
+    const float *Y = side == 0 ? h->V : h->U;
+    // data views: X = rows x K (M or M^T), XT = K x rows
+    const float *X = side == 0 ? h->M : h->MT;
+    const float *XT = side == 0 ? h->MT : h->M;
+    const int64_t *xp = side == 0 ? h->rp : h->trp;
+    const int32_t *xc = side == 0 ? h->ci : h->tci;
+    const float *xv = side == 0 ? h->cv : h->tcv;
+    const int64_t *xtp = side == 0 ? h->trp : h->rp;
+    const int32_t *xtc = side == 0 ? h->tci : h->ci;
+    const float *xtv = side == 0 ? h->tcv : h->cv;
+    const bool dense = h->has_dense;
+    int64_t gram_d = dd;
+
+    mark(pe, DSANLS_PHASE_SKETCH, s);
+    if (h->sketch == DSANLS_SKETCH_GAUSSIAN) {
+        const float scale = (float)(1.0 / std::sqrt((double)dd));
+        const bool tc = dense && h->opt.precision == DSANLS_PREC_BF16;
+        // S (K x dd), N(0, 1/dd) entries of the field, stream `side`
+        launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, s);
+        if (tc) launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, s);
+        mark(pe, DSANLS_PHASE_B, s);
+        // B = Y^T S  (k x dd), split over K, partials summed in order
+        {
+            const int64_t tiles = ceil_div(k, 128) * ceil_div(dd, 128);
+            int splits = (int)std::min<int64_t>(MAX_SPLITS, std::max<int64_t>(1, (2 * 152) / std::max<int64_t>(1, tiles)));
+            splits = (int)std::min<int64_t>(splits, std::max<int64_t>(1, K / 256));
+            GemmArgs g{};
+            g.M = k; g.N = dd; g.K = K;
+            g.A = Y; g.lda = k; g.ga = nullptr; g.a_kcontig = false;
+            g.B = h->S; g.ldb = dd; g.gb = nullptr; g.b_kcontig = false;
+            g.C = h->Wpart; g.ldc = dd; g.alpha = 1.0f; g.splits = splits; g.c_split_stride = (int64_t)k * dd;
+            launch_sgemm(g, s);
+            launch_split_reduce(h->Wpart, (int64_t)k * dd, splits, k, dd, dd, h->W, dd, s);
+        }
+        mark(pe, DSANLS_PHASE_PRODUCT, s);
+        if (tc) {
+            // R = (X S) B^T on tcgen05, X and S in bf16, A never stored
+            const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
+            launch_tc_sketch_rhs(Xb, h->Sb, h->W, rows, K, dd, k, h->Rpart, h->R, s);
+            mark(pe, DSANLS_PHASE_RHS, s);
+        } else {
+            if (dense) {
+                GemmArgs g{};
+                g.M = rows; g.N = dd; g.K = K;
+                g.A = X; g.lda = K; g.a_kcontig = true;
+                g.B = h->S; g.ldb = dd; g.b_kcontig = false;
+                g.C = h->A; g.ldc = dd; g.alpha = 1.0f; g.splits = 1;
+                launch_sgemm(g, s);
+            } else {
+                launch_spmm_rows(xp, xc, xv, rows, h->S, dd, dd, 1.0f, h->A, dd, s);
+            }
+            mark(pe, DSANLS_PHASE_RHS, s);
+            GemmArgs g{};
+            g.M = rows; g.N = k; g.K = dd;
+            g.A = h->A; g.lda = dd; g.a_kcontig = true;
+            g.B = h->W; g.ldb = dd; g.b_kcontig = true;
+            g.C = h->R; g.ldc = k; g.alpha = 1.0f; g.splits = 1;
+            launch_sgemm(g, s);
+        }
+    } else if (h->sketch == DSANLS_SKETCH_SUBSAMPLE) {
+        const float c = (float)std::sqrt((double)K / (double)dd);
+        const float c2 = c * c;
+        launch_subsample(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, h->J, s);
+        mark(pe, DSANLS_PHASE_B, s);
+        launch_gather_w(Y, k, h->J, dd, c, h->W, s);
+        mark(pe, DSANLS_PHASE_PRODUCT, s);
+        if (dense) {
+            GemmArgs g{};
+            g.M = rows; g.N = k; g.K = dd;
+            g.A = XT; g.lda = rows; g.ga = h->J; g.a_kcontig = false;
+            g.B = Y; g.ldb = k; g.gb = h->J; g.b_kcontig = false;
+            g.C = h->R; g.ldc = k; g.alpha = c2; g.splits = 1;
+            mark(pe, DSANLS_PHASE_RHS, s);
+            launch_sgemm(g, s);
+        } else {
+            launch_subcsr(xtp, xtc, xtv, h->J, dd, rows, h->sub, s);
+            mark(pe, DSANLS_PHASE_RHS, s);
+            launch_spmm_rows(h->sub.ptr, h->sub.col, h->sub.val, rows, Y, k, k, c2, h->R, k, s);
+        }
+    } else {  // identity
+        mark(pe, DSANLS_PHASE_B, s);
+        launch_transpose(Y, k, K, k, h->W, K, s);
+        gram_d = K;
+        mark(pe, DSANLS_PHASE_PRODUCT, s);
+        mark(pe, DSANLS_PHASE_RHS, s);
+        if (dense) {
+            GemmArgs g{};
+            g.M = rows; g.N = k; g.K = K;
+            g.A = X; g.lda = K; g.a_kcontig = true;
+            g.B = Y; g.ldb = k; g.b_kcontig = false;
+            g.C = h->R; g.ldc = k; g.alpha = 1.0f; g.splits = 1;
+            launch_sgemm(g, s);
+        } else {
+            launch_spmm_rows(xp, xc, xv, rows, Y, k, k, 1.0f, h->R, k, s);
+        }
+    }
+    mark(pe, DSANLS_PHASE_GRAM, s);
+    launch_gram(h->W, k, gram_d, h->G64[side], h->work, WORK_ELEMS, s);
+    const int kp = kp_bucket(k);
+    mark(pe, DSANLS_PHASE_STEP_SIZE, s);
+    launch_step_size(h->G64[side], k, h->opt.power_iters, h->opt.alpha, h->opt.beta, h->t_dev, h->scal[side], h->Gf,
+                     kp, s);
+    mark(pe, DSANLS_PHASE_UPDATE, s);
+    launch_update(h->opt.solver, Z, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->flag, s);
+    mark(pe, DSANLS_NPHASES, s);
+}
+
+void outer_iteration(dsanls_ctx *h, cudaStream_t s) {
+    half_step(h, 0, s);
+    half_step(h, 1, s);
+    launch_increment_t(h->t_dev, 1, s);
+}
+
+int check_ready(dsanls_ctx *h) {
+    if (!h->has_dense && !h->has_sparse) return fail(h, DSANLS_ESTATE, "no data: call dsanls_set_dense or dsanls_set_csr first");
+    return DSANLS_OK;
+}
+
+int pending_status(dsanls_ctx *h) {
+    DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
+    int flag = 0;
+    DSANLS_CUDA(cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        DSANLS_CUDA(cudaMemset(h->flag, 0, sizeof(int)));
+        return fail(h, DSANLS_ENUMERIC, "an update produced NaN or Inf");
+    }
+    return DSANLS_OK;
+}
+
+void copy_in(void *dst, const void *src, size_t bytes, int on_device, cudaStream_t s) {
+    DSANLS_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+void set_bound(dsanls_ctx *h) {
+    h->bound = 0.0f;
+    if (h->opt.bound_clamp && (h->has_dense || h->has_sparse)) {
+        double mm = 0.0;
+        DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
+        DSANLS_CUDA(cudaMemcpy(&mm, h->dscal + 0, sizeof(double), cudaMemcpyDeviceToHost));
+        h->bound = (float)std::sqrt(2.0 * std::sqrt(mm));
+    }
+}
+
+}  // namespace
+
+namespace dsanls {
+static std::atomic<uint64_t> g_launches{0};
+uint64_t launch_count() { return g_launches.load(); }
+void add_launches(uint64_t n) { g_launches.fetch_add(n); }
+
+void prime_kernel_attributes() {
+    static bool done = false;
+    if (done) return;
+    int dev = 0, max_smem = 0;
+    DSANLS_CUDA(cudaGetDevice(&dev));
+    DSANLS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    prime_rng_attributes(max_smem);
+    prime_solver_attributes(max_smem);
+    prime_tc_attributes();
+    done = true;
+}
+}  // namespace dsanls
+
+// ---------------------------------------------------------------------------
+// exported API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int dsanls_default_options(dsanls_options *opt) {
+    if (!opt) return DSANLS_EINVAL;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->solver = DSANLS_SOLVER_PGD;
+    opt->precision = DSANLS_PREC_FP32;
+    opt->d_v = 0;
+    opt->power_iters = 32;
+    opt->alpha = 1.0;
+    opt->beta = 1.0;
+    opt->t = 0;
+    opt->bound_clamp = 0;
+    opt->use_graph = 0;
+    opt->stream = nullptr;
+    return DSANLS_OK;
+}
+
+int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kind, uint64_t seed, dsanls_t *out) {
+    if (!out) return DSANLS_EINVAL;
+    *out = nullptr;
+    if (m < 1 || n < 1 || k < 1 || k > 128 || d < 1) return DSANLS_EINVAL;
+    if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return DSANLS_EINVAL;
+    if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_IDENTITY) return DSANLS_EINVAL;
+    if (sketch_kind == DSANLS_SKETCH_SUBSAMPLE && (d > n || d > 16384)) return DSANLS_EINVAL;
+    if (sketch_kind == DSANLS_SKETCH_IDENTITY && d != n) return DSANLS_EINVAL;
+    dsanls_ctx *h = nullptr;
+    try {
+        h = new dsanls_ctx();
+    } catch (...) {
+        return DSANLS_ENOMEM;
+    }
+    h->m = m; h->n = n; h->k = k; h->d = d; h->sketch = sketch_kind; h->seed = seed;
+    dsanls_default_options(&h->opt);
+    if (sketch_kind == DSANLS_SKETCH_IDENTITY) h->opt.d_v = (int32_t)m;
+    const int rc = guarded(h, [&]() {
+        DSANLS_CUDA(cudaGetDevice(&h->device));
+        DSANLS_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+        prime_kernel_attributes();
+        cudaStream_t s = h->stream();
+        dalloc(h->U, m * k);
+        dalloc(h->V, n * k);
+        for (int side = 0; side < 2; ++side) {
+            dalloc(h->G64[side], (int64_t)k * k);
+            dalloc(h->scal[side], 4);
+            DSANLS_CUDA(cudaMemsetAsync(h->G64[side], 0, sizeof(double) * k * k, s));
+            DSANLS_CUDA(cudaMemsetAsync(h->scal[side], 0, sizeof(double) * 4, s));
+        }
+        dalloc(h->Gf, 128 * 128);
+        dalloc(h->work, WORK_ELEMS);
+        dalloc(h->t_dev, 1);
+        dalloc(h->flag, 1);
+        dalloc(h->dscal, 3 + 2 * 128 * 128);
+        DSANLS_CUDA(cudaMemsetAsync(h->t_dev, 0, sizeof(int64_t), s));
+        DSANLS_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        DSANLS_CUDA(cudaMemsetAsync(h->dscal, 0, sizeof(double) * 3, s));
+        launch_uniform_field(seed, DSANLS_STREAM_INIT_U, 0, m, k, h->U, s);
+        launch_uniform_field(seed, DSANLS_STREAM_INIT_V, 0, n, k, h->V, s);
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        return DSANLS_OK;
+    });
+    if (rc != DSANLS_OK) {
+        dsanls_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return DSANLS_OK;
+}
+
+int dsanls_get_options(dsanls_t h, dsanls_options *opt) {
+    if (!h || !opt) return DSANLS_EINVAL;
+    *opt = h->opt;
+    opt->t = h->t_host;
+    return DSANLS_OK;
+}
+
+int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
+    if (!h) return DSANLS_EINVAL;
+    if (!opt) return fail(h, DSANLS_EINVAL, "options pointer is NULL");
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        if (opt->solver != DSANLS_SOLVER_PGD && opt->solver != DSANLS_SOLVER_RCD) throw ArgError{"unknown solver"};
+        if (opt->precision != DSANLS_PREC_FP32 && opt->precision != DSANLS_PREC_BF16) throw ArgError{"unknown precision"};
+        if (opt->precision == DSANLS_PREC_BF16 &&
+            (h->has_sparse || h->sketch != DSANLS_SKETCH_GAUSSIAN || !tc_supported(h->k)))
+            throw ArgError{"BF16 precision needs dense data, a Gaussian sketch and k a multiple of 16 up to 128"};
+        if (opt->power_iters < 0 || opt->power_iters > 10000) throw ArgError{"power_iters out of range"};
+        if (!(opt->alpha >= 0.0) || !(opt->beta >= 0.0) || !std::isfinite(opt->alpha) || !std::isfinite(opt->beta))
+            throw ArgError{"alpha and beta must be finite and >= 0"};
+        if (opt->t < 0) throw ArgError{"t must be >= 0"};
+        const int dv = opt->d_v > 0 ? opt->d_v : h->d;
+        check_sketch(h->sketch, h->m, dv, "d_v");
+        const bool cfg_change = (opt->precision != h->opt.precision) || (dv != d_v_of(h)) ||
+                                (opt->stream != h->opt.stream) || (opt->solver != h->opt.solver) ||
+                                (opt->power_iters != h->opt.power_iters) || (opt->alpha != h->opt.alpha) ||
+                                (opt->beta != h->opt.beta) || (opt->bound_clamp != h->opt.bound_clamp) ||
+                                (opt->use_graph != h->opt.use_graph);
+        // finish work queued on the old stream before switching
+        DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
+        h->opt = *opt;
+        if (cfg_change) invalidate_graph(h);
+        if (h->opt.precision == DSANLS_PREC_BF16 && h->has_dense && !h->Mb) {
+            dalloc(h->Mb, h->m * h->n);
+            dalloc(h->MTb, h->m * h->n);
+            launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, h->stream());
+            launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, h->stream());
+        }
+        if (opt->t != h->t_host) {
+            h->t_host = opt->t;
+            DSANLS_CUDA(cudaMemcpyAsync(h->t_dev, &h->t_host, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream()));
+        }
+        set_bound(h);
+        DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device) {
+    if (!h) return DSANLS_EINVAL;
+    if (!M || ld < h->n) return fail(h, DSANLS_EINVAL, "M is NULL or ld < n");
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        cudaStream_t s = h->stream();
+        if (h->has_sparse) {
+            dfree(h->rp); dfree(h->ci); dfree(h->cv); dfree(h->trp); dfree(h->tci); dfree(h->tcv);
+            h->has_sparse = false;
+        }
+        if (!h->M) dalloc(h->M, h->m * h->n);
+        if (!h->MT) dalloc(h->MT, h->m * h->n);
+        DSANLS_CUDA(cudaMemcpy2DAsync(h->M, h->n * sizeof(float), M, ld * sizeof(float), h->n * sizeof(float), h->m,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        launch_transpose(h->M, h->n, h->m, h->n, h->MT, h->m, s);
+        launch_sumsq(h->M, h->m * h->n, h->work, WORK_ELEMS, h->dscal + 0, s);
+        h->has_dense = true;
+        dfree(h->Mb);
+        dfree(h->MTb);
+        if (h->opt.precision == DSANLS_PREC_BF16) {
+            dalloc(h->Mb, h->m * h->n);
+            dalloc(h->MTb, h->m * h->n);
+            launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, s);
+            launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, s);
+        }
+        invalidate_graph(h);
+        std::fill(h->cfg_key, h->cfg_key + 6, -1);
+        set_bound(h);
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_set_csr(dsanls_t h, const int64_t *rowptr, const int32_t *col, const float *val, int64_t nnz,
+                   const int64_t *t_rowptr, const int32_t *t_col, const float *t_val, int32_t on_device) {
+    if (!h) return DSANLS_EINVAL;
+    if (!rowptr || nnz < 0 || (nnz > 0 && (!col || !val))) return fail(h, DSANLS_EINVAL, "bad CSR pointers");
+    if (t_rowptr && (nnz > 0 && (!t_col || !t_val))) return fail(h, DSANLS_EINVAL, "bad transposed CSR pointers");
+    if (!t_rowptr && on_device) return fail(h, DSANLS_EINVAL, "device CSR input needs the transposed CSR too");
+    if (h->opt.precision == DSANLS_PREC_BF16) return fail(h, DSANLS_EINVAL, "BF16 precision needs dense data");
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        cudaStream_t s = h->stream();
+        const int64_t m = h->m, n = h->n;
+        // host copies of the row pointers (validation and capacity planning)
+        h->h_rp.assign(m + 1, 0);
+        h->h_trp.assign(n + 1, 0);
+        std::vector<int32_t> hcol, htcol;
+        std::vector<float> hval, htval;
+        if (on_device) {
+            DSANLS_CUDA(cudaMemcpy(h->h_rp.data(), rowptr, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            DSANLS_CUDA(cudaMemcpy(h->h_trp.data(), t_rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(h->h_rp.data(), rowptr, (m + 1) * sizeof(int64_t));
+        }
+        if (h->h_rp[0] != 0 || h->h_rp[m] != nnz) throw ArgError{"rowptr[0] must be 0 and rowptr[m] == nnz"};
+        for (int64_t i = 0; i < m; ++i)
+            if (h->h_rp[i + 1] < h->h_rp[i]) throw ArgError{"rowptr must be nondecreasing"};
+        const int32_t *tc_src = t_col;
+        const float *tv_src = t_val;
+        if (!on_device) {
+            for (int64_t e = 0; e < nnz; ++e)
+                if (col[e] < 0 || col[e] >= n) throw ArgError{"column index out of range"};
+            if (t_rowptr) {
+                std::memcpy(h->h_trp.data(), t_rowptr, (n + 1) * sizeof(int64_t));
+                if (h->h_trp[0] != 0 || h->h_trp[n] != nnz) throw ArgError{"t_rowptr[0] must be 0 and t_rowptr[n] == nnz"};
+                for (int64_t j = 0; j < n; ++j)
+                    if (h->h_trp[j + 1] < h->h_trp[j]) throw ArgError{"t_rowptr must be nondecreasing"};
+                for (int64_t e = 0; e < nnz; ++e)
+                    if (t_col[e] < 0 || t_col[e] >= m) throw ArgError{"transposed column index out of range"};
+            } else {
+                // counting-sort transpose; rows come out in increasing order within each column
+                for (int64_t e = 0; e < nnz; ++e) h->h_trp[col[e] + 1]++;
+                for (int64_t j = 0; j < n; ++j) h->h_trp[j + 1] += h->h_trp[j];
+                htcol.resize(nnz);
+                htval.resize(nnz);
+                std::vector<int64_t> cur(h->h_trp.begin(), h->h_trp.end() - 1);
+                for (int64_t i = 0; i < m; ++i)
+                    for (int64_t e = h->h_rp[i]; e < h->h_rp[i + 1]; ++e) {
+                        const int64_t pos = cur[col[e]]++;
+                        htcol[pos] = (int32_t)i;
+                        htval[pos] = val[e];
+                    }
+                tc_src = htcol.data();
+                tv_src = htval.data();
+            }
+        } else if (h->h_trp[0] != 0 || h->h_trp[n] != nnz) {
+            throw ArgError{"t_rowptr[0] must be 0 and t_rowptr[n] == nnz"};
+        }
+        if (h->has_dense) {
+            dfree(h->M); dfree(h->MT); dfree(h->Mb); dfree(h->MTb);
+            h->has_dense = false;
+        }
+        dalloc(h->rp, m + 1);
+        dalloc(h->trp, n + 1);
+        dalloc(h->ci, std::max<int64_t>(nnz, 1));
+        dalloc(h->cv, std::max<int64_t>(nnz, 1));
+        dalloc(h->tci, std::max<int64_t>(nnz, 1));
+        dalloc(h->tcv, std::max<int64_t>(nnz, 1));
+        DSANLS_CUDA(cudaMemcpyAsync(h->rp, h->h_rp.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        DSANLS_CUDA(cudaMemcpyAsync(h->trp, h->h_trp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        if (nnz > 0) {
+            copy_in(h->ci, col, nnz * sizeof(int32_t), on_device, s);
+            copy_in(h->cv, val, nnz * sizeof(float), on_device, s);
+            copy_in(h->tci, tc_src, nnz * sizeof(int32_t), on_device, s);
+            copy_in(h->tcv, tv_src, nnz * sizeof(float), on_device, s);
+        }
+        h->nnz = nnz;
+        launch_sumsq(h->cv, nnz, h->work, WORK_ELEMS, h->dscal + 0, s);
+        h->has_sparse = true;
+        invalidate_graph(h);
+        std::fill(h->cfg_key, h->cfg_key + 6, -1);
+        set_bound(h);
+        DSANLS_CUDA(cudaStreamSynchronize(s));  // host staging buffers go out of scope
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_set_factors(dsanls_t h, const float *U, const float *V, int32_t on_device) {
+    if (!h) return DSANLS_EINVAL;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        cudaStream_t s = h->stream();
+        if (U) copy_in(h->U, U, (size_t)h->m * h->k * sizeof(float), on_device, s);
+        if (V) copy_in(h->V, V, (size_t)h->n * h->k * sizeof(float), on_device, s);
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_step(dsanls_t h, int32_t outer_iters) {
+    if (!h) return DSANLS_EINVAL;
+    if (outer_iters < 0) return fail(h, DSANLS_EINVAL, "outer_iters < 0");
+    if (int rc = check_ready(h)) return rc;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        cudaStream_t s = h->stream();
+        prepare(h);
+        if (h->opt.use_graph) {
+            if (!h->graph_valid) {
+                cudaGraph_t g = nullptr;
+                const uint64_t before = launch_count();
+                DSANLS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                try {
+                    outer_iteration(h, s);
+                } catch (...) {
+                    cudaGraph_t dummy = nullptr;
+                    cudaStreamEndCapture(s, &dummy);
+                    if (dummy) cudaGraphDestroy(dummy);
+                    throw;
+                }
+                DSANLS_CUDA(cudaStreamEndCapture(s, &g));
+                h->graph_launches = launch_count() - before;
+                add_launches(0 - h->graph_launches);  // captured, not run
+                cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
+                cudaGraphDestroy(g);
+                DSANLS_CUDA(e);
+                h->graph_valid = true;
+            }
+            for (int it = 0; it < outer_iters; ++it) DSANLS_CUDA(cudaGraphLaunch(h->graph, s));
+            add_launches(h->graph_launches * (uint64_t)outer_iters);
+        } else {
+            for (int it = 0; it < outer_iters; ++it) outer_iteration(h, s);
+        }
+        h->t_host += outer_iters;
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_half_step(dsanls_t h, int32_t side) {
+    if (!h) return DSANLS_EINVAL;
+    if (side != 0 && side != 1) return fail(h, DSANLS_EINVAL, "side must be 0 or 1");
+    if (int rc = check_ready(h)) return rc;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        prepare(h);
+        half_step(h, side, h->stream());
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_rel_error(dsanls_t h, double *out) {
+    if (!h) return DSANLS_EINVAL;
+    if (!out) return fail(h, DSANLS_EINVAL, "out is NULL");
+    if (int rc = check_ready(h)) return rc;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        cudaStream_t s = h->stream();
+        if (h->has_dense) {
+            launch_dense_residual(h->M, h->n, h->U, h->V, h->m, h->n, h->k, h->work, WORK_ELEMS, h->dscal + 1, s);
+        } else {
+            double *GU = h->dscal + 3, *GV = h->dscal + 3 + 128 * 128;
+            launch_sparse_cross(h->rp, h->ci, h->cv, h->m, h->U, h->V, h->k, h->work, WORK_ELEMS, h->dscal + 2, s);
+            launch_factor_gram(h->U, h->m, h->k, h->work, WORK_ELEMS, GU, s);
+            launch_factor_gram(h->V, h->n, h->k, h->work, WORK_ELEMS, GV, s);
+            launch_sparse_combine(h->dscal + 0, h->dscal + 2, GU, GV, h->k, h->dscal + 1, s);
+        }
+        if (int rc = pending_status(h)) return rc;
+        double v[2];
+        DSANLS_CUDA(cudaMemcpy(v, h->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+        *out = v[0] > 0.0 ? std::sqrt(std::max(v[1], 0.0) / v[0]) : 0.0;
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_get_factors(dsanls_t h, float *U, float *V, int32_t on_device) {
+    if (!h) return DSANLS_EINVAL;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        if (int rc = pending_status(h)) return rc;
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (U) DSANLS_CUDA(cudaMemcpyAsync(U, h->U, (size_t)h->m * h->k * sizeof(float), kind, h->stream()));
+        if (V) DSANLS_CUDA(cudaMemcpyAsync(V, h->V, (size_t)h->n * h->k * sizeof(float), kind, h->stream()));
+        DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_get_gram(dsanls_t h, int32_t side, double *G, double *eta) {
+    if (!h) return DSANLS_EINVAL;
+    if (side != 0 && side != 1) return fail(h, DSANLS_EINVAL, "side must be 0 or 1");
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        if (int rc = pending_status(h)) return rc;
+        if (G) DSANLS_CUDA(cudaMemcpy(G, h->G64[side], (size_t)h->k * h->k * sizeof(double), cudaMemcpyDeviceToHost));
+        if (eta) DSANLS_CUDA(cudaMemcpy(eta, h->scal[side] + 2, sizeof(double), cudaMemcpyDeviceToHost));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_sync(dsanls_t h) {
+    if (!h) return DSANLS_EINVAL;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() { return pending_status(h); });
+}
+
+int dsanls_profile_half_step(dsanls_t h, int32_t side, int32_t reps, double *ms) {
+    if (!h) return DSANLS_EINVAL;
+    if ((side != 0 && side != 1) || reps < 1 || !ms) return fail(h, DSANLS_EINVAL, "bad side, reps or output");
+    if (int rc = check_ready(h)) return rc;
+    DeviceGuard dg(h->device);
+    PhaseEvents pe;
+    int created = 0;
+    const int rc = guarded(h, [&]() {
+        prepare(h);
+        for (; created <= DSANLS_NPHASES; ++created) DSANLS_CUDA(cudaEventCreate(&pe.ev[created]));
+        cudaStream_t s = h->stream();
+        for (int i = 0; i < DSANLS_NPHASES; ++i) ms[i] = 0.0;
+        for (int r = 0; r < reps; ++r) {
+            half_step(h, side, s, &pe);
+            DSANLS_CUDA(cudaEventSynchronize(pe.ev[DSANLS_NPHASES]));
+            for (int i = 0; i < DSANLS_NPHASES; ++i) {
+                float t = 0.0f;
+                DSANLS_CUDA(cudaEventElapsedTime(&t, pe.ev[i], pe.ev[i + 1]));
+                ms[i] += t / reps;
+            }
+        }
+        return pending_status(h);
+    });
+    for (int i = 0; i < created; ++i) cudaEventDestroy(pe.ev[i]);
+    return rc;
+}
+
+int dsanls_kernel_launches(uint64_t *out) {
+    if (!out) return DSANLS_EINVAL;
+    *out = launch_count();
+    return DSANLS_OK;
+}
+
+const char *dsanls_last_error(dsanls_t h) {
+    if (!h) return "invalid handle";
+    return h->err.c_str();
+}
+
+void dsanls_destroy(dsanls_t h) {
+    if (!h) return;
+    {
+        DeviceGuard dg(h->device);
+        if (h->own_stream) cudaStreamSynchronize(h->own_stream);
+        if (h->opt.stream) cudaStreamSynchronize((cudaStream_t)h->opt.stream);
+        invalidate_graph(h);
+        dfree(h->M); dfree(h->MT); dfree(h->Mb); dfree(h->MTb);
+        dfree(h->rp); dfree(h->trp); dfree(h->ci); dfree(h->tci); dfree(h->cv); dfree(h->tcv);
+        dfree(h->U); dfree(h->V);
+        dfree(h->S); dfree(h->Sb); dfree(h->J); dfree(h->A); dfree(h->W); dfree(h->Wpart); dfree(h->R);
+        dfree(h->Rpart);
+        for (int side = 0; side < 2; ++side) {
+            dfree(h->G64[side]);
+            dfree(h->scal[side]);
+        }
+        dfree(h->Gf); dfree(h->work); dfree(h->t_dev); dfree(h->flag); dfree(h->dscal);
+        dfree(h->sub.off); dfree(h->sub.total); dfree(h->sub.cnt); dfree(h->sub.ptr); dfree(h->sub.bsum);
+        dfree(h->sub.col); dfree(h->sub.val);
+        if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    }
+    delete h;
+}
+
+// ---- stateless primitives ---------------------------------------------
+int dsanls_philox_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows, int64_t cols, uint32_t *out,
+                        void *stream) {
+    if (rows < 0 || cols < 0 || rows > (1ll << 34) || cols > (1ll << 31) - 1) return DSANLS_EINVAL;
+    if (rows * cols > 0 && !out) return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        launch_field_words(seed, stream_id, t, rows, cols, out, (cudaStream_t)stream);
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_gaussian_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows, int64_t cols, float scale,
+                          int32_t transposed, float *out, void *stream) {
+    if (rows < 0 || cols < 0 || rows > (1ll << 34) || cols > (1ll << 31) - 1) return DSANLS_EINVAL;
+    if (rows * cols > 0 && !out) return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out,
+                                     (cudaStream_t)stream);
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows, int64_t cols, float *out,
+                         void *stream) {
+    if (rows < 0 || cols < 0 || rows > (1ll << 34) || cols > (1ll << 31) - 1) return DSANLS_EINVAL;
+    if (rows * cols > 0 && !out) return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        launch_uniform_field(seed, stream_id, t, rows, cols, out, (cudaStream_t)stream);
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_subsample_indices(uint64_t seed, uint32_t side, uint64_t t, int64_t n, int32_t d, int32_t *J,
+                             void *stream) {
+    if (n < 1 || n > (1ll << 31) - 1 || d < 1 || d > n || d > 16384 || !J || side > 0xef) return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        launch_subsample(seed, side, t, nullptr, n, d, J, (cudaStream_t)stream);
+        return DSANLS_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Launchers of the hot-path kernels (host side declarations).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsanls {
+
+template <typename T>
+__device__ __forceinline__ T store_cast(float v);
+template <>
+__device__ __forceinline__ float store_cast<float>(float v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// Raise the dynamic shared-memory limit of every kernel that needs more than
+// 48 KB once per process (before any graph capture).
+void prime_kernel_attributes();
+void prime_rng_attributes(int max_smem);
+void prime_solver_attributes(int max_smem);
+
+// ---- rng.cu ---------------------------------------------------------------
+int feistel_half_bits(int64_t n);
+void launch_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, uint32_t *out,
+                        cudaStream_t s);
+template <typename OutT>
+void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_t *t_dev, int64_t rows,
+                           int64_t cols, float scale, bool transposed, OutT *out, cudaStream_t s);
+void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, float *out,
+                          cudaStream_t s);
+void launch_subsample(uint64_t seed, uint32_t side, uint64_t t, const int64_t *t_dev, int64_t n, int d,
+                      int32_t *J, cudaStream_t s);
+
+// ---- gemm_simt.cu ---------------------------------------------------------
+// C[i][j] = alpha * sum_l a(i,l) b(l,j) over l in [0,K), binary32 FMA chain in
+// increasing l (per split).  Operand access:
+//   a_kcontig: a(i,l) = A[i*lda + l]           else a(i,l) = A[ga(l)*lda + i]
+//   b_kcontig: b(l,j) = B[j*ldb + l]           else b(l,j) = B[gb(l)*ldb + j]
+// ga/gb are optional row-gather index arrays (nullptr = identity).
+// With splits > 1 the K range is cut into `splits` contiguous parts whose
+// partial products land in C + z*c_split_stride; reduce them with
+// launch_split_reduce (fixed order, deterministic).
+struct GemmArgs {
+    int64_t M, N, K;
+    const float *A;
+    int64_t lda;
+    const int32_t *ga;
+    bool a_kcontig;
+    const float *B;
+    int64_t ldb;
+    const int32_t *gb;
+    bool b_kcontig;
+    float *C;
+    int64_t ldc;
+    float alpha;
+    int splits;
+    int64_t c_split_stride;
+};
+void launch_sgemm(const GemmArgs &g, cudaStream_t s);
+// out[i*ldo + j] = sum_{z<splits} part[z*stride + i*ldp + j], z ascending.
+void launch_split_reduce(const float *part, int64_t stride, int splits, int64_t M, int64_t N, int64_t ldp,
+                         float *out, int64_t ldo, cudaStream_t s);
+
+// ---- solver.cu ------------------------------------------------------------
+// Gram G = W W^T (W k x d, row-major fp32) accumulated in FP64; partials over
+// d-chunks reduced in fixed order.  Writes G64 (k x k).
+void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, int64_t work_elems,
+                 cudaStream_t s);
+// lambda_max(G) by `iters` power iterations from the all-ones vector, mu_t =
+// alpha + beta t (t from t_dev), eta = 1/(lambda + mu).  Writes scal[0] =
+// lambda, scal[1] = mu, scal[2] = eta and the fp32 copy Gf (kp x kp, zero
+// padded; kp is the update kernel's padded width 16, 32, 64 or 128).
+void launch_step_size(const double *G64, int k, int iters, double alpha, double beta, const int64_t *t_dev,
+                      double *scal, float *Gf, int kp, cudaStream_t s);
+// Z <- max(0, Z - eta (Z G - R)) (PGD) or Alg. 3 sweep (RCD), rows x k,
+// optional clamp at `bound` (> 0).  Sets *flag = 1 when a NaN/Inf appears.
+void launch_update(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp,
+                   const double *scal, float bound, int *flag, cudaStream_t s);
+void launch_increment_t(int64_t *t_dev, int64_t by, cudaStream_t s);
+
+// ---- error.cu -------------------------------------------------------------
+// sum_ij (M_ij - U_i . V_j)^2 in FP64 -> *out (device), M m x n (row stride ld).
+void launch_dense_residual(const float *M, int64_t ld, const float *U, const float *V, int64_t m, int64_t n,
+                           int k, double *work, int64_t work_elems, double *out, cudaStream_t s);
+// sum of squares of x[0..len) in FP64 -> *out.
+void launch_sumsq(const float *x, int64_t len, double *work, int64_t work_elems, double *out, cudaStream_t s);
+// sparse: sum_nnz M_ij (U_i . V_j) -> *out (FP64)
+void launch_sparse_cross(const int64_t *rowptr, const int32_t *col, const float *val, int64_t m,
+                         const float *U, const float *V, int k, double *work, int64_t work_elems, double *out,
+                         cudaStream_t s);
+// X^T X (rows x k -> k x k) in FP64 -> out
+void launch_factor_gram(const float *X, int64_t rows, int k, double *work, int64_t work_elems, double *out,
+                        cudaStream_t s);
+// out = (||M||^2 - 2 cross + <GU, GV>) with the three device scalars/matrices
+void launch_sparse_combine(const double *mm, const double *cross, const double *GU, const double *GV, int k,
+                           double *out, cudaStream_t s);
+
+// ---- dense_ops.cu ---------------------------------------------------------
+// out[j*ldo + i] = in[i*ldi + j] (rows x cols -> cols x rows)
+void launch_transpose(const float *in, int64_t ldi, int64_t rows, int64_t cols, float *out, int64_t ldo,
+                      cudaStream_t s);
+// W[c][p] = scale * Y[J[p]][c]  (k x d)
+void launch_gather_w(const float *Y, int k, const int32_t *J, int d, float scale, float *W, cudaStream_t s);
+// W = Y^T (k x K) for the identity sketch
+void launch_copy_cast_bf16(const float *in, int64_t n, __nv_bfloat16 *out, cudaStream_t s);
+
+// ---- sparse.cu ------------------------------------------------------------
+// out[i][0..w) = alpha * sum_{e in row i} val_e * D[col_e*ldd + 0..w)
+void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
+                      const float *D, int64_t ldd, int w, float alpha, float *out, int64_t ldo, cudaStream_t s);
+
+}  // namespace dsanls

@@ -1,0 +1,192 @@
+// Random sketches S^t, S'^t and default initial factors (Section 3.4;
+// shared-seed regeneration of Section 3.3).
+//
+//  * field words, Gaussian and uniform fields: one thread per Philox block
+//    (four consecutive rows of one column).  The Gaussian field can be
+//    written as S (rows x cols) or S^T (cols x rows); the transposed form puts
+//    the four values of a block next to each other (one 16-byte store).
+//  * subsampling: d indices pi(0..d-1) of a keyed 4-round Feistel permutation
+//    on 2h-bit words restricted to {0..n-1} by cycle walking (Black and
+//    Rogaway 2002), then sorted ascending in one CTA (bitonic network in
+//    shared memory).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace dsanls {
+
+__global__ void k_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols,
+                              uint32_t *out) {
+    const int64_t nb4 = (rows + 3) >> 2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nb4 * cols) return;
+    const int64_t q = idx % nb4;
+    const int64_t j = idx / nb4;
+    const Philox4 b = field_block(seed, sid, t, (uint32_t)q, (uint32_t)j);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = 4 * q + r;
+        if (i < rows) out[i * cols + j] = word_of(b, r);
+    }
+}
+
+// t is read from device memory when t_dev != nullptr (graph replays).
+template <bool TRANSPOSED, typename OutT>
+__global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, const int64_t *t_dev,
+                                 int64_t rows, int64_t cols, float scale, OutT *out) {
+    const int64_t nb4 = (rows + 3) >> 2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nb4 * cols) return;
+    const uint64_t t = t_dev ? (uint64_t)*t_dev : t_host;
+    int64_t q, j;
+    if (TRANSPOSED) {  // consecutive threads walk the rows of one column: contiguous S^T stores
+        q = idx % nb4;
+        j = idx / nb4;
+    } else {  // consecutive threads walk the columns of four rows: contiguous S stores
+        j = idx % cols;
+        q = idx / cols;
+    }
+    float z[4];
+    gaussian4(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) z[r] = __fmul_rn(z[r], scale);
+    const int64_t i0 = 4 * q;
+    if (TRANSPOSED) {
+        OutT *dst = out + j * rows + i0;
+        if (sizeof(OutT) == 4 && i0 + 3 < rows && (rows & 3) == 0) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(z[0], z[1], z[2], z[3]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (i0 + r < rows) dst[r] = store_cast<OutT>(z[r]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (i0 + r < rows) out[(i0 + r) * cols + j] = store_cast<OutT>(z[r]);
+    }
+}
+
+__global__ void k_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols,
+                                float *out) {
+    const int64_t nb4 = (rows + 3) >> 2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nb4 * cols) return;
+    const int64_t j = idx % cols;
+    const int64_t q = idx / cols;
+    const Philox4 b = field_block(seed, sid, t, (uint32_t)q, (uint32_t)j);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = 4 * q + r;
+        if (i < rows) out[i * cols + j] = uniform01(word_of(b, r));
+    }
+}
+
+DSANLS_DEV uint32_t feistel_pass(uint64_t seed, uint32_t side, uint64_t t, int h, uint32_t x) {
+    const uint32_t mask = (1u << h) - 1u;
+    uint32_t L = x >> h, R = x & mask;
+    const uint32_t c3 = ((0x10u | side) & 0xffu) | ((uint32_t)(t >> 32) << 8);
+#pragma unroll
+    for (uint32_t round = 0; round < 4; ++round) {
+        const Philox4 b = philox4x32_10(R, round, (uint32_t)t, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint32_t nr = L ^ (b.x & mask);
+        L = R;
+        R = nr;
+    }
+    return (L << h) | R;
+}
+
+// One CTA: pi(p) for p < d into shared memory, bitonic sort, write J.
+__global__ void k_subsample(uint64_t seed, uint32_t side, uint64_t t_host, const int64_t *t_dev,
+                            int64_t n, int d, int h, int cap, int32_t *J) {
+    extern __shared__ uint32_t sv[];
+    const uint64_t t = t_dev ? (uint64_t)*t_dev : t_host;
+    const uint64_t walk_limit = 1ull << (2 * h);
+    for (int p = threadIdx.x; p < cap; p += blockDim.x) {
+        uint32_t v = 0xffffffffu;
+        if (p < d) {
+            uint32_t x = (uint32_t)p;
+            // cycle walking: the orbit of p returns below n within 2^(2h) passes
+            for (uint64_t it = 0; it < walk_limit; ++it) {
+                x = feistel_pass(seed, side, t, h, x);
+                if ((int64_t)x < n) break;
+            }
+            v = x;
+        }
+        sv[p] = v;
+    }
+    __syncthreads();
+    for (int size = 2; size <= cap; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+                const int partner = i ^ stride;
+                if (partner > i) {
+                    const bool up = (i & size) == 0;
+                    const uint32_t a = sv[i], b = sv[partner];
+                    if ((a > b) == up) {
+                        sv[i] = b;
+                        sv[partner] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int p = threadIdx.x; p < d; p += blockDim.x) J[p] = (int32_t)sv[p];
+}
+
+void prime_rng_attributes(int max_smem) {
+    DSANLS_CUDA(cudaFuncSetAttribute(k_subsample, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+}
+
+int feistel_half_bits(int64_t n) {
+    int h = 1;
+    while (h < 16 && (1ll << (2 * h)) < n) ++h;
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+
+void launch_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols,
+                        uint32_t *out, cudaStream_t s) {
+    const int64_t total = ((rows + 3) >> 2) * cols;
+    if (total == 0) return;
+    k_field_words<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(seed, sid, t, rows, cols, out);
+    DSANLS_LAUNCH_CHECK();
+}
+
+template <typename OutT>
+void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_t *t_dev, int64_t rows,
+                           int64_t cols, float scale, bool transposed, OutT *out, cudaStream_t s) {
+    const int64_t total = ((rows + 3) >> 2) * cols;
+    if (total == 0) return;
+    const unsigned grid = (unsigned)ceil_div(total, 256);
+    if (transposed)
+        k_gaussian_field<true, OutT><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
+    else
+        k_gaussian_field<false, OutT><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
+    DSANLS_LAUNCH_CHECK();
+}
+template void launch_gaussian_field<float>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t, int64_t,
+                                           float, bool, float *, cudaStream_t);
+template void launch_gaussian_field<__nv_bfloat16>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t,
+                                                   int64_t, float, bool, __nv_bfloat16 *, cudaStream_t);
+
+void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, float *out,
+                          cudaStream_t s) {
+    const int64_t total = ((rows + 3) >> 2) * cols;
+    if (total == 0) return;
+    k_uniform_field<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(seed, sid, t, rows, cols, out);
+    DSANLS_LAUNCH_CHECK();
+}
+
+void launch_subsample(uint64_t seed, uint32_t side, uint64_t t, const int64_t *t_dev, int64_t n, int d,
+                      int32_t *J, cudaStream_t s) {
+    int cap = 1;
+    while (cap < d) cap <<= 1;
+    const int h = feistel_half_bits(n);
+    const size_t smem = (size_t)cap * sizeof(uint32_t);
+    k_subsample<<<1, 1024, smem, s>>>(seed, side, t, t_dev, n, d, h, cap, J);
+    DSANLS_LAUNCH_CHECK();
+}
+
+}  // namespace dsanls

@@ -1,0 +1,324 @@
+// Gram matrix, step size and the NNLS subproblem update (Section 3.5).
+//
+//  * G = B B^T (k x k) accumulated in FP64 from the binary32 sketch product
+//    B (k x d): chunks of d per CTA, products exact in FP64, chunk partials
+//    summed in a fixed order (deterministic).
+//  * step size of the projected gradient step: eta_t = 1/(lambda_max(G) +
+//    mu_t), mu_t = alpha + beta t; lambda_max by power iteration from the
+//    all-ones vector (binary32 iterations, FP64 Rayleigh quotient).
+//  * fused row update, one thread per row with the row held in registers and
+//    G in shared memory:
+//      PGD (eq. gradient_descent):  z <- max(0, z - eta (z G - r))
+//      RCD (Alg. 3, eq. entry_sol): for j: z_j <- max(0, (mu z_j + r_j -
+//           sum_{l != j} G_lj z_l) / (G_jj + mu)), in place, so columns l < j
+//           already hold their new values.
+//    Optional clamp at sqrt(2 ||M||_F) (eq. extra_con); a NaN/Inf before the
+//    projection raises a device flag that the host turns into an error.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace dsanls {
+
+// ---------------------------------------------------------------------------
+// Gram in FP64
+// ---------------------------------------------------------------------------
+constexpr int GRAM_THREADS = 256;
+constexpr int GRAM_MAXP = 33;  // pairs per thread: k(k+1)/2 <= 8256 < 33 * 256
+
+// Each CTA sums chunks blockIdx.x, blockIdx.x + gridDim.x, ... of the d axis
+// for every pair (a <= b); each thread owns up to GRAM_MAXP pairs with FP64
+// accumulators in registers.
+__global__ void __launch_bounds__(GRAM_THREADS)
+    k_gram_partial(const float *__restrict__ W, int k, int64_t d, int64_t dc, double *__restrict__ part) {
+    extern __shared__ float ws[];  // k x (dc + 1), padded against bank conflicts
+    const int64_t ldw = dc + 1;
+    const int npairs = k * (k + 1) / 2;
+    double acc[GRAM_MAXP];
+    int pa[GRAM_MAXP], pb[GRAM_MAXP];
+#pragma unroll
+    for (int q = 0; q < GRAM_MAXP; ++q) {
+        acc[q] = 0.0;
+        const int p = threadIdx.x + q * GRAM_THREADS;
+        int a = 0, rem = p;
+        if (p < npairs)
+            while (rem >= k - a) {
+                rem -= k - a;
+                ++a;
+            }
+        pa[q] = a;
+        pb[q] = a + rem;
+    }
+    const int64_t chunks = ceil_div(d, dc);
+    for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+        const int64_t j0 = ch * dc;
+        const int64_t len = min(dc, d - j0);
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)k * dc; e += GRAM_THREADS) {
+            const int a = (int)(e / dc);
+            const int64_t j = e % dc;
+            ws[a * ldw + j] = (j < len) ? W[(int64_t)a * d + j0 + j] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < GRAM_MAXP; ++q) {
+            if (threadIdx.x + q * GRAM_THREADS < npairs) {
+                const float *wa = ws + (int64_t)pa[q] * ldw;
+                const float *wb = ws + (int64_t)pb[q] * ldw;
+                double s = acc[q];
+                for (int64_t j = 0; j < len; ++j) s = fma((double)wa[j], (double)wb[j], s);
+                acc[q] = s;
+            }
+        }
+    }
+    double *out = part + (int64_t)blockIdx.x * k * k;
+#pragma unroll
+    for (int q = 0; q < GRAM_MAXP; ++q)
+        if (threadIdx.x + q * GRAM_THREADS < npairs) out[pa[q] * k + pb[q]] = acc[q];
+}
+
+__global__ void k_gram_reduce(const double *__restrict__ part, int nparts, int k, double *__restrict__ G) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= k * k) return;
+    const int a = idx / k, b = idx % k;
+    const int lo = min(a, b), hi = max(a, b);
+    double acc = 0.0;
+    for (int c = 0; c < nparts; ++c) acc += part[(int64_t)c * k * k + lo * k + hi];
+    G[idx] = acc;
+}
+
+void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, int64_t work_elems,
+                 cudaStream_t s) {
+    // chunk width: about two chunks per SM, at most ~200 KB of shared memory
+    int64_t dc = ceil_div(ceil_div(d, 2 * 152), 4) * 4;
+    const int64_t dc_max = (200 * 1024) / (4 * (int64_t)k) - 1;
+    if (dc > dc_max) dc = dc_max;
+    if (dc < 1) dc = 1;
+    int64_t grid = ceil_div(d, dc);
+    if (grid > work_elems / ((int64_t)k * k)) grid = work_elems / ((int64_t)k * k);
+    if (grid > 2 * 152) grid = 2 * 152;
+    if (grid < 1) grid = 1;
+    const size_t smem = (size_t)k * (dc + 1) * sizeof(float);
+    k_gram_partial<<<(unsigned)grid, GRAM_THREADS, smem, s>>>(W, k, d, dc, work);
+    DSANLS_LAUNCH_CHECK();
+    k_gram_reduce<<<(unsigned)ceil_div((int64_t)k * k, 256), 256, 0, s>>>(work, (int)grid, k, G64);
+    DSANLS_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// step size: lambda_max by power iteration, mu_t, eta_t
+// ---------------------------------------------------------------------------
+__device__ float block_sum_f(float v, float *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    float tot = 0.0f;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) tot += red[i];
+    return tot;
+}
+
+__device__ double block_sum_d(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double tot = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) tot += red[i];
+    return tot;
+}
+
+// blockDim.x == 128 >= k
+__global__ void k_step_size(const double *__restrict__ G64, int k, int iters, double alpha, double beta,
+                            const int64_t *__restrict__ t_dev, double *__restrict__ scal, float *__restrict__ Gf,
+                            int kp) {
+    extern __shared__ float gs[];  // k x (k+1)
+    __shared__ float x[128];
+    __shared__ float redf[4];
+    __shared__ double redd[4];
+    const int i = threadIdx.x;
+    for (int e = i; e < kp * kp; e += blockDim.x) {
+        const int a = e / kp, b = e % kp;
+        const float v = (a < k && b < k) ? (float)G64[a * k + b] : 0.0f;
+        Gf[e] = v;
+        if (a < k && b < k) gs[a * (k + 1) + b] = v;
+    }
+    if (i < 128) x[i] = (i < k) ? rsqrtf((float)k) : 0.0f;
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+        float y = 0.0f;
+        if (i < k)
+            for (int l = 0; l < k; ++l) y = fmaf(gs[i * (k + 1) + l], x[l], y);
+        const float nrm2 = block_sum_f(y * y, redf);
+        __syncthreads();
+        if (nrm2 > 0.0f && i < k) x[i] = y * rsqrtf(nrm2);
+        __syncthreads();
+        if (nrm2 == 0.0f) break;
+    }
+    // Rayleigh quotient x^T G x in FP64 with the FP64 G
+    double part = 0.0;
+    if (i < k) {
+        double gx = 0.0;
+        for (int l = 0; l < k; ++l) gx = fma(G64[i * k + l], (double)x[l], gx);
+        part = (double)x[i] * gx;
+    }
+    const double xgx = block_sum_d(part, redd);
+    double xx = block_sum_d(i < k ? (double)x[i] * (double)x[i] : 0.0, redd);
+    if (i == 0) {
+        const double lam = xx > 0.0 ? xgx / xx : 0.0;
+        const double t = (double)(*t_dev);
+        const double mu = alpha + beta * t;
+        scal[0] = lam;
+        scal[1] = mu;
+        scal[2] = 1.0 / (lam + mu);
+    }
+}
+
+void launch_step_size(const double *G64, int k, int iters, double alpha, double beta, const int64_t *t_dev,
+                      double *scal, float *Gf, int kp, cudaStream_t s) {
+    const size_t smem = (size_t)k * (k + 1) * sizeof(float);
+    k_step_size<<<1, 128, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
+    DSANLS_LAUNCH_CHECK();
+}
+
+__global__ void k_increment_t(int64_t *t, int64_t by) { *t += by; }
+
+void launch_increment_t(int64_t *t_dev, int64_t by, cudaStream_t s) {
+    k_increment_t<<<1, 1, 0, s>>>(t_dev, by);
+    DSANLS_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// fused row update
+// ---------------------------------------------------------------------------
+constexpr int UPD_ROWS = 128;
+
+DSANLS_DEV float project_clamp(float v, float bound, int *flag) {
+    if (!(fabsf(v) <= 3.402823466e38f)) {  // NaN or Inf
+        *flag = 1;
+        return 0.0f;
+    }
+    float r = v > 0.0f ? v : 0.0f;
+    if (bound > 0.0f) r = fminf(r, bound);
+    return r;
+}
+
+template <int KP, int SOLVER>
+__global__ void __launch_bounds__(UPD_ROWS)
+    k_update(float *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k, const float *__restrict__ Gf,
+             const double *__restrict__ scal, float bound, int *__restrict__ flag) {
+    extern __shared__ __align__(16) float sm[];
+    float *gs = sm;                 // KP x KP, gs[l*KP + c] = G[l][c]
+    float *zs = sm + KP * KP;       // UPD_ROWS x (k+1)
+    const int ldz = k + 1;
+    const int64_t r0 = (int64_t)blockIdx.x * UPD_ROWS;
+    const int nr = (int)min((int64_t)UPD_ROWS, rows - r0);
+    for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) gs[e] = Gf[e];
+    for (int e = threadIdx.x; e < nr * k; e += blockDim.x) {
+        const int i = e / k, c = e % k;
+        zs[i * ldz + c] = Z[(r0 + i) * k + c];
+    }
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i < nr) {
+        float z[KP];
+#pragma unroll
+        for (int l = 0; l < KP; ++l) z[l] = (l < k) ? zs[i * ldz + l] : 0.0f;
+        const float *r = R + (r0 + i) * k;
+        if (SOLVER == 0) {
+            const float eta = (float)scal[2];
+#pragma unroll 1
+            for (int c0 = 0; c0 < KP; c0 += 16) {
+                float acc[16];
+#pragma unroll
+                for (int cc = 0; cc < 16; ++cc) acc[cc] = 0.0f;
+#pragma unroll
+                for (int l = 0; l < KP; ++l) {
+                    const float zl = z[l];
+#pragma unroll
+                    for (int cc = 0; cc < 16; cc += 4) {
+                        const float4 g = *reinterpret_cast<const float4 *>(&gs[l * KP + c0 + cc]);
+                        acc[cc] = __fmaf_rn(zl, g.x, acc[cc]);
+                        acc[cc + 1] = __fmaf_rn(zl, g.y, acc[cc + 1]);
+                        acc[cc + 2] = __fmaf_rn(zl, g.z, acc[cc + 2]);
+                        acc[cc + 3] = __fmaf_rn(zl, g.w, acc[cc + 3]);
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < 16; ++cc) {
+                    const int c = c0 + cc;
+                    if (c < k) {
+                        const float zc = zs[i * ldz + c];  // not yet overwritten: column c belongs to this chunk
+                        const float grad = __fsub_rn(acc[cc], r[c]);
+                        zs[i * ldz + c] = project_clamp(__fmaf_rn(-eta, grad, zc), bound, flag);
+                    }
+                }
+            }
+        } else {
+            const float mu = (float)scal[1];
+#pragma unroll
+            for (int j = 0; j < KP; ++j) {
+                if (j < k) {
+                    float tj = __fmaf_rn(mu, z[j], r[j]);
+#pragma unroll
+                    for (int l = 0; l < KP; ++l)
+                        if (l != j) tj = __fmaf_rn(-gs[l * KP + j], z[l], tj);
+                    const float den = __fadd_rn(gs[j * KP + j], mu);
+                    z[j] = project_clamp(__fdiv_rn(tj, den), bound, flag);
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < KP; ++l)
+                if (l < k) zs[i * ldz + l] = z[l];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * k; e += blockDim.x) {
+        const int ii = e / k, c = e % k;
+        Z[(r0 + ii) * k + c] = zs[ii * ldz + c];
+    }
+}
+
+template <int KP>
+static void update_kp(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf,
+                      const double *scal, float bound, int *flag, cudaStream_t s) {
+    const size_t smem = (size_t)(KP * KP + UPD_ROWS * (k + 1)) * sizeof(float);
+    const unsigned grid = (unsigned)ceil_div(rows, UPD_ROWS);
+    if (solver == 0)
+        k_update<KP, 0><<<grid, UPD_ROWS, smem, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
+    else
+        k_update<KP, 1><<<grid, UPD_ROWS, smem, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
+    DSANLS_LAUNCH_CHECK();
+}
+
+void prime_solver_attributes(int max_smem) {
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    DSANLS_CUDA(cudaFuncSetAttribute(k_gram_partial, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_step_size, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<16, 0>, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<16, 1>, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<32, 0>, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<32, 1>, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<64, 0>, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<64, 1>, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<128, 0>, a, max_smem));
+    DSANLS_CUDA(cudaFuncSetAttribute(k_update<128, 1>, a, max_smem));
+}
+
+void launch_update(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp,
+                   const double *scal, float bound, int *flag, cudaStream_t s) {
+    if (rows <= 0) return;
+    if (kp <= 16)
+        update_kp<16>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+    else if (kp <= 32)
+        update_kp<32>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+    else if (kp <= 64)
+        update_kp<64>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+    else
+        update_kp<128>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+}
+
+}  // namespace dsanls

@@ -1,0 +1,283 @@
+"""Parity of the GPU half-steps and outer iterations with the FP64 oracle.
+
+Tolerance (binary32 path): norm-wise relative difference of the updated
+factor <= 1e-5 from an identical input state (U^t, V^t, t) -- the sketch values
+are bit-identical on both sides, so the difference is binary32 rounding of
+the products A = X S (length-n sums), B = Y^T S, R = A B^T and the update,
+i.e. O(sqrt(n) * 2^-24) relative, far below 1e-5 at these sizes.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import method, rng
+from synthdata import initial_factors, planted_dense, sparse_text
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2009_02845_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _oracle_half(M64, U, V, kind, solver, seed, t, side, d, alpha=1.0, beta=1.0, sparse=False):
+    X = M64 if side == 0 else M64.T
+    if sparse:
+        X = X.tocsr()
+    Y = V if side == 0 else U
+    Z = U if side == 0 else V
+    S = method.Sketch(kind, seed, t, side, X.shape[1], d)
+    mu = method.mu_t(alpha, beta, t)
+    return method.half_step(X, Y.astype(np.float64), Z.astype(np.float64), S, solver, mu)
+
+
+def _gpu_half(pkg, M, U, V, kind, solver, seed, t, side, d, d_v=None, csr=None):
+    m, n = U.shape[0], V.shape[0]
+    k = U.shape[1]
+    h = pkg.DSANLS(m, n, k, d, kind, seed=seed)
+    opts = dict(solver=solver, t=t)
+    if d_v is not None:
+        opts["d_v"] = d_v
+    h.set_options(**opts)
+    if csr is None:
+        h.set_dense(M)
+    else:
+        h.set_csr(*csr)
+    h.set_factors(U, V)
+    h.half_step(side)
+    Ug, Vg = h.factors()
+    G, eta = h.gram(side)
+    h.close()
+    return (Ug if side == 0 else Vg), G, eta
+
+
+CASES = [
+    # m, n, k, d, d_v
+    (333, 257, 10, 40, 50),
+    (1000, 800, 10, 100, 100),
+    (640, 515, 64, 130, 129),
+    (300, 260, 100, 96, 96),
+    (260, 300, 128, 64, 70),
+    (129, 70, 1, 9, 9),
+]
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("case", CASES)
+def test_dense_gaussian_half_steps(pkg, case, solver):
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 1)
+    U, V = initial_factors(m, n, k, 2)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        t = 3
+        got, G, eta = _gpu_half(pkg, M, U, V, method.GAUSSIAN, solver, 11, t, side, d, d_v=d_v)
+        want = _oracle_half(M64, U, V, method.GAUSSIAN, solver, 11, t, side, dd)
+        assert got.min() >= 0
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+        # the Gram matrix and step size of that half-step
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 11, t, side, X.shape[1], dd)
+        _, _, Go, _ = method.sketched_terms(X, Y, S)
+        assert _rel(G, Go) <= 1e-5
+        if solver == 0:
+            eta_o = 1.0 / (method.lambda_max(Go) + method.mu_t(1.0, 1.0, t))
+            assert abs(eta - eta_o) <= 1e-5 * eta_o
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("case", CASES[:5])
+def test_dense_subsample_half_steps(pkg, case, solver):
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 3)
+    U, V = initial_factors(m, n, k, 4)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        got, _, _ = _gpu_half(pkg, M, U, V, method.SUBSAMPLE, solver, 5, 7, side, d, d_v=d_v)
+        want = _oracle_half(M64, U, V, method.SUBSAMPLE, solver, 5, 7, side, dd)
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_dense_identity_half_steps(pkg, solver):
+    m, n, k = 200, 150, 12
+    M, _, _ = planted_dense(m, n, k, 5)
+    U, V = initial_factors(m, n, k, 6)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, n), (1, m)):
+        got, _, _ = _gpu_half(pkg, M, U, V, method.IDENTITY, solver, 0, 2, side, n, d_v=m)
+        want = _oracle_half(M64, U, V, method.IDENTITY, solver, 0, 2, side, dd)
+        assert _rel(got, want) <= TOL_STEP
+
+
+def _csr(m, n, seed):
+    rp, col, val = sparse_text(m, n, seed, mean_len=12.0)
+    return rp, col, val, sp.csr_matrix((val.astype(np.float64), col, rp), shape=(m, n))
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("kind", [method.SUBSAMPLE, method.GAUSSIAN, method.IDENTITY])
+def test_sparse_half_steps(pkg, kind, solver):
+    m, n, k = 700, 300, 16
+    rp, col, val, Msp = _csr(m, n, 9)
+    U, V = initial_factors(m, n, k, 7)
+    d, d_v = (n, m) if kind == method.IDENTITY else (60, 70)
+    for side, dd in ((0, d), (1, d_v)):
+        got, _, _ = _gpu_half(pkg, None, U, V, kind, solver, 3, 4, side, d, d_v=d_v, csr=(rp, col, val))
+        want = _oracle_half(Msp, U, V, kind, solver, 3, 4, side, dd, sparse=True)
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
+def test_sparse_given_transpose_equals_built_transpose(pkg):
+    m, n, k = 500, 200, 8
+    rp, col, val, Msp = _csr(m, n, 4)
+    T = Msp.T.tocsr()
+    U, V = initial_factors(m, n, k, 1)
+    a, _, _ = _gpu_half(pkg, None, U, V, method.SUBSAMPLE, 0, 2, 1, 1, 40, d_v=50, csr=(rp, col, val))
+    b, _, _ = _gpu_half(pkg, None, U, V, method.SUBSAMPLE, 0, 2, 1, 1, 40, d_v=50,
+                        csr=(rp, col, val, T.indptr.astype(np.int64), T.indices.astype(np.int32),
+                             T.data.astype(np.float32)))
+    assert np.array_equal(a, b)
+
+
+def test_sparse_rel_error(pkg):
+    m, n, k = 600, 250, 10
+    rp, col, val, Msp = _csr(m, n, 2)
+    U, V = initial_factors(m, n, k, 3)
+    h = pkg.DSANLS(m, n, k, 40, pkg.SUBSAMPLE, seed=1)
+    h.set_csr(rp, col, val)
+    h.set_factors(U, V)
+    e = h.rel_error()
+    h.close()
+    assert abs(e - method.rel_error(Msp, U.astype(np.float64), V.astype(np.float64))) <= 1e-6
+
+
+def test_config0_run_tracks_oracle(pkg):
+    """50 outer iterations of the planted 1000 x 800, k = 10, Gaussian d = 100 problem:
+    relative error after every iteration within 1e-4 of the oracle's."""
+    m, n, k, d, T = 1000, 800, 10, 100, 50
+    M, _, _ = planted_dense(m, n, k, 0)
+    U0, V0 = method.default_init(0, m, n, k)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=0)
+    h.set_dense(M)
+    Ug0, Vg0 = h.factors()
+    assert np.array_equal(Ug0, U0) and np.array_equal(Vg0, V0)  # default init is the Philox uniform field
+    errs = []
+    for _ in range(T):
+        h.step(1)
+        errs.append(h.rel_error())
+    U, V = h.factors()
+    h.close()
+    Uo, Vo, errs_o = method.run(M, U0, V0, 0, T, method.Options(sketch=method.GAUSSIAN, d=d))
+    diffs = np.abs(np.array(errs) - np.array(errs_o))
+    assert diffs.max() <= 1e-4, diffs.max()
+    assert _rel(U @ V.T, Uo @ Vo.T) <= 1e-3
+
+
+@pytest.mark.parametrize("kind,solver", [(0, 0), (0, 1), (1, 1)])
+def test_graph_replay_is_bitwise_equal_to_eager(pkg, kind, solver):
+    m, n, k, d = 400, 300, 16, 50
+    M, _, _ = planted_dense(m, n, k, 8)
+    out = []
+    for use_graph in (0, 1):
+        h = pkg.DSANLS(m, n, k, d, kind, seed=4, solver=solver, use_graph=use_graph)
+        h.set_dense(M)
+        h.step(5)
+        out.append(h.factors())
+        h.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_resume_from_checkpoint_is_bitwise(pkg):
+    """S^t is a pure function of (seed, t, side): factors + t reproduce the trajectory."""
+    m, n, k, d = 300, 200, 8, 30
+    M, _, _ = planted_dense(m, n, k, 2)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=7)
+    h.set_dense(M)
+    h.step(10)
+    U10, V10 = h.factors()
+    h.close()
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=7)
+    h.set_dense(M)
+    h.step(5)
+    U5, V5 = h.factors()
+    h.close()
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=7, t=5)
+    h.set_dense(M)
+    h.set_factors(U5, V5)
+    h.step(5)
+    U, V = h.factors()
+    h.close()
+    assert np.array_equal(U, U10) and np.array_equal(V, V10)
+
+
+def test_nan_input_raises_numeric_error(pkg):
+    m, n, k = 50, 40, 4
+    M, _, _ = planted_dense(m, n, k, 0)
+    h = pkg.DSANLS(m, n, k, 10, pkg.GAUSSIAN, seed=0)
+    h.set_dense(M)
+    U = np.ones((m, k), np.float32)
+    U[3, 1] = np.nan
+    h.set_factors(U, None)
+    h.half_step(1)
+    h.half_step(0)
+    with pytest.raises(pkg.DSANLSError) as e:
+        h.sync()
+    assert e.value.code == -5
+    h.sync()  # the flag is cleared once reported
+    h.close()
+
+
+def test_state_and_argument_errors(pkg):
+    h = pkg.DSANLS(20, 10, 3, 5, pkg.SUBSAMPLE, seed=0)
+    with pytest.raises(pkg.DSANLSError) as e:
+        h.step(1)
+    assert e.value.code == -4
+    with pytest.raises(pkg.DSANLSError) as e:
+        h.set_options(d_v=21)
+    assert e.value.code == -1
+    with pytest.raises(pkg.DSANLSError) as e:
+        h.half_step(2)
+    assert e.value.code == -1
+    bad_rp = np.array([0, 2, 1] + [2] * 18, np.int64)  # decreasing
+    with pytest.raises(pkg.DSANLSError):
+        h.set_csr(bad_rp, np.array([0, 1], np.int32), np.ones(2, np.float32))
+    h.close()
+
+
+def test_bound_clamp(pkg):
+    m, n, k = 100, 80, 5
+    M, _, _ = planted_dense(m, n, k, 0)
+    M *= 1e-4
+    U, V = initial_factors(m, n, k, 0)
+    U *= 50.0
+    h = pkg.DSANLS(m, n, k, 20, pkg.GAUSSIAN, seed=0, bound_clamp=1)
+    h.set_dense(M)
+    h.set_factors(U, V * 50.0)
+    h.step(2)
+    Ug, Vg = h.factors()
+    h.close()
+    bound = np.sqrt(2.0 * np.linalg.norm(M.astype(np.float64)))
+    assert Ug.max() <= bound * (1 + 1e-6) and Vg.max() <= bound * (1 + 1e-6)
+
+
+def test_run_is_deterministic(pkg):
+    m, n, k, d = 500, 400, 16, 64
+    M, _, _ = planted_dense(m, n, k, 3)
+    outs = []
+    for _ in range(2):
+        h = pkg.DSANLS(m, n, k, d, pkg.SUBSAMPLE, seed=9, solver=pkg.RCD)
+        h.set_dense(M)
+        h.step(4)
+        outs.append(h.factors())
+        h.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
