@@ -235,10 +235,12 @@ def run_ours(args, w):
         dist.init_process_group("nccl")
     prec = pkg.BF16 if args.precision == "bf16" else pkg.FP32
     M = make_inputs(w, rank)
+    # all library work and all timing events on one dedicated (non-default) stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=rank, d_v=w["d_v"], solver=pkg.PGD,
                    precision=prec, use_graph=1)
     h.set_dense(M)
-    stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
         h.step(1)

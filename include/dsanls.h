@@ -162,6 +162,9 @@ int dsanls_profile_half_step(dsanls_t h, int32_t side, int32_t reps, double *ms)
  * process (a replayed CUDA graph counts each of its kernels).  No GPU work. */
 int dsanls_kernel_launches(uint64_t *out);
 
+/* Message of the last failed call on handle h; with h == NULL, of the last
+ * failed dsanls_create or stateless primitive on the calling thread ("" if
+ * none).  The string stays valid until the next call that fails. */
 const char *dsanls_last_error(dsanls_t h);
 void dsanls_destroy(dsanls_t h);
 

@@ -116,6 +116,31 @@ def project(X, bound=None):
     return Y
 
 
+def round_bf16(x):
+    """Round to the nearest bfloat16 (ties to even), returned as FP64.  Models
+    the reduced-precision form's operand rounding (1 sign, 8 exponent, 7
+    fraction bits).  Goes through binary32 first, as the GPU operands do."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    r = ((b + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def sketched_terms_bf16(X, Y, S):
+    """The sketched terms of the reduced-precision form: X and S rounded to
+    bf16, A = X S accumulated exactly, A and B rounded to bf16 before
+    R = A B^T; B and G themselves stay FP64 (they are not tensor-core
+    operands)."""
+    Xb = round_bf16(X)
+    Sb = round_bf16(S.dense32)
+    A = round_bf16(Xb @ Sb)
+    B = Y.T @ S.dense32.astype(np.float64)
+    G = B @ B.T
+    R = A @ round_bf16(B).T
+    return A, B, G, R
+
+
 def sketched_terms(X, Y, S):
     """A = X S, B = Y^T S, G = B B^T, R = A B^T  (eq. def_A_B; gradient terms of
     eq. gradient_descent).  X: rows x n data (M or M^T), Y: n x k fixed factor."""
@@ -154,7 +179,7 @@ def rcd_update(Z, G, R, mu, bound=None):
     return Znew
 
 
-def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None):
+def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf16=False):
     """Update of the factor Z (rows x k) against data X (rows x n) with the
     other factor Y (n x k) fixed and sketch S (n x d): one solver step on the
     sketched subproblem (eq. sketched_sub).  ``rows`` restricts the result to a
@@ -162,7 +187,7 @@ def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None):
     if rows is not None:
         X = X[rows]
         Z = Z[rows]
-    A, B, G, R = sketched_terms(X, Y, S)
+    A, B, G, R = sketched_terms_bf16(X, Y, S) if bf16 else sketched_terms(X, Y, S)
     if solver == PGD:
         eta = 1.0 / (lambda_max(G, power_iters) + mu)
         return pgd_update(Z, G, R, eta, bound)

@@ -104,11 +104,9 @@ def _stream_ptr(stream=None):
 
 def _check(code, what="", handle=None):
     if code != OK:
-        msg = what
-        if handle is not None:
-            m = lib().dsanls_last_error(handle)
-            msg = (m.decode() if m else "") or what
-        raise DSANLSError(code, msg)
+        m = lib().dsanls_last_error(handle)
+        detail = m.decode() if m else ""
+        raise DSANLSError(code, "%s: %s" % (what, detail) if detail else what)
 
 
 def _dev_ptr(t):
@@ -218,6 +216,9 @@ class DSANLS:
         return o
 
     def set_options(self, stream="current", **kw):
+        """Apply options.  stream="current" hands the library torch's current
+        stream; torch's legacy default stream (handle 0) maps to the handle's
+        own stream, so synchronise with the handle (sync / factors) there."""
         o = self.options()
         for key, v in kw.items():
             if not hasattr(o, key) or key == "stream":

@@ -127,22 +127,25 @@ struct DeviceGuard {
     }
 };
 
+thread_local std::string g_last_error;
+
 template <typename F>
 int guarded(dsanls_ctx *h, F &&body) {
+    std::string &err = h ? h->err : g_last_error;
     try {
         return body();
     } catch (const CudaError &e) {
-        if (h) h->err = std::string("CUDA error: ") + cudaGetErrorString(e.err) + " (" + e.where + ")";
+        err = std::string("CUDA error: ") + cudaGetErrorString(e.err) + " (" + e.where + ")";
         cudaGetLastError();
         return DSANLS_ECUDA;
     } catch (const ArgError &e) {
-        if (h) h->err = e.what;
+        err = e.what;
         return DSANLS_EINVAL;
     } catch (const std::bad_alloc &) {
-        if (h) h->err = "out of memory";
+        err = "out of memory";
         return DSANLS_ENOMEM;
     } catch (...) {
-        if (h) h->err = "unexpected internal error";
+        err = "unexpected internal error";
         return DSANLS_ECUDA;
     }
 }
@@ -270,7 +273,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         if (tc) {
             // R = (X S) B^T on tcgen05, X and S in bf16, A never stored
             const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
-            launch_tc_sketch_rhs(Xb, h->Sb, h->W, rows, K, dd, k, h->Rpart, h->R, s);
+            launch_tc_sketch_rhs(Xb, h->Sb, h->W, rows, K, dd, k, h->Rpart, h->R, h->flag, s);
             mark(pe, DSANLS_PHASE_RHS, s);
         } else {
             if (dense) {
@@ -356,6 +359,7 @@ int pending_status(dsanls_ctx *h) {
     DSANLS_CUDA(cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         DSANLS_CUDA(cudaMemset(h->flag, 0, sizeof(int)));
+        if (flag & 2) return fail(h, DSANLS_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
         return fail(h, DSANLS_ENUMERIC, "an update produced NaN or Inf");
     }
     return DSANLS_OK;
@@ -390,7 +394,7 @@ void prime_kernel_attributes() {
     DSANLS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     prime_rng_attributes(max_smem);
     prime_solver_attributes(max_smem);
-    prime_tc_attributes();
+    prime_tc_attributes(max_smem);
     done = true;
 }
 }  // namespace dsanls
@@ -460,6 +464,7 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
         return DSANLS_OK;
     });
     if (rc != DSANLS_OK) {
+        g_last_error = h->err;
         dsanls_destroy(h);
         return rc;
     }
@@ -483,7 +488,12 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
         if (opt->precision != DSANLS_PREC_FP32 && opt->precision != DSANLS_PREC_BF16) throw ArgError{"unknown precision"};
         if (opt->precision == DSANLS_PREC_BF16 &&
             (h->has_sparse || h->sketch != DSANLS_SKETCH_GAUSSIAN || !tc_supported(h->k)))
-            throw ArgError{"BF16 precision needs dense data, a Gaussian sketch and k a multiple of 16 up to 128"};
+            throw ArgError{"BF16 precision needs dense data and a Gaussian sketch"};
+        if (opt->precision == DSANLS_PREC_BF16) {
+            const int dv = opt->d_v > 0 ? opt->d_v : h->d;
+            if (h->m % 8 || h->n % 8 || h->d % 8 || dv % 8)
+                throw ArgError{"BF16 precision needs m, n, d and d_v multiples of 8 (16-byte TMA rows)"};
+        }
         if (opt->power_iters < 0 || opt->power_iters > 10000) throw ArgError{"power_iters out of range"};
         if (!(opt->alpha >= 0.0) || !(opt->beta >= 0.0) || !std::isfinite(opt->alpha) || !std::isfinite(opt->beta))
             throw ArgError{"alpha and beta must be finite and >= 0"};
@@ -785,7 +795,7 @@ int dsanls_kernel_launches(uint64_t *out) {
 }
 
 const char *dsanls_last_error(dsanls_t h) {
-    if (!h) return "invalid handle";
+    if (!h) return g_last_error.c_str();
     return h->err.c_str();
 }
 

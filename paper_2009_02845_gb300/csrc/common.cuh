@@ -161,4 +161,14 @@ void add_launches(uint64_t n);
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Allow `func` the largest dynamic shared memory the device grants a block
+// next to the kernel's own static shared memory.
+template <typename F>
+void allow_max_dynamic_smem(F *func, int optin_bytes) {
+    cudaFuncAttributes a;
+    DSANLS_CUDA(cudaFuncGetAttributes(&a, (const void *)func));
+    const int dyn = optin_bytes - (int)a.sharedSizeBytes;
+    DSANLS_CUDA(cudaFuncSetAttribute((const void *)func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+}
+
 }  // namespace dsanls

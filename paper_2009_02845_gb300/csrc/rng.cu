@@ -135,7 +135,7 @@ __global__ void k_subsample(uint64_t seed, uint32_t side, uint64_t t_host, const
 }
 
 void prime_rng_attributes(int max_smem) {
-    DSANLS_CUDA(cudaFuncSetAttribute(k_subsample, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    allow_max_dynamic_smem(k_subsample, max_smem);
 }
 
 int feistel_half_bits(int64_t n) {

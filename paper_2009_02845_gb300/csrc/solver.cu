@@ -295,17 +295,16 @@ static void update_kp(int solver, float *Z, const float *R, int64_t rows, int k,
 }
 
 void prime_solver_attributes(int max_smem) {
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    DSANLS_CUDA(cudaFuncSetAttribute(k_gram_partial, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_step_size, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<16, 0>, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<16, 1>, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<32, 0>, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<32, 1>, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<64, 0>, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<64, 1>, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<128, 0>, a, max_smem));
-    DSANLS_CUDA(cudaFuncSetAttribute(k_update<128, 1>, a, max_smem));
+    allow_max_dynamic_smem(k_gram_partial, max_smem);
+    allow_max_dynamic_smem(k_step_size, max_smem);
+    allow_max_dynamic_smem(k_update<16, 0>, max_smem);
+    allow_max_dynamic_smem(k_update<16, 1>, max_smem);
+    allow_max_dynamic_smem(k_update<32, 0>, max_smem);
+    allow_max_dynamic_smem(k_update<32, 1>, max_smem);
+    allow_max_dynamic_smem(k_update<64, 0>, max_smem);
+    allow_max_dynamic_smem(k_update<64, 1>, max_smem);
+    allow_max_dynamic_smem(k_update<128, 0>, max_smem);
+    allow_max_dynamic_smem(k_update<128, 1>, max_smem);
 }
 
 void launch_update(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp,

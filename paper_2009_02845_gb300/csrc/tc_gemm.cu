@@ -1,19 +1,433 @@
-// Tensor-core (tcgen05) path of the sketched right-hand side.
+// Tensor-core (tcgen05 / TMA) path of the sketched right-hand side
+//     R = (X S) B^T          (A = X S of eq. def_A_B, then the gradient term
+//                              A B^T of eq. gradient_descent)
+// with X (rows x K) and S^T (d x K) in bf16, fp32 accumulation in tensor
+// memory, and A never written to global memory.
+//
+// One CTA per 128 x 256 tile of A = X S:
+//   warp 0     TMA producer: K-blocks of 64 of the X tile (128 x 64) and the
+//              S^T tile (256 x 64), 128-byte swizzle, into a STAGES-deep ring
+//              guarded by full/empty mbarriers; plus the B tile (kp x 256).
+//   warp 1     MMA issuer (one thread): tcgen05.mma kind::f16, M=128, N=256,
+//              K=16, accumulator D1 in TMEM columns [0, 256); then the fused
+//              second product D2 (128 x kp, TMEM columns [256, 256+kp)) =
+//              bf16(D1) (from shared memory) times B_tile^T.
+//   warps 4-7  epilogue: tcgen05.ld of D1 (one TMEM lane = one row per
+//              thread), convert to bf16, store in the 128B-swizzled K-major
+//              layout the second MMA reads; then tcgen05.ld of D2 and store
+//              of the partial R of this d-chunk.
+// Partial R of the d/256 chunks is summed in chunk order by a second kernel
+// (deterministic).  Every mbarrier wait is bounded: on timeout the kernel
+// raises bit 2 of the error flag, drains its own TMA copies, frees TMEM and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
 
 namespace dsanls {
 
-bool tc_supported(int) { return false; }
+namespace {
 
-int64_t tc_rpart_elems(int64_t, int64_t, int) { return 0; }
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;  // bf16 elements = 128 bytes = one swizzle row
+constexpr int TC_THREADS = 256;
+constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KB
+constexpr int B_STAGE_BYTES = BN * BK * 2;  // 32 KB
+constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t D2_COL = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded wait: 2 s of wall time
 
-void launch_tc_sketch_rhs(const __nv_bfloat16 *, const __nv_bfloat16 *, const float *, int64_t, int64_t, int64_t, int,
-                          float *, float *, cudaStream_t) {
-    throw ArgError{"tensor-core path not available"};
+// ---- PTX helpers ---------------------------------------------------------
+DSANLS_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+DSANLS_DEV void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-void prime_tc_attributes() {}
+DSANLS_DEV void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+DSANLS_DEV void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+DSANLS_DEV bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+DSANLS_DEV unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true when phase `parity` of the barrier completed within WAIT_NS
+DSANLS_DEV bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() - t0 > WAIT_NS) return false;
+    return true;
+}
+
+DSANLS_DEV void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand with 128-byte
+// swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+DSANLS_DEV uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);     // start address
+    d |= (uint64_t)(16u >> 4) << 16;              // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024u >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with bf16 A and B, fp32 D, both K-major.
+DSANLS_DEV uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+DSANLS_DEV void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+DSANLS_DEV void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+DSANLS_DEV void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+DSANLS_DEV void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+DSANLS_DEV void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+DSANLS_DEV void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+DSANLS_DEV uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+struct __align__(8) TcSmemTail {
+    uint64_t full[4];
+    uint64_t empty[4];
+    uint64_t b_full;
+    uint64_t d1_full;
+    uint64_t a2_ready;
+    uint64_t d2_full;
+    uint64_t mma_done;
+    uint32_t tmem_base;
+    int failed;
+};
+
+}  // namespace
+
+// X: rows x K bf16 (map_x: box 64 x 128), S^T: d x K bf16 (map_s: box 64 x 256),
+// B: k x d bf16 (map_b: box 64 x kp).  Rpart[chunk][rows][k] (chunk = N tile).
+template <int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_sketch_rhs(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
+                    const __grid_constant__ CUtensorMap map_b, int64_t rows, int64_t K, int64_t d, int k, int kp,
+                    float *__restrict__ Rpart, int *__restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte alignment for the swizzled tiles
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t *stage_base = smem;                                  // STAGES x (A 16 KB | B 32 KB)
+    uint8_t *btile = smem + STAGES * STAGE_BYTES;                // 4 atoms of kp x 128 B
+    TcSmemTail *tail = (TcSmemTail *)(btile + 4 * kp * 128);
+    uint8_t *a2 = stage_base;                                    // reused after the main loop: 4 x 16 KB
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nchunks = (int)ceil_div(d, BN);
+    const int chunk = blockIdx.x % nchunks;
+    const int64_t m0 = (int64_t)(blockIdx.x / nchunks) * BM;
+    const int n0 = chunk * BN;
+    const int nk = (int)ceil_div(K, BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&tail->full[s], 1);
+            mbar_init(&tail->empty[s], 1);
+        }
+        mbar_init(&tail->b_full, 1);
+        mbar_init(&tail->d1_full, 1);
+        mbar_init(&tail->a2_ready, 128);
+        mbar_init(&tail->d2_full, 1);
+        mbar_init(&tail->mma_done, 1);
+        tail->failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tail->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tail->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // B tile first (needed only at the end), then the K ring
+            mbar_expect_tx(&tail->b_full, 4u * kp * 128u);
+            for (int a = 0; a < 4; ++a) tma_load_2d(btile + a * kp * 128, &map_b, n0 + a * 64, 0, &tail->b_full);
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES && !mbar_wait(&tail->empty[s], ((kb / STAGES) - 1) & 1)) {
+                    atomicOr(err, 2);
+                    tail->failed = 1;
+                    break;
+                }
+                if (*(volatile int *)&tail->failed) break;
+                uint8_t *sa = stage_base + s * STAGE_BYTES;
+                mbar_expect_tx(&tail->full[s], STAGE_BYTES);
+                tma_load_2d(sa, &map_x, kb * BK, (int)m0, &tail->full[s]);
+                tma_load_2d(sa + A_STAGE_BYTES, &map_s, kb * BK, n0, &tail->full[s]);
+                ++issued;
+            }
+            // drain: every copy this thread issued has landed before the CTA can exit
+            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+                mbar_wait(&tail->full[kb % STAGES], (kb / STAGES) & 1);
+            mbar_wait(&tail->b_full, 0);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id1 = idesc_bf16(BM, BN);
+            bool ok = true;
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(&tail->full[s], (kb / STAGES) & 1)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
+                const uint32_t sb = sa + A_STAGE_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (kb | kk) != 0);
+                mma_commit(&tail->empty[s]);
+            }
+            if (ok) {
+                mma_commit(&tail->d1_full);
+                // second product: D2 = bf16(D1) B_tile^T, K = 256 in 16 steps
+                if (mbar_wait(&tail->a2_ready, 0) && mbar_wait(&tail->b_full, 0)) {
+                    fence_after();
+                    const uint32_t id2 = idesc_bf16(BM, kp);
+                    const uint32_t a2s = smem_u32(a2), bts = smem_u32(btile);
+#pragma unroll
+                    for (int kk = 0; kk < BN / 16; ++kk) {
+                        const uint32_t ad = a2s + (kk >> 2) * (BM * 128) + (kk & 3) * 32;
+                        const uint32_t bd = bts + (kk >> 2) * (kp * 128) + (kk & 3) * 32;
+                        mma_bf16(tmem + D2_COL, sw128_desc(ad), sw128_desc(bd), id2, kk != 0);
+                    }
+                    mma_commit(&tail->d2_full);
+                } else {
+                    ok = false;
+                }
+            }
+            if (!ok) {
+                atomicOr(err, 2);
+                tail->failed = 1;
+            }
+            // every MMA this thread issued has retired before TMEM is freed
+            mma_commit(&tail->mma_done);
+            mbar_wait(&tail->mma_done, 0);
+        }
+    } else if (warp >= 4) {
+        const int q = warp & 3;  // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        bool ok = mbar_wait(&tail->d1_full, 0);
+        if (ok) {
+            fence_after();
+            // D1 (fp32) -> bf16, 128B-swizzled K-major layout: atom a = col / 64
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(trow + c * 32, v);
+                tmem_ld_wait();
+                uint8_t *atom = a2 + (c >> 1) * (BM * 128) + r * 128;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {  // 4 chunks of 8 bf16 (16 bytes)
+                    const int chunk16 = (c & 1) * 4 + j;
+                    uint4 w;
+                    w.x = pack_bf16(__uint_as_float(v[8 * j + 0]), __uint_as_float(v[8 * j + 1]));
+                    w.y = pack_bf16(__uint_as_float(v[8 * j + 2]), __uint_as_float(v[8 * j + 3]));
+                    w.z = pack_bf16(__uint_as_float(v[8 * j + 4]), __uint_as_float(v[8 * j + 5]));
+                    w.w = pack_bf16(__uint_as_float(v[8 * j + 6]), __uint_as_float(v[8 * j + 7]));
+                    *reinterpret_cast<uint4 *>(atom + ((chunk16 ^ (r & 7)) << 4)) = w;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        mbar_arrive(&tail->a2_ready);
+        if (ok) ok = mbar_wait(&tail->d2_full, 0);
+        if (ok) {
+            fence_after();
+            const int64_t row = m0 + r;
+            float *dst = Rpart + ((int64_t)chunk * rows + row) * k;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kp; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(trow + D2_COL + c0, v);
+                tmem_ld_wait();
+                if (row < rows) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < k) dst[c0 + j] = __uint_as_float(v[j]);
+                }
+            }
+        } else {
+            atomicOr(err, 2);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// R[i][c] = sum over chunks (ascending) of Rpart[chunk][i][c]
+__global__ void k_reduce_chunks(const float *__restrict__ Rpart, int nchunks, int64_t rows, int k,
+                                float *__restrict__ R) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * k) return;
+    float acc = 0.0f;
+    for (int c = 0; c < nchunks; ++c) acc = __fadd_rn(acc, Rpart[(int64_t)c * rows * k + idx]);
+    R[idx] = acc;
+}
+
+__global__ void k_to_bf16(const float *__restrict__ in, int64_t n, __nv_bfloat16 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    if (!fn) throw ArgError{"cuTensorMapEncodeTiled is unavailable"};
+    return fn;
+}
+
+// 2-D bf16 row-major tensor (rows x cols), box (64 cols x box_rows), 128-byte swizzle.
+CUtensorMap make_map(const void *base, int64_t rows, int64_t cols, int box_rows) {
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw ArgError{"cuTensorMapEncodeTiled failed"};
+    return m;
+}
+
+int kp_of(int k) { return (int)ceil_div(k, 16) * 16; }
+
+size_t smem_bytes(int stages, int kp) {
+    return 1024 /* alignment slack */ + (size_t)stages * STAGE_BYTES + 4 * (size_t)kp * 128 + sizeof(TcSmemTail);
+}
+
+int stages_for(int kp) { return smem_bytes(4, kp) <= 227 * 1024 ? 4 : 3; }  // opt-in limit of sm_100/sm_103
+
+}  // namespace
+
+bool tc_supported(int k) { return k >= 1 && k <= 128; }
+
+int64_t tc_rpart_elems(int64_t rows, int64_t d, int k) {
+    // partial R per 256-wide chunk of d, plus the bf16 copy of B (k x d) at the end
+    return ceil_div(d, BN) * rows * k + ceil_div((int64_t)k * d, 2) + 64;
+}
+
+void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const float *B, int64_t rows, int64_t K,
+                          int64_t d, int k, float *Rpart, float *R, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || d > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0 || d % 8 != 0) throw ArgError{"tensor-core path needs K and d multiples of 8"};
+    const int kp = kp_of(k);
+    const int nchunks = (int)ceil_div(d, BN);
+    // bf16 copy of B after the partial-R region, 16-byte aligned
+    __nv_bfloat16 *Bb = reinterpret_cast<__nv_bfloat16 *>(
+        (reinterpret_cast<uintptr_t>(Rpart + (int64_t)nchunks * rows * k) + 15) & ~(uintptr_t)15);
+    k_to_bf16<<<(unsigned)ceil_div((int64_t)k * d, 256), 256, 0, s>>>(B, (int64_t)k * d, Bb);
+    DSANLS_LAUNCH_CHECK();
+    const CUtensorMap mx = make_map(X, rows, K, BM);
+    const CUtensorMap ms = make_map(St, d, K, BN);
+    const CUtensorMap mb = make_map(Bb, k, d, kp);
+    const int64_t tiles = ceil_div(rows, BM) * nchunks;
+    const int stages = stages_for(kp);
+    const size_t smem = smem_bytes(stages, kp);
+    if (stages == 4)
+        k_tc_sketch_rhs<4><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, Rpart, err);
+    else
+        k_tc_sketch_rhs<3><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, Rpart, err);
+    DSANLS_LAUNCH_CHECK();
+    k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
+    DSANLS_LAUNCH_CHECK();
+}
+
+void prime_tc_attributes(int max_smem) {
+    allow_max_dynamic_smem(k_tc_sketch_rhs<4>, max_smem);
+    allow_max_dynamic_smem(k_tc_sketch_rhs<3>, max_smem);
+}
 
 }  // namespace dsanls

@@ -12,9 +12,10 @@ bool tc_supported(int k);
 // Elements of the fp32 partial-R workspace for up to `rows` rows, sketch size d, rank k.
 int64_t tc_rpart_elems(int64_t rows, int64_t d, int k);
 // R (rows x k, fp32) = (X S) B^T with X rows x K (bf16, row-major), S^T d x K (bf16,
-// row-major) and B k x d (fp32).  Rpart is scratch of tc_rpart_elems entries.
+// row-major) and B k x d (fp32).  Rpart is scratch of tc_rpart_elems entries.  A
+// bounded wait that gives up sets bit 2 of *err.  K and d must be multiples of 8.
 void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const float *B, int64_t rows, int64_t K,
-                          int64_t d, int k, float *Rpart, float *R, cudaStream_t s);
-void prime_tc_attributes();
+                          int64_t d, int k, float *Rpart, float *R, int *err, cudaStream_t s);
+void prime_tc_attributes(int max_smem);
 
 }  // namespace dsanls

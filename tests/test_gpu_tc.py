@@ -1,0 +1,97 @@
+"""Parity of the bf16 tensor-core (tcgen05) form of the sketched products.
+
+Two references:
+  * the oracle's bf16 model (operands X, S, A, B rounded to bf16 exactly as
+    the tensor-core path rounds them, products and sums in FP64): the only
+    remaining difference is fp32 accumulation order in tensor memory and the
+    fp32 B used for G, so the step agrees to <= 2e-4 (norm-wise, relative);
+  * the plain FP64 oracle: bf16 operand rounding (unit roundoff 2^-8) limits
+    agreement to <= 5e-3 per step.
+Shapes span several 128 x 256 tiles with ragged row tails and several d-chunks.
+"""
+import numpy as np
+import pytest
+
+from oracle import method
+from synthdata import initial_factors, planted_dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2009_02845_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+CASES = [
+    # m, n, k, d, d_v
+    (256, 128, 16, 256, 256),
+    (1000, 808, 10, 104, 96),
+    (640, 520, 64, 520, 264),
+    (384, 1032, 128, 768, 256),
+    (136, 200, 32, 2048, 64),
+]
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("case", CASES)
+def test_bf16_half_steps(pkg, case, solver):
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 2)
+    U, V = initial_factors(m, n, k, 3)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=21, d_v=d_v, solver=solver, precision=pkg.BF16, t=2)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 21, 2, side, X.shape[1], dd)
+        mu = method.mu_t(1.0, 1.0, 2)
+        model = method.half_step(X, Y, Z, S, solver, mu, bf16=True)
+        exact = method.half_step(X, Y, Z, S, solver, mu)
+        assert got.min() >= 0
+        assert _rel(got, model) <= 2e-4, (side, _rel(got, model))
+        assert _rel(got, exact) <= 5e-3, (side, _rel(got, exact))
+
+
+def test_bf16_run_final_error(pkg):
+    """Reduced precision plus closing fp32 iterations ends within 2e-3 of the
+    oracle's final relative error (planted 1000 x 808, k = 10, d = 104)."""
+    m, n, k, d, T = 1000, 808, 10, 104, 30
+    M, _, _ = planted_dense(m, n, k, 0)
+    U0, V0 = method.default_init(0, m, n, k)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=0, precision=pkg.BF16)
+    h.set_dense(M)
+    h.step(T - 3)
+    h.set_options(precision=pkg.FP32)
+    h.step(3)
+    err = h.rel_error()
+    h.close()
+    _, _, errs = method.run(M, U0, V0, 0, T, method.Options(sketch=method.GAUSSIAN, d=d))
+    assert abs(err - errs[-1]) <= 2e-3, (err, errs[-1])
+
+
+def test_bf16_rejects_unsupported_shapes(pkg):
+    h = pkg.DSANLS(104, 64, 8, 20, pkg.GAUSSIAN, seed=0)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(precision=pkg.BF16)  # d = 20 is not a multiple of 8
+    h.close()
+    h = pkg.DSANLS(100, 64, 8, 16, pkg.GAUSSIAN, seed=0)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(precision=pkg.BF16)  # m = 100 is not a multiple of 8
+    h.close()
+    h = pkg.DSANLS(100, 64, 8, 16, pkg.SUBSAMPLE, seed=0)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(precision=pkg.BF16)
+    h.close()

@@ -282,3 +282,15 @@ def test_mutant_missing_gaussian_scale_is_caught():
                 self.dense32 = rng.gaussian_field(seed, side, t, n, d, 1.0)
     mut = _Mutant(Sketch=BadSketch)
     assert pin_unbiased_gradient(mut, method.GAUSSIAN, trials=300) > 0.2
+
+
+def test_round_bf16_matches_torch():
+    """The oracle's bf16 rounding equals torch's float32 -> bfloat16 conversion."""
+    import torch
+    g = np.random.default_rng(0)
+    x = np.concatenate([g.standard_normal(20000).astype(np.float32) * 100,
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.0078125, 3.0e38, 1e-40], np.float32)])
+    # exact ties in the 16 dropped bits
+    x = np.concatenate([x, (np.arange(1, 200, dtype=np.uint32) << 16 | 0x8000).view(np.float32)])
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(method.round_bf16(x), want)
