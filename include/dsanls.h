@@ -198,6 +198,30 @@ int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t 
 int dsanls_subsample_indices(uint64_t seed, uint32_t side, uint64_t t, int64_t n, int32_t d,
                              int32_t *J, void *stream);
 
+/* ---- allocation-free Gram ---------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate device memory -- a host framework that
+ * owns all device memory through its own pool and forbids cudaMalloc/cudaFree
+ * in plugins, or a latency-critical loop that cannot afford the implicit
+ * device synchronisation of cudaFree.
+ *
+ * G (k x k, FP64, row-major, device) = B B^T for B (k x d, binary32,
+ * row-major, device), the same kernels and arithmetic as the Gram of a
+ * half-step.  It allocates nothing: its only scratch is a fixed 2 MiB
+ * file-scope device array inside libdsanls.so (FP64 partial Grams of up to
+ * floor(262144 / k^2) CTAs), which every GPU that loads the library holds
+ * until the process exits.  The first call on a device resolves that array's
+ * device address (cudaGetSymbolAddress, with the device current); make that
+ * first call before any stream capture.  All calls on a device share the
+ * array: calls whose executions overlap on the GPU race and give wrong
+ * results -- serialise them (one stream, or events).  Every partial a call
+ * reads is written by the same call, so stale contents from an earlier call
+ * never leak into G.  Queued on `stream` (cudaStream_t, NULL = default
+ * stream); returns once queued.  EINVAL for NULL pointers, k outside
+ * [1, 128] or d outside [1, 2^31 - 1] (message in dsanls_last_error(NULL));
+ * ECUDA on a launch failure. */
+int dsanls_gram_noalloc(const float *B, int32_t k, int64_t d, double *G, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ EXPORTED_SYMBOLS = [
     "dsanls_set_dense", "dsanls_set_csr", "dsanls_set_factors", "dsanls_step", "dsanls_half_step",
     "dsanls_rel_error", "dsanls_get_factors", "dsanls_get_gram", "dsanls_sync", "dsanls_last_error",
     "dsanls_destroy", "dsanls_philox_field", "dsanls_gaussian_field", "dsanls_uniform_field",
-    "dsanls_subsample_indices", "dsanls_profile_half_step", "dsanls_kernel_launches",
+    "dsanls_subsample_indices", "dsanls_profile_half_step", "dsanls_kernel_launches", "dsanls_gram_noalloc",
 ]
 NPHASES = 7
 PHASES = ["sketch", "B", "product", "rhs", "gram", "step_size", "update"]
@@ -82,6 +82,7 @@ def lib():
             "dsanls_subsample_indices": ([u64, u32, u64, i64, i32, vp, vp], ctypes.c_int),
             "dsanls_profile_half_step": ([vp, i32, i32, vp], ctypes.c_int),
             "dsanls_kernel_launches": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+            "dsanls_gram_noalloc": ([vp, i32, i64, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -122,6 +123,18 @@ def kernel_launches():
     v = ctypes.c_uint64()
     _check(lib().dsanls_kernel_launches(ctypes.byref(v)), "kernel_launches")
     return v.value
+
+
+def gram_noalloc(B, G=None):
+    """G = B B^T (FP64) through the allocation-free entry point.  B: k x d
+    float32 CUDA tensor; G: optional k x k float64 CUDA tensor to fill (the
+    binding allocates it with torch when not given)."""
+    torch = _torch()
+    k, d = B.shape
+    if G is None:
+        G = torch.empty((k, k), dtype=torch.float64, device=B.device)
+    _check(lib().dsanls_gram_noalloc(_dev_ptr(B), int(k), int(d), _dev_ptr(G), _stream_ptr()), "gram_noalloc")
+    return G
 
 
 def philox_field(seed, stream_id, t, rows, cols, device="cuda"):

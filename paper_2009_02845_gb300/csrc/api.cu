@@ -382,6 +382,8 @@ void set_bound(dsanls_ctx *h) {
 }  // namespace
 
 namespace dsanls {
+void record_handleless_error(const std::string &msg) { g_last_error = msg; }
+
 static std::atomic<uint64_t> g_launches{0};
 uint64_t launch_count() { return g_launches.load(); }
 void add_launches(uint64_t n) { g_launches.fetch_add(n); }

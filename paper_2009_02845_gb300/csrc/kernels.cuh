@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace dsanls {
 
 template <typename T>
@@ -21,6 +23,8 @@ __device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(float v) {
 // Raise the dynamic shared-memory limit of every kernel that needs more than
 // 48 KB once per process (before any graph capture).
 void prime_kernel_attributes();
+// Message returned by dsanls_last_error(NULL) on this thread.
+void record_handleless_error(const std::string &msg);
 void prime_rng_attributes(int max_smem);
 void prime_solver_attributes(int max_smem);
 
