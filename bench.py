@@ -43,6 +43,14 @@ WORKLOADS = {
                                 "Gaussian sketch d=d'=2048, PGD"),
     "dense_subsample": dict(m=65536, n=16384, k=64, d=2048, d_v=2048, sketch=1, zero_frac=0.7, noise=0.01,
                             desc="dense 65536x16384 planted (k=64), subsampling sketch d=d'=2048, PGD"),
+    "dense_gaussian_8k": dict(m=8192, n=16384, k=64, d=2048, d_v=2048, sketch=0, zero_frac=0.7, noise=0.01,
+                              desc="dense 8192x16384 planted (k=64), Gaussian sketch d=d'=2048, PGD "
+                                   "(profiling case: M 0.5 GB)"),
+    "sparse_text": dict(m=2_000_000, n=500_000, k=100, d=5000, d_v=5000, sketch=1, sparse=True,
+                        desc="CSR 2e6 docs x 5e5 terms (lognormal lengths mean 100, Zipf 1.07 ids, "
+                             "log(1+Poisson) values, ~2e8 nnz), k=100, subsampling d=d'=5000, PGD"),
+    "sparse_text_small": dict(m=200_000, n=50_000, k=100, d=500, d_v=500, sketch=1, sparse=True,
+                              desc="CSR 2e5 x 5e4 text-like (~2e7 nnz), k=100, subsampling d=d'=500, PGD"),
     "small": dict(m=1000, n=800, k=10, d=100, d_v=100, sketch=0, zero_frac=0.0, noise=0.01,
                   desc="planted 1000x800, k=10, Gaussian d=100, PGD"),
 }
@@ -117,9 +125,24 @@ class Clocks:
 
 
 def make_inputs(w, seed):
+    """Dense M (float32 ndarray) or a CSR triple (rowptr, col, val)."""
+    if w.get("sparse"):
+        from synthdata import sparse_text
+        return sparse_text(w["m"], w["n"], seed)
     from synthdata import planted_dense
     M, _, _ = planted_dense(w["m"], w["n"], w["k"], seed, zero_frac=w["zero_frac"], noise=w["noise"])
     return M
+
+
+def _input_bytes(M):
+    return int(sum(a.nbytes for a in M)) if isinstance(M, tuple) else int(M.nbytes)
+
+
+def _set_data(h, M):
+    if isinstance(M, tuple):
+        h.set_csr(*M)
+    else:
+        h.set_dense(M)
 
 
 # ---------------------------------------------------------------------------
@@ -150,7 +173,12 @@ def oracle_sample(M, w, seed, rows_budget):
         G = B @ B.T
         lam = method.lambda_max(G)
         t1 = time.perf_counter()
-        X = M[rows].astype(np.float64) if side == 0 else M[:, rows].T.astype(np.float64)
+        if isinstance(M, tuple):
+            import scipy.sparse as sp
+            Msp = sp.csr_matrix((M[2].astype(np.float64), M[1], M[0]), shape=(m, n))
+            X = Msp[rows] if side == 0 else Msp[:, rows].T.tocsr()
+        else:
+            X = M[rows].astype(np.float64) if side == 0 else M[:, rows].T.astype(np.float64)
         A = S.right_multiply(X)
         R = A @ B.T
         Z = (U0 if side == 0 else V0)[rows]
@@ -223,6 +251,48 @@ def _traffic(kernel_key, workload):
     return ent["bytes_per_launch"] if h == ent["source_sha"] else None
 
 
+def time_to_eps(pkg, torch, M, w, T, check_every, stream):
+    """Relative error every `check_every` outer iterations for the plain FP32
+    path and for the bf16 form with its last 3 iterations in FP32; eps is the
+    FP32 path's error after T iterations + 1e-3.  Times are CUDA-event sums of
+    the steps alone (error evaluations excluded)."""
+    def trajectory(prec_plan):
+        h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=0, d_v=w["d_v"], solver=pkg.PGD,
+                       precision=prec_plan[0], use_graph=1)
+        h.set_dense(M)
+        errs, total_ms = [], 0.0
+        for it in range(T):
+            prec = prec_plan[1] if it >= T - 3 else prec_plan[0]
+            if prec != prec_plan[0] and it == T - 3:
+                h.set_options(precision=prec)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            if (it + 1) % check_every == 0 or it == T - 1:
+                errs.append((it + 1, total_ms, h.rel_error()))
+        h.close()
+        return errs
+
+    fp32 = trajectory((pkg.FP32, pkg.FP32))
+    eps = fp32[-1][2] + 1e-3
+    bf16 = trajectory((pkg.BF16, pkg.FP32))
+
+    def first_hit(tr):
+        for it, ms, e in tr:
+            if e <= eps:
+                return {"iters": it, "seconds": ms / 1000.0, "err": e}
+        return None
+
+    a, b = first_hit(fp32), first_hit(bf16)
+    return {"eps": eps, "T": T, "checked_every": check_every,
+            "fp32": {"to_eps": a, "final_err": fp32[-1][2], "seconds_T": fp32[-1][1] / 1000.0},
+            "bf16_closing_fp32": {"to_eps": b, "final_err": bf16[-1][2], "seconds_T": bf16[-1][1] / 1000.0},
+            "speedup_time_to_eps": (a["seconds"] / b["seconds"]) if (a and b) else None}
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -240,7 +310,7 @@ def run_ours(args, w):
     torch.cuda.set_stream(stream)
     h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=rank, d_v=w["d_v"], solver=pkg.PGD,
                    precision=prec, use_graph=1)
-    h.set_dense(M)
+    _set_data(h, M)
 
     for _ in range(args.warmup):
         h.step(1)
@@ -285,12 +355,19 @@ def run_ours(args, w):
         else:
             bound, peak, unit, kernel_key = "alu", FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "sgemm_simt"
             peak_note = "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
-    else:
+    elif not w.get("sparse"):
         # subsampling: the gathered product reads d columns of M^T per half
         bytes_ = [4.0 * (m * d + d * k) + 4.0 * m * k, 4.0 * (n * d_v + d_v * k) + 4.0 * n * k]
         prod_ms = [p["rhs"] for p in phases]
         achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
         bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "sgemm_simt_gather"
+        peak_note = "hbm_gbs of %s" % peak_src
+    else:
+        # sparse subsampling: the fused row update reads Z and R and writes Z (12 bytes per entry)
+        bytes_ = [12.0 * m * k, 12.0 * n * k]
+        prod_ms = [p["update"] for p in phases]
+        achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
+        bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "update"
         peak_note = "hbm_gbs of %s" % peak_src
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": _traffic(kernel_key, args.workload), "kernel": kernel_key, "peak_source": peak_note,
@@ -299,13 +376,14 @@ def run_ours(args, w):
     # end to end through the public API with host buffers
     e2e = None
     if rank == 0 and not args.no_e2e:
-        Mp = torch.from_numpy(M).pin_memory()
+        Mp = tuple(torch.from_numpy(a).pin_memory() for a in M) if isinstance(M, tuple) else \
+            torch.from_numpy(M).pin_memory()
         Uh = torch.empty((m, k), dtype=torch.float32).pin_memory()
         Vh = torch.empty((n, k), dtype=torch.float32).pin_memory()
         he = pkg.DSANLS(m, n, k, d, w["sketch"], seed=rank, d_v=d_v, solver=pkg.PGD, precision=prec, use_graph=1)
 
         def e2e_step():
-            he.set_dense(Mp)
+            _set_data(he, Mp)
             he.step(1)
             he.factors()  # synchronising device->host read of U and V
         e2e_step()
@@ -317,14 +395,19 @@ def run_ours(args, w):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
         he.close()
-        e2e = {"value": 1.0 / dt, "unit": UNIT, "h2d_bytes_per_step": int(M.nbytes),
+        e2e = {"value": 1.0 / dt, "unit": UNIT, "h2d_bytes_per_step": _input_bytes(M),
                "d2h_bytes_per_step": int((m + n) * k * 4),
-               "note": "per step: set_dense from pinned host M, 1 outer iteration, get_factors to host"}
+               "note": "per step: set_dense/set_csr from pinned host memory, 1 outer iteration, "
+                       "get_factors to host"}
         del Mp
+
+    tte = None
+    if rank == 0 and args.time_to_eps > 0 and w["sketch"] == 0:
+        tte = time_to_eps(pkg, torch, M, w, args.time_to_eps, 5, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rows = 512 if m > 10000 else m
+        rows = (20000 if w.get("sparse") else 512) if m > 10000 else m
         v, desc = oracle_sample(M, w, rank, rows)
         cpu = {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": desc}
 
@@ -336,11 +419,12 @@ def run_ours(args, w):
             "vs_baseline": None, "dtype": "bf16" if prec == pkg.BF16 else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "k": k, "d": d, "d_v": d_v,
                        "precision": args.precision, "solver": "pgd", "graph": True, "replicas": ws,
-                       "l2": "inputs larger than L2 (M is %.1f GB)" % (M.nbytes / 1e9)},
+                       "l2": "inputs larger than L2 (M is %.1f GB)" % (_input_bytes(M) / 1e9)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "phases_ms": {"U": {k_: round(v_, 4) for k_, v_ in phases[0].items()},
                           "V": {k_: round(v_, 4) for k_, v_ in phases[1].items()}},
             "rel_error_after": err,
+            "time_to_eps": tte,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -357,6 +441,8 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-to-eps", type=int, default=0,
+                    help="also run T outer iterations of the fp32 and bf16 forms and report time to eps")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -128,14 +128,13 @@ def round_bf16(x):
 
 
 def sketched_terms_bf16(X, Y, S):
-    """The sketched terms of the reduced-precision form: X and S rounded to
-    bf16, A = X S accumulated exactly, A and B rounded to bf16 before
-    R = A B^T; B and G themselves stay FP64 (they are not tensor-core
-    operands)."""
-    Xb = round_bf16(X)
+    """The sketched terms of the reduced-precision form: the operands X, Y and
+    S rounded to bf16, products accumulated exactly; A = X S and B = Y^T S
+    rounded to bf16 again where they enter R = A B^T; G = B B^T from the
+    unrounded B."""
     Sb = round_bf16(S.dense32)
-    A = round_bf16(Xb @ Sb)
-    B = Y.T @ S.dense32.astype(np.float64)
+    A = round_bf16(round_bf16(X) @ Sb)
+    B = round_bf16(Y).T @ Sb
     G = B @ B.T
     R = A @ round_bf16(B).T
     return A, B, G, R

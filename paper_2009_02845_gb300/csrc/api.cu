@@ -91,6 +91,8 @@ struct dsanls_ctx {
     float *Wpart = nullptr;
     float *R = nullptr;
     float *Rpart = nullptr;
+    __nv_bfloat16 *Ytb = nullptr;  // bf16 Y^T (k x K) for the tensor-core B = Y^T S
+    float *Bpart = nullptr;        // split-K slices of that product
     double *G64[2] = {nullptr, nullptr};
     double *scal[2] = {nullptr, nullptr};
     float *Gf = nullptr;
@@ -194,12 +196,14 @@ void prepare(dsanls_ctx *h) {
     const bool gauss = h->sketch == DSANLS_SKETCH_GAUSSIAN;
     const bool ident = h->sketch == DSANLS_SKETCH_IDENTITY;
     const bool bf16 = h->opt.precision == DSANLS_PREC_BF16;
-    dalloc(h->S, gauss ? std::max(n * h->d, m * dv) : 0);
+    dalloc(h->S, (gauss && !bf16) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->Sb, (gauss && bf16) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->J, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? dmax : 0);
     dalloc(h->A, (gauss && !bf16) ? std::max(m * h->d, n * dv) : 0);
     dalloc(h->W, k * (ident ? std::max(m, n) : dmax));
-    dalloc(h->Wpart, gauss ? (int64_t)MAX_SPLITS * k * dmax : 0);
+    dalloc(h->Wpart, (gauss && !bf16) ? (int64_t)MAX_SPLITS * k * dmax : 0);
+    dalloc(h->Ytb, (gauss && bf16) ? k * std::max(m, n) : 0);
+    dalloc(h->Bpart, (gauss && bf16) ? tc_gemm_part_elems(k, dmax) : 0);
     dalloc(h->R, std::max(m, n) * k);
     dalloc(h->Rpart, (gauss && bf16) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
     if (h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE) {
@@ -252,12 +256,19 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     if (h->sketch == DSANLS_SKETCH_GAUSSIAN) {
         const float scale = (float)(1.0 / std::sqrt((double)dd));
         const bool tc = dense && h->opt.precision == DSANLS_PREC_BF16;
-        // S (K x dd), N(0, 1/dd) entries of the field, stream `side`
-        launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, s);
-        if (tc) launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, s);
+        // S (K x dd), N(0, 1/dd) entries of the field, stream `side`: fp32 S for the
+        // CUDA-core form, bf16 S^T (K-major operand) for the tensor-core form
+        if (tc)
+            launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, s);
+        else
+            launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, s);
         mark(pe, DSANLS_PHASE_B, s);
-        // B = Y^T S  (k x dd), split over K, partials summed in order
-        {
+        if (tc) {
+            // B = Y^T S (k x dd) on tensor cores from bf16 Y^T and S^T, split-K
+            launch_transpose_bf16(Y, K, k, h->Ytb, s);
+            launch_tc_gemm(h->Ytb, h->Sb, k, K, dd, h->Bpart, h->W, h->flag, s);
+        } else {
+            // B = Y^T S  (k x dd), split over K, partials summed in order
             const int64_t tiles = ceil_div(k, 128) * ceil_div(dd, 128);
             int splits = (int)std::min<int64_t>(MAX_SPLITS, std::max<int64_t>(1, (2 * 152) / std::max<int64_t>(1, tiles)));
             splits = (int)std::min<int64_t>(splits, std::max<int64_t>(1, K / 256));
@@ -812,7 +823,7 @@ void dsanls_destroy(dsanls_t h) {
         dfree(h->rp); dfree(h->trp); dfree(h->ci); dfree(h->tci); dfree(h->cv); dfree(h->tcv);
         dfree(h->U); dfree(h->V);
         dfree(h->S); dfree(h->Sb); dfree(h->J); dfree(h->A); dfree(h->W); dfree(h->Wpart); dfree(h->R);
-        dfree(h->Rpart);
+        dfree(h->Rpart); dfree(h->Ytb); dfree(h->Bpart);
         for (int side = 0; side < 2; ++side) {
             dfree(h->G64[side]);
             dfree(h->scal[side]);

@@ -76,14 +76,26 @@ __global__ void __launch_bounds__(GRAM_THREADS)
         if (threadIdx.x + q * GRAM_THREADS < npairs) out[pa[q] * k + pb[q]] = acc[q];
 }
 
+// One warp per pair (a <= b): lanes take every 32nd partial, then a fixed
+// shuffle tree; the result is written to G[a][b] and G[b][a].
 __global__ void k_gram_reduce(const double *__restrict__ part, int nparts, int k, double *__restrict__ G) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= k * k) return;
-    const int a = idx / k, b = idx % k;
-    const int lo = min(a, b), hi = max(a, b);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int npairs = k * (k + 1) / 2;
+    if (warp >= npairs) return;
+    int a = 0, rem = (int)warp;
+    while (rem >= k - a) {
+        rem -= k - a;
+        ++a;
+    }
+    const int b = a + rem;
     double acc = 0.0;
-    for (int c = 0; c < nparts; ++c) acc += part[(int64_t)c * k * k + lo * k + hi];
-    G[idx] = acc;
+    for (int c = lane; c < nparts; c += 32) acc += part[(int64_t)c * k * k + a * k + b];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        G[a * k + b] = acc;
+        G[b * k + a] = acc;
+    }
 }
 
 void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, int64_t work_elems,
@@ -100,77 +112,83 @@ void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, in
     const size_t smem = (size_t)k * (dc + 1) * sizeof(float);
     k_gram_partial<<<(unsigned)grid, GRAM_THREADS, smem, s>>>(W, k, d, dc, work);
     DSANLS_LAUNCH_CHECK();
-    k_gram_reduce<<<(unsigned)ceil_div((int64_t)k * k, 256), 256, 0, s>>>(work, (int)grid, k, G64);
+    const int64_t npairs = (int64_t)k * (k + 1) / 2;
+    k_gram_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, s>>>(work, (int)grid, k, G64);
     DSANLS_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------------------
 // step size: lambda_max by power iteration, mu_t, eta_t
 // ---------------------------------------------------------------------------
-__device__ float block_sum_f(float v, float *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    float tot = 0.0f;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) tot += red[i];
-    return tot;
-}
-
-__device__ double block_sum_d(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double tot = 0.0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) tot += red[i];
-    return tot;
-}
-
-// blockDim.x == 128 >= k
-__global__ void k_step_size(const double *__restrict__ G64, int k, int iters, double alpha, double beta,
-                            const int64_t *__restrict__ t_dev, double *__restrict__ scal, float *__restrict__ Gf,
-                            int kp) {
+// One warp: lane l owns rows l, l+32, l+64, l+96 of the power iteration
+// (binary32, G in shared memory); Rayleigh quotient x^T G x in FP64.
+__global__ void __launch_bounds__(32)
+    k_step_size(const double *__restrict__ G64, int k, int iters, double alpha, double beta,
+                const int64_t *__restrict__ t_dev, double *__restrict__ scal, float *__restrict__ Gf, int kp) {
     extern __shared__ float gs[];  // k x (k+1)
     __shared__ float x[128];
-    __shared__ float redf[4];
-    __shared__ double redd[4];
-    const int i = threadIdx.x;
-    for (int e = i; e < kp * kp; e += blockDim.x) {
+    const int lane = threadIdx.x;
+    for (int e = lane; e < kp * kp; e += 32) {
         const int a = e / kp, b = e % kp;
         const float v = (a < k && b < k) ? (float)G64[a * k + b] : 0.0f;
         Gf[e] = v;
         if (a < k && b < k) gs[a * (k + 1) + b] = v;
     }
-    if (i < 128) x[i] = (i < k) ? rsqrtf((float)k) : 0.0f;
-    __syncthreads();
+    const float x0 = rsqrtf((float)k);
+    for (int i = lane; i < 128; i += 32) x[i] = (i < k) ? x0 : 0.0f;
+    __syncwarp();
     for (int it = 0; it < iters; ++it) {
-        float y = 0.0f;
-        if (i < k)
-            for (int l = 0; l < k; ++l) y = fmaf(gs[i * (k + 1) + l], x[l], y);
-        const float nrm2 = block_sum_f(y * y, redf);
-        __syncthreads();
-        if (nrm2 > 0.0f && i < k) x[i] = y * rsqrtf(nrm2);
-        __syncthreads();
+        float y[4];
+        float nrm2 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            // four interleaved partial sums (l mod 4) shorten the dependency chain
+            float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+            if (i < k) {
+                const float *gi = gs + i * (k + 1);
+                int l = 0;
+                for (; l + 3 < k; l += 4) {
+                    a0 = fmaf(gi[l], x[l], a0);
+                    a1 = fmaf(gi[l + 1], x[l + 1], a1);
+                    a2 = fmaf(gi[l + 2], x[l + 2], a2);
+                    a3 = fmaf(gi[l + 3], x[l + 3], a3);
+                }
+                for (; l < k; ++l) a0 = fmaf(gi[l], x[l], a0);
+            }
+            const float acc = (a0 + a1) + (a2 + a3);
+            y[q] = acc;
+            nrm2 = fmaf(acc, acc, nrm2);
+        }
+        for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
         if (nrm2 == 0.0f) break;
+        const float inv = rsqrtf(nrm2);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            if (i < k) x[i] = y[q] * inv;
+        }
+        __syncwarp();
     }
-    // Rayleigh quotient x^T G x in FP64 with the FP64 G
-    double part = 0.0;
-    if (i < k) {
-        double gx = 0.0;
-        for (int l = 0; l < k; ++l) gx = fma(G64[i * k + l], (double)x[l], gx);
-        part = (double)x[i] * gx;
+    double xgx = 0.0, xx = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        if (i < k) {
+            double gx = 0.0;
+            for (int l = 0; l < k; ++l) gx = fma(G64[i * k + l], (double)x[l], gx);
+            xgx = fma((double)x[i], gx, xgx);
+            xx = fma((double)x[i], (double)x[i], xx);
+        }
     }
-    const double xgx = block_sum_d(part, redd);
-    double xx = block_sum_d(i < k ? (double)x[i] * (double)x[i] : 0.0, redd);
-    if (i == 0) {
+    for (int o = 16; o > 0; o >>= 1) {
+        xgx += __shfl_xor_sync(0xffffffffu, xgx, o);
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
+    if (lane == 0) {
         const double lam = xx > 0.0 ? xgx / xx : 0.0;
-        const double t = (double)(*t_dev);
-        const double mu = alpha + beta * t;
+        const double mu = alpha + beta * (double)(*t_dev);
         scal[0] = lam;
         scal[1] = mu;
         scal[2] = 1.0 / (lam + mu);
@@ -180,7 +198,7 @@ __global__ void k_step_size(const double *__restrict__ G64, int k, int iters, do
 void launch_step_size(const double *G64, int k, int iters, double alpha, double beta, const int64_t *t_dev,
                       double *scal, float *Gf, int kp, cudaStream_t s) {
     const size_t smem = (size_t)k * (k + 1) * sizeof(float);
-    k_step_size<<<1, 128, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
+    k_step_size<<<1, 32, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
     DSANLS_LAUNCH_CHECK();
 }
 

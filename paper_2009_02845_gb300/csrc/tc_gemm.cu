@@ -17,12 +17,15 @@
 //              layout the second MMA reads; then tcgen05.ld of D2 and store
 //              of the partial R of this d-chunk.
 // Partial R of the d/256 chunks is summed in chunk order by a second kernel
-// (deterministic).  Every mbarrier wait is bounded: on timeout the kernel
+// (deterministic).  The same kernel without the second product (FUSED =
+// false) computes the plain product B = Y^T S with split-K over a grid of
+// about one wave; the split slices are summed in order.  Every mbarrier wait is bounded: on timeout the kernel
 // raises bit 2 of the error flag, drains its own TMA copies, frees TMEM and
 // returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -43,6 +46,7 @@ constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t D2_COL = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded wait: 2 s of wall time
+constexpr int kMaxSplits = 32;                         // split-K slices of the plain product
 
 // ---- PTX helpers ---------------------------------------------------------
 DSANLS_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -161,19 +165,23 @@ struct __align__(8) TcSmemTail {
 
 }  // namespace
 
-// X: rows x K bf16 (map_x: box 64 x 128), S^T: d x K bf16 (map_s: box 64 x 256),
-// B: k x d bf16 (map_b: box 64 x kp).  Rpart[chunk][rows][k] (chunk = N tile).
-template <int STAGES>
+// FUSED = true:  X rows x K bf16 (map_x: box 64 x 128), S^T d x K bf16
+//   (map_s: box 64 x 256), B k x d bf16 (map_b: box 64 x kp); writes the partial
+//   R of this d-chunk: out[chunk][rows][k].
+// FUSED = false: plain product C = X S over the K-range of split blockIdx.y
+//   (k-blocks [y*kb_per_split, ...)); writes out[split][rows][ldo] for the
+//   columns of this chunk (columns < d).
+template <int STAGES, bool FUSED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_sketch_rhs(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
-                    const __grid_constant__ CUtensorMap map_b, int64_t rows, int64_t K, int64_t d, int k, int kp,
-                    float *__restrict__ Rpart, int *__restrict__ err) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
+              const __grid_constant__ CUtensorMap map_b, int64_t rows, int64_t K, int64_t d, int k, int kp,
+              int kb_per_split, float *__restrict__ out, int *__restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *stage_base = smem;                                  // STAGES x (A 16 KB | B 32 KB)
-    uint8_t *btile = smem + STAGES * STAGE_BYTES;                // 4 atoms of kp x 128 B
-    TcSmemTail *tail = (TcSmemTail *)(btile + 4 * kp * 128);
+    uint8_t *btile = smem + STAGES * STAGE_BYTES;                // 4 atoms of kp x 128 B (FUSED)
+    TcSmemTail *tail = (TcSmemTail *)(btile + (FUSED ? 4 * kp * 128 : 0));
     uint8_t *a2 = stage_base;                                    // reused after the main loop: 4 x 16 KB
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -181,7 +189,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int chunk = blockIdx.x % nchunks;
     const int64_t m0 = (int64_t)(blockIdx.x / nchunks) * BM;
     const int n0 = chunk * BN;
-    const int nk = (int)ceil_div(K, BK);
+    const int nk_total = (int)ceil_div(K, BK);
+    const int kb0 = FUSED ? 0 : (int)blockIdx.y * kb_per_split;
+    const int nk = FUSED ? nk_total : max(0, min(kb_per_split, nk_total - kb0));
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -211,9 +221,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // B tile first (needed only at the end), then the K ring
-            mbar_expect_tx(&tail->b_full, 4u * kp * 128u);
-            for (int a = 0; a < 4; ++a) tma_load_2d(btile + a * kp * 128, &map_b, n0 + a * 64, 0, &tail->b_full);
+            if (FUSED) {  // B tile first (needed only at the end), then the K ring
+                mbar_expect_tx(&tail->b_full, 4u * kp * 128u);
+                for (int a = 0; a < 4; ++a) tma_load_2d(btile + a * kp * 128, &map_b, n0 + a * 64, 0, &tail->b_full);
+            }
             int issued = 0;
             for (int kb = 0; kb < nk; ++kb) {
                 const int s = kb % STAGES;
@@ -225,14 +236,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (*(volatile int *)&tail->failed) break;
                 uint8_t *sa = stage_base + s * STAGE_BYTES;
                 mbar_expect_tx(&tail->full[s], STAGE_BYTES);
-                tma_load_2d(sa, &map_x, kb * BK, (int)m0, &tail->full[s]);
-                tma_load_2d(sa + A_STAGE_BYTES, &map_s, kb * BK, n0, &tail->full[s]);
+                tma_load_2d(sa, &map_x, (kb0 + kb) * BK, (int)m0, &tail->full[s]);
+                tma_load_2d(sa + A_STAGE_BYTES, &map_s, (kb0 + kb) * BK, n0, &tail->full[s]);
                 ++issued;
             }
             // drain: every copy this thread issued has landed before the CTA can exit
             for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
                 mbar_wait(&tail->full[kb % STAGES], (kb / STAGES) & 1);
-            mbar_wait(&tail->b_full, 0);
+            if (FUSED) mbar_wait(&tail->b_full, 0);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -254,20 +265,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (ok) {
                 mma_commit(&tail->d1_full);
-                // second product: D2 = bf16(D1) B_tile^T, K = 256 in 16 steps
-                if (mbar_wait(&tail->a2_ready, 0) && mbar_wait(&tail->b_full, 0)) {
-                    fence_after();
-                    const uint32_t id2 = idesc_bf16(BM, kp);
-                    const uint32_t a2s = smem_u32(a2), bts = smem_u32(btile);
+                if (FUSED) {
+                    // second product: D2 = bf16(D1) B_tile^T, K = 256 in 16 steps
+                    if (mbar_wait(&tail->a2_ready, 0) && mbar_wait(&tail->b_full, 0)) {
+                        fence_after();
+                        const uint32_t id2 = idesc_bf16(BM, kp);
+                        const uint32_t a2s = smem_u32(a2), bts = smem_u32(btile);
 #pragma unroll
-                    for (int kk = 0; kk < BN / 16; ++kk) {
-                        const uint32_t ad = a2s + (kk >> 2) * (BM * 128) + (kk & 3) * 32;
-                        const uint32_t bd = bts + (kk >> 2) * (kp * 128) + (kk & 3) * 32;
-                        mma_bf16(tmem + D2_COL, sw128_desc(ad), sw128_desc(bd), id2, kk != 0);
+                        for (int kk = 0; kk < BN / 16; ++kk) {
+                            const uint32_t ad = a2s + (kk >> 2) * (BM * 128) + (kk & 3) * 32;
+                            const uint32_t bd = bts + (kk >> 2) * (kp * 128) + (kk & 3) * 32;
+                            mma_bf16(tmem + D2_COL, sw128_desc(ad), sw128_desc(bd), id2, kk != 0);
+                        }
+                        mma_commit(&tail->d2_full);
+                    } else {
+                        ok = false;
                     }
-                    mma_commit(&tail->d2_full);
-                } else {
-                    ok = false;
                 }
             }
             if (!ok) {
@@ -281,49 +294,70 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp >= 4) {
         const int q = warp & 3;  // TMEM lane quarter of this warp
         const int r = q * 32 + lane;
+        const int64_t row = m0 + r;
         const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
         bool ok = mbar_wait(&tail->d1_full, 0);
-        if (ok) {
-            fence_after();
-            // D1 (fp32) -> bf16, 128B-swizzled K-major layout: atom a = col / 64
+        if (!FUSED) {
+            // D1 (fp32) straight to the split's slice; nk == 0 leaves D1 unwritten: store zeros
+            if (ok) {
+                fence_after();
+                float *dst = out + ((int64_t)blockIdx.y * rows + row) * d + n0;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                uint32_t v[32];
-                tmem_ld32(trow + c * 32, v);
-                tmem_ld_wait();
-                uint8_t *atom = a2 + (c >> 1) * (BM * 128) + r * 128;
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t v[32];
+                    tmem_ld32(trow + c * 32, v);
+                    tmem_ld_wait();
+                    if (row < rows) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {  // 4 chunks of 8 bf16 (16 bytes)
-                    const int chunk16 = (c & 1) * 4 + j;
-                    uint4 w;
-                    w.x = pack_bf16(__uint_as_float(v[8 * j + 0]), __uint_as_float(v[8 * j + 1]));
-                    w.y = pack_bf16(__uint_as_float(v[8 * j + 2]), __uint_as_float(v[8 * j + 3]));
-                    w.z = pack_bf16(__uint_as_float(v[8 * j + 4]), __uint_as_float(v[8 * j + 5]));
-                    w.w = pack_bf16(__uint_as_float(v[8 * j + 6]), __uint_as_float(v[8 * j + 7]));
-                    *reinterpret_cast<uint4 *>(atom + ((chunk16 ^ (r & 7)) << 4)) = w;
+                        for (int j = 0; j < 32; ++j)
+                            if (n0 + c * 32 + j < d) dst[c * 32 + j] = nk > 0 ? __uint_as_float(v[j]) : 0.0f;
+                    }
                 }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
-        mbar_arrive(&tail->a2_ready);
-        if (ok) ok = mbar_wait(&tail->d2_full, 0);
-        if (ok) {
-            fence_after();
-            const int64_t row = m0 + r;
-            float *dst = Rpart + ((int64_t)chunk * rows + row) * k;
-#pragma unroll 1
-            for (int c0 = 0; c0 < kp; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(trow + D2_COL + c0, v);
-                tmem_ld_wait();
-                if (row < rows) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (c0 + j < k) dst[c0 + j] = __uint_as_float(v[j]);
-                }
+            } else {
+                atomicOr(err, 2);
             }
         } else {
-            atomicOr(err, 2);
+            if (ok) {
+                fence_after();
+                // D1 (fp32) -> bf16, 128B-swizzled K-major layout: atom a = col / 64
+#pragma unroll 1
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t v[32];
+                    tmem_ld32(trow + c * 32, v);
+                    tmem_ld_wait();
+                    uint8_t *atom = a2 + (c >> 1) * (BM * 128) + r * 128;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {  // 4 chunks of 8 bf16 (16 bytes)
+                        const int chunk16 = (c & 1) * 4 + j;
+                        uint4 w;
+                        w.x = pack_bf16(__uint_as_float(v[8 * j + 0]), __uint_as_float(v[8 * j + 1]));
+                        w.y = pack_bf16(__uint_as_float(v[8 * j + 2]), __uint_as_float(v[8 * j + 3]));
+                        w.z = pack_bf16(__uint_as_float(v[8 * j + 4]), __uint_as_float(v[8 * j + 5]));
+                        w.w = pack_bf16(__uint_as_float(v[8 * j + 6]), __uint_as_float(v[8 * j + 7]));
+                        *reinterpret_cast<uint4 *>(atom + ((chunk16 ^ (r & 7)) << 4)) = w;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            mbar_arrive(&tail->a2_ready);
+            if (ok) ok = mbar_wait(&tail->d2_full, 0);
+            if (ok) {
+                fence_after();
+                float *dst = out + ((int64_t)chunk * rows + row) * k;
+#pragma unroll 1
+                for (int c0 = 0; c0 < kp; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(trow + D2_COL + c0, v);
+                    tmem_ld_wait();
+                    if (row < rows) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < k) dst[c0 + j] = __uint_as_float(v[j]);
+                    }
+                }
+            } else {
+                atomicOr(err, 2);
+            }
         }
     }
     fence_before();
@@ -417,17 +451,62 @@ void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const
     const int stages = stages_for(kp);
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
-        k_tc_sketch_rhs<4><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, Rpart, err);
+        k_tc_gemm<4, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart, err);
     else
-        k_tc_sketch_rhs<3><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, Rpart, err);
+        k_tc_gemm<3, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart, err);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
     DSANLS_LAUNCH_CHECK();
 }
 
+int64_t tc_gemm_part_elems(int64_t rows, int64_t d) { return (int64_t)kMaxSplits * rows * d; }
+
+void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t rows, int64_t K, int64_t d,
+                    float *part, float *C, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || d > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0 || d % 8 != 0) throw ArgError{"tensor-core path needs K and d multiples of 8"};
+    const int64_t tiles = ceil_div(rows, BM) * ceil_div(d, BN);
+    const int nk = (int)ceil_div(K, BK);
+    // about one wave of CTAs; every split gets at least one k-block
+    int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, ceil_div(152, tiles)));
+    splits = std::min(splits, nk);
+    const int kb_per_split = (int)ceil_div(nk, splits);
+    splits = (int)ceil_div(nk, kb_per_split);
+    const CUtensorMap mx = make_map(X, rows, K, BM);
+    const CUtensorMap ms = make_map(St, d, K, BN);
+    dim3 grid((unsigned)tiles, (unsigned)splits);
+    k_tc_gemm<4, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, d, 0, 0, kb_per_split, part,
+                                                                  err);
+    DSANLS_LAUNCH_CHECK();
+    launch_split_reduce(part, rows * d, splits, rows, d, d, C, d, s);
+}
+
+__global__ void k_transpose_bf16(const float *__restrict__ in, int64_t rows, int64_t cols,
+                                 __nv_bfloat16 *__restrict__ out) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t r = r0 + y, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[y][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t c = c0 + y, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+    }
+}
+
+void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *out, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
+    k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, out);
+    DSANLS_LAUNCH_CHECK();
+}
+
 void prime_tc_attributes(int max_smem) {
-    allow_max_dynamic_smem(k_tc_sketch_rhs<4>, max_smem);
-    allow_max_dynamic_smem(k_tc_sketch_rhs<3>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, true>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<3, true>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, false>, max_smem);
 }
 
 }  // namespace dsanls

@@ -16,6 +16,13 @@ int64_t tc_rpart_elems(int64_t rows, int64_t d, int k);
 // bounded wait that gives up sets bit 2 of *err.  K and d must be multiples of 8.
 void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const float *B, int64_t rows, int64_t K,
                           int64_t d, int k, float *Rpart, float *R, int *err, cudaStream_t s);
+// C (rows x d, fp32) = X S with X rows x K bf16 and S^T d x K bf16, split-K;
+// `part` is scratch of tc_gemm_part_elems(rows, d) floats.
+int64_t tc_gemm_part_elems(int64_t rows, int64_t d);
+void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t rows, int64_t K, int64_t d,
+                    float *part, float *C, int *err, cudaStream_t s);
+// out (cols x rows, bf16) = in^T for in rows x cols fp32 row-major.
+void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *out, cudaStream_t s);
 void prime_tc_attributes(int max_smem);
 
 }  // namespace dsanls

@@ -1,0 +1,75 @@
+"""Full-size parity on the benchmark workload (dense 65,536 x 16,384 planted,
+k = 64, Gaussian d = d' = 2048), in the launch configuration bench.py times
+(CUDA-graph handle, default Philox initial factors).
+
+The oracle cannot redo whole half-steps at this size in a test, but the
+subproblem is row-independent (eq. u_block): it recomputes a sample of rows
+(first, last, ragged-tile neighbours and random rows) from the full sketch,
+the full B = Y^T S and G, and compares them with the GPU's rows.
+Tolerances: binary32 form <= 1e-5 norm-wise on the sampled rows; bf16 form
+<= 3e-4 against the oracle's bf16 model and <= 5e-3 against plain FP64.
+"""
+import numpy as np
+import pytest
+
+from oracle import method
+from synthdata import planted_dense
+
+pytestmark = pytest.mark.gpu
+
+M_ROWS, N_COLS, K, D = 65536, 16384, 64, 2048
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2009_02845_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def data():
+    M, _, _ = planted_dense(M_ROWS, N_COLS, K, 0, zero_frac=0.7)
+    U0, V0 = method.default_init(0, M_ROWS, N_COLS, K)
+    return M, U0.astype(np.float64), V0.astype(np.float64)
+
+
+def _sample(n, rng):
+    fixed = [0, 1, 127, 128, 129, n // 2, n - 129, n - 128, n - 2, n - 1]
+    return np.unique(np.concatenate([fixed, rng.choice(n, 54, replace=False)]))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("side", [0, 1])
+def test_fullsize_half_step_sampled_rows(pkg, data, precision, side):
+    M, U0, V0 = data
+    prec = pkg.BF16 if precision == "bf16" else pkg.FP32
+    h = pkg.DSANLS(M_ROWS, N_COLS, K, D, pkg.GAUSSIAN, seed=0, precision=prec, use_graph=1)
+    h.set_dense(M)
+    h.half_step(side)
+    Ug, Vg = h.factors()
+    G_gpu, eta_gpu = h.gram(side)
+    h.close()
+    got = Ug if side == 0 else Vg
+    rng = np.random.default_rng(side)
+    rows_all = M_ROWS if side == 0 else N_COLS
+    rows = _sample(rows_all, rng)
+    K_dim = N_COLS if side == 0 else M_ROWS
+    S = method.Sketch(method.GAUSSIAN, 0, 0, side, K_dim, D)
+    Xs = (M[rows] if side == 0 else M[:, rows].T).astype(np.float64)
+    Y = V0 if side == 0 else U0
+    Z = (U0 if side == 0 else V0)[rows]
+    mu = method.mu_t(1.0, 1.0, 0)
+    exact = method.half_step(Xs, Y, Z, S, method.PGD, mu)
+    if precision == "fp32":
+        assert _rel(got[rows], exact) <= 1e-5
+        _, _, G, _ = method.sketched_terms(Xs[:1], Y, S)
+        assert _rel(G_gpu, G) <= 1e-5
+    else:
+        model = method.half_step(Xs, Y, Z, S, method.PGD, mu, bf16=True)
+        assert _rel(got[rows], model) <= 3e-4, _rel(got[rows], model)
+        assert _rel(got[rows], exact) <= 5e-3, _rel(got[rows], exact)
+    assert got.min() >= 0.0 and np.isfinite(got).all()
