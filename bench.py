@@ -51,6 +51,11 @@ WORKLOADS = {
                              "log(1+Poisson) values, ~2e8 nnz), k=100, subsampling d=d'=5000, PGD"),
     "sparse_text_small": dict(m=200_000, n=50_000, k=100, d=500, d_v=500, sketch=1, sparse=True,
                               desc="CSR 2e5 x 5e4 text-like (~2e7 nnz), k=100, subsampling d=d'=500, PGD"),
+    "batched": dict(batched=True, count=1024, m=0, n=0, k=0, d=0, d_v=0, sketch=0,
+                    desc="1024 uneven planted instances (m in [128,4096], n in [64,2048], k in {8,16,32}), "
+                         "Gaussian d=max(4k,n/8), d'=max(4k,m/8), PGD, binary32"),
+    "batched_small": dict(batched=True, count=64, m=0, n=0, k=0, d=0, d_v=0, sketch=0,
+                          desc="64 uneven planted instances (same recipe), binary32"),
     "small": dict(m=1000, n=800, k=10, d=100, d_v=100, sketch=0, zero_frac=0.0, noise=0.01,
                   desc="planted 1000x800, k=10, Gaussian d=100, PGD"),
 }
@@ -445,10 +450,111 @@ def main():
                     help="also run T outer iterations of the fp32 and bf16 forms and report time to eps")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if w.get("batched"):
+        run_batch(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_ours(args, w)
+
+
+def _batch_inputs(count):
+    from synthdata import batch_specs, planted_dense
+    specs = batch_specs(count, 0)
+    Ms = [planted_dense(s["m"], s["n"], s["k"], s["seed"])[0] for s in specs]
+    return specs, Ms
+
+
+def run_batch(args, w):
+    """Batched uneven instances: one step = one outer iteration of every
+    instance; value = batch outer iterations/s (x ranks for replicas)."""
+    ws, rank, local = _dist()
+    specs, Ms = _batch_inputs(w["count"])
+    flops = sum(2.0 * s["m"] * s["n"] * (s["d"] + s["d_v"]) + 2.0 * s["k"] * (s["m"] * s["d"] + s["n"] * s["d_v"])
+                for s in specs)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from oracle import method
+        # bounded sample: one outer iteration of every 64th instance, scaled by problem size
+        t0 = time.perf_counter()
+        sample = list(range(0, len(specs), 64))
+        sf = 0.0
+        for i in sample:
+            s = specs[i]
+            U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+            method.run(Ms[i], U0, V0, s["seed"], 1, method.Options(sketch=0, d=s["d"], d_v=s["d_v"]), log_error=False)
+            sf += 2.0 * s["m"] * s["n"] * (s["d"] + s["d_v"])
+        dt = (time.perf_counter() - t0) * (flops / sf)
+        value = 1.0 / dt
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                          "steps": 1, "warmup": 0, "ms_per_step": 1000 * dt, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": args.workload, "desc": w["desc"], "instances": len(specs)},
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                                           "sample": "%d of %d instances, scaled by FLOPs" % (len(sample), len(specs))},
+                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    import torch
+    import paper_2009_02845_gb300 as pkg
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b = pkg.Batch(specs, use_graph=1)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    for _ in range(args.warmup):
+        b.step(1)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = pkg.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = pkg.kernel_launches() - l0
+    clk = clocks.stop()
+    errs = b.rel_errors()
+    prof = b.profile()
+    ar_ms = prof["U"]["AR"] + prof["V"]["AR"]
+    ar_flops = flops
+    achieved = ar_flops / (ar_ms / 1000.0) / 1e12
+    value = ws * args.steps / (ms / 1000.0)
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import method
+        t0 = time.perf_counter()
+        sample = list(range(0, len(specs), 128))
+        sf = 0.0
+        for i in sample:
+            s = specs[i]
+            U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+            method.run(Ms[i], U0, V0, s["seed"], 1, method.Options(sketch=0, d=s["d"], d_v=s["d_v"]), log_error=False)
+            sf += 2.0 * s["m"] * s["n"] * (s["d"] + s["d_v"])
+        dt = (time.perf_counter() - t0) * (flops / sf)
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+               "sample": "one outer iteration of %d of %d instances, scaled by FLOPs" % (len(sample), len(specs))}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "instances": len(specs),
+                       "graph": True, "persistent_ctas": b.tuned_blocks(),
+                       "l2": "inputs larger than L2 (M_i total %.1f GB)" % (sum(M.nbytes for M in Ms) / 1e9)},
+            "instance_iters_per_s": value * len(specs),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None, "kernel": "kb_ar",
+                         "peak_source": "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz",
+                         "launch_ms": [prof["U"]["AR"], prof["V"]["AR"]]},
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk,
+            "phases_ms": prof, "rel_error_median": float(np.median(errs)), "rel_error_max": float(errs.max()),
+        }), flush=True)
+    b.close()
 
 
 if __name__ == "__main__":

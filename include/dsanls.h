@@ -198,6 +198,90 @@ int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t 
 int dsanls_subsample_indices(uint64_t seed, uint32_t side, uint64_t t, int64_t n, int32_t d,
                              int32_t *J, void *stream);
 
+/* ---- batched form: many independent dense problems ---------------------
+ * A batch advances `count` independent problems M_i (m_i x n_i) ~ U_i V_i^T
+ * together, each with its own rank k_i (1..32), sketch sizes d_i, d'_i and
+ * Philox seed_i (Gaussian sketches; binary32 arithmetic).  Every phase of a
+ * half-step is one persistent kernel that takes (instance, tile) work items
+ * from a device queue; with use_graph each outer iteration is one CUDA graph
+ * launch.  The first dsanls_batch_step times a few persistent launch
+ * geometries on the real batch (factors and t are restored afterwards) and
+ * keeps the fastest, cached per batch shape list and dtype in the process
+ * and, when DSANLS_TUNE_CACHE names a file, across processes.  Default
+ * factors are the Uniform[0,1) draws of streams 2 and 3 keyed by seed_i.
+ * Instance i follows exactly the single-problem method of dsanls_create. */
+typedef struct dsanls_batch_ctx *dsanls_batch_t;
+
+/* Arrays of length count: m, n (1..2^24), k (1..32), d and d_v (1..2^20), seeds.
+ * EINVAL, ENOMEM, ECUDA (message in dsanls_last_error(NULL)). */
+int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const int32_t *k,
+                        const int32_t *d, const int32_t *d_v, const uint64_t *seeds,
+                        dsanls_batch_t *out);
+/* solver, alpha, beta, power_iters, t, use_graph, stream are used; precision
+ * must be FP32, bound_clamp 0, d_v ignored (given per instance). */
+int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt);
+/* Dense M_i (m_i x n_i, row stride ld); copied, with its transpose. Synchronises. */
+int dsanls_batch_set_dense(dsanls_batch_t b, int32_t i, const float *M, int64_t ld, int32_t on_device);
+int dsanls_batch_set_factors(dsanls_batch_t b, int32_t i, const float *U, const float *V, int32_t on_device);
+/* outer_iters iterations of every instance; ESTATE until every M_i is set. */
+int dsanls_batch_step(dsanls_batch_t b, int32_t outer_iters);
+int dsanls_batch_get_factors(dsanls_batch_t b, int32_t i, float *U, float *V, int32_t on_device);
+/* out[i] = ||M_i - U_i V_i^T||_F / ||M_i||_F for every instance (host array of count). */
+int dsanls_batch_rel_error(dsanls_batch_t b, double *out);
+/* Run both half-steps once (advancing the factors, not t) with CUDA events
+ * around the five phases; ms[side*5 + p] = milliseconds of phase p (0 sketch,
+ * 1 B = Y^T S, 2 R = (X S) B^T, 3 Gram and step size, 4 update).  Synchronises. */
+int dsanls_batch_profile(dsanls_batch_t b, double *ms);
+/* Persistent CTAs chosen by the autotuner (0 before the first step). */
+int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas);
+const char *dsanls_batch_last_error(dsanls_batch_t b);
+void dsanls_batch_destroy(dsanls_batch_t b);
+
+/* ---- learned warm start (k <= 32) ---------------------------------------
+ * Learned form of a half-step: for each row, the proximal row problem
+ *   f(x) = 1/2 x^T (G + mu_t I) x - (r + mu_t u)^T x,  x >= 0   (eq. reg_sub)
+ * is started from a small MLP's prediction, corrected by pg_iters projected
+ * gradient steps (step eta_t), and the plain projected-gradient step of
+ * eq. gradient_descent is kept instead whenever its objective is lower.
+ * Network: h1 = GELU(W1g vec(Gn) + W1b bn + b1), h2 = GELU(W2 h1 + b2),
+ * y = ReLU(W3 h2 + b3) on the normalised inputs Gn = (G + mu I)/s,
+ * s = tr(G + mu I)/k, bn = b/beta, beta = ||b||/sqrt(k); x0 = y beta/s.
+ * Parameters (fp32 masters, used rounded to bf16; fp32 accumulation), in
+ * order: W1g (h x k*k), W1b (h x k), b1 (h), W2 (h x h), b2 (h), W3 (k x h), b3 (k). */
+typedef struct dsanls_mlp_ctx *dsanls_mlp_t;
+
+/* k in [1, 32], hidden in [1, 256]; buffers for up to max_rows rows in
+ * max_groups subproblems per call; weights U(-sqrt(3/fan_in), +) from Philox
+ * stream 0x20 keyed by seed, biases 0. */
+int dsanls_mlp_create(int32_t k, int32_t hidden, int64_t max_rows, int32_t max_groups, uint64_t seed,
+                      dsanls_mlp_t *out);
+int dsanls_mlp_param_count(dsanls_mlp_t m, int64_t *count);
+int dsanls_mlp_get_params(dsanls_mlp_t m, float *theta);        /* host array of param_count */
+int dsanls_mlp_set_params(dsanls_mlp_t m, const float *theta);  /* host array of param_count */
+/* Device arrays: G (ngroups x k x k), mu (ngroups), group_off (ngroups + 1,
+ * rows of group g are group_off[g] .. group_off[g+1]-1), b (rows x k, b = r + mu u).
+ * x_out (rows x k) = the network's warm start in the original scale. */
+int dsanls_mlp_predict(dsanls_mlp_t m, const float *G, const float *mu, const int64_t *group_off, int32_t ngroups,
+                       const float *b, int64_t rows, float *x_out, void *stream);
+/* Loss 1/2 mean ||y - y*||^2 against the normalised exact minimisers
+ * y* = xstar s / beta, its gradient (host array, nullable) and, if lr > 0,
+ * one Adam step (beta1 0.9, beta2 0.999, eps 1e-8).  Synchronises. */
+int dsanls_mlp_train_step(dsanls_mlp_t m, const float *G, const float *mu, const int64_t *group_off,
+                          int32_t ngroups, const float *b, const float *xstar, int64_t rows, float lr,
+                          double *loss, float *grad, void *stream);
+void dsanls_mlp_destroy(dsanls_mlp_t m);
+/* Use network m (NULL: the plain solver) in the handle's half-steps; m must
+ * outlive its use; needs k <= 32 and m's max_rows >= max(m, n). */
+int dsanls_set_mlp(dsanls_t h, dsanls_mlp_t m, int32_t pg_iters);
+/* Rows (cumulative) for which the learned point was kept.  Synchronises. */
+int dsanls_mlp_kept(dsanls_t h, int64_t *kept);
+/* Training triples of the current state, without updating it: runs the
+ * sketched products of `side` at the current t and returns G (k x k, device
+ * fp32), mu_t (device, 1), b = r + mu u (rows x k, device) and x* (rows x k,
+ * device), the proximal minimiser by `iters` FISTA steps (Beck and Teboulle
+ * 2009).  k <= 32.  Synchronises. */
+int dsanls_harvest(dsanls_t h, int32_t side, int32_t iters, float *G, float *mu, float *b, float *xstar);
+
 /* ---- allocation-free Gram ---------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot let a library allocate device memory -- a host framework that

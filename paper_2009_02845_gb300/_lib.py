@@ -22,6 +22,12 @@ EXPORTED_SYMBOLS = [
     "dsanls_rel_error", "dsanls_get_factors", "dsanls_get_gram", "dsanls_sync", "dsanls_last_error",
     "dsanls_destroy", "dsanls_philox_field", "dsanls_gaussian_field", "dsanls_uniform_field",
     "dsanls_subsample_indices", "dsanls_profile_half_step", "dsanls_kernel_launches", "dsanls_gram_noalloc",
+    "dsanls_batch_create", "dsanls_batch_set_options", "dsanls_batch_set_dense", "dsanls_batch_set_factors",
+    "dsanls_batch_step", "dsanls_batch_get_factors", "dsanls_batch_rel_error", "dsanls_batch_tuned_blocks", "dsanls_batch_profile",
+    "dsanls_batch_last_error", "dsanls_batch_destroy",
+    "dsanls_mlp_create", "dsanls_mlp_param_count", "dsanls_mlp_get_params", "dsanls_mlp_set_params",
+    "dsanls_mlp_predict", "dsanls_mlp_train_step", "dsanls_mlp_destroy", "dsanls_set_mlp", "dsanls_mlp_kept",
+    "dsanls_harvest",
 ]
 NPHASES = 7
 PHASES = ["sketch", "B", "product", "rhs", "gram", "step_size", "update"]
@@ -83,6 +89,28 @@ def lib():
             "dsanls_profile_half_step": ([vp, i32, i32, vp], ctypes.c_int),
             "dsanls_kernel_launches": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
             "dsanls_gram_noalloc": ([vp, i32, i64, vp, vp], ctypes.c_int),
+            "dsanls_batch_create": ([i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], ctypes.c_int),
+            "dsanls_batch_set_options": ([vp, ctypes.POINTER(Options)], ctypes.c_int),
+            "dsanls_batch_set_dense": ([vp, i32, vp, i64, i32], ctypes.c_int),
+            "dsanls_batch_set_factors": ([vp, i32, vp, vp, i32], ctypes.c_int),
+            "dsanls_batch_step": ([vp, i32], ctypes.c_int),
+            "dsanls_batch_get_factors": ([vp, i32, vp, vp, i32], ctypes.c_int),
+            "dsanls_batch_rel_error": ([vp, vp], ctypes.c_int),
+            "dsanls_batch_tuned_blocks": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
+            "dsanls_batch_profile": ([vp, vp], ctypes.c_int),
+            "dsanls_batch_last_error": ([vp], ctypes.c_char_p),
+            "dsanls_batch_destroy": ([vp], None),
+            "dsanls_mlp_create": ([i32, i32, i64, i32, u64, ctypes.POINTER(vp)], ctypes.c_int),
+            "dsanls_mlp_param_count": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+            "dsanls_mlp_get_params": ([vp, vp], ctypes.c_int),
+            "dsanls_mlp_set_params": ([vp, vp], ctypes.c_int),
+            "dsanls_mlp_predict": ([vp, vp, vp, vp, i32, vp, i64, vp, vp], ctypes.c_int),
+            "dsanls_mlp_train_step": ([vp, vp, vp, vp, i32, vp, vp, i64, ctypes.c_float, dbl_p, vp, vp],
+                                      ctypes.c_int),
+            "dsanls_mlp_destroy": ([vp], None),
+            "dsanls_set_mlp": ([vp, vp, i32], ctypes.c_int),
+            "dsanls_mlp_kept": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+            "dsanls_harvest": ([vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -306,9 +334,165 @@ class DSANLS:
                "profile_half_step", self._h)
         return dict(zip(PHASES, ms.tolist()))
 
+    def set_mlp(self, mlp, pg_iters=4):
+        """Use the learned warm start `mlp` (an MLP; None for the plain solver)."""
+        self._mlp = mlp
+        _check(lib().dsanls_set_mlp(self._h, mlp._h if mlp is not None else None, int(pg_iters)), "set_mlp", self._h)
+
+    def mlp_kept(self):
+        v = ctypes.c_int64()
+        _check(lib().dsanls_mlp_kept(self._h, ctypes.byref(v)), "mlp_kept", self._h)
+        return v.value
+
+    def harvest(self, side, iters=300):
+        """(G, mu, b, x*) of the current state's `side` half-step as CUDA tensors (no update)."""
+        torch = _torch()
+        rows = self.m if side == 0 else self.n
+        G = torch.empty((self.k, self.k), dtype=torch.float32, device="cuda")
+        mu = torch.empty((1,), dtype=torch.float32, device="cuda")
+        b = torch.empty((rows, self.k), dtype=torch.float32, device="cuda")
+        x = torch.empty((rows, self.k), dtype=torch.float32, device="cuda")
+        _check(lib().dsanls_harvest(self._h, int(side), int(iters), _dev_ptr(G), _dev_ptr(mu), _dev_ptr(b),
+                                    _dev_ptr(x)), "harvest", self._h)
+        return G, mu, b, x
+
     def gram(self, side):
         G = np.empty((self.k, self.k), dtype=np.float64)
         eta = ctypes.c_double()
         _check(lib().dsanls_get_gram(self._h, int(side), G.ctypes.data_as(ctypes.c_void_p), ctypes.byref(eta)),
                "get_gram", self._h)
         return G, eta.value
+
+
+class Batch:
+    """Many independent dense problems advanced together (binary32)."""
+
+    def __init__(self, shapes, **options):
+        """shapes: list of dicts with m, n, k, d, d_v, seed."""
+        self.shapes = list(shapes)
+        c = len(self.shapes)
+        arr = lambda key, dt: np.ascontiguousarray([s[key] for s in self.shapes], dtype=dt)
+        self._keep = [arr("m", np.int64), arr("n", np.int64), arr("k", np.int32), arr("d", np.int32),
+                      arr("d_v", np.int32), arr("seed", np.uint64)]
+        ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in self._keep]
+        h = ctypes.c_void_p()
+        _check(lib().dsanls_batch_create(c, *ptrs, ctypes.byref(h)), "dsanls_batch_create")
+        self._h = h
+        if options:
+            self.set_options(**options)
+
+    def _err(self, code, what):
+        if code != OK:
+            m = lib().dsanls_batch_last_error(self._h)
+            raise DSANLSError(code, "%s: %s" % (what, m.decode() if m else ""))
+
+    def set_options(self, stream="current", **kw):
+        o = Options()
+        lib().dsanls_default_options(ctypes.byref(o))
+        for key, v in kw.items():
+            if not hasattr(o, key) or key == "stream":
+                raise TypeError("unknown option %r" % key)
+            setattr(o, key, v)
+        o.stream = _stream_ptr().value if stream == "current" else (None if stream is None else stream.cuda_stream)
+        self._err(lib().dsanls_batch_set_options(self._h, ctypes.byref(o)), "batch_set_options")
+
+    def set_dense(self, i, M):
+        p, dev, keep = _host_or_device(M, _dt("f32"))
+        self._err(lib().dsanls_batch_set_dense(self._h, int(i), p, int(keep.shape[1]), dev), "batch_set_dense")
+
+    def set_factors(self, i, U=None, V=None):
+        up, udev, ku = _host_or_device(U, _dt("f32")) if U is not None else (None, 0, None)
+        vp, vdev, kv = _host_or_device(V, _dt("f32")) if V is not None else (None, 0, None)
+        self._err(lib().dsanls_batch_set_factors(self._h, int(i), up, vp, udev or vdev), "batch_set_factors")
+
+    def step(self, iters=1):
+        self._err(lib().dsanls_batch_step(self._h, int(iters)), "batch_step")
+
+    def factors(self, i):
+        sh = self.shapes[i]
+        U = np.empty((sh["m"], sh["k"]), np.float32)
+        V = np.empty((sh["n"], sh["k"]), np.float32)
+        self._err(lib().dsanls_batch_get_factors(self._h, int(i), U.ctypes.data_as(ctypes.c_void_p),
+                                                 V.ctypes.data_as(ctypes.c_void_p), 0), "batch_get_factors")
+        return U, V
+
+    def rel_errors(self):
+        out = np.empty(len(self.shapes), np.float64)
+        self._err(lib().dsanls_batch_rel_error(self._h, out.ctypes.data_as(ctypes.c_void_p)), "batch_rel_error")
+        return out
+
+    def profile(self):
+        """Milliseconds per phase of one eager outer iteration: {side: {phase: ms}}."""
+        ms = np.zeros(10, np.float64)
+        self._err(lib().dsanls_batch_profile(self._h, ms.ctypes.data_as(ctypes.c_void_p)), "batch_profile")
+        names = ["sketch", "B", "AR", "gram", "update"]
+        return {side: dict(zip(names, ms[5 * i:5 * i + 5].tolist())) for i, side in enumerate(("U", "V"))}
+
+    def tuned_blocks(self):
+        v = ctypes.c_int32()
+        self._err(lib().dsanls_batch_tuned_blocks(self._h, ctypes.byref(v)), "batch_tuned_blocks")
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dsanls_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The learned warm start's network (k <= 32, hidden <= 256)."""
+
+    def __init__(self, k, hidden=256, max_rows=1 << 16, max_groups=64, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().dsanls_mlp_create(int(k), int(hidden), int(max_rows), int(max_groups), int(seed),
+                                       ctypes.byref(h)), "dsanls_mlp_create")
+        self._h = h
+        self.k, self.hidden = k, hidden
+        c = ctypes.c_int64()
+        _check(lib().dsanls_mlp_param_count(self._h, ctypes.byref(c)), "mlp_param_count")
+        self.n_params = c.value
+
+    def params(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(lib().dsanls_mlp_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)), "mlp_get_params")
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.n_params
+        _check(lib().dsanls_mlp_set_params(self._h, theta.ctypes.data_as(ctypes.c_void_p)), "mlp_set_params")
+
+    def predict(self, G, mu, off, b):
+        """G (groups x k x k), mu (groups), off (groups + 1, int64), b (rows x k): CUDA tensors."""
+        torch = _torch()
+        x = torch.empty_like(b)
+        _check(lib().dsanls_mlp_predict(self._h, _dev_ptr(G), _dev_ptr(mu), _dev_ptr(off), int(mu.numel()),
+                                        _dev_ptr(b), int(b.shape[0]), _dev_ptr(x), _stream_ptr()), "mlp_predict")
+        return x
+
+    def train_step(self, G, mu, off, b, xstar, lr, want_grad=False):
+        loss = ctypes.c_double()
+        grad = np.empty(self.n_params, np.float32) if want_grad else None
+        _check(lib().dsanls_mlp_train_step(self._h, _dev_ptr(G), _dev_ptr(mu), _dev_ptr(off), int(mu.numel()),
+                                           _dev_ptr(b), _dev_ptr(xstar), int(b.shape[0]), float(lr),
+                                           ctypes.byref(loss),
+                                           grad.ctypes.data_as(ctypes.c_void_p) if want_grad else None,
+                                           _stream_ptr()), "mlp_train_step")
+        return (loss.value, grad) if want_grad else loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dsanls_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -23,7 +23,7 @@
 #include "../../include/dsanls.h"
 #include "common.cuh"
 #include "kernels.cuh"
-#include "sparse.cuh"
+#include "mlp.cuh"
 #include "tc_gemm.cuh"
 
 using namespace dsanls;
@@ -76,7 +76,7 @@ struct dsanls_ctx {
     int64_t *rp = nullptr, *trp = nullptr;
     int32_t *ci = nullptr, *tci = nullptr;
     float *cv = nullptr, *tcv = nullptr;
-    std::vector<int64_t> h_rp, h_trp;  // host copies of the row pointers (capacity planning)
+    std::vector<int64_t> h_rp, h_trp;  // host copies of the row pointers (validation)
 
     // factors
     float *U = nullptr, *V = nullptr;
@@ -100,7 +100,10 @@ struct dsanls_ctx {
     int64_t *t_dev = nullptr;
     int *flag = nullptr;
     double *dscal = nullptr;  // [0] ||M||^2, [1] residual^2, [2] cross, [3..] Gram of U, Gram of V
-    SubCsr sub;
+    uint32_t *bits = nullptr;  // membership bitmap of the sampled set (sparse subsampling)
+    dsanls_mlp_ctx *mlp = nullptr;          // learned warm start (borrowed), or none
+    int pg_iters = 0;
+    unsigned long long *kept = nullptr;     // rows whose learned point was kept
     float bound = 0.0f;
 
     cudaGraphExec_t graph = nullptr;
@@ -174,17 +177,6 @@ void invalidate_graph(dsanls_ctx *h) {
 
 int d_v_of(const dsanls_ctx *h) { return h->opt.d_v > 0 ? h->opt.d_v : h->d; }
 
-// Sum of the `take` largest segment lengths of a CSR row pointer.
-int64_t top_lengths(const std::vector<int64_t> &ptr, int64_t take) {
-    std::vector<int64_t> len(ptr.size() - 1);
-    for (size_t i = 0; i + 1 < ptr.size(); ++i) len[i] = ptr[i + 1] - ptr[i];
-    take = std::min<int64_t>(take, (int64_t)len.size());
-    std::nth_element(len.begin(), len.begin() + (take > 0 ? take - 1 : 0), len.end(), std::greater<int64_t>());
-    int64_t s = 0;
-    for (int64_t i = 0; i < take; ++i) s += len[i];
-    return s;
-}
-
 // (Re)allocate the per-configuration workspaces.
 void prepare(dsanls_ctx *h) {
     const int dv = d_v_of(h);
@@ -206,18 +198,7 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->Bpart, (gauss && bf16) ? tc_gemm_part_elems(k, dmax) : 0);
     dalloc(h->R, std::max(m, n) * k);
     dalloc(h->Rpart, (gauss && bf16) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
-    if (h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE) {
-        const int64_t cap = std::max(top_lengths(h->h_trp, h->d), top_lengths(h->h_rp, dv));
-        const int64_t rows = std::max(m, n);
-        dalloc(h->sub.off, dmax + 1);
-        dalloc(h->sub.total, 1);
-        dalloc(h->sub.cnt, rows);
-        dalloc(h->sub.ptr, rows + 1);
-        dalloc(h->sub.bsum, ceil_div(rows, 4096) + 1);
-        dalloc(h->sub.col, std::max<int64_t>(cap, 1));
-        dalloc(h->sub.val, std::max<int64_t>(cap, 1));
-        h->sub.capacity = cap;
-    }
+    dalloc(h->bits, (h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE) ? ceil_div(std::max(m, n), 32) + 1 : 0);
     std::copy(key, key + 6, h->cfg_key);
 }
 
@@ -233,7 +214,7 @@ inline void mark(PhaseEvents *pe, int i, cudaStream_t s) {
     if (pe) DSANLS_CUDA(cudaEventRecord(pe->ev[i], s));
 }
 
-void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullptr) {
+void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullptr, bool update = true) {
     const int64_t rows = side == 0 ? h->m : h->n;
     const int64_t K = side == 0 ? h->n : h->m;
     const int dd = side == 0 ? h->d : d_v_of(h);
@@ -246,9 +227,6 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     const int64_t *xp = side == 0 ? h->rp : h->trp;
     const int32_t *xc = side == 0 ? h->ci : h->tci;
     const float *xv = side == 0 ? h->cv : h->tcv;
-    const int64_t *xtp = side == 0 ? h->trp : h->rp;
-    const int32_t *xtc = side == 0 ? h->tci : h->ci;
-    const float *xtv = side == 0 ? h->tcv : h->cv;
     const bool dense = h->has_dense;
     int64_t gram_d = dd;
 
@@ -321,9 +299,8 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             mark(pe, DSANLS_PHASE_RHS, s);
             launch_sgemm(g, s);
         } else {
-            launch_subcsr(xtp, xtc, xtv, h->J, dd, rows, h->sub, s);
             mark(pe, DSANLS_PHASE_RHS, s);
-            launch_spmm_rows(h->sub.ptr, h->sub.col, h->sub.val, rows, Y, k, k, c2, h->R, k, s);
+            launch_sampled_spmm(xp, xc, xv, rows, h->J, dd, K, h->bits, Y, k, c2, h->R, s);
         }
     } else {  // identity
         mark(pe, DSANLS_PHASE_B, s);
@@ -349,7 +326,12 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     launch_step_size(h->G64[side], k, h->opt.power_iters, h->opt.alpha, h->opt.beta, h->t_dev, h->scal[side], h->Gf,
                      kp, s);
     mark(pe, DSANLS_PHASE_UPDATE, s);
-    launch_update(h->opt.solver, Z, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->flag, s);
+    if (!update) return;
+    if (h->mlp)
+        mlp_learned_update(h->mlp->st, Z, h->R, rows, h->G64[side], h->Gf, kp, h->scal[side], h->pg_iters, h->kept,
+                           h->flag, s);
+    else
+        launch_update(h->opt.solver, Z, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->flag, s);
     mark(pe, DSANLS_NPHASES, s);
 }
 
@@ -801,6 +783,65 @@ int dsanls_profile_half_step(dsanls_t h, int32_t side, int32_t reps, double *ms)
     return rc;
 }
 
+int dsanls_set_mlp(dsanls_t h, dsanls_mlp_t m, int32_t pg_iters) {
+    if (!h) return DSANLS_EINVAL;
+    if (pg_iters < 0 || pg_iters > 1000) return fail(h, DSANLS_EINVAL, "pg_iters must be in [0, 1000]");
+    if (m && (m->st.k != h->k || h->k > 32 || m->st.max_rows < std::max(h->m, h->n)))
+        return fail(h, DSANLS_EINVAL, "the network's k must equal the handle's (<= 32) and max_rows >= max(m, n)");
+    if (m && h->opt.bound_clamp) return fail(h, DSANLS_EINVAL, "the learned form has no bound clamp");
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
+        if (!h->kept) {
+            dalloc(h->kept, 1);
+            DSANLS_CUDA(cudaMemset(h->kept, 0, sizeof(unsigned long long)));
+        }
+        h->mlp = m;
+        h->pg_iters = pg_iters;
+        invalidate_graph(h);
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_mlp_kept(dsanls_t h, int64_t *kept) {
+    if (!h || !kept) return DSANLS_EINVAL;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        unsigned long long v = 0;
+        DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
+        if (h->kept) DSANLS_CUDA(cudaMemcpy(&v, h->kept, sizeof v, cudaMemcpyDeviceToHost));
+        *kept = (int64_t)v;
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_harvest(dsanls_t h, int32_t side, int32_t iters, float *G, float *mu, float *b, float *xstar) {
+    if (!h) return DSANLS_EINVAL;
+    if ((side != 0 && side != 1) || iters < 1 || !G || !mu || !b || !xstar)
+        return fail(h, DSANLS_EINVAL, "bad side, iters or output pointers");
+    if (h->k > 32) return fail(h, DSANLS_EINVAL, "harvesting supports k <= 32");
+    if (int rc = check_ready(h)) return rc;
+    DeviceGuard dg(h->device);
+    return guarded(h, [&]() {
+        cudaStream_t s = h->stream();
+        prepare(h);
+        half_step(h, side, s, nullptr, false);
+        const int64_t rows = side == 0 ? h->m : h->n;
+        const float *Z = side == 0 ? h->U : h->V;
+        mlp_harvest(Z, h->R, h->Gf, kp_bucket(h->k), h->scal[side], rows, h->k, iters, b, xstar, s);
+        std::vector<double> g((size_t)h->k * h->k + 1);
+        DSANLS_CUDA(cudaMemcpyAsync(g.data(), h->G64[side], (size_t)h->k * h->k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DSANLS_CUDA(cudaMemcpyAsync(g.data() + (size_t)h->k * h->k, h->scal[side] + 1, sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        std::vector<float> gf(g.begin(), g.end());
+        DSANLS_CUDA(cudaMemcpyAsync(G, gf.data(), (size_t)h->k * h->k * sizeof(float), cudaMemcpyHostToDevice, s));
+        DSANLS_CUDA(cudaMemcpyAsync(mu, gf.data() + (size_t)h->k * h->k, sizeof(float), cudaMemcpyHostToDevice, s));
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        return DSANLS_OK;
+    });
+}
+
 int dsanls_kernel_launches(uint64_t *out) {
     if (!out) return DSANLS_EINVAL;
     *out = launch_count();
@@ -829,8 +870,7 @@ void dsanls_destroy(dsanls_t h) {
             dfree(h->scal[side]);
         }
         dfree(h->Gf); dfree(h->work); dfree(h->t_dev); dfree(h->flag); dfree(h->dscal);
-        dfree(h->sub.off); dfree(h->sub.total); dfree(h->sub.cnt); dfree(h->sub.ptr); dfree(h->sub.bsum);
-        dfree(h->sub.col); dfree(h->sub.val);
+        dfree(h->bits); dfree(h->kept);
         if (h->own_stream) cudaStreamDestroy(h->own_stream);
     }
     delete h;

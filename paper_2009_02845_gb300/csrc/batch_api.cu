@@ -1,0 +1,503 @@
+// C ABI of the batched form: many independent dense problems, one persistent
+// work-queue launch per phase, one CUDA graph per outer iteration, and an
+// autotuner for the persistent launch geometry.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dsanls.h"
+#include "batch.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace dsanls;
+
+struct dsanls_batch_ctx {
+    int device = 0;
+    std::vector<BatchInst> h;
+    BatchDev g;
+    BatchLaunch cfg;
+    bool tuned = false;
+    dsanls_options opt{};
+    int64_t t_host = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    uint64_t graph_launches = 0;
+    std::vector<char> has_data;
+    std::vector<double> mm;  // ||M_i||^2
+    double *work = nullptr;
+    double *dres = nullptr;  // residual^2 per instance
+    std::string err;
+    cudaStream_t stream() const { return opt.stream ? (cudaStream_t)opt.stream : own_stream; }
+};
+
+namespace {
+
+constexpr int64_t B_WORK = 152 * 8;
+
+template <typename T>
+void balloc(T *&p, int64_t count) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (count <= 0) return;
+    if (cudaMalloc((void **)&p, (size_t)count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        throw std::bad_alloc();
+    }
+}
+
+template <typename T>
+void bfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+template <typename F>
+int bguard(dsanls_batch_ctx *b, F &&body) {
+    try {
+        return body();
+    } catch (const CudaError &e) {
+        b->err = std::string("CUDA error: ") + cudaGetErrorString(e.err) + " (" + e.where + ")";
+        cudaGetLastError();
+        return DSANLS_ECUDA;
+    } catch (const ArgError &e) {
+        b->err = e.what;
+        return DSANLS_EINVAL;
+    } catch (const std::bad_alloc &) {
+        b->err = "out of memory";
+        return DSANLS_ENOMEM;
+    } catch (...) {
+        b->err = "unexpected internal error";
+        return DSANLS_ECUDA;
+    }
+}
+
+void drop_graph(dsanls_batch_ctx *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+void iteration(dsanls_batch_ctx *b, cudaStream_t s) {
+    batch_half_step(b->g, 0, b->cfg, s);
+    batch_half_step(b->g, 1, b->cfg, s);
+    launch_increment_t(b->g.t_dev, 1, s);
+}
+
+// ---- autotuner: persistent CTAs per SM, cached per batch shape and dtype ----
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;
+
+std::string tune_key(const dsanls_batch_ctx *b) {
+    std::vector<std::string> shapes;
+    for (const BatchInst &i : b->h) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "%lld,%lld,%d,%d,%d", (long long)i.m, (long long)i.n, i.k, i.d, i.dv);
+        shapes.push_back(buf);
+    }
+    std::sort(shapes.begin(), shapes.end());
+    std::string key = "f32";
+    for (const std::string &sh : shapes) key += ";" + sh;
+    return std::to_string(std::hash<std::string>()(key)) + "/f32";
+}
+
+std::string cache_path() {
+    const char *p = std::getenv("DSANLS_TUNE_CACHE");
+    return p ? std::string(p) : std::string();
+}
+
+bool cache_lookup(const std::string &key, int &value) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+        value = it->second;
+        return true;
+    }
+    const std::string path = cache_path();
+    if (path.empty()) return false;
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    char k[256];
+    int v;
+    bool found = false;
+    while (std::fscanf(f, "%255s %d", k, &v) == 2) {
+        g_tune_cache[k] = v;
+        if (key == k) {
+            value = v;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, int value) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = value;
+    const std::string path = cache_path();
+    if (path.empty()) return;
+    FILE *f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", key.c_str(), value);
+    std::fclose(f);
+}
+
+// Time one full outer iteration for each candidate (factors restored after
+// each trial) and keep the fastest.
+void autotune(dsanls_batch_ctx *b) {
+    const std::string key = tune_key(b);
+    int per_sm = 0;
+    if (!cache_lookup(key, per_sm)) {
+        cudaStream_t s = b->stream();
+        int64_t fbytes = 0;
+        for (const BatchInst &i : b->h) fbytes = std::max<int64_t>(fbytes, i.offV + i.n * i.k);
+        float *backup = nullptr;
+        balloc(backup, fbytes);
+        int64_t t_backup = 0;
+        DSANLS_CUDA(cudaMemcpyAsync(&t_backup, b->g.t_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        DSANLS_CUDA(cudaMemcpyAsync(backup, b->g.factors, fbytes * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        cudaEvent_t e0, e1;
+        DSANLS_CUDA(cudaEventCreate(&e0));
+        DSANLS_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        const int candidates[4] = {1, 2, 4, 8};
+        try {
+            for (int c : candidates) {
+                b->cfg.persistent_blocks = 152 * c;
+                iteration(b, s);  // warm
+                DSANLS_CUDA(cudaEventRecord(e0, s));
+                iteration(b, s);
+                DSANLS_CUDA(cudaEventRecord(e1, s));
+                DSANLS_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                DSANLS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    per_sm = c;
+                }
+                DSANLS_CUDA(cudaMemcpyAsync(b->g.factors, backup, fbytes * sizeof(float), cudaMemcpyDeviceToDevice, s));
+                DSANLS_CUDA(cudaMemcpyAsync(b->g.t_dev, &t_backup, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+                DSANLS_CUDA(cudaStreamSynchronize(s));
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            bfree(backup);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        bfree(backup);
+        cache_store(key, per_sm);
+    }
+    b->cfg.persistent_blocks = 152 * per_sm;
+    b->tuned = true;
+}
+
+int bfail(dsanls_batch_ctx *b, int code, const char *msg) {
+    b->err = msg;
+    return code;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const int32_t *k, const int32_t *d,
+                        const int32_t *d_v, const uint64_t *seeds, dsanls_batch_t *out) {
+    if (!out) return DSANLS_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !m || !n || !k || !d || !d_v || !seeds) return DSANLS_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (m[i] < 1 || n[i] < 1 || m[i] > (1 << 24) || n[i] > (1 << 24)) return DSANLS_EINVAL;
+        if (k[i] < 1 || k[i] > 32 || d[i] < 1 || d_v[i] < 1 || d[i] > (1 << 20) || d_v[i] > (1 << 20))
+            return DSANLS_EINVAL;
+    }
+    dsanls_batch_ctx *b = nullptr;
+    try {
+        b = new dsanls_batch_ctx();
+    } catch (...) {
+        return DSANLS_ENOMEM;
+    }
+    dsanls_default_options(&b->opt);
+    const int rc = bguard(b, [&]() {
+        DSANLS_CUDA(cudaGetDevice(&b->device));
+        DSANLS_CUDA(cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking));
+        prime_kernel_attributes();
+        b->h.resize(count);
+        int64_t offM = 0, offF = 0, offS = 0, offB = 0, offR = 0, offG = 0;
+        for (int i = 0; i < count; ++i) {
+            BatchInst &x = b->h[i];
+            std::memset(&x, 0, sizeof x);
+            x.m = m[i];
+            x.n = n[i];
+            x.k = k[i];
+            x.d = d[i];
+            x.dv = d_v[i];
+            x.seed = seeds[i];
+            x.scale[0] = (float)(1.0 / std::sqrt((double)d[i]));
+            x.scale[1] = (float)(1.0 / std::sqrt((double)d_v[i]));
+            x.offM = offM;
+            offM += 2 * x.m * x.n;
+            x.offU = offF;
+            offF += x.m * x.k;
+            x.offV = offF;
+            offF += x.n * x.k;
+            x.offS = offS;
+            offS += std::max(x.n * x.d, x.m * x.dv);
+            x.offB = offB;
+            offB += (int64_t)x.k * std::max(x.d, x.dv);
+            x.offR = offR;
+            offR += std::max(x.m, x.n) * x.k;
+            x.offG = offG;
+            offG += (int64_t)x.k * x.k + 4;
+        }
+        cudaStream_t s = b->stream();
+        BatchDev &g = b->g;
+        g.count = count;
+        balloc(g.inst, count);
+        balloc(g.data, offM);
+        balloc(g.factors, offF);
+        balloc(g.S, offS);
+        balloc(g.B, offB);
+        balloc(g.R, offR);
+        balloc(g.G, offG);
+        balloc(g.counters, 8);
+        balloc(g.t_dev, 1);
+        balloc(g.flag, 1);
+        balloc(b->work, B_WORK);
+        balloc(b->dres, count);
+        DSANLS_CUDA(cudaMemcpyAsync(g.inst, b->h.data(), count * sizeof(BatchInst), cudaMemcpyHostToDevice, s));
+        DSANLS_CUDA(cudaMemsetAsync(g.t_dev, 0, sizeof(int64_t), s));
+        DSANLS_CUDA(cudaMemsetAsync(g.flag, 0, sizeof(int), s));
+        for (int side = 0; side < 2; ++side) {
+            std::vector<int2> bi, ai, ui;
+            std::vector<int64_t> pre;
+            batch_build_items(b->h, side, bi, ai, ui, pre);
+            balloc(g.bitems[side], (int64_t)bi.size());
+            balloc(g.aritems[side], (int64_t)ai.size());
+            balloc(g.uitems[side], (int64_t)ui.size());
+            balloc(g.sketch_prefix[side], (int64_t)pre.size());
+            g.nb[side] = (int)bi.size();
+            g.nar[side] = (int)ai.size();
+            g.nu[side] = (int)ui.size();
+            DSANLS_CUDA(cudaMemcpyAsync(g.bitems[side], bi.data(), bi.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaMemcpyAsync(g.aritems[side], ai.data(), ai.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaMemcpyAsync(g.uitems[side], ui.data(), ui.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaMemcpyAsync(g.sketch_prefix[side], pre.data(), pre.size() * sizeof(int64_t),
+                                        cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+        }
+        batch_init_factors(g.inst, count, g.factors, s);
+        b->has_data.assign(count, 0);
+        b->mm.assign(count, 0.0);
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        return DSANLS_OK;
+    });
+    if (rc != DSANLS_OK) {
+        record_handleless_error(b->err);
+        dsanls_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return DSANLS_OK;
+}
+
+int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
+    if (!b) return DSANLS_EINVAL;
+    if (!opt) return bfail(b, DSANLS_EINVAL, "options pointer is NULL");
+    if (opt->solver != DSANLS_SOLVER_PGD && opt->solver != DSANLS_SOLVER_RCD) return bfail(b, DSANLS_EINVAL, "unknown solver");
+    if (opt->precision != DSANLS_PREC_FP32) return bfail(b, DSANLS_EINVAL, "the batched form computes in binary32");
+    if (opt->power_iters < 0 || opt->power_iters > 10000 || !(opt->alpha >= 0.0) || !(opt->beta >= 0.0) ||
+        !std::isfinite(opt->alpha) || !std::isfinite(opt->beta) || opt->t < 0)
+        return bfail(b, DSANLS_EINVAL, "bad power_iters, alpha, beta or t");
+    if (opt->bound_clamp) return bfail(b, DSANLS_EINVAL, "the batched form has no bound clamp");
+    return bguard(b, [&]() {
+        DSANLS_CUDA(cudaStreamSynchronize(b->stream()));
+        b->opt = *opt;
+        b->g.solver = opt->solver;
+        b->g.alpha = opt->alpha;
+        b->g.beta = opt->beta;
+        b->g.power_iters = opt->power_iters;
+        drop_graph(b);
+        if (opt->t != b->t_host) {
+            b->t_host = opt->t;
+            DSANLS_CUDA(cudaMemcpyAsync(b->g.t_dev, &b->t_host, sizeof(int64_t), cudaMemcpyHostToDevice, b->stream()));
+        }
+        DSANLS_CUDA(cudaStreamSynchronize(b->stream()));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_batch_set_dense(dsanls_batch_t b, int32_t i, const float *M, int64_t ld, int32_t on_device) {
+    if (!b) return DSANLS_EINVAL;
+    if (i < 0 || i >= (int)b->h.size()) return bfail(b, DSANLS_EINVAL, "instance index out of range");
+    const BatchInst &x = b->h[i];
+    if (!M || ld < x.n) return bfail(b, DSANLS_EINVAL, "M is NULL or ld < n");
+    return bguard(b, [&]() {
+        cudaStream_t s = b->stream();
+        float *dst = b->g.data + x.offM;
+        DSANLS_CUDA(cudaMemcpy2DAsync(dst, x.n * sizeof(float), M, ld * sizeof(float), x.n * sizeof(float), x.m,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        launch_transpose(dst, x.n, x.m, x.n, dst + x.m * x.n, x.m, s);
+        launch_sumsq(dst, x.m * x.n, b->work, B_WORK, b->dres + i, s);
+        double v = 0.0;
+        DSANLS_CUDA(cudaMemcpyAsync(&v, b->dres + i, sizeof(double), cudaMemcpyDeviceToHost, s));
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        b->mm[i] = v;
+        b->has_data[i] = 1;
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_batch_set_factors(dsanls_batch_t b, int32_t i, const float *U, const float *V, int32_t on_device) {
+    if (!b) return DSANLS_EINVAL;
+    if (i < 0 || i >= (int)b->h.size()) return bfail(b, DSANLS_EINVAL, "instance index out of range");
+    const BatchInst &x = b->h[i];
+    return bguard(b, [&]() {
+        cudaStream_t s = b->stream();
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (U) DSANLS_CUDA(cudaMemcpyAsync(b->g.factors + x.offU, U, x.m * x.k * sizeof(float), kind, s));
+        if (V) DSANLS_CUDA(cudaMemcpyAsync(b->g.factors + x.offV, V, x.n * x.k * sizeof(float), kind, s));
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_batch_step(dsanls_batch_t b, int32_t outer_iters) {
+    if (!b) return DSANLS_EINVAL;
+    if (outer_iters < 0) return bfail(b, DSANLS_EINVAL, "outer_iters < 0");
+    for (char c : b->has_data)
+        if (!c) return bfail(b, DSANLS_ESTATE, "every instance needs dsanls_batch_set_dense first");
+    return bguard(b, [&]() {
+        cudaStream_t s = b->stream();
+        if (!b->tuned) autotune(b);
+        if (b->opt.use_graph) {
+            if (!b->graph) {
+                cudaGraph_t gr = nullptr;
+                const uint64_t before = launch_count();
+                DSANLS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                try {
+                    iteration(b, s);
+                } catch (...) {
+                    cudaGraph_t dummy = nullptr;
+                    cudaStreamEndCapture(s, &dummy);
+                    if (dummy) cudaGraphDestroy(dummy);
+                    throw;
+                }
+                DSANLS_CUDA(cudaStreamEndCapture(s, &gr));
+                b->graph_launches = launch_count() - before;
+                add_launches(0 - b->graph_launches);
+                const cudaError_t e = cudaGraphInstantiate(&b->graph, gr, 0);
+                cudaGraphDestroy(gr);
+                DSANLS_CUDA(e);
+            }
+            for (int it = 0; it < outer_iters; ++it) DSANLS_CUDA(cudaGraphLaunch(b->graph, s));
+            add_launches(b->graph_launches * (uint64_t)outer_iters);
+        } else {
+            for (int it = 0; it < outer_iters; ++it) iteration(b, s);
+        }
+        b->t_host += outer_iters;
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_batch_get_factors(dsanls_batch_t b, int32_t i, float *U, float *V, int32_t on_device) {
+    if (!b) return DSANLS_EINVAL;
+    if (i < 0 || i >= (int)b->h.size()) return bfail(b, DSANLS_EINVAL, "instance index out of range");
+    const BatchInst &x = b->h[i];
+    return bguard(b, [&]() {
+        cudaStream_t s = b->stream();
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        int flag = 0;
+        DSANLS_CUDA(cudaMemcpy(&flag, b->g.flag, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            DSANLS_CUDA(cudaMemset(b->g.flag, 0, sizeof(int)));
+            return bfail(b, DSANLS_ENUMERIC, "an update produced NaN or Inf");
+        }
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (U) DSANLS_CUDA(cudaMemcpyAsync(U, b->g.factors + x.offU, x.m * x.k * sizeof(float), kind, s));
+        if (V) DSANLS_CUDA(cudaMemcpyAsync(V, b->g.factors + x.offV, x.n * x.k * sizeof(float), kind, s));
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_batch_rel_error(dsanls_batch_t b, double *out) {
+    if (!b) return DSANLS_EINVAL;
+    if (!out) return bfail(b, DSANLS_EINVAL, "out is NULL");
+    return bguard(b, [&]() {
+        cudaStream_t s = b->stream();
+        const int count = (int)b->h.size();
+        for (int i = 0; i < count; ++i) {
+            const BatchInst &x = b->h[i];
+            launch_dense_residual(b->g.data + x.offM, x.n, b->g.factors + x.offU, b->g.factors + x.offV, x.m, x.n,
+                                  x.k, b->work, B_WORK, b->dres + i, s);
+        }
+        std::vector<double> r(count);
+        DSANLS_CUDA(cudaMemcpyAsync(r.data(), b->dres, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DSANLS_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < count; ++i) out[i] = b->mm[i] > 0.0 ? std::sqrt(std::max(r[i], 0.0) / b->mm[i]) : 0.0;
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_batch_profile(dsanls_batch_t b, double *ms) {
+    if (!b || !ms) return DSANLS_EINVAL;
+    for (char c : b->has_data)
+        if (!c) return bfail(b, DSANLS_ESTATE, "every instance needs dsanls_batch_set_dense first");
+    cudaEvent_t ev[6] = {};
+    int created = 0;
+    const int rc = bguard(b, [&]() {
+        if (!b->tuned) autotune(b);
+        for (; created < 6; ++created) DSANLS_CUDA(cudaEventCreate(&ev[created]));
+        cudaStream_t s = b->stream();
+        for (int side = 0; side < 2; ++side) {
+            batch_half_step(b->g, side, b->cfg, s, ev);
+            DSANLS_CUDA(cudaEventSynchronize(ev[5]));
+            for (int p = 0; p < 5; ++p) {
+                float t = 0.0f;
+                DSANLS_CUDA(cudaEventElapsedTime(&t, ev[p], ev[p + 1]));
+                ms[side * 5 + p] = t;
+            }
+        }
+        return DSANLS_OK;
+    });
+    for (int i = 0; i < created; ++i) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas) {
+    if (!b || !persistent_ctas) return DSANLS_EINVAL;
+    *persistent_ctas = b->tuned ? b->cfg.persistent_blocks : 0;
+    return DSANLS_OK;
+}
+
+const char *dsanls_batch_last_error(dsanls_batch_t b) { return b ? b->err.c_str() : "invalid handle"; }
+
+void dsanls_batch_destroy(dsanls_batch_t b) {
+    if (!b) return;
+    if (b->own_stream) cudaStreamSynchronize(b->own_stream);
+    if (b->opt.stream) cudaStreamSynchronize((cudaStream_t)b->opt.stream);
+    drop_graph(b);
+    BatchDev &g = b->g;
+    bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.G);
+    for (int side = 0; side < 2; ++side) {
+        bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]);
+    }
+    bfree(g.counters); bfree(g.t_dev); bfree(g.flag); bfree(b->work); bfree(b->dres);
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -117,5 +117,10 @@ void launch_copy_cast_bf16(const float *in, int64_t n, __nv_bfloat16 *out, cudaS
 // out[i][0..w) = alpha * sum_{e in row i} val_e * D[col_e*ldd + 0..w)
 void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
                       const float *D, int64_t ldd, int w, float alpha, float *out, int64_t ldo, cudaStream_t s);
+// out[i][0..k) = alpha * sum over entries e of row i with col_e in J of val_e * Y[col_e][0..k)
+// (CSR order); bits is scratch of ceil(K/32) words, K = number of columns; k <= 128.
+void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows, const int32_t *J,
+                         int d, int64_t K, uint32_t *bits, const float *Y, int k, float alpha, float *out,
+                         cudaStream_t s);
 
 }  // namespace dsanls

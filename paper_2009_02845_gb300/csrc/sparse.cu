@@ -4,15 +4,14 @@
 //  * warp-per-row SpMM  out[i][:] = alpha * sum_{e in row i} val_e D[col_e][:]
 //    (lanes across the output columns, 16-byte loads when aligned; one FMA
 //    chain per output in CSR order, deterministic).
-//  * sub-CSR of the sampled columns: for a subsampling sketch the U-half
-//    needs, per row i of M, only the entries whose column is in J.  They are
-//    read from the transposed CSR (rows J of M^T), counted per row of M,
-//    placed by an exclusive scan, filled, and each row sorted by column so
-//    the layout (and every later sum) is independent of thread timing.
-//    The V-half does the same with the roles of the two CSRs swapped.
+//  * subsampled product: for a subsampling sketch the U-half needs, per row
+//    i of M, only the entries whose column is in J (R_i = (n/d) sum over
+//    those entries of M_ij V_j).  A bitmap of J marks the sampled columns; a
+//    warp streams row i of the CSR, keeps the marked entries and accumulates
+//    them in CSR order.  The V-half does the same on the transposed CSR with
+//    a bitmap of the sampled rows J'.
 #include "common.cuh"
 #include "kernels.cuh"
-#include "sparse.cuh"
 
 namespace dsanls {
 
@@ -71,184 +70,69 @@ void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *va
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan of int32 counts into int64 offsets (n + 1 entries)
+// subsampled product of a CSR matrix: membership bitmap of the sampled set
 // ---------------------------------------------------------------------------
-constexpr int SCAN_T = 1024;
-constexpr int SCAN_PER = 4;
-constexpr int SCAN_CHUNK = SCAN_T * SCAN_PER;
-
-DSANLS_DEV int64_t block_exclusive_scan(int64_t v, int64_t *tmp, int64_t &total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) tmp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int64_t t = (lane < (int)(blockDim.x >> 5)) ? tmp[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        tmp[lane] = t;  // inclusive warp totals
-    }
-    __syncthreads();
-    const int64_t warp_off = (w > 0) ? tmp[w - 1] : 0;
-    total = tmp[(blockDim.x >> 5) - 1];
-    __syncthreads();
-    return warp_off + x - v;
+__global__ void k_bitmap_set(const int32_t *__restrict__ J, int d, uint32_t *__restrict__ bits) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < d) atomicOr(&bits[J[p] >> 5], 1u << (J[p] & 31));
 }
 
-__global__ void k_scan_local(const int32_t *__restrict__ cnt, int64_t n, int64_t *__restrict__ out,
-                             int64_t *__restrict__ bsum) {
-    __shared__ int64_t tmp[32];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER;
-    int64_t v[SCAN_PER];
-    int64_t s = 0;
+// One warp per row: lanes read 32 entries at a time, keep those whose column
+// is in the sampled set (bitmap test), and the whole warp accumulates
+// val * Y[col][:] for each kept entry in CSR order (lanes across the k output
+// columns).  Deterministic: one FMA chain per output in CSR order.
+__global__ void __launch_bounds__(256)
+    k_sampled_spmm(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, const float *__restrict__ val,
+                   int64_t rows, const uint32_t *__restrict__ bits, const float *__restrict__ Y, int k, float alpha,
+                   float *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < rows; i += nwarps) {
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
+        for (int64_t base = e0; base < e1; base += 32) {
+            const int64_t e = base + lane;
+            int32_t c = 0;
+            float v = 0.0f;
+            bool hit = false;
+            if (e < e1) {
+                c = col[e];
+                hit = (__ldg(&bits[c >> 5]) >> (c & 31)) & 1u;
+                if (hit) v = val[e];
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, hit);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int32_t cj = __shfl_sync(0xffffffffu, c, src);
+                const float vj = __shfl_sync(0xffffffffu, v, src);
+                const float *y = Y + (int64_t)cj * k;
 #pragma unroll
-    for (int q = 0; q < SCAN_PER; ++q) {
-        v[q] = (base + q < n) ? cnt[base + q] : 0;
-        s += v[q];
-    }
-    int64_t total;
-    int64_t off = block_exclusive_scan(s, tmp, total);
+                for (int q = 0; q < 4; ++q) {
+                    const int cc = lane + 32 * q;
+                    if (cc < k) acc[q] = __fmaf_rn(vj, y[cc], acc[q]);
+                }
+            }
+        }
 #pragma unroll
-    for (int q = 0; q < SCAN_PER; ++q) {
-        if (base + q < n) out[base + q] = off;
-        off += v[q];
-    }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
-}
-
-__global__ void k_scan_bsum(int64_t *__restrict__ bsum, int64_t nb) {
-    __shared__ int64_t tmp[32];
-    int64_t carry = 0;
-    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_T) {
-        const int64_t b = b0 + threadIdx.x;
-        const int64_t v = (b < nb) ? bsum[b] : 0;
-        int64_t total;
-        const int64_t ex = block_exclusive_scan(v, tmp, total);
-        if (b < nb) bsum[b] = carry + ex;
-        carry += total;
-    }
-    if (threadIdx.x == 0) bsum[nb] = carry;
-}
-
-__global__ void k_scan_apply(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ bsum, int64_t nb) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] += bsum[i / SCAN_CHUNK];
-    if (i == 0) out[n] = bsum[nb];
-}
-
-// bsum needs ceil(n / 4096) + 1 entries
-void launch_exclusive_scan(const int32_t *cnt, int64_t n, int64_t *out, int64_t *bsum, cudaStream_t s) {
-    const int64_t nb = ceil_div(n, SCAN_CHUNK);
-    if (nb > 0) {
-        k_scan_local<<<(unsigned)nb, SCAN_T, 0, s>>>(cnt, n, out, bsum);
-        DSANLS_LAUNCH_CHECK();
-    }
-    k_scan_bsum<<<1, SCAN_T, 0, s>>>(bsum, nb);
-    DSANLS_LAUNCH_CHECK();
-    k_scan_apply<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(out, n, bsum, nb);
-    DSANLS_LAUNCH_CHECK();
-}
-
-// ---------------------------------------------------------------------------
-// sub-CSR of sampled source rows
-// ---------------------------------------------------------------------------
-// off[p] = sum_{q<p} len(J_q) for p <= d; *total = off[d].  One CTA.
-__global__ void k_sub_offsets(const int64_t *__restrict__ sptr, const int32_t *__restrict__ J, int d,
-                              int64_t *__restrict__ off, int64_t *__restrict__ total) {
-    __shared__ int64_t tmp[32];
-    const int per = (d + SCAN_T - 1) / SCAN_T;
-    const int p0 = threadIdx.x * per;
-    int64_t s = 0;
-    for (int q = 0; q < per; ++q) {
-        const int p = p0 + q;
-        if (p < d) s += sptr[J[p] + 1] - sptr[J[p]];
-    }
-    int64_t tot;
-    int64_t o = block_exclusive_scan(s, tmp, tot);
-    for (int q = 0; q < per; ++q) {
-        const int p = p0 + q;
-        if (p < d) {
-            off[p] = o;
-            o += sptr[J[p] + 1] - sptr[J[p]];
-        }
-    }
-    if (threadIdx.x == 0) {
-        off[d] = tot;
-        *total = tot;
-    }
-}
-
-DSANLS_DEV int find_segment(const int64_t *off, int d, int64_t e) {
-    int lo = 0, hi = d;  // off[lo] <= e < off[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (off[mid] <= e)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
-template <bool FILL>
-__global__ void k_sub_scatter(const int64_t *__restrict__ sptr, const int32_t *__restrict__ sidx,
-                              const float *__restrict__ sval, const int32_t *__restrict__ J, int d,
-                              const int64_t *__restrict__ off, const int64_t *__restrict__ total_dev,
-                              int32_t *__restrict__ cnt, const int64_t *__restrict__ ptr, int32_t *__restrict__ ocol,
-                              float *__restrict__ oval) {
-    const int64_t total = *total_dev;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int p = find_segment(off, d, e);
-        const int64_t q = sptr[J[p]] + (e - off[p]);
-        const int32_t i = sidx[q];
-        const int32_t pos = atomicAdd(&cnt[i], 1);
-        if (FILL) {
-            ocol[ptr[i] + pos] = J[p];
-            oval[ptr[i] + pos] = sval[q];
+        for (int q = 0; q < 4; ++q) {
+            const int cc = lane + 32 * q;
+            if (cc < k) out[i * k + cc] = __fmul_rn(alpha, acc[q]);
         }
     }
 }
 
-__global__ void k_sub_sort(const int64_t *__restrict__ ptr, int64_t rows, int32_t *__restrict__ col,
-                           float *__restrict__ val) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    const int64_t b = ptr[i], e = ptr[i + 1];
-    for (int64_t x = b + 1; x < e; ++x) {
-        const int32_t c = col[x];
-        const float v = val[x];
-        int64_t y = x - 1;
-        while (y >= b && col[y] > c) {
-            col[y + 1] = col[y];
-            val[y + 1] = val[y];
-            --y;
-        }
-        col[y + 1] = c;
-        val[y + 1] = v;
-    }
-}
-
-void launch_subcsr(const int64_t *sptr, const int32_t *sidx, const float *sval, const int32_t *J, int d,
-                   int64_t out_rows, SubCsr &sub, cudaStream_t s) {
-    k_sub_offsets<<<1, SCAN_T, 0, s>>>(sptr, J, d, sub.off, sub.total);
+void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows, const int32_t *J,
+                         int d, int64_t K, uint32_t *bits, const float *Y, int k, float alpha, float *out,
+                         cudaStream_t s) {
+    DSANLS_CUDA(cudaMemsetAsync(bits, 0, (size_t)ceil_div(K, 32) * sizeof(uint32_t), s));
+    k_bitmap_set<<<(unsigned)ceil_div(d, 256), 256, 0, s>>>(J, d, bits);
     DSANLS_LAUNCH_CHECK();
-    DSANLS_CUDA(cudaMemsetAsync(sub.cnt, 0, (size_t)out_rows * sizeof(int32_t), s));
-    const unsigned grid = 152 * 8;
-    k_sub_scatter<false><<<grid, 256, 0, s>>>(sptr, sidx, sval, J, d, sub.off, sub.total, sub.cnt, nullptr, nullptr,
-                                              nullptr);
-    DSANLS_LAUNCH_CHECK();
-    launch_exclusive_scan(sub.cnt, out_rows, sub.ptr, sub.bsum, s);
-    DSANLS_CUDA(cudaMemsetAsync(sub.cnt, 0, (size_t)out_rows * sizeof(int32_t), s));
-    k_sub_scatter<true><<<grid, 256, 0, s>>>(sptr, sidx, sval, J, d, sub.off, sub.total, sub.cnt, sub.ptr, sub.col,
-                                             sub.val);
-    DSANLS_LAUNCH_CHECK();
-    k_sub_sort<<<(unsigned)ceil_div(out_rows, 256), 256, 0, s>>>(sub.ptr, out_rows, sub.col, sub.val);
+    if (rows <= 0) return;
+    int64_t blocks = ceil_div(rows, 8);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_sampled_spmm<<<(unsigned)blocks, 256, 0, s>>>(rowptr, col, val, rows, bits, Y, k, alpha, out);
     DSANLS_LAUNCH_CHECK();
 }
 

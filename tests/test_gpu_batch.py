@@ -1,0 +1,121 @@
+"""Parity of the batched form with the FP64 oracle, instance by instance.
+
+Each instance of a batch follows the single-problem method (Alg. 1 with the
+sketched subproblems, Gaussian sketch, its own seed, d and d').  After one
+outer iteration from the default factors: U within 1e-5 and V within 2e-5
+(norm-wise relative; V inherits U's rounding through the V-half).  After 20
+iterations the relative errors agree to 1e-4.
+"""
+import numpy as np
+import pytest
+
+from oracle import method
+from synthdata import batch_specs, planted_dense
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [
+    dict(m=130, n=70, k=8, d=32, d_v=32, seed=0),
+    dict(m=1000, n=333, k=16, d=64, d_v=125, seed=1),
+    dict(m=257, n=1024, k=32, d=128, d_v=128, seed=2),
+    dict(m=64, n=64, k=32, d=128, d_v=128, seed=3),
+    dict(m=4096, n=512, k=8, d=64, d_v=512, seed=4),
+    dict(m=700, n=2048, k=16, d=256, d_v=87, seed=5),
+]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2009_02845_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _inputs(shapes):
+    return [planted_dense(s["m"], s["n"], s["k"], 100 + i)[0] for i, s in enumerate(shapes)]
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_one_iteration(pkg, solver, use_graph):
+    Ms = _inputs(SHAPES)
+    b = pkg.Batch(SHAPES, solver=solver, use_graph=use_graph)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(1)
+    assert b.tuned_blocks() > 0
+    for i, (s, M) in enumerate(zip(SHAPES, Ms)):
+        U, V = b.factors(i)
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        opt = method.Options(sketch=method.GAUSSIAN, d=s["d"], d_v=s["d_v"], solver=solver)
+        Uo, Vo, _ = method.run(M, U0, V0, s["seed"], 1, opt, log_error=False)
+        assert _rel(U, Uo) <= 1e-5, (i, _rel(U, Uo))
+        assert _rel(V, Vo) <= 2e-5, (i, _rel(V, Vo))
+        assert U.min() >= 0 and V.min() >= 0
+    b.close()
+
+
+def test_batch_run_errors(pkg):
+    Ms = _inputs(SHAPES)
+    b = pkg.Batch(SHAPES, use_graph=1)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(20)
+    errs = b.rel_errors()
+    b.close()
+    for i, (s, M) in enumerate(zip(SHAPES, Ms)):
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        opt = method.Options(sketch=method.GAUSSIAN, d=s["d"], d_v=s["d_v"])
+        _, _, eo = method.run(M, U0, V0, s["seed"], 20, opt)
+        assert abs(errs[i] - eo[-1]) <= 1e-4, (i, errs[i], eo[-1])
+
+
+def test_batch_matches_single_problem_handle(pkg):
+    """The batched kernels and the single-problem kernels agree (same method)."""
+    s = SHAPES[1]
+    M = _inputs([s])[0]
+    b = pkg.Batch([s], use_graph=1)
+    b.set_dense(0, M)
+    b.step(3)
+    Ub, Vb = b.factors(0)
+    b.close()
+    h = pkg.DSANLS(s["m"], s["n"], s["k"], s["d"], pkg.GAUSSIAN, seed=s["seed"], d_v=s["d_v"])
+    h.set_dense(M)
+    h.step(3)
+    Uh, Vh = h.factors()
+    h.close()
+    assert _rel(Ub, Uh.astype(np.float64)) <= 1e-4 and _rel(Vb, Vh.astype(np.float64)) <= 1e-4
+
+
+def test_batch_uneven_specs_sampled(pkg):
+    """64 instances from the uneven recipe (m in [128, 4096], n in [64, 2048],
+    k in {8, 16, 32}); every 8th instance checked after one iteration."""
+    specs = batch_specs(64, 0)
+    Ms = [planted_dense(s["m"], s["n"], s["k"], s["seed"])[0] for s in specs]
+    b = pkg.Batch(specs, use_graph=1)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(1)
+    for i in range(0, 64, 8):
+        s = specs[i]
+        U, V = b.factors(i)
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        opt = method.Options(sketch=method.GAUSSIAN, d=s["d"], d_v=s["d_v"])
+        Uo, Vo, _ = method.run(Ms[i], U0, V0, s["seed"], 1, opt, log_error=False)
+        assert _rel(U, Uo) <= 1e-5 and _rel(V, Vo) <= 2e-5, i
+    b.close()
+
+
+def test_batch_rejects_bad_arguments(pkg):
+    with pytest.raises(pkg.DSANLSError):
+        pkg.Batch([dict(m=10, n=10, k=33, d=4, d_v=4, seed=0)])
+    b = pkg.Batch([dict(m=10, n=12, k=4, d=4, d_v=4, seed=0)])
+    with pytest.raises(pkg.DSANLSError) as e:
+        b.step(1)
+    assert e.value.code == -4
+    with pytest.raises(pkg.DSANLSError):
+        b.set_options(precision=pkg.BF16)
+    b.close()
