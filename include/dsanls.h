@@ -62,6 +62,9 @@ extern "C" {
 /* ---- arithmetic of the sketched products A = M S and R = A B^T -------- */
 #define DSANLS_PREC_FP32 0    /* binary32 operands and accumulation (CUDA cores)  */
 #define DSANLS_PREC_BF16 1    /* bf16 operands, fp32 accumulation (tcgen05)       */
+#define DSANLS_PREC_FP8 2     /* fp8 E4M3 M (one scale per 128-row block) and S
+                                 (entries N(0,1), 1/sqrt(d) applied to the fp32
+                                 accumulator); B = Y^T S and R = A B^T in bf16   */
 
 /* ---- Philox field streams (counter word 3, low byte) ------------------ */
 #define DSANLS_STREAM_SKETCH_U 0
@@ -98,7 +101,8 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
 
 int dsanls_get_options(dsanls_t h, dsanls_options *opt);
 /* Validates and applies options; d_v follows the same rules as d for the
- * V-half (against m).  Changing precision to BF16 requires dense data. */
+ * V-half (against m).  BF16 and FP8 need dense data and a Gaussian sketch;
+ * BF16 needs m, n, d, d_v multiples of 8, FP8 m and n multiples of 16. */
 int dsanls_set_options(dsanls_t h, const dsanls_options *opt);
 
 /* Dense M: m rows of n binary32 values, row stride ld >= n (elements).  The

@@ -140,6 +140,47 @@ def sketched_terms_bf16(X, Y, S):
     return A, B, G, R
 
 
+def round_e4m3(x):
+    """Round binary32 values to the nearest fp8 E4M3 value (ties to even,
+    saturating at +-448; 3 fraction bits, exponent bias 7, subnormal quantum
+    2^-9), returned as FP64."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(np.where(a > 0, a, 1.0))
+    e = np.maximum(ex - 1, -6)                     # binade exponent, subnormals share 2^-6
+    q = np.ldexp(1.0, e - 3)                       # spacing of E4M3 values in that binade
+    r = np.rint(a / q) * q
+    r = np.minimum(r, 448.0)
+    return np.copysign(r, x)
+
+
+def quantise_rowblocks_e4m3(X):
+    """Per 128-row block: scale = max|x| / 448 (binary32, 1 if zero) and
+    Xq = e4m3(x / scale) (binary32 division); returns the dequantised FP64 X."""
+    X32 = np.asarray(X, dtype=np.float32)
+    out = np.empty(X32.shape, dtype=np.float64)
+    for r0 in range(0, X32.shape[0], 128):
+        blk = X32[r0:r0 + 128]
+        mx = np.float32(np.max(np.abs(blk))) if blk.size else np.float32(0.0)
+        sc = np.float32(mx / np.float32(448.0)) if mx > 0 else np.float32(1.0)
+        out[r0:r0 + 128] = round_e4m3(blk / sc) * np.float64(sc)
+    return out
+
+
+def sketched_terms_fp8(X, Y, S, seed, t, side):
+    """The sketched terms of the fp8 form: X quantised per 128-row block to
+    E4M3, the unit-variance draws z of S to E4M3, A = (Xq zq) / sqrt(d)
+    rounded to bf16 where it enters R; B = Y^T S from bf16 operands as in the
+    bf16 form."""
+    z = rng.gaussian_field(seed, side, t, S.n, S.d, np.float32(1.0))
+    A = round_bf16((quantise_rowblocks_e4m3(X) @ round_e4m3(z)) * np.float64(S.scale))
+    Sb = round_bf16(S.dense32)
+    B = round_bf16(Y).T @ Sb
+    G = B @ B.T
+    R = A @ round_bf16(B).T
+    return A, B, G, R
+
+
 def sketched_terms(X, Y, S):
     """A = X S, B = Y^T S, G = B B^T, R = A B^T  (eq. def_A_B; gradient terms of
     eq. gradient_descent).  X: rows x n data (M or M^T), Y: n x k fixed factor."""
@@ -178,7 +219,7 @@ def rcd_update(Z, G, R, mu, bound=None):
     return Znew
 
 
-def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf16=False):
+def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf16=False, fp8=None):
     """Update of the factor Z (rows x k) against data X (rows x n) with the
     other factor Y (n x k) fixed and sketch S (n x d): one solver step on the
     sketched subproblem (eq. sketched_sub).  ``rows`` restricts the result to a
@@ -186,7 +227,12 @@ def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf1
     if rows is not None:
         X = X[rows]
         Z = Z[rows]
-    A, B, G, R = sketched_terms_bf16(X, Y, S) if bf16 else sketched_terms(X, Y, S)
+    if fp8 is not None:  # fp8 = (seed, t, side) of the sketch, to redraw its unit-variance values
+        A, B, G, R = sketched_terms_fp8(X, Y, S, *fp8)
+    elif bf16:
+        A, B, G, R = sketched_terms_bf16(X, Y, S)
+    else:
+        A, B, G, R = sketched_terms(X, Y, S)
     if solver == PGD:
         eta = 1.0 / (lambda_max(G, power_iters) + mu)
         return pgd_update(Z, G, R, eta, bound)

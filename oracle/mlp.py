@@ -126,8 +126,9 @@ def prox_exact(G, mu, b):
     return np.stack([_nnls.active_set(Gm, bi) for bi in b])
 
 
-def learned_update(P, G, mu, R, Z, eta, pg_iters):
-    """The learned form of one half-step for rows R (N x k), current rows Z."""
+def learned_candidates(P, G, mu, R, Z, eta, pg_iters):
+    """Both candidates of the learned form and their proximal objectives:
+    (x_mlp, x_pgd, f_mlp, f_pgd)."""
     b = R + mu * Z
     Gn, bn, s, beta = normalise(G, mu, b)
     y0, _ = forward(P, Gn, bn)
@@ -136,7 +137,11 @@ def learned_update(P, G, mu, R, Z, eta, pg_iters):
     for _ in range(pg_iters):
         x = np.where(x - eta * (x @ Gm - b) > 0.0, x - eta * (x @ Gm - b), 0.0)
     x_pgd = np.where(Z - eta * (Z @ G - R) > 0.0, Z - eta * (Z @ G - R), 0.0)
-    f_mlp = prox_objective(G, mu, b, x)
-    f_pgd = prox_objective(G, mu, b, x_pgd)
+    return x, x_pgd, prox_objective(G, mu, b, x), prox_objective(G, mu, b, x_pgd)
+
+
+def learned_update(P, G, mu, R, Z, eta, pg_iters):
+    """The learned form of one half-step for rows R (N x k), current rows Z."""
+    x, x_pgd, f_mlp, f_pgd = learned_candidates(P, G, mu, R, Z, eta, pg_iters)
     keep = f_mlp <= f_pgd
     return np.where(keep[:, None], x, x_pgd), keep

@@ -10,7 +10,7 @@ lib_path = os.path.join(_PKG, "libdsanls.so")
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENUMERIC, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 GAUSSIAN, SUBSAMPLE, IDENTITY = 0, 1, 2
 PGD, RCD = 0, 1
-FP32, BF16 = 0, 1
+FP32, BF16, FP8 = 0, 1, 2
 STREAM_SKETCH_U, STREAM_SKETCH_V, STREAM_INIT_U, STREAM_INIT_V = 0, 1, 2, 3
 
 _NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE",

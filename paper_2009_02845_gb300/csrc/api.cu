@@ -92,6 +92,8 @@ struct dsanls_ctx {
     float *R = nullptr;
     float *Rpart = nullptr;
     __nv_bfloat16 *Ytb = nullptr;  // bf16 Y^T (k x K) for the tensor-core B = Y^T S
+    uint8_t *Mq = nullptr, *MTq = nullptr, *Sq = nullptr;  // fp8 E4M3 forms (FP8 precision)
+    float *qscale[2] = {nullptr, nullptr};                  // per 128-row block scales of M, M^T
     float *Bpart = nullptr;        // split-K slices of that product
     double *G64[2] = {nullptr, nullptr};
     double *scal[2] = {nullptr, nullptr};
@@ -101,6 +103,7 @@ struct dsanls_ctx {
     int *flag = nullptr;
     double *dscal = nullptr;  // [0] ||M||^2, [1] residual^2, [2] cross, [3..] Gram of U, Gram of V
     uint32_t *bits = nullptr;  // membership bitmap of the sampled set (sparse subsampling)
+    LongRows lr[2];            // chunked long rows of the CSR of M (0) and of M^T (1)
     dsanls_mlp_ctx *mlp = nullptr;          // learned warm start (borrowed), or none
     int pg_iters = 0;
     unsigned long long *kept = nullptr;     // rows whose learned point was kept
@@ -187,7 +190,8 @@ void prepare(dsanls_ctx *h) {
     const int64_t dmax = std::max<int64_t>(h->d, dv);
     const bool gauss = h->sketch == DSANLS_SKETCH_GAUSSIAN;
     const bool ident = h->sketch == DSANLS_SKETCH_IDENTITY;
-    const bool bf16 = h->opt.precision == DSANLS_PREC_BF16;
+    const bool fp8 = h->opt.precision == DSANLS_PREC_FP8;
+    const bool bf16 = h->opt.precision == DSANLS_PREC_BF16 || fp8;  // fp8 keeps bf16 S^T for B = Y^T S
     dalloc(h->S, (gauss && !bf16) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->Sb, (gauss && bf16) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->J, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? dmax : 0);
@@ -198,6 +202,7 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->Bpart, (gauss && bf16) ? tc_gemm_part_elems(k, dmax) : 0);
     dalloc(h->R, std::max(m, n) * k);
     dalloc(h->Rpart, (gauss && bf16) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
+    dalloc(h->Sq, (gauss && fp8) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->bits, (h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE) ? ceil_div(std::max(m, n), 32) + 1 : 0);
     std::copy(key, key + 6, h->cfg_key);
 }
@@ -233,10 +238,14 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     mark(pe, DSANLS_PHASE_SKETCH, s);
     if (h->sketch == DSANLS_SKETCH_GAUSSIAN) {
         const float scale = (float)(1.0 / std::sqrt((double)dd));
-        const bool tc = dense && h->opt.precision == DSANLS_PREC_BF16;
+        const bool fp8 = dense && h->opt.precision == DSANLS_PREC_FP8;
+        const bool tc = dense && (h->opt.precision == DSANLS_PREC_BF16 || fp8);
         // S (K x dd), N(0, 1/dd) entries of the field, stream `side`: fp32 S for the
-        // CUDA-core form, bf16 S^T (K-major operand) for the tensor-core form
-        if (tc)
+        // CUDA-core form, bf16 S^T (K-major operand) for the tensor-core forms, and
+        // for the fp8 form also fp8 S^T of the unit-variance draws
+        if (fp8)
+            launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, s);
+        else if (tc)
             launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, s);
         else
             launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, s);
@@ -261,8 +270,13 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         mark(pe, DSANLS_PHASE_PRODUCT, s);
         if (tc) {
             // R = (X S) B^T on tcgen05, X and S in bf16, A never stored
-            const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
-            launch_tc_sketch_rhs(Xb, h->Sb, h->W, rows, K, dd, k, h->Rpart, h->R, h->flag, s);
+            if (fp8) {
+                launch_tc_sketch_rhs_fp8(side == 0 ? h->Mq : h->MTq, h->qscale[side], h->Sq, scale, h->W, rows, K, dd,
+                                         k, h->Rpart, h->R, h->flag, s);
+            } else {
+                const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
+                launch_tc_sketch_rhs(Xb, h->Sb, h->W, rows, K, dd, k, h->Rpart, h->R, h->flag, s);
+            }
             mark(pe, DSANLS_PHASE_RHS, s);
         } else {
             if (dense) {
@@ -300,7 +314,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             launch_sgemm(g, s);
         } else {
             mark(pe, DSANLS_PHASE_RHS, s);
-            launch_sampled_spmm(xp, xc, xv, rows, h->J, dd, K, h->bits, Y, k, c2, h->R, s);
+            launch_sampled_spmm(xp, xc, xv, rows, h->J, dd, K, h->bits, Y, k, c2, h->R, h->lr[side], s);
         }
     } else {  // identity
         mark(pe, DSANLS_PHASE_B, s);
@@ -341,6 +355,40 @@ void outer_iteration(dsanls_ctx *h, cudaStream_t s) {
     launch_increment_t(h->t_dev, 1, s);
 }
 
+void free_long_rows(LongRows &lr) {
+    dfree(lr.rows); dfree(lr.first); dfree(lr.cbeg); dfree(lr.cend); dfree(lr.partial);
+    lr.nlong = lr.nchunks = 0;
+}
+
+// Rows longer than LONG_ROW entries and their chunks (host row pointer).
+void build_long_rows(LongRows &lr, const std::vector<int64_t> &ptr, int k, cudaStream_t s) {
+    free_long_rows(lr);
+    std::vector<int64_t> rows, first(1, 0), cb, ce;
+    for (size_t i = 0; i + 1 < ptr.size(); ++i) {
+        const int64_t len = ptr[i + 1] - ptr[i];
+        if (len <= LONG_ROW) continue;
+        rows.push_back((int64_t)i);
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; e += LONG_ROW) {
+            cb.push_back(e);
+            ce.push_back(std::min(e + LONG_ROW, ptr[i + 1]));
+        }
+        first.push_back((int64_t)cb.size());
+    }
+    if (rows.empty()) return;
+    lr.nlong = (int64_t)rows.size();
+    lr.nchunks = (int64_t)cb.size();
+    dalloc(lr.rows, lr.nlong);
+    dalloc(lr.first, lr.nlong + 1);
+    dalloc(lr.cbeg, lr.nchunks);
+    dalloc(lr.cend, lr.nchunks);
+    dalloc(lr.partial, lr.nchunks * k);
+    DSANLS_CUDA(cudaMemcpyAsync(lr.rows, rows.data(), rows.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DSANLS_CUDA(cudaMemcpyAsync(lr.first, first.data(), first.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DSANLS_CUDA(cudaMemcpyAsync(lr.cbeg, cb.data(), cb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DSANLS_CUDA(cudaMemcpyAsync(lr.cend, ce.data(), ce.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DSANLS_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+}
+
 int check_ready(dsanls_ctx *h) {
     if (!h->has_dense && !h->has_sparse) return fail(h, DSANLS_ESTATE, "no data: call dsanls_set_dense or dsanls_set_csr first");
     return DSANLS_OK;
@@ -356,6 +404,26 @@ int pending_status(dsanls_ctx *h) {
         return fail(h, DSANLS_ENUMERIC, "an update produced NaN or Inf");
     }
     return DSANLS_OK;
+}
+
+// bf16 (BF16 form) or fp8 with per-128-row-block scales (FP8 form) copies of M and M^T.
+void make_reduced_copies(dsanls_ctx *h) {
+    if (!h->has_dense) return;
+    cudaStream_t s = h->stream();
+    if (h->opt.precision == DSANLS_PREC_BF16 && !h->Mb) {
+        dalloc(h->Mb, h->m * h->n);
+        dalloc(h->MTb, h->m * h->n);
+        launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, s);
+        launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, s);
+    }
+    if (h->opt.precision == DSANLS_PREC_FP8 && !h->Mq) {
+        dalloc(h->Mq, h->m * h->n);
+        dalloc(h->MTq, h->m * h->n);
+        dalloc(h->qscale[0], ceil_div(h->m, 128));
+        dalloc(h->qscale[1], ceil_div(h->n, 128));
+        launch_quant_rowblocks(h->M, h->m, h->n, h->qscale[0], h->Mq, s);
+        launch_quant_rowblocks(h->MT, h->n, h->m, h->qscale[1], h->MTq, s);
+    }
 }
 
 void copy_in(void *dst, const void *src, size_t bytes, int on_device, cudaStream_t s) {
@@ -480,7 +548,11 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
     DeviceGuard dg(h->device);
     return guarded(h, [&]() {
         if (opt->solver != DSANLS_SOLVER_PGD && opt->solver != DSANLS_SOLVER_RCD) throw ArgError{"unknown solver"};
-        if (opt->precision != DSANLS_PREC_FP32 && opt->precision != DSANLS_PREC_BF16) throw ArgError{"unknown precision"};
+        if (opt->precision < DSANLS_PREC_FP32 || opt->precision > DSANLS_PREC_FP8) throw ArgError{"unknown precision"};
+        if (opt->precision == DSANLS_PREC_FP8 &&
+            (h->has_sparse || h->sketch != DSANLS_SKETCH_GAUSSIAN || h->m % 16 || h->n % 16 ||
+             h->d % 8 || (opt->d_v > 0 ? opt->d_v : h->d) % 8))
+            throw ArgError{"FP8 precision needs dense data, a Gaussian sketch, m and n multiples of 16, d and d_v of 8"};
         if (opt->precision == DSANLS_PREC_BF16 &&
             (h->has_sparse || h->sketch != DSANLS_SKETCH_GAUSSIAN || !tc_supported(h->k)))
             throw ArgError{"BF16 precision needs dense data and a Gaussian sketch"};
@@ -504,12 +576,7 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
         DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
         h->opt = *opt;
         if (cfg_change) invalidate_graph(h);
-        if (h->opt.precision == DSANLS_PREC_BF16 && h->has_dense && !h->Mb) {
-            dalloc(h->Mb, h->m * h->n);
-            dalloc(h->MTb, h->m * h->n);
-            launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, h->stream());
-            launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, h->stream());
-        }
+        make_reduced_copies(h);
         if (opt->t != h->t_host) {
             h->t_host = opt->t;
             DSANLS_CUDA(cudaMemcpyAsync(h->t_dev, &h->t_host, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream()));
@@ -539,12 +606,9 @@ int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device) 
         h->has_dense = true;
         dfree(h->Mb);
         dfree(h->MTb);
-        if (h->opt.precision == DSANLS_PREC_BF16) {
-            dalloc(h->Mb, h->m * h->n);
-            dalloc(h->MTb, h->m * h->n);
-            launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, s);
-            launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, s);
-        }
+        dfree(h->Mq);
+        dfree(h->MTq);
+        make_reduced_copies(h);
         invalidate_graph(h);
         std::fill(h->cfg_key, h->cfg_key + 6, -1);
         set_bound(h);
@@ -610,7 +674,7 @@ int dsanls_set_csr(dsanls_t h, const int64_t *rowptr, const int32_t *col, const 
             throw ArgError{"t_rowptr[0] must be 0 and t_rowptr[n] == nnz"};
         }
         if (h->has_dense) {
-            dfree(h->M); dfree(h->MT); dfree(h->Mb); dfree(h->MTb);
+            dfree(h->M); dfree(h->MT); dfree(h->Mb); dfree(h->MTb); dfree(h->Mq); dfree(h->MTq);
             h->has_dense = false;
         }
         dalloc(h->rp, m + 1);
@@ -628,6 +692,7 @@ int dsanls_set_csr(dsanls_t h, const int64_t *rowptr, const int32_t *col, const 
             copy_in(h->tcv, tv_src, nnz * sizeof(float), on_device, s);
         }
         h->nnz = nnz;
+        for (int which = 0; which < 2; ++which) build_long_rows(h->lr[which], which == 0 ? h->h_rp : h->h_trp, h->k, s);
         launch_sumsq(h->cv, nnz, h->work, WORK_ELEMS, h->dscal + 0, s);
         h->has_sparse = true;
         invalidate_graph(h);
@@ -865,12 +930,15 @@ void dsanls_destroy(dsanls_t h) {
         dfree(h->U); dfree(h->V);
         dfree(h->S); dfree(h->Sb); dfree(h->J); dfree(h->A); dfree(h->W); dfree(h->Wpart); dfree(h->R);
         dfree(h->Rpart); dfree(h->Ytb); dfree(h->Bpart);
+        dfree(h->Mq); dfree(h->MTq); dfree(h->Sq); dfree(h->qscale[0]); dfree(h->qscale[1]);
         for (int side = 0; side < 2; ++side) {
             dfree(h->G64[side]);
             dfree(h->scal[side]);
         }
         dfree(h->Gf); dfree(h->work); dfree(h->t_dev); dfree(h->flag); dfree(h->dscal);
         dfree(h->bits); dfree(h->kept);
+        free_long_rows(h->lr[0]);
+        free_long_rows(h->lr[1]);
         if (h->own_stream) cudaStreamDestroy(h->own_stream);
     }
     delete h;

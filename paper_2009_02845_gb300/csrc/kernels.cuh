@@ -37,6 +37,9 @@ void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_
                            int64_t cols, float scale, bool transposed, OutT *out, cudaStream_t s);
 void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, float *out,
                           cudaStream_t s);
+// S^T (cols x rows) as bf16 of z * scale and as fp8 E4M3 of z (t from t_dev).
+void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
+                          __nv_bfloat16 *out_b, uint8_t *out_q, cudaStream_t s);
 void launch_subsample(uint64_t seed, uint32_t side, uint64_t t, const int64_t *t_dev, int64_t n, int d,
                       int32_t *J, cudaStream_t s);
 
@@ -117,10 +120,21 @@ void launch_copy_cast_bf16(const float *in, int64_t n, __nv_bfloat16 *out, cudaS
 // out[i][0..w) = alpha * sum_{e in row i} val_e * D[col_e*ldd + 0..w)
 void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
                       const float *D, int64_t ldd, int w, float alpha, float *out, int64_t ldo, cudaStream_t s);
+// Rows longer than LONG_ROW entries, split into chunks of at most LONG_ROW
+// (built on the host from the row pointer): long row l has chunks
+// first[l] .. first[l+1]-1 covering [cbeg, cend) each; partial is scratch of
+// nchunks x k floats.
+constexpr int64_t LONG_ROW = 2048;
+struct LongRows {
+    int64_t nlong = 0, nchunks = 0;
+    int64_t *rows = nullptr, *first = nullptr, *cbeg = nullptr, *cend = nullptr;
+    float *partial = nullptr;
+};
 // out[i][0..k) = alpha * sum over entries e of row i with col_e in J of val_e * Y[col_e][0..k)
-// (CSR order); bits is scratch of ceil(K/32) words, K = number of columns; k <= 128.
+// (CSR order; long rows summed chunk by chunk, chunks in order); bits is
+// scratch of ceil(K/32) words, K = number of columns; k <= 128.
 void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows, const int32_t *J,
                          int d, int64_t K, uint32_t *bits, const float *Y, int k, float alpha, float *out,
-                         cudaStream_t s);
+                         const LongRows &lr, cudaStream_t s);
 
 }  // namespace dsanls

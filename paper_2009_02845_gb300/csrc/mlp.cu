@@ -141,7 +141,7 @@ __global__ void k_segment_colsum(const float *__restrict__ X, const int64_t *__r
     out[idx] = acc;
 }
 
-__global__ void k_sum_doubles(const double *__restrict__ x, int64_t n, double *__restrict__ out) {
+__global__ void k_sum_doubles(const double *__restrict__ x, int64_t n, double scale, double *__restrict__ out) {
     __shared__ double red[256];
     double v = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += x[i];
@@ -151,7 +151,7 @@ __global__ void k_sum_doubles(const double *__restrict__ x, int64_t n, double *_
         if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
+    if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
 __global__ void k_adam(float *__restrict__ theta, float *__restrict__ m, float *__restrict__ v,
@@ -286,7 +286,7 @@ void mlp_backward(MlpState &st, const int64_t *off, int ngroups, const float *ys
     float *dG = st.grad;
     k_out_grad<<<nblk(rows), 256, 0, s>>>(st.o, st.y, ystar, rows, k, 1.0f / (float)rows, st.dout, st.rowloss);
     DSANLS_LAUNCH_CHECK();
-    k_sum_doubles<<<1, 256, 0, s>>>(st.rowloss, rows, st.loss);
+    k_sum_doubles<<<1, 256, 0, s>>>(st.rowloss, rows, 1.0 / (double)rows, st.loss);  // mean over rows
     DSANLS_LAUNCH_CHECK();
     // dW3 = do^T h2, db3 = colsum(do)
     launch_sgemm(gemm(k, h, rows, st.dout, k, false, st.h2, h, false, dG + O.W3, h), s);

@@ -12,6 +12,8 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <cuda_fp8.h>
+
 namespace dsanls {
 
 __global__ void k_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols,
@@ -64,6 +66,35 @@ __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, c
         for (int r = 0; r < 4; ++r)
             if (i0 + r < rows) out[(i0 + r) * cols + j] = store_cast<OutT>(z[r]);
     }
+}
+
+// S^T in two forms at once (cols x rows): bf16 of z * scale and fp8 E4M3 of z.
+__global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols,
+                                float scale, __nv_bfloat16 *out_b, __nv_fp8_e4m3 *out_q) {
+    const int64_t nb4 = (rows + 3) >> 2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nb4 * cols) return;
+    const uint64_t t = (uint64_t)*t_dev;
+    const int64_t q = idx % nb4, j = idx / nb4;
+    float z[4];
+    gaussian4(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+    const int64_t i0 = 4 * q;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (i0 + r < rows) {
+            out_b[j * rows + i0 + r] = __float2bfloat16_rn(__fmul_rn(z[r], scale));
+            out_q[j * rows + i0 + r] = __nv_fp8_e4m3(z[r]);
+        }
+    }
+}
+
+void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
+                          __nv_bfloat16 *out_b, uint8_t *out_q, cudaStream_t s) {
+    const int64_t total = ((rows + 3) >> 2) * cols;
+    if (total == 0) return;
+    k_gaussian_dual<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b,
+                                                                   reinterpret_cast<__nv_fp8_e4m3 *>(out_q));
+    DSANLS_LAUNCH_CHECK();
 }
 
 __global__ void k_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols,

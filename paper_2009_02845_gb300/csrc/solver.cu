@@ -300,21 +300,83 @@ __global__ void __launch_bounds__(UPD_ROWS)
     }
 }
 
+// PGD update as a register-blocked product: a CTA owns 64 rows, thread
+// (ty, tx) the outputs of rows 4ty..4ty+3 and columns tx*TN..tx*TN+TN-1
+// (TN = KP/16); Z tile and G in shared memory, one FMA chain per output in
+// increasing l (the same order as the row kernel).
+template <int KP>
+__global__ void __launch_bounds__(256)
+    k_update_pgd_tiled(float *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k,
+                       const float *__restrict__ Gf, const double *__restrict__ scal, float bound,
+                       int *__restrict__ flag) {
+    constexpr int TN = KP / 16;
+    constexpr int LDG = KP + 4;
+    extern __shared__ __align__(16) float sm[];
+    float *gs = sm;              // KP x LDG
+    float *zs = sm + KP * LDG;   // 64 x LDG
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int nr = (int)min((int64_t)64, rows - r0);
+    for (int e = threadIdx.x; e < KP * KP; e += 256) gs[(e / KP) * LDG + (e % KP)] = Gf[e];
+    for (int e = threadIdx.x; e < 64 * k; e += 256) {
+        const int i = e / k, c = e % k;
+        zs[i * LDG + c] = (i < nr) ? Z[(r0 + i) * k + c] : 0.0f;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float acc[4][TN];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
+    for (int l = 0; l < k; ++l) {
+        float zv[4], gv[TN];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) zv[a] = zs[(ty * 4 + a) * LDG + l];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) gv[b] = gs[l * LDG + tx * TN + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) acc[a][b] = __fmaf_rn(zv[a], gv[b], acc[a][b]);
+    }
+    const float eta = (float)scal[2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = ty * 4 + a;
+        if (i >= nr) continue;
+#pragma unroll
+        for (int b = 0; b < TN; ++b) {
+            const int c = tx * TN + b;
+            if (c < k) {
+                const float grad = __fsub_rn(acc[a][b], R[(r0 + i) * k + c]);
+                Z[(r0 + i) * k + c] = project_clamp(__fmaf_rn(-eta, grad, zs[i * LDG + c]), bound, flag);
+            }
+        }
+    }
+}
+
 template <int KP>
 static void update_kp(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf,
                       const double *scal, float bound, int *flag, cudaStream_t s) {
+    if (solver == 0) {
+        const size_t smem_t = (size_t)(KP + 64) * (KP + 4) * sizeof(float);
+        k_update_pgd_tiled<KP><<<(unsigned)ceil_div(rows, 64), 256, smem_t, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
+        DSANLS_LAUNCH_CHECK();
+        return;
+    }
     const size_t smem = (size_t)(KP * KP + UPD_ROWS * (k + 1)) * sizeof(float);
     const unsigned grid = (unsigned)ceil_div(rows, UPD_ROWS);
-    if (solver == 0)
-        k_update<KP, 0><<<grid, UPD_ROWS, smem, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
-    else
-        k_update<KP, 1><<<grid, UPD_ROWS, smem, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
+    k_update<KP, 1><<<grid, UPD_ROWS, smem, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
     DSANLS_LAUNCH_CHECK();
 }
 
 void prime_solver_attributes(int max_smem) {
     allow_max_dynamic_smem(k_gram_partial, max_smem);
     allow_max_dynamic_smem(k_step_size, max_smem);
+    allow_max_dynamic_smem(k_update_pgd_tiled<16>, max_smem);
+    allow_max_dynamic_smem(k_update_pgd_tiled<32>, max_smem);
+    allow_max_dynamic_smem(k_update_pgd_tiled<64>, max_smem);
+    allow_max_dynamic_smem(k_update_pgd_tiled<128>, max_smem);
     allow_max_dynamic_smem(k_update<16, 0>, max_smem);
     allow_max_dynamic_smem(k_update<16, 1>, max_smem);
     allow_max_dynamic_smem(k_update<32, 0>, max_smem);

@@ -81,6 +81,37 @@ __global__ void k_bitmap_set(const int32_t *__restrict__ J, int d, uint32_t *__r
 // is in the sampled set (bitmap test), and the whole warp accumulates
 // val * Y[col][:] for each kept entry in CSR order (lanes across the k output
 // columns).  Deterministic: one FMA chain per output in CSR order.
+// Sum over the sampled entries of CSR range [e0, e1) into acc (lanes across k).
+DSANLS_DEV void sampled_range(const int32_t *__restrict__ col, const float *__restrict__ val, int64_t e0, int64_t e1,
+                              const uint32_t *__restrict__ bits, const float *__restrict__ Y, int k, int lane,
+                              float acc[4]) {
+    for (int64_t base = e0; base < e1; base += 32) {
+        const int64_t e = base + lane;
+        int32_t c = 0;
+        float v = 0.0f;
+        bool hit = false;
+        if (e < e1) {
+            c = col[e];
+            hit = (__ldg(&bits[c >> 5]) >> (c & 31)) & 1u;
+            if (hit) v = val[e];
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, hit);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int32_t cj = __shfl_sync(0xffffffffu, c, src);
+            const float vj = __shfl_sync(0xffffffffu, v, src);
+            const float *y = Y + (int64_t)cj * k;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int cc = lane + 32 * q;
+                if (cc < k) acc[q] = __fmaf_rn(vj, y[cc], acc[q]);
+            }
+        }
+    }
+}
+
+// Rows longer than LONG_ROW entries are skipped here and handled in chunks.
 __global__ void __launch_bounds__(256)
     k_sampled_spmm(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, const float *__restrict__ val,
                    int64_t rows, const uint32_t *__restrict__ bits, const float *__restrict__ Y, int k, float alpha,
@@ -91,6 +122,7 @@ __global__ void __launch_bounds__(256)
     for (int64_t i = warp; i < rows; i += nwarps) {
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         const int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
+        if (e1 - e0 > LONG_ROW) continue;
         for (int64_t base = e0; base < e1; base += 32) {
             const int64_t e = base + lane;
             int32_t c = 0;
@@ -123,9 +155,40 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// One warp per chunk of a long row: partial[chunk][0..k)
+__global__ void __launch_bounds__(256)
+    k_sampled_chunks(const int64_t *__restrict__ cbeg, const int64_t *__restrict__ cend, int64_t nchunks,
+                     const int32_t *__restrict__ col, const float *__restrict__ val, const uint32_t *__restrict__ bits,
+                     const float *__restrict__ Y, int k, float *__restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = warp; c < nchunks; c += nwarps) {
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        sampled_range(col, val, cbeg[c], cend[c], bits, Y, k, lane, acc);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int cc = lane + 32 * q;
+            if (cc < k) partial[c * k + cc] = acc[q];
+        }
+    }
+}
+
+// out[row] = alpha * sum of the row's chunk partials in chunk order
+__global__ void k_combine_long(const int64_t *__restrict__ lrows, const int64_t *__restrict__ first, int64_t nlong,
+                               const float *__restrict__ partial, int k, float alpha, float *__restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nlong * k) return;
+    const int64_t l = idx / k;
+    const int c = (int)(idx % k);
+    float acc = 0.0f;
+    for (int64_t ch = first[l]; ch < first[l + 1]; ++ch) acc += partial[ch * k + c];
+    out[lrows[l] * k + c] = __fmul_rn(alpha, acc);
+}
+
 void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows, const int32_t *J,
                          int d, int64_t K, uint32_t *bits, const float *Y, int k, float alpha, float *out,
-                         cudaStream_t s) {
+                         const LongRows &lr, cudaStream_t s) {
     DSANLS_CUDA(cudaMemsetAsync(bits, 0, (size_t)ceil_div(K, 32) * sizeof(uint32_t), s));
     k_bitmap_set<<<(unsigned)ceil_div(d, 256), 256, 0, s>>>(J, d, bits);
     DSANLS_LAUNCH_CHECK();
@@ -134,6 +197,15 @@ void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float 
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_sampled_spmm<<<(unsigned)blocks, 256, 0, s>>>(rowptr, col, val, rows, bits, Y, k, alpha, out);
     DSANLS_LAUNCH_CHECK();
+    if (lr.nlong > 0) {
+        int64_t cb = ceil_div(lr.nchunks, 8);
+        if (cb > 152 * 16) cb = 152 * 16;
+        k_sampled_chunks<<<(unsigned)cb, 256, 0, s>>>(lr.cbeg, lr.cend, lr.nchunks, col, val, bits, Y, k, lr.partial);
+        DSANLS_LAUNCH_CHECK();
+        k_combine_long<<<(unsigned)ceil_div(lr.nlong * k, 256), 256, 0, s>>>(lr.rows, lr.first, lr.nlong, lr.partial,
+                                                                            k, alpha, out);
+        DSANLS_LAUNCH_CHECK();
+    }
 }
 
 }  // namespace dsanls

@@ -24,6 +24,7 @@
 // returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <mutex>
@@ -125,6 +126,20 @@ DSANLS_DEV void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32
         : "memory");
 }
 
+// Instruction descriptor: kind::f8f6f4 with E4M3 A and B, fp32 D, both K-major.
+DSANLS_DEV uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+DSANLS_DEV void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 DSANLS_DEV void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -171,11 +186,16 @@ struct __align__(8) TcSmemTail {
 // FUSED = false: plain product C = X S over the K-range of split blockIdx.y
 //   (k-blocks [y*kb_per_split, ...)); writes out[split][rows][ldo] for the
 //   columns of this chunk (columns < d).
-template <int STAGES, bool FUSED>
+// FP8 = true: X and S^T are fp8 E4M3 (kind::f8f6f4, K blocks of 128 elements,
+//   still 128 bytes per row); the fused epilogue multiplies D1 by
+//   row_scale[m0 / 128] * extra_scale before the bf16 repack.
+template <int STAGES, bool FUSED, bool FP8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
               const __grid_constant__ CUtensorMap map_b, int64_t rows, int64_t K, int64_t d, int k, int kp,
-              int kb_per_split, float *__restrict__ out, int *__restrict__ err) {
+              int kb_per_split, float *__restrict__ out, int *__restrict__ err, const float *__restrict__ row_scale,
+              float extra_scale) {
+    constexpr int BKE = FP8 ? 128 : BK;  // K elements per stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -189,7 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int chunk = blockIdx.x % nchunks;
     const int64_t m0 = (int64_t)(blockIdx.x / nchunks) * BM;
     const int n0 = chunk * BN;
-    const int nk_total = (int)ceil_div(K, BK);
+    const int nk_total = (int)ceil_div(K, BKE);
     const int kb0 = FUSED ? 0 : (int)blockIdx.y * kb_per_split;
     const int nk = FUSED ? nk_total : max(0, min(kb_per_split, nk_total - kb0));
 
@@ -236,8 +256,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (*(volatile int *)&tail->failed) break;
                 uint8_t *sa = stage_base + s * STAGE_BYTES;
                 mbar_expect_tx(&tail->full[s], STAGE_BYTES);
-                tma_load_2d(sa, &map_x, (kb0 + kb) * BK, (int)m0, &tail->full[s]);
-                tma_load_2d(sa + A_STAGE_BYTES, &map_s, (kb0 + kb) * BK, n0, &tail->full[s]);
+                tma_load_2d(sa, &map_x, (kb0 + kb) * BKE, (int)m0, &tail->full[s]);
+                tma_load_2d(sa + A_STAGE_BYTES, &map_s, (kb0 + kb) * BKE, n0, &tail->full[s]);
                 ++issued;
             }
             // drain: every copy this thread issued has landed before the CTA can exit
@@ -247,7 +267,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id1 = idesc_bf16(BM, BN);
+            const uint32_t id1 = FP8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
             bool ok = true;
             for (int kb = 0; kb < nk && ok; ++kb) {
                 const int s = kb % STAGES;
@@ -260,7 +280,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t sb = sa + A_STAGE_BYTES;
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk)
-                    mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (kb | kk) != 0);
+                    if (FP8)  // 32 fp8 elements = 32 bytes per MMA, as 16 bf16 elements
+                        mma_e4m3(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (kb | kk) != 0);
+                    else
+                        mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (kb | kk) != 0);
                 mma_commit(&tail->empty[s]);
             }
             if (ok) {
@@ -319,12 +342,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         } else {
             if (ok) {
                 fence_after();
+                const float dscale = FP8 ? row_scale[m0 / BM] * extra_scale : 1.0f;
                 // D1 (fp32) -> bf16, 128B-swizzled K-major layout: atom a = col / 64
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t v[32];
                     tmem_ld32(trow + c * 32, v);
                     tmem_ld_wait();
+                    if (FP8) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * dscale);
+                    }
                     uint8_t *atom = a2 + (c >> 1) * (BM * 128) + r * 128;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {  // 4 chunks of 8 bf16 (16 bytes)
@@ -416,6 +444,20 @@ CUtensorMap make_map(const void *base, int64_t rows, int64_t cols, int box_rows)
     return m;
 }
 
+// 2-D fp8 (one byte) row-major tensor, box (128 cols x box_rows), 128-byte swizzle.
+CUtensorMap make_map_u8(const void *base, int64_t rows, int64_t cols, int box_rows) {
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols};
+    const cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box,
+                                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw ArgError{"cuTensorMapEncodeTiled failed (fp8)"};
+    return m;
+}
+
 int kp_of(int k) { return (int)ceil_div(k, 16) * 16; }
 
 size_t smem_bytes(int stages, int kp) {
@@ -451,11 +493,71 @@ void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const
     const int stages = stages_for(kp);
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
-        k_tc_gemm<4, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart, err);
+        k_tc_gemm<4, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+                                                                            err, nullptr, 1.0f);
     else
-        k_tc_gemm<3, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart, err);
+        k_tc_gemm<3, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+                                                                            err, nullptr, 1.0f);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
+    DSANLS_LAUNCH_CHECK();
+}
+
+void launch_tc_sketch_rhs_fp8(const uint8_t *Xq, const float *row_scale, const uint8_t *Sq, float s_scale,
+                              const float *B, int64_t rows, int64_t K, int64_t d, int k, float *Rpart, float *R,
+                              int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || d > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 16 != 0 || d % 8 != 0) throw ArgError{"fp8 path needs K a multiple of 16 and d of 8"};
+    const int kp = kp_of(k);
+    const int nchunks = (int)ceil_div(d, BN);
+    __nv_bfloat16 *Bb = reinterpret_cast<__nv_bfloat16 *>(
+        (reinterpret_cast<uintptr_t>(Rpart + (int64_t)nchunks * rows * k) + 15) & ~(uintptr_t)15);
+    k_to_bf16<<<(unsigned)ceil_div((int64_t)k * d, 256), 256, 0, s>>>(B, (int64_t)k * d, Bb);
+    DSANLS_LAUNCH_CHECK();
+    const CUtensorMap mx = make_map_u8(Xq, rows, K, BM);
+    const CUtensorMap ms = make_map_u8(Sq, d, K, BN);
+    const CUtensorMap mb = make_map(Bb, k, d, kp);
+    const int64_t tiles = ceil_div(rows, BM) * nchunks;
+    const int stages = stages_for(kp);
+    const size_t smem = smem_bytes(stages, kp);
+    if (stages == 4)
+        k_tc_gemm<4, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+                                                                           err, row_scale, s_scale);
+    else
+        k_tc_gemm<3, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+                                                                           err, row_scale, s_scale);
+    DSANLS_LAUNCH_CHECK();
+    k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
+    DSANLS_LAUNCH_CHECK();
+}
+
+// Per 128-row block of X (rows x K fp32): scale = max |x| / 448 (1 if the block is 0),
+// Xq = e4m3(x / scale) with round-to-nearest-even and saturation.
+__global__ void k_rowblock_absmax(const float *__restrict__ X, int64_t rows, int64_t K, float *__restrict__ scale) {
+    __shared__ float red[256];
+    const int64_t r0 = (int64_t)blockIdx.x * 128;
+    const int64_t nr = min((int64_t)128, rows - r0);
+    float mx = 0.0f;
+    for (int64_t e = threadIdx.x; e < nr * K; e += blockDim.x) mx = fmaxf(mx, fabsf(X[r0 * K + e]));
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scale[blockIdx.x] = red[0] > 0.0f ? __fdiv_rn(red[0], 448.0f) : 1.0f;
+}
+
+__global__ void k_quant_e4m3(const float *__restrict__ X, int64_t rows, int64_t K, const float *__restrict__ scale,
+                             __nv_fp8_e4m3 *__restrict__ Xq) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * K; i += (int64_t)gridDim.x * blockDim.x)
+        Xq[i] = __nv_fp8_e4m3(__fdiv_rn(X[i], scale[(i / K) / 128]));
+}
+
+void launch_quant_rowblocks(const float *X, int64_t rows, int64_t K, float *scale, uint8_t *Xq, cudaStream_t s) {
+    k_rowblock_absmax<<<(unsigned)ceil_div(rows, 128), 256, 0, s>>>(X, rows, K, scale);
+    DSANLS_LAUNCH_CHECK();
+    k_quant_e4m3<<<152 * 16, 256, 0, s>>>(X, rows, K, scale, reinterpret_cast<__nv_fp8_e4m3 *>(Xq));
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -475,8 +577,8 @@ void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t row
     const CUtensorMap mx = make_map(X, rows, K, BM);
     const CUtensorMap ms = make_map(St, d, K, BN);
     dim3 grid((unsigned)tiles, (unsigned)splits);
-    k_tc_gemm<4, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, d, 0, 0, kb_per_split, part,
-                                                                  err);
+    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, d, 0, 0, kb_per_split,
+                                                                         part, err, nullptr, 1.0f);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * d, splits, rows, d, d, C, d, s);
 }
@@ -504,9 +606,11 @@ void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfl
 }
 
 void prime_tc_attributes(int max_smem) {
-    allow_max_dynamic_smem(k_tc_gemm<4, true>, max_smem);
-    allow_max_dynamic_smem(k_tc_gemm<3, true>, max_smem);
-    allow_max_dynamic_smem(k_tc_gemm<4, false>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, true, false>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<3, true, false>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, false, false>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, true, true>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<3, true, true>, max_smem);
 }
 
 }  // namespace dsanls

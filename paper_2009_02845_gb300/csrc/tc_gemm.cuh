@@ -16,6 +16,13 @@ int64_t tc_rpart_elems(int64_t rows, int64_t d, int k);
 // bounded wait that gives up sets bit 2 of *err.  K and d must be multiples of 8.
 void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const float *B, int64_t rows, int64_t K,
                           int64_t d, int k, float *Rpart, float *R, int *err, cudaStream_t s);
+// The same with X and S^T in fp8 E4M3: X = Xq * row_scale[row / 128], S = Sq * s_scale
+// (K a multiple of 16, d of 8).
+void launch_tc_sketch_rhs_fp8(const uint8_t *Xq, const float *row_scale, const uint8_t *Sq, float s_scale,
+                              const float *B, int64_t rows, int64_t K, int64_t d, int k, float *Rpart, float *R,
+                              int *err, cudaStream_t s);
+// Per 128-row block scale = max |x| / 448 and Xq = e4m3(x / scale) (rows x K).
+void launch_quant_rowblocks(const float *X, int64_t rows, int64_t K, float *scale, uint8_t *Xq, cudaStream_t s);
 // C (rows x d, fp32) = X S with X rows x K bf16 and S^T d x K bf16, split-K;
 // `part` is scratch of tc_gemm_part_elems(rows, d) floats.
 int64_t tc_gemm_part_elems(int64_t rows, int64_t d);

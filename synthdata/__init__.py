@@ -138,3 +138,20 @@ def batch_specs(count, seed):
         k = int(g.choice([8, 16, 32]))
         specs.append(dict(m=m, n=n, k=k, d=max(4 * k, n // 8), d_v=max(4 * k, m // 8), seed=i))
     return specs
+
+
+def planted_dense_torch(m, n, k, seed, zero_frac=0.0, noise=0.01, device="cuda"):
+    """Same recipe as planted_dense, drawn with torch's generator on `device`
+    (fast, for large throw-away training matrices; not bit-identical to the
+    numpy recipe).  Returns M (m x n float32 tensor)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 7919 + 17)
+    U0 = torch.rand((m, k), generator=g, device=device)
+    V0 = torch.rand((n, k), generator=g, device=device)
+    if zero_frac > 0:
+        U0[torch.rand((m, k), generator=g, device=device) < zero_frac] = 0.0
+        V0[torch.rand((n, k), generator=g, device=device) < zero_frac] = 0.0
+    M = torch.randn((m, n), generator=g, device=device).abs_().mul_(noise)
+    M.addmm_(U0, V0.T)
+    return M

@@ -1,0 +1,172 @@
+"""Learned warm start on the GPU against the FP64 oracle.
+
+* network output and loss gradient: the GPU passes use the fp32 master
+  weights rounded to bf16; the oracle is given the same rounded weights, so
+  the only difference is fp32 vs FP64 arithmetic: outputs within 1e-4 and
+  gradients within 1e-3 (norm-wise relative);
+* harvested triples: b = r + mu u matches the oracle's terms (1e-5) and the
+  FISTA minimiser matches the oracle's exact active-set minimiser (1e-3);
+* the learned half-step: every row equals the oracle's chosen candidate, or
+  the other candidate when the two objectives tie within 1e-5 (the choice is
+  an fp32 comparison on the GPU);
+* training on harvested triples lowers the loss, and the trained network
+  gains over the plain method on a held-out problem.
+"""
+import numpy as np
+import pytest
+
+from oracle import method
+from oracle import mlp as omlp
+from synthdata import planted_dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2009_02845_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _groups(k, n_groups, rows_per, seed):
+    g = np.random.default_rng(seed)
+    Gs, mus, bs = [], [], []
+    for _ in range(n_groups):
+        B = g.random((k, 3 * k))
+        Gs.append((B @ B.T).astype(np.float32))
+        mus.append(np.float32(g.uniform(0.1, 1.0)))
+        bs.append((g.random((rows_per, k)) * 3.0).astype(np.float32))
+    return Gs, mus, bs
+
+
+def _dev(Gs, mus, bs):
+    import torch
+    off = np.concatenate([[0], np.cumsum([b.shape[0] for b in bs])]).astype(np.int64)
+    return (torch.tensor(np.stack(Gs)).cuda(), torch.tensor(np.array(mus, np.float32)).cuda(),
+            torch.tensor(off).cuda(), torch.tensor(np.concatenate(bs)).cuda())
+
+
+def test_network_output_and_gradient_match_oracle(pkg):
+    import torch
+    k, h = 8, 32
+    net = pkg.MLP(k, h, max_rows=1024, max_groups=8, seed=3)
+    P = omlp.unflatten(method.round_bf16(net.params()), k, h)
+    Gs, mus, bs = _groups(k, 3, 40, 0)
+    G, mu, off, b = _dev(Gs, mus, bs)
+    x = net.predict(G, mu, off, b).cpu().numpy()
+    xo, groups, xstars = [], [], []
+    for Gi, mi, bi in zip(Gs, mus, bs):
+        Gn, bn, s, beta = omlp.normalise(Gi.astype(np.float64), float(mi), bi.astype(np.float64))
+        y, _ = omlp.forward(P, Gn, bn)
+        xo.append(y * (beta / s)[:, None])
+        xs = omlp.prox_exact(Gi.astype(np.float64), float(mi), bi.astype(np.float64))
+        xstars.append(xs.astype(np.float32))
+        groups.append((Gn, bn, xstars[-1].astype(np.float64) * s / beta[:, None]))
+    assert _rel(x, np.concatenate(xo)) <= 1e-4
+    loss, grad = net.train_step(G, mu, off, b, torch.tensor(np.concatenate(xstars)).cuda(), 0.0, want_grad=True)
+    loss_o, grads_o = omlp.loss_and_grads(P, groups)
+    assert abs(loss - loss_o) <= 1e-4 * loss_o
+    go = omlp.flatten(grads_o, k, h)
+    gg = grad.astype(np.float64)
+    off_p = 0
+    for name, shape in omlp.param_shapes(k, h):
+        n = int(np.prod(shape))
+        assert _rel(gg[off_p:off_p + n], go[off_p:off_p + n]) <= 1e-3, name
+        off_p += n
+    net.close()
+
+
+def _handle(pkg, m, n, k, d, seed, M=None):
+    if M is None:
+        M, _, _ = planted_dense(m, n, k, seed, zero_frac=0.7)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=seed, t=2)
+    h.set_dense(M)
+    return h, M
+
+
+def test_harvest_matches_oracle(pkg):
+    m, n, k, d = 400, 300, 16, 64
+    h, M = _handle(pkg, m, n, k, d, 5)
+    U0, V0 = method.default_init(5, m, n, k)
+    G, mu, b, x = (t.cpu().numpy() for t in h.harvest(0, iters=600))
+    h.close()
+    S = method.Sketch(method.GAUSSIAN, 5, 2, 0, n, d)
+    _, _, Go, Ro = method.sketched_terms(M.astype(np.float64), V0.astype(np.float64), S)
+    mu_o = method.mu_t(1.0, 1.0, 2)
+    assert abs(float(mu[0]) - mu_o) <= 1e-6 * mu_o
+    assert _rel(G, Go) <= 1e-5
+    assert _rel(b, Ro + mu_o * U0) <= 1e-5
+    xs = omlp.prox_exact(Go, mu_o, Ro + mu_o * U0)
+    assert _rel(x, xs) <= 1e-3
+
+
+def test_learned_half_step_matches_oracle(pkg):
+    m, n, k, d, hidden = 500, 350, 16, 80, 64
+    net = pkg.MLP(k, hidden, max_rows=1024, max_groups=4, seed=11)
+    P = omlp.unflatten(method.round_bf16(net.params()), k, hidden)
+    h, M = _handle(pkg, m, n, k, d, 7)
+    h.set_mlp(net, pg_iters=3)
+    h.half_step(0)
+    U1, _ = h.factors()
+    kept = h.mlp_kept()
+    h.close()
+    U0, V0 = method.default_init(7, m, n, k)
+    S = method.Sketch(method.GAUSSIAN, 7, 2, 0, n, d)
+    _, _, Go, Ro = method.sketched_terms(M.astype(np.float64), V0.astype(np.float64), S)
+    mu = method.mu_t(1.0, 1.0, 2)
+    eta = 1.0 / (method.lambda_max(Go) + mu)
+    xm, xp, fm, fp = omlp.learned_candidates(P, Go, mu, Ro, U0.astype(np.float64), eta, 3)
+    chosen = np.where((fm <= fp)[:, None], xm, xp)
+    other = np.where((fm <= fp)[:, None], xp, xm)
+    tie = np.abs(fm - fp) <= 1e-5 * np.maximum(np.abs(fm), np.abs(fp))
+    scale = np.linalg.norm(chosen, axis=1) + 1e-12
+    ok_chosen = np.linalg.norm(U1 - chosen, axis=1) <= 1e-4 * scale
+    ok_other = tie & (np.linalg.norm(U1 - other, axis=1) <= 1e-4 * scale)
+    assert np.all(ok_chosen | ok_other)
+    assert abs(kept - int((fm <= fp).sum())) <= int(tie.sum())
+    net.close()
+
+
+def test_training_lowers_loss_and_trained_network_gains(pkg):
+    """Harvest triples from planted training problems (seeds 1-4), train on the
+    GPU, and compare the learned form with the plain method on seed 21."""
+    import torch
+    m, n, k, d, hidden = 1024, 512, 16, 128, 128
+    net = pkg.MLP(k, hidden, max_rows=4096, max_groups=64, seed=1)
+    Gs, mus, bs, xs = [], [], [], []
+    for seed in (1, 2, 3, 4):
+        h, _ = _handle(pkg, m, n, k, d, seed)
+        for it in range(4):
+            for side in (0, 1):
+                G, mu, b, x = h.harvest(side, iters=300)
+                Gs.append(G); mus.append(mu); bs.append(b); xs.append(x)
+                h.half_step(side)
+            h.set_options(t=3 + it)
+        h.close()
+    rng = np.random.default_rng(0)
+    losses = []
+    for step in range(600):
+        pick = rng.choice(len(Gs), 8, replace=False)
+        rows = [min(256, bs[i].shape[0]) for i in pick]
+        G = torch.stack([Gs[i] for i in pick])
+        mu = torch.cat([mus[i] for i in pick])
+        off = torch.tensor(np.concatenate([[0], np.cumsum(rows)]), dtype=torch.int64, device="cuda")
+        b = torch.cat([bs[i][:r] for i, r in zip(pick, rows)])
+        x = torch.cat([xs[i][:r] for i, r in zip(pick, rows)])
+        losses.append(net.train_step(G, mu, off, b, x, 3e-3))
+    assert np.mean(losses[-20:]) < 0.7 * np.mean(losses[:20])
+    errs = {}
+    for learned in (False, True):
+        h, _ = _handle(pkg, m, n, k, d, 21)
+        if learned:
+            h.set_mlp(net, pg_iters=4)
+        h.set_options(t=0)
+        h.step(15)
+        errs[learned] = h.rel_error()
+        h.close()
+    assert errs[True] < errs[False], errs
+    net.close()

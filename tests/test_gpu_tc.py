@@ -95,3 +95,56 @@ def test_bf16_rejects_unsupported_shapes(pkg):
     with pytest.raises(pkg.DSANLSError):
         h.set_options(precision=pkg.BF16)
     h.close()
+
+
+FP8_CASES = [
+    (256, 128, 16, 256, 256),
+    (1024, 816, 10, 104, 96),
+    (640, 528, 64, 520, 264),
+]
+
+
+@pytest.mark.parametrize("case", FP8_CASES)
+def test_fp8_half_steps(pkg, case):
+    """fp8 form against the oracle's fp8 model (same E4M3 codes and scales on
+    both sides: the only difference is fp32 accumulation) <= 3e-4, and against
+    plain FP64 <= 3e-2 (E4M3 keeps 3 fraction bits)."""
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 4)
+    U, V = initial_factors(m, n, k, 5)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=23, d_v=d_v, precision=pkg.FP8, t=2)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 23, 2, side, X.shape[1], dd)
+        mu = method.mu_t(1.0, 1.0, 2)
+        model = method.half_step(X, Y, Z, S, method.PGD, mu, fp8=(23, 2, side))
+        exact = method.half_step(X, Y, Z, S, method.PGD, mu)
+        assert got.min() >= 0
+        assert _rel(got, model) <= 3e-4, (side, _rel(got, model))
+        assert _rel(got, exact) <= 3e-2, (side, _rel(got, exact))
+
+
+def test_fp8_run_final_error(pkg):
+    """fp8 form plus three closing fp32 iterations ends within 2e-3 of the
+    oracle's final relative error."""
+    m, n, k, d, T = 1024, 816, 10, 104, 30
+    M, _, _ = planted_dense(m, n, k, 0)
+    U0, V0 = method.default_init(0, m, n, k)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=0, precision=pkg.FP8)
+    h.set_dense(M)
+    h.step(T - 3)
+    h.set_options(precision=pkg.FP32)
+    h.step(3)
+    err = h.rel_error()
+    h.close()
+    _, _, errs = method.run(M, U0, V0, 0, T, method.Options(sketch=method.GAUSSIAN, d=d))
+    assert abs(err - errs[-1]) <= 2e-3, (err, errs[-1])

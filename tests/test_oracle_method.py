@@ -294,3 +294,27 @@ def test_round_bf16_matches_torch():
     x = np.concatenate([x, (np.arange(1, 200, dtype=np.uint32) << 16 | 0x8000).view(np.float32)])
     want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(method.round_bf16(x), want)
+
+
+def test_round_e4m3_matches_torch():
+    """The oracle's E4M3 rounding equals torch's float32 -> float8_e4m3fn conversion (in range)."""
+    import torch
+    g = np.random.default_rng(1)
+    x = np.concatenate([g.standard_normal(20000).astype(np.float32) * 20,
+                        g.uniform(-448, 448, 2000).astype(np.float32),
+                        np.array([0.0, 1.0, 1.0625, 1.1875, 0.001953125, 0.0029296875, 447.9, 448.0, -3.0e-3],
+                                 np.float32)])
+    x = x[np.abs(x) <= 448.0]
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(method.round_e4m3(x), want)
+
+
+def test_rowblock_quantisation_error_bound():
+    """Per-block scaling keeps every entry within half an E4M3 quantum of its block."""
+    g = np.random.default_rng(2)
+    X = (g.random((300, 50)) * np.repeat([1.0, 100.0, 0.01], 100)[:, None]).astype(np.float32)
+    Xd = method.quantise_rowblocks_e4m3(X)
+    for r0 in range(0, 300, 128):
+        blk = X[r0:r0 + 128].astype(np.float64)
+        sc = blk.max() / 448.0
+        assert np.all(np.abs(Xd[r0:r0 + 128] - blk) <= np.maximum(np.abs(blk) * 2.0 ** -4, sc * 2.0 ** -9) * 1.0001)
