@@ -196,6 +196,33 @@ def sketched_terms(X, Y, S):
     return A, B, G, R
 
 
+def sketched_terms_reassociated(X, Y, S):
+    """B, G and R of sketched_terms with R formed in the other order:
+    P = S B^T (n x k) first, then R = X P.  In exact arithmetic R = (X S) B^T
+    = X (S B^T) (associativity of the matrix product); the work is
+    2 n d k + 2 rows n k instead of 2 rows n d + 2 rows d k.  A = X S is not
+    formed (None)."""
+    Sd = S.dense()
+    B = Y.T @ Sd
+    G = B @ B.T
+    P = Sd @ B.T
+    R = X @ P
+    R = np.asarray(R.toarray() if hasattr(R, "toarray") else R, dtype=np.float64)
+    return None, B, G, R
+
+
+def sketched_terms_reassociated_bf16(X, Y, S):
+    """The reassociated order with bf16 operands: S, Y rounded to bf16 for
+    B = Y^T S (exact accumulation); P = S round(B)^T rounded to bf16 where it
+    enters R = round(X) P; G = B B^T from the unrounded B."""
+    Sb = round_bf16(S.dense32)
+    B = round_bf16(Y).T @ Sb
+    G = B @ B.T
+    P = round_bf16(Sb @ round_bf16(B).T)
+    R = round_bf16(X) @ P
+    return None, B, G, R
+
+
 def pgd_update(Z, G, R, eta, bound=None):
     """One projected-gradient step, eq. gradient_descent:
     Z <- max{Z - eta (Z G - R), 0} (the gradient's factor 2 is inside eta)."""
@@ -219,7 +246,8 @@ def rcd_update(Z, G, R, mu, bound=None):
     return Znew
 
 
-def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf16=False, fp8=None):
+def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf16=False, fp8=None,
+              reassociate=False):
     """Update of the factor Z (rows x k) against data X (rows x n) with the
     other factor Y (n x k) fixed and sketch S (n x d): one solver step on the
     sketched subproblem (eq. sketched_sub).  ``rows`` restricts the result to a
@@ -227,7 +255,9 @@ def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf1
     if rows is not None:
         X = X[rows]
         Z = Z[rows]
-    if fp8 is not None:  # fp8 = (seed, t, side) of the sketch, to redraw its unit-variance values
+    if reassociate:
+        A, B, G, R = (sketched_terms_reassociated_bf16 if bf16 else sketched_terms_reassociated)(X, Y, S)
+    elif fp8 is not None:  # fp8 = (seed, t, side) of the sketch, to redraw its unit-variance values
         A, B, G, R = sketched_terms_fp8(X, Y, S, *fp8)
     elif bf16:
         A, B, G, R = sketched_terms_bf16(X, Y, S)

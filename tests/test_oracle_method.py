@@ -318,3 +318,103 @@ def test_rowblock_quantisation_error_bound():
         blk = X[r0:r0 + 128].astype(np.float64)
         sc = blk.max() / 448.0
         assert np.all(np.abs(Xd[r0:r0 + 128] - blk) <= np.maximum(np.abs(blk) * 2.0 ** -4, sc * 2.0 ** -9) * 1.0001)
+
+
+# --------------------------------------------------------------------------
+# the reassociated order R = X (S B^T) and the rounding points of the bf16
+# models
+# --------------------------------------------------------------------------
+
+class _FixedSketch:
+    """A Gaussian-kind sketch with given binary32 values (for exact cases)."""
+
+    def __init__(self, values):
+        self.kind = method.GAUSSIAN
+        self.dense32 = np.asarray(values, dtype=np.float32)
+        self.n, self.d = self.dense32.shape
+        self.scale = np.float32(1.0)
+        self.J = None
+
+    def dense(self):
+        return self.dense32.astype(np.float64)
+
+    def right_multiply(self, X):
+        return np.asarray(X @ self.dense(), dtype=np.float64)
+
+
+@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE, method.IDENTITY])
+@pytest.mark.parametrize("sparse", [False, True])
+def test_reassociated_order_equals_paper_order(kind, sparse):
+    """(X S) B^T = X (S B^T): both orders give the same B, G and R."""
+    M, U, V = _problem(40, 32, 5, 3)
+    d = 32 if kind == method.IDENTITY else 12
+    S = method.Sketch(kind, 11, 2, 0, 32, d)
+    X = sp.csr_matrix(np.where(M > 0.6, M, 0.0)) if sparse else M
+    _, B1, G1, R1 = method.sketched_terms(X, V, S)
+    _, B2, G2, R2 = method.sketched_terms_reassociated(X, V, S)
+    for a, b in ((B1, B2), (G1, G2), (R1, R2)):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("model", ["paper", "reassociated"])
+def test_bf16_models_are_exact_on_representable_inputs(model):
+    """Small integers are bf16 values and their products stay exact: the bf16
+    models then equal the exact terms bit for bit."""
+    g = np.random.default_rng(4)
+    X = g.integers(0, 3, (9, 7)).astype(np.float64)
+    Y = g.integers(0, 3, (7, 2)).astype(np.float64)
+    S = _FixedSketch(g.integers(-1, 2, (7, 3)))
+    f = method.sketched_terms_bf16 if model == "paper" else method.sketched_terms_reassociated_bf16
+    _, B, G, R = f(X, Y, S)
+    _, Be, Ge, Re = method.sketched_terms(X, Y, S)
+    assert np.array_equal(B, Be) and np.array_equal(G, Ge) and np.array_equal(R, Re)
+
+
+def test_reassociated_bf16_rounding_points():
+    """Where the reassociated bf16 model rounds: X, Y, S on entry, B where it
+    enters P (not in G), and P where it enters R.  Hand-computed: with
+    S = [[1],[1]], Y = [[128],[129]]: B = 257 (G = 257^2 exact), round(B) = 256
+    (tie to even), P = [[256],[256]], R = X P."""
+    X = np.array([[1.0, 0.0]])
+    _, B, G, R = method.sketched_terms_reassociated_bf16(X, np.array([[128.0], [129.0]]), _FixedSketch([[1.0], [1.0]]))
+    assert B[0, 0] == 257.0 and G[0, 0] == 257.0 ** 2 and R[0, 0] == 256.0
+    # P rounded: S = [[7],[1]], Y = [[0],[43]]: B = 43, P = [[301],[43]] -> 301 rounds to 300
+    _, B, _, R = method.sketched_terms_reassociated_bf16(X, np.array([[0.0], [43.0]]), _FixedSketch([[7.0], [1.0]]))
+    assert B[0, 0] == 43.0 and R[0, 0] == 300.0
+    # X, Y and S rounded on entry: 1 + 2^-9 is not a bf16 value (rounds to 1)
+    e = 1.0 + 2.0 ** -9
+    _, B, _, R = method.sketched_terms_reassociated_bf16(np.array([[e, 0.0]]), np.array([[e], [0.0]]),
+                                                         _FixedSketch([[e], [0.0]]))
+    assert B[0, 0] == 1.0 and R[0, 0] == 1.0
+
+
+def test_paper_order_bf16_rounding_points():
+    """Where the paper-order bf16 model rounds: A = X S where it enters R, B
+    where it enters R (not in G).  X = [[128, 129]], S = [[1],[1]]: A = 257 ->
+    256; Y = [[1],[0]]: B = 1, R = 256."""
+    _, B, G, R = method.sketched_terms_bf16(np.array([[128.0, 129.0]]), np.array([[1.0], [0.0]]),
+                                            _FixedSketch([[1.0], [1.0]]))
+    assert B[0, 0] == 1.0 and R[0, 0] == 256.0
+    _, B, G, R = method.sketched_terms_bf16(np.array([[1.0, 0.0]]), np.array([[128.0], [129.0]]),
+                                            _FixedSketch([[1.0], [1.0]]))
+    assert B[0, 0] == 257.0 and G[0, 0] == 257.0 ** 2 and R[0, 0] == 256.0
+
+
+def test_reassociated_bf16_error_is_small_but_nonzero():
+    """On Gaussian data the bf16 reassociated R is within a few bf16 units of
+    the exact R (relative Frobenius error between 1e-5 and 2e-2)."""
+    M, U, V = _problem(64, 48, 6, 5)
+    S = method.Sketch(method.GAUSSIAN, 3, 0, 0, 48, 16)
+    _, _, _, Re = method.sketched_terms(M, V, S)
+    _, _, _, Rb = method.sketched_terms_reassociated_bf16(M, V, S)
+    rel = np.linalg.norm(Rb - Re) / np.linalg.norm(Re)
+    assert 1e-5 < rel < 2e-2
+
+
+def test_reassociated_half_step_matches_paper_order():
+    """A full PGD half-step in either order agrees to rounding."""
+    M, U, V = _problem(30, 24, 4, 6)
+    S = method.Sketch(method.GAUSSIAN, 1, 4, 0, 24, 10)
+    a = method.half_step(M, V, U, S, method.PGD, 2.0)
+    b = method.half_step(M, V, U, S, method.PGD, 2.0, reassociate=True)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
