@@ -42,6 +42,10 @@ WORKLOADS = {
     "dense_gaussian": dict(m=65536, n=16384, k=64, d=2048, d_v=2048, sketch=0, zero_frac=0.7, noise=0.01,
                            desc="dense 65536x16384 planted (k=64, 70% zero factors, |N(0,0.01^2)| noise), "
                                 "Gaussian sketch d=d'=2048, PGD"),
+    "dense_gaussian_reassoc": dict(m=65536, n=16384, k=64, d=2048, d_v=2048, sketch=0, zero_frac=0.7, noise=0.01,
+                                   order=1,
+                                   desc="dense 65536x16384 planted (k=64), Gaussian sketch d=d'=2048, PGD, "
+                                        "reassociated order R = M (S B^T)"),
     "dense_subsample": dict(m=65536, n=16384, k=64, d=2048, d_v=2048, sketch=1, zero_frac=0.7, noise=0.01,
                             desc="dense 65536x16384 planted (k=64), subsampling sketch d=d'=2048, PGD"),
     "dense_gaussian_8k": dict(m=8192, n=16384, k=64, d=2048, d_v=2048, sketch=0, zero_frac=0.7, noise=0.01,
@@ -60,6 +64,13 @@ WORKLOADS = {
                          "Gaussian d=max(4k,n/8), d'=max(4k,m/8), PGD, binary32"),
     "batched_small": dict(batched=True, count=64, m=0, n=0, k=0, d=0, d_v=0, sketch=0,
                           desc="64 uneven planted instances (same recipe), binary32"),
+    "dense_identity": dict(m=65536, n=16384, k=64, d=16384, d_v=65536, sketch=2, zero_frac=0.7, noise=0.01,
+                           desc="dense 65536x16384 planted (k=64), identity sketch (unsketched subproblem; "
+                                "with --solver rcd --alpha 0 --beta 0 this is HALS)"),
+    "compare": dict(compare=True, m=65536, n=16384, k=64, d=2048, d_v=2048, sketch=0, zero_frac=0.7, noise=0.01,
+                    eps=0.05, t_max=600,
+                    desc="dense 65536x16384 planted (k=64, 70% zero factors): iterations and time to rel. error "
+                         "0.05 of sketched and unsketched forms on the same kernels"),
     "small": dict(m=1000, n=800, k=10, d=100, d_v=100, sketch=0, zero_frac=0.0, noise=0.01,
                   desc="planted 1000x800, k=10, Gaussian d=100, PGD"),
 }
@@ -197,6 +208,7 @@ def oracle_sample(M, w, seed, rows_budget):
             B = (Y[S.J, :] * np.float64(S.scale)).T
         G = B @ B.T
         lam = method.lambda_max(G)
+        P = S.dense() @ B.T if w.get("order") == 1 else None  # reassociated order: P = S B^T in full
         t1 = time.perf_counter()
         if isinstance(M, tuple):
             import scipy.sparse as sp
@@ -204,8 +216,7 @@ def oracle_sample(M, w, seed, rows_budget):
             X = Msp[rows] if side == 0 else Msp[:, rows].T.tocsr()
         else:
             X = M[rows].astype(np.float64) if side == 0 else M[:, rows].T.astype(np.float64)
-        A = S.right_multiply(X)
-        R = A @ B.T
+        R = X @ P if P is not None else S.right_multiply(X) @ B.T
         Z = (U0 if side == 0 else V0)[rows]
         method.pgd_update(Z, G, R, 1.0 / (lam + mu))
         t2 = time.perf_counter()
@@ -281,15 +292,15 @@ def time_to_eps(pkg, torch, M, w, T, check_every, stream):
     path and for the bf16 form with its last 3 iterations in FP32; eps is the
     FP32 path's error after T iterations + 1e-3.  Times are CUDA-event sums of
     the steps alone (error evaluations excluded)."""
-    def trajectory(prec_plan):
+    def trajectory(prec_plan, order=0):
         h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=0, d_v=w["d_v"], solver=pkg.PGD,
-                       precision=prec_plan[0], use_graph=1)
+                       precision=prec_plan[0], use_graph=1, order=order)
         h.set_dense(M)
         errs, total_ms = [], 0.0
         for it in range(T):
             prec = prec_plan[1] if it >= T - 3 else prec_plan[0]
             if prec != prec_plan[0] and it == T - 3:
-                h.set_options(precision=prec)
+                h.set_options(precision=prec, order=0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             h.step(1)
@@ -303,7 +314,8 @@ def time_to_eps(pkg, torch, M, w, T, check_every, stream):
 
     fp32 = trajectory((pkg.FP32, pkg.FP32))
     eps = fp32[-1][2] + 1e-3
-    forms = {"bf16_closing_fp32": trajectory((pkg.BF16, pkg.FP32)), "fp8_closing_fp32": trajectory((pkg.FP8, pkg.FP32))}
+    forms = {"bf16_closing_fp32": trajectory((pkg.BF16, pkg.FP32)), "fp8_closing_fp32": trajectory((pkg.FP8, pkg.FP32)),
+             "bf16_reassociated_closing_fp32": trajectory((pkg.BF16, pkg.FP32), order=1)}
 
     def first_hit(tr):
         for it, ms, e in tr:
@@ -332,14 +344,16 @@ def run_ours(args, w):
     if ws > 1:
         dist.init_process_group("nccl")
     prec = {"fp32": pkg.FP32, "bf16": pkg.BF16, "fp8": pkg.FP8}[args.precision]
-    if w.get("sparse") or w["sketch"] != 0:
-        prec = pkg.FP32  # the tensor-core forms serve dense data with a Gaussian sketch
+    if w.get("sparse") or w["sketch"] == 1 or (w["sketch"] == 2 and prec == pkg.FP8):
+        prec = pkg.FP32  # the tensor-core forms serve dense data with a Gaussian (or, bf16, identity) sketch
     M = make_inputs(w, rank)
     # all library work and all timing events on one dedicated (non-default) stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=rank, d_v=w["d_v"], solver=pkg.PGD,
-                   precision=prec, use_graph=1)
+    order = w.get("order", 0)
+    solver = {"pgd": pkg.PGD, "rcd": pkg.RCD}[args.solver]
+    h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=rank, d_v=w["d_v"], solver=solver,
+                   precision=prec, use_graph=1, order=order, alpha=args.alpha, beta=args.beta)
     _set_data(h, M)
 
     for _ in range(args.warmup):
@@ -370,7 +384,22 @@ def run_ours(args, w):
     phases = [h.profile_half_step(0, reps=2), h.profile_half_step(1, reps=2)]
     peaks, peak_src = _peaks()
     m, n, d, d_v, k = w["m"], w["n"], w["d"], w["d_v"], w["k"]
-    if w["sketch"] == 0:
+    if (w["sketch"] == 0 and order == 1) or (w["sketch"] == 2 and not w.get("sparse")):
+        # reassociated order (R = X P) or identity sketch (R = X Y): the streaming
+        # product reads X once (bf16 or fp32) and the k x K factor, and writes R
+        eb = 2.0 if prec == pkg.BF16 else 4.0
+        bytes_ = [eb * (m * n + k * n) + 4.0 * m * k, eb * (n * m + k * m) + 4.0 * n * k]
+        flops = [2.0 * m * n * k, 2.0 * n * m * k]
+        prod_ms = [p["rhs"] for p in phases]
+        if prec == pkg.BF16:
+            achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
+            bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "tc_skinny"
+            peak_note = "hbm_gbs of %s" % peak_src
+        else:
+            achieved = sum(flops) / (sum(prod_ms) / 1000.0) / 1e12
+            bound, peak, unit, kernel_key = "alu", FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "sgemm_simt"
+            peak_note = "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
+    elif w["sketch"] == 0:
         flops = [2.0 * m * n * d, 2.0 * n * m * d_v]
         if prec != pkg.FP32:
             flops = [f + 2.0 * m * d * k for f in flops]  # R = A B^T is fused into the same kernel
@@ -410,7 +439,8 @@ def run_ours(args, w):
             torch.from_numpy(M).pin_memory()
         Uh = torch.empty((m, k), dtype=torch.float32).pin_memory()
         Vh = torch.empty((n, k), dtype=torch.float32).pin_memory()
-        he = pkg.DSANLS(m, n, k, d, w["sketch"], seed=rank, d_v=d_v, solver=pkg.PGD, precision=prec, use_graph=1)
+        he = pkg.DSANLS(m, n, k, d, w["sketch"], seed=rank, d_v=d_v, solver=solver, precision=prec, use_graph=1,
+                        order=order, alpha=args.alpha, beta=args.beta)
 
         def e2e_step():
             _set_data(he, Mp)
@@ -449,7 +479,8 @@ def run_ours(args, w):
             "vs_baseline": None, "dtype": {pkg.FP32: "f32", pkg.BF16: "bf16", pkg.FP8: "e4m3"}[prec],
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "k": k, "d": d, "d_v": d_v,
-                       "precision": {pkg.FP32: "fp32", pkg.BF16: "bf16", pkg.FP8: "fp8"}[prec], "solver": "pgd", "graph": True, "replicas": ws,
+                       "precision": {pkg.FP32: "fp32", pkg.BF16: "bf16", pkg.FP8: "fp8"}[prec], "solver": args.solver, "alpha": args.alpha, "beta": args.beta, "graph": True, "replicas": ws,
+                       "order": ["paper", "reassociated"][order],
                        "l2": "inputs larger than L2 (M is %.1f GB)" % (_input_bytes(M) / 1e9)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "phases_ms": {"U": {k_: round(v_, 4) for k_, v_ in phases[0].items()},
@@ -470,15 +501,24 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense_gaussian")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="bf16")
+    ap.add_argument("--order", choices=["paper", "reassociated"], default=None,
+                    help="order of R = M S B^T for Gaussian sketches (default: the workload's)")
+    ap.add_argument("--solver", choices=["pgd", "rcd"], default="pgd")
+    ap.add_argument("--alpha", type=float, default=1.0, help="mu_t = alpha + beta t")
+    ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned workload")
     ap.add_argument("--time-to-eps", type=int, default=100,
                     help="also run T outer iterations of the fp32 and bf16 forms and report time to eps")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.order is not None:
+        w["order"] = ["paper", "reassociated"].index(args.order)
     if w.get("learned"):
         run_learned(args, w)
+    elif w.get("compare"):
+        run_compare(args, w)
     elif w.get("batched"):
         run_batch(args, w)
     elif args.impl == "reference":
@@ -595,6 +635,64 @@ def run_learned(args, w):
         "speedup_time_to_eps_vs_fp32": (base["seconds"] / best["seconds"]) if (base and best) else None,
     }), flush=True)
     net.close()
+
+
+def run_compare(args, w):
+    """Sketched and unsketched forms of the method on one dense planted problem
+    (the same kernels): outer iterations and CUDA-event time of the steps
+    until the relative error (checked after every iteration) reaches eps.
+    Gaussian / subsampling sketches with PGD and RCD (Section 3.5), the
+    identity sketch with PGD (plain projected gradient ANLS) and with RCD at
+    mu = 0 (HALS), bf16 and fp32 where the form allows it."""
+    import torch
+    import paper_2009_02845_gb300 as pkg
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    m, n, k, d = w["m"], w["n"], w["k"], w["d"]
+    M = make_inputs(w, rank)
+    G_, S_, I_ = pkg.GAUSSIAN, pkg.SUBSAMPLE, pkg.IDENTITY
+    forms = [
+        # name, sketch, d, d_v, solver, precision, order, alpha, beta
+        ("sanls_gaussian_pgd_bf16", G_, d, d, pkg.PGD, pkg.BF16, 0, 1.0, 1.0),
+        ("sanls_gaussian_pgd_bf16_reassociated", G_, d, d, pkg.PGD, pkg.BF16, 1, 1.0, 1.0),
+        ("sanls_gaussian_rcd_bf16_reassociated", G_, d, d, pkg.RCD, pkg.BF16, 1, 1.0, 1.0),
+        ("sanls_subsample_pgd_fp32", S_, d, d, pkg.PGD, pkg.FP32, 0, 1.0, 1.0),
+        ("sanls_subsample_rcd_fp32", S_, d, d, pkg.RCD, pkg.FP32, 0, 1.0, 1.0),
+        ("plain_pg_bf16", I_, n, m, pkg.PGD, pkg.BF16, 0, 1.0, 1.0),
+        ("hals_bf16", I_, n, m, pkg.RCD, pkg.BF16, 0, 0.0, 0.0),
+        ("hals_fp32", I_, n, m, pkg.RCD, pkg.FP32, 0, 0.0, 0.0),
+    ]
+    res = {}
+    for name, sk, dd, ddv, solver, prec, order, alpha, beta in forms:
+        h = pkg.DSANLS(m, n, k, dd, sk, seed=0, d_v=ddv, solver=solver, precision=prec, use_graph=1, order=order,
+                       alpha=alpha, beta=beta)
+        h.set_dense(M)
+        total, hit, err = 0.0, None, None
+        for it in range(w["t_max"]):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            err = h.rel_error()
+            if err <= w["eps"]:
+                hit = {"iters": it + 1, "seconds": total / 1000.0, "err": err}
+                break
+        h.close()
+        res[name] = {"to_eps": hit, "iters_run": it + 1, "final_err": err, "ms_per_iter": total / (it + 1)}
+        print(json.dumps({"form": name, **res[name]}), file=sys.stderr, flush=True)
+    best = min((r["to_eps"]["seconds"] for r in res.values() if r["to_eps"]), default=None)
+    print(json.dumps({
+        "metric": METRIC, "value": (1.0 / best) if best else 0.0, "unit": "1/time_to_eps (1/s), fastest form",
+        "n_gpus": ws, "steps": w["t_max"], "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "k": k, "d": d, "eps": w["eps"],
+                   "t_max": w["t_max"]},
+        "results": res,
+    }), flush=True)
 
 
 def _batch_inputs(count):

@@ -54,6 +54,11 @@ extern "C" {
 #define DSANLS_SKETCH_GAUSSIAN 0   /* i.i.d. N(0, 1/d) entries                       */
 #define DSANLS_SKETCH_SUBSAMPLE 1  /* d columns sqrt(n/d) e_i, drawn w/o replacement */
 #define DSANLS_SKETCH_IDENTITY 2   /* S = I (needs d = n and d_v = m)                */
+#define DSANLS_SKETCH_RADEMACHER 3 /* i.i.d. +-1/sqrt(d) entries: the sign is the top
+                                      bit of the entry's Philox word (one of Section
+                                      3.4's other random matrices; E[S S^T] = I).
+                                      Accepted wherever GAUSSIAN is (all orders and
+                                      precisions; not by the batched form)         */
 
 /* ---- subproblem solvers (Section 3.5) -------------------------------- */
 #define DSANLS_SOLVER_PGD 0   /* one projected gradient step, eq. gradient_descent */
@@ -65,6 +70,16 @@ extern "C" {
 #define DSANLS_PREC_FP8 2     /* fp8 E4M3 M (one scale per 128-row block) and S
                                  (entries N(0,1), 1/sqrt(d) applied to the fp32
                                  accumulator); B = Y^T S and R = A B^T in bf16   */
+
+/* ---- order of the Gaussian right-hand side R = M S B^T ----------------- */
+#define DSANLS_ORDER_PAPER 0  /* R = (M S) B^T: A = M S first (eq. def_A_B), then
+                                 A B^T (eq. gradient_descent); 2 rows K d flops   */
+#define DSANLS_ORDER_REASSOCIATED 1
+                              /* R = M (S B^T): P = S B^T (K x k) first, then
+                                 M P; 2 K d k + 2 rows K k flops.  Equal in exact
+                                 arithmetic (associativity), rounded differently;
+                                 Gaussian sketch with FP32 (dense or sparse M) or
+                                 BF16 (dense M: S, B and P rounded to bf16)      */
 
 /* ---- Philox field streams (counter word 3, low byte) ------------------ */
 #define DSANLS_STREAM_SKETCH_U 0
@@ -82,6 +97,7 @@ typedef struct dsanls_options {
     int64_t t;             /* iteration index of the next outer iteration; default 0 */
     int32_t bound_clamp;   /* 1: clamp entries at sqrt(2 ||M||_F) (eq. extra_con)    */
     int32_t use_graph;     /* 1: replay each outer iteration as a CUDA graph         */
+    int32_t order;         /* DSANLS_ORDER_*; default PAPER                          */
     void *stream;          /* cudaStream_t for all work; NULL = the handle's own     */
 } dsanls_options;
 
@@ -101,8 +117,12 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
 
 int dsanls_get_options(dsanls_t h, dsanls_options *opt);
 /* Validates and applies options; d_v follows the same rules as d for the
- * V-half (against m).  BF16 and FP8 need dense data and a Gaussian sketch;
- * BF16 needs m, n, d, d_v multiples of 8, FP8 m and n multiples of 16. */
+ * V-half (against m).  BF16 needs dense data and a Gaussian or identity
+ * sketch (identity: R = M V from bf16 operands, the unsketched subproblem),
+ * FP8 dense data and a Gaussian sketch; BF16 needs m, n, d, d_v multiples of
+ * 8, FP8 m and n multiples of 16.
+ * ORDER_REASSOCIATED needs a Gaussian sketch and FP32 or BF16 (EINVAL with
+ * FP8 or another sketch kind). */
 int dsanls_set_options(dsanls_t h, const dsanls_options *opt);
 
 /* Dense M: m rows of n binary32 values, row stride ld >= n (elements).  The
@@ -190,6 +210,14 @@ int dsanls_philox_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t r
 int dsanls_gaussian_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,
                           int64_t cols, float scale, int32_t transposed, float *out,
                           void *stream);
+
+/* Rademacher sketch entries S[i][j] = (top bit of w(i, j) set ? -scale :
+ * +scale), w the entry's field word (same counter layout as above); the
+ * +-1/sqrt(d) matrix of DSANLS_SKETCH_RADEMACHER with scale = 1/sqrt(d).
+ * transposed as above. */
+int dsanls_rademacher_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,
+                            int64_t cols, float scale, int32_t transposed, float *out,
+                            void *stream);
 
 /* Uniform [0,1) field X[i][j] = (w >> 8) * 2^-24, row-major rows x cols. */
 int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,

@@ -31,6 +31,8 @@ from . import rng
 GAUSSIAN = 0
 SUBSAMPLE = 1
 IDENTITY = 2
+RADEMACHER = 3
+DENSE_KINDS = (GAUSSIAN, RADEMACHER)
 
 PGD = 0
 RCD = 1
@@ -40,9 +42,11 @@ SIDE_V = 1
 
 
 class Sketch:
-    """The random matrix S^t (n x d) of Section 3.4, in one of three kinds.
+    """The random matrix S^t (n x d) of Section 3.4, in one of four kinds.
 
     kind GAUSSIAN: dense, entries N(0, 1/d) from the Philox field.
+    kind RADEMACHER: dense, entries +-1/sqrt(d) with the sign of the entry's
+        Philox word (one of Section 3.4's "other choices" of random matrix).
     kind SUBSAMPLE: columns sqrt(n/d) e_{J_p}, J drawn without replacement.
     kind IDENTITY: S = I (requires d = n); the unsketched subproblem.
     """
@@ -54,6 +58,9 @@ class Sketch:
         if kind == GAUSSIAN:
             self.scale = rng.gaussian_scale(d)
             self.dense32 = rng.gaussian_field(seed, side, t, n, d, self.scale)
+        elif kind == RADEMACHER:
+            self.scale = rng.gaussian_scale(d)
+            self.dense32 = rng.rademacher_field(seed, side, t, n, d, self.scale)
         elif kind == SUBSAMPLE:
             if d > n:
                 raise ValueError("subsampling needs d <= n")
@@ -67,7 +74,7 @@ class Sketch:
 
     def dense(self):
         """S as an n x d FP64 array."""
-        if self.kind == GAUSSIAN:
+        if self.kind in DENSE_KINDS:
             return self.dense32.astype(np.float64)
         S = np.zeros((self.n, self.d))
         if self.kind == SUBSAMPLE:
@@ -78,7 +85,7 @@ class Sketch:
 
     def right_multiply(self, X):
         """X S for X with n columns (dense ndarray or scipy sparse)."""
-        if self.kind == GAUSSIAN:
+        if self.kind in DENSE_KINDS:
             out = X @ self.dense32.astype(np.float64)
         elif self.kind == SUBSAMPLE:
             out = X[:, self.J] * np.float64(self.scale)
@@ -131,7 +138,11 @@ def sketched_terms_bf16(X, Y, S):
     """The sketched terms of the reduced-precision form: the operands X, Y and
     S rounded to bf16, products accumulated exactly; A = X S and B = Y^T S
     rounded to bf16 again where they enter R = A B^T; G = B B^T from the
-    unrounded B."""
+    unrounded B.  For S = I: R = X Y from bf16 X and Y, G = Y^T Y from the
+    unrounded Y (A is not formed)."""
+    if S.kind == IDENTITY:
+        Y = np.asarray(Y, dtype=np.float64)
+        return None, Y.T.copy(), Y.T @ Y, round_bf16(X) @ round_bf16(Y)
     Sb = round_bf16(S.dense32)
     A = round_bf16(round_bf16(X) @ Sb)
     B = round_bf16(Y).T @ Sb
@@ -172,7 +183,8 @@ def sketched_terms_fp8(X, Y, S, seed, t, side):
     E4M3, the unit-variance draws z of S to E4M3, A = (Xq zq) / sqrt(d)
     rounded to bf16 where it enters R; B = Y^T S from bf16 operands as in the
     bf16 form."""
-    z = rng.gaussian_field(seed, side, t, S.n, S.d, np.float32(1.0))
+    unit = rng.rademacher_field if S.kind == RADEMACHER else rng.gaussian_field
+    z = unit(seed, side, t, S.n, S.d, np.float32(1.0))
     A = round_bf16((quantise_rowblocks_e4m3(X) @ round_e4m3(z)) * np.float64(S.scale))
     Sb = round_bf16(S.dense32)
     B = round_bf16(Y).T @ Sb

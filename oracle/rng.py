@@ -127,6 +127,14 @@ def gaussian_field(seed, stream, t, rows, cols, scale):
     return out
 
 
+def rademacher_field(seed, stream, t, rows, cols, scale):
+    """rows x cols binary32 field of +-scale: the sign is the top bit of the
+    entry's Philox word (set bit: -scale)."""
+    w = field_words(seed, stream, t, rows, cols)
+    sc = np.float32(scale)
+    return np.where((w >> np.uint32(31)) != 0, -sc, sc).astype(np.float32)
+
+
 def uniform_field(seed, stream, t, rows, cols):
     out = np.empty((rows, cols), dtype=np.float32)
     lib().ora_uniform_field(seed, stream, t, rows, cols, _ptr(out, ctypes.c_float))

@@ -51,6 +51,9 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
+// Gaussian and Rademacher sketches are dense matrices drawn from the field
+bool dense_kind(int kind) { return kind == DSANLS_SKETCH_GAUSSIAN || kind == DSANLS_SKETCH_RADEMACHER; }
+
 int kp_bucket(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 64 ? 64 : 128)); }
 
 constexpr int MAX_SPLITS = 32;
@@ -82,7 +85,7 @@ struct dsanls_ctx {
     float *U = nullptr, *V = nullptr;
 
     // workspaces (sized by prepare())
-    int64_t cfg_key[6] = {-1, -1, -1, -1, -1, -1};
+    int64_t cfg_key[7] = {-1, -1, -1, -1, -1, -1, -1};
     float *S = nullptr;
     __nv_bfloat16 *Sb = nullptr;
     int32_t *J = nullptr;
@@ -95,6 +98,11 @@ struct dsanls_ctx {
     uint8_t *Mq = nullptr, *MTq = nullptr, *Sq = nullptr;  // fp8 E4M3 forms (FP8 precision)
     float *qscale[2] = {nullptr, nullptr};                  // per 128-row block scales of M, M^T
     float *Bpart = nullptr;        // split-K slices of that product
+    // reassociated order: P = S B^T (K x k fp32, FP32 form); bf16 S (K x d), bf16 B,
+    // bf16 P^T (k x K) and the split-K partials of P^T and of R (BF16 form)
+    float *P = nullptr;
+    __nv_bfloat16 *Sn = nullptr, *Bb = nullptr, *Ptb = nullptr;
+    float *Ppart = nullptr, *Rpart2 = nullptr;
     double *G64[2] = {nullptr, nullptr};
     double *scal[2] = {nullptr, nullptr};
     float *Gf = nullptr;
@@ -183,28 +191,41 @@ int d_v_of(const dsanls_ctx *h) { return h->opt.d_v > 0 ? h->opt.d_v : h->d; }
 // (Re)allocate the per-configuration workspaces.
 void prepare(dsanls_ctx *h) {
     const int dv = d_v_of(h);
-    const int64_t key[6] = {h->sketch, h->d, dv, h->opt.precision, h->has_dense ? 1 : 0, h->has_sparse ? 1 : 0};
-    if (std::equal(key, key + 6, h->cfg_key)) return;
+    const int64_t key[7] = {h->sketch, h->d, dv, h->opt.precision, h->has_dense ? 1 : 0, h->has_sparse ? 1 : 0,
+                            h->opt.order};
+    if (std::equal(key, key + 7, h->cfg_key)) return;
     invalidate_graph(h);
     const int64_t m = h->m, n = h->n, k = h->k;
     const int64_t dmax = std::max<int64_t>(h->d, dv);
-    const bool gauss = h->sketch == DSANLS_SKETCH_GAUSSIAN;
+    const bool gauss = dense_kind(h->sketch);  // Gaussian or Rademacher: dense S
     const bool ident = h->sketch == DSANLS_SKETCH_IDENTITY;
     const bool fp8 = h->opt.precision == DSANLS_PREC_FP8;
     const bool bf16 = h->opt.precision == DSANLS_PREC_BF16 || fp8;  // fp8 keeps bf16 S^T for B = Y^T S
+    const bool reas = gauss && h->opt.order == DSANLS_ORDER_REASSOCIATED;
+    // identity sketch in bf16: R = X Y on the streaming tensor-core product
+    const bool ident_tc = ident && h->opt.precision == DSANLS_PREC_BF16 && h->has_dense;
+    const int64_t kmax = std::max(m, n);
     dalloc(h->S, (gauss && !bf16) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->Sb, (gauss && bf16) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->J, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? dmax : 0);
-    dalloc(h->A, (gauss && !bf16) ? std::max(m * h->d, n * dv) : 0);
+    dalloc(h->A, (gauss && !bf16 && !reas) ? std::max(m * h->d, n * dv) : 0);
+    dalloc(h->P, (reas && !bf16) ? kmax * k : 0);
+    dalloc(h->Sn, (reas && bf16) ? std::max(n * h->d, m * dv) : 0);
+    dalloc(h->Bb, (reas && bf16) ? k * dmax : 0);
+    dalloc(h->Ptb, (reas && bf16) ? k * kmax : 0);
+    dalloc(h->Ppart, (reas && bf16) ? std::max(tc_gemm_bf16out_part_elems(k, h->d, n),
+                                               tc_gemm_bf16out_part_elems(k, dv, m)) : 0);
+    dalloc(h->Rpart2, ((reas && bf16) || ident_tc)
+                          ? std::max(tc_skinny_part_elems(m, n, k), tc_skinny_part_elems(n, m, k)) : 0);
     dalloc(h->W, k * (ident ? std::max(m, n) : dmax));
     dalloc(h->Wpart, (gauss && !bf16) ? (int64_t)MAX_SPLITS * k * dmax : 0);
-    dalloc(h->Ytb, (gauss && bf16) ? k * std::max(m, n) : 0);
+    dalloc(h->Ytb, ((gauss && bf16) || ident_tc) ? k * std::max(m, n) : 0);
     dalloc(h->Bpart, (gauss && bf16) ? tc_gemm_part_elems(k, dmax) : 0);
     dalloc(h->R, std::max(m, n) * k);
-    dalloc(h->Rpart, (gauss && bf16) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
+    dalloc(h->Rpart, (gauss && bf16 && !reas) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
     dalloc(h->Sq, (gauss && fp8) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->bits, (h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE) ? ceil_div(std::max(m, n), 32) + 1 : 0);
-    std::copy(key, key + 6, h->cfg_key);
+    std::copy(key, key + 7, h->cfg_key);
 }
 
 // ---------------------------------------------------------------------------
@@ -236,19 +257,26 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     int64_t gram_d = dd;
 
     mark(pe, DSANLS_PHASE_SKETCH, s);
-    if (h->sketch == DSANLS_SKETCH_GAUSSIAN) {
+    if (dense_kind(h->sketch)) {
+        const bool rade = h->sketch == DSANLS_SKETCH_RADEMACHER;
         const float scale = (float)(1.0 / std::sqrt((double)dd));
         const bool fp8 = dense && h->opt.precision == DSANLS_PREC_FP8;
         const bool tc = dense && (h->opt.precision == DSANLS_PREC_BF16 || fp8);
+        const bool reas = h->opt.order == DSANLS_ORDER_REASSOCIATED;
+        const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
         // S (K x dd), N(0, 1/dd) entries of the field, stream `side`: fp32 S for the
         // CUDA-core form, bf16 S^T (K-major operand) for the tensor-core forms, and
-        // for the fp8 form also fp8 S^T of the unit-variance draws
+        // for the fp8 form also fp8 S^T of the unit-variance draws; the reassociated
+        // bf16 form also keeps bf16 S (d-major operand of P^T = B S^T)
         if (fp8)
-            launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, s);
+            launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, rade, s);
+        else if (tc && reas)
+            launch_gaussian_pair(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sn, rade, s);
         else if (tc)
-            launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, s);
+            launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, rade,
+                                                 s);
         else
-            launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, s);
+            launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, rade, s);
         mark(pe, DSANLS_PHASE_B, s);
         if (tc) {
             // B = Y^T S (k x dd) on tensor cores from bf16 Y^T and S^T, split-K
@@ -268,13 +296,38 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             launch_split_reduce(h->Wpart, (int64_t)k * dd, splits, k, dd, dd, h->W, dd, s);
         }
         mark(pe, DSANLS_PHASE_PRODUCT, s);
-        if (tc) {
+        if (reas) {
+            // P = S B^T (K x k), then R = X P: 2 K dd k + 2 rows K k flops
+            if (tc) {
+                launch_copy_cast_bf16(h->W, (int64_t)k * dd, h->Bb, s);
+                launch_tc_gemm_bf16out(h->Bb, h->Sn, k, dd, K, h->Ppart, h->Ptb, h->flag, s);
+            } else {
+                GemmArgs g{};
+                g.M = K; g.N = k; g.K = dd;
+                g.A = h->S; g.lda = dd; g.a_kcontig = true;
+                g.B = h->W; g.ldb = dd; g.b_kcontig = true;
+                g.C = h->P; g.ldc = k; g.alpha = 1.0f; g.splits = 1;
+                launch_sgemm(g, s);
+            }
+            mark(pe, DSANLS_PHASE_RHS, s);
+            if (tc) {
+                launch_tc_skinny(Xb, h->Ptb, rows, K, k, h->Rpart2, h->R, h->flag, s);
+            } else if (dense) {
+                GemmArgs g{};
+                g.M = rows; g.N = k; g.K = K;
+                g.A = X; g.lda = K; g.a_kcontig = true;
+                g.B = h->P; g.ldb = k; g.b_kcontig = false;
+                g.C = h->R; g.ldc = k; g.alpha = 1.0f; g.splits = 1;
+                launch_sgemm(g, s);
+            } else {
+                launch_spmm_rows(xp, xc, xv, rows, h->P, k, k, 1.0f, h->R, k, s);
+            }
+        } else if (tc) {
             // R = (X S) B^T on tcgen05, X and S in bf16, A never stored
             if (fp8) {
                 launch_tc_sketch_rhs_fp8(side == 0 ? h->Mq : h->MTq, h->qscale[side], h->Sq, scale, h->W, rows, K, dd,
                                          k, h->Rpart, h->R, h->flag, s);
             } else {
-                const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
                 launch_tc_sketch_rhs(Xb, h->Sb, h->W, rows, K, dd, k, h->Rpart, h->R, h->flag, s);
             }
             mark(pe, DSANLS_PHASE_RHS, s);
@@ -322,7 +375,11 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         gram_d = K;
         mark(pe, DSANLS_PHASE_PRODUCT, s);
         mark(pe, DSANLS_PHASE_RHS, s);
-        if (dense) {
+        if (dense && h->opt.precision == DSANLS_PREC_BF16) {
+            // R = X Y on the streaming tensor-core product from bf16 X and bf16 Y^T
+            launch_transpose_bf16(Y, K, k, h->Ytb, s);
+            launch_tc_skinny(side == 0 ? h->Mb : h->MTb, h->Ytb, rows, K, k, h->Rpart2, h->R, h->flag, s);
+        } else if (dense) {
             GemmArgs g{};
             g.M = rows; g.N = k; g.K = K;
             g.A = X; g.lda = K; g.a_kcontig = true;
@@ -479,6 +536,7 @@ int dsanls_default_options(dsanls_options *opt) {
     opt->t = 0;
     opt->bound_clamp = 0;
     opt->use_graph = 0;
+    opt->order = DSANLS_ORDER_PAPER;
     opt->stream = nullptr;
     return DSANLS_OK;
 }
@@ -488,7 +546,7 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
     *out = nullptr;
     if (m < 1 || n < 1 || k < 1 || k > 128 || d < 1) return DSANLS_EINVAL;
     if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return DSANLS_EINVAL;
-    if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_IDENTITY) return DSANLS_EINVAL;
+    if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_RADEMACHER) return DSANLS_EINVAL;
     if (sketch_kind == DSANLS_SKETCH_SUBSAMPLE && (d > n || d > 16384)) return DSANLS_EINVAL;
     if (sketch_kind == DSANLS_SKETCH_IDENTITY && d != n) return DSANLS_EINVAL;
     dsanls_ctx *h = nullptr;
@@ -550,17 +608,21 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
         if (opt->solver != DSANLS_SOLVER_PGD && opt->solver != DSANLS_SOLVER_RCD) throw ArgError{"unknown solver"};
         if (opt->precision < DSANLS_PREC_FP32 || opt->precision > DSANLS_PREC_FP8) throw ArgError{"unknown precision"};
         if (opt->precision == DSANLS_PREC_FP8 &&
-            (h->has_sparse || h->sketch != DSANLS_SKETCH_GAUSSIAN || h->m % 16 || h->n % 16 ||
+            (h->has_sparse || !dense_kind(h->sketch) || h->m % 16 || h->n % 16 ||
              h->d % 8 || (opt->d_v > 0 ? opt->d_v : h->d) % 8))
             throw ArgError{"FP8 precision needs dense data, a Gaussian sketch, m and n multiples of 16, d and d_v of 8"};
         if (opt->precision == DSANLS_PREC_BF16 &&
-            (h->has_sparse || h->sketch != DSANLS_SKETCH_GAUSSIAN || !tc_supported(h->k)))
-            throw ArgError{"BF16 precision needs dense data and a Gaussian sketch"};
+            (h->has_sparse || h->sketch == DSANLS_SKETCH_SUBSAMPLE || !tc_supported(h->k)))
+            throw ArgError{"BF16 precision needs dense data and a Gaussian or identity sketch"};
         if (opt->precision == DSANLS_PREC_BF16) {
             const int dv = opt->d_v > 0 ? opt->d_v : h->d;
             if (h->m % 8 || h->n % 8 || h->d % 8 || dv % 8)
                 throw ArgError{"BF16 precision needs m, n, d and d_v multiples of 8 (16-byte TMA rows)"};
         }
+        if (opt->order != DSANLS_ORDER_PAPER && opt->order != DSANLS_ORDER_REASSOCIATED) throw ArgError{"unknown order"};
+        if (opt->order == DSANLS_ORDER_REASSOCIATED &&
+            (!dense_kind(h->sketch) || opt->precision == DSANLS_PREC_FP8))
+            throw ArgError{"the reassociated order needs a Gaussian sketch and FP32 or BF16 precision"};
         if (opt->power_iters < 0 || opt->power_iters > 10000) throw ArgError{"power_iters out of range"};
         if (!(opt->alpha >= 0.0) || !(opt->beta >= 0.0) || !std::isfinite(opt->alpha) || !std::isfinite(opt->beta))
             throw ArgError{"alpha and beta must be finite and >= 0"};
@@ -571,7 +633,7 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
                                 (opt->stream != h->opt.stream) || (opt->solver != h->opt.solver) ||
                                 (opt->power_iters != h->opt.power_iters) || (opt->alpha != h->opt.alpha) ||
                                 (opt->beta != h->opt.beta) || (opt->bound_clamp != h->opt.bound_clamp) ||
-                                (opt->use_graph != h->opt.use_graph);
+                                (opt->use_graph != h->opt.use_graph) || (opt->order != h->opt.order);
         // finish work queued on the old stream before switching
         DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
         h->opt = *opt;
@@ -930,6 +992,7 @@ void dsanls_destroy(dsanls_t h) {
         dfree(h->U); dfree(h->V);
         dfree(h->S); dfree(h->Sb); dfree(h->J); dfree(h->A); dfree(h->W); dfree(h->Wpart); dfree(h->R);
         dfree(h->Rpart); dfree(h->Ytb); dfree(h->Bpart);
+        dfree(h->P); dfree(h->Sn); dfree(h->Bb); dfree(h->Ptb); dfree(h->Ppart); dfree(h->Rpart2);
         dfree(h->Mq); dfree(h->MTq); dfree(h->Sq); dfree(h->qscale[0]); dfree(h->qscale[1]);
         for (int side = 0; side < 2; ++side) {
             dfree(h->G64[side]);
@@ -960,7 +1023,18 @@ int dsanls_gaussian_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t
     if (rows < 0 || cols < 0 || rows > (1ll << 34) || cols > (1ll << 31) - 1) return DSANLS_EINVAL;
     if (rows * cols > 0 && !out) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
-        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out,
+        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out, false,
+                                     (cudaStream_t)stream);
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_rademacher_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows, int64_t cols, float scale,
+                            int32_t transposed, float *out, void *stream) {
+    if (rows < 0 || cols < 0 || rows > (1ll << 34) || cols > (1ll << 31) - 1) return DSANLS_EINVAL;
+    if (rows * cols > 0 && !out) return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out, true,
                                      (cudaStream_t)stream);
         return DSANLS_OK;
     });

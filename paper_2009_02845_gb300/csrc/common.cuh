@@ -130,6 +130,24 @@ DSANLS_DEV void gaussian4(uint64_t seed, uint32_t stream_id, uint64_t t, uint32_
     box_muller(b.z, b.w, z[2], z[3]);
 }
 
+// Rademacher draws: +-1 with the sign of each word's top bit (set: -1).
+DSANLS_DEV void rademacher4(uint64_t seed, uint32_t stream_id, uint64_t t, uint32_t row4, uint32_t col, float z[4]) {
+    const Philox4 b = field_block(seed, stream_id, t, row4, col);
+    z[0] = (b.x >> 31) ? -1.0f : 1.0f;
+    z[1] = (b.y >> 31) ? -1.0f : 1.0f;
+    z[2] = (b.z >> 31) ? -1.0f : 1.0f;
+    z[3] = (b.w >> 31) ? -1.0f : 1.0f;
+}
+
+// Unit-variance draws of the dense sketch kinds for one Philox block.
+template <bool RADE>
+DSANLS_DEV void unit_draw4(uint64_t seed, uint32_t stream_id, uint64_t t, uint32_t row4, uint32_t col, float z[4]) {
+    if (RADE)
+        rademacher4(seed, stream_id, t, row4, col, z);
+    else
+        gaussian4(seed, stream_id, t, row4, col, z);
+}
+
 // ---------------------------------------------------------------------------
 // host-side helpers
 // ---------------------------------------------------------------------------

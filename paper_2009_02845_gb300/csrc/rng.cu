@@ -1,8 +1,9 @@
 // Random sketches S^t, S'^t and default initial factors (Section 3.4;
 // shared-seed regeneration of Section 3.3).
 //
-//  * field words, Gaussian and uniform fields: one thread per Philox block
-//    (four consecutive rows of one column).  The Gaussian field can be
+//  * field words, Gaussian, Rademacher and uniform fields: one thread per
+//    Philox block (four consecutive rows of one column).  The dense sketch
+//    fields (Gaussian: Box-Muller; Rademacher: the sign of each word) can be
 //    written as S (rows x cols) or S^T (cols x rows); the transposed form puts
 //    the four values of a block next to each other (one 16-byte store).
 //  * subsampling: d indices pi(0..d-1) of a keyed 4-round Feistel permutation
@@ -32,7 +33,7 @@ __global__ void k_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t r
 }
 
 // t is read from device memory when t_dev != nullptr (graph replays).
-template <bool TRANSPOSED, typename OutT>
+template <bool TRANSPOSED, typename OutT, bool RADE>
 __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, const int64_t *t_dev,
                                  int64_t rows, int64_t cols, float scale, OutT *out) {
     const int64_t nb4 = (rows + 3) >> 2;
@@ -48,7 +49,7 @@ __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, c
         q = idx / cols;
     }
     float z[4];
-    gaussian4(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+    unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
 #pragma unroll
     for (int r = 0; r < 4; ++r) z[r] = __fmul_rn(z[r], scale);
     const int64_t i0 = 4 * q;
@@ -69,6 +70,7 @@ __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, c
 }
 
 // S^T in two forms at once (cols x rows): bf16 of z * scale and fp8 E4M3 of z.
+template <bool RADE>
 __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols,
                                 float scale, __nv_bfloat16 *out_b, __nv_fp8_e4m3 *out_q) {
     const int64_t nb4 = (rows + 3) >> 2;
@@ -77,7 +79,7 @@ __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_de
     const uint64_t t = (uint64_t)*t_dev;
     const int64_t q = idx % nb4, j = idx / nb4;
     float z[4];
-    gaussian4(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+    unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
     const int64_t i0 = 4 * q;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -88,12 +90,74 @@ __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_de
     }
 }
 
+// bf16 S (rows x cols) and S^T (cols x rows) of z * scale at once, for the
+// reassociated order (S^T feeds B = Y^T S, S feeds P = S B^T).  One CTA per
+// tile of 128 rows x 64 columns; a warp walks 32 Philox blocks (four rows of
+// one column each).  S^T: each thread stores its four values as one 8-byte
+// word, a warp 256 contiguous bytes.  S: the values go through a shared tile
+// kept column by column (8-byte stores, conflict-free) and leave it row by
+// row, 128 contiguous bytes per tile row.
+constexpr int PAIR_ROWS = 128, PAIR_COLS = 64, PAIR_LD = PAIR_ROWS + 4;  // 264-byte rows
+
+template <bool RADE>
+__global__ void __launch_bounds__(256)
+    k_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
+                    __nv_bfloat16 *__restrict__ out_t, __nv_bfloat16 *__restrict__ out_n) {
+    __shared__ __align__(16) __nv_bfloat16 tile[PAIR_COLS][PAIR_LD];
+    const uint64_t t = (uint64_t)*t_dev;
+    const int64_t r0 = (int64_t)blockIdx.y * PAIR_ROWS, c0 = (int64_t)blockIdx.x * PAIR_COLS;
+    const int qi = threadIdx.x & 31, cj = threadIdx.x >> 5;
+    const int64_t q = (r0 >> 2) + qi;
+    const bool vec = (rows & 3) == 0;
+    for (int cc = cj; cc < PAIR_COLS; cc += 8) {
+        const int64_t j = c0 + cc;
+        if (j >= cols || 4 * q >= rows) continue;
+        float z[4];
+        unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+        __nv_bfloat16 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = __float2bfloat16_rn(__fmul_rn(z[r], scale));
+        const uint2 w = make_uint2((uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16),
+                                   (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16));
+        *reinterpret_cast<uint2 *>(&tile[cc][4 * qi]) = w;
+        if (vec) {
+            *reinterpret_cast<uint2 *>(out_t + j * rows + 4 * q) = w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (4 * q + r < rows) out_t[j * rows + 4 * q + r] = v[r];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PAIR_ROWS * PAIR_COLS; e += blockDim.x) {
+        const int rr = e / PAIR_COLS, cc = e % PAIR_COLS;
+        const int64_t i = r0 + rr, j = c0 + cc;
+        if (i < rows && j < cols) out_n[i * cols + j] = tile[cc][rr];
+    }
+}
+
+void launch_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
+                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, bool rademacher, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    if (ceil_div(rows, PAIR_ROWS) > 65535) throw ArgError{"launch_gaussian_pair: too many rows"};
+    dim3 grid((unsigned)ceil_div(cols, PAIR_COLS), (unsigned)ceil_div(rows, PAIR_ROWS));
+    if (rademacher)
+        k_gaussian_pair<true><<<grid, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
+    else
+        k_gaussian_pair<false><<<grid, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
+    DSANLS_LAUNCH_CHECK();
+}
+
 void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_b, uint8_t *out_q, cudaStream_t s) {
+                          __nv_bfloat16 *out_b, uint8_t *out_q, bool rademacher, cudaStream_t s) {
     const int64_t total = ((rows + 3) >> 2) * cols;
     if (total == 0) return;
-    k_gaussian_dual<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b,
-                                                                   reinterpret_cast<__nv_fp8_e4m3 *>(out_q));
+    if (rademacher)
+        k_gaussian_dual<true><<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(
+            seed, sid, t_dev, rows, cols, scale, out_b, reinterpret_cast<__nv_fp8_e4m3 *>(out_q));
+    else
+        k_gaussian_dual<false><<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(
+            seed, sid, t_dev, rows, cols, scale, out_b, reinterpret_cast<__nv_fp8_e4m3 *>(out_q));
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -187,20 +251,24 @@ void launch_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, i
 
 template <typename OutT>
 void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_t *t_dev, int64_t rows,
-                           int64_t cols, float scale, bool transposed, OutT *out, cudaStream_t s) {
+                           int64_t cols, float scale, bool transposed, OutT *out, bool rademacher, cudaStream_t s) {
     const int64_t total = ((rows + 3) >> 2) * cols;
     if (total == 0) return;
     const unsigned grid = (unsigned)ceil_div(total, 256);
-    if (transposed)
-        k_gaussian_field<true, OutT><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
+    if (transposed && rademacher)
+        k_gaussian_field<true, OutT, true><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
+    else if (transposed)
+        k_gaussian_field<true, OutT, false><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
+    else if (rademacher)
+        k_gaussian_field<false, OutT, true><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
     else
-        k_gaussian_field<false, OutT><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
+        k_gaussian_field<false, OutT, false><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
     DSANLS_LAUNCH_CHECK();
 }
 template void launch_gaussian_field<float>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t, int64_t,
-                                           float, bool, float *, cudaStream_t);
+                                           float, bool, float *, bool, cudaStream_t);
 template void launch_gaussian_field<__nv_bfloat16>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t,
-                                                   int64_t, float, bool, __nv_bfloat16 *, cudaStream_t);
+                                                   int64_t, float, bool, __nv_bfloat16 *, bool, cudaStream_t);
 
 void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, float *out,
                           cudaStream_t s) {

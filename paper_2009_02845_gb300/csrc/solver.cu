@@ -27,10 +27,12 @@ constexpr int GRAM_MAXP = 33;  // pairs per thread: k(k+1)/2 <= 8256 < 33 * 256
 
 // Each CTA sums chunks blockIdx.x, blockIdx.x + gridDim.x, ... of the d axis
 // for every pair (a <= b); each thread owns up to GRAM_MAXP pairs with FP64
-// accumulators in registers.
+// accumulators in registers.  The chunk is staged in shared memory already
+// converted to FP64 (one conversion per entry, not one per product: the FP64
+// pipe is the scarce unit).
 __global__ void __launch_bounds__(GRAM_THREADS)
     k_gram_partial(const float *__restrict__ W, int k, int64_t d, int64_t dc, double *__restrict__ part) {
-    extern __shared__ float ws[];  // k x (dc + 1), padded against bank conflicts
+    extern __shared__ double ws[];  // k x (dc + 1), padded against bank conflicts
     const int64_t ldw = dc + 1;
     const int npairs = k * (k + 1) / 2;
     double acc[GRAM_MAXP];
@@ -53,19 +55,17 @@ __global__ void __launch_bounds__(GRAM_THREADS)
         const int64_t j0 = ch * dc;
         const int64_t len = min(dc, d - j0);
         __syncthreads();
-        for (int64_t e = threadIdx.x; e < (int64_t)k * dc; e += GRAM_THREADS) {
-            const int a = (int)(e / dc);
-            const int64_t j = e % dc;
-            ws[a * ldw + j] = (j < len) ? W[(int64_t)a * d + j0 + j] : 0.0f;
-        }
+        for (int a = 0; a < k; ++a)
+            for (int64_t j = threadIdx.x; j < dc; j += GRAM_THREADS)
+                ws[a * ldw + j] = (j < len) ? (double)W[(int64_t)a * d + j0 + j] : 0.0;
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < GRAM_MAXP; ++q) {
             if (threadIdx.x + q * GRAM_THREADS < npairs) {
-                const float *wa = ws + (int64_t)pa[q] * ldw;
-                const float *wb = ws + (int64_t)pb[q] * ldw;
+                const double *wa = ws + (int64_t)pa[q] * ldw;
+                const double *wb = ws + (int64_t)pb[q] * ldw;
                 double s = acc[q];
-                for (int64_t j = 0; j < len; ++j) s = fma((double)wa[j], (double)wb[j], s);
+                for (int64_t j = 0; j < len; ++j) s = fma(wa[j], wb[j], s);
                 acc[q] = s;
             }
         }
@@ -102,14 +102,14 @@ void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, in
                  cudaStream_t s) {
     // chunk width: about two chunks per SM, at most ~200 KB of shared memory
     int64_t dc = ceil_div(ceil_div(d, 2 * 152), 4) * 4;
-    const int64_t dc_max = (200 * 1024) / (4 * (int64_t)k) - 1;
+    const int64_t dc_max = (200 * 1024) / (8 * (int64_t)k) - 1;
     if (dc > dc_max) dc = dc_max;
     if (dc < 1) dc = 1;
     int64_t grid = ceil_div(d, dc);
     if (grid > work_elems / ((int64_t)k * k)) grid = work_elems / ((int64_t)k * k);
     if (grid > 2 * 152) grid = 2 * 152;
     if (grid < 1) grid = 1;
-    const size_t smem = (size_t)k * (dc + 1) * sizeof(float);
+    const size_t smem = (size_t)k * (dc + 1) * sizeof(double);
     k_gram_partial<<<(unsigned)grid, GRAM_THREADS, smem, s>>>(W, k, d, dc, work);
     DSANLS_LAUNCH_CHECK();
     const int64_t npairs = (int64_t)k * (k + 1) / 2;
@@ -120,73 +120,85 @@ void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, in
 // ---------------------------------------------------------------------------
 // step size: lambda_max by power iteration, mu_t, eta_t
 // ---------------------------------------------------------------------------
-// One warp: lane l owns rows l, l+32, l+64, l+96 of the power iteration
-// (binary32, G in shared memory); Rayleigh quotient x^T G x in FP64.
-__global__ void __launch_bounds__(32)
+// One CTA of 256 threads: thread t works on row t / 2 of the power iteration
+// (binary32, G in shared memory), the two threads of a row each summing one
+// half of its columns; norms and the FP64 Rayleigh quotient x^T G x are
+// reduced in a fixed order (warp shuffles, then the eight warp partials).
+constexpr int STEP_THREADS = 256;
+
+DSANLS_DEV float block_sum_f(float v, float *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float tot = 0.0f;
+#pragma unroll
+    for (int w = 0; w < STEP_THREADS / 32; ++w) tot += red[w];
+    return tot;
+}
+
+DSANLS_DEV double block_sum_d(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < STEP_THREADS / 32; ++w) tot += red[w];
+    return tot;
+}
+
+__global__ void __launch_bounds__(STEP_THREADS)
     k_step_size(const double *__restrict__ G64, int k, int iters, double alpha, double beta,
                 const int64_t *__restrict__ t_dev, double *__restrict__ scal, float *__restrict__ Gf, int kp) {
     extern __shared__ float gs[];  // k x (k+1)
     __shared__ float x[128];
-    const int lane = threadIdx.x;
-    for (int e = lane; e < kp * kp; e += 32) {
+    __shared__ float redf[STEP_THREADS / 32];
+    __shared__ double redd[2][STEP_THREADS / 32];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kp * kp; e += STEP_THREADS) {
         const int a = e / kp, b = e % kp;
         const float v = (a < k && b < k) ? (float)G64[a * k + b] : 0.0f;
         Gf[e] = v;
         if (a < k && b < k) gs[a * (k + 1) + b] = v;
     }
     const float x0 = rsqrtf((float)k);
-    for (int i = lane; i < 128; i += 32) x[i] = (i < k) ? x0 : 0.0f;
-    __syncwarp();
+    for (int i = tid; i < 128; i += STEP_THREADS) x[i] = (i < k) ? x0 : 0.0f;
+    __syncthreads();
+    const int row = tid >> 1, half = tid & 1;
+    const int lh = (k + 1) / 2;
+    const int l0 = half ? lh : 0, l1 = half ? k : lh;
     for (int it = 0; it < iters; ++it) {
-        float y[4];
-        float nrm2 = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = lane + 32 * q;
-            // four interleaved partial sums (l mod 4) shorten the dependency chain
-            float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-            if (i < k) {
-                const float *gi = gs + i * (k + 1);
-                int l = 0;
-                for (; l + 3 < k; l += 4) {
-                    a0 = fmaf(gi[l], x[l], a0);
-                    a1 = fmaf(gi[l + 1], x[l + 1], a1);
-                    a2 = fmaf(gi[l + 2], x[l + 2], a2);
-                    a3 = fmaf(gi[l + 3], x[l + 3], a3);
-                }
-                for (; l < k; ++l) a0 = fmaf(gi[l], x[l], a0);
+        float a0 = 0.0f, a1 = 0.0f;
+        if (row < k) {
+            const float *gi = gs + row * (k + 1);
+            int l = l0;
+            for (; l + 1 < l1; l += 2) {
+                a0 = fmaf(gi[l], x[l], a0);
+                a1 = fmaf(gi[l + 1], x[l + 1], a1);
             }
-            const float acc = (a0 + a1) + (a2 + a3);
-            y[q] = acc;
-            nrm2 = fmaf(acc, acc, nrm2);
+            if (l < l1) a0 = fmaf(gi[l], x[l], a0);
         }
-        for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+        float y = a0 + a1;
+        y += __shfl_xor_sync(0xffffffffu, y, 1);  // both halves of the row
+        const float nrm2 = block_sum_f(half == 0 && row < k ? y * y : 0.0f, redf);
         if (nrm2 == 0.0f) break;
         const float inv = rsqrtf(nrm2);
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = lane + 32 * q;
-            if (i < k) x[i] = y[q] * inv;
-        }
-        __syncwarp();
+        if (half == 0 && row < k) x[row] = y * inv;
+        __syncthreads();
     }
+    // Rayleigh quotient in FP64; G is symmetric, so (G x)_i = sum_l G[l][i] x_l
+    // (consecutive threads read consecutive entries of a row of G)
     double xgx = 0.0, xx = 0.0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = lane + 32 * q;
-        if (i < k) {
-            double gx = 0.0;
-            for (int l = 0; l < k; ++l) gx = fma(G64[i * k + l], (double)x[l], gx);
-            xgx = fma((double)x[i], gx, xgx);
-            xx = fma((double)x[i], (double)x[i], xx);
-        }
+    if (tid < k) {
+        double gx = 0.0;
+        for (int l = 0; l < k; ++l) gx = fma(G64[l * k + tid], (double)x[l], gx);
+        xgx = (double)x[tid] * gx;
+        xx = (double)x[tid] * (double)x[tid];
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        xgx += __shfl_xor_sync(0xffffffffu, xgx, o);
-        xx += __shfl_xor_sync(0xffffffffu, xx, o);
-    }
-    if (lane == 0) {
+    xgx = block_sum_d(xgx, redd[0]);
+    xx = block_sum_d(xx, redd[1]);
+    if (tid == 0) {
         const double lam = xx > 0.0 ? xgx / xx : 0.0;
         const double mu = alpha + beta * (double)(*t_dev);
         scal[0] = lam;
@@ -197,8 +209,9 @@ __global__ void __launch_bounds__(32)
 
 void launch_step_size(const double *G64, int k, int iters, double alpha, double beta, const int64_t *t_dev,
                       double *scal, float *Gf, int kp, cudaStream_t s) {
+    if (k > 128) throw ArgError{"launch_step_size: k > 128"};
     const size_t smem = (size_t)k * (k + 1) * sizeof(float);
-    k_step_size<<<1, 32, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
+    k_step_size<<<1, STEP_THREADS, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -300,10 +313,42 @@ __global__ void __launch_bounds__(UPD_ROWS)
     }
 }
 
-// PGD update as a register-blocked product: a CTA owns 64 rows, thread
-// (ty, tx) the outputs of rows 4ty..4ty+3 and columns tx*TN..tx*TN+TN-1
-// (TN = KP/16); Z tile and G in shared memory, one FMA chain per output in
-// increasing l (the same order as the row kernel).
+// PGD update as a register-blocked product: a CTA owns 64 consecutive rows,
+// whose Z and R entries form two contiguous ranges of 64 k floats; both are
+// copied flat into shared memory with 16-byte asynchronous copies (R's copy
+// overlaps the product).  Thread (ty, tx) computes rows 4ty..4ty+3 against TN
+// = KP/16 columns of G: for TN >= 4 the columns tx*4 + 64 j + {0..3}, so that
+// a warp's 16-byte loads of a G row are contiguous; for TN < 4 the columns
+// tx*TN + {0..TN-1}.  One FMA chain per output in increasing l (the order of
+// the row kernel).  The new rows are written back in place in shared memory
+// and stored flat.
+DSANLS_DEV void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+DSANLS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+DSANLS_DEV void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int TN>
+DSANLS_DEV int upd_col(int tx, int b) {
+    if constexpr (TN >= 4)
+        return (b >> 2) * 64 + tx * 4 + (b & 3);
+    else
+        return tx * TN + b;
+}
+
+// stage n floats from global src to shared dst with 16-byte copies (both
+// 16-byte aligned); the n % 4 tail with plain loads
+DSANLS_DEV void stage_flat(float *dst, const float *src, int n) {
+    const int n4 = n >> 2;
+    for (int e = threadIdx.x; e < n4; e += blockDim.x) cp_async16(dst + 4 * e, src + 4 * e);
+    for (int e = 4 * n4 + threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+}
+
 template <int KP>
 __global__ void __launch_bounds__(256)
     k_update_pgd_tiled(float *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k,
@@ -312,15 +357,19 @@ __global__ void __launch_bounds__(256)
     constexpr int TN = KP / 16;
     constexpr int LDG = KP + 4;
     extern __shared__ __align__(16) float sm[];
-    float *gs = sm;              // KP x LDG
-    float *zs = sm + KP * LDG;   // 64 x LDG
+    float *gs = sm;                // k x LDG, gs[l][c] = G[l][c] (c < KP, zero beyond k)
+    float *zr = gs + k * LDG;      // 64 x k, row-major (the Z tile, then the new rows)
+    float *rr = zr + 64 * k;       // 64 x k, the R tile
     const int64_t r0 = (int64_t)blockIdx.x * 64;
     const int nr = (int)min((int64_t)64, rows - r0);
-    for (int e = threadIdx.x; e < KP * KP; e += 256) gs[(e / KP) * LDG + (e % KP)] = Gf[e];
-    for (int e = threadIdx.x; e < 64 * k; e += 256) {
-        const int i = e / k, c = e % k;
-        zs[i * LDG + c] = (i < nr) ? Z[(r0 + i) * k + c] : 0.0f;
-    }
+    const int n = nr * k;
+    stage_flat(zr, Z + r0 * k, n);
+    cp_async_commit();
+    stage_flat(rr, R + r0 * k, n);
+    cp_async_commit();
+    for (int e = threadIdx.x; e < k * KP; e += 256) gs[(e / KP) * LDG + (e % KP)] = Gf[e];
+    for (int e = n + threadIdx.x; e < 64 * k; e += 256) zr[e] = 0.0f;
+    cp_async_wait<1>();  // the Z tile
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float acc[4][TN];
@@ -328,17 +377,32 @@ __global__ void __launch_bounds__(256)
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
+    const float *z0 = zr + (ty * 4) * k;
+#pragma unroll 2
     for (int l = 0; l < k; ++l) {
-        float zv[4], gv[TN];
+        const float zv[4] = {z0[l], z0[k + l], z0[2 * k + l], z0[3 * k + l]};
+        float gv[TN];
+        const float *gl = gs + l * LDG;
+        if constexpr (TN >= 4) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) zv[a] = zs[(ty * 4 + a) * LDG + l];
+            for (int j = 0; j < TN / 4; ++j) {
+                const float4 g4 = *reinterpret_cast<const float4 *>(gl + j * 64 + tx * 4);
+                gv[4 * j] = g4.x;
+                gv[4 * j + 1] = g4.y;
+                gv[4 * j + 2] = g4.z;
+                gv[4 * j + 3] = g4.w;
+            }
+        } else {
 #pragma unroll
-        for (int b = 0; b < TN; ++b) gv[b] = gs[l * LDG + tx * TN + b];
+            for (int b = 0; b < TN; ++b) gv[b] = gl[tx * TN + b];
+        }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < TN; ++b) acc[a][b] = __fmaf_rn(zv[a], gv[b], acc[a][b]);
     }
+    cp_async_wait<0>();  // the R tile
+    __syncthreads();     // every thread is done reading the old Z tile
     const float eta = (float)scal[2];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -346,20 +410,26 @@ __global__ void __launch_bounds__(256)
         if (i >= nr) continue;
 #pragma unroll
         for (int b = 0; b < TN; ++b) {
-            const int c = tx * TN + b;
+            const int c = upd_col<TN>(tx, b);
             if (c < k) {
-                const float grad = __fsub_rn(acc[a][b], R[(r0 + i) * k + c]);
-                Z[(r0 + i) * k + c] = project_clamp(__fmaf_rn(-eta, grad, zs[i * LDG + c]), bound, flag);
+                const float grad = __fsub_rn(acc[a][b], rr[i * k + c]);
+                zr[i * k + c] = project_clamp(__fmaf_rn(-eta, grad, zr[i * k + c]), bound, flag);
             }
         }
     }
+    __syncthreads();
+    float *zo = Z + r0 * k;
+    const int n4 = n >> 2;
+    for (int e = threadIdx.x; e < n4; e += 256)
+        reinterpret_cast<float4 *>(zo)[e] = reinterpret_cast<const float4 *>(zr)[e];
+    for (int e = 4 * n4 + threadIdx.x; e < n; e += 256) zo[e] = zr[e];
 }
 
 template <int KP>
 static void update_kp(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf,
                       const double *scal, float bound, int *flag, cudaStream_t s) {
     if (solver == 0) {
-        const size_t smem_t = (size_t)(KP + 64) * (KP + 4) * sizeof(float);
+        const size_t smem_t = ((size_t)k * (KP + 4) + 2 * 64 * (size_t)k) * sizeof(float);
         k_update_pgd_tiled<KP><<<(unsigned)ceil_div(rows, 64), 256, smem_t, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
         DSANLS_LAUNCH_CHECK();
         return;

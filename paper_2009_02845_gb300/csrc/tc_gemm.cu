@@ -42,9 +42,9 @@ constexpr int BN = 256;
 constexpr int BK = 64;  // bf16 elements = 128 bytes = one swizzle row
 constexpr int TC_THREADS = 256;
 constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KB
-constexpr int B_STAGE_BYTES = BN * BK * 2;  // 32 KB
-constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
-constexpr uint32_t TMEM_COLS = 512;
+// one stage: the X tile (16 KB) and BNT rows of 128 bytes of the second operand
+__host__ __device__ constexpr int stage_bytes(int bnt) { return A_STAGE_BYTES + bnt * BK * 2; }
+constexpr int STAGE_BYTES = stage_bytes(BN);
 constexpr uint32_t D2_COL = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded wait: 2 s of wall time
 constexpr int kMaxSplits = 32;                         // split-K slices of the plain product
@@ -189,26 +189,33 @@ struct __align__(8) TcSmemTail {
 // FP8 = true: X and S^T are fp8 E4M3 (kind::f8f6f4, K blocks of 128 elements,
 //   still 128 bytes per row); the fused epilogue multiplies D1 by
 //   row_scale[m0 / 128] * extra_scale before the bf16 repack.
-template <int STAGES, bool FUSED, bool FP8>
+// BNT: width of the N tile (256 for the fused kernel; 64, 128 or 256 for the
+//   plain product).  TMEM: 512 columns for the fused kernel, BNT otherwise, so
+//   two plain CTAs with BNT <= 128 can share an SM.
+template <int STAGES, bool FUSED, bool FP8, int BNT = BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
               const __grid_constant__ CUtensorMap map_b, int64_t rows, int64_t K, int64_t d, int k, int kp,
               int kb_per_split, float *__restrict__ out, int *__restrict__ err, const float *__restrict__ row_scale,
               float extra_scale) {
     constexpr int BKE = FP8 ? 128 : BK;  // K elements per stage
+    static_assert(!FUSED || BNT == BN, "the fused kernel uses 256-wide N tiles");
+    static_assert(BNT == 64 || BNT == 128 || BNT == 256, "N tile of 64, 128 or 256");
+    constexpr int SB = stage_bytes(BNT);
+    constexpr uint32_t TMEM_COLS = FUSED ? 512u : (uint32_t)BNT;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint8_t *stage_base = smem;                                  // STAGES x (A 16 KB | B 32 KB)
-    uint8_t *btile = smem + STAGES * STAGE_BYTES;                // 4 atoms of kp x 128 B (FUSED)
+    uint8_t *stage_base = smem;                                  // STAGES x (A 16 KB | B BNT x 128 B)
+    uint8_t *btile = smem + STAGES * SB;                         // 4 atoms of kp x 128 B (FUSED)
     TcSmemTail *tail = (TcSmemTail *)(btile + (FUSED ? 4 * kp * 128 : 0));
     uint8_t *a2 = stage_base;                                    // reused after the main loop: 4 x 16 KB
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nchunks = (int)ceil_div(d, BN);
+    const int nchunks = (int)ceil_div(d, BNT);
     const int chunk = blockIdx.x % nchunks;
     const int64_t m0 = (int64_t)(blockIdx.x / nchunks) * BM;
-    const int n0 = chunk * BN;
+    const int n0 = chunk * BNT;
     const int nk_total = (int)ceil_div(K, BKE);
     const int kb0 = FUSED ? 0 : (int)blockIdx.y * kb_per_split;
     const int nk = FUSED ? nk_total : max(0, min(kb_per_split, nk_total - kb0));
@@ -254,8 +261,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 if (*(volatile int *)&tail->failed) break;
-                uint8_t *sa = stage_base + s * STAGE_BYTES;
-                mbar_expect_tx(&tail->full[s], STAGE_BYTES);
+                uint8_t *sa = stage_base + s * SB;
+                mbar_expect_tx(&tail->full[s], SB);
                 tma_load_2d(sa, &map_x, (kb0 + kb) * BKE, (int)m0, &tail->full[s]);
                 tma_load_2d(sa + A_STAGE_BYTES, &map_s, (kb0 + kb) * BKE, n0, &tail->full[s]);
                 ++issued;
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id1 = FP8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
+            const uint32_t id1 = FP8 ? idesc_e4m3(BM, BNT) : idesc_bf16(BM, BNT);
             bool ok = true;
             for (int kb = 0; kb < nk && ok; ++kb) {
                 const int s = kb % STAGES;
@@ -276,7 +283,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 fence_after();
-                const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
+                const uint32_t sa = smem_u32(stage_base + s * SB);
                 const uint32_t sb = sa + A_STAGE_BYTES;
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk)
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 fence_after();
                 float *dst = out + ((int64_t)blockIdx.y * rows + row) * d + n0;
 #pragma unroll 1
-                for (int c = 0; c < BN / 32; ++c) {
+                for (int c = 0; c < BNT / 32; ++c) {
                     uint32_t v[32];
                     tmem_ld32(trow + c * 32, v);
                     tmem_ld_wait();
@@ -460,9 +467,54 @@ CUtensorMap make_map_u8(const void *base, int64_t rows, int64_t cols, int box_ro
 
 int kp_of(int k) { return (int)ceil_div(k, 16) * 16; }
 
-size_t smem_bytes(int stages, int kp) {
-    return 1024 /* alignment slack */ + (size_t)stages * STAGE_BYTES + 4 * (size_t)kp * 128 + sizeof(TcSmemTail);
+size_t smem_bytes(int stages, int kp, int bnt = BN) {
+    return 1024 /* alignment slack */ + (size_t)stages * stage_bytes(bnt) + 4 * (size_t)kp * 128 +
+           sizeof(TcSmemTail);
 }
+
+// Split-K plan of a plain product: `tiles` output tiles, `splits` K-ranges of
+// `kb_per_split` k-blocks each.
+struct PlainPlan {
+    int64_t tiles;
+    int splits, kb_per_split;
+};
+
+PlainPlan finish_plan(int64_t tiles, int nk, int splits) {
+    splits = std::max(1, std::min(splits, nk));
+    const int kb = (int)ceil_div(nk, splits);
+    return {tiles, (int)ceil_div(nk, kb), kb};
+}
+
+// About one wave of CTAs (small-N products such as B = Y^T S).
+PlainPlan plan_one_wave(int64_t rows, int64_t K, int64_t N, int bnt) {
+    const int64_t tiles = ceil_div(rows, BM) * ceil_div(N, bnt);
+    const int nk = (int)ceil_div(K, BK);
+    return finish_plan(tiles, nk, (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, ceil_div(152, tiles))));
+}
+
+// Streaming products (R = X P): the split count that best fills whole waves
+// of `slots` resident CTAs, with at least 16 k-blocks per split; among
+// counts within 2 % of the best fill, the smallest (fewer partial sums).
+PlainPlan plan_stream(int64_t rows, int64_t K, int64_t N, int bnt, int slots) {
+    const int64_t tiles = ceil_div(rows, BM) * ceil_div(N, bnt);
+    const int nk = (int)ceil_div(K, BK);
+    const int max_s = std::max(1, std::min(16, nk / 16));
+    double fill[17] = {0};
+    double best = 0.0;
+    for (int sp = 1; sp <= max_s; ++sp) {
+        const PlainPlan p = finish_plan(tiles, nk, sp);
+        const double waves = (double)(p.tiles * p.splits) / slots;
+        fill[sp] = waves / std::ceil(waves);
+        best = std::max(best, fill[sp]);
+    }
+    for (int sp = 1; sp <= max_s; ++sp)
+        if (fill[sp] >= best - 0.02) return finish_plan(tiles, nk, sp);
+    return finish_plan(tiles, nk, 1);
+}
+
+constexpr int kSkinnySlots = 2 * 152;  // two 96 KB CTAs per SM
+
+int skinny_bnt(int k) { return k <= 64 ? 64 : 128; }
 
 int stages_for(int kp) { return smem_bytes(4, kp) <= 227 * 1024 ? 4 : 3; }  // opt-in limit of sm_100/sm_103
 
@@ -567,20 +619,69 @@ void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t row
                     float *part, float *C, int *err, cudaStream_t s) {
     if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || d > (1ll << 31) - 1) throw ArgError{"sizes too large"};
     if (K % 8 != 0 || d % 8 != 0) throw ArgError{"tensor-core path needs K and d multiples of 8"};
-    const int64_t tiles = ceil_div(rows, BM) * ceil_div(d, BN);
-    const int nk = (int)ceil_div(K, BK);
-    // about one wave of CTAs; every split gets at least one k-block
-    int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, ceil_div(152, tiles)));
-    splits = std::min(splits, nk);
-    const int kb_per_split = (int)ceil_div(nk, splits);
-    splits = (int)ceil_div(nk, kb_per_split);
+    const PlainPlan p = plan_one_wave(rows, K, d, BN);
     const CUtensorMap mx = make_map(X, rows, K, BM);
     const CUtensorMap ms = make_map(St, d, K, BN);
-    dim3 grid((unsigned)tiles, (unsigned)splits);
-    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, d, 0, 0, kb_per_split,
-                                                                         part, err, nullptr, 1.0f);
+    dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
+    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, d, 0, 0,
+                                                                         p.kb_per_split, part, err, nullptr, 1.0f);
     DSANLS_LAUNCH_CHECK();
-    launch_split_reduce(part, rows * d, splits, rows, d, d, C, d, s);
+    launch_split_reduce(part, rows * d, p.splits, rows, d, d, C, d, s);
+}
+
+// C[i] = bf16(sum over splits, ascending, of part[split][i])
+__global__ void k_split_reduce_bf16(const float *__restrict__ part, int splits, int64_t n,
+                                    __nv_bfloat16 *__restrict__ C) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float acc = 0.0f;
+    for (int sp = 0; sp < splits; ++sp) acc = __fadd_rn(acc, part[(int64_t)sp * n + i]);
+    C[i] = __float2bfloat16_rn(acc);
+}
+
+int64_t tc_gemm_bf16out_part_elems(int64_t rows, int64_t K, int64_t N) {
+    const PlainPlan p = plan_one_wave(rows, K, N, BN);
+    return (int64_t)p.splits * rows * N;
+}
+
+void launch_tc_gemm_bf16out(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t rows, int64_t K, int64_t N,
+                            float *part, __nv_bfloat16 *C, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || N > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0 || N % 8 != 0) throw ArgError{"tensor-core path needs K and N multiples of 8"};
+    const PlainPlan p = plan_one_wave(rows, K, N, BN);
+    const CUtensorMap mx = make_map(X, rows, K, BM);
+    const CUtensorMap ms = make_map(St, N, K, BN);
+    dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
+    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, N, 0, 0,
+                                                                         p.kb_per_split, part, err, nullptr, 1.0f);
+    DSANLS_LAUNCH_CHECK();
+    k_split_reduce_bf16<<<(unsigned)ceil_div(rows * N, 256), 256, 0, s>>>(part, p.splits, rows * N, C);
+    DSANLS_LAUNCH_CHECK();
+}
+
+int64_t tc_skinny_part_elems(int64_t rows, int64_t K, int k) {
+    const PlainPlan p = plan_stream(rows, K, k, skinny_bnt(k), kSkinnySlots);
+    return (int64_t)p.splits * rows * k;
+}
+
+void launch_tc_skinny(const __nv_bfloat16 *X, const __nv_bfloat16 *Pt, int64_t rows, int64_t K, int k, float *part,
+                      float *R, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0) throw ArgError{"tensor-core path needs K a multiple of 8"};
+    if (k < 1 || k > 128) throw ArgError{"skinny product needs 1 <= k <= 128"};
+    const int bnt = skinny_bnt(k);
+    const PlainPlan p = plan_stream(rows, K, k, bnt, kSkinnySlots);
+    const CUtensorMap mx = make_map(X, rows, K, BM);
+    const CUtensorMap mp = make_map(Pt, k, K, bnt);
+    dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
+    if (bnt == 64)
+        k_tc_gemm<4, false, false, 64><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
+            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f);
+    else
+        k_tc_gemm<3, false, false, 128><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
+            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f);
+    DSANLS_LAUNCH_CHECK();
+    launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
 }
 
 __global__ void k_transpose_bf16(const float *__restrict__ in, int64_t rows, int64_t cols,
@@ -611,6 +712,8 @@ void prime_tc_attributes(int max_smem) {
     allow_max_dynamic_smem(k_tc_gemm<4, false, false>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, true, true>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, true, true>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, false, false, 64>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<3, false, false, 128>, max_smem);
 }
 
 }  // namespace dsanls

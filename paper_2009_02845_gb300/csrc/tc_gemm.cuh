@@ -28,6 +28,19 @@ void launch_quant_rowblocks(const float *X, int64_t rows, int64_t K, float *scal
 int64_t tc_gemm_part_elems(int64_t rows, int64_t d);
 void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t rows, int64_t K, int64_t d,
                     float *part, float *C, int *err, cudaStream_t s);
+// C (rows x N, bf16) = bf16(X St^T) with X rows x K and St N x K (bf16, row-major),
+// split-K partials (scratch of tc_gemm_bf16out_part_elems floats) summed in order in
+// fp32 before the rounding.  Reassociated order: P^T = B S^T from bf16 B (k x d) and
+// bf16 S (K x d).  K and N multiples of 8.
+int64_t tc_gemm_bf16out_part_elems(int64_t rows, int64_t K, int64_t N);
+void launch_tc_gemm_bf16out(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t rows, int64_t K, int64_t N,
+                            float *part, __nv_bfloat16 *C, int *err, cudaStream_t s);
+// R (rows x k, fp32) = X P with X rows x K bf16 and Pt = P^T k x K bf16 (1 <= k <= 128):
+// the streaming product of the reassociated order, N tile 64 or 128, split-K chosen to
+// fill whole waves; partials (scratch of tc_skinny_part_elems floats) summed in order.
+int64_t tc_skinny_part_elems(int64_t rows, int64_t K, int k);
+void launch_tc_skinny(const __nv_bfloat16 *X, const __nv_bfloat16 *Pt, int64_t rows, int64_t K, int k, float *part,
+                      float *R, int *err, cudaStream_t s);
 // out (cols x rows, bf16) = in^T for in rows x cols fp32 row-major.
 void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *out, cudaStream_t s);
 void prime_tc_attributes(int max_smem);

@@ -1,0 +1,228 @@
+"""Parity of the reassociated order R = X (S B^T) of the Gaussian sketch.
+
+P = S B^T (K x k) is formed first, then R = X P (2 K d k + 2 rows K k flops
+instead of 2 rows K d + 2 rows d k).  References:
+  * FP32 form (dense SIMT GEMMs, sparse CSR SpMM): the FP64 oracle of the
+    same order, 1e-5 norm-wise per half-step (the tolerance of the paper
+    order, which equals it in exact arithmetic);
+  * BF16 form (tcgen05): the oracle's bf16 model of this order (S, Y, B, P
+    and X rounded to bf16 where the GPU rounds them) <= 3e-4, and plain FP64
+    <= 1e-2 per half-step: R passes through four bf16 roundings (X, S, B where
+    it enters P, and P; unit roundoff 2^-9 each, about 4 x 2^-9 = 7.8e-3
+    together);
+  * a short bf16 run with closing fp32 iterations ends within 2e-3 of the
+    oracle's final relative error.
+Shapes span several tiles, ragged row tails, the 64- and 128-wide N tiles of
+the streaming product (k <= 64 and 64 < k <= 128) and d of one to eight
+256-wide chunks.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import method
+from synthdata import initial_factors, planted_dense, sparse_text
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2009_02845_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _run_half(pkg, m, n, k, d, d_v, side, U, V, solver, precision, dense=None, csr=None, t=2, seed=21):
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=seed, d_v=d_v, solver=solver, precision=precision, t=t,
+                   order=pkg.ORDER_REASSOCIATED)
+    if dense is not None:
+        h.set_dense(dense)
+    else:
+        h.set_csr(*csr)
+    h.set_factors(U, V)
+    h.half_step(side)
+    Ug, Vg = h.factors()
+    h.close()
+    return Ug if side == 0 else Vg
+
+
+def _oracle(X64, U, V, side, dd, solver, t=2, seed=21, bf16=False):
+    X = X64 if side == 0 else X64.T
+    if sp.issparse(X):
+        X = X.tocsr()
+    Y = (V if side == 0 else U).astype(np.float64)
+    Z = (U if side == 0 else V).astype(np.float64)
+    S = method.Sketch(method.GAUSSIAN, seed, t, side, X.shape[1], dd)
+    return method.half_step(X, Y, Z, S, solver, method.mu_t(1.0, 1.0, t), bf16=bf16, reassociate=True)
+
+
+FP32_CASES = [
+    # m, n, k, d, d_v
+    (333, 257, 10, 40, 50),
+    (640, 515, 64, 130, 129),
+    (300, 260, 100, 96, 96),
+    (129, 70, 1, 9, 9),
+]
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("case", FP32_CASES)
+def test_fp32_dense_half_steps(pkg, case, solver):
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 1)
+    U, V = initial_factors(m, n, k, 2)
+    for side, dd in ((0, d), (1, d_v)):
+        got = _run_half(pkg, m, n, k, d, d_v, side, U, V, solver, pkg.FP32, dense=M)
+        want = _oracle(M.astype(np.float64), U, V, side, dd, solver)
+        assert got.min() >= 0
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_fp32_sparse_half_steps(pkg, solver):
+    m, n, k = 700, 300, 16
+    rp, col, val = sparse_text(m, n, 9, mean_len=12.0)
+    Msp = sp.csr_matrix((val.astype(np.float64), col, rp), shape=(m, n))
+    U, V = initial_factors(m, n, k, 7)
+    for side, dd in ((0, 60), (1, 70)):
+        got = _run_half(pkg, m, n, k, 60, 70, side, U, V, solver, pkg.FP32, csr=(rp, col, val))
+        want = _oracle(Msp, U, V, side, dd, solver)
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
+BF16_CASES = [
+    (256, 128, 16, 256, 256),
+    (1000, 808, 10, 104, 96),
+    (640, 520, 64, 520, 264),
+    (384, 1032, 128, 768, 256),
+    (136, 200, 32, 2048, 64),
+    (2056, 4104, 100, 512, 1024),
+]
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("case", BF16_CASES)
+def test_bf16_half_steps(pkg, case, solver):
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 2)
+    U, V = initial_factors(m, n, k, 3)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        got = _run_half(pkg, m, n, k, d, d_v, side, U, V, solver, pkg.BF16, dense=M)
+        model = _oracle(M64, U, V, side, dd, solver, bf16=True)
+        exact = _oracle(M64, U, V, side, dd, solver)
+        assert got.min() >= 0
+        assert _rel(got, model) <= 3e-4, (side, _rel(got, model))
+        assert _rel(got, exact) <= 1e-2, (side, _rel(got, exact))
+
+
+def test_bf16_run_final_error(pkg):
+    """bf16 reassociated iterations plus 3 closing fp32 iterations (paper
+    order) end within 2e-3 of the oracle's final relative error."""
+    m, n, k, d, T = 1000, 808, 10, 104, 30
+    M, _, _ = planted_dense(m, n, k, 0)
+    U0, V0 = method.default_init(0, m, n, k)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=0, precision=pkg.BF16, order=pkg.ORDER_REASSOCIATED,
+                   use_graph=1)
+    h.set_dense(M)
+    h.step(T - 3)
+    h.set_options(precision=pkg.FP32, order=pkg.ORDER_PAPER)
+    h.step(3)
+    err = h.rel_error()
+    h.close()
+    _, _, errs = method.run(M, U0, V0, 0, T, method.Options(sketch=method.GAUSSIAN, d=d))
+    assert abs(err - errs[-1]) <= 2e-3, (err, errs[-1])
+
+
+def test_graph_replay_equals_eager(pkg):
+    """Replaying the captured iteration gives the eager iteration's factors."""
+    m, n, k, d = 520, 264, 32, 256
+    M, _, _ = planted_dense(m, n, 16, 5)
+    out = []
+    for g in (0, 1):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=4, precision=pkg.BF16, order=pkg.ORDER_REASSOCIATED,
+                       use_graph=g)
+        h.set_dense(M)
+        h.step(4)
+        out.append(h.factors())
+        h.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_reassociated_rejects_other_forms(pkg):
+    h = pkg.DSANLS(256, 128, 8, 64, pkg.GAUSSIAN, seed=0)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(precision=pkg.FP8, order=pkg.ORDER_REASSOCIATED)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(order=2)
+    h.close()
+    h = pkg.DSANLS(256, 128, 8, 64, pkg.SUBSAMPLE, seed=0)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(order=pkg.ORDER_REASSOCIATED)
+    h.close()
+
+
+IDENT_CASES = [(256, 136, 16), (1000, 808, 10), (520, 264, 100)]
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("case", IDENT_CASES)
+def test_bf16_identity_half_steps(pkg, case, solver):
+    """The unsketched subproblem (S = I) in bf16: R = X Y on the streaming
+    tensor-core product, against the oracle's bf16 model (X and Y rounded,
+    G = Y^T Y from the unrounded Y) <= 3e-4 and plain FP64 <= 1e-2."""
+    m, n, k = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 6)
+    U, V = initial_factors(m, n, k, 8)
+    M64 = M.astype(np.float64)
+    for side in (0, 1):
+        h = pkg.DSANLS(m, n, k, n, pkg.IDENTITY, seed=1, solver=solver, precision=pkg.BF16, t=3)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.IDENTITY, 1, 3, side, X.shape[1], X.shape[1])
+        mu = method.mu_t(1.0, 1.0, 3)
+        model = method.half_step(X, Y, Z, S, solver, mu, bf16=True)
+        exact = method.half_step(X, Y, Z, S, solver, mu)
+        assert _rel(got, model) <= 3e-4, (side, _rel(got, model))
+        assert _rel(got, exact) <= 1e-2, (side, _rel(got, exact))
+
+
+@pytest.mark.parametrize("precision,order", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0)])
+def test_rademacher_half_steps(pkg, precision, order):
+    """The +-1/sqrt(d) sketch runs through every dense-sketch path: FP32 and
+    BF16 in both orders and FP8 (paper order), against the matching oracle
+    models (FP32: 1e-5; bf16 / fp8 models: 3e-4)."""
+    m, n, k, d, d_v = 640, 528, 32, 264, 136
+    M, _, _ = planted_dense(m, n, 16, 3)
+    U, V = initial_factors(m, n, k, 4)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        h = pkg.DSANLS(m, n, k, d, pkg.RADEMACHER, seed=9, d_v=d_v, precision=precision, order=order, t=5)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.RADEMACHER, 9, 5, side, X.shape[1], dd)
+        mu = method.mu_t(1.0, 1.0, 5)
+        want = method.half_step(X, Y, Z, S, 0, mu, bf16=precision == 1, fp8=(9, 5, side) if precision == 2 else None,
+                                reassociate=order == 1)
+        tol = 1e-5 if precision == 0 else 3e-4
+        assert _rel(got, want) <= tol, (side, _rel(got, want))

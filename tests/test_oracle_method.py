@@ -85,7 +85,7 @@ def pin_pgd_identity(mod):
 # pins
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE])
+@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE, method.RADEMACHER])
 def test_sketched_gradient_is_unbiased(kind):
     assert pin_unbiased_gradient(method, kind) < 0.08
 
@@ -418,3 +418,24 @@ def test_reassociated_half_step_matches_paper_order():
     a = method.half_step(M, V, U, S, method.PGD, 2.0)
     b = method.half_step(M, V, U, S, method.PGD, 2.0, reassociate=True)
     assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+def test_identity_bf16_model_rounding_points():
+    """S = I in bf16: R = round(X) round(Y), G from the unrounded Y.  With
+    X = [[1, 1]] and Y = [[1 + 2^-9], [1]]: R = 2 (Y rounded), G = (1 + 2^-9)^2 + 1."""
+    e = 1.0 + 2.0 ** -9
+    S = method.Sketch(method.IDENTITY, 0, 0, 0, 2, 2)
+    _, B, G, R = method.sketched_terms_bf16(np.array([[1.0, 1.0]]), np.array([[e], [1.0]]), S)
+    assert R[0, 0] == 2.0 and G[0, 0] == e * e + 1.0 and B[0, 0] == e
+    _, _, _, R = method.sketched_terms_bf16(np.array([[e, 0.0]]), np.array([[1.0], [0.0]]), S)
+    assert R[0, 0] == 1.0
+
+
+def test_identity_bf16_model_is_exact_on_representable_inputs():
+    g = np.random.default_rng(8)
+    X = g.integers(0, 4, (7, 6)).astype(np.float64)
+    Y = g.integers(0, 4, (6, 3)).astype(np.float64)
+    S = method.Sketch(method.IDENTITY, 0, 0, 0, 6, 6)
+    _, B, G, R = method.sketched_terms_bf16(X, Y, S)
+    _, Be, Ge, Re = method.sketched_terms(X, Y, S)
+    assert np.array_equal(B, Be) and np.array_equal(G, Ge) and np.array_equal(R, Re)

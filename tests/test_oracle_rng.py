@@ -157,16 +157,37 @@ def test_subsample_inclusion_is_uniform():
     assert abs(pair / trials - p_pair) < 5 * math.sqrt(p_pair * (1 - p_pair) / trials)
 
 
-@pytest.mark.parametrize("kind", ["gaussian", "subsample"])
+@pytest.mark.parametrize("kind", ["gaussian", "subsample", "rademacher"])
 def test_sketch_second_moment_is_identity(kind):
     """Assumption 1: E[S S^T] = I (Monte-Carlo over t)."""
     from oracle import method
     n, d, trials = 12, 4, 6000
     acc = np.zeros((n, n))
+    kinds = {"gaussian": method.GAUSSIAN, "subsample": method.SUBSAMPLE, "rademacher": method.RADEMACHER}
     for t in range(trials):
-        S = method.Sketch(method.GAUSSIAN if kind == "gaussian" else method.SUBSAMPLE, 21, t, 0, n, d).dense()
+        S = method.Sketch(kinds[kind], 21, t, 0, n, d).dense()
         acc += S @ S.T
     mean = acc / trials
     # Gaussian: Var[(SS^T)_ii] = 2/d, off-diagonal 1/d; subsampling: diag (n/d)^2 p(1-p)
     tol = 6.0 * math.sqrt(max(2.0 / d, (n / d - 1.0)) / trials)
     assert np.max(np.abs(mean - np.eye(n))) < tol
+
+
+def test_rademacher_field_values_and_balance():
+    """Entries are exactly +-float32(1/sqrt(d)); the signs are balanced
+    (binomial bound), uncorrelated between neighbouring entries, and differ
+    between iterations and streams."""
+    from scipy import stats
+    d = 64
+    sc = rng.gaussian_scale(d)
+    S = rng.rademacher_field(5, 0, 3, 4096, d, sc)
+    assert set(np.unique(S).tolist()) == {float(-sc), float(sc)}
+    pos = int((S > 0).sum())
+    assert stats.binomtest(pos, S.size, 0.5).pvalue > 1e-4
+    sgn = np.sign(S).astype(np.float64)
+    assert abs(np.mean(sgn[:, :-1] * sgn[:, 1:])) < 5.0 / math.sqrt(sgn[:, 1:].size)
+    assert abs(np.mean(sgn[:-1] * sgn[1:])) < 5.0 / math.sqrt(sgn[1:].size)
+    other_t = np.sign(rng.rademacher_field(5, 0, 4, 4096, d, sc))
+    other_s = np.sign(rng.rademacher_field(5, 1, 3, 4096, d, sc))
+    for o in (other_t, other_s):
+        assert abs(np.mean(sgn * o)) < 5.0 / math.sqrt(sgn.size)
