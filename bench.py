@@ -292,9 +292,9 @@ def time_to_eps(pkg, torch, M, w, T, check_every, stream):
     path and for the bf16 form with its last 3 iterations in FP32; eps is the
     FP32 path's error after T iterations + 1e-3.  Times are CUDA-event sums of
     the steps alone (error evaluations excluded)."""
-    def trajectory(prec_plan, order=0):
+    def trajectory(prec_plan, order=0, inner=1):
         h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=0, d_v=w["d_v"], solver=pkg.PGD,
-                       precision=prec_plan[0], use_graph=1, order=order)
+                       precision=prec_plan[0], use_graph=1, order=order, inner_iters=inner)
         h.set_dense(M)
         errs, total_ms = [], 0.0
         for it in range(T):
@@ -315,7 +315,8 @@ def time_to_eps(pkg, torch, M, w, T, check_every, stream):
     fp32 = trajectory((pkg.FP32, pkg.FP32))
     eps = fp32[-1][2] + 1e-3
     forms = {"bf16_closing_fp32": trajectory((pkg.BF16, pkg.FP32)), "fp8_closing_fp32": trajectory((pkg.FP8, pkg.FP32)),
-             "bf16_reassociated_closing_fp32": trajectory((pkg.BF16, pkg.FP32), order=1)}
+             "bf16_reassociated_closing_fp32": trajectory((pkg.BF16, pkg.FP32), order=1),
+             "bf16_reassociated_inner16_closing_fp32": trajectory((pkg.BF16, pkg.FP32), order=1, inner=16)}
 
     def first_hit(tr):
         for it, ms, e in tr:
@@ -353,7 +354,8 @@ def run_ours(args, w):
     order = w.get("order", 0)
     solver = {"pgd": pkg.PGD, "rcd": pkg.RCD}[args.solver]
     h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=rank, d_v=w["d_v"], solver=solver,
-                   precision=prec, use_graph=1, order=order, alpha=args.alpha, beta=args.beta)
+                   precision=prec, use_graph=1, order=order, alpha=args.alpha, beta=args.beta,
+                   inner_iters=args.inner_iters)
     _set_data(h, M)
 
     for _ in range(args.warmup):
@@ -440,7 +442,7 @@ def run_ours(args, w):
         Uh = torch.empty((m, k), dtype=torch.float32).pin_memory()
         Vh = torch.empty((n, k), dtype=torch.float32).pin_memory()
         he = pkg.DSANLS(m, n, k, d, w["sketch"], seed=rank, d_v=d_v, solver=solver, precision=prec, use_graph=1,
-                        order=order, alpha=args.alpha, beta=args.beta)
+                        order=order, alpha=args.alpha, beta=args.beta, inner_iters=args.inner_iters)
 
         def e2e_step():
             _set_data(he, Mp)
@@ -479,7 +481,8 @@ def run_ours(args, w):
             "vs_baseline": None, "dtype": {pkg.FP32: "f32", pkg.BF16: "bf16", pkg.FP8: "e4m3"}[prec],
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "k": k, "d": d, "d_v": d_v,
-                       "precision": {pkg.FP32: "fp32", pkg.BF16: "bf16", pkg.FP8: "fp8"}[prec], "solver": args.solver, "alpha": args.alpha, "beta": args.beta, "graph": True, "replicas": ws,
+                       "precision": {pkg.FP32: "fp32", pkg.BF16: "bf16", pkg.FP8: "fp8"}[prec], "solver": args.solver, "alpha": args.alpha, "beta": args.beta,
+                       "inner_iters": args.inner_iters, "graph": True, "replicas": ws,
                        "order": ["paper", "reassociated"][order],
                        "l2": "inputs larger than L2 (M is %.1f GB)" % (_input_bytes(M) / 1e9)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -504,6 +507,8 @@ def main():
     ap.add_argument("--order", choices=["paper", "reassociated"], default=None,
                     help="order of R = M S B^T for Gaussian sketches (default: the workload's)")
     ap.add_argument("--solver", choices=["pgd", "rcd"], default="pgd")
+    ap.add_argument("--inner-iters", type=int, default=1,
+                    help="PGD steps per half-step on the proximal row objective (1: the paper's single step)")
     ap.add_argument("--alpha", type=float, default=1.0, help="mu_t = alpha + beta t")
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -532,10 +537,13 @@ def run_learned(args, w):
     harvest (G, b, x*) triples from training seeds 1..20 (both halves at 15
     iterations spread over the first 300 of a plain bf16 run, 16384 rows per
     half-step, ~1e7 triples), train the network on the GPU, then run the
-    held-out seed 21 to relative error eps with (a) the plain fp32 path, (b)
-    the bf16 form, (c) the bf16 form with the learned warm start.  Times are
-    CUDA-event sums of the steps; errors are checked after every outer
-    iteration."""
+    held-out seed 21 to relative error eps with: the plain fp32 and bf16 paths
+    (one projected-gradient step per half); the learned form (network point +
+    PG_ITERS correction steps, fallback to the single plain step); bf16 with
+    INNER plain steps per half (the correction without a network: the
+    ablation); and the learned form whose fallback is that INNER-step update.
+    Times are CUDA-event sums of the steps; errors are checked after every
+    outer iteration."""
     import torch
     import paper_2009_02845_gb300 as pkg
     from synthdata import planted_dense_torch
@@ -545,6 +553,7 @@ def run_learned(args, w):
     torch.cuda.set_stream(stream)
     m, n, k, d = w["m"], w["n"], w["k"], w["d"]
     hidden, eps, t_max, seeds = 256, w["eps"], w["t_max"], list(range(1, 21))
+    PG_ITERS, INNER = 16, 16
     points = [0, 1, 2, 3, 5, 8, 12, 18, 27, 40, 60, 90, 135, 200, 300]
     per_group = 16384
     net = pkg.MLP(k, hidden, max_rows=max(m, n), max_groups=64, seed=0)
@@ -595,11 +604,11 @@ def run_learned(args, w):
     from synthdata import planted_dense
     M, _, _ = planted_dense(m, n, k, 21, zero_frac=0.7)
 
-    def run(prec, learned):
-        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=21, precision=prec, use_graph=1)
+    def run(prec, learned, inner=1, pg_iters=PG_ITERS):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=21, precision=prec, use_graph=1, inner_iters=inner)
         h.set_dense(M)
         if learned:
-            h.set_mlp(net, pg_iters=4)
+            h.set_mlp(net, pg_iters=pg_iters)
         total, hist, hit = 0.0, [], None
         for it in range(t_max):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -618,18 +627,25 @@ def run_learned(args, w):
         return {"to_eps": hit, "final_err": hist[-1], "iters_run": len(hist), "seconds_run": total / 1000.0,
                 "ms_per_iter": total / len(hist), "rows_kept_learned": kept}
 
-    res = {"fp32_plain": run(pkg.FP32, False), "bf16": run(pkg.BF16, False), "bf16_learned": run(pkg.BF16, True)}
+    # plain fp32 and bf16 (the paper's single step); bf16 with INNER steps from u
+    # (the same correction without a network); the learned form with the network's
+    # point corrected by PG_ITERS steps, falling back to the single plain step or
+    # to the INNER-step plain update
+    res = {"fp32_plain": run(pkg.FP32, False), "bf16": run(pkg.BF16, False),
+           "bf16_learned": run(pkg.BF16, True, 1),
+           "bf16_inner%d" % INNER: run(pkg.BF16, False, INNER),
+           "bf16_learned_inner%d" % INNER: run(pkg.BF16, True, INNER)}
     base = res["fp32_plain"]["to_eps"]
-    best = res["bf16_learned"]["to_eps"]
+    best = res["bf16_learned_inner%d" % INNER]["to_eps"]
     value = (1.0 / best["seconds"]) if best else 0.0
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "1/time_to_eps (1/s)", "n_gpus": ws, "steps": t_max,
-        "warmup": 0, "ms_per_step": res["bf16_learned"]["ms_per_iter"], "higher_is_better": True, "scaling": "weak",
+        "warmup": 0, "ms_per_step": res["bf16_learned_inner%d" % INNER]["ms_per_iter"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "k": k, "d": d, "eps": eps,
                    "train_seeds": "1-20", "eval_seed": 21, "triples": triples, "train_steps": steps,
                    "harvest_iterations": points, "rows_per_step": groups * rows_per, "hidden": hidden,
-                   "pg_iters": 4},
+                   "pg_iters": PG_ITERS, "inner_iters": INNER},
         "harvest_s": harvest_s, "train_s": train_s, "loss_first": float(np.mean(losses[:20])),
         "loss_last": float(np.mean(losses[-20:])), "results": res,
         "speedup_time_to_eps_vs_fp32": (base["seconds"] / best["seconds"]) if (base and best) else None,
@@ -658,6 +674,8 @@ def run_compare(args, w):
         ("sanls_gaussian_pgd_bf16", G_, d, d, pkg.PGD, pkg.BF16, 0, 1.0, 1.0),
         ("sanls_gaussian_pgd_bf16_reassociated", G_, d, d, pkg.PGD, pkg.BF16, 1, 1.0, 1.0),
         ("sanls_gaussian_rcd_bf16_reassociated", G_, d, d, pkg.RCD, pkg.BF16, 1, 1.0, 1.0),
+        ("sanls_gaussian_pgd16_bf16_reassociated", G_, d, d, pkg.PGD, pkg.BF16, 1, 1.0, 1.0, 16),
+        ("sanls_subsample_pgd16_fp32", S_, d, d, pkg.PGD, pkg.FP32, 0, 1.0, 1.0, 16),
         ("sanls_subsample_pgd_fp32", S_, d, d, pkg.PGD, pkg.FP32, 0, 1.0, 1.0),
         ("sanls_subsample_rcd_fp32", S_, d, d, pkg.RCD, pkg.FP32, 0, 1.0, 1.0),
         ("plain_pg_bf16", I_, n, m, pkg.PGD, pkg.BF16, 0, 1.0, 1.0),
@@ -665,9 +683,9 @@ def run_compare(args, w):
         ("hals_fp32", I_, n, m, pkg.RCD, pkg.FP32, 0, 0.0, 0.0),
     ]
     res = {}
-    for name, sk, dd, ddv, solver, prec, order, alpha, beta in forms:
+    for name, sk, dd, ddv, solver, prec, order, alpha, beta, *inner in forms:
         h = pkg.DSANLS(m, n, k, dd, sk, seed=0, d_v=ddv, solver=solver, precision=prec, use_graph=1, order=order,
-                       alpha=alpha, beta=beta)
+                       alpha=alpha, beta=beta, inner_iters=inner[0] if inner else 1)
         h.set_dense(M)
         total, hit, err = 0.0, None, None
         for it in range(w["t_max"]):

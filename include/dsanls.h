@@ -98,6 +98,11 @@ typedef struct dsanls_options {
     int32_t bound_clamp;   /* 1: clamp entries at sqrt(2 ||M||_F) (eq. extra_con)    */
     int32_t use_graph;     /* 1: replay each outer iteration as a CUDA graph         */
     int32_t order;         /* DSANLS_ORDER_*; default PAPER                          */
+    int32_t inner_iters;   /* PGD: projected-gradient steps per half-step on the
+                              proximal row objective 1/2 x^T (G + mu_t I) x -
+                              (r + mu_t u)^T x (eq. reg_sub), from x = u; 1 (the
+                              default) is the single step of eq. gradient_descent.
+                              1..256; must be 1 with RCD and in the batched form */
     void *stream;          /* cudaStream_t for all work; NULL = the handle's own     */
 } dsanls_options;
 

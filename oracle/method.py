@@ -241,6 +241,20 @@ def pgd_update(Z, G, R, eta, bound=None):
     return project(Z - eta * (Z @ G - R), bound)
 
 
+def pgd_inner(Z, G, R, eta, mu, iters, bound=None):
+    """``iters`` projected-gradient steps on the proximal row objective of eq.
+    reg_sub (halved), f(x) = 1/2 x^T (G + mu I) x - (r + mu u)^T x with u the
+    current row of Z, starting at x = u with step eta:
+        x <- max{x - eta ((G + mu I) x - (R + mu Z)), 0}.
+    At x = u the mu terms cancel, so the first step is eq. gradient_descent
+    (pgd_update); more steps approach the exact minimiser of the subproblem."""
+    b = R + mu * Z
+    x = Z
+    for _ in range(iters):
+        x = project(x - eta * (x @ G + mu * x - b), bound)
+    return x
+
+
 def rcd_update(Z, G, R, mu, bound=None):
     """Proximal coordinate descent, Alg. 3 / eq. entry_sol: for j = 1..k,
     T = mu Z^t_j + R_j - sum_{l<j} G_lj Z^{t+1}_l - sum_{l>j} G_lj Z^t_l,
@@ -259,11 +273,12 @@ def rcd_update(Z, G, R, mu, bound=None):
 
 
 def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf16=False, fp8=None,
-              reassociate=False):
+              reassociate=False, inner_iters=1):
     """Update of the factor Z (rows x k) against data X (rows x n) with the
     other factor Y (n x k) fixed and sketch S (n x d): one solver step on the
-    sketched subproblem (eq. sketched_sub).  ``rows`` restricts the result to a
-    subset of rows (the subproblem is row-independent, eq. u_block)."""
+    sketched subproblem (eq. sketched_sub), or ``inner_iters`` projected
+    gradient steps on its proximal form (PGD).  ``rows`` restricts the result
+    to a subset of rows (the subproblem is row-independent, eq. u_block)."""
     if rows is not None:
         X = X[rows]
         Z = Z[rows]
@@ -277,6 +292,8 @@ def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf1
         A, B, G, R = sketched_terms(X, Y, S)
     if solver == PGD:
         eta = 1.0 / (lambda_max(G, power_iters) + mu)
+        if inner_iters > 1:
+            return pgd_inner(Z, G, R, eta, mu, inner_iters, bound)
         return pgd_update(Z, G, R, eta, bound)
     if solver == RCD:
         return rcd_update(Z, G, R, mu, bound)
@@ -285,9 +302,10 @@ def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf1
 
 class Options:
     def __init__(self, sketch=GAUSSIAN, d=None, d_v=None, solver=PGD, alpha=1.0, beta=1.0,
-                 power_iters=32, bound_clamp=False):
+                 power_iters=32, bound_clamp=False, inner_iters=1):
         self.sketch, self.d, self.d_v = sketch, d, d_v
         self.solver, self.alpha, self.beta = solver, alpha, beta
+        self.inner_iters = inner_iters
         self.power_iters, self.bound_clamp = power_iters, bound_clamp
 
 
@@ -305,9 +323,9 @@ def outer_iteration(M, MT, U, V, seed, t, opt, bound=None):
     d_v = opt.d_v if opt.d_v is not None else d
     mu = mu_t(opt.alpha, opt.beta, t)
     S = Sketch(opt.sketch, seed, t, SIDE_U, n, d)
-    U = half_step(M, V, U, S, opt.solver, mu, opt.power_iters, bound)
+    U = half_step(M, V, U, S, opt.solver, mu, opt.power_iters, bound, inner_iters=opt.inner_iters)
     Sp = Sketch(opt.sketch, seed, t, SIDE_V, m, d_v)
-    V = half_step(MT, U, V, Sp, opt.solver, mu, opt.power_iters, bound)
+    V = half_step(MT, U, V, Sp, opt.solver, mu, opt.power_iters, bound, inner_iters=opt.inner_iters)
     return U, V
 
 

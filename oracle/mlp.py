@@ -13,8 +13,9 @@ Learned form of one half-step (the same choices the GPU library makes):
     h1 = GELU(W1g vec(Gn) + W1b bn + b1)  (W1g vec(Gn) is shared by all rows);
   * x0 = y0 beta / s, then P projected-gradient steps on f with step
     eta = 1/(lambda_max(G) + mu): x <- max(0, x - eta ((G + mu I) x - (r + mu u)));
-  * fallback: the plain projected-gradient step x_pgd = max(0, u - eta (u G - r))
-    is kept whenever f(x_pgd) < f(x_mlp).
+  * fallback: the plain path's update x_pgd -- the projected-gradient step
+    max(0, u - eta (u G - r)), or the same number of steps on f from u as the
+    plain path takes -- is kept whenever f(x_pgd) < f(x_mlp).
 Training: mean squared error 1/2 mean ||y0 - y*||^2 against the normalised
 exact minimiser y*, Adam.  GELU is the exact x Phi(x).
 """
@@ -126,9 +127,11 @@ def prox_exact(G, mu, b):
     return np.stack([_nnls.active_set(Gm, bi) for bi in b])
 
 
-def learned_candidates(P, G, mu, R, Z, eta, pg_iters):
+def learned_candidates(P, G, mu, R, Z, eta, pg_iters, plain_iters=1):
     """Both candidates of the learned form and their proximal objectives:
-    (x_mlp, x_pgd, f_mlp, f_pgd)."""
+    (x_mlp, x_pgd, f_mlp, f_pgd).  x_pgd is the plain path's update: one
+    projected gradient step from u (eq. gradient_descent), or ``plain_iters``
+    steps on the proximal objective."""
     b = R + mu * Z
     Gn, bn, s, beta = normalise(G, mu, b)
     y0, _ = forward(P, Gn, bn)
@@ -136,12 +139,17 @@ def learned_candidates(P, G, mu, R, Z, eta, pg_iters):
     Gm = G + mu * np.eye(G.shape[0])
     for _ in range(pg_iters):
         x = np.where(x - eta * (x @ Gm - b) > 0.0, x - eta * (x @ Gm - b), 0.0)
-    x_pgd = np.where(Z - eta * (Z @ G - R) > 0.0, Z - eta * (Z @ G - R), 0.0)
+    if plain_iters > 1:
+        x_pgd = Z
+        for _ in range(plain_iters):
+            x_pgd = np.where(x_pgd - eta * (x_pgd @ Gm - b) > 0.0, x_pgd - eta * (x_pgd @ Gm - b), 0.0)
+    else:
+        x_pgd = np.where(Z - eta * (Z @ G - R) > 0.0, Z - eta * (Z @ G - R), 0.0)
     return x, x_pgd, prox_objective(G, mu, b, x), prox_objective(G, mu, b, x_pgd)
 
 
-def learned_update(P, G, mu, R, Z, eta, pg_iters):
+def learned_update(P, G, mu, R, Z, eta, pg_iters, plain_iters=1):
     """The learned form of one half-step for rows R (N x k), current rows Z."""
-    x, x_pgd, f_mlp, f_pgd = learned_candidates(P, G, mu, R, Z, eta, pg_iters)
+    x, x_pgd, f_mlp, f_pgd = learned_candidates(P, G, mu, R, Z, eta, pg_iters, plain_iters)
     keep = f_mlp <= f_pgd
     return np.where(keep[:, None], x, x_pgd), keep

@@ -52,6 +52,7 @@ class Options(ctypes.Structure):
         ("bound_clamp", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("order", ctypes.c_int32),
+        ("inner_iters", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

@@ -399,10 +399,12 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     mark(pe, DSANLS_PHASE_UPDATE, s);
     if (!update) return;
     if (h->mlp)
-        mlp_learned_update(h->mlp->st, Z, h->R, rows, h->G64[side], h->Gf, kp, h->scal[side], h->pg_iters, h->kept,
+        mlp_learned_update(h->mlp->st, Z, h->R, rows, h->G64[side], h->Gf, kp, h->scal[side], h->pg_iters,
+                           h->opt.inner_iters, h->kept,
                            h->flag, s);
     else
-        launch_update(h->opt.solver, Z, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->flag, s);
+        launch_update(h->opt.solver, Z, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->opt.inner_iters, h->flag,
+                      s);
     mark(pe, DSANLS_NPHASES, s);
 }
 
@@ -537,6 +539,7 @@ int dsanls_default_options(dsanls_options *opt) {
     opt->bound_clamp = 0;
     opt->use_graph = 0;
     opt->order = DSANLS_ORDER_PAPER;
+    opt->inner_iters = 1;
     opt->stream = nullptr;
     return DSANLS_OK;
 }
@@ -624,6 +627,9 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
             (!dense_kind(h->sketch) || opt->precision == DSANLS_PREC_FP8))
             throw ArgError{"the reassociated order needs a Gaussian sketch and FP32 or BF16 precision"};
         if (opt->power_iters < 0 || opt->power_iters > 10000) throw ArgError{"power_iters out of range"};
+        if (opt->inner_iters < 1 || opt->inner_iters > 256) throw ArgError{"inner_iters must be in 1..256"};
+        if (opt->inner_iters > 1 && opt->solver != DSANLS_SOLVER_PGD)
+            throw ArgError{"inner_iters > 1 needs the PGD solver"};
         if (!(opt->alpha >= 0.0) || !(opt->beta >= 0.0) || !std::isfinite(opt->alpha) || !std::isfinite(opt->beta))
             throw ArgError{"alpha and beta must be finite and >= 0"};
         if (opt->t < 0) throw ArgError{"t must be >= 0"};
@@ -633,7 +639,8 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
                                 (opt->stream != h->opt.stream) || (opt->solver != h->opt.solver) ||
                                 (opt->power_iters != h->opt.power_iters) || (opt->alpha != h->opt.alpha) ||
                                 (opt->beta != h->opt.beta) || (opt->bound_clamp != h->opt.bound_clamp) ||
-                                (opt->use_graph != h->opt.use_graph) || (opt->order != h->opt.order);
+                                (opt->use_graph != h->opt.use_graph) || (opt->order != h->opt.order) ||
+                                (opt->inner_iters != h->opt.inner_iters);
         // finish work queued on the old stream before switching
         DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
         h->opt = *opt;

@@ -322,6 +322,8 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
         !std::isfinite(opt->alpha) || !std::isfinite(opt->beta) || opt->t < 0)
         return bfail(b, DSANLS_EINVAL, "bad power_iters, alpha, beta or t");
     if (opt->bound_clamp) return bfail(b, DSANLS_EINVAL, "the batched form has no bound clamp");
+    if (opt->inner_iters != 1 || opt->order != DSANLS_ORDER_PAPER)
+        return bfail(b, DSANLS_EINVAL, "the batched form takes one solver step per half in the paper's order");
     return bguard(b, [&]() {
         DSANLS_CUDA(cudaStreamSynchronize(b->stream()));
         b->opt = *opt;

@@ -90,9 +90,10 @@ void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, in
 void launch_step_size(const double *G64, int k, int iters, double alpha, double beta, const int64_t *t_dev,
                       double *scal, float *Gf, int kp, cudaStream_t s);
 // Z <- max(0, Z - eta (Z G - R)) (PGD) or Alg. 3 sweep (RCD), rows x k,
-// optional clamp at `bound` (> 0).  Sets *flag = 1 when a NaN/Inf appears.
+// optional clamp at `bound` (> 0); PGD with inner > 1 takes `inner` steps on
+// the proximal objective from Z.  Sets *flag = 1 when a NaN/Inf appears.
 void launch_update(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp,
-                   const double *scal, float bound, int *flag, cudaStream_t s);
+                   const double *scal, float bound, int inner, int *flag, cudaStream_t s);
 void launch_increment_t(int64_t *t_dev, int64_t by, cudaStream_t s);
 
 // ---- error.cu -------------------------------------------------------------

@@ -379,12 +379,29 @@ void mlp_unscale(MlpState &st, const int64_t *off, int ngroups, int64_t rows, fl
 }
 
 // ---------------------------------------------------------------------------
-// learned update of one half-step (k <= 32): thread per row
+// learned update of one half-step (k <= 32): one warp per row, lane c owns
+// column c of the row; (x G)_c = sum_l x_l G[l][c] with x_l broadcast from
+// lane l (an FMA chain in increasing l)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+constexpr int LF_THREADS = 256;
+
+DSANLS_DEV float row_times_g(float x, float init, const float (*gs)[33], int lane) {
+    float acc = init;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) acc = __fmaf_rn(__shfl_sync(0xffffffffu, x, l), gs[l][lane], acc);
+    return acc;
+}
+
+DSANLS_DEV float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(LF_THREADS)
     k_learned_finish(float *__restrict__ Z, const float *__restrict__ R, const float *__restrict__ y,
                      const float *__restrict__ beta, const float *__restrict__ s_g, const float *__restrict__ Gf,
-                     int kp, const double *__restrict__ scal, int64_t rows, int k, int pg_iters,
+                     int kp, const double *__restrict__ scal, int64_t rows, int k, int pg_iters, int plain_iters,
                      unsigned long long *__restrict__ kept, int *__restrict__ flag) {
     __shared__ float gs[32][33];
     for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
@@ -392,73 +409,52 @@ __global__ void __launch_bounds__(128)
         gs[a][c] = (a < k && c < k) ? Gf[a * kp + c] : 0.0f;
     }
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
+    const int lane = threadIdx.x & 31;
+    const bool on = lane < k;
     const float mu = (float)scal[1], eta = (float)scal[2];
-    const float scale = beta[r] / s_g[0];
-    float u[32], bb[32], x[32], xp[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        u[j] = j < k ? Z[r * k + j] : 0.0f;
-        const float rj = j < k ? R[r * k + j] : 0.0f;
-        bb[j] = __fmaf_rn(mu, u[j], rj);
-        x[j] = j < k ? y[r * k + j] * scale : 0.0f;
-    }
-    // plain step from u: xp = max(0, u - eta (u G - r))
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int l = 0; l < 32; ++l) acc = __fmaf_rn(u[l], gs[l][c], acc);
-        const float rc = bb[c] - mu * u[c];
-        const float v = __fmaf_rn(-eta, acc - rc, u[c]);
-        xp[c] = (c < k && v > 0.0f) ? v : 0.0f;
-    }
-    // correction: pg_iters projected-gradient steps on f from the network's point
-    for (int it = 0; it < pg_iters; ++it) {
-        float nx[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            float acc = mu * x[c];
-#pragma unroll
-            for (int l = 0; l < 32; ++l) acc = __fmaf_rn(x[l], gs[l][c], acc);
-            const float v = __fmaf_rn(-eta, acc - bb[c], x[c]);
-            nx[c] = (c < k && v > 0.0f) ? v : 0.0f;
-        }
-#pragma unroll
-        for (int c = 0; c < 32; ++c) x[c] = nx[c];
-    }
-    // objectives f(x) = 1/2 x^T (G + mu I) x - b^T x
-    float fx = 0.0f, fp = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        float ax = mu * x[c], ap = mu * xp[c];
-#pragma unroll
-        for (int l = 0; l < 32; ++l) {
-            ax = __fmaf_rn(x[l], gs[l][c], ax);
-            ap = __fmaf_rn(xp[l], gs[l][c], ap);
-        }
-        fx += x[c] * (0.5f * ax - bb[c]);
-        fp += xp[c] * (0.5f * ap - bb[c]);
-    }
-    const bool use_mlp = fx <= fp;
-    if (use_mlp) atomicAdd(kept, 1ull);
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        if (c < k) {
-            const float v = use_mlp ? x[c] : xp[c];
-            if (!(fabsf(v) <= 3.402823466e38f)) {
-                *flag = 1;
-                Z[r * k + c] = 0.0f;
-            } else {
-                Z[r * k + c] = v;
+    const float inv_s = 1.0f / s_g[0];
+    unsigned long long nkept = 0;
+    const int64_t nwarps = (int64_t)gridDim.x * (LF_THREADS / 32);
+    for (int64_t r = (int64_t)blockIdx.x * (LF_THREADS / 32) + (threadIdx.x >> 5); r < rows; r += nwarps) {
+        const float u = on ? Z[r * k + lane] : 0.0f;
+        const float rc = on ? R[r * k + lane] : 0.0f;
+        const float bb = __fmaf_rn(mu, u, rc);
+        float x = on ? y[r * k + lane] * (beta[r] * inv_s) : 0.0f;
+        // the plain path's update from u: one step of eq. gradient_descent, or
+        // plain_iters steps on f from u
+        float xp;
+        if (plain_iters <= 1) {
+            const float v = __fmaf_rn(-eta, row_times_g(u, 0.0f, gs, lane) - rc, u);
+            xp = (on && v > 0.0f) ? v : 0.0f;
+        } else {
+            xp = u;
+            for (int it = 0; it < plain_iters; ++it) {
+                const float v = __fmaf_rn(-eta, row_times_g(xp, mu * xp, gs, lane) - bb, xp);
+                xp = (on && v > 0.0f) ? v : 0.0f;
             }
         }
+        // correction: pg_iters projected-gradient steps on f from the network's point
+        for (int it = 0; it < pg_iters; ++it) {
+            const float v = __fmaf_rn(-eta, row_times_g(x, mu * x, gs, lane) - bb, x);
+            x = (on && v > 0.0f) ? v : 0.0f;
+        }
+        // objectives f(x) = 1/2 x^T (G + mu I) x - b^T x
+        const float fx = warp_sum(x * (0.5f * row_times_g(x, mu * x, gs, lane) - bb));
+        const float fp = warp_sum(xp * (0.5f * row_times_g(xp, mu * xp, gs, lane) - bb));
+        const bool use_mlp = fx <= fp;
+        nkept += use_mlp ? 1 : 0;
+        float v = use_mlp ? x : xp;
+        if (!(fabsf(v) <= 3.402823466e38f)) {
+            *flag = 1;
+            v = 0.0f;
+        }
+        if (on) Z[r * k + lane] = v;
     }
+    if (lane == 0 && nkept) atomicAdd(kept, nkept);
 }
 
 void mlp_learned_update(MlpState &st, float *Z, const float *R, int64_t rows, const double *G64, const float *Gf,
-                        int kp, const double *scal, int pg_iters, unsigned long long *kept, int *flag,
+                        int kp, const double *scal, int pg_iters, int plain_iters, unsigned long long *kept, int *flag,
                         cudaStream_t s) {
     const int k = st.k;
     // one group: G (fp32) and mu from the half-step
@@ -468,15 +464,17 @@ void mlp_learned_update(MlpState &st, float *Z, const float *R, int64_t rows, co
     k_rhs_b<<<nblk(rows * k), 256, 0, s>>>(R, Z, scal, rows * k, st.dout);
     DSANLS_LAUNCH_CHECK();
     mlp_forward(st, st.gf1, st.mu1, st.off1, 1, st.dout, rows, s);
-    k_learned_finish<<<(unsigned)ceil_div(rows, 128), 128, 0, s>>>(Z, R, st.y, st.beta, st.s, Gf, kp, scal, rows, k,
-                                                                   pg_iters, kept, flag);
+    const int64_t blocks = std::min<int64_t>(ceil_div(rows, LF_THREADS / 32), 152 * 8);
+    k_learned_finish<<<(unsigned)blocks, LF_THREADS, 0, s>>>(Z, R, st.y, st.beta, st.s, Gf, kp, scal, rows, k,
+                                                            pg_iters, plain_iters, kept, flag);
     DSANLS_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------------------
-// harvesting training triples: exact proximal minimiser by FISTA
+// harvesting training triples: exact proximal minimiser by FISTA (Beck and
+// Teboulle 2009), one warp per row as above
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(LF_THREADS)
     k_harvest(const float *__restrict__ Z, const float *__restrict__ R, const float *__restrict__ Gf, int kp,
               const double *__restrict__ scal, int64_t rows, int k, int iters, float *__restrict__ b_out,
               float *__restrict__ x_out) {
@@ -486,47 +484,33 @@ __global__ void __launch_bounds__(128)
         gs[a][c] = (a < k && c < k) ? Gf[a * kp + c] : 0.0f;
     }
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
+    const int lane = threadIdx.x & 31;
+    const bool on = lane < k;
     const float mu = (float)scal[1];
     const float step = (float)(1.0 / (scal[0] * 1.0001 + scal[1]));  // 1 / (lambda_max(G) + mu)
-    float bb[32], x[32], yv[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const float u = j < k ? Z[r * k + j] : 0.0f;
-        bb[j] = j < k ? __fmaf_rn(mu, u, R[r * k + j]) : 0.0f;
-        x[j] = u;
-        yv[j] = u;
-        if (j < k) b_out[r * k + j] = bb[j];
-    }
-    float tk = 1.0f;
-    for (int it = 0; it < iters; ++it) {
-        float nx[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            float acc = mu * yv[c];
-#pragma unroll
-            for (int l = 0; l < 32; ++l) acc = __fmaf_rn(yv[l], gs[l][c], acc);
-            const float v = yv[c] - step * (acc - bb[c]);
-            nx[c] = (c < k && v > 0.0f) ? v : 0.0f;
+    const int64_t nwarps = (int64_t)gridDim.x * (LF_THREADS / 32);
+    for (int64_t r = (int64_t)blockIdx.x * (LF_THREADS / 32) + (threadIdx.x >> 5); r < rows; r += nwarps) {
+        const float u = on ? Z[r * k + lane] : 0.0f;
+        const float bb = on ? __fmaf_rn(mu, u, R[r * k + lane]) : 0.0f;
+        if (on) b_out[r * k + lane] = bb;
+        float x = u, yv = u, tk = 1.0f;
+        for (int it = 0; it < iters; ++it) {
+            const float v = yv - step * (row_times_g(yv, mu * yv, gs, lane) - bb);
+            const float nx = (on && v > 0.0f) ? v : 0.0f;
+            const float tn = 0.5f * (1.0f + sqrtf(1.0f + 4.0f * tk * tk));
+            const float w = (tk - 1.0f) / tn;
+            yv = nx + w * (nx - x);
+            x = nx;
+            tk = tn;
         }
-        const float tn = 0.5f * (1.0f + sqrtf(1.0f + 4.0f * tk * tk));
-        const float w = (tk - 1.0f) / tn;
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            yv[c] = nx[c] + w * (nx[c] - x[c]);
-            x[c] = nx[c];
-        }
-        tk = tn;
+        if (on) x_out[r * k + lane] = x;
     }
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-        if (j < k) x_out[r * k + j] = x[j];
 }
 
 void mlp_harvest(const float *Z, const float *R, const float *Gf, int kp, const double *scal, int64_t rows, int k,
                  int iters, float *b_out, float *x_out, cudaStream_t s) {
-    k_harvest<<<(unsigned)ceil_div(rows, 128), 128, 0, s>>>(Z, R, Gf, kp, scal, rows, k, iters, b_out, x_out);
+    const int64_t blocks = std::min<int64_t>(ceil_div(rows, LF_THREADS / 32), 152 * 8);
+    k_harvest<<<(unsigned)blocks, LF_THREADS, 0, s>>>(Z, R, Gf, kp, scal, rows, k, iters, b_out, x_out);
     DSANLS_LAUNCH_CHECK();
 }
 

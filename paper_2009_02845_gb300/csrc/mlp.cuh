@@ -40,7 +40,7 @@ void mlp_adam(MlpState &st, float lr, cudaStream_t s);
 // Learned form of a half-step's update of Z (rows x k, k <= 32) from R, G (FP64 and
 // padded fp32 Gf with row stride kp) and scal = {lambda, mu, eta}; counts kept rows.
 void mlp_learned_update(MlpState &st, float *Z, const float *R, int64_t rows, const double *G64, const float *Gf,
-                        int kp, const double *scal, int pg_iters, unsigned long long *kept, int *flag,
+                        int kp, const double *scal, int pg_iters, int plain_iters, unsigned long long *kept, int *flag,
                         cudaStream_t s);
 // b = R + mu Z and the exact proximal minimiser x* (FISTA, `iters` steps) per row.
 void mlp_harvest(const float *Z, const float *R, const float *Gf, int kp, const double *scal, int64_t rows, int k,

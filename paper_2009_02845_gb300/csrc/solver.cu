@@ -76,25 +76,37 @@ __global__ void __launch_bounds__(GRAM_THREADS)
         if (threadIdx.x + q * GRAM_THREADS < npairs) out[pa[q] * k + pb[q]] = acc[q];
 }
 
-// One warp per pair (a <= b): lanes take every 32nd partial, then a fixed
-// shuffle tree; the result is written to G[a][b] and G[b][a].
-__global__ void k_gram_reduce(const double *__restrict__ part, int nparts, int k, double *__restrict__ G) {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+// 32 consecutive pairs (a <= b, row-major order of the upper triangle) per
+// CTA of 256 threads: warp w sums the partials c = w, w + 8, ... of every pair
+// (lane = pair; consecutive lanes read consecutive entries of a partial), then
+// thread p adds the eight warp sums in warp order.  A fixed order: the result
+// does not depend on scheduling.
+__global__ void __launch_bounds__(256)
+    k_gram_reduce(const double *__restrict__ part, int nparts, int k, double *__restrict__ G) {
+    __shared__ double ws[8][33];
     const int npairs = k * (k + 1) / 2;
-    if (warp >= npairs) return;
-    int a = 0, rem = (int)warp;
-    while (rem >= k - a) {
-        rem -= k - a;
-        ++a;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
+    int a = 0, b = 0;
+    if (p < npairs) {
+        int rem = p;
+        while (rem >= k - a) {
+            rem -= k - a;
+            ++a;
+        }
+        b = a + rem;
     }
-    const int b = a + rem;
     double acc = 0.0;
-    for (int c = lane; c < nparts; c += 32) acc += part[(int64_t)c * k * k + a * k + b];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-        G[a * k + b] = acc;
-        G[b * k + a] = acc;
+    if (p < npairs)
+        for (int c = warp; c < nparts; c += 8) acc += part[(int64_t)c * k * k + a * k + b];
+    ws[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && p < npairs) {
+        double tot = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) tot += ws[w][lane];
+        G[a * k + b] = tot;
+        G[b * k + a] = tot;
     }
 }
 
@@ -113,7 +125,7 @@ void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, in
     k_gram_partial<<<(unsigned)grid, GRAM_THREADS, smem, s>>>(W, k, d, dc, work);
     DSANLS_LAUNCH_CHECK();
     const int64_t npairs = (int64_t)k * (k + 1) / 2;
-    k_gram_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, s>>>(work, (int)grid, k, G64);
+    k_gram_reduce<<<(unsigned)ceil_div(npairs, 32), 256, 0, s>>>(work, (int)grid, k, G64);
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -352,7 +364,7 @@ DSANLS_DEV void stage_flat(float *dst, const float *src, int n) {
 template <int KP>
 __global__ void __launch_bounds__(256)
     k_update_pgd_tiled(float *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k,
-                       const float *__restrict__ Gf, const double *__restrict__ scal, float bound,
+                       const float *__restrict__ Gf, const double *__restrict__ scal, float bound, int inner,
                        int *__restrict__ flag) {
     constexpr int TN = KP / 16;
     constexpr int LDG = KP + 4;
@@ -372,52 +384,68 @@ __global__ void __launch_bounds__(256)
     cp_async_wait<1>();  // the Z tile
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float acc[4][TN];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
+    const float eta = (float)scal[2];
+    const float mu = (float)scal[1];
     const float *z0 = zr + (ty * 4) * k;
-#pragma unroll 2
-    for (int l = 0; l < k; ++l) {
-        const float zv[4] = {z0[l], z0[k + l], z0[2 * k + l], z0[3 * k + l]};
-        float gv[TN];
-        const float *gl = gs + l * LDG;
-        if constexpr (TN >= 4) {
-#pragma unroll
-            for (int j = 0; j < TN / 4; ++j) {
-                const float4 g4 = *reinterpret_cast<const float4 *>(gl + j * 64 + tx * 4);
-                gv[4 * j] = g4.x;
-                gv[4 * j + 1] = g4.y;
-                gv[4 * j + 2] = g4.z;
-                gv[4 * j + 3] = g4.w;
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < TN; ++b) gv[b] = gl[tx * TN + b];
-        }
+    for (int it = 0; it < inner; ++it) {
+        float acc[4][TN];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < TN; ++b) acc[a][b] = __fmaf_rn(zv[a], gv[b], acc[a][b]);
-    }
-    cp_async_wait<0>();  // the R tile
-    __syncthreads();     // every thread is done reading the old Z tile
-    const float eta = (float)scal[2];
+            for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
+#pragma unroll 2
+        for (int l = 0; l < k; ++l) {
+            const float zv[4] = {z0[l], z0[k + l], z0[2 * k + l], z0[3 * k + l]};
+            float gv[TN];
+            const float *gl = gs + l * LDG;
+            if constexpr (TN >= 4) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = ty * 4 + a;
-        if (i >= nr) continue;
+                for (int j = 0; j < TN / 4; ++j) {
+                    const float4 g4 = *reinterpret_cast<const float4 *>(gl + j * 64 + tx * 4);
+                    gv[4 * j] = g4.x;
+                    gv[4 * j + 1] = g4.y;
+                    gv[4 * j + 2] = g4.z;
+                    gv[4 * j + 3] = g4.w;
+                }
+            } else {
 #pragma unroll
-        for (int b = 0; b < TN; ++b) {
-            const int c = upd_col<TN>(tx, b);
-            if (c < k) {
-                const float grad = __fsub_rn(acc[a][b], rr[i * k + c]);
-                zr[i * k + c] = project_clamp(__fmaf_rn(-eta, grad, zr[i * k + c]), bound, flag);
+                for (int b = 0; b < TN; ++b) gv[b] = gl[tx * TN + b];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < TN; ++b) acc[a][b] = __fmaf_rn(zv[a], gv[b], acc[a][b]);
+        }
+        if (it == 0) {
+            cp_async_wait<0>();  // the R tile
+            __syncthreads();     // every thread is done reading the Z tile
+            if (inner > 1) {
+                // b = r + mu u, kept in the R tile for the steps on the proximal objective
+                for (int e = threadIdx.x; e < n; e += 256) rr[e] = __fmaf_rn(mu, zr[e], rr[e]);
+                __syncthreads();
+            }
+        } else {
+            __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = ty * 4 + a;
+            if (i >= nr) continue;
+#pragma unroll
+            for (int b = 0; b < TN; ++b) {
+                const int c = upd_col<TN>(tx, b);
+                if (c < k) {
+                    const float x = zr[i * k + c];
+                    // one step: the gradient of eq. gradient_descent (r in the tile);
+                    // several: (G + mu I) x - (r + mu u) (b in the tile)
+                    const float grad = inner > 1 ? __fsub_rn(__fmaf_rn(mu, x, acc[a][b]), rr[i * k + c])
+                                                 : __fsub_rn(acc[a][b], rr[i * k + c]);
+                    zr[i * k + c] = project_clamp(__fmaf_rn(-eta, grad, x), bound, flag);
+                }
             }
         }
+        __syncthreads();  // the new rows are complete before the next product reads them
     }
-    __syncthreads();
     float *zo = Z + r0 * k;
     const int n4 = n >> 2;
     for (int e = threadIdx.x; e < n4; e += 256)
@@ -427,10 +455,11 @@ __global__ void __launch_bounds__(256)
 
 template <int KP>
 static void update_kp(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf,
-                      const double *scal, float bound, int *flag, cudaStream_t s) {
+                      const double *scal, float bound, int inner, int *flag, cudaStream_t s) {
     if (solver == 0) {
         const size_t smem_t = ((size_t)k * (KP + 4) + 2 * 64 * (size_t)k) * sizeof(float);
-        k_update_pgd_tiled<KP><<<(unsigned)ceil_div(rows, 64), 256, smem_t, s>>>(Z, R, rows, k, Gf, scal, bound, flag);
+        k_update_pgd_tiled<KP><<<(unsigned)ceil_div(rows, 64), 256, smem_t, s>>>(Z, R, rows, k, Gf, scal, bound, inner,
+                                                                               flag);
         DSANLS_LAUNCH_CHECK();
         return;
     }
@@ -458,16 +487,17 @@ void prime_solver_attributes(int max_smem) {
 }
 
 void launch_update(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp,
-                   const double *scal, float bound, int *flag, cudaStream_t s) {
+                   const double *scal, float bound, int inner, int *flag, cudaStream_t s) {
     if (rows <= 0) return;
+    if (inner < 1 || (inner > 1 && solver != 0)) throw ArgError{"launch_update: inner steps need PGD"};
     if (kp <= 16)
-        update_kp<16>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+        update_kp<16>(solver, Z, R, rows, k, Gf, scal, bound, inner, flag, s);
     else if (kp <= 32)
-        update_kp<32>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+        update_kp<32>(solver, Z, R, rows, k, Gf, scal, bound, inner, flag, s);
     else if (kp <= 64)
-        update_kp<64>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+        update_kp<64>(solver, Z, R, rows, k, Gf, scal, bound, inner, flag, s);
     else
-        update_kp<128>(solver, Z, R, rows, k, Gf, scal, bound, flag, s);
+        update_kp<128>(solver, Z, R, rows, k, Gf, scal, bound, inner, flag, s);
 }
 
 }  // namespace dsanls

@@ -492,24 +492,32 @@ PlainPlan plan_one_wave(int64_t rows, int64_t K, int64_t N, int bnt) {
     return finish_plan(tiles, nk, (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, ceil_div(152, tiles))));
 }
 
-// Streaming products (R = X P): the split count that best fills whole waves
-// of `slots` resident CTAs, with at least 16 k-blocks per split; among
-// counts within 2 % of the best fill, the smallest (fewer partial sums).
+// Streaming products (R = X P): the split count with the lowest estimated time
+// under a simple model -- whole waves of `slots` resident CTAs, each CTA
+// streaming its 128 x K/splits slab of X at 1/slots of the HBM bandwidth plus
+// a fixed per-CTA cost (prologue, TMEM allocation, epilogue), plus writing
+// and re-reading the split partials of R -- with at least 16 k-blocks per
+// split.
 PlainPlan plan_stream(int64_t rows, int64_t K, int64_t N, int bnt, int slots) {
     const int64_t tiles = ceil_div(rows, BM) * ceil_div(N, bnt);
     const int nk = (int)ceil_div(K, BK);
     const int max_s = std::max(1, std::min(16, nk / 16));
-    double fill[17] = {0};
-    double best = 0.0;
+    const double bw = 6.8e12, per_cta = 3.0e-6;
+    const double x_bytes = 2.0 * (double)ceil_div(rows, BM) * BM * (double)K;
+    double best_t = 1e30;
+    int best_s = 1;
     for (int sp = 1; sp <= max_s; ++sp) {
         const PlainPlan p = finish_plan(tiles, nk, sp);
-        const double waves = (double)(p.tiles * p.splits) / slots;
-        fill[sp] = waves / std::ceil(waves);
-        best = std::max(best, fill[sp]);
+        const double ctas = (double)(p.tiles * p.splits);
+        const double waves = std::ceil(ctas / slots);
+        const double t = waves * ((x_bytes / ctas) / (bw / slots) + per_cta) +
+                         2.0 * p.splits * (double)rows * (double)N * 4.0 / bw;
+        if (t < best_t * 0.999) {
+            best_t = t;
+            best_s = sp;
+        }
     }
-    for (int sp = 1; sp <= max_s; ++sp)
-        if (fill[sp] >= best - 0.02) return finish_plan(tiles, nk, sp);
-    return finish_plan(tiles, nk, 1);
+    return finish_plan(tiles, nk, best_s);
 }
 
 constexpr int kSkinnySlots = 2 * 152;  // two 96 KB CTAs per SM

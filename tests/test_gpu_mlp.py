@@ -104,11 +104,15 @@ def test_harvest_matches_oracle(pkg):
     assert _rel(x, xs) <= 1e-3
 
 
-def test_learned_half_step_matches_oracle(pkg):
+@pytest.mark.parametrize("plain_iters", [1, 6])
+def test_learned_half_step_matches_oracle(pkg, plain_iters):
+    """Every row holds the oracle's chosen candidate; the fallback is the plain
+    path's update (one step, or plain_iters steps on the proximal objective)."""
     m, n, k, d, hidden = 500, 350, 16, 80, 64
     net = pkg.MLP(k, hidden, max_rows=1024, max_groups=4, seed=11)
     P = omlp.unflatten(method.round_bf16(net.params()), k, hidden)
     h, M = _handle(pkg, m, n, k, d, 7)
+    h.set_options(inner_iters=plain_iters)
     h.set_mlp(net, pg_iters=3)
     h.half_step(0)
     U1, _ = h.factors()
@@ -119,7 +123,7 @@ def test_learned_half_step_matches_oracle(pkg):
     _, _, Go, Ro = method.sketched_terms(M.astype(np.float64), V0.astype(np.float64), S)
     mu = method.mu_t(1.0, 1.0, 2)
     eta = 1.0 / (method.lambda_max(Go) + mu)
-    xm, xp, fm, fp = omlp.learned_candidates(P, Go, mu, Ro, U0.astype(np.float64), eta, 3)
+    xm, xp, fm, fp = omlp.learned_candidates(P, Go, mu, Ro, U0.astype(np.float64), eta, 3, plain_iters)
     chosen = np.where((fm <= fp)[:, None], xm, xp)
     other = np.where((fm <= fp)[:, None], xp, xm)
     tie = np.abs(fm - fp) <= 1e-5 * np.maximum(np.abs(fm), np.abs(fp))

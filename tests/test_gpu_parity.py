@@ -281,3 +281,37 @@ def test_run_is_deterministic(pkg):
         outs.append(h.factors())
         h.close()
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("inner", [2, 16])
+@pytest.mark.parametrize("case", [(333, 257, 10, 40, 50), (640, 515, 64, 130, 129), (300, 260, 100, 96, 96)])
+def test_pgd_inner_iterations(pkg, case, inner):
+    """inner_iters projected-gradient steps on the proximal row objective per
+    half-step against the oracle's pgd_inner (FP32 vs FP64, 1e-5)."""
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 3)
+    U, V = initial_factors(m, n, k, 4)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=5, d_v=d_v, t=3, inner_iters=inner)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 5, 3, side, X.shape[1], dd)
+        want = method.half_step(X, Y, Z, S, method.PGD, method.mu_t(1.0, 1.0, 3), inner_iters=inner)
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
+def test_inner_iterations_need_pgd(pkg):
+    h = pkg.DSANLS(64, 48, 4, 16, pkg.GAUSSIAN, seed=0)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(solver=pkg.RCD, inner_iters=4)
+    with pytest.raises(pkg.DSANLSError):
+        h.set_options(inner_iters=0)
+    h.close()

@@ -439,3 +439,60 @@ def test_identity_bf16_model_is_exact_on_representable_inputs():
     _, B, G, R = method.sketched_terms_bf16(X, Y, S)
     _, Be, Ge, Re = method.sketched_terms(X, Y, S)
     assert np.array_equal(B, Be) and np.array_equal(G, Ge) and np.array_equal(R, Re)
+
+
+# --------------------------------------------------------------------------
+# several projected-gradient steps on the proximal subproblem
+# --------------------------------------------------------------------------
+
+def _prox_problem(seed=3, rows=40, k=5):
+    M, U, V = _problem(rows, 30, k, seed)
+    S = method.Sketch(method.GAUSSIAN, seed, 2, 0, 30, 12)
+    _, _, G, R = method.sketched_terms(M, V, S)
+    mu = 0.7
+    eta = 1.0 / (method.lambda_max(G) + mu)
+    return U, G, R, mu, eta
+
+
+def test_one_inner_step_is_the_paper_step():
+    U, G, R, mu, eta = _prox_problem()
+    a = method.pgd_inner(U, G, R, eta, mu, 1)
+    b = method.pgd_update(U, G, R, eta)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+def test_inner_steps_reach_the_exact_proximal_minimiser():
+    """Many steps converge to the minimiser of 1/2 x^T (G + mu I) x - (r + mu u)^T x
+    over x >= 0, computed independently by the Lawson-Hanson active-set method."""
+    from oracle import mlp as omlp
+    U, G, R, mu, eta = _prox_problem()
+    x = method.pgd_inner(U, G, R, eta, mu, 20000)
+    xs = omlp.prox_exact(G, mu, R + mu * U)
+    assert np.max(np.abs(x - xs)) <= 1e-7 * max(1.0, np.max(np.abs(xs)))
+
+
+def test_inner_steps_descend():
+    from oracle import mlp as omlp
+    U, G, R, mu, eta = _prox_problem(5)
+    b = R + mu * U
+    f_prev = omlp.prox_objective(G, mu, b, U)
+    for p in range(1, 12):
+        f = omlp.prox_objective(G, mu, b, method.pgd_inner(U, G, R, eta, mu, p))
+        assert np.all(f <= f_prev + 1e-9 * np.abs(f_prev))
+        f_prev = f
+
+
+def test_mutant_inner_prox_sign_is_caught():
+    """b = r - mu u instead of r + mu u: no longer the minimiser of eq. reg_sub."""
+    from oracle import mlp as omlp
+
+    def bad_inner(Z, G, R, eta, mu, iters, bound=None):
+        b = R - mu * Z
+        x = Z
+        for _ in range(iters):
+            x = method.project(x - eta * (x @ G + mu * x - b), bound)
+        return x
+    U, G, R, mu, eta = _prox_problem()
+    x = bad_inner(U, G, R, eta, mu, 20000)
+    xs = omlp.prox_exact(G, mu, R + mu * U)
+    assert np.max(np.abs(x - xs)) > 1e-3 * max(1.0, np.max(np.abs(xs)))

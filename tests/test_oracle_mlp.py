@@ -134,3 +134,24 @@ def test_perfect_warm_start_is_a_fixed_point():
     for _ in range(5):
         x = np.maximum(x - eta * (x @ Gm - b), 0.0)
     assert np.allclose(x, xs, atol=1e-9)
+
+
+def test_learned_fallback_with_plain_inner_steps():
+    """With plain_iters = p the fallback candidate is the plain path's p-step
+    update (method.pgd_inner) and the learned update is never worse than it."""
+    from oracle import method
+    g = np.random.default_rng(12)
+    k, hidden = 6, 16
+    theta = g.standard_normal(sum(int(np.prod(s)) for _, s in mlp.param_shapes(k, hidden))) * 0.1
+    P = mlp.unflatten(theta, k, hidden)
+    B = g.random((k, 3 * k))
+    G = B @ B.T
+    R = g.random((30, k)) * 3.0
+    Z = g.random((30, k))
+    mu = 0.4
+    eta = 1.0 / (method.lambda_max(G) + mu)
+    _, xp, fm, fp = mlp.learned_candidates(P, G, mu, R, Z, eta, 3, plain_iters=5)
+    assert np.allclose(xp, method.pgd_inner(Z, G, R, eta, mu, 5), rtol=1e-12, atol=1e-12)
+    x, keep = mlp.learned_update(P, G, mu, R, Z, eta, 3, plain_iters=5)
+    b = R + mu * Z
+    assert np.all(mlp.prox_objective(G, mu, b, x) <= mlp.prox_objective(G, mu, b, xp) + 1e-12)
