@@ -580,14 +580,38 @@ def run_learned(args, w):
         del M
     triples = sum(p[2].shape[0] for p in pool)
     harvest_s = time.perf_counter() - t0
+
+    def norm_target(G, mu, b, x):
+        # y* = x* s / beta, s = tr(G + mu I) / k, beta = ||b|| / sqrt(k) (1 if zero)
+        s_ = (torch.trace(G) + k * mu[0]) / k
+        beta = b.norm(dim=1) / math.sqrt(k)
+        beta = torch.where(beta > 0, beta, torch.ones_like(beta))
+        return x * (s_ / beta)[:, None]
+
+    def val_loss():
+        # 1/2 mean ||y - y*||^2 in normalised units on the held-out groups (every 10th)
+        tot, cnt = 0.0, 0
+        for G, mu, b, x in pool[5::10]:
+            bb, xx = b[-512:], x[-512:]
+            off1 = torch.tensor([0, bb.shape[0]], dtype=torch.int64, device="cuda")
+            pred = net.predict(G[None], mu, off1, bb)
+            tot += 0.5 * float(((norm_target(G, mu, bb, pred) - norm_target(G, mu, bb, xx)) ** 2).sum(1).mean())
+            cnt += 1
+        return tot / cnt
+
+    ynorm = torch.cat([norm_target(G, mu, b, x).norm(dim=1) for G, mu, b, x in pool[5::10]])
+    target_stats = {"p50": float(ynorm.median()), "p99": float(torch.quantile(ynorm.float(), 0.99)),
+                    "max": float(ynorm.max()), "zero_loss": float(0.5 * (ynorm ** 2).mean())}
+    val_before = val_loss()
     # -- train: 16 groups x 512 rows per step, Adam with a cosine learning rate
     t0 = time.perf_counter()
     g = np.random.default_rng(0)
     losses = []
     steps = args.train_steps
     groups, rows_per = 16, 512
+    train_ids = np.array([i for i in range(len(pool)) if i % 10 != 5])
     for step in range(steps):
-        pick = g.choice(len(pool), groups, replace=False)
+        pick = g.choice(train_ids, groups, replace=False)
         bs, xs = [], []
         for i in pick:
             r0 = int(g.integers(0, pool[i][2].shape[0] - rows_per + 1))
@@ -599,16 +623,22 @@ def run_learned(args, w):
         lr = 1e-5 + 0.5 * (1e-3 - 1e-5) * (1.0 + math.cos(math.pi * step / steps))
         losses.append(net.train_step(G, mu, off, torch.cat(bs), torch.cat(xs), lr))
     train_s = time.perf_counter() - t0
+    val_after = val_loss()
     del pool
     # -- evaluate on the held-out seed
     from synthdata import planted_dense
     M, _, _ = planted_dense(m, n, k, 21, zero_frac=0.7)
 
-    def run(prec, learned, inner=1, pg_iters=PG_ITERS):
+    # a network with all parameters zero proposes x0 = 0: the learned form with it
+    # measures what restarting the correction steps from zero gains by itself
+    net0 = pkg.MLP(k, hidden, max_rows=max(m, n), max_groups=1, seed=0)
+    net0.set_params(np.zeros(net0.n_params, np.float32))
+
+    def run(prec, learned, inner=1, pg_iters=PG_ITERS, network=None):
         h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=21, precision=prec, use_graph=1, inner_iters=inner)
         h.set_dense(M)
         if learned:
-            h.set_mlp(net, pg_iters=pg_iters)
+            h.set_mlp(network if network is not None else net, pg_iters=pg_iters)
         total, hist, hit = 0.0, [], None
         for it in range(t_max):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -634,7 +664,9 @@ def run_learned(args, w):
     res = {"fp32_plain": run(pkg.FP32, False), "bf16": run(pkg.BF16, False),
            "bf16_learned": run(pkg.BF16, True, 1),
            "bf16_inner%d" % INNER: run(pkg.BF16, False, INNER),
-           "bf16_learned_inner%d" % INNER: run(pkg.BF16, True, INNER)}
+           "bf16_learned_inner%d" % INNER: run(pkg.BF16, True, INNER),
+           "bf16_zero_network_inner%d" % INNER: run(pkg.BF16, True, INNER, network=net0)}
+    net0.close()
     base = res["fp32_plain"]["to_eps"]
     best = res["bf16_learned_inner%d" % INNER]["to_eps"]
     value = (1.0 / best["seconds"]) if best else 0.0
@@ -647,7 +679,8 @@ def run_learned(args, w):
                    "harvest_iterations": points, "rows_per_step": groups * rows_per, "hidden": hidden,
                    "pg_iters": PG_ITERS, "inner_iters": INNER},
         "harvest_s": harvest_s, "train_s": train_s, "loss_first": float(np.mean(losses[:20])),
-        "loss_last": float(np.mean(losses[-20:])), "results": res,
+        "loss_last": float(np.mean(losses[-20:])), "val_loss_before": val_before, "val_loss_after": val_after,
+        "target_norm": target_stats, "results": res,
         "speedup_time_to_eps_vs_fp32": (base["seconds"] / best["seconds"]) if (base and best) else None,
     }), flush=True)
     net.close()
@@ -679,8 +712,9 @@ def run_compare(args, w):
         ("sanls_subsample_pgd_fp32", S_, d, d, pkg.PGD, pkg.FP32, 0, 1.0, 1.0),
         ("sanls_subsample_rcd_fp32", S_, d, d, pkg.RCD, pkg.FP32, 0, 1.0, 1.0),
         ("plain_pg_bf16", I_, n, m, pkg.PGD, pkg.BF16, 0, 1.0, 1.0),
-        ("hals_bf16", I_, n, m, pkg.RCD, pkg.BF16, 0, 0.0, 0.0),
-        ("hals_fp32", I_, n, m, pkg.RCD, pkg.FP32, 0, 0.0, 0.0),
+        # HALS: mu_t = 1e-6 only guards the division when a column of the fixed factor is zero
+        ("hals_bf16", I_, n, m, pkg.RCD, pkg.BF16, 0, 1e-6, 0.0),
+        ("hals_fp32", I_, n, m, pkg.RCD, pkg.FP32, 0, 1e-6, 0.0),
     ]
     res = {}
     for name, sk, dd, ddv, solver, prec, order, alpha, beta, *inner in forms:

@@ -115,7 +115,7 @@ int dsanls_default_options(dsanls_options *opt);
  * U-half (and, unless set_options overrides d_v, for the V-half).
  * seed keys the Philox field (S^t, S'^t, default U^0, V^0; Section 3.3's
  * shared seed).  Requires m, n >= 1, 1 <= k <= 128, d >= 1; for SUBSAMPLE
- * d <= n and d <= 16384; for IDENTITY d == n.  Factors start as the default
+ * d <= n; for IDENTITY d == n.  Factors start as the default
  * Uniform[0,1) draws of streams 2 and 3.  EINVAL, ENOMEM, ECUDA. */
 int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kind,
                   uint64_t seed, dsanls_t *out);
@@ -231,7 +231,7 @@ int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t 
 /* The d column indices of a subsampling sketch (Section 3.4: columns drawn
  * uniformly without replacement), ascending: {pi(0), ..., pi(d-1)} for the
  * 4-round Feistel permutation pi of {0..n-1} keyed by (seed, t, side) with
- * cycle walking.  1 <= d <= min(n, 16384). */
+ * cycle walking.  1 <= d <= n. */
 int dsanls_subsample_indices(uint64_t seed, uint32_t side, uint64_t t, int64_t n, int32_t d,
                              int32_t *J, void *stream);
 

@@ -193,6 +193,31 @@ def sketched_terms_fp8(X, Y, S, seed, t, side):
     return A, B, G, R
 
 
+def quantise_rows_e4m3(X):
+    """Per row: scale = max|x| / 448 (binary32, 1 if zero) and Xq = e4m3(x / scale)
+    (binary32 division); returns the dequantised FP64 X."""
+    X32 = np.asarray(X, dtype=np.float32)
+    out = np.empty(X32.shape, dtype=np.float64)
+    for r in range(X32.shape[0]):
+        mx = np.float32(np.max(np.abs(X32[r]))) if X32.shape[1] else np.float32(0.0)
+        sc = np.float32(mx / np.float32(448.0)) if mx > 0 else np.float32(1.0)
+        out[r] = round_e4m3(X32[r] / sc) * np.float64(sc)
+    return out
+
+
+def sketched_terms_reassociated_fp8(X, Y, S):
+    """The reassociated order with an fp8 streaming product: B and P^T = B S^T
+    as in the bf16 model but P^T kept in binary32, then quantised per row of
+    P^T (one scale per column of P) to E4M3; X quantised per 128-row block to
+    E4M3; R = Xq P_q.  G = B B^T from the unrounded B."""
+    Sb = round_bf16(S.dense32)
+    B = round_bf16(Y).T @ Sb
+    G = B @ B.T
+    Pt = (round_bf16(B) @ Sb.T).astype(np.float32)
+    R = quantise_rowblocks_e4m3(X) @ quantise_rows_e4m3(Pt).T
+    return None, B, G, R
+
+
 def sketched_terms(X, Y, S):
     """A = X S, B = Y^T S, G = B B^T, R = A B^T  (eq. def_A_B; gradient terms of
     eq. gradient_descent).  X: rows x n data (M or M^T), Y: n x k fixed factor."""
@@ -282,7 +307,9 @@ def half_step(X, Y, Z, S, solver, mu, power_iters=32, bound=None, rows=None, bf1
     if rows is not None:
         X = X[rows]
         Z = Z[rows]
-    if reassociate:
+    if reassociate and fp8 is not None:
+        A, B, G, R = sketched_terms_reassociated_fp8(X, Y, S)
+    elif reassociate:
         A, B, G, R = (sketched_terms_reassociated_bf16 if bf16 else sketched_terms_reassociated)(X, Y, S)
     elif fp8 is not None:  # fp8 = (seed, t, side) of the sketch, to redraw its unit-variance values
         A, B, G, R = sketched_terms_fp8(X, Y, S, *fp8)

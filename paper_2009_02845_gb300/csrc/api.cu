@@ -173,8 +173,8 @@ int fail(dsanls_ctx *h, int code, const std::string &msg) {
 
 void check_sketch(int kind, int64_t K, int64_t dd, const char *what) {
     if (dd < 1) throw ArgError{std::string(what) + " must be >= 1"};
-    if (kind == DSANLS_SKETCH_SUBSAMPLE && (dd > K || dd > 16384))
-        throw ArgError{std::string(what) + ": subsampling needs sketch size <= dimension and <= 16384"};
+    if (kind == DSANLS_SKETCH_SUBSAMPLE && dd > K)
+        throw ArgError{std::string(what) + ": subsampling needs sketch size <= dimension"};
     if (kind == DSANLS_SKETCH_IDENTITY && dd != K)
         throw ArgError{std::string(what) + ": the identity sketch needs sketch size == dimension"};
     if (dd > (1 << 30)) throw ArgError{std::string(what) + " too large"};
@@ -224,7 +224,7 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->R, std::max(m, n) * k);
     dalloc(h->Rpart, (gauss && bf16 && !reas) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
     dalloc(h->Sq, (gauss && fp8) ? std::max(n * h->d, m * dv) : 0);
-    dalloc(h->bits, (h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE) ? ceil_div(std::max(m, n), 32) + 1 : 0);
+    dalloc(h->bits, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? ceil_div(std::max(m, n), 32) + 1 : 0);
     std::copy(key, key + 7, h->cfg_key);
 }
 
@@ -271,7 +271,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         if (fp8)
             launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, rade, s);
         else if (tc && reas)
-            launch_gaussian_pair(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sn, rade, s);
+            launch_gaussian_pair(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sn, rade, 0, s);
         else if (tc)
             launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, rade,
                                                  s);
@@ -353,7 +353,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     } else if (h->sketch == DSANLS_SKETCH_SUBSAMPLE) {
         const float c = (float)std::sqrt((double)K / (double)dd);
         const float c2 = c * c;
-        launch_subsample(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, h->J, s);
+        launch_subsample(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, h->J, h->bits, s);
         mark(pe, DSANLS_PHASE_B, s);
         launch_gather_w(Y, k, h->J, dd, c, h->W, s);
         mark(pe, DSANLS_PHASE_PRODUCT, s);
@@ -367,7 +367,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             launch_sgemm(g, s);
         } else {
             mark(pe, DSANLS_PHASE_RHS, s);
-            launch_sampled_spmm(xp, xc, xv, rows, h->J, dd, K, h->bits, Y, k, c2, h->R, h->lr[side], s);
+            launch_sampled_spmm(xp, xc, xv, rows, h->bits, Y, k, c2, h->R, h->lr[side], s);
         }
     } else {  // identity
         mark(pe, DSANLS_PHASE_B, s);
@@ -550,7 +550,7 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
     if (m < 1 || n < 1 || k < 1 || k > 128 || d < 1) return DSANLS_EINVAL;
     if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return DSANLS_EINVAL;
     if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_RADEMACHER) return DSANLS_EINVAL;
-    if (sketch_kind == DSANLS_SKETCH_SUBSAMPLE && (d > n || d > 16384)) return DSANLS_EINVAL;
+    if (sketch_kind == DSANLS_SKETCH_SUBSAMPLE && d > n) return DSANLS_EINVAL;
     if (sketch_kind == DSANLS_SKETCH_IDENTITY && d != n) return DSANLS_EINVAL;
     dsanls_ctx *h = nullptr;
     try {
@@ -1059,9 +1059,19 @@ int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t 
 
 int dsanls_subsample_indices(uint64_t seed, uint32_t side, uint64_t t, int64_t n, int32_t d, int32_t *J,
                              void *stream) {
-    if (n < 1 || n > (1ll << 31) - 1 || d < 1 || d > n || d > 16384 || !J || side > 0xef) return DSANLS_EINVAL;
+    if (n < 1 || n > (1ll << 31) - 1 || d < 1 || d > n || !J || side > 0xef) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
-        launch_subsample(seed, side, t, nullptr, n, d, J, (cudaStream_t)stream);
+        uint32_t *bits = nullptr;  // scratch bitmap of this call
+        DSANLS_CUDA(cudaMalloc((void **)&bits, (size_t)ceil_div(n, 32) * sizeof(uint32_t)));
+        try {
+            launch_subsample(seed, side, t, nullptr, n, d, J, bits, (cudaStream_t)stream);
+        } catch (...) {
+            cudaFree(bits);
+            throw;
+        }
+        const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        cudaFree(bits);
+        DSANLS_CUDA(e);
         return DSANLS_OK;
     });
 }

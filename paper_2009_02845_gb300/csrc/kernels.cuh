@@ -42,11 +42,14 @@ void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows,
 // S^T (cols x rows) as bf16 of z * scale and as fp8 E4M3 of z (t from t_dev).
 void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
                           __nv_bfloat16 *out_b, uint8_t *out_q, bool rademacher, cudaStream_t s);
-// bf16 of z * scale as S^T (out_t, cols x rows) and S (out_n, rows x cols), t from t_dev.
+// bf16 of z * scale as S^T (out_t, cols x rows) and S (out_n, rows x cols), t from t_dev;
+// max_ctas > 0 caps the grid (the CTAs then walk the tiles).
 void launch_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, bool rademacher, cudaStream_t s);
+                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, bool rademacher, int max_ctas, cudaStream_t s);
+// J (d entries, ascending) = the sampled columns of {0..n-1}; bits (ceil(n/32)
+// words, scratch) is left holding their membership bitmap.
 void launch_subsample(uint64_t seed, uint32_t side, uint64_t t, const int64_t *t_dev, int64_t n, int d,
-                      int32_t *J, cudaStream_t s);
+                      int32_t *J, uint32_t *bits, cudaStream_t s);
 
 // ---- gemm_simt.cu ---------------------------------------------------------
 // C[i][j] = alpha * sum_l a(i,l) b(l,j) over l in [0,K), binary32 FMA chain in
@@ -137,10 +140,10 @@ struct LongRows {
     float *partial = nullptr;
 };
 // out[i][0..k) = alpha * sum over entries e of row i with col_e in J of val_e * Y[col_e][0..k)
-// (CSR order; long rows summed chunk by chunk, chunks in order); bits is
-// scratch of ceil(K/32) words, K = number of columns; k <= 128.
-void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows, const int32_t *J,
-                         int d, int64_t K, uint32_t *bits, const float *Y, int k, float alpha, float *out,
-                         const LongRows &lr, cudaStream_t s);
+// (CSR order; long rows summed chunk by chunk, chunks in order); bits is the
+// membership bitmap of J over the columns (as left by launch_subsample); k <= 128.
+void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
+                         const uint32_t *bits, const float *Y, int k, float alpha, float *out, const LongRows &lr,
+                         cudaStream_t s);
 
 }  // namespace dsanls

@@ -8,8 +8,10 @@
 //    the four values of a block next to each other (one 16-byte store).
 //  * subsampling: d indices pi(0..d-1) of a keyed 4-round Feistel permutation
 //    on 2h-bit words restricted to {0..n-1} by cycle walking (Black and
-//    Rogaway 2002), then sorted ascending in one CTA (bitonic network in
-//    shared memory).
+//    Rogaway 2002), marked in a bitmap of the n columns and listed in
+//    ascending order.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -105,46 +107,54 @@ __global__ void __launch_bounds__(256)
                     __nv_bfloat16 *__restrict__ out_t, __nv_bfloat16 *__restrict__ out_n) {
     __shared__ __align__(16) __nv_bfloat16 tile[PAIR_COLS][PAIR_LD];
     const uint64_t t = (uint64_t)*t_dev;
-    const int64_t r0 = (int64_t)blockIdx.y * PAIR_ROWS, c0 = (int64_t)blockIdx.x * PAIR_COLS;
+    const int64_t tiles_x = (cols + PAIR_COLS - 1) / PAIR_COLS;
+    const int64_t ntiles = tiles_x * ((rows + PAIR_ROWS - 1) / PAIR_ROWS);
     const int qi = threadIdx.x & 31, cj = threadIdx.x >> 5;
-    const int64_t q = (r0 >> 2) + qi;
     const bool vec = (rows & 3) == 0;
-    for (int cc = cj; cc < PAIR_COLS; cc += 8) {
-        const int64_t j = c0 + cc;
-        if (j >= cols || 4 * q >= rows) continue;
-        float z[4];
-        unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
-        __nv_bfloat16 v[4];
+    // a grid of fewer CTAs than tiles walks the tiles (the overlapped form runs one CTA per SM)
+    for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const int64_t r0 = (tl / tiles_x) * PAIR_ROWS, c0 = (tl % tiles_x) * PAIR_COLS;
+        const int64_t q = (r0 >> 2) + qi;
+        __syncthreads();  // the previous tile has left shared memory
+        for (int cc = cj; cc < PAIR_COLS; cc += 8) {
+            const int64_t j = c0 + cc;
+            if (j >= cols || 4 * q >= rows) continue;
+            float z[4];
+            unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+            __nv_bfloat16 v[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) v[r] = __float2bfloat16_rn(__fmul_rn(z[r], scale));
-        const uint2 w = make_uint2((uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16),
-                                   (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16));
-        *reinterpret_cast<uint2 *>(&tile[cc][4 * qi]) = w;
-        if (vec) {
-            *reinterpret_cast<uint2 *>(out_t + j * rows + 4 * q) = w;
-        } else {
+            for (int r = 0; r < 4; ++r) v[r] = __float2bfloat16_rn(__fmul_rn(z[r], scale));
+            const uint2 w =
+                make_uint2((uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16),
+                           (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16));
+            *reinterpret_cast<uint2 *>(&tile[cc][4 * qi]) = w;
+            if (vec) {
+                *reinterpret_cast<uint2 *>(out_t + j * rows + 4 * q) = w;
+            } else {
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (4 * q + r < rows) out_t[j * rows + 4 * q + r] = v[r];
+                for (int r = 0; r < 4; ++r)
+                    if (4 * q + r < rows) out_t[j * rows + 4 * q + r] = v[r];
+            }
         }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < PAIR_ROWS * PAIR_COLS; e += blockDim.x) {
-        const int rr = e / PAIR_COLS, cc = e % PAIR_COLS;
-        const int64_t i = r0 + rr, j = c0 + cc;
-        if (i < rows && j < cols) out_n[i * cols + j] = tile[cc][rr];
+        __syncthreads();
+        for (int e = threadIdx.x; e < PAIR_ROWS * PAIR_COLS; e += blockDim.x) {
+            const int rr = e / PAIR_COLS, cc = e % PAIR_COLS;
+            const int64_t i = r0 + rr, j = c0 + cc;
+            if (i < rows && j < cols) out_n[i * cols + j] = tile[cc][rr];
+        }
     }
 }
 
 void launch_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, bool rademacher, cudaStream_t s) {
+                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, bool rademacher, int max_ctas, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return;
-    if (ceil_div(rows, PAIR_ROWS) > 65535) throw ArgError{"launch_gaussian_pair: too many rows"};
-    dim3 grid((unsigned)ceil_div(cols, PAIR_COLS), (unsigned)ceil_div(rows, PAIR_ROWS));
+    int64_t tiles = ceil_div(cols, PAIR_COLS) * ceil_div(rows, PAIR_ROWS);
+    if (max_ctas > 0 && tiles > max_ctas) tiles = max_ctas;
+    if (tiles > (1ll << 31) - 1) tiles = (1ll << 31) - 1;
     if (rademacher)
-        k_gaussian_pair<true><<<grid, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
+        k_gaussian_pair<true><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
     else
-        k_gaussian_pair<false><<<grid, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
+        k_gaussian_pair<false><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -190,48 +200,63 @@ DSANLS_DEV uint32_t feistel_pass(uint64_t seed, uint32_t side, uint64_t t, int h
     return (L << h) | R;
 }
 
-// One CTA: pi(p) for p < d into shared memory, bitonic sort, write J.
-__global__ void k_subsample(uint64_t seed, uint32_t side, uint64_t t_host, const int64_t *t_dev,
-                            int64_t n, int d, int h, int cap, int32_t *J) {
-    extern __shared__ uint32_t sv[];
+// The sampled set J = sorted pi(0..d-1): one thread per p < d sets bit pi(p)
+// of `bits` (n bits, zeroed before); then one CTA lists the set bits in
+// increasing order (a popcount prefix over the words).  The bitmap is left
+// for the sampled CSR product.
+__global__ void k_subsample_mark(uint64_t seed, uint32_t side, uint64_t t_host, const int64_t *t_dev, int64_t n,
+                                 int d, int h, uint32_t *__restrict__ bits) {
     const uint64_t t = t_dev ? (uint64_t)*t_dev : t_host;
     const uint64_t walk_limit = 1ull << (2 * h);
-    for (int p = threadIdx.x; p < cap; p += blockDim.x) {
-        uint32_t v = 0xffffffffu;
-        if (p < d) {
-            uint32_t x = (uint32_t)p;
-            // cycle walking: the orbit of p returns below n within 2^(2h) passes
-            for (uint64_t it = 0; it < walk_limit; ++it) {
-                x = feistel_pass(seed, side, t, h, x);
-                if ((int64_t)x < n) break;
-            }
-            v = x;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < d; p += gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)p;
+        for (uint64_t it = 0; it < walk_limit; ++it) {
+            x = feistel_pass(seed, side, t, h, x);
+            if ((int64_t)x < n) break;
         }
-        sv[p] = v;
+        if ((int64_t)x < n) atomicOr(&bits[x >> 5], 1u << (x & 31));
     }
-    __syncthreads();
-    for (int size = 2; size <= cap; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < cap; i += blockDim.x) {
-                const int partner = i ^ stride;
-                if (partner > i) {
-                    const bool up = (i & size) == 0;
-                    const uint32_t a = sv[i], b = sv[partner];
-                    if ((a > b) == up) {
-                        sv[i] = b;
-                        sv[partner] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int p = threadIdx.x; p < d; p += blockDim.x) J[p] = (int32_t)sv[p];
 }
 
-void prime_rng_attributes(int max_smem) {
-    allow_max_dynamic_smem(k_subsample, max_smem);
+constexpr int COMPACT_THREADS = 1024;
+
+__global__ void __launch_bounds__(COMPACT_THREADS)
+    k_bitmap_compact(const uint32_t *__restrict__ bits, int64_t words, int32_t *__restrict__ J) {
+    __shared__ int wsum[COMPACT_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (words + COMPACT_THREADS - 1) / COMPACT_THREADS;
+    const int64_t w0 = min(words, (int64_t)tid * per), w1 = min(words, w0 + per);
+    int cnt = 0;
+    for (int64_t w = w0; w < w1; ++w) cnt += __popc(bits[w]);
+    // exclusive prefix of cnt over the CTA (thread order = word order)
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        wsum[lane] = v;  // inclusive prefix of the warp totals
+    }
+    __syncthreads();
+    int pos = (warp > 0 ? wsum[warp - 1] : 0) + incl - cnt;
+    for (int64_t w = w0; w < w1; ++w) {
+        uint32_t b = bits[w];
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            J[pos++] = (int32_t)(w * 32 + bit);
+        }
+    }
 }
+
+void prime_rng_attributes(int max_smem) { (void)max_smem; }
 
 int feistel_half_bits(int64_t n) {
     int h = 1;
@@ -279,12 +304,14 @@ void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows,
 }
 
 void launch_subsample(uint64_t seed, uint32_t side, uint64_t t, const int64_t *t_dev, int64_t n, int d,
-                      int32_t *J, cudaStream_t s) {
-    int cap = 1;
-    while (cap < d) cap <<= 1;
+                      int32_t *J, uint32_t *bits, cudaStream_t s) {
     const int h = feistel_half_bits(n);
-    const size_t smem = (size_t)cap * sizeof(uint32_t);
-    k_subsample<<<1, 1024, smem, s>>>(seed, side, t, t_dev, n, d, h, cap, J);
+    const int64_t words = ceil_div(n, 32);
+    DSANLS_CUDA(cudaMemsetAsync(bits, 0, (size_t)words * sizeof(uint32_t), s));
+    const int blocks = (int)std::min<int64_t>(ceil_div(d, 256), 152 * 4);
+    k_subsample_mark<<<blocks, 256, 0, s>>>(seed, side, t, t_dev, n, d, h, bits);
+    DSANLS_LAUNCH_CHECK();
+    k_bitmap_compact<<<1, COMPACT_THREADS, 0, s>>>(bits, words, J);
     DSANLS_LAUNCH_CHECK();
 }
 

@@ -55,9 +55,11 @@ __global__ void __launch_bounds__(GRAM_THREADS)
         const int64_t j0 = ch * dc;
         const int64_t len = min(dc, d - j0);
         __syncthreads();
-        for (int a = 0; a < k; ++a)
-            for (int64_t j = threadIdx.x; j < dc; j += GRAM_THREADS)
-                ws[a * ldw + j] = (j < len) ? (double)W[(int64_t)a * d + j0 + j] : 0.0;
+        for (int64_t e = threadIdx.x; e < (int64_t)k * dc; e += GRAM_THREADS) {
+            const int a = (int)(e / dc);
+            const int64_t j = e - (int64_t)a * dc;
+            ws[a * ldw + j] = (j < len) ? (double)W[(int64_t)a * d + j0 + j] : 0.0;
+        }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < GRAM_MAXP; ++q) {

@@ -70,75 +70,42 @@ void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *va
 }
 
 // ---------------------------------------------------------------------------
-// subsampled product of a CSR matrix: membership bitmap of the sampled set
+// subsampled product of a CSR matrix against the membership bitmap of the
+// sampled set (left by launch_subsample)
 // ---------------------------------------------------------------------------
-__global__ void k_bitmap_set(const int32_t *__restrict__ J, int d, uint32_t *__restrict__ bits) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < d) atomicOr(&bits[J[p] >> 5], 1u << (J[p] & 31));
-}
 
-// One warp per row: lanes read 32 entries at a time, keep those whose column
-// is in the sampled set (bitmap test), and the whole warp accumulates
-// val * Y[col][:] for each kept entry in CSR order (lanes across the k output
-// columns).  Deterministic: one FMA chain per output in CSR order.
+// One warp per row: lanes read 128 entries at a time (lane L takes entries
+// base + 4L .. base + 4L + 3, four independent loads, then four independent
+// bitmap tests), keep those whose column is in the sampled set, and the whole
+// warp accumulates val * Y[col][:] for each kept entry in CSR order (lanes
+// across the k output columns).  Deterministic: one FMA chain per output in
+// CSR order.
 // Sum over the sampled entries of CSR range [e0, e1) into acc (lanes across k).
 DSANLS_DEV void sampled_range(const int32_t *__restrict__ col, const float *__restrict__ val, int64_t e0, int64_t e1,
                               const uint32_t *__restrict__ bits, const float *__restrict__ Y, int k, int lane,
                               float acc[4]) {
-    for (int64_t base = e0; base < e1; base += 32) {
-        const int64_t e = base + lane;
-        int32_t c = 0;
-        float v = 0.0f;
-        bool hit = false;
-        if (e < e1) {
-            c = col[e];
-            hit = (__ldg(&bits[c >> 5]) >> (c & 31)) & 1u;
-            if (hit) v = val[e];
-        }
-        unsigned mask = __ballot_sync(0xffffffffu, hit);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int32_t cj = __shfl_sync(0xffffffffu, c, src);
-            const float vj = __shfl_sync(0xffffffffu, v, src);
-            const float *y = Y + (int64_t)cj * k;
+    for (int64_t base = e0; base < e1; base += 128) {
+        int32_t c[4];
+        unsigned nib = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int cc = lane + 32 * q;
-                if (cc < k) acc[q] = __fmaf_rn(vj, y[cc], acc[q]);
-            }
+        for (int j = 0; j < 4; ++j) {
+            const int64_t e = base + 4 * lane + j;
+            c[j] = e < e1 ? col[e] : -1;
         }
-    }
-}
-
-// Rows longer than LONG_ROW entries are skipped here and handled in chunks.
-__global__ void __launch_bounds__(256)
-    k_sampled_spmm(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, const float *__restrict__ val,
-                   int64_t rows, const uint32_t *__restrict__ bits, const float *__restrict__ Y, int k, float alpha,
-                   float *__restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < rows; i += nwarps) {
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        const int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
-        if (e1 - e0 > LONG_ROW) continue;
-        for (int64_t base = e0; base < e1; base += 32) {
-            const int64_t e = base + lane;
-            int32_t c = 0;
-            float v = 0.0f;
-            bool hit = false;
-            if (e < e1) {
-                c = col[e];
-                hit = (__ldg(&bits[c >> 5]) >> (c & 31)) & 1u;
-                if (hit) v = val[e];
-            }
-            unsigned mask = __ballot_sync(0xffffffffu, hit);
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int32_t cj = __shfl_sync(0xffffffffu, c, src);
-                const float vj = __shfl_sync(0xffffffffu, v, src);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (c[j] >= 0 && ((__ldg(&bits[c[j] >> 5]) >> (c[j] & 31)) & 1u)) nib |= 1u << j;
+        unsigned lanes = __ballot_sync(0xffffffffu, nib != 0);
+        while (lanes) {
+            const int src = __ffs(lanes) - 1;
+            lanes &= lanes - 1;
+            const unsigned sn = __shfl_sync(0xffffffffu, nib, src);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!((sn >> j) & 1u)) continue;
+                const int32_t cj = __shfl_sync(0xffffffffu, c[j], src);
+                const int64_t ej = base + 4 * src + j;
+                const float vj = val[ej];
                 const float *y = Y + (int64_t)cj * k;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -147,11 +114,43 @@ __global__ void __launch_bounds__(256)
                 }
             }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int cc = lane + 32 * q;
-            if (cc < k) out[i * k + cc] = __fmul_rn(alpha, acc[q]);
+    }
+}
+
+// Rows longer than LONG_ROW entries are skipped here and handled in chunks.
+// The next row's bounds are loaded before the current row is processed.
+__global__ void __launch_bounds__(256)
+    k_sampled_spmm(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, const float *__restrict__ val,
+                   int64_t rows, const uint32_t *__restrict__ bits, const float *__restrict__ Y, int k, float alpha,
+                   float *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t i = warp;
+    int64_t e0 = 0, e1 = 0;
+    if (i < rows) {
+        e0 = rowptr[i];
+        e1 = rowptr[i + 1];
+    }
+    while (i < rows) {
+        const int64_t inext = i + nwarps;
+        int64_t n0 = 0, n1 = 0;
+        if (inext < rows) {
+            n0 = rowptr[inext];
+            n1 = rowptr[inext + 1];
         }
+        if (e1 - e0 <= LONG_ROW) {
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            sampled_range(col, val, e0, e1, bits, Y, k, lane, acc);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int cc = lane + 32 * q;
+                if (cc < k) out[i * k + cc] = __fmul_rn(alpha, acc[q]);
+            }
+        }
+        i = inext;
+        e0 = n0;
+        e1 = n1;
     }
 }
 
@@ -186,12 +185,9 @@ __global__ void k_combine_long(const int64_t *__restrict__ lrows, const int64_t 
     out[lrows[l] * k + c] = __fmul_rn(alpha, acc);
 }
 
-void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows, const int32_t *J,
-                         int d, int64_t K, uint32_t *bits, const float *Y, int k, float alpha, float *out,
-                         const LongRows &lr, cudaStream_t s) {
-    DSANLS_CUDA(cudaMemsetAsync(bits, 0, (size_t)ceil_div(K, 32) * sizeof(uint32_t), s));
-    k_bitmap_set<<<(unsigned)ceil_div(d, 256), 256, 0, s>>>(J, d, bits);
-    DSANLS_LAUNCH_CHECK();
+void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
+                         const uint32_t *bits, const float *Y, int k, float alpha, float *out, const LongRows &lr,
+                         cudaStream_t s) {
     if (rows <= 0) return;
     int64_t blocks = ceil_div(rows, 8);
     if (blocks > 152 * 16) blocks = 152 * 16;

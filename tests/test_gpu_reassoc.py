@@ -226,3 +226,29 @@ def test_rademacher_half_steps(pkg, precision, order):
                                 reassociate=order == 1)
         tol = 1e-5 if precision == 0 else 3e-4
         assert _rel(got, want) <= tol, (side, _rel(got, want))
+
+
+@pytest.mark.parametrize("case", [(1000, 808, 10, 104, 96), (640, 520, 64, 520, 264), (2056, 4104, 100, 512, 1024)])
+def test_bf16_reassociated_inner_steps(pkg, case):
+    """bf16 reassociated terms with 8 projected-gradient steps on the proximal
+    objective, against the oracle's bf16 model with the same steps (<= 3e-4)."""
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 7)
+    U, V = initial_factors(m, n, k, 9)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=3, d_v=d_v, precision=pkg.BF16,
+                       order=pkg.ORDER_REASSOCIATED, t=4, inner_iters=8)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 3, 4, side, X.shape[1], dd)
+        want = method.half_step(X, Y, Z, S, 0, method.mu_t(1.0, 1.0, 4), bf16=True, reassociate=True,
+                                inner_iters=8)
+        assert _rel(got, want) <= 3e-4, (side, _rel(got, want))

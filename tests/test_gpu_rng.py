@@ -54,7 +54,8 @@ def test_uniform_field_bits(pkg):
 
 
 @pytest.mark.parametrize("n,d", [(1, 1), (2, 1), (2, 2), (17, 17), (800, 100), (1000, 100), (16384, 2048),
-                                 (65536, 2048), (500_000, 5000), (2_000_000, 5000), (40_000, 16384)])
+                                 (65536, 2048), (500_000, 5000), (2_000_000, 5000), (40_000, 16384),
+                                 (100_000, 50_000), (70_001, 70_001)])
 @pytest.mark.parametrize("side,t", [(0, 0), (1, 3), (0, (1 << 32) + 11)])
 def test_subsample_indices_bits(pkg, n, d, side, t):
     got = pkg.subsample_indices(123, side, t, n, d).cpu().numpy()
