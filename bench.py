@@ -202,7 +202,7 @@ def oracle_sample(M, w, seed, rows_budget):
         t0 = time.perf_counter()
         S = method.Sketch(w["sketch"], seed, 0, side, K, dd)
         Y = V0 if side == 0 else U0
-        if w["sketch"] == method.GAUSSIAN:
+        if w["sketch"] in method.DENSE_KINDS:
             B = Y.T @ S.dense32.astype(np.float64)
         else:
             B = (Y[S.J, :] * np.float64(S.scale)).T
@@ -316,7 +316,9 @@ def time_to_eps(pkg, torch, M, w, T, check_every, stream):
     eps = fp32[-1][2] + 1e-3
     forms = {"bf16_closing_fp32": trajectory((pkg.BF16, pkg.FP32)), "fp8_closing_fp32": trajectory((pkg.FP8, pkg.FP32)),
              "bf16_reassociated_closing_fp32": trajectory((pkg.BF16, pkg.FP32), order=1),
-             "bf16_reassociated_inner16_closing_fp32": trajectory((pkg.BF16, pkg.FP32), order=1, inner=16)}
+             "bf16_reassociated_inner16_closing_fp32": trajectory((pkg.BF16, pkg.FP32), order=1, inner=16),
+             "fp8_reassociated_closing_fp32": trajectory((pkg.FP8, pkg.FP32), order=1),
+             "fp8_reassociated_inner16_closing_fp32": trajectory((pkg.FP8, pkg.FP32), order=1, inner=16)}
 
     def first_hit(tr):
         for it, ms, e in tr:
@@ -386,22 +388,24 @@ def run_ours(args, w):
     phases = [h.profile_half_step(0, reps=2), h.profile_half_step(1, reps=2)]
     peaks, peak_src = _peaks()
     m, n, d, d_v, k = w["m"], w["n"], w["d"], w["d_v"], w["k"]
-    if (w["sketch"] == 0 and order == 1) or (w["sketch"] == 2 and not w.get("sparse")):
+    dense_sketch = w["sketch"] in (0, 3, 4)  # Gaussian, Rademacher, count: S a dense matrix
+    if (dense_sketch and order == 1) or (w["sketch"] == 2 and not w.get("sparse")):
         # reassociated order (R = X P) or identity sketch (R = X Y): the streaming
         # product reads X once (bf16 or fp32) and the k x K factor, and writes R
-        eb = 2.0 if prec == pkg.BF16 else 4.0
+        eb = {pkg.BF16: 2.0, pkg.FP8: 1.0}.get(prec, 4.0)
         bytes_ = [eb * (m * n + k * n) + 4.0 * m * k, eb * (n * m + k * m) + 4.0 * n * k]
         flops = [2.0 * m * n * k, 2.0 * n * m * k]
         prod_ms = [p["rhs"] for p in phases]
-        if prec == pkg.BF16:
+        if prec in (pkg.BF16, pkg.FP8):
             achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
-            bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "tc_skinny"
+            bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+            kernel_key = "tc_skinny" if prec == pkg.BF16 else "tc_skinny_fp8"
             peak_note = "hbm_gbs of %s" % peak_src
         else:
             achieved = sum(flops) / (sum(prod_ms) / 1000.0) / 1e12
             bound, peak, unit, kernel_key = "alu", FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "sgemm_simt"
             peak_note = "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
-    elif w["sketch"] == 0:
+    elif dense_sketch:
         flops = [2.0 * m * n * d, 2.0 * n * m * d_v]
         if prec != pkg.FP32:
             flops = [f + 2.0 * m * d * k for f in flops]  # R = A B^T is fused into the same kernel
@@ -504,6 +508,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense_gaussian")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="bf16")
+    ap.add_argument("--sketch", choices=["gaussian", "subsample", "rademacher", "count"], default=None,
+                    help="sketch kind (default: the workload's)")
     ap.add_argument("--order", choices=["paper", "reassociated"], default=None,
                     help="order of R = M S B^T for Gaussian sketches (default: the workload's)")
     ap.add_argument("--solver", choices=["pgd", "rcd"], default="pgd")
@@ -520,6 +526,8 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.order is not None:
         w["order"] = ["paper", "reassociated"].index(args.order)
+    if args.sketch is not None:
+        w["sketch"] = {"gaussian": 0, "subsample": 1, "rademacher": 3, "count": 4}[args.sketch]
     if w.get("learned"):
         run_learned(args, w)
     elif w.get("compare"):
@@ -589,15 +597,17 @@ def run_learned(args, w):
         return x * (s_ / beta)[:, None]
 
     def val_loss():
-        # 1/2 mean ||y - y*||^2 in normalised units on the held-out groups (every 10th)
-        tot, cnt = 0.0, 0
+        # 1/2 mean ||y - y*||^2 in normalised units on the held-out groups (every 10th),
+        # and the fraction of positive network outputs there
+        tot, pos, cnt = 0.0, 0.0, 0
         for G, mu, b, x in pool[5::10]:
             bb, xx = b[-512:], x[-512:]
             off1 = torch.tensor([0, bb.shape[0]], dtype=torch.int64, device="cuda")
             pred = net.predict(G[None], mu, off1, bb)
             tot += 0.5 * float(((norm_target(G, mu, bb, pred) - norm_target(G, mu, bb, xx)) ** 2).sum(1).mean())
+            pos += float((pred > 0).float().mean())
             cnt += 1
-        return tot / cnt
+        return tot / cnt, pos / cnt
 
     ynorm = torch.cat([norm_target(G, mu, b, x).norm(dim=1) for G, mu, b, x in pool[5::10]])
     target_stats = {"p50": float(ynorm.median()), "p99": float(torch.quantile(ynorm.float(), 0.99)),
@@ -679,7 +689,8 @@ def run_learned(args, w):
                    "harvest_iterations": points, "rows_per_step": groups * rows_per, "hidden": hidden,
                    "pg_iters": PG_ITERS, "inner_iters": INNER},
         "harvest_s": harvest_s, "train_s": train_s, "loss_first": float(np.mean(losses[:20])),
-        "loss_last": float(np.mean(losses[-20:])), "val_loss_before": val_before, "val_loss_after": val_after,
+        "loss_last": float(np.mean(losses[-20:])), "val_loss_before": val_before[0], "val_loss_after": val_after[0],
+        "val_positive_outputs_before": val_before[1], "val_positive_outputs_after": val_after[1],
         "target_norm": target_stats, "results": res,
         "speedup_time_to_eps_vs_fp32": (base["seconds"] / best["seconds"]) if (base and best) else None,
     }), flush=True)
@@ -759,8 +770,13 @@ def run_batch(args, w):
     instance; value = batch outer iterations/s (x ranks for replicas)."""
     ws, rank, local = _dist()
     specs, Ms = _batch_inputs(w["count"])
-    flops = sum(2.0 * s["m"] * s["n"] * (s["d"] + s["d_v"]) + 2.0 * s["k"] * (s["m"] * s["d"] + s["n"] * s["d_v"])
-                for s in specs)
+    order = w.get("order", 0)
+    if order == 1:  # P_i = S_i B_i^T then R_i = X_i P_i, both halves
+        flops = sum(2.0 * s["k"] * (s["n"] * s["d"] + s["m"] * s["d_v"]) + 4.0 * s["m"] * s["n"] * s["k"]
+                    for s in specs)
+    else:
+        flops = sum(2.0 * s["m"] * s["n"] * (s["d"] + s["d_v"]) + 2.0 * s["k"] * (s["m"] * s["d"] + s["n"] * s["d_v"])
+                    for s in specs)
     if args.impl == "reference":
         if rank != 0:
             return
@@ -792,7 +808,7 @@ def run_batch(args, w):
         dist.init_process_group("nccl")
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    b = pkg.Batch(specs, use_graph=1)
+    b = pkg.Batch(specs, use_graph=1, order=order)
     for i, M in enumerate(Ms):
         b.set_dense(i, M)
     for _ in range(args.warmup):
@@ -840,6 +856,7 @@ def run_batch(args, w):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "instances": len(specs),
+                       "order": ["paper", "reassociated"][order],
                        "graph": True, "persistent_ctas": b.tuned_blocks(),
                        "l2": "inputs larger than L2 (M_i total %.1f GB)" % (sum(M.nbytes for M in Ms) / 1e9)},
             "instance_iters_per_s": value * len(specs),

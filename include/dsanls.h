@@ -59,6 +59,12 @@ extern "C" {
                                       3.4's other random matrices; E[S S^T] = I).
                                       Accepted wherever GAUSSIAN is (all orders and
                                       precisions; not by the batched form)         */
+#define DSANLS_SKETCH_COUNT 4      /* count sketch: one entry +-1 per row of S, in the
+                                      bucket ((w >> 1) * d) >> 31 with sign -1 for odd
+                                      w, w the row's Philox word (column 0, stream
+                                      0x30 | side); E[S S^T] = I, no scaling.  Runs
+                                      through the dense-sketch paths like GAUSSIAN
+                                      (S materialised; not by the batched form)   */
 
 /* ---- subproblem solvers (Section 3.5) -------------------------------- */
 #define DSANLS_SOLVER_PGD 0   /* one projected gradient step, eq. gradient_descent */
@@ -78,8 +84,11 @@ extern "C" {
                               /* R = M (S B^T): P = S B^T (K x k) first, then
                                  M P; 2 K d k + 2 rows K k flops.  Equal in exact
                                  arithmetic (associativity), rounded differently;
-                                 Gaussian sketch with FP32 (dense or sparse M) or
-                                 BF16 (dense M: S, B and P rounded to bf16)      */
+                                 dense sketches (Gaussian, Rademacher) with FP32
+                                 (dense or sparse M), BF16 (dense M: S, B and P
+                                 rounded to bf16) or FP8 (dense M: B and P^T
+                                 from bf16 operands, then M in E4M3 per 128-row
+                                 block and P^T in E4M3 per row for R = M P)      */
 
 /* ---- Philox field streams (counter word 3, low byte) ------------------ */
 #define DSANLS_STREAM_SKETCH_U 0
@@ -126,8 +135,8 @@ int dsanls_get_options(dsanls_t h, dsanls_options *opt);
  * sketch (identity: R = M V from bf16 operands, the unsketched subproblem),
  * FP8 dense data and a Gaussian sketch; BF16 needs m, n, d, d_v multiples of
  * 8, FP8 m and n multiples of 16.
- * ORDER_REASSOCIATED needs a Gaussian sketch and FP32 or BF16 (EINVAL with
- * FP8 or another sketch kind). */
+ * ORDER_REASSOCIATED needs a Gaussian or Rademacher sketch (EINVAL
+ * otherwise). */
 int dsanls_set_options(dsanls_t h, const dsanls_options *opt);
 
 /* Dense M: m rows of n binary32 values, row stride ld >= n (elements).  The
@@ -223,6 +232,12 @@ int dsanls_gaussian_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t
 int dsanls_rademacher_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,
                             int64_t cols, float scale, int32_t transposed, float *out,
                             void *stream);
+
+/* Count sketch S (rows x cols) of DSANLS_SKETCH_COUNT for side (0 or 1,
+ * stream 0x30 | side) and iteration t: S[i][h(i)] = s(i), zero elsewhere.
+ * transposed as above. */
+int dsanls_count_field(uint64_t seed, uint32_t side, uint64_t t, int64_t rows, int64_t cols,
+                       int32_t transposed, float *out, void *stream);
 
 /* Uniform [0,1) field X[i][j] = (w >> 8) * 2^-24, row-major rows x cols. */
 int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,

@@ -32,7 +32,8 @@ GAUSSIAN = 0
 SUBSAMPLE = 1
 IDENTITY = 2
 RADEMACHER = 3
-DENSE_KINDS = (GAUSSIAN, RADEMACHER)
+COUNT = 4
+DENSE_KINDS = (GAUSSIAN, RADEMACHER, COUNT)
 
 PGD = 0
 RCD = 1
@@ -42,11 +43,13 @@ SIDE_V = 1
 
 
 class Sketch:
-    """The random matrix S^t (n x d) of Section 3.4, in one of four kinds.
+    """The random matrix S^t (n x d) of Section 3.4, in one of five kinds.
 
     kind GAUSSIAN: dense, entries N(0, 1/d) from the Philox field.
     kind RADEMACHER: dense, entries +-1/sqrt(d) with the sign of the entry's
         Philox word (one of Section 3.4's "other choices" of random matrix).
+    kind COUNT: count sketch, one entry +-1 per row at a hashed column
+        (another of those choices; E[S S^T] = I without scaling).
     kind SUBSAMPLE: columns sqrt(n/d) e_{J_p}, J drawn without replacement.
     kind IDENTITY: S = I (requires d = n); the unsketched subproblem.
     """
@@ -61,6 +64,9 @@ class Sketch:
         elif kind == RADEMACHER:
             self.scale = rng.gaussian_scale(d)
             self.dense32 = rng.rademacher_field(seed, side, t, n, d, self.scale)
+        elif kind == COUNT:
+            self.scale = np.float32(1.0)
+            self.dense32 = rng.count_field(seed, side, t, n, d)
         elif kind == SUBSAMPLE:
             if d > n:
                 raise ValueError("subsampling needs d <= n")
@@ -183,8 +189,11 @@ def sketched_terms_fp8(X, Y, S, seed, t, side):
     E4M3, the unit-variance draws z of S to E4M3, A = (Xq zq) / sqrt(d)
     rounded to bf16 where it enters R; B = Y^T S from bf16 operands as in the
     bf16 form."""
-    unit = rng.rademacher_field if S.kind == RADEMACHER else rng.gaussian_field
-    z = unit(seed, side, t, S.n, S.d, np.float32(1.0))
+    if S.kind == COUNT:
+        z = rng.count_field(seed, side, t, S.n, S.d)
+    else:
+        unit = rng.rademacher_field if S.kind == RADEMACHER else rng.gaussian_field
+        z = unit(seed, side, t, S.n, S.d, np.float32(1.0))
     A = round_bf16((quantise_rowblocks_e4m3(X) @ round_e4m3(z)) * np.float64(S.scale))
     Sb = round_bf16(S.dense32)
     B = round_bf16(Y).T @ Sb

@@ -16,8 +16,8 @@ Learned form of one half-step (the same choices the GPU library makes):
   * fallback: the plain path's update x_pgd -- the projected-gradient step
     max(0, u - eta (u G - r)), or the same number of steps on f from u as the
     plain path takes -- is kept whenever f(x_pgd) < f(x_mlp).
-Training: mean squared error 1/2 mean ||y0 - y*||^2 against the normalised
-exact minimiser y*, Adam.  GELU is the exact x Phi(x).
+Training: squared error against the normalised exact minimiser y* (one-sided
+below zero, see loss_and_grads), Adam.  GELU is the exact x Phi(x).
 """
 import math
 
@@ -77,15 +77,20 @@ def forward(P, Gn, bn):
 
 
 def loss_and_grads(P, groups):
-    """groups: list of (Gn, bn, ystar); loss = 1/2 mean over all rows of ||y - y*||^2."""
+    """groups: list of (Gn, bn, ystar).  Loss = 1/2 mean over all rows of
+    sum_j e_j^2 with e_j = o_j - y*_j where y*_j > 0 and e_j = max(o_j, 0)
+    where y*_j = 0 (o the output before the ReLU).  This equals the squared
+    error of the ReLU output y = max(o, 0) except where o_j < 0 < y*_j, where
+    it keeps a gradient pulling o_j up: an output unit negative on every row
+    can then not stay dead."""
     N = sum(g[1].shape[0] for g in groups)
     grads = {name: np.zeros_like(v) for name, v in P.items()}
     loss = 0.0
     for Gn, bn, ys in groups:
         y, (Gn, bn, z1, h1, z2, h2, o) = forward(P, Gn, bn)
-        diff = y - ys
-        loss += 0.5 * float(np.sum(diff * diff))
-        do = diff * (o > 0.0) / N
+        e = np.where(ys > 0.0, o - ys, np.maximum(o, 0.0))
+        loss += 0.5 * float(np.sum(e * e))
+        do = e / N
         grads["W3"] += do.T @ h2
         grads["b3"] += do.sum(axis=0)
         dz2 = (do @ P["W3"]) * gelu_grad(z2)

@@ -135,6 +135,27 @@ def rademacher_field(seed, stream, t, rows, cols, scale):
     return np.where((w >> np.uint32(31)) != 0, -sc, sc).astype(np.float32)
 
 
+STREAM_COUNT = 0x30     # count sketch hashes (| side)
+
+
+def count_buckets(seed, side, t, n, d):
+    """Bucket h(i) in [0, d) and sign s(i) of each of the n rows of a count
+    sketch: w = the field word of (row i, column 0) of stream 0x30 | side;
+    h = ((w >> 1) * d) >> 31 (integer arithmetic), s = -1 if w is odd else +1."""
+    w = field_words(seed, STREAM_COUNT | side, t, n, 1)[:, 0].astype(np.uint64)
+    h = ((w >> np.uint64(1)) * np.uint64(d)) >> np.uint64(31)
+    sgn = np.where((w & np.uint64(1)) != 0, -1.0, 1.0).astype(np.float32)
+    return h.astype(np.int64), sgn
+
+
+def count_field(seed, side, t, n, d):
+    """The n x d count sketch as binary32: S[i][h(i)] = s(i), zero elsewhere."""
+    h, sgn = count_buckets(seed, side, t, n, d)
+    S = np.zeros((n, d), dtype=np.float32)
+    S[np.arange(n), h] = sgn
+    return S
+
+
 def uniform_field(seed, stream, t, rows, cols):
     out = np.empty((rows, cols), dtype=np.float32)
     lib().ora_uniform_field(seed, stream, t, rows, cols, _ptr(out, ctypes.c_float))

@@ -52,7 +52,14 @@ void dfree(T *&p) {
 }
 
 // Gaussian and Rademacher sketches are dense matrices drawn from the field
-bool dense_kind(int kind) { return kind == DSANLS_SKETCH_GAUSSIAN || kind == DSANLS_SKETCH_RADEMACHER; }
+bool dense_kind(int kind) {
+    return kind == DSANLS_SKETCH_GAUSSIAN || kind == DSANLS_SKETCH_RADEMACHER || kind == DSANLS_SKETCH_COUNT;
+}
+
+// generator of a dense sketch kind (DRAW_* of the field kernels)
+int draw_kind(int kind) {
+    return kind == DSANLS_SKETCH_RADEMACHER ? DRAW_RADEMACHER : (kind == DSANLS_SKETCH_COUNT ? DRAW_COUNT : DRAW_GAUSS);
+}
 
 int kp_bucket(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 64 ? 64 : 128)); }
 
@@ -103,6 +110,9 @@ struct dsanls_ctx {
     float *P = nullptr;
     __nv_bfloat16 *Sn = nullptr, *Bb = nullptr, *Ptb = nullptr;
     float *Ppart = nullptr, *Rpart2 = nullptr;
+    // fp8 reassociated order: P^T in fp32, its E4M3 codes and one scale per row of P^T
+    float *Ptf = nullptr, *pscale = nullptr;
+    uint8_t *Pq = nullptr;
     double *G64[2] = {nullptr, nullptr};
     double *scal[2] = {nullptr, nullptr};
     float *Gf = nullptr;
@@ -216,14 +226,20 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->Ppart, (reas && bf16) ? std::max(tc_gemm_bf16out_part_elems(k, h->d, n),
                                                tc_gemm_bf16out_part_elems(k, dv, m)) : 0);
     dalloc(h->Rpart2, ((reas && bf16) || ident_tc)
-                          ? std::max(tc_skinny_part_elems(m, n, k), tc_skinny_part_elems(n, m, k)) : 0);
+                          ? std::max({tc_skinny_part_elems(m, n, k), tc_skinny_part_elems(n, m, k),
+                                      fp8 ? tc_skinny_fp8_part_elems(m, n, k) : 0,
+                                      fp8 ? tc_skinny_fp8_part_elems(n, m, k) : 0})
+                          : 0);
+    dalloc(h->Ptf, (reas && fp8) ? k * kmax : 0);
+    dalloc(h->Pq, (reas && fp8) ? k * kmax : 0);
+    dalloc(h->pscale, (reas && fp8) ? 2 * k : 0);  // scales, then the row maxima (scratch)
     dalloc(h->W, k * (ident ? std::max(m, n) : dmax));
     dalloc(h->Wpart, (gauss && !bf16) ? (int64_t)MAX_SPLITS * k * dmax : 0);
     dalloc(h->Ytb, ((gauss && bf16) || ident_tc) ? k * std::max(m, n) : 0);
     dalloc(h->Bpart, (gauss && bf16) ? tc_gemm_part_elems(k, dmax) : 0);
     dalloc(h->R, std::max(m, n) * k);
     dalloc(h->Rpart, (gauss && bf16 && !reas) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
-    dalloc(h->Sq, (gauss && fp8) ? std::max(n * h->d, m * dv) : 0);
+    dalloc(h->Sq, (gauss && fp8 && !reas) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->bits, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? ceil_div(std::max(m, n), 32) + 1 : 0);
     std::copy(key, key + 7, h->cfg_key);
 }
@@ -258,8 +274,9 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
 
     mark(pe, DSANLS_PHASE_SKETCH, s);
     if (dense_kind(h->sketch)) {
-        const bool rade = h->sketch == DSANLS_SKETCH_RADEMACHER;
-        const float scale = (float)(1.0 / std::sqrt((double)dd));
+        const int rade = draw_kind(h->sketch);
+        // Gaussian / Rademacher entries carry 1/sqrt(dd); count sketch entries are +-1
+        const float scale = h->sketch == DSANLS_SKETCH_COUNT ? 1.0f : (float)(1.0 / std::sqrt((double)dd));
         const bool fp8 = dense && h->opt.precision == DSANLS_PREC_FP8;
         const bool tc = dense && (h->opt.precision == DSANLS_PREC_BF16 || fp8);
         const bool reas = h->opt.order == DSANLS_ORDER_REASSOCIATED;
@@ -268,10 +285,10 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         // CUDA-core form, bf16 S^T (K-major operand) for the tensor-core forms, and
         // for the fp8 form also fp8 S^T of the unit-variance draws; the reassociated
         // bf16 form also keeps bf16 S (d-major operand of P^T = B S^T)
-        if (fp8)
-            launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, rade, s);
-        else if (tc && reas)
+        if (tc && reas)
             launch_gaussian_pair(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sn, rade, 0, s);
+        else if (fp8)
+            launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, rade, s);
         else if (tc)
             launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, rade,
                                                  s);
@@ -298,7 +315,12 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         mark(pe, DSANLS_PHASE_PRODUCT, s);
         if (reas) {
             // P = S B^T (K x k), then R = X P: 2 K dd k + 2 rows K k flops
-            if (tc) {
+            if (fp8) {
+                // P^T in fp32, then one E4M3 scale per row of P^T
+                launch_copy_cast_bf16(h->W, (int64_t)k * dd, h->Bb, s);
+                launch_tc_gemm(h->Bb, h->Sn, k, dd, K, h->Ppart, h->Ptf, h->flag, s);
+                launch_quant_rows(h->Ptf, k, K, h->pscale, h->Pq, reinterpret_cast<unsigned int *>(h->pscale + k), s);
+            } else if (tc) {
                 launch_copy_cast_bf16(h->W, (int64_t)k * dd, h->Bb, s);
                 launch_tc_gemm_bf16out(h->Bb, h->Sn, k, dd, K, h->Ppart, h->Ptb, h->flag, s);
             } else {
@@ -310,7 +332,10 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
                 launch_sgemm(g, s);
             }
             mark(pe, DSANLS_PHASE_RHS, s);
-            if (tc) {
+            if (fp8) {
+                launch_tc_skinny_fp8(side == 0 ? h->Mq : h->MTq, h->qscale[side], h->Pq, h->pscale, rows, K, k,
+                                     h->Rpart2, h->R, h->flag, s);
+            } else if (tc) {
                 launch_tc_skinny(Xb, h->Ptb, rows, K, k, h->Rpart2, h->R, h->flag, s);
             } else if (dense) {
                 GemmArgs g{};
@@ -549,7 +574,7 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
     *out = nullptr;
     if (m < 1 || n < 1 || k < 1 || k > 128 || d < 1) return DSANLS_EINVAL;
     if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return DSANLS_EINVAL;
-    if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_RADEMACHER) return DSANLS_EINVAL;
+    if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_COUNT) return DSANLS_EINVAL;
     if (sketch_kind == DSANLS_SKETCH_SUBSAMPLE && d > n) return DSANLS_EINVAL;
     if (sketch_kind == DSANLS_SKETCH_IDENTITY && d != n) return DSANLS_EINVAL;
     dsanls_ctx *h = nullptr;
@@ -623,9 +648,8 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
                 throw ArgError{"BF16 precision needs m, n, d and d_v multiples of 8 (16-byte TMA rows)"};
         }
         if (opt->order != DSANLS_ORDER_PAPER && opt->order != DSANLS_ORDER_REASSOCIATED) throw ArgError{"unknown order"};
-        if (opt->order == DSANLS_ORDER_REASSOCIATED &&
-            (!dense_kind(h->sketch) || opt->precision == DSANLS_PREC_FP8))
-            throw ArgError{"the reassociated order needs a Gaussian sketch and FP32 or BF16 precision"};
+        if (opt->order == DSANLS_ORDER_REASSOCIATED && !dense_kind(h->sketch))
+            throw ArgError{"the reassociated order needs a Gaussian or Rademacher sketch"};
         if (opt->power_iters < 0 || opt->power_iters > 10000) throw ArgError{"power_iters out of range"};
         if (opt->inner_iters < 1 || opt->inner_iters > 256) throw ArgError{"inner_iters must be in 1..256"};
         if (opt->inner_iters > 1 && opt->solver != DSANLS_SOLVER_PGD)
@@ -1000,6 +1024,7 @@ void dsanls_destroy(dsanls_t h) {
         dfree(h->S); dfree(h->Sb); dfree(h->J); dfree(h->A); dfree(h->W); dfree(h->Wpart); dfree(h->R);
         dfree(h->Rpart); dfree(h->Ytb); dfree(h->Bpart);
         dfree(h->P); dfree(h->Sn); dfree(h->Bb); dfree(h->Ptb); dfree(h->Ppart); dfree(h->Rpart2);
+        dfree(h->Ptf); dfree(h->Pq); dfree(h->pscale);
         dfree(h->Mq); dfree(h->MTq); dfree(h->Sq); dfree(h->qscale[0]); dfree(h->qscale[1]);
         for (int side = 0; side < 2; ++side) {
             dfree(h->G64[side]);
@@ -1030,7 +1055,7 @@ int dsanls_gaussian_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t
     if (rows < 0 || cols < 0 || rows > (1ll << 34) || cols > (1ll << 31) - 1) return DSANLS_EINVAL;
     if (rows * cols > 0 && !out) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
-        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out, false,
+        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out, DRAW_GAUSS,
                                      (cudaStream_t)stream);
         return DSANLS_OK;
     });
@@ -1041,7 +1066,18 @@ int dsanls_rademacher_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64
     if (rows < 0 || cols < 0 || rows > (1ll << 34) || cols > (1ll << 31) - 1) return DSANLS_EINVAL;
     if (rows * cols > 0 && !out) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
-        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out, true,
+        launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out,
+                                     DRAW_RADEMACHER, (cudaStream_t)stream);
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_count_field(uint64_t seed, uint32_t side, uint64_t t, int64_t rows, int64_t cols, int32_t transposed,
+                       float *out, void *stream) {
+    if (rows < 0 || cols < 1 || rows > (1ll << 34) || cols > (1ll << 31) - 1 || side > 0xf) return DSANLS_EINVAL;
+    if (rows * cols > 0 && !out) return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        launch_gaussian_field<float>(seed, side, t, nullptr, rows, cols, 1.0f, transposed != 0, out, DRAW_COUNT,
                                      (cudaStream_t)stream);
         return DSANLS_OK;
     });

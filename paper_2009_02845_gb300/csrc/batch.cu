@@ -11,7 +11,9 @@
 //   sketch  S_i (K_i x d_i) Gaussian N(0, 1/d_i) from Philox keyed by seed_i
 //   B       B_i = Y_i^T S_i (k_i x d_i)                    (eq. def_A_B)
 //   AR      R_i = (X_i S_i) B_i^T per 64-row tile; the A tile lives only in
-//           shared memory                                  (eq. gradient_descent)
+//           shared memory                                  (eq. gradient_descent);
+//           reassociated order: P_i = S_i B_i^T per 64-row tile of K_i, then
+//           R_i = X_i P_i per 64-row tile
 //   gram    G_i = B_i B_i^T in FP64, eta_i = 1/(lambda_max + mu_t)
 //   update  PGD step or Alg. 3 sweep per row
 #include <algorithm>
@@ -114,6 +116,126 @@ __global__ void __launch_bounds__(256)
         for (int q = 0; q < 8; ++q) {
             const int c = cg * 8 + q;
             if (c < k && j0 + j < dd) B[(int64_t)c * dd + j0 + j] = acc[q];
+        }
+    }
+}
+
+// ---- reassociated order ---------------------------------------------------
+// P = S B^T (K x k): item = (instance, 64-row tile of K); thread (rp, cg) owns
+// rows 2 rp, 2 rp + 1 and columns 4 cg .. 4 cg + 3; one FMA chain per output in
+// increasing j.
+constexpr int P_ROWS = 64, P_JC = 64;
+__global__ void __launch_bounds__(256)
+    kb_pmat(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
+            int side, const float *__restrict__ S_all, const float *__restrict__ B_all, float *__restrict__ P_all) {
+    __shared__ float ss[P_ROWS][P_JC + 1];
+    __shared__ __align__(16) float bs[P_JC][32 + 4];  // bs[j][c] = B[c][j]
+    __shared__ int item_s;
+    const int rp = threadIdx.x / 8, cg = threadIdx.x % 8;
+    while (true) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = item_s;
+        __syncthreads();
+        if (it >= nitems) break;
+        const BatchInst b = inst[items[it].x];
+        const int64_t l0 = (int64_t)items[it].y * P_ROWS;
+        const int k = b.k, dd = d_of(b, side);
+        const int64_t K = kdim_of(b, side);
+        const float *S = S_all + b.offS;
+        const float *B = B_all + b.offB;
+        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+        for (int j0 = 0; j0 < dd; j0 += P_JC) {
+            for (int e = threadIdx.x; e < P_ROWS * P_JC; e += 256) {
+                const int r = e / P_JC, jj = e % P_JC;
+                ss[r][jj] = (l0 + r < K && j0 + jj < dd) ? S[(l0 + r) * dd + j0 + jj] : 0.0f;
+            }
+            for (int e = threadIdx.x; e < 32 * P_JC; e += 256) {
+                const int c = e / P_JC, jj = e % P_JC;
+                bs[jj][c] = (c < k && j0 + jj < dd) ? B[(int64_t)c * dd + j0 + jj] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int jj = 0; jj < P_JC; ++jj) {
+                const float s0 = ss[2 * rp][jj], s1 = ss[2 * rp + 1][jj];
+                const float4 bv = *reinterpret_cast<const float4 *>(&bs[jj][4 * cg]);
+                const float bq[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[0][q] = __fmaf_rn(s0, bq[q], acc[0][q]);
+                    acc[1][q] = __fmaf_rn(s1, bq[q], acc[1][q]);
+                }
+            }
+            __syncthreads();
+        }
+        float *P = P_all + b.offR;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int64_t l = l0 + 2 * rp + a;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 4 * cg + q;
+                if (l < K && c < k) P[l * k + c] = acc[a][q];
+            }
+        }
+    }
+}
+
+// R = X P (rows x k): item = (instance, 64-row tile); thread (rp, cg) as above;
+// one FMA chain per output in increasing l.
+constexpr int RP_ROWS = 64, RP_LC = 32;
+__global__ void __launch_bounds__(256)
+    kb_rp(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
+          int side, const float *__restrict__ data, const float *__restrict__ P_all, float *__restrict__ R_all) {
+    __shared__ float xs[RP_LC][RP_ROWS + 1];        // xs[l][r] = X[r0 + r][l0 + l]
+    __shared__ __align__(16) float ps[RP_LC][32 + 4];  // ps[l][c] = P[l0 + l][c]
+    __shared__ int item_s;
+    const int rp = threadIdx.x / 8, cg = threadIdx.x % 8;
+    while (true) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = item_s;
+        __syncthreads();
+        if (it >= nitems) break;
+        const BatchInst b = inst[items[it].x];
+        const int64_t r0 = (int64_t)items[it].y * RP_ROWS;
+        const int k = b.k;
+        const int64_t K = kdim_of(b, side), rows = rows_of(b, side);
+        const float *X = data + b.offM + (side == 0 ? 0 : b.m * b.n);
+        const float *P = P_all + b.offR;
+        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+        for (int64_t l0 = 0; l0 < K; l0 += RP_LC) {
+            for (int e = threadIdx.x; e < RP_ROWS * RP_LC; e += 256) {
+                const int r = e / RP_LC, l = e % RP_LC;
+                xs[l][r] = (r0 + r < rows && l0 + l < K) ? X[(r0 + r) * K + l0 + l] : 0.0f;
+            }
+            for (int e = threadIdx.x; e < RP_LC * 32; e += 256) {
+                const int l = e / 32, c = e % 32;
+                ps[l][c] = (l0 + l < K && c < k) ? P[(l0 + l) * k + c] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int l = 0; l < RP_LC; ++l) {
+                const float x0 = xs[l][2 * rp], x1 = xs[l][2 * rp + 1];
+                const float4 pv = *reinterpret_cast<const float4 *>(&ps[l][4 * cg]);
+                const float pq[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[0][q] = __fmaf_rn(x0, pq[q], acc[0][q]);
+                    acc[1][q] = __fmaf_rn(x1, pq[q], acc[1][q]);
+                }
+            }
+            __syncthreads();
+        }
+        float *R = R_all + b.offR;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int64_t r = r0 + 2 * rp + a;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 4 * cg + q;
+                if (r < rows && c < k) R[r * k + c] = acc[a][q];
+            }
         }
     }
 }
@@ -381,10 +503,11 @@ __global__ void kb_init(const BatchInst *__restrict__ inst, int count, float *__
 // host side
 // ---------------------------------------------------------------------------
 void batch_build_items(const std::vector<BatchInst> &h, int side, std::vector<int2> &bitems, std::vector<int2> &aritems,
-                       std::vector<int2> &uitems, std::vector<int64_t> &sketch_prefix) {
+                       std::vector<int2> &uitems, std::vector<int2> &pitems, std::vector<int64_t> &sketch_prefix) {
     bitems.clear();
     aritems.clear();
     uitems.clear();
+    pitems.clear();
     sketch_prefix.assign(1, 0);
     // largest instances first: long items start early, short ones fill the tail
     std::vector<int> order(h.size());
@@ -401,6 +524,8 @@ void batch_build_items(const std::vector<BatchInst> &h, int side, std::vector<in
         for (int t = 0; t < (int)ceil_div(dd, BT); ++t) bitems.push_back(make_int2(i, t));
         for (int t = 0; t < (int)ceil_div(rows, AR_ROWS); ++t) aritems.push_back(make_int2(i, t));
         for (int t = 0; t < (int)ceil_div(rows, 128); ++t) uitems.push_back(make_int2(i, t));
+        const int64_t K = side == 0 ? b.n : b.m;
+        for (int t = 0; t < (int)ceil_div(K, P_ROWS); ++t) pitems.push_back(make_int2(i, t));
     }
     for (size_t i = 0; i < h.size(); ++i) {
         const int64_t K = side == 0 ? h[i].n : h[i].m;
@@ -411,11 +536,11 @@ void batch_build_items(const std::vector<BatchInst> &h, int side, std::vector<in
 
 void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaStream_t s, cudaEvent_t *ev) {
     const int count = g.count;
-    int *ctr = g.counters + side * 4;
+    int *ctr = g.counters + side * 6;
     auto mark = [&](int i) {
         if (ev) DSANLS_CUDA(cudaEventRecord(ev[i], s));
     };
-    DSANLS_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(int), s));
+    DSANLS_CUDA(cudaMemsetAsync(ctr, 0, 6 * sizeof(int), s));
     mark(0);
     kb_sketch<<<cfg.sketch_blocks, 256, 0, s>>>(g.inst, count, g.sketch_prefix[side], side, g.t_dev, g.S);
     DSANLS_LAUNCH_CHECK();
@@ -424,8 +549,16 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
                                                  g.B);
     DSANLS_LAUNCH_CHECK();
     mark(2);
-    kb_ar<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.S,
-                                               g.B, g.R);
+    if (g.order == 1) {
+        kb_pmat<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.pitems[side], g.np[side], ctr + 4, side, g.S, g.B,
+                                                     g.P);
+        DSANLS_LAUNCH_CHECK();
+        kb_rp<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.P,
+                                                   g.R);
+    } else {
+        kb_ar<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.S,
+                                                   g.B, g.R);
+    }
     DSANLS_LAUNCH_CHECK();
     mark(3);
     kb_gram<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, count, ctr + 2, side, g.B, g.alpha, g.beta, g.power_iters,

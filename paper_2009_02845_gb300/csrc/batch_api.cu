@@ -106,9 +106,10 @@ std::string tune_key(const dsanls_batch_ctx *b) {
         shapes.push_back(buf);
     }
     std::sort(shapes.begin(), shapes.end());
-    std::string key = "f32";
+    const std::string form = b->g.order == 1 ? "f32r" : "f32";
+    std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
-    return std::to_string(std::hash<std::string>()(key)) + "/f32";
+    return std::to_string(std::hash<std::string>()(key)) + "/" + form;
 }
 
 std::string cache_path() {
@@ -271,8 +272,9 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
         balloc(g.S, offS);
         balloc(g.B, offB);
         balloc(g.R, offR);
+        balloc(g.P, offR);
         balloc(g.G, offG);
-        balloc(g.counters, 8);
+        balloc(g.counters, 12);
         balloc(g.t_dev, 1);
         balloc(g.flag, 1);
         balloc(b->work, B_WORK);
@@ -281,9 +283,12 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
         DSANLS_CUDA(cudaMemsetAsync(g.t_dev, 0, sizeof(int64_t), s));
         DSANLS_CUDA(cudaMemsetAsync(g.flag, 0, sizeof(int), s));
         for (int side = 0; side < 2; ++side) {
-            std::vector<int2> bi, ai, ui;
+            std::vector<int2> bi, ai, ui, pi;
             std::vector<int64_t> pre;
-            batch_build_items(b->h, side, bi, ai, ui, pre);
+            batch_build_items(b->h, side, bi, ai, ui, pi, pre);
+            balloc(g.pitems[side], (int64_t)pi.size());
+            g.np[side] = (int)pi.size();
+            DSANLS_CUDA(cudaMemcpyAsync(g.pitems[side], pi.data(), pi.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
             balloc(g.bitems[side], (int64_t)bi.size());
             balloc(g.aritems[side], (int64_t)ai.size());
             balloc(g.uitems[side], (int64_t)ui.size());
@@ -322,8 +327,9 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
         !std::isfinite(opt->alpha) || !std::isfinite(opt->beta) || opt->t < 0)
         return bfail(b, DSANLS_EINVAL, "bad power_iters, alpha, beta or t");
     if (opt->bound_clamp) return bfail(b, DSANLS_EINVAL, "the batched form has no bound clamp");
-    if (opt->inner_iters != 1 || opt->order != DSANLS_ORDER_PAPER)
-        return bfail(b, DSANLS_EINVAL, "the batched form takes one solver step per half in the paper's order");
+    if (opt->inner_iters != 1) return bfail(b, DSANLS_EINVAL, "the batched form takes one solver step per half");
+    if (opt->order != DSANLS_ORDER_PAPER && opt->order != DSANLS_ORDER_REASSOCIATED)
+        return bfail(b, DSANLS_EINVAL, "unknown order");
     return bguard(b, [&]() {
         DSANLS_CUDA(cudaStreamSynchronize(b->stream()));
         b->opt = *opt;
@@ -331,6 +337,8 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
         b->g.alpha = opt->alpha;
         b->g.beta = opt->beta;
         b->g.power_iters = opt->power_iters;
+        if (b->g.order != opt->order) b->tuned = false;  // the launch geometry is tuned per order
+        b->g.order = opt->order;
         drop_graph(b);
         if (opt->t != b->t_host) {
             b->t_host = opt->t;
@@ -493,9 +501,9 @@ void dsanls_batch_destroy(dsanls_batch_t b) {
     if (b->opt.stream) cudaStreamSynchronize((cudaStream_t)b->opt.stream);
     drop_graph(b);
     BatchDev &g = b->g;
-    bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.G);
+    bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.P); bfree(g.G);
     for (int side = 0; side < 2; ++side) {
-        bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]);
+        bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]); bfree(g.pitems[side]);
     }
     bfree(g.counters); bfree(g.t_dev); bfree(g.flag); bfree(b->work); bfree(b->dres);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);

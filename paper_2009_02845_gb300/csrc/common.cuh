@@ -139,11 +139,31 @@ DSANLS_DEV void rademacher4(uint64_t seed, uint32_t stream_id, uint64_t t, uint3
     z[3] = (b.w >> 31) ? -1.0f : 1.0f;
 }
 
-// Unit-variance draws of the dense sketch kinds for one Philox block.
-template <bool RADE>
-DSANLS_DEV void unit_draw4(uint64_t seed, uint32_t stream_id, uint64_t t, uint32_t row4, uint32_t col, float z[4]) {
-    if (RADE)
+// Count sketch entries of rows 4*row4..+3 at column col: the row's word w of
+// stream 0x30 | side at column 0 gives the bucket ((w >> 1) * d) >> 31 and the
+// sign (w odd: -1); the entry is the sign in the row's bucket, else 0.
+DSANLS_DEV void count4(uint64_t seed, uint32_t side, uint64_t t, uint32_t row4, uint32_t col, uint32_t d,
+                       float z[4]) {
+    const Philox4 b = field_block(seed, 0x30u | side, t, row4, 0u);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t w = word_of(b, r);
+        const uint32_t hb = (uint32_t)(((uint64_t)(w >> 1) * (uint64_t)d) >> 31);
+        z[r] = hb == col ? ((w & 1u) ? -1.0f : 1.0f) : 0.0f;
+    }
+}
+
+// Unit draws of the dense sketch kinds for one Philox block:
+// KIND 0 Gaussian (Box-Muller), 1 Rademacher (sign of each word), 2 count sketch.
+constexpr int DRAW_GAUSS = 0, DRAW_RADEMACHER = 1, DRAW_COUNT = 2;
+
+template <int KIND>
+DSANLS_DEV void unit_draw4(uint64_t seed, uint32_t stream_id, uint64_t t, uint32_t row4, uint32_t col, uint32_t d,
+                           float z[4]) {
+    if (KIND == DRAW_RADEMACHER)
         rademacher4(seed, stream_id, t, row4, col, z);
+    else if (KIND == DRAW_COUNT)
+        count4(seed, stream_id, t, row4, col, d, z);
     else
         gaussian4(seed, stream_id, t, row4, col, z);
 }

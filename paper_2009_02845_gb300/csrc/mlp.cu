@@ -110,16 +110,20 @@ __global__ void k_bias_act(float *__restrict__ z, float *__restrict__ act, const
     act[idx] = relu ? fmaxf(v, 0.0f) : gelu_f(v);
 }
 
-// do = (y - y*) [o > 0] / N ; per-row loss 1/2 ||y - y*||^2
-__global__ void k_out_grad(const float *__restrict__ o, const float *__restrict__ y, const float *__restrict__ ys,
-                           int64_t rows, int k, float invN, float *__restrict__ dout, double *__restrict__ rowloss) {
+// e = o - y* where y* > 0, max(o, 0) where y* = 0 (o before the ReLU);
+// do = e / N; per-row loss 1/2 ||e||^2.  Equal to the squared error of the
+// ReLU output except where o < 0 < y*, where it keeps a gradient.  ys and
+// dout may be the same array (each element is read before it is written).
+__global__ void k_out_grad(const float *__restrict__ o, const float *ys, int64_t rows, int k, float invN, float *dout,
+                           double *__restrict__ rowloss) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
     double l = 0.0;
     for (int j = 0; j < k; ++j) {
-        const float diff = y[r * k + j] - ys[r * k + j];
-        l += 0.5 * (double)diff * (double)diff;
-        dout[r * k + j] = o[r * k + j] > 0.0f ? diff * invN : 0.0f;
+        const float oj = o[r * k + j], t = ys[r * k + j];
+        const float e = t > 0.0f ? oj - t : fmaxf(oj, 0.0f);
+        l += 0.5 * (double)e * (double)e;
+        dout[r * k + j] = e * invN;
     }
     rowloss[r] = l;
 }
@@ -278,13 +282,13 @@ void mlp_forward(MlpState &st, const float *G, const float *mu, const int64_t *o
     DSANLS_LAUNCH_CHECK();
 }
 
-// Loss and gradient (into st.grad) of 1/2 mean ||y - y*||^2 after mlp_forward.
+// Loss and gradient (into st.grad) of the one-sided squared error (k_out_grad) after mlp_forward.
 void mlp_backward(MlpState &st, const int64_t *off, int ngroups, const float *ystar, int64_t rows, cudaStream_t s) {
     const int k = st.k, h = st.h;
     const MlpOffsets O = mlp_offsets(k, h);
     const float *W = st.wq;
     float *dG = st.grad;
-    k_out_grad<<<nblk(rows), 256, 0, s>>>(st.o, st.y, ystar, rows, k, 1.0f / (float)rows, st.dout, st.rowloss);
+    k_out_grad<<<nblk(rows), 256, 0, s>>>(st.o, ystar, rows, k, 1.0f / (float)rows, st.dout, st.rowloss);
     DSANLS_LAUNCH_CHECK();
     k_sum_doubles<<<1, 256, 0, s>>>(st.rowloss, rows, 1.0 / (double)rows, st.loss);  // mean over rows
     DSANLS_LAUNCH_CHECK();

@@ -35,7 +35,7 @@ __global__ void k_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t r
 }
 
 // t is read from device memory when t_dev != nullptr (graph replays).
-template <bool TRANSPOSED, typename OutT, bool RADE>
+template <bool TRANSPOSED, typename OutT, int KIND>
 __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, const int64_t *t_dev,
                                  int64_t rows, int64_t cols, float scale, OutT *out) {
     const int64_t nb4 = (rows + 3) >> 2;
@@ -51,7 +51,7 @@ __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, c
         q = idx / cols;
     }
     float z[4];
-    unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+    unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, z);
 #pragma unroll
     for (int r = 0; r < 4; ++r) z[r] = __fmul_rn(z[r], scale);
     const int64_t i0 = 4 * q;
@@ -72,7 +72,7 @@ __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, c
 }
 
 // S^T in two forms at once (cols x rows): bf16 of z * scale and fp8 E4M3 of z.
-template <bool RADE>
+template <int KIND>
 __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols,
                                 float scale, __nv_bfloat16 *out_b, __nv_fp8_e4m3 *out_q) {
     const int64_t nb4 = (rows + 3) >> 2;
@@ -81,7 +81,7 @@ __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_de
     const uint64_t t = (uint64_t)*t_dev;
     const int64_t q = idx % nb4, j = idx / nb4;
     float z[4];
-    unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+    unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, z);
     const int64_t i0 = 4 * q;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -101,7 +101,7 @@ __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_de
 // row, 128 contiguous bytes per tile row.
 constexpr int PAIR_ROWS = 128, PAIR_COLS = 64, PAIR_LD = PAIR_ROWS + 4;  // 264-byte rows
 
-template <bool RADE>
+template <int KIND>
 __global__ void __launch_bounds__(256)
     k_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
                     __nv_bfloat16 *__restrict__ out_t, __nv_bfloat16 *__restrict__ out_n) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256)
             const int64_t j = c0 + cc;
             if (j >= cols || 4 * q >= rows) continue;
             float z[4];
-            unit_draw4<RADE>(seed, sid, t, (uint32_t)q, (uint32_t)j, z);
+            unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, z);
             __nv_bfloat16 v[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) v[r] = __float2bfloat16_rn(__fmul_rn(z[r], scale));
@@ -146,28 +146,33 @@ __global__ void __launch_bounds__(256)
 }
 
 void launch_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, bool rademacher, int max_ctas, cudaStream_t s) {
+                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, int kind, int max_ctas, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return;
     int64_t tiles = ceil_div(cols, PAIR_COLS) * ceil_div(rows, PAIR_ROWS);
     if (max_ctas > 0 && tiles > max_ctas) tiles = max_ctas;
     if (tiles > (1ll << 31) - 1) tiles = (1ll << 31) - 1;
-    if (rademacher)
-        k_gaussian_pair<true><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
+    if (kind == DRAW_RADEMACHER)
+        k_gaussian_pair<DRAW_RADEMACHER><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t,
+                                                                         out_n);
+    else if (kind == DRAW_COUNT)
+        k_gaussian_pair<DRAW_COUNT><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
     else
-        k_gaussian_pair<false><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
+        k_gaussian_pair<DRAW_GAUSS><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
     DSANLS_LAUNCH_CHECK();
 }
 
 void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_b, uint8_t *out_q, bool rademacher, cudaStream_t s) {
+                          __nv_bfloat16 *out_b, uint8_t *out_q, int kind, cudaStream_t s) {
     const int64_t total = ((rows + 3) >> 2) * cols;
     if (total == 0) return;
-    if (rademacher)
-        k_gaussian_dual<true><<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(
-            seed, sid, t_dev, rows, cols, scale, out_b, reinterpret_cast<__nv_fp8_e4m3 *>(out_q));
+    const unsigned g = (unsigned)ceil_div(total, 256);
+    __nv_fp8_e4m3 *q = reinterpret_cast<__nv_fp8_e4m3 *>(out_q);
+    if (kind == DRAW_RADEMACHER)
+        k_gaussian_dual<DRAW_RADEMACHER><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b, q);
+    else if (kind == DRAW_COUNT)
+        k_gaussian_dual<DRAW_COUNT><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b, q);
     else
-        k_gaussian_dual<false><<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(
-            seed, sid, t_dev, rows, cols, scale, out_b, reinterpret_cast<__nv_fp8_e4m3 *>(out_q));
+        k_gaussian_dual<DRAW_GAUSS><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b, q);
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -276,24 +281,28 @@ void launch_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, i
 
 template <typename OutT>
 void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_t *t_dev, int64_t rows,
-                           int64_t cols, float scale, bool transposed, OutT *out, bool rademacher, cudaStream_t s) {
+                           int64_t cols, float scale, bool transposed, OutT *out, int kind, cudaStream_t s) {
     const int64_t total = ((rows + 3) >> 2) * cols;
     if (total == 0) return;
     const unsigned grid = (unsigned)ceil_div(total, 256);
-    if (transposed && rademacher)
-        k_gaussian_field<true, OutT, true><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
-    else if (transposed)
-        k_gaussian_field<true, OutT, false><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
-    else if (rademacher)
-        k_gaussian_field<false, OutT, true><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
-    else
-        k_gaussian_field<false, OutT, false><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out);
+#define DSANLS_FIELD_LAUNCH(TR, KD) \
+    k_gaussian_field<TR, OutT, KD><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out)
+    if (transposed) {
+        if (kind == DRAW_RADEMACHER) DSANLS_FIELD_LAUNCH(true, DRAW_RADEMACHER);
+        else if (kind == DRAW_COUNT) DSANLS_FIELD_LAUNCH(true, DRAW_COUNT);
+        else DSANLS_FIELD_LAUNCH(true, DRAW_GAUSS);
+    } else {
+        if (kind == DRAW_RADEMACHER) DSANLS_FIELD_LAUNCH(false, DRAW_RADEMACHER);
+        else if (kind == DRAW_COUNT) DSANLS_FIELD_LAUNCH(false, DRAW_COUNT);
+        else DSANLS_FIELD_LAUNCH(false, DRAW_GAUSS);
+    }
+#undef DSANLS_FIELD_LAUNCH
     DSANLS_LAUNCH_CHECK();
 }
 template void launch_gaussian_field<float>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t, int64_t,
-                                           float, bool, float *, bool, cudaStream_t);
+                                           float, bool, float *, int, cudaStream_t);
 template void launch_gaussian_field<__nv_bfloat16>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t,
-                                                   int64_t, float, bool, __nv_bfloat16 *, bool, cudaStream_t);
+                                                   int64_t, float, bool, __nv_bfloat16 *, int, cudaStream_t);
 
 void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, float *out,
                           cudaStream_t s) {

@@ -14,6 +14,8 @@
 //           already hold their new values.
 //    Optional clamp at sqrt(2 ||M||_F) (eq. extra_con); a NaN/Inf before the
 //    projection raises a device flag that the host turns into an error.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -374,85 +376,90 @@ __global__ void __launch_bounds__(256)
     float *gs = sm;                // k x LDG, gs[l][c] = G[l][c] (c < KP, zero beyond k)
     float *zr = gs + k * LDG;      // 64 x k, row-major (the Z tile, then the new rows)
     float *rr = zr + 64 * k;       // 64 x k, the R tile
-    const int64_t r0 = (int64_t)blockIdx.x * 64;
-    const int nr = (int)min((int64_t)64, rows - r0);
-    const int n = nr * k;
-    stage_flat(zr, Z + r0 * k, n);
-    cp_async_commit();
-    stage_flat(rr, R + r0 * k, n);
-    cp_async_commit();
+    // G once per CTA; the CTAs then walk the 64-row tiles
     for (int e = threadIdx.x; e < k * KP; e += 256) gs[(e / KP) * LDG + (e % KP)] = Gf[e];
-    for (int e = n + threadIdx.x; e < 64 * k; e += 256) zr[e] = 0.0f;
-    cp_async_wait<1>();  // the Z tile
-    __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const float eta = (float)scal[2];
     const float mu = (float)scal[1];
     const float *z0 = zr + (ty * 4) * k;
-    for (int it = 0; it < inner; ++it) {
-        float acc[4][TN];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
-#pragma unroll 2
-        for (int l = 0; l < k; ++l) {
-            const float zv[4] = {z0[l], z0[k + l], z0[2 * k + l], z0[3 * k + l]};
-            float gv[TN];
-            const float *gl = gs + l * LDG;
-            if constexpr (TN >= 4) {
-#pragma unroll
-                for (int j = 0; j < TN / 4; ++j) {
-                    const float4 g4 = *reinterpret_cast<const float4 *>(gl + j * 64 + tx * 4);
-                    gv[4 * j] = g4.x;
-                    gv[4 * j + 1] = g4.y;
-                    gv[4 * j + 2] = g4.z;
-                    gv[4 * j + 3] = g4.w;
-                }
-            } else {
-#pragma unroll
-                for (int b = 0; b < TN; ++b) gv[b] = gl[tx * TN + b];
-            }
+    const int64_t ntiles = (rows + 63) / 64;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * 64;
+        const int nr = (int)min((int64_t)64, rows - r0);
+        const int n = nr * k;
+        stage_flat(zr, Z + r0 * k, n);
+        cp_async_commit();
+        stage_flat(rr, R + r0 * k, n);
+        cp_async_commit();
+        for (int e = n + threadIdx.x; e < 64 * k; e += 256) zr[e] = 0.0f;
+        cp_async_wait<1>();  // the Z tile
+        __syncthreads();
+        for (int it = 0; it < inner; ++it) {
+            float acc[4][TN];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < TN; ++b) acc[a][b] = __fmaf_rn(zv[a], gv[b], acc[a][b]);
-        }
-        if (it == 0) {
-            cp_async_wait<0>();  // the R tile
-            __syncthreads();     // every thread is done reading the Z tile
-            if (inner > 1) {
-                // b = r + mu u, kept in the R tile for the steps on the proximal objective
-                for (int e = threadIdx.x; e < n; e += 256) rr[e] = __fmaf_rn(mu, zr[e], rr[e]);
+                for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
+#pragma unroll 2
+            for (int l = 0; l < k; ++l) {
+                const float zv[4] = {z0[l], z0[k + l], z0[2 * k + l], z0[3 * k + l]};
+                float gv[TN];
+                const float *gl = gs + l * LDG;
+                if constexpr (TN >= 4) {
+#pragma unroll
+                    for (int j = 0; j < TN / 4; ++j) {
+                        const float4 g4 = *reinterpret_cast<const float4 *>(gl + j * 64 + tx * 4);
+                        gv[4 * j] = g4.x;
+                        gv[4 * j + 1] = g4.y;
+                        gv[4 * j + 2] = g4.z;
+                        gv[4 * j + 3] = g4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < TN; ++b) gv[b] = gl[tx * TN + b];
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < TN; ++b) acc[a][b] = __fmaf_rn(zv[a], gv[b], acc[a][b]);
+            }
+            if (it == 0) {
+                cp_async_wait<0>();  // the R tile
+                __syncthreads();     // every thread is done reading the Z tile
+                if (inner > 1) {
+                    // b = r + mu u, kept in the R tile for the steps on the proximal objective
+                    for (int e = threadIdx.x; e < n; e += 256) rr[e] = __fmaf_rn(mu, zr[e], rr[e]);
+                    __syncthreads();
+                }
+            } else {
                 __syncthreads();
             }
-        } else {
-            __syncthreads();
-        }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int i = ty * 4 + a;
-            if (i >= nr) continue;
+            for (int a = 0; a < 4; ++a) {
+                const int i = ty * 4 + a;
+                if (i >= nr) continue;
 #pragma unroll
-            for (int b = 0; b < TN; ++b) {
-                const int c = upd_col<TN>(tx, b);
-                if (c < k) {
-                    const float x = zr[i * k + c];
-                    // one step: the gradient of eq. gradient_descent (r in the tile);
-                    // several: (G + mu I) x - (r + mu u) (b in the tile)
-                    const float grad = inner > 1 ? __fsub_rn(__fmaf_rn(mu, x, acc[a][b]), rr[i * k + c])
-                                                 : __fsub_rn(acc[a][b], rr[i * k + c]);
-                    zr[i * k + c] = project_clamp(__fmaf_rn(-eta, grad, x), bound, flag);
+                for (int b = 0; b < TN; ++b) {
+                    const int c = upd_col<TN>(tx, b);
+                    if (c < k) {
+                        const float x = zr[i * k + c];
+                        // one step: the gradient of eq. gradient_descent (r in the tile);
+                        // several: (G + mu I) x - (r + mu u) (b in the tile)
+                        const float grad = inner > 1 ? __fsub_rn(__fmaf_rn(mu, x, acc[a][b]), rr[i * k + c])
+                                                     : __fsub_rn(acc[a][b], rr[i * k + c]);
+                        zr[i * k + c] = project_clamp(__fmaf_rn(-eta, grad, x), bound, flag);
+                    }
                 }
             }
+            __syncthreads();  // the new rows are complete before the next product reads them
         }
-        __syncthreads();  // the new rows are complete before the next product reads them
+        float *zo = Z + r0 * k;
+        const int n4 = n >> 2;
+        for (int e = threadIdx.x; e < n4; e += 256)
+            reinterpret_cast<float4 *>(zo)[e] = reinterpret_cast<const float4 *>(zr)[e];
+        for (int e = 4 * n4 + threadIdx.x; e < n; e += 256) zo[e] = zr[e];
+        __syncthreads();  // the tile has left shared memory before the next one is staged
     }
-    float *zo = Z + r0 * k;
-    const int n4 = n >> 2;
-    for (int e = threadIdx.x; e < n4; e += 256)
-        reinterpret_cast<float4 *>(zo)[e] = reinterpret_cast<const float4 *>(zr)[e];
-    for (int e = 4 * n4 + threadIdx.x; e < n; e += 256) zo[e] = zr[e];
 }
 
 template <int KP>
@@ -460,8 +467,13 @@ static void update_kp(int solver, float *Z, const float *R, int64_t rows, int k,
                       const double *scal, float bound, int inner, int *flag, cudaStream_t s) {
     if (solver == 0) {
         const size_t smem_t = ((size_t)k * (KP + 4) + 2 * 64 * (size_t)k) * sizeof(float);
-        k_update_pgd_tiled<KP><<<(unsigned)ceil_div(rows, 64), 256, smem_t, s>>>(Z, R, rows, k, Gf, scal, bound, inner,
-                                                                               flag);
+        // persistent: as many CTAs as fit on the GPU at once (G is staged once per CTA)
+        int per_sm = 1, sms = 152, dev = 0;
+        DSANLS_CUDA(cudaGetDevice(&dev));
+        DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_pgd_tiled<KP>, 256, smem_t));
+        const int64_t grid = std::min<int64_t>(ceil_div(rows, 64), (int64_t)std::max(1, per_sm) * sms);
+        k_update_pgd_tiled<KP><<<(unsigned)grid, 256, smem_t, s>>>(Z, R, rows, k, Gf, scal, bound, inner, flag);
         DSANLS_LAUNCH_CHECK();
         return;
     }

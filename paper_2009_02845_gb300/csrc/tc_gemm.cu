@@ -188,7 +188,9 @@ struct __align__(8) TcSmemTail {
 //   columns of this chunk (columns < d).
 // FP8 = true: X and S^T are fp8 E4M3 (kind::f8f6f4, K blocks of 128 elements,
 //   still 128 bytes per row); the fused epilogue multiplies D1 by
-//   row_scale[m0 / 128] * extra_scale before the bf16 repack.
+//   row_scale[m0 / 128] * extra_scale before the bf16 repack; the plain fp8
+//   product (streaming R = Xq Pq of the fp8 reassociated order) multiplies
+//   each output by row_scale[m0 / 128] * col_scale[column].
 // BNT: width of the N tile (256 for the fused kernel; 64, 128 or 256 for the
 //   plain product).  TMEM: 512 columns for the fused kernel, BNT otherwise, so
 //   two plain CTAs with BNT <= 128 can share an SM.
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
               const __grid_constant__ CUtensorMap map_b, int64_t rows, int64_t K, int64_t d, int k, int kp,
               int kb_per_split, float *__restrict__ out, int *__restrict__ err, const float *__restrict__ row_scale,
-              float extra_scale) {
+              float extra_scale, const float *__restrict__ col_scale) {
     constexpr int BKE = FP8 ? 128 : BK;  // K elements per stage
     static_assert(!FUSED || BNT == BN, "the fused kernel uses 256-wide N tiles");
     static_assert(BNT == 64 || BNT == 128 || BNT == 256, "N tile of 64, 128 or 256");
@@ -332,6 +334,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (ok) {
                 fence_after();
                 float *dst = out + ((int64_t)blockIdx.y * rows + row) * d + n0;
+                const float rs = FP8 ? row_scale[m0 / BM] : 1.0f;
 #pragma unroll 1
                 for (int c = 0; c < BNT / 32; ++c) {
                     uint32_t v[32];
@@ -339,8 +342,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tmem_ld_wait();
                     if (row < rows) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (n0 + c * 32 + j < d) dst[c * 32 + j] = nk > 0 ? __uint_as_float(v[j]) : 0.0f;
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = n0 + c * 32 + j;
+                            if (col < d) {
+                                float x = nk > 0 ? __uint_as_float(v[j]) : 0.0f;
+                                if (FP8) x = __fmul_rn(x, __fmul_rn(rs, col_scale[col]));
+                                dst[c * 32 + j] = x;
+                            }
+                        }
                     }
                 }
             } else {
@@ -498,12 +507,12 @@ PlainPlan plan_one_wave(int64_t rows, int64_t K, int64_t N, int bnt) {
 // a fixed per-CTA cost (prologue, TMEM allocation, epilogue), plus writing
 // and re-reading the split partials of R -- with at least 16 k-blocks per
 // split.
-PlainPlan plan_stream(int64_t rows, int64_t K, int64_t N, int bnt, int slots) {
+PlainPlan plan_stream(int64_t rows, int64_t K, int64_t N, int bnt, int slots, int bk = BK, int elem_bytes = 2) {
     const int64_t tiles = ceil_div(rows, BM) * ceil_div(N, bnt);
-    const int nk = (int)ceil_div(K, BK);
+    const int nk = (int)ceil_div(K, bk);
     const int max_s = std::max(1, std::min(16, nk / 16));
     const double bw = 6.8e12, per_cta = 3.0e-6;
-    const double x_bytes = 2.0 * (double)ceil_div(rows, BM) * BM * (double)K;
+    const double x_bytes = (double)elem_bytes * (double)ceil_div(rows, BM) * BM * (double)K;
     double best_t = 1e30;
     int best_s = 1;
     for (int sp = 1; sp <= max_s; ++sp) {
@@ -554,10 +563,10 @@ void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
         k_tc_gemm<4, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
-                                                                            err, nullptr, 1.0f);
+                                                                            err, nullptr, 1.0f, nullptr);
     else
         k_tc_gemm<3, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
-                                                                            err, nullptr, 1.0f);
+                                                                            err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
     DSANLS_LAUNCH_CHECK();
@@ -582,10 +591,10 @@ void launch_tc_sketch_rhs_fp8(const uint8_t *Xq, const float *row_scale, const u
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
         k_tc_gemm<4, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
-                                                                           err, row_scale, s_scale);
+                                                                           err, row_scale, s_scale, nullptr);
     else
         k_tc_gemm<3, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
-                                                                           err, row_scale, s_scale);
+                                                                           err, row_scale, s_scale, nullptr);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
     DSANLS_LAUNCH_CHECK();
@@ -632,7 +641,7 @@ void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t row
     const CUtensorMap ms = make_map(St, d, K, BN);
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, d, 0, 0,
-                                                                         p.kb_per_split, part, err, nullptr, 1.0f);
+                                                                         p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * d, p.splits, rows, d, d, C, d, s);
 }
@@ -661,7 +670,7 @@ void launch_tc_gemm_bf16out(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int
     const CUtensorMap ms = make_map(St, N, K, BN);
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, N, 0, 0,
-                                                                         p.kb_per_split, part, err, nullptr, 1.0f);
+                                                                         p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     k_split_reduce_bf16<<<(unsigned)ceil_div(rows * N, 256), 256, 0, s>>>(part, p.splits, rows * N, C);
     DSANLS_LAUNCH_CHECK();
@@ -684,12 +693,83 @@ void launch_tc_skinny(const __nv_bfloat16 *X, const __nv_bfloat16 *Pt, int64_t r
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     if (bnt == 64)
         k_tc_gemm<4, false, false, 64><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
-            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f);
+            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     else
         k_tc_gemm<3, false, false, 128><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
-            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f);
+            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
+}
+
+int64_t tc_skinny_fp8_part_elems(int64_t rows, int64_t K, int k) {
+    const PlainPlan p = plan_stream(rows, K, k, skinny_bnt(k), kSkinnySlots, 128, 1);
+    return (int64_t)p.splits * rows * k;
+}
+
+void launch_tc_skinny_fp8(const uint8_t *Xq, const float *xscale, const uint8_t *Pq, const float *pscale,
+                          int64_t rows, int64_t K, int k, float *part, float *R, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 16 != 0) throw ArgError{"fp8 streaming product needs K a multiple of 16"};
+    if (k < 1 || k > 128) throw ArgError{"skinny product needs 1 <= k <= 128"};
+    const int bnt = skinny_bnt(k);
+    const PlainPlan p = plan_stream(rows, K, k, bnt, kSkinnySlots, 128, 1);
+    const CUtensorMap mx = make_map_u8(Xq, rows, K, BM);
+    const CUtensorMap mp = make_map_u8(Pq, k, K, bnt);
+    dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
+    if (bnt == 64)
+        k_tc_gemm<4, false, true, 64><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
+            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
+    else
+        k_tc_gemm<3, false, true, 128><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
+            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
+    DSANLS_LAUNCH_CHECK();
+    launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
+}
+
+// Per row of X (rows x K fp32): scale = max |x| / 448 (1 if the row is 0) and
+// Xq = e4m3(x / scale), round to nearest even with saturation.  The row
+// maxima come from many CTAs per row (atomicMax on the bits of non-negative
+// floats, whose integer order is their order: the result does not depend on
+// scheduling), then a grid-wide pass quantises.
+__global__ void k_row_absmax(const float *__restrict__ X, int64_t rows, int64_t K, int chunks,
+                             unsigned int *__restrict__ maxbits) {
+    __shared__ float red[256];
+    const int64_t r = blockIdx.x / chunks;
+    const int c = blockIdx.x % chunks;
+    const int64_t e0 = K * c / chunks, e1 = K * (c + 1) / chunks;
+    float mx = 0.0f;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) mx = fmaxf(mx, fabsf(X[r * K + e]));
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(&maxbits[r], __float_as_uint(red[0]));
+}
+
+__global__ void k_quant_rows_e4m3(const float *__restrict__ X, int64_t rows, int64_t K,
+                                  const unsigned int *__restrict__ maxbits, float *__restrict__ scale,
+                                  __nv_fp8_e4m3 *__restrict__ Xq) {
+    const int64_t total = rows * K;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / K;
+        const float mx = __uint_as_float(maxbits[r]);
+        const float sc = mx > 0.0f ? __fdiv_rn(mx, 448.0f) : 1.0f;
+        if (i == r * K) scale[r] = sc;
+        Xq[i] = __nv_fp8_e4m3(__fdiv_rn(X[i], sc));
+    }
+}
+
+void launch_quant_rows(const float *X, int64_t rows, int64_t K, float *scale, uint8_t *Xq, unsigned int *maxbits,
+                       cudaStream_t s) {
+    if (rows <= 0) return;
+    DSANLS_CUDA(cudaMemsetAsync(maxbits, 0, (size_t)rows * sizeof(unsigned int), s));
+    const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(K, 4096), ceil_div(4 * 152, rows)));
+    k_row_absmax<<<(unsigned)(rows * chunks), 256, 0, s>>>(X, rows, K, chunks, maxbits);
+    DSANLS_LAUNCH_CHECK();
+    k_quant_rows_e4m3<<<152 * 8, 256, 0, s>>>(X, rows, K, maxbits, scale, reinterpret_cast<__nv_fp8_e4m3 *>(Xq));
+    DSANLS_LAUNCH_CHECK();
 }
 
 __global__ void k_transpose_bf16(const float *__restrict__ in, int64_t rows, int64_t cols,
@@ -722,6 +802,8 @@ void prime_tc_attributes(int max_smem) {
     allow_max_dynamic_smem(k_tc_gemm<3, true, true>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, false, 64>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, false, false, 128>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, false, true, 64>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<3, false, true, 128>, max_smem);
 }
 
 }  // namespace dsanls

@@ -41,6 +41,15 @@ void launch_tc_gemm_bf16out(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int
 int64_t tc_skinny_part_elems(int64_t rows, int64_t K, int k);
 void launch_tc_skinny(const __nv_bfloat16 *X, const __nv_bfloat16 *Pt, int64_t rows, int64_t K, int k, float *part,
                       float *R, int *err, cudaStream_t s);
+// The same streaming product in fp8 E4M3: R[i][a] = xscale[i / 128] * pscale[a] *
+// sum_j Xq[i][j] Pq[a][j] (fp8 reassociated order; K a multiple of 16).
+int64_t tc_skinny_fp8_part_elems(int64_t rows, int64_t K, int k);
+void launch_tc_skinny_fp8(const uint8_t *Xq, const float *xscale, const uint8_t *Pq, const float *pscale,
+                          int64_t rows, int64_t K, int k, float *part, float *R, int *err, cudaStream_t s);
+// Per row scale = max |x| / 448 and Xq = e4m3(x / scale) (rows x K); maxbits is
+// scratch of `rows` words.
+void launch_quant_rows(const float *X, int64_t rows, int64_t K, float *scale, uint8_t *Xq, unsigned int *maxbits,
+                       cudaStream_t s);
 // out (cols x rows, bf16) = in^T for in rows x cols fp32 row-major.
 void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *out, cudaStream_t s);
 void prime_tc_attributes(int max_smem);

@@ -119,3 +119,26 @@ def test_batch_rejects_bad_arguments(pkg):
     with pytest.raises(pkg.DSANLSError):
         b.set_options(precision=pkg.BF16)
     b.close()
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_reassociated_one_iteration(pkg, use_graph):
+    """The batched reassociated order R_i = X_i (S_i B_i^T) against the FP64
+    oracle of the same order, per instance (1e-5)."""
+    Ms = _inputs(SHAPES)
+    b = pkg.Batch(SHAPES, use_graph=use_graph, order=pkg.ORDER_REASSOCIATED)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(1)
+    for i, (s, M) in enumerate(zip(SHAPES, Ms)):
+        U, V = b.factors(i)
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        M64 = M.astype(np.float64)
+        mu = method.mu_t(1.0, 1.0, 0)
+        S = method.Sketch(method.GAUSSIAN, s["seed"], 0, 0, s["n"], s["d"])
+        Uo = method.half_step(M64, V0.astype(np.float64), U0.astype(np.float64), S, 0, mu, reassociate=True)
+        Sp = method.Sketch(method.GAUSSIAN, s["seed"], 0, 1, s["m"], s["d_v"])
+        Vo = method.half_step(M64.T, Uo, V0.astype(np.float64), Sp, 0, mu, reassociate=True)
+        assert _rel(U, Uo) <= 1e-5, (i, _rel(U, Uo))
+        assert _rel(V, Vo) <= 1e-5, (i, _rel(V, Vo))
+    b.close()

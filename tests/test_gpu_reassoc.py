@@ -158,8 +158,6 @@ def test_graph_replay_equals_eager(pkg):
 def test_reassociated_rejects_other_forms(pkg):
     h = pkg.DSANLS(256, 128, 8, 64, pkg.GAUSSIAN, seed=0)
     with pytest.raises(pkg.DSANLSError):
-        h.set_options(precision=pkg.FP8, order=pkg.ORDER_REASSOCIATED)
-    with pytest.raises(pkg.DSANLSError):
         h.set_options(order=2)
     h.close()
     h = pkg.DSANLS(256, 128, 8, 64, pkg.SUBSAMPLE, seed=0)
@@ -200,17 +198,19 @@ def test_bf16_identity_half_steps(pkg, case, solver):
         assert _rel(got, exact) <= 1e-2, (side, _rel(got, exact))
 
 
-@pytest.mark.parametrize("precision,order", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0)])
-def test_rademacher_half_steps(pkg, precision, order):
-    """The +-1/sqrt(d) sketch runs through every dense-sketch path: FP32 and
-    BF16 in both orders and FP8 (paper order), against the matching oracle
-    models (FP32: 1e-5; bf16 / fp8 models: 3e-4)."""
+@pytest.mark.parametrize("kind", ["rademacher", "count"])
+@pytest.mark.parametrize("precision,order", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
+def test_other_dense_sketch_half_steps(pkg, kind, precision, order):
+    """The +-1/sqrt(d) and count sketches run through every dense-sketch path:
+    FP32, BF16 and FP8 in both orders, against the matching oracle models
+    (FP32: 1e-5; bf16 / fp8 models: 3e-4)."""
     m, n, k, d, d_v = 640, 528, 32, 264, 136
     M, _, _ = planted_dense(m, n, 16, 3)
     U, V = initial_factors(m, n, k, 4)
     M64 = M.astype(np.float64)
+    gkind, okind = ((pkg.RADEMACHER, method.RADEMACHER) if kind == "rademacher" else (pkg.COUNT, method.COUNT))
     for side, dd in ((0, d), (1, d_v)):
-        h = pkg.DSANLS(m, n, k, d, pkg.RADEMACHER, seed=9, d_v=d_v, precision=precision, order=order, t=5)
+        h = pkg.DSANLS(m, n, k, d, gkind, seed=9, d_v=d_v, precision=precision, order=order, t=5)
         h.set_dense(M)
         h.set_factors(U, V)
         h.half_step(side)
@@ -220,7 +220,7 @@ def test_rademacher_half_steps(pkg, precision, order):
         X = M64 if side == 0 else M64.T
         Y = (V if side == 0 else U).astype(np.float64)
         Z = (U if side == 0 else V).astype(np.float64)
-        S = method.Sketch(method.RADEMACHER, 9, 5, side, X.shape[1], dd)
+        S = method.Sketch(okind, 9, 5, side, X.shape[1], dd)
         mu = method.mu_t(1.0, 1.0, 5)
         want = method.half_step(X, Y, Z, S, 0, mu, bf16=precision == 1, fp8=(9, 5, side) if precision == 2 else None,
                                 reassociate=order == 1)
@@ -252,3 +252,47 @@ def test_bf16_reassociated_inner_steps(pkg, case):
         want = method.half_step(X, Y, Z, S, 0, method.mu_t(1.0, 1.0, 4), bf16=True, reassociate=True,
                                 inner_iters=8)
         assert _rel(got, want) <= 3e-4, (side, _rel(got, want))
+
+
+FP8_CASES = [(256, 128, 16, 256, 256), (1024, 816, 10, 104, 96), (640, 528, 64, 520, 264), (2064, 4112, 100, 512, 1024)]
+
+
+@pytest.mark.parametrize("case", FP8_CASES)
+def test_fp8_reassociated_half_steps(pkg, case):
+    """fp8 streaming product (M per 128-row block and P^T per row in E4M3)
+    against the oracle's fp8 model of this order <= 3e-4 (the same codes and
+    scales up to the rare rounding-boundary flip of a code), and plain FP64
+    <= 5e-2 (E4M3 keeps 3 fraction bits)."""
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 11)
+    U, V = initial_factors(m, n, k, 12)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        got = _run_half(pkg, m, n, k, d, d_v, side, U, V, 0, pkg.FP8, dense=M, t=3, seed=13)
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 13, 3, side, X.shape[1], dd)
+        mu = method.mu_t(1.0, 1.0, 3)
+        model = method.half_step(X, Y, Z, S, 0, mu, fp8=(13, 3, side), reassociate=True)
+        exact = method.half_step(X, Y, Z, S, 0, mu)
+        assert got.min() >= 0
+        assert _rel(got, model) <= 3e-4, (side, _rel(got, model))
+        assert _rel(got, exact) <= 5e-2, (side, _rel(got, exact))
+
+
+def test_fp8_reassociated_run_final_error(pkg):
+    """fp8 reassociated iterations plus 3 closing fp32 iterations end within
+    2e-3 of the oracle's final relative error."""
+    m, n, k, d, T = 1024, 816, 10, 104, 30
+    M, _, _ = planted_dense(m, n, k, 0)
+    U0, V0 = method.default_init(0, m, n, k)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=0, precision=pkg.FP8, order=pkg.ORDER_REASSOCIATED, use_graph=1)
+    h.set_dense(M)
+    h.step(T - 3)
+    h.set_options(precision=pkg.FP32, order=pkg.ORDER_PAPER)
+    h.step(3)
+    err = h.rel_error()
+    h.close()
+    _, _, errs = method.run(M, U0, V0, 0, T, method.Options(sketch=method.GAUSSIAN, d=d))
+    assert abs(err - errs[-1]) <= 2e-3, (err, errs[-1])

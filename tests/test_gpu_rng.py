@@ -47,6 +47,16 @@ def test_rademacher_field_bits(pkg, transposed, seed, stream, t, rows, cols):
     assert np.array_equal(np.ascontiguousarray(got).view(np.uint32), want.view(np.uint32))
 
 
+@pytest.mark.parametrize("transposed", [False, True])
+@pytest.mark.parametrize("seed,side,t,rows,cols", [(0, 0, 0, 800, 100), (3, 1, 9, 1001, 33), (7, 0, (1 << 33) + 1, 5, 7)])
+def test_count_field_bits(pkg, transposed, seed, side, t, rows, cols):
+    got = pkg.count_field(seed, side, t, rows, cols, transposed=transposed).cpu().numpy()
+    if transposed:
+        got = got.T
+    want = rng.count_field(seed, side, t, rows, cols)
+    assert np.array_equal(np.ascontiguousarray(got).view(np.uint32), want.view(np.uint32))
+
+
 def test_uniform_field_bits(pkg):
     got = pkg.uniform_field(9, 2, 0, 1003, 10).cpu().numpy()
     want = rng.uniform_field(9, 2, 0, 1003, 10)

@@ -85,7 +85,7 @@ def pin_pgd_identity(mod):
 # pins
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE, method.RADEMACHER])
+@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE, method.RADEMACHER, method.COUNT])
 def test_sketched_gradient_is_unbiased(kind):
     assert pin_unbiased_gradient(method, kind) < 0.08
 
@@ -496,3 +496,30 @@ def test_mutant_inner_prox_sign_is_caught():
     x = bad_inner(U, G, R, eta, mu, 20000)
     xs = omlp.prox_exact(G, mu, R + mu * U)
     assert np.max(np.abs(x - xs)) > 1e-3 * max(1.0, np.max(np.abs(xs)))
+
+
+def test_row_quantisation_error_bound():
+    """One scale per row: every entry within half an E4M3 quantum of its row
+    (relative 2^-4 above the subnormal range, scale 2^-9 below)."""
+    g = np.random.default_rng(13)
+    X = (g.standard_normal((40, 300)) * np.repeat([1.0, 1e3, 1e-3, 0.0], 10)[:, None]).astype(np.float32)
+    Xd = method.quantise_rows_e4m3(X)
+    for r in range(X.shape[0]):
+        row = X[r].astype(np.float64)
+        sc = np.abs(row).max() / 448.0 if np.abs(row).max() > 0 else 1.0
+        assert np.all(np.abs(Xd[r] - row) <= np.maximum(np.abs(row) * 2.0 ** -4, sc * 2.0 ** -9) * 1.0001)
+
+
+def test_reassociated_fp8_model_error():
+    """The fp8 reassociated model is within E4M3 accuracy of the exact terms:
+    relative error of R between the bf16 model's and 0.1, and B, G unchanged
+    from the bf16 model."""
+    M, U, V = _problem(256, 96, 6, 9)
+    S = method.Sketch(method.GAUSSIAN, 2, 1, 0, 96, 32)
+    _, Be, _, Re = method.sketched_terms(M, V, S)
+    _, Bb, Gb, Rb = method.sketched_terms_reassociated_bf16(M, V, S)
+    _, B8, G8, R8 = method.sketched_terms_reassociated_fp8(M, V, S)
+    assert np.array_equal(B8, Bb) and np.array_equal(G8, Gb)
+    e8 = np.linalg.norm(R8 - Re) / np.linalg.norm(Re)
+    eb = np.linalg.norm(Rb - Re) / np.linalg.norm(Re)
+    assert eb < e8 < 0.1

@@ -28,6 +28,7 @@ def _groups(k, seed, n_groups=2, rows=5):
         b = g.standard_normal((rows, k)) + 1.0
         Gn, bn, _, _ = mlp.normalise(G, 0.3, b)
         ys = np.abs(g.standard_normal((rows, k)))
+        ys[g.random((rows, k)) < 0.4] = 0.0  # NNLS minimisers have zero entries
         out.append((Gn, bn, ys))
     return out
 
@@ -155,3 +156,32 @@ def test_learned_fallback_with_plain_inner_steps():
     x, keep = mlp.learned_update(P, G, mu, R, Z, eta, 3, plain_iters=5)
     b = R + mu * Z
     assert np.all(mlp.prox_objective(G, mu, b, x) <= mlp.prox_objective(G, mu, b, xp) + 1e-12)
+
+
+def test_one_sided_loss_equals_relu_error_where_outputs_are_nonnegative():
+    """With every pre-activation output o >= 0 the training loss is the plain
+    1/2 mean ||max(o, 0) - y*||^2."""
+    k, h = 3, 7
+    P = _params(k, h, 1)
+    P["b3"] = P["b3"] + 50.0  # pushes every o above zero
+    groups = _groups(k, 2)
+    loss, _ = mlp.loss_and_grads(P, groups)
+    N = sum(g[1].shape[0] for g in groups)
+    ref = sum(0.5 * float(np.sum((mlp.forward(P, Gn, bn)[0] - ys) ** 2)) for Gn, bn, ys in groups) / N
+    assert abs(loss - ref) <= 1e-12 * max(1.0, ref)
+
+
+def test_dead_outputs_still_get_a_gradient_from_positive_targets():
+    """All outputs below zero: the ReLU error has no gradient, the training loss
+    still pulls the biases of outputs with positive targets up (negative
+    gradient) and leaves those whose targets are all zero alone."""
+    k, h = 3, 7
+    P = _params(k, h, 2)
+    P["b3"] = P["b3"] - 50.0
+    Gn, bn, ys = _groups(k, 3)[0]
+    ys = ys.copy()
+    ys[:, 0] = 0.0
+    ys[:, 1:] = np.abs(ys[:, 1:]) + 0.5
+    _, grads = mlp.loss_and_grads(P, [(Gn, bn, ys)])
+    assert grads["b3"][0] == 0.0
+    assert np.all(grads["b3"][1:] < 0.0)

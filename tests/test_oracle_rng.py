@@ -157,13 +157,14 @@ def test_subsample_inclusion_is_uniform():
     assert abs(pair / trials - p_pair) < 5 * math.sqrt(p_pair * (1 - p_pair) / trials)
 
 
-@pytest.mark.parametrize("kind", ["gaussian", "subsample", "rademacher"])
+@pytest.mark.parametrize("kind", ["gaussian", "subsample", "rademacher", "count"])
 def test_sketch_second_moment_is_identity(kind):
     """Assumption 1: E[S S^T] = I (Monte-Carlo over t)."""
     from oracle import method
     n, d, trials = 12, 4, 6000
     acc = np.zeros((n, n))
-    kinds = {"gaussian": method.GAUSSIAN, "subsample": method.SUBSAMPLE, "rademacher": method.RADEMACHER}
+    kinds = {"gaussian": method.GAUSSIAN, "subsample": method.SUBSAMPLE, "rademacher": method.RADEMACHER,
+             "count": method.COUNT}
     for t in range(trials):
         S = method.Sketch(kinds[kind], 21, t, 0, n, d).dense()
         acc += S @ S.T
@@ -191,3 +192,21 @@ def test_rademacher_field_values_and_balance():
     other_s = np.sign(rng.rademacher_field(5, 1, 3, 4096, d, sc))
     for o in (other_t, other_s):
         assert abs(np.mean(sgn * o)) < 5.0 / math.sqrt(sgn.size)
+
+
+def test_count_sketch_structure_and_law():
+    """One nonzero per row, equal to +-1; buckets uniform on [0, d) (chi-square)
+    and signs balanced (binomial); hashes differ between iterations and sides."""
+    n, d = 60000, 37
+    S = rng.count_field(4, 0, 9, n, d)
+    nz = S != 0
+    assert np.all(nz.sum(axis=1) == 1) and set(np.unique(S[nz]).tolist()) == {-1.0, 1.0}
+    h = np.argmax(nz, axis=1)
+    counts = np.bincount(h, minlength=d)
+    chi2 = float(np.sum((counts - n / d) ** 2 / (n / d)))
+    assert stats.chi2.sf(chi2, d - 1) > 1e-4
+    assert stats.binomtest(int((S[nz] > 0).sum()), n, 0.5).pvalue > 1e-4
+    h_t, _ = rng.count_buckets(4, 0, 10, n, d)
+    h_s, _ = rng.count_buckets(4, 1, 9, n, d)
+    for o in (h_t, h_s):
+        assert np.mean(o == h) < 1.0 / d + 5.0 * math.sqrt(1.0 / (d * n))
