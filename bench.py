@@ -61,9 +61,9 @@ WORKLOADS = {
                          "on ~1e7 triples harvested from seeds 1-20, evaluated on seed 21 to rel. error 0.05"),
     "batched": dict(batched=True, count=1024, m=0, n=0, k=0, d=0, d_v=0, sketch=0,
                     desc="1024 uneven planted instances (m in [128,4096], n in [64,2048], k in {8,16,32}), "
-                         "Gaussian d=max(4k,n/8), d'=max(4k,m/8), PGD, binary32"),
+                         "Gaussian d=max(4k,n/8), d'=max(4k,m/8), PGD"),
     "batched_small": dict(batched=True, count=64, m=0, n=0, k=0, d=0, d_v=0, sketch=0,
-                          desc="64 uneven planted instances (same recipe), binary32"),
+                          desc="64 uneven planted instances (same recipe)"),
     "dense_identity": dict(m=65536, n=16384, k=64, d=16384, d_v=65536, sketch=2, zero_frac=0.7, noise=0.01,
                            desc="dense 65536x16384 planted (k=64), identity sketch (unsketched subproblem; "
                                 "with --solver rcd --alpha 0 --beta 0 this is HALS)"),
@@ -507,7 +507,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense_gaussian")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="bf16")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default=None,
+                    help="arithmetic of the products (default: bf16; fp32 for the batched workloads)")
     ap.add_argument("--sketch", choices=["gaussian", "subsample", "rademacher", "count"], default=None,
                     help="sketch kind (default: the workload's)")
     ap.add_argument("--order", choices=["paper", "reassociated"], default=None,
@@ -524,6 +525,8 @@ def main():
                     help="also run T outer iterations of the fp32 and bf16 forms and report time to eps")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
+    if args.precision is None:
+        args.precision = "fp32" if w.get("batched") else "bf16"
     if args.order is not None:
         w["order"] = ["paper", "reassociated"].index(args.order)
     if args.sketch is not None:
@@ -808,7 +811,8 @@ def run_batch(args, w):
         dist.init_process_group("nccl")
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    b = pkg.Batch(specs, use_graph=1, order=order)
+    prec = {"fp32": pkg.FP32, "bf16": pkg.BF16}[args.precision]
+    b = pkg.Batch(specs, use_graph=1, order=order, precision=prec)
     for i, M in enumerate(Ms):
         b.set_dense(i, M)
     for _ in range(args.warmup):
@@ -854,7 +858,7 @@ def run_batch(args, w):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if prec == pkg.FP32 else "bf16", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "instances": len(specs),
                        "order": ["paper", "reassociated"][order],
                        "graph": True, "persistent_ctas": b.tuned_blocks(),

@@ -269,8 +269,11 @@ typedef struct dsanls_batch_ctx *dsanls_batch_t;
 int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const int32_t *k,
                         const int32_t *d, const int32_t *d_v, const uint64_t *seeds,
                         dsanls_batch_t *out);
-/* solver, alpha, beta, power_iters, t, use_graph, stream are used; precision
- * must be FP32, bound_clamp 0, d_v ignored (given per instance). */
+/* solver, alpha, beta, power_iters, t, use_graph, order, precision and stream
+ * are used; precision FP32 or BF16 (M_i, S_i, Y_i, B_i and A_i or P_i rounded
+ * to bf16 where they enter a product, fp32 accumulation, G_i in FP64 from the
+ * unrounded B_i), inner_iters 1, bound_clamp 0, d_v ignored (given per
+ * instance). */
 int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt);
 /* Dense M_i (m_i x n_i, row stride ld); copied, with its transpose. Synchronises. */
 int dsanls_batch_set_dense(dsanls_batch_t b, int32_t i, const float *M, int64_t ld, int32_t on_device);

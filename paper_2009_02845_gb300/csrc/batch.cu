@@ -7,7 +7,8 @@
 // iteration (both halves, five phases each) is captured once as a CUDA graph.
 //
 // Phases of a half-step (side 0: U against M_i and V_i; side 1: V against
-// M_i^T and U_i), binary32 unless stated:
+// M_i^T and U_i), binary32 unless stated (the bf16 form rounds M_i, S_i, Y_i,
+// B_i and A_i or P_i to bf16 where they enter a product, fp32 accumulation):
 //   sketch  S_i (K_i x d_i) Gaussian N(0, 1/d_i) from Philox keyed by seed_i
 //   B       B_i = Y_i^T S_i (k_i x d_i)                    (eq. def_A_B)
 //   AR      R_i = (X_i S_i) B_i^T per 64-row tile; the A tile lives only in
@@ -16,6 +17,8 @@
 //           R_i = X_i P_i per 64-row tile
 //   gram    G_i = B_i B_i^T in FP64, eta_i = 1/(lambda_max + mu_t)
 //   update  PGD step or Alg. 3 sweep per row
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -41,6 +44,16 @@ DSANLS_DEV int find_inst(const int64_t *prefix, int count, int64_t idx) {
 }
 
 DSANLS_DEV int64_t rows_of(const BatchInst &b, int side) { return side == 0 ? b.m : b.n; }
+
+// bf16 form: operands rounded to bf16 where they enter a product (fp32 accumulation)
+template <bool BF16>
+DSANLS_DEV float op(float x) {
+    return BF16 ? __bfloat162float(__float2bfloat16_rn(x)) : x;
+}
+template <bool BF16>
+DSANLS_DEV float ldx(const float *X, const __nv_bfloat16 *Xb, int64_t i) {
+    return BF16 ? __bfloat162float(Xb[i]) : X[i];
+}
 DSANLS_DEV int64_t kdim_of(const BatchInst &b, int side) { return side == 0 ? b.n : b.m; }
 DSANLS_DEV int d_of(const BatchInst &b, int side) { return side == 0 ? b.d : b.dv; }
 
@@ -71,6 +84,7 @@ __global__ void kb_sketch(const BatchInst *__restrict__ inst, int count, const i
 
 // ---- B = Y^T S: item = (instance, 64-column tile) --------------------------
 constexpr int BT = 64;
+template <bool BF16>
 __global__ void __launch_bounds__(256)
     kb_bmat(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
             int side, const float *__restrict__ factors, const float *__restrict__ S_all, float *__restrict__ B_all) {
@@ -96,11 +110,11 @@ __global__ void __launch_bounds__(256)
         for (int64_t l0 = 0; l0 < K; l0 += 32) {
             for (int e = threadIdx.x; e < 32 * 32; e += 256) {
                 const int l = e / 32, c = e % 32;
-                ys[l][c] = (l0 + l < K && c < k) ? Y[(l0 + l) * k + c] : 0.0f;
+                ys[l][c] = (l0 + l < K && c < k) ? op<BF16>(Y[(l0 + l) * k + c]) : 0.0f;
             }
             for (int e = threadIdx.x; e < 32 * BT; e += 256) {
                 const int l = e / BT, jj = e % BT;
-                ss[l][jj] = (l0 + l < K && j0 + jj < dd) ? S[(l0 + l) * dd + j0 + jj] : 0.0f;
+                ss[l][jj] = (l0 + l < K && j0 + jj < dd) ? op<BF16>(S[(l0 + l) * dd + j0 + jj]) : 0.0f;
             }
             __syncthreads();
 #pragma unroll 8
@@ -121,15 +135,21 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---- reassociated order ---------------------------------------------------
-// P = S B^T (K x k): item = (instance, 64-row tile of K); thread (rp, cg) owns
-// rows 2 rp, 2 rp + 1 and columns 4 cg .. 4 cg + 3; one FMA chain per output in
-// increasing j.
+// Both products stage 64-wide slabs of their operands in shared memory; the
+// next slab is loaded into registers while the current one is multiplied (the
+// global loads overlap the FMAs).  Thread (rp, cg) owns rows 2 rp, 2 rp + 1
+// and columns 4 cg .. 4 cg + 3 of a 64 x 32 output tile; one FMA chain per
+// output in increasing summation index.
 constexpr int P_ROWS = 64, P_JC = 64;
-__global__ void __launch_bounds__(256)
+constexpr int RP_ROWS = 64, RP_LC = 64;
+
+// P = S B^T (K x k): item = (instance, 64-row tile of K), sum over j < d.
+template <bool BF16>
+__global__ void __launch_bounds__(256, 3)
     kb_pmat(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
             int side, const float *__restrict__ S_all, const float *__restrict__ B_all, float *__restrict__ P_all) {
-    __shared__ float ss[P_ROWS][P_JC + 1];
-    __shared__ __align__(16) float bs[P_JC][32 + 4];  // bs[j][c] = B[c][j]
+    __shared__ float ss[P_ROWS][P_JC + 1];            // ss[r][j] = S[l0 + r][j0 + j]
+    __shared__ __align__(16) float bs[P_JC][32 + 4];  // bs[j][c] = B[c][j0 + j]
     __shared__ int item_s;
     const int rp = threadIdx.x / 8, cg = threadIdx.x % 8;
     while (true) {
@@ -144,17 +164,34 @@ __global__ void __launch_bounds__(256)
         const int64_t K = kdim_of(b, side);
         const float *S = S_all + b.offS;
         const float *B = B_all + b.offB;
-        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
-        for (int j0 = 0; j0 < dd; j0 += P_JC) {
-            for (int e = threadIdx.x; e < P_ROWS * P_JC; e += 256) {
-                const int r = e / P_JC, jj = e % P_JC;
-                ss[r][jj] = (l0 + r < K && j0 + jj < dd) ? S[(l0 + r) * dd + j0 + jj] : 0.0f;
+        float sreg[16], breg[8];
+        auto load = [&](int j0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = threadIdx.x + 256 * q, r = e / P_JC, jj = e % P_JC;
+                sreg[q] = (l0 + r < K && j0 + jj < dd) ? op<BF16>(S[(l0 + r) * dd + j0 + jj]) : 0.0f;
             }
-            for (int e = threadIdx.x; e < 32 * P_JC; e += 256) {
-                const int c = e / P_JC, jj = e % P_JC;
-                bs[jj][c] = (c < k && j0 + jj < dd) ? B[(int64_t)c * dd + j0 + jj] : 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = threadIdx.x + 256 * q, c = e / P_JC, jj = e % P_JC;
+                breg[q] = (c < k && j0 + jj < dd) ? op<BF16>(B[(int64_t)c * dd + j0 + jj]) : 0.0f;
+            }
+        };
+        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+        load(0);
+        for (int j0 = 0; j0 < dd; j0 += P_JC) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = threadIdx.x + 256 * q;
+                ss[e / P_JC][e % P_JC] = sreg[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = threadIdx.x + 256 * q;
+                bs[e % P_JC][e / P_JC] = breg[q];
             }
             __syncthreads();
+            if (j0 + P_JC < dd) load(j0 + P_JC);
 #pragma unroll 8
             for (int jj = 0; jj < P_JC; ++jj) {
                 const float s0 = ss[2 * rp][jj], s1 = ss[2 * rp + 1][jj];
@@ -175,19 +212,19 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = 4 * cg + q;
-                if (l < K && c < k) P[l * k + c] = acc[a][q];
+                if (l < K && c < k) P[l * k + c] = op<BF16>(acc[a][q]);
             }
         }
     }
 }
 
-// R = X P (rows x k): item = (instance, 64-row tile); thread (rp, cg) as above;
-// one FMA chain per output in increasing l.
-constexpr int RP_ROWS = 64, RP_LC = 32;
-__global__ void __launch_bounds__(256)
+// R = X P (rows x k): item = (instance, 64-row tile), sum over l < K.
+template <bool BF16>
+__global__ void __launch_bounds__(256, 3)
     kb_rp(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
-          int side, const float *__restrict__ data, const float *__restrict__ P_all, float *__restrict__ R_all) {
-    __shared__ float xs[RP_LC][RP_ROWS + 1];        // xs[l][r] = X[r0 + r][l0 + l]
+          int side, const float *__restrict__ data, const __nv_bfloat16 *__restrict__ data_b,
+          const float *__restrict__ P_all, float *__restrict__ R_all) {
+    __shared__ float xs[RP_LC][RP_ROWS + 1];           // xs[l][r] = X[r0 + r][l0 + l]
     __shared__ __align__(16) float ps[RP_LC][32 + 4];  // ps[l][c] = P[l0 + l][c]
     __shared__ int item_s;
     const int rp = threadIdx.x / 8, cg = threadIdx.x % 8;
@@ -201,19 +238,38 @@ __global__ void __launch_bounds__(256)
         const int64_t r0 = (int64_t)items[it].y * RP_ROWS;
         const int k = b.k;
         const int64_t K = kdim_of(b, side), rows = rows_of(b, side);
-        const float *X = data + b.offM + (side == 0 ? 0 : b.m * b.n);
+        const int64_t xoff = b.offM + (side == 0 ? 0 : b.m * b.n);
+        const float *X = data + xoff;
+        const __nv_bfloat16 *Xb = data_b + xoff;
         const float *P = P_all + b.offR;
-        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
-        for (int64_t l0 = 0; l0 < K; l0 += RP_LC) {
-            for (int e = threadIdx.x; e < RP_ROWS * RP_LC; e += 256) {
-                const int r = e / RP_LC, l = e % RP_LC;
-                xs[l][r] = (r0 + r < rows && l0 + l < K) ? X[(r0 + r) * K + l0 + l] : 0.0f;
+        float xreg[16], preg[8];
+        auto load = [&](int64_t l0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = threadIdx.x + 256 * q, r = e / RP_LC, l = e % RP_LC;
+                xreg[q] = (r0 + r < rows && l0 + l < K) ? ldx<BF16>(X, Xb, (r0 + r) * K + l0 + l) : 0.0f;
             }
-            for (int e = threadIdx.x; e < RP_LC * 32; e += 256) {
-                const int l = e / 32, c = e % 32;
-                ps[l][c] = (l0 + l < K && c < k) ? P[(l0 + l) * k + c] : 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = threadIdx.x + 256 * q, l = e / 32, c = e % 32;
+                preg[q] = (l0 + l < K && c < k) ? P[(l0 + l) * k + c] : 0.0f;
+            }
+        };
+        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+        load(0);
+        for (int64_t l0 = 0; l0 < K; l0 += RP_LC) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = threadIdx.x + 256 * q;
+                xs[e % RP_LC][e / RP_LC] = xreg[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = threadIdx.x + 256 * q;
+                ps[e / 32][e % 32] = preg[q];
             }
             __syncthreads();
+            if (l0 + RP_LC < K) load(l0 + RP_LC);
 #pragma unroll 8
             for (int l = 0; l < RP_LC; ++l) {
                 const float x0 = xs[l][2 * rp], x1 = xs[l][2 * rp + 1];
@@ -244,10 +300,11 @@ __global__ void __launch_bounds__(256)
 constexpr int AR_ROWS = 64;
 constexpr int AR_DC = 64;
 constexpr int AR_KC = 16;
+template <bool BF16>
 __global__ void __launch_bounds__(256)
     kb_ar(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
-          int side, const float *__restrict__ data, const float *__restrict__ S_all, const float *__restrict__ B_all,
-          float *__restrict__ R_all) {
+          int side, const float *__restrict__ data, const __nv_bfloat16 *__restrict__ data_b,
+          const float *__restrict__ S_all, const float *__restrict__ B_all, float *__restrict__ R_all) {
     __shared__ __align__(16) float xs[AR_KC][AR_ROWS + 4];
     __shared__ __align__(16) float ss[AR_KC][AR_DC + 4];
     __shared__ float as[AR_ROWS][AR_DC + 1];
@@ -265,7 +322,9 @@ __global__ void __launch_bounds__(256)
         const int64_t r0 = (int64_t)items[it].y * AR_ROWS;
         const int k = b.k, dd = d_of(b, side);
         const int64_t K = kdim_of(b, side), rows = rows_of(b, side);
-        const float *X = data + b.offM + (side == 0 ? 0 : b.m * b.n);
+        const int64_t xoff = b.offM + (side == 0 ? 0 : b.m * b.n);
+        const float *X = data + xoff;
+        const __nv_bfloat16 *Xb = data_b + xoff;
         const float *S = S_all + b.offS;
         const float *B = B_all + b.offB;
         float racc[8];
@@ -280,11 +339,11 @@ __global__ void __launch_bounds__(256)
             for (int64_t l0 = 0; l0 < K; l0 += AR_KC) {
                 for (int e = threadIdx.x; e < AR_ROWS * AR_KC; e += 256) {
                     const int r = e / AR_KC, l = e % AR_KC;
-                    xs[l][r] = (r0 + r < rows && l0 + l < K) ? X[(r0 + r) * K + l0 + l] : 0.0f;
+                    xs[l][r] = (r0 + r < rows && l0 + l < K) ? ldx<BF16>(X, Xb, (r0 + r) * K + l0 + l) : 0.0f;
                 }
                 for (int e = threadIdx.x; e < AR_KC * AR_DC; e += 256) {
                     const int l = e / AR_DC, j = e % AR_DC;
-                    ss[l][j] = (l0 + l < K && dc + j < dd) ? S[(l0 + l) * dd + dc + j] : 0.0f;
+                    ss[l][j] = (l0 + l < K && dc + j < dd) ? op<BF16>(S[(l0 + l) * dd + dc + j]) : 0.0f;
                 }
                 __syncthreads();
 #pragma unroll
@@ -304,10 +363,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) as[ty * 4 + a][tx * 4 + c] = acc[a][c];
+                for (int c = 0; c < 4; ++c) as[ty * 4 + a][tx * 4 + c] = op<BF16>(acc[a][c]);
             for (int e = threadIdx.x; e < 32 * AR_DC; e += 256) {
                 const int c = e / AR_DC, j = e % AR_DC;
-                bs[c][j] = (c < k && dc + j < dd) ? B[(int64_t)c * dd + dc + j] : 0.0f;
+                bs[c][j] = (c < k && dc + j < dd) ? op<BF16>(B[(int64_t)c * dd + dc + j]) : 0.0f;
             }
             __syncthreads();
             const int jmax = min(AR_DC, dd - dc);
@@ -545,19 +604,34 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
     kb_sketch<<<cfg.sketch_blocks, 256, 0, s>>>(g.inst, count, g.sketch_prefix[side], side, g.t_dev, g.S);
     DSANLS_LAUNCH_CHECK();
     mark(1);
-    kb_bmat<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.bitems[side], g.nb[side], ctr + 0, side, g.factors, g.S,
-                                                 g.B);
+    if (g.bf16)
+        kb_bmat<true><<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.bitems[side], g.nb[side], ctr + 0, side,
+                                                           g.factors, g.S, g.B);
+    else
+        kb_bmat<false><<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.bitems[side], g.nb[side], ctr + 0, side,
+                                                            g.factors, g.S, g.B);
     DSANLS_LAUNCH_CHECK();
     mark(2);
+    const int pb = cfg.persistent_blocks;
     if (g.order == 1) {
-        kb_pmat<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.pitems[side], g.np[side], ctr + 4, side, g.S, g.B,
-                                                     g.P);
+        if (g.bf16)
+            kb_pmat<true><<<pb, 256, 0, s>>>(g.inst, g.pitems[side], g.np[side], ctr + 4, side, g.S, g.B, g.P);
+        else
+            kb_pmat<false><<<pb, 256, 0, s>>>(g.inst, g.pitems[side], g.np[side], ctr + 4, side, g.S, g.B, g.P);
         DSANLS_LAUNCH_CHECK();
-        kb_rp<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.P,
-                                                   g.R);
+        if (g.bf16)
+            kb_rp<true><<<pb, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.data_b, g.P,
+                                          g.R);
+        else
+            kb_rp<false><<<pb, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.data_b, g.P,
+                                           g.R);
     } else {
-        kb_ar<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.S,
-                                                   g.B, g.R);
+        if (g.bf16)
+            kb_ar<true><<<pb, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.data_b, g.S,
+                                          g.B, g.R);
+        else
+            kb_ar<false><<<pb, 256, 0, s>>>(g.inst, g.aritems[side], g.nar[side], ctr + 1, side, g.data, g.data_b, g.S,
+                                           g.B, g.R);
     }
     DSANLS_LAUNCH_CHECK();
     mark(3);

@@ -1,6 +1,7 @@
 // Batched sketched ANLS: instance table and launch plumbing.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +24,8 @@ struct BatchDev {
     BatchInst *inst = nullptr;
     float *data = nullptr, *factors = nullptr, *S = nullptr, *B = nullptr, *R = nullptr;
     float *P = nullptr;  // reassociated order: P_i = S_i B_i^T (K_i x k_i, at the offsets of R)
+    __nv_bfloat16 *data_b = nullptr;  // bf16 form: bf16 copy of data
+    int bf16 = 0;
     double *G = nullptr;
     int2 *bitems[2] = {nullptr, nullptr}, *aritems[2] = {nullptr, nullptr}, *uitems[2] = {nullptr, nullptr};
     int nb[2] = {0, 0}, nar[2] = {0, 0}, nu[2] = {0, 0};

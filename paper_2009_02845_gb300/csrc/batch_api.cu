@@ -34,6 +34,8 @@ struct dsanls_batch_ctx {
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_launches = 0;
     std::vector<char> has_data;
+    int64_t data_elems = 0;   // packed M_i and M_i^T
+    bool bf16_stale = true;   // the bf16 copy of data no longer matches it
     std::vector<double> mm;  // ||M_i||^2
     double *work = nullptr;
     double *dres = nullptr;  // residual^2 per instance
@@ -94,6 +96,14 @@ void iteration(dsanls_batch_ctx *b, cudaStream_t s) {
     launch_increment_t(b->g.t_dev, 1, s);
 }
 
+// bf16 form: bring the bf16 copy of the packed data up to date (after set_dense)
+void refresh_bf16(dsanls_batch_ctx *b, cudaStream_t s) {
+    if (b->g.bf16 && b->bf16_stale) {
+        launch_copy_cast_bf16(b->g.data, b->data_elems, b->g.data_b, s);
+        b->bf16_stale = false;
+    }
+}
+
 // ---- autotuner: persistent CTAs per SM, cached per batch shape and dtype ----
 std::mutex g_tune_mutex;
 std::map<std::string, int> g_tune_cache;
@@ -106,7 +116,7 @@ std::string tune_key(const dsanls_batch_ctx *b) {
         shapes.push_back(buf);
     }
     std::sort(shapes.begin(), shapes.end());
-    const std::string form = b->g.order == 1 ? "f32r" : "f32";
+    const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "");
     std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
     return std::to_string(std::hash<std::string>()(key)) + "/" + form;
@@ -268,6 +278,7 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
         g.count = count;
         balloc(g.inst, count);
         balloc(g.data, offM);
+        b->data_elems = offM;
         balloc(g.factors, offF);
         balloc(g.S, offS);
         balloc(g.B, offB);
@@ -322,7 +333,8 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
     if (!b) return DSANLS_EINVAL;
     if (!opt) return bfail(b, DSANLS_EINVAL, "options pointer is NULL");
     if (opt->solver != DSANLS_SOLVER_PGD && opt->solver != DSANLS_SOLVER_RCD) return bfail(b, DSANLS_EINVAL, "unknown solver");
-    if (opt->precision != DSANLS_PREC_FP32) return bfail(b, DSANLS_EINVAL, "the batched form computes in binary32");
+    if (opt->precision != DSANLS_PREC_FP32 && opt->precision != DSANLS_PREC_BF16)
+        return bfail(b, DSANLS_EINVAL, "the batched form computes in binary32 or bf16");
     if (opt->power_iters < 0 || opt->power_iters > 10000 || !(opt->alpha >= 0.0) || !(opt->beta >= 0.0) ||
         !std::isfinite(opt->alpha) || !std::isfinite(opt->beta) || opt->t < 0)
         return bfail(b, DSANLS_EINVAL, "bad power_iters, alpha, beta or t");
@@ -337,8 +349,12 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
         b->g.alpha = opt->alpha;
         b->g.beta = opt->beta;
         b->g.power_iters = opt->power_iters;
-        if (b->g.order != opt->order) b->tuned = false;  // the launch geometry is tuned per order
+        if (b->g.order != opt->order || b->g.bf16 != (opt->precision == DSANLS_PREC_BF16))
+            b->tuned = false;  // the launch geometry is tuned per form
         b->g.order = opt->order;
+        b->g.bf16 = opt->precision == DSANLS_PREC_BF16 ? 1 : 0;
+        if (b->g.bf16 && !b->g.data_b) balloc(b->g.data_b, b->data_elems);
+        b->bf16_stale = true;
         drop_graph(b);
         if (opt->t != b->t_host) {
             b->t_host = opt->t;
@@ -366,6 +382,7 @@ int dsanls_batch_set_dense(dsanls_batch_t b, int32_t i, const float *M, int64_t 
         DSANLS_CUDA(cudaStreamSynchronize(s));
         b->mm[i] = v;
         b->has_data[i] = 1;
+        b->bf16_stale = true;
         return DSANLS_OK;
     });
 }
@@ -391,6 +408,7 @@ int dsanls_batch_step(dsanls_batch_t b, int32_t outer_iters) {
         if (!c) return bfail(b, DSANLS_ESTATE, "every instance needs dsanls_batch_set_dense first");
     return bguard(b, [&]() {
         cudaStream_t s = b->stream();
+        refresh_bf16(b, s);
         if (!b->tuned) autotune(b);
         if (b->opt.use_graph) {
             if (!b->graph) {
@@ -469,6 +487,7 @@ int dsanls_batch_profile(dsanls_batch_t b, double *ms) {
     cudaEvent_t ev[6] = {};
     int created = 0;
     const int rc = bguard(b, [&]() {
+        refresh_bf16(b, b->stream());
         if (!b->tuned) autotune(b);
         for (; created < 6; ++created) DSANLS_CUDA(cudaEventCreate(&ev[created]));
         cudaStream_t s = b->stream();
@@ -501,7 +520,7 @@ void dsanls_batch_destroy(dsanls_batch_t b) {
     if (b->opt.stream) cudaStreamSynchronize((cudaStream_t)b->opt.stream);
     drop_graph(b);
     BatchDev &g = b->g;
-    bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.P); bfree(g.G);
+    bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.P); bfree(g.G); bfree(g.data_b);
     for (int side = 0; side < 2; ++side) {
         bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]); bfree(g.pitems[side]);
     }

@@ -117,7 +117,11 @@ def test_batch_rejects_bad_arguments(pkg):
         b.step(1)
     assert e.value.code == -4
     with pytest.raises(pkg.DSANLSError):
-        b.set_options(precision=pkg.BF16)
+        b.set_options(precision=pkg.FP8)
+    with pytest.raises(pkg.DSANLSError):
+        b.set_options(inner_iters=4)
+    with pytest.raises(pkg.DSANLSError):
+        b.set_options(order=2)
     b.close()
 
 
@@ -141,4 +145,30 @@ def test_batch_reassociated_one_iteration(pkg, use_graph):
         Vo = method.half_step(M64.T, Uo, V0.astype(np.float64), Sp, 0, mu, reassociate=True)
         assert _rel(U, Uo) <= 1e-5, (i, _rel(U, Uo))
         assert _rel(V, Vo) <= 1e-5, (i, _rel(V, Vo))
+    b.close()
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_batch_bf16_one_iteration(pkg, order):
+    """The bf16 batched form against the oracle's bf16 model of the same order,
+    per instance (<= 3e-4: fp32 accumulation order and the rare bf16 rounding
+    flip of an fp32-accumulated A or P entry)."""
+    Ms = _inputs(SHAPES)
+    b = pkg.Batch(SHAPES, use_graph=1, order=order, precision=pkg.BF16)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(1)
+    for i, (s, M) in enumerate(zip(SHAPES, Ms)):
+        U, V = b.factors(i)
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        M64 = M.astype(np.float64)
+        mu = method.mu_t(1.0, 1.0, 0)
+        S = method.Sketch(method.GAUSSIAN, s["seed"], 0, 0, s["n"], s["d"])
+        Uo = method.half_step(M64, V0.astype(np.float64), U0.astype(np.float64), S, 0, mu, bf16=True,
+                              reassociate=order == 1)
+        Sp = method.Sketch(method.GAUSSIAN, s["seed"], 0, 1, s["m"], s["d_v"])
+        Vo = method.half_step(M64.T, U.astype(np.float64), V0.astype(np.float64), Sp, 0, mu, bf16=True,
+                              reassociate=order == 1)
+        assert _rel(U, Uo) <= 3e-4, (i, _rel(U, Uo))
+        assert _rel(V, Vo) <= 3e-4, (i, _rel(V, Vo))
     b.close()
