@@ -33,7 +33,8 @@ SUBSAMPLE = 1
 IDENTITY = 2
 RADEMACHER = 3
 COUNT = 4
-DENSE_KINDS = (GAUSSIAN, RADEMACHER, COUNT)
+SRHT = 5
+DENSE_KINDS = (GAUSSIAN, RADEMACHER, COUNT, SRHT)
 
 PGD = 0
 RCD = 1
@@ -43,13 +44,15 @@ SIDE_V = 1
 
 
 class Sketch:
-    """The random matrix S^t (n x d) of Section 3.4, in one of five kinds.
+    """The random matrix S^t (n x d) of Section 3.4, in one of six kinds.
 
     kind GAUSSIAN: dense, entries N(0, 1/d) from the Philox field.
     kind RADEMACHER: dense, entries +-1/sqrt(d) with the sign of the entry's
         Philox word (one of Section 3.4's "other choices" of random matrix).
     kind COUNT: count sketch, one entry +-1 per row at a hashed column
         (another of those choices; E[S S^T] = I without scaling).
+    kind SRHT: subsampled randomized Hadamard transform sqrt(p/d) D H R
+        (the third of those choices), materialised as a dense +-1/sqrt(d) matrix.
     kind SUBSAMPLE: columns sqrt(n/d) e_{J_p}, J drawn without replacement.
     kind IDENTITY: S = I (requires d = n); the unsketched subproblem.
     """
@@ -67,6 +70,11 @@ class Sketch:
         elif kind == COUNT:
             self.scale = np.float32(1.0)
             self.dense32 = rng.count_field(seed, side, t, n, d)
+        elif kind == SRHT:
+            if d > rng.srht_pad(n):
+                raise ValueError("SRHT needs d <= the padded order")
+            self.scale = rng.gaussian_scale(d)
+            self.dense32 = rng.srht_field(seed, side, t, n, d, self.scale)
         elif kind == SUBSAMPLE:
             if d > n:
                 raise ValueError("subsampling needs d <= n")
@@ -191,6 +199,8 @@ def sketched_terms_fp8(X, Y, S, seed, t, side):
     bf16 form."""
     if S.kind == COUNT:
         z = rng.count_field(seed, side, t, S.n, S.d)
+    elif S.kind == SRHT:
+        z = rng.srht_field(seed, side, t, S.n, S.d, np.float32(1.0))
     else:
         unit = rng.rademacher_field if S.kind == RADEMACHER else rng.gaussian_field
         z = unit(seed, side, t, S.n, S.d, np.float32(1.0))

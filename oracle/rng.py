@@ -156,6 +156,53 @@ def count_field(seed, side, t, n, d):
     return S
 
 
+STREAM_SRHT = 0x40      # SRHT row signs (| side); its column subset uses side 0x40 | side
+
+
+def srht_pad(n):
+    """Order of the Walsh-Hadamard matrix of an SRHT over n rows: the least
+    power of two >= n (the rows are padded with zeros up to it)."""
+    p = 1
+    while p < n:
+        p *= 2
+    return p
+
+
+def srht_signs(seed, side, t, n):
+    """Diagonal D of the SRHT: -1 where the field word of (row i, column 0) of
+    stream 0x40 | side has its top bit set, else +1."""
+    w = field_words(seed, STREAM_SRHT | side, t, n, 1)[:, 0]
+    return np.where((w >> np.uint32(31)) != 0, -1.0, 1.0)
+
+
+def srht_columns(seed, side, t, n, d):
+    """The d Hadamard columns R picks, drawn without replacement from
+    {0..srht_pad(n)-1} by the subsampling draw with side 0x40 | side; ascending."""
+    return subsample_indices(seed, STREAM_SRHT | side, t, srht_pad(n), d)
+
+
+def _parity(x):
+    """Parity of the set bits of each entry of a non-negative int array (< 2^32)."""
+    x = np.asarray(x, dtype=np.uint64).copy()
+    for sh in (16, 8, 4, 2, 1):
+        x ^= x >> np.uint64(sh)
+    return (x & np.uint64(1)).astype(np.int64)
+
+
+def srht_field(seed, side, t, n, d, scale):
+    """The n x d subsampled randomized Hadamard transform S = sqrt(p/d) D H R
+    (Section 3.4's SRHT; p = srht_pad(n), H the p x p Walsh-Hadamard matrix of
+    Sylvester's construction normalised by 1/sqrt(p), R the columns
+    srht_columns) restricted to its first n rows, as binary32: entry (i, j) =
+    D_i (-1)^popcount(i & J_j) * scale, with scale = float32(1/sqrt(d)) for
+    the SRHT itself (sqrt(p/d) / sqrt(p)), or 1 for the unit draws."""
+    D = srht_signs(seed, side, t, n)
+    J = srht_columns(seed, side, t, n, d).astype(np.int64)
+    i = np.arange(n, dtype=np.int64)
+    H = 1.0 - 2.0 * _parity(i[:, None] & J[None, :])
+    return (D[:, None] * H * np.float64(np.float32(scale))).astype(np.float32)
+
+
 def uniform_field(seed, stream, t, rows, cols):
     out = np.empty((rows, cols), dtype=np.float32)
     lib().ora_uniform_field(seed, stream, t, rows, cols, _ptr(out, ctypes.c_float))

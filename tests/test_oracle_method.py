@@ -85,7 +85,7 @@ def pin_pgd_identity(mod):
 # pins
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE, method.RADEMACHER, method.COUNT])
+@pytest.mark.parametrize("kind", [method.GAUSSIAN, method.SUBSAMPLE, method.RADEMACHER, method.COUNT, method.SRHT])
 def test_sketched_gradient_is_unbiased(kind):
     assert pin_unbiased_gradient(method, kind) < 0.08
 

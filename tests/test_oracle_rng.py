@@ -157,14 +157,14 @@ def test_subsample_inclusion_is_uniform():
     assert abs(pair / trials - p_pair) < 5 * math.sqrt(p_pair * (1 - p_pair) / trials)
 
 
-@pytest.mark.parametrize("kind", ["gaussian", "subsample", "rademacher", "count"])
+@pytest.mark.parametrize("kind", ["gaussian", "subsample", "rademacher", "count", "srht"])
 def test_sketch_second_moment_is_identity(kind):
     """Assumption 1: E[S S^T] = I (Monte-Carlo over t)."""
     from oracle import method
     n, d, trials = 12, 4, 6000
     acc = np.zeros((n, n))
     kinds = {"gaussian": method.GAUSSIAN, "subsample": method.SUBSAMPLE, "rademacher": method.RADEMACHER,
-             "count": method.COUNT}
+             "count": method.COUNT, "srht": method.SRHT}
     for t in range(trials):
         S = method.Sketch(kinds[kind], 21, t, 0, n, d).dense()
         acc += S @ S.T
@@ -210,3 +210,101 @@ def test_count_sketch_structure_and_law():
     h_s, _ = rng.count_buckets(4, 1, 9, n, d)
     for o in (h_t, h_s):
         assert np.mean(o == h) < 1.0 / d + 5.0 * math.sqrt(1.0 / (d * n))
+
+
+def _fwht(X):
+    """Unnormalised fast Walsh-Hadamard transform along the last axis (length a
+    power of two): the butterfly (a, b) -> (a + b, a - b) over doubling spans."""
+    X = np.array(X, dtype=np.float64)
+    p = X.shape[-1]
+    h = 1
+    while h < p:
+        Y = X.reshape(X.shape[:-1] + (p // (2 * h), 2, h))
+        a, b = Y[..., 0, :].copy(), Y[..., 1, :].copy()
+        Y[..., 0, :], Y[..., 1, :] = a + b, a - b
+        X = Y.reshape(X.shape)
+        h *= 2
+    return X
+
+
+@pytest.mark.parametrize("n,d", [(16, 4), (13, 5), (100, 37), (128, 128), (70, 100)])
+def test_srht_field_is_signs_times_sylvester_hadamard_columns(n, d):
+    """S = sqrt(p/d) D H R: built here from scipy's Hadamard matrix (Sylvester's
+    construction, a library routine) with the oracle's D and J, it matches the
+    oracle's closed-form entries; every entry is +-float32(1/sqrt(d))."""
+    from scipy.linalg import hadamard
+    p = rng.srht_pad(n)
+    assert p >= n and p & (p - 1) == 0 and (p == 1 or p // 2 < n)
+    sc = rng.gaussian_scale(d)
+    S = rng.srht_field(9, 1, 4, n, d, sc)
+    D = rng.srht_signs(9, 1, 4, n)
+    J = rng.srht_columns(9, 1, 4, n, d)
+    assert len(J) == d and np.all(np.diff(J) > 0) and J[0] >= 0 and J[-1] < p
+    want = math.sqrt(p / d) * (D[:, None] * hadamard(p)[:n][:, J] / math.sqrt(p))
+    assert np.array_equal(np.sign(S), np.sign(want))
+    assert np.all(np.abs(S) == sc)
+    np.testing.assert_allclose(S, want, rtol=1e-6, atol=0)
+
+
+def test_srht_with_every_column_is_orthogonal():
+    """With d = p every Hadamard column is kept and S S^T = (p s^2) I exactly
+    (H is orthogonal, D^2 = I): the off-diagonal sums cancel to zero."""
+    for n in (64, 50):
+        p = rng.srht_pad(n)
+        sc = rng.gaussian_scale(p)
+        S = rng.srht_field(2, 0, 7, n, p, sc).astype(np.float64)
+        SS = S @ S.T
+        off = SS - np.diag(np.diag(SS))
+        assert np.all(off == 0.0)
+        assert np.all(np.diag(SS) == p * np.float64(sc) ** 2)
+
+
+def test_srht_product_equals_fast_transform():
+    """X S = (fwht(X D) / sqrt(p))[:, J] sqrt(p/d), the transform form of the
+    SRHT (the rows of X padded with zeros to p columns)."""
+    g = np.random.default_rng(3)
+    n, d = 200, 48
+    p = rng.srht_pad(n)
+    X = g.standard_normal((7, n))
+    S = rng.srht_field(5, 0, 11, n, d, rng.gaussian_scale(d)).astype(np.float64)
+    D = rng.srht_signs(5, 0, 11, n)
+    J = rng.srht_columns(5, 0, 11, n, d)
+    Xp = np.zeros((7, p))
+    Xp[:, :n] = X * D[None, :]
+    want = _fwht(Xp)[:, J] / math.sqrt(d)
+    np.testing.assert_allclose(X @ S, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+
+
+def test_srht_signs_and_columns_law():
+    """Row signs balanced (binomial); the column subset is the subsampling draw
+    over {0..p-1} (inclusion uniform, chi-square over t); signs and subsets
+    differ between iterations and sides."""
+    n = 50000
+    D = rng.srht_signs(6, 0, 2, n)
+    assert set(np.unique(D).tolist()) == {-1.0, 1.0}
+    assert stats.binomtest(int((D > 0).sum()), n, 0.5).pvalue > 1e-4
+    for o in (rng.srht_signs(6, 0, 3, n), rng.srht_signs(6, 1, 2, n)):
+        assert abs(np.mean(D * o)) < 5.0 / math.sqrt(n)
+    n, d, trials = 20, 6, 4000
+    p = rng.srht_pad(n)
+    counts = np.zeros(p)
+    for t in range(trials):
+        counts[rng.srht_columns(1, 1, t, n, d)] += 1
+    expected = trials * d / p
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    assert stats.chi2.sf(chi2, p - 1) > 1e-4
+    # its own stream: not the plain subsampling draw over the same range
+    assert not np.array_equal(rng.srht_columns(1, 0, 0, 2000, 100), rng.subsample_indices(1, 0, 0, 2048, 100))
+
+
+def test_srht_pin_catches_a_wrong_hadamard_index(monkeypatch):
+    """A planted mistake in the oracle's entry rule (the parity taken with the
+    lowest bit forced on, i.e. a wrong Hadamard index) fails the Sylvester pin."""
+    from scipy.linalg import hadamard
+    monkeypatch.setattr(rng, "_parity", lambda x, f=rng._parity: f(np.asarray(x) | 1))
+    n, d = 16, 8
+    S = rng.srht_field(9, 1, 4, n, d, rng.gaussian_scale(d))
+    D = rng.srht_signs(9, 1, 4, n)
+    J = rng.srht_columns(9, 1, 4, n, d)
+    want = D[:, None] * hadamard(n)[:, J]
+    assert not np.array_equal(np.sign(S), np.sign(want))
