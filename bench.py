@@ -388,7 +388,7 @@ def run_ours(args, w):
     phases = [h.profile_half_step(0, reps=2), h.profile_half_step(1, reps=2)]
     peaks, peak_src = _peaks()
     m, n, d, d_v, k = w["m"], w["n"], w["d"], w["d_v"], w["k"]
-    dense_sketch = w["sketch"] in (0, 3, 4)  # Gaussian, Rademacher, count: S a dense matrix
+    dense_sketch = w["sketch"] in (0, 3, 4, 5)  # Gaussian, Rademacher, count, SRHT: S a dense matrix
     if (dense_sketch and order == 1) or (w["sketch"] == 2 and not w.get("sparse")):
         # reassociated order (R = X P) or identity sketch (R = X Y): the streaming
         # product reads X once (bf16 or fp32) and the k x K factor, and writes R
@@ -509,7 +509,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense_gaussian")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default=None,
                     help="arithmetic of the products (default: bf16; fp32 for the batched workloads)")
-    ap.add_argument("--sketch", choices=["gaussian", "subsample", "rademacher", "count"], default=None,
+    ap.add_argument("--sketch", choices=["gaussian", "subsample", "rademacher", "count", "srht"], default=None,
                     help="sketch kind (default: the workload's)")
     ap.add_argument("--order", choices=["paper", "reassociated"], default=None,
                     help="order of R = M S B^T for Gaussian sketches (default: the workload's)")
@@ -530,7 +530,7 @@ def main():
     if args.order is not None:
         w["order"] = ["paper", "reassociated"].index(args.order)
     if args.sketch is not None:
-        w["sketch"] = {"gaussian": 0, "subsample": 1, "rademacher": 3, "count": 4}[args.sketch]
+        w["sketch"] = {"gaussian": 0, "subsample": 1, "rademacher": 3, "count": 4, "srht": 5}[args.sketch]
     if w.get("learned"):
         run_learned(args, w)
     elif w.get("compare"):

@@ -65,6 +65,18 @@ extern "C" {
                                       0x30 | side); E[S S^T] = I, no scaling.  Runs
                                       through the dense-sketch paths like GAUSSIAN
                                       (S materialised; not by the batched form)   */
+#define DSANLS_SKETCH_SRHT 5       /* subsampled randomized Hadamard transform
+                                      S = sqrt(p/d) D H R (Section 3.4's third named
+                                      choice): p = the dimension rounded up to a
+                                      power of two, H the normalised p x p Sylvester
+                                      Walsh-Hadamard matrix, D row signs (top bit of
+                                      the row's word, column 0, stream 0x40 | side),
+                                      R d of the p columns drawn without replacement
+                                      (the subsampling draw with side 0x40 | side),
+                                      ascending.  Entry (i, j) = D_i (-1)^popcount(
+                                      i & J_j) / sqrt(d); needs d <= p.  Runs through
+                                      the dense-sketch paths like GAUSSIAN (S
+                                      materialised; not by the batched form)       */
 
 /* ---- subproblem solvers (Section 3.5) -------------------------------- */
 #define DSANLS_SOLVER_PGD 0   /* one projected gradient step, eq. gradient_descent */
@@ -238,6 +250,16 @@ int dsanls_rademacher_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64
  * transposed as above. */
 int dsanls_count_field(uint64_t seed, uint32_t side, uint64_t t, int64_t rows, int64_t cols,
                        int32_t transposed, float *out, void *stream);
+
+/* SRHT S (rows x cols) of DSANLS_SKETCH_SRHT for side (0 or 1) and iteration
+ * t, times scale (1/sqrt(cols) gives the sketch itself, 1 the unit draws):
+ * S[i][j] = D_i (-1)^popcount(i & J_j) scale.  Needs 1 <= cols <= p (rows
+ * rounded up to a power of two) and rows <= 2^30; out is a device buffer of
+ * rows x cols floats (cols x rows if transposed).  Allocates and frees its
+ * own scratch (J and a p-bit bitmap) and synchronises the stream; EINVAL on
+ * bad sizes, ENOMEM / ECUDA from the allocation or the launches. */
+int dsanls_srht_field(uint64_t seed, uint32_t side, uint64_t t, int64_t rows, int64_t cols,
+                      float scale, int32_t transposed, float *out, void *stream);
 
 /* Uniform [0,1) field X[i][j] = (w >> 8) * 2^-24, row-major rows x cols. */
 int dsanls_uniform_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t rows,

@@ -10,11 +10,11 @@ The library must have been built (``paper_2009_02845_gb300.build.build()``);
 importing the binding without it raises ImportError -- there is no CPU path.
 """
 from ._lib import (  # noqa: F401
-    DSANLS, Batch, MLP, DSANLSError, GAUSSIAN, SUBSAMPLE, IDENTITY, RADEMACHER, COUNT, PGD, RCD, FP32, BF16, FP8,
+    DSANLS, Batch, MLP, DSANLSError, GAUSSIAN, SUBSAMPLE, IDENTITY, RADEMACHER, COUNT, SRHT, PGD, RCD, FP32, BF16, FP8,
     ORDER_PAPER, ORDER_REASSOCIATED,
     STREAM_SKETCH_U, STREAM_SKETCH_V, STREAM_INIT_U, STREAM_INIT_V,
     lib, lib_path, kernel_launches, PHASES, gram_noalloc, philox_field, gaussian_field, rademacher_field, count_field,
-    uniform_field,
+    srht_field, uniform_field,
     subsample_indices,
     EXPORTED_SYMBOLS,
 )

@@ -8,7 +8,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_PKG, "libdsanls.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENUMERIC, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-GAUSSIAN, SUBSAMPLE, IDENTITY, RADEMACHER, COUNT = 0, 1, 2, 3, 4
+GAUSSIAN, SUBSAMPLE, IDENTITY, RADEMACHER, COUNT, SRHT = 0, 1, 2, 3, 4, 5
 PGD, RCD = 0, 1
 FP32, BF16, FP8 = 0, 1, 2
 ORDER_PAPER, ORDER_REASSOCIATED = 0, 1
@@ -21,7 +21,7 @@ EXPORTED_SYMBOLS = [
     "dsanls_default_options", "dsanls_create", "dsanls_get_options", "dsanls_set_options",
     "dsanls_set_dense", "dsanls_set_csr", "dsanls_set_factors", "dsanls_step", "dsanls_half_step",
     "dsanls_rel_error", "dsanls_get_factors", "dsanls_get_gram", "dsanls_sync", "dsanls_last_error",
-    "dsanls_destroy", "dsanls_philox_field", "dsanls_gaussian_field", "dsanls_rademacher_field", "dsanls_count_field",
+    "dsanls_destroy", "dsanls_philox_field", "dsanls_gaussian_field", "dsanls_rademacher_field", "dsanls_count_field", "dsanls_srht_field",
     "dsanls_uniform_field",
     "dsanls_subsample_indices", "dsanls_profile_half_step", "dsanls_kernel_launches", "dsanls_gram_noalloc",
     "dsanls_batch_create", "dsanls_batch_set_options", "dsanls_batch_set_dense", "dsanls_batch_set_factors",
@@ -90,6 +90,7 @@ def lib():
             "dsanls_gaussian_field": ([u64, u32, u64, i64, i64, ctypes.c_float, i32, vp, vp], ctypes.c_int),
             "dsanls_rademacher_field": ([u64, u32, u64, i64, i64, ctypes.c_float, i32, vp, vp], ctypes.c_int),
             "dsanls_count_field": ([u64, u32, u64, i64, i64, i32, vp, vp], ctypes.c_int),
+            "dsanls_srht_field": ([u64, u32, u64, i64, i64, ctypes.c_float, i32, vp, vp], ctypes.c_int),
             "dsanls_uniform_field": ([u64, u32, u64, i64, i64, vp, vp], ctypes.c_int),
             "dsanls_subsample_indices": ([u64, u32, u64, i64, i32, vp, vp], ctypes.c_int),
             "dsanls_profile_half_step": ([vp, i32, i32, vp], ctypes.c_int),
@@ -202,6 +203,15 @@ def count_field(seed, side, t, rows, cols, transposed=False, device="cuda"):
     out = torch.empty(shape, dtype=torch.float32, device=device)
     _check(lib().dsanls_count_field(seed, side, t, rows, cols, int(bool(transposed)), _dev_ptr(out), _stream_ptr()),
            "count_field")
+    return out
+
+
+def srht_field(seed, side, t, rows, cols, scale, transposed=False, device="cuda"):
+    torch = _torch()
+    shape = (cols, rows) if transposed else (rows, cols)
+    out = torch.empty(shape, dtype=torch.float32, device=device)
+    _check(lib().dsanls_srht_field(seed, side, t, rows, cols, float(scale), int(bool(transposed)), _dev_ptr(out),
+                                   _stream_ptr()), "srht_field")
     return out
 
 

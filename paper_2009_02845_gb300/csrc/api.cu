@@ -51,14 +51,27 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
-// Gaussian and Rademacher sketches are dense matrices drawn from the field
+// Gaussian, Rademacher, count and SRHT sketches are dense matrices drawn from the field
 bool dense_kind(int kind) {
-    return kind == DSANLS_SKETCH_GAUSSIAN || kind == DSANLS_SKETCH_RADEMACHER || kind == DSANLS_SKETCH_COUNT;
+    return kind == DSANLS_SKETCH_GAUSSIAN || kind == DSANLS_SKETCH_RADEMACHER || kind == DSANLS_SKETCH_COUNT ||
+           kind == DSANLS_SKETCH_SRHT;
 }
 
 // generator of a dense sketch kind (DRAW_* of the field kernels)
 int draw_kind(int kind) {
-    return kind == DSANLS_SKETCH_RADEMACHER ? DRAW_RADEMACHER : (kind == DSANLS_SKETCH_COUNT ? DRAW_COUNT : DRAW_GAUSS);
+    switch (kind) {
+        case DSANLS_SKETCH_RADEMACHER: return DRAW_RADEMACHER;
+        case DSANLS_SKETCH_COUNT: return DRAW_COUNT;
+        case DSANLS_SKETCH_SRHT: return DRAW_SRHT;
+        default: return DRAW_GAUSS;
+    }
+}
+
+// order of the Walsh-Hadamard matrix of an SRHT over K rows: the least power of two >= K
+int64_t srht_pad(int64_t K) {
+    int64_t p = 1;
+    while (p < K) p <<= 1;
+    return p;
 }
 
 int kp_bucket(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 64 ? 64 : 128)); }
@@ -185,6 +198,8 @@ void check_sketch(int kind, int64_t K, int64_t dd, const char *what) {
     if (dd < 1) throw ArgError{std::string(what) + " must be >= 1"};
     if (kind == DSANLS_SKETCH_SUBSAMPLE && dd > K)
         throw ArgError{std::string(what) + ": subsampling needs sketch size <= dimension"};
+    if (kind == DSANLS_SKETCH_SRHT && dd > srht_pad(K))
+        throw ArgError{std::string(what) + ": the SRHT needs sketch size <= the dimension rounded up to a power of two"};
     if (kind == DSANLS_SKETCH_IDENTITY && dd != K)
         throw ArgError{std::string(what) + ": the identity sketch needs sketch size == dimension"};
     if (dd > (1 << 30)) throw ArgError{std::string(what) + " too large"};
@@ -217,7 +232,8 @@ void prepare(dsanls_ctx *h) {
     const int64_t kmax = std::max(m, n);
     dalloc(h->S, (gauss && !bf16) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->Sb, (gauss && bf16) ? std::max(n * h->d, m * dv) : 0);
-    dalloc(h->J, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? dmax : 0);
+    const bool srht = h->sketch == DSANLS_SKETCH_SRHT;
+    dalloc(h->J, (h->sketch == DSANLS_SKETCH_SUBSAMPLE || srht) ? dmax : 0);
     dalloc(h->A, (gauss && !bf16 && !reas) ? std::max(m * h->d, n * dv) : 0);
     dalloc(h->P, (reas && !bf16) ? kmax * k : 0);
     dalloc(h->Sn, (reas && bf16) ? std::max(n * h->d, m * dv) : 0);
@@ -240,7 +256,8 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->R, std::max(m, n) * k);
     dalloc(h->Rpart, (gauss && bf16 && !reas) ? tc_rpart_elems(std::max(m, n), dmax, k) : 0);
     dalloc(h->Sq, (gauss && fp8 && !reas) ? std::max(n * h->d, m * dv) : 0);
-    dalloc(h->bits, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? ceil_div(std::max(m, n), 32) + 1 : 0);
+    dalloc(h->bits, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? ceil_div(std::max(m, n), 32) + 1
+                    : (srht ? ceil_div(srht_pad(std::max(m, n)), 32) + 1 : 0));
     std::copy(key, key + 7, h->cfg_key);
 }
 
@@ -281,19 +298,26 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         const bool tc = dense && (h->opt.precision == DSANLS_PREC_BF16 || fp8);
         const bool reas = h->opt.order == DSANLS_ORDER_REASSOCIATED;
         const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
+        // SRHT: the sampled Hadamard columns J (dd of srht_pad(K), side 0x40 | side)
+        const int32_t *hcols = nullptr;
+        if (h->sketch == DSANLS_SKETCH_SRHT) {
+            launch_subsample(h->seed, 0x40u | (uint32_t)side, 0, h->t_dev, srht_pad(K), dd, h->J, h->bits, s);
+            hcols = h->J;
+        }
         // S (K x dd), N(0, 1/dd) entries of the field, stream `side`: fp32 S for the
         // CUDA-core form, bf16 S^T (K-major operand) for the tensor-core forms, and
         // for the fp8 form also fp8 S^T of the unit-variance draws; the reassociated
         // bf16 form also keeps bf16 S (d-major operand of P^T = B S^T)
         if (tc && reas)
-            launch_gaussian_pair(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sn, rade, 0, s);
+            launch_gaussian_pair(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sn, rade, hcols, 0, s);
         else if (fp8)
-            launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, rade, s);
+            launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, rade, hcols, s);
         else if (tc)
             launch_gaussian_field<__nv_bfloat16>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, true, h->Sb, rade,
-                                                 s);
+                                                 hcols, s);
         else
-            launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, rade, s);
+            launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, rade,
+                                         hcols, s);
         mark(pe, DSANLS_PHASE_B, s);
         if (tc) {
             // B = Y^T S (k x dd) on tensor cores from bf16 Y^T and S^T, split-K
@@ -574,8 +598,9 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
     *out = nullptr;
     if (m < 1 || n < 1 || k < 1 || k > 128 || d < 1) return DSANLS_EINVAL;
     if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return DSANLS_EINVAL;
-    if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_COUNT) return DSANLS_EINVAL;
+    if (sketch_kind < DSANLS_SKETCH_GAUSSIAN || sketch_kind > DSANLS_SKETCH_SRHT) return DSANLS_EINVAL;
     if (sketch_kind == DSANLS_SKETCH_SUBSAMPLE && d > n) return DSANLS_EINVAL;
+    if (sketch_kind == DSANLS_SKETCH_SRHT && d > srht_pad(n)) return DSANLS_EINVAL;
     if (sketch_kind == DSANLS_SKETCH_IDENTITY && d != n) return DSANLS_EINVAL;
     dsanls_ctx *h = nullptr;
     try {
@@ -649,7 +674,7 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
         }
         if (opt->order != DSANLS_ORDER_PAPER && opt->order != DSANLS_ORDER_REASSOCIATED) throw ArgError{"unknown order"};
         if (opt->order == DSANLS_ORDER_REASSOCIATED && !dense_kind(h->sketch))
-            throw ArgError{"the reassociated order needs a Gaussian or Rademacher sketch"};
+            throw ArgError{"the reassociated order needs a dense sketch (Gaussian, Rademacher, count or SRHT)"};
         if (opt->power_iters < 0 || opt->power_iters > 10000) throw ArgError{"power_iters out of range"};
         if (opt->inner_iters < 1 || opt->inner_iters > 256) throw ArgError{"inner_iters must be in 1..256"};
         if (opt->inner_iters > 1 && opt->solver != DSANLS_SOLVER_PGD)
@@ -1056,7 +1081,7 @@ int dsanls_gaussian_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64_t
     if (rows * cols > 0 && !out) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
         launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out, DRAW_GAUSS,
-                                     (cudaStream_t)stream);
+                                     nullptr, (cudaStream_t)stream);
         return DSANLS_OK;
     });
 }
@@ -1067,7 +1092,7 @@ int dsanls_rademacher_field(uint64_t seed, uint32_t stream_id, uint64_t t, int64
     if (rows * cols > 0 && !out) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
         launch_gaussian_field<float>(seed, stream_id, t, nullptr, rows, cols, scale, transposed != 0, out,
-                                     DRAW_RADEMACHER, (cudaStream_t)stream);
+                                     DRAW_RADEMACHER, nullptr, (cudaStream_t)stream);
         return DSANLS_OK;
     });
 }
@@ -1078,7 +1103,39 @@ int dsanls_count_field(uint64_t seed, uint32_t side, uint64_t t, int64_t rows, i
     if (rows * cols > 0 && !out) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
         launch_gaussian_field<float>(seed, side, t, nullptr, rows, cols, 1.0f, transposed != 0, out, DRAW_COUNT,
-                                     (cudaStream_t)stream);
+                                     nullptr, (cudaStream_t)stream);
+        return DSANLS_OK;
+    });
+}
+
+int dsanls_srht_field(uint64_t seed, uint32_t side, uint64_t t, int64_t rows, int64_t cols, float scale,
+                      int32_t transposed, float *out, void *stream) {
+    if (rows < 1 || cols < 1 || rows > (1ll << 30) || cols > srht_pad(rows) || side > 0xf || !out)
+        return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        const int64_t p = srht_pad(rows);
+        cudaStream_t s = (cudaStream_t)stream;
+        int32_t *J = nullptr;      // scratch: the sampled Hadamard columns
+        uint32_t *bits = nullptr;  // scratch: their membership bitmap
+        DSANLS_CUDA(cudaMalloc((void **)&J, (size_t)cols * sizeof(int32_t)));
+        const cudaError_t ea = cudaMalloc((void **)&bits, (size_t)ceil_div(p, 32) * sizeof(uint32_t));
+        if (ea != cudaSuccess) {
+            cudaFree(J);
+            DSANLS_CUDA(ea);
+        }
+        try {
+            launch_subsample(seed, 0x40u | side, t, nullptr, p, (int)cols, J, bits, s);
+            launch_gaussian_field<float>(seed, side, t, nullptr, rows, cols, scale, transposed != 0, out, DRAW_SRHT,
+                                         J, s);
+        } catch (...) {
+            cudaFree(J);
+            cudaFree(bits);
+            throw;
+        }
+        const cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(J);
+        cudaFree(bits);
+        DSANLS_CUDA(e);
         return DSANLS_OK;
     });
 }

@@ -153,17 +153,33 @@ DSANLS_DEV void count4(uint64_t seed, uint32_t side, uint64_t t, uint32_t row4, 
     }
 }
 
+// SRHT entries of rows 4*row4..+3 at a column whose Hadamard index is hcol:
+// the row sign D_i (top bit of the row's word of stream 0x40 | side at column
+// 0; set: -1) times the Sylvester entry (-1)^popcount(i & hcol).
+DSANLS_DEV void srht4(uint64_t seed, uint32_t side, uint64_t t, uint32_t row4, uint32_t hcol, float z[4]) {
+    const Philox4 b = field_block(seed, 0x40u | side, t, row4, 0u);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t i = 4u * row4 + (uint32_t)r;
+        const uint32_t neg = (word_of(b, r) >> 31) ^ ((uint32_t)__popc(i & hcol) & 1u);
+        z[r] = neg ? -1.0f : 1.0f;
+    }
+}
+
 // Unit draws of the dense sketch kinds for one Philox block:
-// KIND 0 Gaussian (Box-Muller), 1 Rademacher (sign of each word), 2 count sketch.
-constexpr int DRAW_GAUSS = 0, DRAW_RADEMACHER = 1, DRAW_COUNT = 2;
+// KIND 0 Gaussian (Box-Muller), 1 Rademacher (sign of each word), 2 count
+// sketch, 3 SRHT (`hcols` = the sampled Hadamard column of each sketch column).
+constexpr int DRAW_GAUSS = 0, DRAW_RADEMACHER = 1, DRAW_COUNT = 2, DRAW_SRHT = 3;
 
 template <int KIND>
 DSANLS_DEV void unit_draw4(uint64_t seed, uint32_t stream_id, uint64_t t, uint32_t row4, uint32_t col, uint32_t d,
-                           float z[4]) {
+                           const int32_t *hcols, float z[4]) {
     if (KIND == DRAW_RADEMACHER)
         rademacher4(seed, stream_id, t, row4, col, z);
     else if (KIND == DRAW_COUNT)
         count4(seed, stream_id, t, row4, col, d, z);
+    else if (KIND == DRAW_SRHT)
+        srht4(seed, stream_id, t, row4, (uint32_t)__ldg(hcols + col), z);
     else
         gaussian4(seed, stream_id, t, row4, col, z);
 }

@@ -34,19 +34,23 @@ void launch_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, i
                         cudaStream_t s);
 template <typename OutT>
 void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_t *t_dev, int64_t rows,
-                           int64_t cols, float scale, bool transposed, OutT *out, int kind, cudaStream_t s);
+                           int64_t cols, float scale, bool transposed, OutT *out, int kind, const int32_t *hcols,
+                           cudaStream_t s);
 void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, float *out,
                           cudaStream_t s);
-// The dense sketch fields below draw z by Box-Muller (kind DRAW_GAUSS), as the
-// sign of each field word (DRAW_RADEMACHER) or as count sketch entries
-// (DRAW_COUNT: the bucket and sign of each row, stream 0x30 | sid).
+// The dense sketch fields draw z by Box-Muller (kind DRAW_GAUSS), as the
+// sign of each field word (DRAW_RADEMACHER), as count sketch entries
+// (DRAW_COUNT: the bucket and sign of each row, stream 0x30 | sid) or as SRHT
+// entries (DRAW_SRHT: row sign of stream 0x40 | sid times the Sylvester entry
+// of the sampled Hadamard column hcols[j]; hcols is unused by the other kinds).
 // S^T (cols x rows) as bf16 of z * scale and as fp8 E4M3 of z (t from t_dev).
 void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_b, uint8_t *out_q, int kind, cudaStream_t s);
+                          __nv_bfloat16 *out_b, uint8_t *out_q, int kind, const int32_t *hcols, cudaStream_t s);
 // bf16 of z * scale as S^T (out_t, cols x rows) and S (out_n, rows x cols), t from t_dev;
 // max_ctas > 0 caps the grid (the CTAs then walk the tiles).
 void launch_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, int kind, int max_ctas, cudaStream_t s);
+                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, int kind, const int32_t *hcols, int max_ctas,
+                          cudaStream_t s);
 // J (d entries, ascending) = the sampled columns of {0..n-1}; bits (ceil(n/32)
 // words, scratch) is left holding their membership bitmap.
 void launch_subsample(uint64_t seed, uint32_t side, uint64_t t, const int64_t *t_dev, int64_t n, int d,

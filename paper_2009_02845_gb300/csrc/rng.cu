@@ -37,7 +37,7 @@ __global__ void k_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t r
 // t is read from device memory when t_dev != nullptr (graph replays).
 template <bool TRANSPOSED, typename OutT, int KIND>
 __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, const int64_t *t_dev,
-                                 int64_t rows, int64_t cols, float scale, OutT *out) {
+                                 int64_t rows, int64_t cols, float scale, const int32_t *hcols, OutT *out) {
     const int64_t nb4 = (rows + 3) >> 2;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nb4 * cols) return;
@@ -51,7 +51,7 @@ __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, c
         q = idx / cols;
     }
     float z[4];
-    unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, z);
+    unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, hcols, z);
 #pragma unroll
     for (int r = 0; r < 4; ++r) z[r] = __fmul_rn(z[r], scale);
     const int64_t i0 = 4 * q;
@@ -74,14 +74,14 @@ __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, c
 // S^T in two forms at once (cols x rows): bf16 of z * scale and fp8 E4M3 of z.
 template <int KIND>
 __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols,
-                                float scale, __nv_bfloat16 *out_b, __nv_fp8_e4m3 *out_q) {
+                                float scale, const int32_t *hcols, __nv_bfloat16 *out_b, __nv_fp8_e4m3 *out_q) {
     const int64_t nb4 = (rows + 3) >> 2;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nb4 * cols) return;
     const uint64_t t = (uint64_t)*t_dev;
     const int64_t q = idx % nb4, j = idx / nb4;
     float z[4];
-    unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, z);
+    unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, hcols, z);
     const int64_t i0 = 4 * q;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -104,7 +104,7 @@ constexpr int PAIR_ROWS = 128, PAIR_COLS = 64, PAIR_LD = PAIR_ROWS + 4;  // 264-
 template <int KIND>
 __global__ void __launch_bounds__(256)
     k_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                    __nv_bfloat16 *__restrict__ out_t, __nv_bfloat16 *__restrict__ out_n) {
+                    const int32_t *hcols, __nv_bfloat16 *__restrict__ out_t, __nv_bfloat16 *__restrict__ out_n) {
     __shared__ __align__(16) __nv_bfloat16 tile[PAIR_COLS][PAIR_LD];
     const uint64_t t = (uint64_t)*t_dev;
     const int64_t tiles_x = (cols + PAIR_COLS - 1) / PAIR_COLS;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256)
             const int64_t j = c0 + cc;
             if (j >= cols || 4 * q >= rows) continue;
             float z[4];
-            unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, z);
+            unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, hcols, z);
             __nv_bfloat16 v[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) v[r] = __float2bfloat16_rn(__fmul_rn(z[r], scale));
@@ -146,33 +146,34 @@ __global__ void __launch_bounds__(256)
 }
 
 void launch_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, int kind, int max_ctas, cudaStream_t s) {
+                          __nv_bfloat16 *out_t, __nv_bfloat16 *out_n, int kind, const int32_t *hcols, int max_ctas,
+                          cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return;
     int64_t tiles = ceil_div(cols, PAIR_COLS) * ceil_div(rows, PAIR_ROWS);
     if (max_ctas > 0 && tiles > max_ctas) tiles = max_ctas;
     if (tiles > (1ll << 31) - 1) tiles = (1ll << 31) - 1;
-    if (kind == DRAW_RADEMACHER)
-        k_gaussian_pair<DRAW_RADEMACHER><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t,
-                                                                         out_n);
-    else if (kind == DRAW_COUNT)
-        k_gaussian_pair<DRAW_COUNT><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
-    else
-        k_gaussian_pair<DRAW_GAUSS><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_t, out_n);
+#define DSANLS_PAIR_LAUNCH(KD) \
+    k_gaussian_pair<KD><<<(unsigned)tiles, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, hcols, out_t, out_n)
+    if (kind == DRAW_RADEMACHER) DSANLS_PAIR_LAUNCH(DRAW_RADEMACHER);
+    else if (kind == DRAW_COUNT) DSANLS_PAIR_LAUNCH(DRAW_COUNT);
+    else if (kind == DRAW_SRHT) DSANLS_PAIR_LAUNCH(DRAW_SRHT);
+    else DSANLS_PAIR_LAUNCH(DRAW_GAUSS);
+#undef DSANLS_PAIR_LAUNCH
     DSANLS_LAUNCH_CHECK();
 }
 
 void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
-                          __nv_bfloat16 *out_b, uint8_t *out_q, int kind, cudaStream_t s) {
+                          __nv_bfloat16 *out_b, uint8_t *out_q, int kind, const int32_t *hcols, cudaStream_t s) {
     const int64_t total = ((rows + 3) >> 2) * cols;
     if (total == 0) return;
     const unsigned g = (unsigned)ceil_div(total, 256);
     __nv_fp8_e4m3 *q = reinterpret_cast<__nv_fp8_e4m3 *>(out_q);
-    if (kind == DRAW_RADEMACHER)
-        k_gaussian_dual<DRAW_RADEMACHER><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b, q);
-    else if (kind == DRAW_COUNT)
-        k_gaussian_dual<DRAW_COUNT><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b, q);
-    else
-        k_gaussian_dual<DRAW_GAUSS><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, out_b, q);
+#define DSANLS_DUAL_LAUNCH(KD) k_gaussian_dual<KD><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, hcols, out_b, q)
+    if (kind == DRAW_RADEMACHER) DSANLS_DUAL_LAUNCH(DRAW_RADEMACHER);
+    else if (kind == DRAW_COUNT) DSANLS_DUAL_LAUNCH(DRAW_COUNT);
+    else if (kind == DRAW_SRHT) DSANLS_DUAL_LAUNCH(DRAW_SRHT);
+    else DSANLS_DUAL_LAUNCH(DRAW_GAUSS);
+#undef DSANLS_DUAL_LAUNCH
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -281,28 +282,32 @@ void launch_field_words(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, i
 
 template <typename OutT>
 void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_t *t_dev, int64_t rows,
-                           int64_t cols, float scale, bool transposed, OutT *out, int kind, cudaStream_t s) {
+                           int64_t cols, float scale, bool transposed, OutT *out, int kind, const int32_t *hcols,
+                           cudaStream_t s) {
     const int64_t total = ((rows + 3) >> 2) * cols;
     if (total == 0) return;
     const unsigned grid = (unsigned)ceil_div(total, 256);
 #define DSANLS_FIELD_LAUNCH(TR, KD) \
-    k_gaussian_field<TR, OutT, KD><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, out)
+    k_gaussian_field<TR, OutT, KD><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, hcols, out)
     if (transposed) {
         if (kind == DRAW_RADEMACHER) DSANLS_FIELD_LAUNCH(true, DRAW_RADEMACHER);
         else if (kind == DRAW_COUNT) DSANLS_FIELD_LAUNCH(true, DRAW_COUNT);
+        else if (kind == DRAW_SRHT) DSANLS_FIELD_LAUNCH(true, DRAW_SRHT);
         else DSANLS_FIELD_LAUNCH(true, DRAW_GAUSS);
     } else {
         if (kind == DRAW_RADEMACHER) DSANLS_FIELD_LAUNCH(false, DRAW_RADEMACHER);
         else if (kind == DRAW_COUNT) DSANLS_FIELD_LAUNCH(false, DRAW_COUNT);
+        else if (kind == DRAW_SRHT) DSANLS_FIELD_LAUNCH(false, DRAW_SRHT);
         else DSANLS_FIELD_LAUNCH(false, DRAW_GAUSS);
     }
 #undef DSANLS_FIELD_LAUNCH
     DSANLS_LAUNCH_CHECK();
 }
 template void launch_gaussian_field<float>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t, int64_t,
-                                           float, bool, float *, int, cudaStream_t);
+                                           float, bool, float *, int, const int32_t *, cudaStream_t);
 template void launch_gaussian_field<__nv_bfloat16>(uint64_t, uint32_t, uint64_t, const int64_t *, int64_t,
-                                                   int64_t, float, bool, __nv_bfloat16 *, int, cudaStream_t);
+                                                   int64_t, float, bool, __nv_bfloat16 *, int, const int32_t *,
+                                                   cudaStream_t);
 
 void launch_uniform_field(uint64_t seed, uint32_t sid, uint64_t t, int64_t rows, int64_t cols, float *out,
                           cudaStream_t s) {

@@ -198,17 +198,18 @@ def test_bf16_identity_half_steps(pkg, case, solver):
         assert _rel(got, exact) <= 1e-2, (side, _rel(got, exact))
 
 
-@pytest.mark.parametrize("kind", ["rademacher", "count"])
+@pytest.mark.parametrize("kind", ["rademacher", "count", "srht"])
 @pytest.mark.parametrize("precision,order", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
 def test_other_dense_sketch_half_steps(pkg, kind, precision, order):
-    """The +-1/sqrt(d) and count sketches run through every dense-sketch path:
-    FP32, BF16 and FP8 in both orders, against the matching oracle models
-    (FP32: 1e-5; bf16 / fp8 models: 3e-4)."""
+    """The +-1/sqrt(d), count and SRHT sketches run through every dense-sketch
+    path: FP32, BF16 and FP8 in both orders, against the matching oracle
+    models (FP32: 1e-5; bf16 / fp8 models: 3e-4)."""
     m, n, k, d, d_v = 640, 528, 32, 264, 136
     M, _, _ = planted_dense(m, n, 16, 3)
     U, V = initial_factors(m, n, k, 4)
     M64 = M.astype(np.float64)
-    gkind, okind = ((pkg.RADEMACHER, method.RADEMACHER) if kind == "rademacher" else (pkg.COUNT, method.COUNT))
+    gkind, okind = {"rademacher": (pkg.RADEMACHER, method.RADEMACHER), "count": (pkg.COUNT, method.COUNT),
+                    "srht": (pkg.SRHT, method.SRHT)}[kind]
     for side, dd in ((0, d), (1, d_v)):
         h = pkg.DSANLS(m, n, k, d, gkind, seed=9, d_v=d_v, precision=precision, order=order, t=5)
         h.set_dense(M)

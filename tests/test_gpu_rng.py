@@ -57,6 +57,29 @@ def test_count_field_bits(pkg, transposed, seed, side, t, rows, cols):
     assert np.array_equal(np.ascontiguousarray(got).view(np.uint32), want.view(np.uint32))
 
 
+@pytest.mark.parametrize("transposed", [False, True])
+@pytest.mark.parametrize("seed,side,t,rows,cols", [
+    (0, 0, 0, 800, 100), (3, 1, 9, 1001, 33), (7, 0, (1 << 33) + 1, 5, 7), (2, 1, 4, 512, 512), (5, 0, 3, 1, 1),
+    (11, 1, 6, 16384, 2048), (4, 0, 1, 3000, 4096)])
+def test_srht_field_bits(pkg, transposed, seed, side, t, rows, cols):
+    """SRHT entries bit-exact with the oracle (signs, sampled Hadamard columns
+    over the padded order, Sylvester parity), including d = p (every column)
+    and d > rows (allowed up to the padded order)."""
+    scale = rng.gaussian_scale(cols)
+    got = pkg.srht_field(seed, side, t, rows, cols, scale, transposed=transposed).cpu().numpy()
+    if transposed:
+        got = got.T
+    want = rng.srht_field(seed, side, t, rows, cols, scale)
+    assert np.array_equal(np.ascontiguousarray(got).view(np.uint32), want.view(np.uint32))
+
+
+def test_srht_field_rejects_bad_sizes(pkg):
+    with pytest.raises(pkg.DSANLSError):
+        pkg.srht_field(0, 0, 0, 1000, 1025, 1.0)  # cols above the padded order 1024
+    with pytest.raises(pkg.DSANLSError):
+        pkg.srht_field(0, 16, 0, 100, 10, 1.0)  # side out of range
+
+
 def test_uniform_field_bits(pkg):
     got = pkg.uniform_field(9, 2, 0, 1003, 10).cpu().numpy()
     want = rng.uniform_field(9, 2, 0, 1003, 10)
