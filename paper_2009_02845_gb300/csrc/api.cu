@@ -90,6 +90,11 @@ struct dsanls_ctx {
     dsanls_options opt{};
     int64_t t_host = 0;
     cudaStream_t own_stream = nullptr;
+    // the Gram and the step size depend only on B, the right-hand side R only on B
+    // and the data: they run as a parallel branch (forked after B, joined before
+    // the update) on this higher-priority stream
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // data
     bool has_dense = false, has_sparse = false;
@@ -288,6 +293,20 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     const float *xv = side == 0 ? h->cv : h->tcv;
     const bool dense = h->has_dense;
     int64_t gram_d = dd;
+    const int kp = kp_bucket(k);
+    // after B: the Gram and the step size on the aux stream, in parallel with R
+    // (profiling keeps every phase in order on one stream)
+    bool forked = false;
+    auto start_gram = [&]() {
+        if (pe) return;
+        DSANLS_CUDA(cudaEventRecord(h->ev_fork, s));
+        DSANLS_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+        launch_gram(h->W, k, gram_d, h->G64[side], h->work, WORK_ELEMS, h->aux_stream);
+        launch_step_size(h->G64[side], k, h->opt.power_iters, h->opt.alpha, h->opt.beta, h->t_dev, h->scal[side],
+                         h->Gf, kp, h->aux_stream);
+        DSANLS_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
+        forked = true;
+    };
 
     mark(pe, DSANLS_PHASE_SKETCH, s);
     if (dense_kind(h->sketch)) {
@@ -337,6 +356,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             launch_split_reduce(h->Wpart, (int64_t)k * dd, splits, k, dd, dd, h->W, dd, s);
         }
         mark(pe, DSANLS_PHASE_PRODUCT, s);
+        start_gram();
         if (reas) {
             // P = S B^T (K x k), then R = X P: 2 K dd k + 2 rows K k flops
             if (fp8) {
@@ -406,6 +426,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         mark(pe, DSANLS_PHASE_B, s);
         launch_gather_w(Y, k, h->J, dd, c, h->W, s);
         mark(pe, DSANLS_PHASE_PRODUCT, s);
+        start_gram();
         if (dense) {
             GemmArgs g{};
             g.M = rows; g.N = k; g.K = dd;
@@ -423,6 +444,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         launch_transpose(Y, k, K, k, h->W, K, s);
         gram_d = K;
         mark(pe, DSANLS_PHASE_PRODUCT, s);
+        start_gram();
         mark(pe, DSANLS_PHASE_RHS, s);
         if (dense && h->opt.precision == DSANLS_PREC_BF16) {
             // R = X Y on the streaming tensor-core product from bf16 X and bf16 Y^T
@@ -439,12 +461,15 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             launch_spmm_rows(xp, xc, xv, rows, Y, k, k, 1.0f, h->R, k, s);
         }
     }
-    mark(pe, DSANLS_PHASE_GRAM, s);
-    launch_gram(h->W, k, gram_d, h->G64[side], h->work, WORK_ELEMS, s);
-    const int kp = kp_bucket(k);
-    mark(pe, DSANLS_PHASE_STEP_SIZE, s);
-    launch_step_size(h->G64[side], k, h->opt.power_iters, h->opt.alpha, h->opt.beta, h->t_dev, h->scal[side], h->Gf,
-                     kp, s);
+    if (forked) {
+        DSANLS_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+    } else {
+        mark(pe, DSANLS_PHASE_GRAM, s);
+        launch_gram(h->W, k, gram_d, h->G64[side], h->work, WORK_ELEMS, s);
+        mark(pe, DSANLS_PHASE_STEP_SIZE, s);
+        launch_step_size(h->G64[side], k, h->opt.power_iters, h->opt.alpha, h->opt.beta, h->t_dev, h->scal[side],
+                         h->Gf, kp, s);
+    }
     mark(pe, DSANLS_PHASE_UPDATE, s);
     if (!update) return;
     if (h->mlp)
@@ -614,6 +639,11 @@ int dsanls_create(int64_t m, int64_t n, int32_t k, int32_t d, int32_t sketch_kin
     const int rc = guarded(h, [&]() {
         DSANLS_CUDA(cudaGetDevice(&h->device));
         DSANLS_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+        int prio_least = 0, prio_greatest = 0;
+        DSANLS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+        DSANLS_CUDA(cudaStreamCreateWithPriority(&h->aux_stream, cudaStreamNonBlocking, prio_greatest));
+        DSANLS_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        DSANLS_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         prime_kernel_attributes();
         cudaStream_t s = h->stream();
         dalloc(h->U, m * k);
@@ -1059,6 +1089,12 @@ void dsanls_destroy(dsanls_t h) {
         dfree(h->bits); dfree(h->kept);
         free_long_rows(h->lr[0]);
         free_long_rows(h->lr[1]);
+        if (h->aux_stream) {
+            cudaStreamSynchronize(h->aux_stream);
+            cudaStreamDestroy(h->aux_stream);
+        }
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->ev_join) cudaEventDestroy(h->ev_join);
         if (h->own_stream) cudaStreamDestroy(h->own_stream);
     }
     delete h;

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(256)
     const int64_t ntiles = tiles_x * ((rows + PAIR_ROWS - 1) / PAIR_ROWS);
     const int qi = threadIdx.x & 31, cj = threadIdx.x >> 5;
     const bool vec = (rows & 3) == 0;
+    const bool vec8 = (cols & 7) == 0;  // 16-byte aligned rows of S
     // a grid of fewer CTAs than tiles walks the tiles (the overlapped form runs one CTA per SM)
     for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
         const int64_t r0 = (tl / tiles_x) * PAIR_ROWS, c0 = (tl % tiles_x) * PAIR_COLS;
@@ -137,10 +138,25 @@ __global__ void __launch_bounds__(256)
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < PAIR_ROWS * PAIR_COLS; e += blockDim.x) {
-            const int rr = e / PAIR_COLS, cc = e % PAIR_COLS;
-            const int64_t i = r0 + rr, j = c0 + cc;
-            if (i < rows && j < cols) out_n[i * cols + j] = tile[cc][rr];
+        // S leaves the tile in units of one row x 8 columns (one 16-byte store):
+        // unit u holds row (u >> 1) & 127 and column group (u & 1) + 2 (u >> 8),
+        // so a warp covers 16 rows x 2 groups (full 32-byte sectors; its shared
+        // loads hit two disjoint sets of 8 banks)
+        for (int u = threadIdx.x; u < PAIR_ROWS * (PAIR_COLS / 8); u += blockDim.x) {
+            const int rr = (u >> 1) & (PAIR_ROWS - 1);
+            const int cg = 8 * ((u & 1) + 2 * (u >> 8));
+            const int64_t i = r0 + rr, j = c0 + cg;
+            if (i >= rows) continue;
+            if (vec8 && j + 8 <= cols) {
+                uint32_t w[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    w[c] = (uint32_t)__bfloat16_as_ushort(tile[cg + 2 * c][rr]) |
+                           ((uint32_t)__bfloat16_as_ushort(tile[cg + 2 * c + 1][rr]) << 16);
+                *reinterpret_cast<uint4 *>(out_n + i * cols + j) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                for (int c = 0; c < 8 && j + c < cols; ++c) out_n[i * cols + j + c] = tile[cg + c][rr];
+            }
         }
     }
 }

@@ -18,66 +18,81 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 
 namespace dsanls {
 
 // ---------------------------------------------------------------------------
 // Gram in FP64
 // ---------------------------------------------------------------------------
-constexpr int GRAM_THREADS = 256;
-constexpr int GRAM_MAXP = 33;  // pairs per thread: k(k+1)/2 <= 8256 < 33 * 256
+// Each CTA sums chunks blockIdx.x, blockIdx.x + gridDim.x, ... of dc columns
+// of the d axis.  A chunk is staged in shared memory already converted to FP64
+// (one conversion per entry, not one per product: the FP64 pipe is the scarce
+// unit), column by column (ws[j][a], rows padded to 4 * ceil(k/4) + 2 doubles).
+// Thread p owns the 4 x 4 tile (bi, bj), bi <= bj, of the p-th block of the
+// upper triangle (row-major): 16 independent FP64 accumulators fed by two
+// 32-byte loads per column, so the FP64 pipe, not latency, bounds the kernel.
+// Every pair a <= b is summed over the CTA's columns in increasing order.
+constexpr int GRAM_TILE = 4;
+constexpr int GRAM_MAX_THREADS = 544;  // 528 tiles at k = 128, rounded up to warps
 
-// Each CTA sums chunks blockIdx.x, blockIdx.x + gridDim.x, ... of the d axis
-// for every pair (a <= b); each thread owns up to GRAM_MAXP pairs with FP64
-// accumulators in registers.  The chunk is staged in shared memory already
-// converted to FP64 (one conversion per entry, not one per product: the FP64
-// pipe is the scarce unit).
-__global__ void __launch_bounds__(GRAM_THREADS)
-    k_gram_partial(const float *__restrict__ W, int k, int64_t d, int64_t dc, double *__restrict__ part) {
-    extern __shared__ double ws[];  // k x (dc + 1), padded against bank conflicts
-    const int64_t ldw = dc + 1;
-    const int npairs = k * (k + 1) / 2;
-    double acc[GRAM_MAXP];
-    int pa[GRAM_MAXP], pb[GRAM_MAXP];
+__global__ void __launch_bounds__(GRAM_MAX_THREADS)
+    k_gram_partial(const float *__restrict__ W, int k, int64_t d, int dc, double *__restrict__ part) {
+    extern __shared__ __align__(16) double ws[];
+    const int kb = (k + GRAM_TILE - 1) / GRAM_TILE;
+    const int ldw = GRAM_TILE * kb + 2;  // 16-byte rows; the +2 staggers the banks of successive columns
+    const int nb = kb * (kb + 1) / 2;
+    const int p = threadIdx.x;
+    int bi = 0, rem = p;
+    if (p < nb)
+        while (rem >= kb - bi) {
+            rem -= kb - bi;
+            ++bi;
+        }
+    const int bj = bi + rem;
+    double acc[GRAM_TILE][GRAM_TILE];
 #pragma unroll
-    for (int q = 0; q < GRAM_MAXP; ++q) {
-        acc[q] = 0.0;
-        const int p = threadIdx.x + q * GRAM_THREADS;
-        int a = 0, rem = p;
-        if (p < npairs)
-            while (rem >= k - a) {
-                rem -= k - a;
-                ++a;
-            }
-        pa[q] = a;
-        pb[q] = a + rem;
-    }
-    const int64_t chunks = ceil_div(d, dc);
+    for (int r = 0; r < GRAM_TILE; ++r)
+#pragma unroll
+        for (int c = 0; c < GRAM_TILE; ++c) acc[r][c] = 0.0;
+    const int64_t chunks = ceil_div(d, (int64_t)dc);
+    const int rows_p = GRAM_TILE * kb;
     for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
         const int64_t j0 = ch * dc;
-        const int64_t len = min(dc, d - j0);
-        __syncthreads();
-        for (int64_t e = threadIdx.x; e < (int64_t)k * dc; e += GRAM_THREADS) {
-            const int a = (int)(e / dc);
-            const int64_t j = e - (int64_t)a * dc;
-            ws[a * ldw + j] = (j < len) ? (double)W[(int64_t)a * d + j0 + j] : 0.0;
+        const int len = (int)min((int64_t)dc, d - j0);
+        __syncthreads();  // the previous chunk has been consumed
+        for (int e = threadIdx.x; e < rows_p * dc; e += blockDim.x) {
+            const int a = e / dc, j = e - a * dc;  // consecutive threads read consecutive columns of a row
+            ws[j * ldw + a] = (a < k && j < len) ? (double)W[(int64_t)a * d + j0 + j] : 0.0;
         }
         __syncthreads();
+        if (p < nb) {
+            const double *wa = ws + GRAM_TILE * bi;
+            const double *wb = ws + GRAM_TILE * bj;
+            for (int j = 0; j < len; ++j) {
+                const double2 a01 = *reinterpret_cast<const double2 *>(wa + j * ldw);
+                const double2 a23 = *reinterpret_cast<const double2 *>(wa + j * ldw + 2);
+                const double2 b01 = *reinterpret_cast<const double2 *>(wb + j * ldw);
+                const double2 b23 = *reinterpret_cast<const double2 *>(wb + j * ldw + 2);
+                const double av[GRAM_TILE] = {a01.x, a01.y, a23.x, a23.y};
+                const double bv[GRAM_TILE] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
-        for (int q = 0; q < GRAM_MAXP; ++q) {
-            if (threadIdx.x + q * GRAM_THREADS < npairs) {
-                const double *wa = ws + (int64_t)pa[q] * ldw;
-                const double *wb = ws + (int64_t)pb[q] * ldw;
-                double s = acc[q];
-                for (int64_t j = 0; j < len; ++j) s = fma(wa[j], wb[j], s);
-                acc[q] = s;
+                for (int r = 0; r < GRAM_TILE; ++r)
+#pragma unroll
+                    for (int c = 0; c < GRAM_TILE; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
             }
         }
     }
-    double *out = part + (int64_t)blockIdx.x * k * k;
+    if (p < nb) {
+        double *out = part + (int64_t)blockIdx.x * k * k;
 #pragma unroll
-    for (int q = 0; q < GRAM_MAXP; ++q)
-        if (threadIdx.x + q * GRAM_THREADS < npairs) out[pa[q] * k + pb[q]] = acc[q];
+        for (int r = 0; r < GRAM_TILE; ++r)
+#pragma unroll
+            for (int c = 0; c < GRAM_TILE; ++c) {
+                const int a = GRAM_TILE * bi + r, b = GRAM_TILE * bj + c;
+                if (a < k && b < k && a <= b) out[a * k + b] = acc[r][c];
+            }
+    }
 }
 
 // 32 consecutive pairs (a <= b, row-major order of the upper triangle) per
@@ -116,17 +131,23 @@ __global__ void __launch_bounds__(256)
 
 void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, int64_t work_elems,
                  cudaStream_t s) {
-    // chunk width: about two chunks per SM, at most ~200 KB of shared memory
+    if (k < 1 || k > 128) throw ArgError{"launch_gram: k must be in [1, 128]"};
+    const int kb = (k + GRAM_TILE - 1) / GRAM_TILE;
+    const int nb = kb * (kb + 1) / 2;
+    const int threads = (int)ceil_div(nb, 32) * 32;
+    const int ldw = GRAM_TILE * kb + 2;
+    // chunk width: about two chunks per SM, a multiple of 4, at most ~96 KB of
+    // shared memory (two CTAs per SM)
     int64_t dc = ceil_div(ceil_div(d, 2 * 152), 4) * 4;
-    const int64_t dc_max = (200 * 1024) / (8 * (int64_t)k) - 1;
+    const int64_t dc_max = std::max<int64_t>(4, (96 * 1024) / (8 * (int64_t)ldw));
     if (dc > dc_max) dc = dc_max;
-    if (dc < 1) dc = 1;
+    if (dc < 4) dc = 4;
     int64_t grid = ceil_div(d, dc);
     if (grid > work_elems / ((int64_t)k * k)) grid = work_elems / ((int64_t)k * k);
     if (grid > 2 * 152) grid = 2 * 152;
     if (grid < 1) grid = 1;
-    const size_t smem = (size_t)k * (dc + 1) * sizeof(double);
-    k_gram_partial<<<(unsigned)grid, GRAM_THREADS, smem, s>>>(W, k, d, dc, work);
+    const size_t smem = (size_t)dc * ldw * sizeof(double);
+    k_gram_partial<<<(unsigned)grid, threads, smem, s>>>(W, k, d, (int)dc, work);
     DSANLS_LAUNCH_CHECK();
     const int64_t npairs = (int64_t)k * (k + 1) / 2;
     k_gram_reduce<<<(unsigned)ceil_div(npairs, 32), 256, 0, s>>>(work, (int)grid, k, G64);
@@ -136,22 +157,21 @@ void launch_gram(const float *W, int k, int64_t d, double *G64, double *work, in
 // ---------------------------------------------------------------------------
 // step size: lambda_max by power iteration, mu_t, eta_t
 // ---------------------------------------------------------------------------
-// One CTA of 256 threads: thread t works on row t / 2 of the power iteration
-// (binary32, G in shared memory), the two threads of a row each summing one
-// half of its columns; norms and the FP64 Rayleigh quotient x^T G x are
-// reduced in a fixed order (warp shuffles, then the eight warp partials).
+// One CTA of 256 threads.  G is staged once in shared memory in FP64 (all
+// loads in flight together), written out as the padded kp x kp binary32 copy
+// the update reads, and held in registers for the power iteration: thread
+// (a, b), a = 2 warp + lane / 16, b = lane % 16, keeps the T x T tile of rows
+// aT.. and columns bT.. (16T >= k, zero padded).  One iteration: a T x T
+// product with its slice of x, a butterfly over the 16 lanes of the row block
+// (every lane ends with the same row sums), the squared norm from the warp's
+// two row blocks, and one block barrier: the normalisation is applied lazily
+// (each iteration writes the unnormalised y = G x and the warp partials of
+// |y|^2 to the other of two buffers; the next one scales its product by 1/|y|,
+// the sum of the partials taken in warp order in every thread).  The FP64
+// Rayleigh quotient x^T G x / x^T x reads the FP64 copy (G symmetric:
+// consecutive threads read consecutive entries of a row) and is reduced in a
+// fixed order over the CTA.
 constexpr int STEP_THREADS = 256;
-
-DSANLS_DEV float block_sum_f(float v, float *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float tot = 0.0f;
-#pragma unroll
-    for (int w = 0; w < STEP_THREADS / 32; ++w) tot += red[w];
-    return tot;
-}
 
 DSANLS_DEV double block_sum_d(double v, double *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -164,53 +184,85 @@ DSANLS_DEV double block_sum_d(double v, double *red) {
     return tot;
 }
 
+template <int T>
 __global__ void __launch_bounds__(STEP_THREADS)
     k_step_size(const double *__restrict__ G64, int k, int iters, double alpha, double beta,
                 const int64_t *__restrict__ t_dev, double *__restrict__ scal, float *__restrict__ Gf, int kp) {
-    extern __shared__ float gs[];  // k x (k+1)
-    __shared__ float x[128];
-    __shared__ float redf[STEP_THREADS / 32];
+    extern __shared__ __align__(16) double gd[];  // k x k FP64
+    __shared__ float xb[2][16 * T];
+    __shared__ float red[2][STEP_THREADS / 32];
     __shared__ double redd[2][STEP_THREADS / 32];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < k * k; e += STEP_THREADS) gd[e] = G64[e];
+    // x_0 = 1/sqrt(k): buffer 0 holds the all-ones vector and |.|^2 = k
+    for (int i = tid; i < 16 * T; i += STEP_THREADS) xb[0][i] = (i < k) ? 1.0f : 0.0f;
+    if (tid < STEP_THREADS / 32) red[0][tid] = tid == 0 ? (float)k : 0.0f;
+    __syncthreads();
     for (int e = tid; e < kp * kp; e += STEP_THREADS) {
         const int a = e / kp, b = e % kp;
-        const float v = (a < k && b < k) ? (float)G64[a * k + b] : 0.0f;
-        Gf[e] = v;
-        if (a < k && b < k) gs[a * (k + 1) + b] = v;
+        Gf[e] = (a < k && b < k) ? (float)gd[a * k + b] : 0.0f;
     }
-    const float x0 = rsqrtf((float)k);
-    for (int i = tid; i < 128; i += STEP_THREADS) x[i] = (i < k) ? x0 : 0.0f;
-    __syncthreads();
-    const int row = tid >> 1, half = tid & 1;
-    const int lh = (k + 1) / 2;
-    const int l0 = half ? lh : 0, l1 = half ? k : lh;
-    for (int it = 0; it < iters; ++it) {
-        float a0 = 0.0f, a1 = 0.0f;
-        if (row < k) {
-            const float *gi = gs + row * (k + 1);
-            int l = l0;
-            for (; l + 1 < l1; l += 2) {
-                a0 = fmaf(gi[l], x[l], a0);
-                a1 = fmaf(gi[l + 1], x[l + 1], a1);
-            }
-            if (l < l1) a0 = fmaf(gi[l], x[l], a0);
+    const int ab = 2 * warp + (lane >> 4), bb = lane & 15;
+    float g[T][T];
+#pragma unroll
+    for (int r = 0; r < T; ++r)
+#pragma unroll
+        for (int c = 0; c < T; ++c) {
+            const int i = ab * T + r, j = bb * T + c;
+            g[r][c] = (i < k && j < k) ? (float)gd[i * k + j] : 0.0f;
         }
-        float y = a0 + a1;
-        y += __shfl_xor_sync(0xffffffffu, y, 1);  // both halves of the row
-        const float nrm2 = block_sum_f(half == 0 && row < k ? y * y : 0.0f, redf);
-        if (nrm2 == 0.0f) break;
-        const float inv = rsqrtf(nrm2);
-        if (half == 0 && row < k) x[row] = y * inv;
+    int cur = 0;
+    for (int it = 0; it < iters; ++it) {
+        float tot = 0.0f;
+#pragma unroll
+        for (int w = 0; w < STEP_THREADS / 32; ++w) tot += red[cur][w];
+        if (tot == 0.0f) break;  // G x = 0 (the same decision in every thread)
+        const float inv = rsqrtf(tot);
+        float xv[T], p[T];
+#pragma unroll
+        for (int c = 0; c < T; ++c) xv[c] = xb[cur][bb * T + c];
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int c = 0; c < T; ++c) acc = fmaf(g[r][c], xv[c], acc);
+            p[r] = acc;
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1)
+#pragma unroll
+            for (int r = 0; r < T; ++r) p[r] += __shfl_xor_sync(0xffffffffu, p[r], o);
+        float sq = 0.0f;
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            p[r] *= inv;
+            sq = fmaf(p[r], p[r], sq);
+        }
+        sq += __shfl_xor_sync(0xffffffffu, sq, 16);  // the warp's two row blocks
+        const int nxt = cur ^ 1;
+#pragma unroll
+        for (int r = 0; r < T; ++r)
+            if (r == bb) xb[nxt][ab * T + r] = p[r];
+        if (lane == 0) red[nxt][warp] = sq;
         __syncthreads();
+        cur = nxt;
     }
-    // Rayleigh quotient in FP64; G is symmetric, so (G x)_i = sum_l G[l][i] x_l
-    // (consecutive threads read consecutive entries of a row of G)
+    float tot = 0.0f;
+#pragma unroll
+    for (int w = 0; w < STEP_THREADS / 32; ++w) tot += red[cur][w];
+    const float inv = tot > 0.0f ? rsqrtf(tot) : 0.0f;
+    // Rayleigh quotient in FP64: thread t takes row i = t % k, column segment t / k
+    const int nseg = STEP_THREADS / k;  // >= 2 for k <= 128
+    const int i = tid % k, seg = tid / k;
+    const int seglen = (k + nseg - 1) / nseg;
     double xgx = 0.0, xx = 0.0;
-    if (tid < k) {
+    if (seg < nseg) {
+        const int c0 = seg * seglen, c1 = min(k, c0 + seglen);
         double gx = 0.0;
-        for (int l = 0; l < k; ++l) gx = fma(G64[l * k + tid], (double)x[l], gx);
-        xgx = (double)x[tid] * gx;
-        xx = (double)x[tid] * (double)x[tid];
+        for (int l = c0; l < c1; ++l) gx = fma(gd[l * k + i], (double)(xb[cur][l] * inv), gx);
+        const double xi = (double)(xb[cur][i] * inv);
+        xgx = xi * gx;
+        if (seg == 0) xx = xi * xi;
     }
     xgx = block_sum_d(xgx, redd[0]);
     xx = block_sum_d(xx, redd[1]);
@@ -225,9 +277,16 @@ __global__ void __launch_bounds__(STEP_THREADS)
 
 void launch_step_size(const double *G64, int k, int iters, double alpha, double beta, const int64_t *t_dev,
                       double *scal, float *Gf, int kp, cudaStream_t s) {
-    if (k > 128) throw ArgError{"launch_step_size: k > 128"};
-    const size_t smem = (size_t)k * (k + 1) * sizeof(float);
-    k_step_size<<<1, STEP_THREADS, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
+    if (k < 1 || k > 128) throw ArgError{"launch_step_size: k must be in [1, 128]"};
+    const size_t smem = (size_t)k * k * sizeof(double);
+    if (k <= 16)
+        k_step_size<1><<<1, STEP_THREADS, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
+    else if (k <= 32)
+        k_step_size<2><<<1, STEP_THREADS, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
+    else if (k <= 64)
+        k_step_size<4><<<1, STEP_THREADS, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
+    else
+        k_step_size<8><<<1, STEP_THREADS, smem, s>>>(G64, k, iters, alpha, beta, t_dev, scal, Gf, kp);
     DSANLS_LAUNCH_CHECK();
 }
 
@@ -485,7 +544,10 @@ static void update_kp(int solver, float *Z, const float *R, int64_t rows, int k,
 
 void prime_solver_attributes(int max_smem) {
     allow_max_dynamic_smem(k_gram_partial, max_smem);
-    allow_max_dynamic_smem(k_step_size, max_smem);
+    allow_max_dynamic_smem(k_step_size<1>, max_smem);
+    allow_max_dynamic_smem(k_step_size<2>, max_smem);
+    allow_max_dynamic_smem(k_step_size<4>, max_smem);
+    allow_max_dynamic_smem(k_step_size<8>, max_smem);
     allow_max_dynamic_smem(k_update_pgd_tiled<16>, max_smem);
     allow_max_dynamic_smem(k_update_pgd_tiled<32>, max_smem);
     allow_max_dynamic_smem(k_update_pgd_tiled<64>, max_smem);
@@ -504,6 +566,11 @@ void launch_update(int solver, float *Z, const float *R, int64_t rows, int k, co
                    const double *scal, float bound, int inner, int *flag, cudaStream_t s) {
     if (rows <= 0) return;
     if (inner < 1 || (inner > 1 && solver != 0)) throw ArgError{"launch_update: inner steps need PGD"};
+    if (solver == 0 && inner == 1 && update_tc_supported(k)) {
+        // one projected-gradient step with Z G on tensor cores (split bf16, binary32 accuracy)
+        launch_update_tc(Z, R, rows, k, Gf, kp, scal, bound, flag, s);
+        return;
+    }
     if (kp <= 16)
         update_kp<16>(solver, Z, R, rows, k, Gf, scal, bound, inner, flag, s);
     else if (kp <= 32)

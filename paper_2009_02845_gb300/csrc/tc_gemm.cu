@@ -794,7 +794,304 @@ void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfl
     DSANLS_LAUNCH_CHECK();
 }
 
+// ---- fused row update on tensor cores ---------------------------------------
+// Z <- max(0, Z - eta (Z G - R)) (eq. gradient_descent, one projected-gradient
+// step) for 32 < k <= 128.  Z G is taken on tcgen05 from a three-way bf16 split
+// of both operands, z = z_h + z_m + z_l with z_h = bf16(z), z_m = bf16(z - z_h),
+// z_l = bf16(z - z_h - z_m) (each difference exact in binary32): the six
+// products z_i g_j with i + j <= 2 accumulate in fp32 in TMEM, and the dropped
+// terms are of order 2^-24 |z| |g|, the rounding level of a binary32 product.
+// Persistent: a CTA splits G once into the three B operands (N = k rounded up
+// to 16 rows, K = k rounded up to 64, 128-byte swizzled K-major), then walks
+// 128-row tiles of Z: the CTA's 512 threads split the tile into the three A
+// operands (written from coalesced flat reads of the nr x k contiguous floats,
+// zeros in the padding), thread 0 issues the 6 x (K / 16) MMAs and commits, the accumulator is moved from
+// TMEM into an fp32 staging tile over the A operands, and the step is applied
+// in a second coalesced flat pass with the exact binary32 z and r.
+namespace {
+
+constexpr int UPD_BM = 128;
+constexpr int UPD_THREADS = 512;
+constexpr int UPD_UNROLL = 8;  // float4 groups per thread: 8 x 512 x 4 = 128 x 128 floats
+
+struct __align__(8) UpdTail {
+    uint64_t done;
+    uint64_t fin;
+    uint32_t tmem_base;
+    uint32_t pad;
+};
+
+DSANLS_DEV float upd_project(float v, float bound, int *flag) {
+    if (!(fabsf(v) <= 3.402823466e38f)) {  // NaN or Inf
+        *flag = 1;
+        return 0.0f;
+    }
+    float r = v > 0.0f ? v : 0.0f;
+    if (bound > 0.0f) r = fminf(r, bound);
+    return r;
+}
+
+DSANLS_DEV void split3_one(float z, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
+    h = __float2bfloat16_rn(z);
+    const float r1 = __fsub_rn(z, __bfloat162float(h));
+    m = __float2bfloat16_rn(r1);
+    l = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
+}
+
+// byte offset of element (r, c) in a 128-byte swizzled K-major operand of `rows` rows
+DSANLS_DEV int sw128_off(int r, int c, int rows) {
+    return (c >> 6) * rows * 128 + r * 128 + ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 7) << 1);
+}
+
+template <int KA>  // K atoms of 64 columns: 1 for k <= 64, 2 for k <= 128
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_update_tc(float *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k, int N,
+                const float *__restrict__ Gf, int kp, const double *__restrict__ scal, float bound,
+                int *__restrict__ flag, uint32_t tmem_cols) {
+    extern __shared__ uint8_t upd_smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(upd_smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int KC = KA * 64;  // padded K
+    const int b_part = KA * N * 128, a_part = KA * UPD_BM * 128;
+    uint8_t *Bp = base;               // 3 parts x KA atoms x N rows x 128 B
+    uint8_t *Ap = Bp + 3 * b_part;    // 3 parts x KA atoms x 128 rows x 128 B; the fp32 staging of Z G after the MMAs
+    float *stage = reinterpret_cast<float *>(Ap);
+    const int lds = N + 1;            // staging row stride (odd: conflict-free column writes)
+    UpdTail *tail = reinterpret_cast<UpdTail *>(Ap + 3 * a_part);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&tail->done, 1);
+        mbar_init(&tail->fin, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tail->tmem_base)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the three parts of G: B row n, K column c holds G[n][c] (G is symmetric)
+    for (int e = tid; e < N * KC; e += UPD_THREADS) {
+        const int n = e / KC, c = e % KC;
+        const float g = (n < k && c < k) ? Gf[n * kp + c] : 0.0f;
+        __nv_bfloat16 h, m, l;
+        split3_one(g, h, m, l);
+        const int off = sw128_off(n, c, N);
+        *reinterpret_cast<__nv_bfloat16 *>(Bp + off) = h;
+        *reinterpret_cast<__nv_bfloat16 *>(Bp + b_part + off) = m;
+        *reinterpret_cast<__nv_bfloat16 *>(Bp + 2 * b_part + off) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tail->tmem_base;
+    const float eta = (float)scal[2];
+    const uint32_t idesc = idesc_bf16(UPD_BM, N);
+    const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
+    const bool vec = (k & 3) == 0;
+    const int q = warp & 3, cw = warp >> 2;  // TMEM lane quarter and 32-column slice of this warp
+    uint32_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int64_t r0 = tile * UPD_BM;
+        const int nr = (int)min((int64_t)UPD_BM, rows - r0);
+        const int64_t f0 = r0 * k;  // the tile is nr * k contiguous floats of Z and of R
+        const int nf = nr * k;
+        // 1. the three A parts: the tile's entries (coalesced flat reads, every load of
+        //    a thread in flight before the first is used), then zeros in the padding
+        //    columns k..KC-1 and in the rows past the end of Z
+        if (vec) {
+            float4 zz[UPD_UNROLL];
+#pragma unroll
+            for (int j = 0; j < UPD_UNROLL; ++j) {
+                const int g = tid + j * UPD_THREADS;
+                if (4 * g < nf) zz[j] = *(reinterpret_cast<const float4 *>(Z + f0) + g);  // re-read by the step
+            }
+#pragma unroll
+            for (int j = 0; j < UPD_UNROLL; ++j) {
+                const int g = tid + j * UPD_THREADS;
+                if (4 * g >= nf) continue;
+                const float zv[4] = {zz[j].x, zz[j].y, zz[j].z, zz[j].w};
+                int r = (4 * g) / k, c = 4 * g - r * k;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    __nv_bfloat16 h, m, l;
+                    split3_one(zv[e], h, m, l);
+                    const int off = sw128_off(r, c, UPD_BM);
+                    *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = h;
+                    *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
+                    *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
+                    if (++c == k) {
+                        c = 0;
+                        ++r;
+                    }
+                }
+            }
+        } else {
+            for (int f = tid; f < nf; f += UPD_THREADS) {
+                const int r = f / k, c = f - r * k;
+                __nv_bfloat16 h, m, l;
+                split3_one(Z[f0 + f], h, m, l);
+                const int off = sw128_off(r, c, UPD_BM);
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = h;
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
+            }
+        }
+        {
+            const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+            const int pc = KC - k;  // padding columns of every row
+            for (int e = tid; e < UPD_BM * pc; e += UPD_THREADS) {
+                const int r = e / pc, c = k + (e - r * pc);
+                const int off = sw128_off(r, c, UPD_BM);
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = zero;
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = zero;
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = zero;
+            }
+            for (int e = nr * k + tid; e < UPD_BM * k; e += UPD_THREADS) {  // rows past the end
+                const int r = e / k, c = e - r * k;
+                const int off = sw128_off(r, c, UPD_BM);
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = zero;
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = zero;
+                *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = zero;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        __syncthreads();  // A complete; the previous tile's staging reads are done
+        fence_after();
+        // 2. the six products into TMEM
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(Ap), b0 = smem_u32(Bp);
+            uint32_t acc = 0;
+#pragma unroll 1
+            for (int i = 0; i < 3; ++i)
+#pragma unroll 1
+                for (int jp = 0; i + jp < 3; ++jp)
+#pragma unroll 1
+                    for (int ka = 0; ka < KA; ++ka)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t ad = a0 + i * a_part + ka * UPD_BM * 128 + kk * 32;
+                            const uint32_t bd = b0 + jp * b_part + ka * N * 128 + kk * 32;
+                            mma_bf16(tmem, sw128_desc(ad), sw128_desc(bd), idesc, acc);
+                            acc = 1;
+                        }
+            mma_commit(&tail->done);
+        }
+        const bool got = mbar_wait(&tail->done, it & 1);
+        if (__syncthreads_or(!got)) {
+            if (tid == 0) atomicOr(flag, 2);
+            break;
+        }
+        fence_after();
+        // 3. Z G from TMEM into the fp32 staging tile (over the A parts, which the
+        //    finished MMAs no longer read): warp (q, cw) moves lanes 32q.. x columns 32cw..
+        if (32 * cw < N) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + 32 * cw, v);
+            tmem_ld_wait();
+            const int r = q * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (32 * cw + j < N) stage[r * lds + 32 * cw + j] = __uint_as_float(v[j]);
+        }
+        fence_before();
+        __syncthreads();
+        // 4. the step on the tile's nr * k contiguous entries (coalesced; all loads of a
+        //    thread in flight first)
+        if (vec) {
+#pragma unroll 1
+          for (int j0 = 0; j0 < UPD_UNROLL; j0 += UPD_UNROLL / 2) {
+            float4 zz[UPD_UNROLL / 2], rr[UPD_UNROLL / 2];
+#pragma unroll
+            for (int j = 0; j < UPD_UNROLL / 2; ++j) {
+                const int g = tid + (j0 + j) * UPD_THREADS;
+                if (4 * g < nf) {
+                    zz[j] = *(reinterpret_cast<const float4 *>(Z + f0) + g);
+                    rr[j] = __ldcs(reinterpret_cast<const float4 *>(R + f0) + g);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < UPD_UNROLL / 2; ++j) {
+                const int g = tid + (j0 + j) * UPD_THREADS;
+                if (4 * g >= nf) continue;
+                float zv[4] = {zz[j].x, zz[j].y, zz[j].z, zz[j].w};
+                const float rv[4] = {rr[j].x, rr[j].y, rr[j].z, rr[j].w};
+                int r = (4 * g) / k, c = 4 * g - r * k;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float grad = __fsub_rn(stage[r * lds + c], rv[e]);
+                    zv[e] = upd_project(__fmaf_rn(-eta, grad, zv[e]), bound, flag);
+                    if (++c == k) {
+                        c = 0;
+                        ++r;
+                    }
+                }
+                __stcs(reinterpret_cast<float4 *>(Z + f0) + g, make_float4(zv[0], zv[1], zv[2], zv[3]));
+            }
+          }
+        } else {
+            for (int f = tid; f < nf; f += UPD_THREADS) {
+                const int r = f / k, c = f - r * k;
+                const float grad = __fsub_rn(stage[r * lds + c], R[f0 + f]);
+                Z[f0 + f] = upd_project(__fmaf_rn(-eta, grad, Z[f0 + f]), bound, flag);
+            }
+        }
+        // the next tile's split overwrites the staging: every thread is done with it
+        __syncthreads();
+    }
+    if (tid == 0) {  // every MMA this thread issued has retired before TMEM is freed
+        mma_commit(&tail->fin);
+        mbar_wait(&tail->fin, 0);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+template <int KA>
+size_t update_tc_smem(int N) {
+    return 1024 + 3 * (size_t)KA * N * 128 + 3 * (size_t)KA * UPD_BM * 128 + sizeof(UpdTail);
+}
+
+}  // namespace
+
+bool update_tc_supported(int k) { return k > 32 && k <= 128; }
+
+void launch_update_tc(float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
+                      float bound, int *flag, cudaStream_t s) {
+    if (!update_tc_supported(k)) throw ArgError{"launch_update_tc: needs 32 < k <= 128"};
+    if (rows <= 0) return;
+    const int N = (k + 15) / 16 * 16;
+    const uint32_t tmem_cols = N <= 64 ? 64u : 128u;
+    int dev = 0, sms = 152, per_sm = 1;
+    DSANLS_CUDA(cudaGetDevice(&dev));
+    DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
+    if (k <= 64) {
+        const size_t smem = update_tc_smem<1>(N);
+        DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<1>, UPD_THREADS, smem));
+        per_sm = std::max(1, std::min(per_sm, 512 / (int)tmem_cols));
+        const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
+        k_update_tc<1><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
+                                                                tmem_cols);
+    } else {
+        const size_t smem = update_tc_smem<2>(N);
+        DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<2>, UPD_THREADS, smem));
+        per_sm = std::max(1, std::min(per_sm, 512 / (int)tmem_cols));
+        const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
+        k_update_tc<2><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
+                                                                tmem_cols);
+    }
+    DSANLS_LAUNCH_CHECK();
+}
+
 void prime_tc_attributes(int max_smem) {
+    allow_max_dynamic_smem(k_update_tc<1>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<2>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, true, false>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, true, false>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, false>, max_smem);

@@ -52,6 +52,14 @@ void launch_quant_rows(const float *X, int64_t rows, int64_t K, float *scale, ui
                        cudaStream_t s);
 // out (cols x rows, bf16) = in^T for in rows x cols fp32 row-major.
 void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *out, cudaStream_t s);
+// Z <- max(0, Z - eta (Z G - R)) (one projected-gradient step, eta = scal[2])
+// for Z rows x k and R rows x k fp32 row-major, G the padded kp x kp fp32 Gram,
+// with Z G on tensor cores from a three-way bf16 split of both operands (six
+// products, accurate to about binary32); entries clamped at `bound` when > 0;
+// NaN/Inf set bit 1 of *flag, a bounded wait that gives up bit 2.
+bool update_tc_supported(int k);
+void launch_update_tc(float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
+                      float bound, int *flag, cudaStream_t s);
 void prime_tc_attributes(int max_smem);
 
 }  // namespace dsanls

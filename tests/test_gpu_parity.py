@@ -220,9 +220,10 @@ def test_resume_from_checkpoint_is_bitwise(pkg):
     assert np.array_equal(U, U10) and np.array_equal(V, V10)
 
 
-def test_nan_input_raises_numeric_error(pkg):
-    m, n, k = 50, 40, 4
-    M, _, _ = planted_dense(m, n, k, 0)
+@pytest.mark.parametrize("k", [4, 64, 100])  # the CUDA-core update and the tensor-core one (k > 32)
+def test_nan_input_raises_numeric_error(pkg, k):
+    m, n = 50, 40
+    M, _, _ = planted_dense(m, n, 4, 0)
     h = pkg.DSANLS(m, n, k, 10, pkg.GAUSSIAN, seed=0)
     h.set_dense(M)
     U = np.ones((m, k), np.float32)
@@ -254,9 +255,10 @@ def test_state_and_argument_errors(pkg):
     h.close()
 
 
-def test_bound_clamp(pkg):
-    m, n, k = 100, 80, 5
-    M, _, _ = planted_dense(m, n, k, 0)
+@pytest.mark.parametrize("k", [5, 64, 100])
+def test_bound_clamp(pkg, k):
+    m, n = 300, 280
+    M, _, _ = planted_dense(m, n, 5, 0)
     M *= 1e-4
     U, V = initial_factors(m, n, k, 0)
     U *= 50.0
@@ -270,12 +272,13 @@ def test_bound_clamp(pkg):
     assert Ug.max() <= bound * (1 + 1e-6) and Vg.max() <= bound * (1 + 1e-6)
 
 
-def test_run_is_deterministic(pkg):
-    m, n, k, d = 500, 400, 16, 64
-    M, _, _ = planted_dense(m, n, k, 3)
+@pytest.mark.parametrize("k,solver", [(16, 1), (100, 0)])
+def test_run_is_deterministic(pkg, k, solver):
+    m, n, d = 500, 400, 64
+    M, _, _ = planted_dense(m, n, 16, 3)
     outs = []
     for _ in range(2):
-        h = pkg.DSANLS(m, n, k, d, pkg.SUBSAMPLE, seed=9, solver=pkg.RCD)
+        h = pkg.DSANLS(m, n, k, d, pkg.SUBSAMPLE, seed=9, solver=solver)
         h.set_dense(M)
         h.step(4)
         outs.append(h.factors())
