@@ -39,17 +39,30 @@ template <bool TRANSPOSED, typename OutT, int KIND>
 __global__ void k_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t_host, const int64_t *t_dev,
                                  int64_t rows, int64_t cols, float scale, const int32_t *hcols, OutT *out) {
     const int64_t nb4 = (rows + 3) >> 2;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nb4 * cols) return;
-    const uint64_t t = t_dev ? (uint64_t)*t_dev : t_host;
     int64_t q, j;
-    if (TRANSPOSED) {  // consecutive threads walk the rows of one column: contiguous S^T stores
-        q = idx % nb4;
-        j = idx / nb4;
-    } else {  // consecutive threads walk the columns of four rows: contiguous S stores
-        j = idx % cols;
-        q = idx / cols;
+    if (gridDim.y > 1) {  // 2D grid: x walks the contiguous axis, y the other (no division)
+        const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (TRANSPOSED) {
+            q = x;
+            j = blockIdx.y;
+            if (q >= nb4) return;
+        } else {
+            j = x;
+            q = blockIdx.y;
+            if (j >= cols) return;
+        }
+    } else {
+        const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (idx >= nb4 * cols) return;
+        if (TRANSPOSED) {  // consecutive threads walk the rows of one column: contiguous S^T stores
+            q = idx % nb4;
+            j = idx / nb4;
+        } else {  // consecutive threads walk the columns of four rows: contiguous S stores
+            j = idx % cols;
+            q = idx / cols;
+        }
     }
+    const uint64_t t = t_dev ? (uint64_t)*t_dev : t_host;
     float z[4];
     unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, hcols, z);
 #pragma unroll
@@ -76,10 +89,18 @@ template <int KIND>
 __global__ void k_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols,
                                 float scale, const int32_t *hcols, __nv_bfloat16 *out_b, __nv_fp8_e4m3 *out_q) {
     const int64_t nb4 = (rows + 3) >> 2;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nb4 * cols) return;
+    int64_t q, j;
+    if (gridDim.y > 1) {  // 2D grid: x walks the rows (blocks of four), y the columns
+        q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        j = blockIdx.y;
+        if (q >= nb4) return;
+    } else {
+        const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (idx >= nb4 * cols) return;
+        q = idx % nb4;
+        j = idx / nb4;
+    }
     const uint64_t t = (uint64_t)*t_dev;
-    const int64_t q = idx % nb4, j = idx / nb4;
     float z[4];
     unit_draw4<KIND>(seed, sid, t, (uint32_t)q, (uint32_t)j, (uint32_t)cols, hcols, z);
     const int64_t i0 = 4 * q;
@@ -180,9 +201,11 @@ void launch_gaussian_pair(uint64_t seed, uint32_t sid, const int64_t *t_dev, int
 
 void launch_gaussian_dual(uint64_t seed, uint32_t sid, const int64_t *t_dev, int64_t rows, int64_t cols, float scale,
                           __nv_bfloat16 *out_b, uint8_t *out_q, int kind, const int32_t *hcols, cudaStream_t s) {
-    const int64_t total = ((rows + 3) >> 2) * cols;
+    const int64_t nb4 = (rows + 3) >> 2, total = nb4 * cols;
     if (total == 0) return;
-    const unsigned g = (unsigned)ceil_div(total, 256);
+    // 2D grid (rows x columns) when the columns fit the y dimension, else 1D
+    const dim3 g = cols <= 65535 ? dim3((unsigned)ceil_div(nb4, 256), (unsigned)cols)
+                                 : dim3((unsigned)ceil_div(total, 256));
     __nv_fp8_e4m3 *q = reinterpret_cast<__nv_fp8_e4m3 *>(out_q);
 #define DSANLS_DUAL_LAUNCH(KD) k_gaussian_dual<KD><<<g, 256, 0, s>>>(seed, sid, t_dev, rows, cols, scale, hcols, out_b, q)
     if (kind == DRAW_RADEMACHER) DSANLS_DUAL_LAUNCH(DRAW_RADEMACHER);
@@ -300,9 +323,12 @@ template <typename OutT>
 void launch_gaussian_field(uint64_t seed, uint32_t sid, uint64_t t, const int64_t *t_dev, int64_t rows,
                            int64_t cols, float scale, bool transposed, OutT *out, int kind, const int32_t *hcols,
                            cudaStream_t s) {
-    const int64_t total = ((rows + 3) >> 2) * cols;
+    const int64_t nb4 = (rows + 3) >> 2, total = nb4 * cols;
     if (total == 0) return;
-    const unsigned grid = (unsigned)ceil_div(total, 256);
+    // 2D grid (contiguous axis in x) when the other axis fits the y dimension, else 1D
+    const int64_t nx = transposed ? nb4 : cols, ny = transposed ? cols : nb4;
+    const dim3 grid = (ny > 1 && ny <= 65535) ? dim3((unsigned)ceil_div(nx, 256), (unsigned)ny)
+                                              : dim3((unsigned)ceil_div(total, 256));
 #define DSANLS_FIELD_LAUNCH(TR, KD) \
     k_gaussian_field<TR, OutT, KD><<<grid, 256, 0, s>>>(seed, sid, t, t_dev, rows, cols, scale, hcols, out)
     if (transposed) {

@@ -807,7 +807,8 @@ void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfl
 // operands (written from coalesced flat reads of the nr x k contiguous floats,
 // zeros in the padding), thread 0 issues the 6 x (K / 16) MMAs and commits, the accumulator is moved from
 // TMEM into an fp32 staging tile over the A operands, and the step is applied
-// in a second coalesced flat pass with the exact binary32 z and r.
+// with the exact binary32 z (kept in registers since the split) and r (loaded
+// while the products run), stored in the same coalesced flat order.
 namespace {
 
 constexpr int UPD_BM = 128;
@@ -900,12 +901,14 @@ __global__ void __launch_bounds__(UPD_THREADS)
         // 1. the three A parts: the tile's entries (coalesced flat reads, every load of
         //    a thread in flight before the first is used), then zeros in the padding
         //    columns k..KC-1 and in the rows past the end of Z
+        // the tile's z stay in registers for the step (the flat mapping of the
+        // split and of the step is the same), r is loaded while the products run
+        float4 zz[UPD_UNROLL], rr[UPD_UNROLL];
         if (vec) {
-            float4 zz[UPD_UNROLL];
 #pragma unroll
             for (int j = 0; j < UPD_UNROLL; ++j) {
                 const int g = tid + j * UPD_THREADS;
-                if (4 * g < nf) zz[j] = *(reinterpret_cast<const float4 *>(Z + f0) + g);  // re-read by the step
+                if (4 * g < nf) zz[j] = __ldcs(reinterpret_cast<const float4 *>(Z + f0) + g);
             }
 #pragma unroll
             for (int j = 0; j < UPD_UNROLL; ++j) {
@@ -979,6 +982,13 @@ __global__ void __launch_bounds__(UPD_THREADS)
                         }
             mma_commit(&tail->done);
         }
+        if (vec) {
+#pragma unroll
+            for (int j = 0; j < UPD_UNROLL; ++j) {
+                const int g = tid + j * UPD_THREADS;
+                if (4 * g < nf) rr[j] = __ldcs(reinterpret_cast<const float4 *>(R + f0) + g);
+            }
+        }
         const bool got = mbar_wait(&tail->done, it & 1);
         if (__syncthreads_or(!got)) {
             if (tid == 0) atomicOr(flag, 2);
@@ -998,23 +1008,12 @@ __global__ void __launch_bounds__(UPD_THREADS)
         }
         fence_before();
         __syncthreads();
-        // 4. the step on the tile's nr * k contiguous entries (coalesced; all loads of a
-        //    thread in flight first)
+        // 4. the step on the tile's nr * k contiguous entries (z still in registers from
+        //    the split, r loaded while the products ran; coalesced stores)
         if (vec) {
-#pragma unroll 1
-          for (int j0 = 0; j0 < UPD_UNROLL; j0 += UPD_UNROLL / 2) {
-            float4 zz[UPD_UNROLL / 2], rr[UPD_UNROLL / 2];
 #pragma unroll
-            for (int j = 0; j < UPD_UNROLL / 2; ++j) {
-                const int g = tid + (j0 + j) * UPD_THREADS;
-                if (4 * g < nf) {
-                    zz[j] = *(reinterpret_cast<const float4 *>(Z + f0) + g);
-                    rr[j] = __ldcs(reinterpret_cast<const float4 *>(R + f0) + g);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < UPD_UNROLL / 2; ++j) {
-                const int g = tid + (j0 + j) * UPD_THREADS;
+            for (int j = 0; j < UPD_UNROLL; ++j) {
+                const int g = tid + j * UPD_THREADS;
                 if (4 * g >= nf) continue;
                 float zv[4] = {zz[j].x, zz[j].y, zz[j].z, zz[j].w};
                 const float rv[4] = {rr[j].x, rr[j].y, rr[j].z, rr[j].w};
@@ -1030,7 +1029,6 @@ __global__ void __launch_bounds__(UPD_THREADS)
                 }
                 __stcs(reinterpret_cast<float4 *>(Z + f0) + g, make_float4(zv[0], zv[1], zv[2], zv[3]));
             }
-          }
         } else {
             for (int f = tid; f < nf; f += UPD_THREADS) {
                 const int r = f / k, c = f - r * k;
