@@ -99,7 +99,9 @@ void launch_step_size(const double *G64, int k, int iters, double alpha, double 
                       double *scal, float *Gf, int kp, cudaStream_t s);
 // Z <- max(0, Z - eta (Z G - R)) (PGD) or Alg. 3 sweep (RCD), rows x k,
 // optional clamp at `bound` (> 0); PGD with inner > 1 takes `inner` steps on
-// the proximal objective from Z.  Sets *flag = 1 when a NaN/Inf appears.
+// the proximal objective from Z.  One PGD step with 32 < k <= 128 runs on
+// tensor cores (launch_update_tc), the rest on CUDA cores.  Sets *flag = 1
+// when a NaN/Inf appears (bit 2 when a bounded tensor-core wait gives up).
 void launch_update(int solver, float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp,
                    const double *scal, float bound, int inner, int *flag, cudaStream_t s);
 void launch_increment_t(int64_t *t_dev, int64_t by, cudaStream_t s);

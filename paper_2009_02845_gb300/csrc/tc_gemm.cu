@@ -805,10 +805,11 @@ void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfl
 // to 16 rows, K = k rounded up to 64, 128-byte swizzled K-major), then walks
 // 128-row tiles of Z: the CTA's 512 threads split the tile into the three A
 // operands (written from coalesced flat reads of the nr x k contiguous floats,
-// zeros in the padding), thread 0 issues the 6 x (K / 16) MMAs and commits, the accumulator is moved from
-// TMEM into an fp32 staging tile over the A operands, and the step is applied
-// with the exact binary32 z (kept in registers since the split) and r (loaded
-// while the products run), stored in the same coalesced flat order.
+// zeros in the padding), thread 0 issues the 6 x (K / 16) MMAs and commits,
+// the accumulator is moved from TMEM into an fp32 staging tile over the A
+// operands, and the step is applied with the exact binary32 z (kept in
+// registers since the split) and r (loaded while the products run), stored in
+// the same coalesced flat order.
 namespace {
 
 constexpr int UPD_BM = 128;
