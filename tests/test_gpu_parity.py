@@ -137,6 +137,40 @@ def test_sparse_half_steps(pkg, kind, solver):
         assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
 
 
+def _csr_with_long_rows(m, n, seed):
+    """Short random rows (about 10 entries) plus rows 7 and 123 with 3,000 and
+    4,500 entries and a column 0 present in 2,500 rows: rows of M and of M^T
+    longer than the 2,048 entries that the sampled product takes in one pass."""
+    g = np.random.default_rng(seed)
+    rows = []
+    for i in range(m):
+        length = {7: 3000, 123: 4500}.get(i, int(g.integers(1, 20)))
+        cols = set(g.choice(n, size=length, replace=False).tolist())
+        if i < 2500:
+            cols.add(0)
+        rows.append(sorted(cols))
+    rp = np.zeros(m + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate([np.asarray(r, np.int32) for r in rows])
+    val = np.log1p(g.poisson(1.0, size=len(col)) + 1.0).astype(np.float32)
+    return rp, col, val, sp.csr_matrix((val.astype(np.float64), col, rp), shape=(m, n))
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_sparse_long_rows_half_steps(pkg, solver):
+    """Subsampled sparse half-steps where rows of M and of M^T exceed one pass
+    of the sampled product (chunked, then combined), against the oracle."""
+    m, n, k = 3000, 5000, 24
+    rp, col, val, Msp = _csr_with_long_rows(m, n, 11)
+    assert np.diff(rp).max() > 2048 and np.diff(Msp.T.tocsr().indptr).max() > 2048
+    U, V = initial_factors(m, n, k, 5)
+    for side, dd in ((0, 500), (1, 300)):
+        got, _, _ = _gpu_half(pkg, None, U, V, method.SUBSAMPLE, solver, 6, 2, side, 500, d_v=300,
+                              csr=(rp, col, val))
+        want = _oracle_half(Msp, U, V, method.SUBSAMPLE, solver, 6, 2, side, dd, sparse=True)
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
 def test_sparse_given_transpose_equals_built_transpose(pkg):
     m, n, k = 500, 200, 8
     rp, col, val, Msp = _csr(m, n, 4)
