@@ -81,6 +81,10 @@ extern "C" {
 /* ---- subproblem solvers (Section 3.5) -------------------------------- */
 #define DSANLS_SOLVER_PGD 0   /* one projected gradient step, eq. gradient_descent */
 #define DSANLS_SOLVER_RCD 1   /* proximal coordinate descent, Alg. 3               */
+/* The row update's U G is binary32-accurate in every precision: for one PGD
+ * step with 32 < k <= 128 it runs on tensor cores from a three-way bf16 split
+ * of U and G (six products, fp32 accumulation; dropped terms of order 2^-24
+ * of the product), otherwise on CUDA cores in binary32. */
 
 /* ---- arithmetic of the sketched products A = M S and R = A B^T -------- */
 #define DSANLS_PREC_FP32 0    /* binary32 operands and accumulation (CUDA cores)  */
