@@ -98,6 +98,7 @@ struct dsanls_ctx {
 
     // data
     bool has_dense = false, has_sparse = false;
+    bool sumsq_dirty = false;  // ||M||^2 of new dense data not computed yet (done when needed)
     float *M = nullptr, *MT = nullptr;
     __nv_bfloat16 *Mb = nullptr, *MTb = nullptr;
     int64_t nnz = 0;
@@ -563,9 +564,17 @@ void copy_in(void *dst, const void *src, size_t bytes, int on_device, cudaStream
     DSANLS_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
 }
 
+// ||M||^2 into dscal[0] when the dense data changed since it was last computed
+void ensure_sumsq(dsanls_ctx *h) {
+    if (!h->sumsq_dirty || !h->has_dense) return;
+    launch_sumsq(h->M, h->m * h->n, h->work, WORK_ELEMS, h->dscal + 0, h->stream());
+    h->sumsq_dirty = false;
+}
+
 void set_bound(dsanls_ctx *h) {
     h->bound = 0.0f;
     if (h->opt.bound_clamp && (h->has_dense || h->has_sparse)) {
+        ensure_sumsq(h);
         double mm = 0.0;
         DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
         DSANLS_CUDA(cudaMemcpy(&mm, h->dscal + 0, sizeof(double), cudaMemcpyDeviceToHost));
@@ -745,20 +754,37 @@ int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device) 
             dfree(h->rp); dfree(h->ci); dfree(h->cv); dfree(h->trp); dfree(h->tci); dfree(h->tcv);
             h->has_sparse = false;
         }
+        // new values in the buffers of earlier dense data keep the captured graph valid
+        const bool refresh = h->has_dense && h->M && h->MT;
         if (!h->M) dalloc(h->M, h->m * h->n);
         if (!h->MT) dalloc(h->MT, h->m * h->n);
         DSANLS_CUDA(cudaMemcpy2DAsync(h->M, h->n * sizeof(float), M, ld * sizeof(float), h->n * sizeof(float), h->m,
                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         launch_transpose(h->M, h->n, h->m, h->n, h->MT, h->m, s);
-        launch_sumsq(h->M, h->m * h->n, h->work, WORK_ELEMS, h->dscal + 0, s);
+        h->sumsq_dirty = true;  // ||M||^2 is computed when a relative error or the bound needs it
         h->has_dense = true;
-        dfree(h->Mb);
-        dfree(h->MTb);
-        dfree(h->Mq);
-        dfree(h->MTq);
+        const bool bf16 = h->opt.precision == DSANLS_PREC_BF16, fp8 = h->opt.precision == DSANLS_PREC_FP8;
+        if (refresh && bf16 && h->Mb) {
+            launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, s);
+            launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, s);
+        } else {
+            dfree(h->Mb);
+            dfree(h->MTb);
+        }
+        if (refresh && fp8 && h->Mq) {
+            launch_quant_rowblocks(h->M, h->m, h->n, h->qscale[0], h->Mq, s);
+            launch_quant_rowblocks(h->MT, h->n, h->m, h->qscale[1], h->MTq, s);
+        } else {
+            dfree(h->Mq);
+            dfree(h->MTq);
+        }
+        const bool had_copies = (bf16 && h->Mb) || (fp8 && h->Mq) || (!bf16 && !fp8);
         make_reduced_copies(h);
-        invalidate_graph(h);
-        std::fill(h->cfg_key, h->cfg_key + 6, -1);
+        // a graph holds the buffer pointers and, with the clamp, the bound by value
+        if (!refresh || !had_copies || h->opt.bound_clamp) {
+            invalidate_graph(h);
+            std::fill(h->cfg_key, h->cfg_key + 6, -1);
+        }
         set_bound(h);
         DSANLS_CUDA(cudaStreamSynchronize(s));
         return DSANLS_OK;
@@ -922,6 +948,7 @@ int dsanls_rel_error(dsanls_t h, double *out) {
     return guarded(h, [&]() {
         cudaStream_t s = h->stream();
         if (h->has_dense) {
+            ensure_sumsq(h);
             launch_dense_residual(h->M, h->n, h->U, h->V, h->m, h->n, h->k, h->work, WORK_ELEMS, h->dscal + 1, s);
         } else {
             double *GU = h->dscal + 3, *GV = h->dscal + 3 + 128 * 128;

@@ -297,3 +297,35 @@ def test_fp8_reassociated_run_final_error(pkg):
     h.close()
     _, _, errs = method.run(M, U0, V0, 0, T, method.Options(sketch=method.GAUSSIAN, d=d))
     assert abs(err - errs[-1]) <= 2e-3, (err, errs[-1])
+
+
+@pytest.mark.parametrize("precision,order", [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1)])
+def test_new_dense_data_in_a_captured_handle(pkg, precision, order):
+    """set_dense on a handle whose iteration graph was captured on other data
+    (the buffers are refilled in place and the graph kept): the factors and
+    the relative error equal those of a fresh handle on the new data."""
+    m, n, k, d = 1024, 768, 32, 128
+    M1, _, _ = planted_dense(m, n, 16, 1)
+    M2, _, _ = planted_dense(m, n, 16, 2)
+    U0, V0 = initial_factors(m, n, k, 4)
+    h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=3, precision=precision, order=order, use_graph=1)
+    h.set_dense(M1)
+    h.set_factors(U0, V0)
+    h.step(2)
+    h.rel_error()
+    h.set_dense(M2)
+    h.set_factors(U0, V0)
+    h.set_options(t=0)
+    h.step(2)
+    got_u, got_v = h.factors()
+    got_e = h.rel_error()
+    h.close()
+    ref = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=3, precision=precision, order=order, use_graph=1)
+    ref.set_dense(M2)
+    ref.set_factors(U0, V0)
+    ref.step(2)
+    want_u, want_v = ref.factors()
+    want_e = ref.rel_error()
+    ref.close()
+    assert np.array_equal(got_u, want_u) and np.array_equal(got_v, want_v)
+    assert got_e == want_e
