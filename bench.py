@@ -283,7 +283,14 @@ def _traffic(kernel_key, workload):
     src = os.path.join(ROOT, "paper_2009_02845_gb300", "csrc", ent["source"])
     if not os.path.exists(src):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(src, "rb").read()
+    marker = ent.get("source_end_marker")
+    if marker:  # only the part of the file that holds the kernel (it ends at the marker)
+        cut = text.find(marker.encode())
+        if cut < 0:
+            return None
+        text = text[:cut]
+    h = hashlib.sha256(text).hexdigest()[:16]
     return ent["bytes_per_launch"] if h == ent["source_sha"] else None
 
 
