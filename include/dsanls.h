@@ -375,9 +375,14 @@ int dsanls_harvest(dsanls_t h, int32_t side, int32_t iters, float *G, float *mu,
  * half-step.  It allocates nothing: its only scratch is a fixed 2 MiB
  * file-scope device array inside libdsanls.so (FP64 partial Grams of up to
  * floor(262144 / k^2) CTAs), which every GPU that loads the library holds
- * until the process exits.  The first call on a device resolves that array's
- * device address (cudaGetSymbolAddress, with the device current); make that
- * first call before any stream capture.  All calls on a device share the
+ * until the process exits.  The fixed size costs parallelism: the partial
+ * Gram runs on at most floor(262144 / k^2) CTAs -- 16 at k = 128, 26 at
+ * k = 100, 64 at k = 64 -- where the handle's Gram uses up to 304 (2 per SM),
+ * so at large k and d it is several times slower; from k <= 29 on it gets
+ * the full grid.  The first call on a device resolves that array's device
+ * address (cudaGetSymbolAddress, with the device current); make that first
+ * call before any stream capture -- a first call while `stream` is being
+ * captured returns EINVAL and queues nothing.  All calls on a device share the
  * array: calls whose executions overlap on the GPU race and give wrong
  * results -- serialise them (one stream, or events).  Every partial a call
  * reads is written by the same call, so stale contents from an earlier call

@@ -16,6 +16,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -591,16 +592,23 @@ static std::atomic<uint64_t> g_launches{0};
 uint64_t launch_count() { return g_launches.load(); }
 void add_launches(uint64_t n) { g_launches.fetch_add(n); }
 
+// cudaFuncSetAttribute applies to the current device only, so the kernels'
+// shared-memory limits are raised once per device, with that device current;
+// the mutex orders callers on different host threads.
 void prime_kernel_attributes() {
-    static bool done = false;
-    if (done) return;
+    constexpr int kMaxPrimedDevices = 64;
+    static std::mutex mu;
+    static bool done[kMaxPrimedDevices] = {};
     int dev = 0, max_smem = 0;
     DSANLS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxPrimedDevices) throw ArgError{"device ordinal out of range"};
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return;
     DSANLS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     prime_rng_attributes(max_smem);
     prime_solver_attributes(max_smem);
     prime_tc_attributes(max_smem);
-    done = true;
+    done[dev] = true;
 }
 }  // namespace dsanls
 

@@ -20,7 +20,11 @@ namespace dsanls {
 namespace {
 
 // 2 MiB of FP64 partial Gram matrices: room for floor(262144 / k^2) CTAs
-// (16 at k = 128, 64 at k = 64, 1024 at k = 16).
+// (16 at k = 128, 26 at k = 100, 64 at k = 64, 256 at k = 32; the kernel
+// never launches more than 304).  The cost of the fixed size: at k = 128 the
+// partial Gram runs on 16 of the 152 SMs and at k = 100 on 26, against up to
+// 304 CTAs with a handle's workspace, so for large d it is correspondingly
+// slower; from k <= 29 on it gets the full grid.
 constexpr int64_t kScratchDoubles = 262144;
 static __device__ __align__(256) double kScratch[kScratchDoubles];
 
@@ -30,13 +34,21 @@ double *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of kScratch for the current device, resolved once per
 // device with that device current.  In host code kScratch is only a host-side
-// stand-in; the kernel must be given this address.
-double *scratch_for_current_device() {
+// stand-in; the kernel must be given this address.  The set-up calls
+// (cudaGetSymbolAddress, cudaFuncSetAttribute) must not run while `stream`
+// is being captured into a graph: such a first call is refused with EINVAL
+// before anything reaches the stream.
+double *scratch_for_current_device(cudaStream_t stream) {
     int dev = 0;
     DSANLS_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) throw ArgError{"device ordinal out of range"};
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        DSANLS_CUDA(cudaStreamIsCapturing(stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            throw ArgError{"the first call on a device sets up the scratch address and must come before any "
+                           "stream capture"};
         void *p = nullptr;
         DSANLS_CUDA(cudaGetSymbolAddress(&p, kScratch));
         prime_kernel_attributes();
@@ -65,7 +77,7 @@ extern "C" int dsanls_gram_noalloc(const float *B, int32_t k, int64_t d, double 
         return DSANLS_EINVAL;
     }
     try {
-        double *scratch = scratch_for_current_device();
+        double *scratch = scratch_for_current_device((cudaStream_t)stream);
         // every partial the reduction reads is written by this call, so
         // nothing in the scratch needs clearing first
         launch_gram(B, k, d, G, scratch, kScratchDoubles, (cudaStream_t)stream);

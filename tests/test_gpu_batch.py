@@ -9,7 +9,7 @@ iterations the relative errors agree to 1e-4.
 import numpy as np
 import pytest
 
-from oracle import method
+from oracle import bounds, method
 from synthdata import batch_specs, planted_dense
 
 pytestmark = pytest.mark.gpu
@@ -150,9 +150,10 @@ def test_batch_reassociated_one_iteration(pkg, use_graph):
 
 @pytest.mark.parametrize("order", [0, 1])
 def test_batch_bf16_one_iteration(pkg, order):
-    """The bf16 batched form against the oracle's bf16 model of the same order,
-    per instance (<= 3e-4: fp32 accumulation order and the rare bf16 rounding
-    flip of an fp32-accumulated A or P entry)."""
+    """The bf16 batched form per instance: against the exact oracle within the
+    derived bound of the form (oracle/bounds.py), and (diagnostic) the
+    oracle's bf16 model of the same order (<= 3e-4: fp32 accumulation order
+    and the rare bf16 rounding flip of an fp32-accumulated A or P entry)."""
     Ms = _inputs(SHAPES)
     b = pkg.Batch(SHAPES, use_graph=1, order=order, precision=pkg.BF16)
     for i, M in enumerate(Ms):
@@ -171,4 +172,9 @@ def test_batch_bf16_one_iteration(pkg, order):
                               reassociate=order == 1)
         assert _rel(U, Uo) <= 3e-4, (i, _rel(U, Uo))
         assert _rel(V, Vo) <= 3e-4, (i, _rel(V, Vo))
+        form = "bf16_reassociated" if order == 1 else "bf16"
+        rel, rb = bounds.check(U, M64, V0.astype(np.float64), U0.astype(np.float64), S, 0, mu, form)
+        assert rel <= rb, (i, rel, rb)
+        rel, rb = bounds.check(V, M64.T, U.astype(np.float64), V0.astype(np.float64), Sp, 0, mu, form)
+        assert rel <= rb, (i, rel, rb)
     b.close()

@@ -182,6 +182,29 @@ def test_rescaling_invariance_lemma1():
     assert abs(method.rel_error(M, U @ D, V @ np.linalg.inv(D)) - method.rel_error(M, U, V)) < 1e-13
 
 
+def test_rel_error_of_an_exact_factorisation_is_zero():
+    """M = U0 V0^T with small-integer factors (every product and sum exact in
+    FP64): the relative error of Section 5.1 is exactly 0, dense and sparse."""
+    g = np.random.default_rng(3)
+    U0 = g.integers(0, 4, size=(37, 5)).astype(np.float64)
+    V0 = g.integers(0, 4, size=(23, 5)).astype(np.float64)
+    M = U0 @ V0.T
+    assert method.rel_error(M, U0, V0) == 0.0
+    assert method.rel_error(sp.csr_matrix(M), U0, V0) == 0.0
+
+
+def test_rel_error_hand_computed_2x2():
+    """M = [[1, 2], [3, 4]], U = [[1], [1]], V = [[1], [2]]: U V^T = [[1, 2],
+    [1, 2]], M - U V^T = [[0, 0], [2, 2]], so the error is sqrt(8 / 30)."""
+    M = np.array([[1.0, 2.0], [3.0, 4.0]])
+    U = np.array([[1.0], [1.0]])
+    V = np.array([[1.0], [2.0]])
+    assert method.rel_error(M, U, V) == pytest.approx(np.sqrt(8.0 / 30.0), rel=1e-15)
+    assert method.rel_error(sp.csr_matrix(M), U, V) == pytest.approx(np.sqrt(8.0 / 30.0), rel=1e-14)
+    # a wrong normalisation (by ||U V^T|| or squared) would give another number
+    assert abs(method.rel_error(M, U, V) - 8.0 / 30.0) > 0.1
+
+
 def test_sparse_error_expansion_equals_direct():
     g = np.random.default_rng(0)
     D = g.random((40, 30))

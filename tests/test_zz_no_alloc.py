@@ -13,6 +13,9 @@ does not leak into the second.  This file sorts last so that a run stopping
 at the first failure has already run every other test.
 """
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -42,7 +45,9 @@ def _existing_gram(pkg, M, U, V):
     return G
 
 
-@pytest.mark.parametrize("m,n,k", [(300, 257, 16), (200, 1500, 64), (150, 700, 100), (96, 333, 128)])
+# k = 10 and 33 run the masked staging and output paths of k % 4 != 0
+@pytest.mark.parametrize("m,n,k", [(300, 257, 16), (200, 1500, 64), (150, 700, 100), (96, 333, 128),
+                                   (300, 257, 10), (120, 901, 33)])
 def test_noalloc_gram_matches_handle_gram(pkg, m, n, k):
     import torch
     M, _, _ = planted_dense(m, n, min(k, 16), 4)
@@ -70,3 +75,38 @@ def test_noalloc_gram_rejects_sizes_beyond_its_scratch(pkg):
     assert rc == -1
     assert b"k must be in [1, 128]" in lib.dsanls_last_error(None)
     assert lib.dsanls_gram_noalloc(None, 4, 8, ctypes.c_void_p(G.data_ptr()), None) == -1
+
+
+_CAPTURE_PROBE = r"""
+import ctypes, sys, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2009_02845_gb300 as pkg
+lib = pkg.lib()
+B = torch.ones((8, 64), dtype=torch.float32, device="cuda")
+G = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+s = torch.cuda.Stream()
+torch.cuda.synchronize()
+g = torch.cuda.CUDAGraph()
+with torch.cuda.graph(g, stream=s):
+    G.mul_(1.0)  # keeps the captured graph non-empty
+    rc = lib.dsanls_gram_noalloc(ctypes.c_void_p(B.data_ptr()), 8, 64, ctypes.c_void_p(G.data_ptr()),
+                                 ctypes.c_void_p(s.cuda_stream))
+msg = lib.dsanls_last_error(None)
+# outside capture the same first call sets the device up and computes G
+rc2 = lib.dsanls_gram_noalloc(ctypes.c_void_p(B.data_ptr()), 8, 64, ctypes.c_void_p(G.data_ptr()), None)
+torch.cuda.synchronize()
+print(rc, rc2, float(G[0, 0].item()), msg.decode())
+"""
+
+
+def test_noalloc_first_call_inside_capture_is_refused():
+    """A fresh process whose first call on the device comes while its stream
+    is being captured gets EINVAL (and nothing is queued, so the capture ends
+    normally); the next call outside capture works."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _CAPTURE_PROBE, root], capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    rc, rc2, g00, msg = out.stdout.strip().splitlines()[-1].split(" ", 3)
+    assert int(rc) == -1 and "before any stream capture" in msg
+    assert int(rc2) == 0 and float(g00) == 64.0
