@@ -340,6 +340,16 @@ def time_to_eps(pkg, torch, M, w, T, check_every, stream):
         b = first_hit(tr)
         out[name] = {"to_eps": b, "final_err": tr[-1][2], "seconds_T": tr[-1][1] / 1000.0,
                      "speedup_time_to_eps": (a["seconds"] / b["seconds"]) if (a and b) else None}
+    # the FP64 oracle's trajectory of the same problem (written offline by
+    # tests/golden/make_dense_trajectory.py): the final error of every form against it
+    gold = os.path.join(ROOT, "tests", "golden", "dense_%dx%d_k%d_d%d_gaussian_pgd_T%d.json" % (
+        w["m"], w["n"], w["k"], w["d"], T))
+    if os.path.exists(gold) and w.get("zero_frac") == 0.7 and w["sketch"] == 0 and w["d_v"] == w["d"]:
+        ge = json.load(open(gold))["errors"]
+        out["oracle_fp64"] = {"final_err": ge[T - 1], "source": os.path.relpath(gold, ROOT)}
+        out["fp32"]["max_abs_diff_vs_oracle"] = max(abs(e - ge[it - 1]) for it, _, e in fp32)
+        for name in ["fp32"] + list(forms):
+            out[name]["final_minus_oracle"] = out[name]["final_err"] - ge[T - 1]
     return out
 
 
@@ -408,6 +418,13 @@ def run_ours(args, w):
             bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
             kernel_key = "tc_skinny" if prec == pkg.BF16 else "tc_skinny_fp8"
             peak_note = "hbm_gbs of %s" % peak_src
+        elif m % 8 == 0 and n % 8 == 0 and dense_sketch:
+            # FP32 on tensor cores: the streaming product reads the three bf16 parts of X
+            # (6 bytes per entry) and the parts of P^T
+            bytes_ = [6.0 * (m * n + k * n) + 4.0 * m * k, 6.0 * (n * m + k * m) + 4.0 * n * k]
+            achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
+            bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "tc_skinny_split3"
+            peak_note = "hbm_gbs of %s (bytes of the three bf16 parts of X)" % peak_src
         else:
             achieved = sum(flops) / (sum(prod_ms) / 1000.0) / 1e12
             bound, peak, unit, kernel_key = "alu", FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "sgemm_simt"
@@ -426,6 +443,12 @@ def run_ours(args, w):
             bound, peak, unit, kernel_key = "tensor", 2.0 * peaks["bf16_tflops"], "TFLOP/s", "tc_sketch_rhs_fp8"
             peak_note = ("2 x bf16_tflops (burst) of %s (nominal fp8:bf16 dense ratio 4.5:2.25); the kernel is "
                          "timed alone by profile_half_step" % peak_src)
+        elif m % 8 == 0 and n % 8 == 0:
+            # binary32 accuracy from six bf16 tensor-core products of three-way splits:
+            # the ceiling for the method's FP32 flops is a sixth of the bf16 peak
+            bound, peak, unit, kernel_key = "tensor", peaks["bf16_tflops"] / 6.0, "TFLOP/s", "tc_gemm_split3"
+            peak_note = ("bf16_tflops (burst) of %s / 6: A = X S as six bf16 products of three-way splits "
+                         "(algorithmic FP32 flops 2 rows K d per half)" % peak_src)
         else:
             bound, peak, unit, kernel_key = "alu", FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "sgemm_simt"
             peak_note = "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
@@ -437,7 +460,7 @@ def run_ours(args, w):
         bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "sgemm_simt_gather"
         peak_note = "hbm_gbs of %s" % peak_src
     else:
-        # sparse subsampling: the fused row update reads Z and R and writes Z (12 bytes per entry)
+        # sparse subsampling: the row update reads Z and R and writes Z (12 bytes per entry)
         bytes_ = [12.0 * m * k, 12.0 * n * k]
         prod_ms = [p["update"] for p in phases]
         achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
@@ -848,6 +871,23 @@ def run_batch(args, w):
     ar_ms = prof["U"]["AR"] + prof["V"]["AR"]
     ar_flops = flops
     achieved = ar_flops / (ar_ms / 1000.0) / 1e12
+    tc = prec == pkg.BF16 and order == 0
+    if tc:
+        # tensor-core product: HBM-bound (about d FLOP per byte of bf16 M, below the ridge):
+        # bf16 X_i read once, S_i^T once, R_i written, both halves
+        peaks, peak_src = _peaks()
+        ar_bytes = sum(2.0 * s["m"] * s["n"] + 2.0 * s["n"] * s["d"] + 4.0 * s["m"] * s["k"] +
+                       2.0 * s["n"] * s["m"] + 2.0 * s["m"] * s["d_v"] + 4.0 * s["n"] * s["k"] for s in specs)
+        gbs = ar_bytes / (ar_ms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "kb_ar_tc",
+                    "peak_source": "hbm_gbs of %s" % peak_src, "tensor_tflops": achieved,
+                    "launch_ms": [prof["U"]["AR"], prof["V"]["AR"]]}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None, "kernel": "kb_ar",
+                    "peak_source": "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz",
+                    "launch_ms": [prof["U"]["AR"], prof["V"]["AR"]]}
     value = job_value(ws, args.steps, ms)
     cpu = None
     if not args.no_cpu_baseline:
@@ -870,13 +910,10 @@ def run_batch(args, w):
             "vs_baseline": None, "dtype": "f32" if prec == pkg.FP32 else "bf16", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "instances": len(specs),
                        "order": ["paper", "reassociated"][order],
-                       "graph": True, "persistent_ctas": b.tuned_blocks(),
+                       "graph": True, "persistent_ctas": b.tuned_blocks(), "tc_tile": b.tuned_tile(),
                        "l2": "inputs larger than L2 (M_i total %.1f GB)" % (sum(M.nbytes for M in Ms) / 1e9)},
             "instance_iters_per_s": value * len(specs),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None, "kernel": "kb_ar",
-                         "peak_source": "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz",
-                         "launch_ms": [prof["U"]["AR"], prof["V"]["AR"]]},
+            "roofline": roofline,
             "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk,
             "phases_ms": prof, "rel_error_median": float(np.median(errs)), "rel_error_max": float(errs.max()),
         }), flush=True)

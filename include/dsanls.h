@@ -216,6 +216,27 @@ int dsanls_profile_half_step(dsanls_t h, int32_t side, int32_t reps, double *ms)
  * process (a replayed CUDA graph counts each of its kernels).  No GPU work. */
 int dsanls_kernel_launches(uint64_t *out);
 
+/* ---- test switches (no counterpart in the paper) ------------------------
+ * For tests of the failure paths without faulting the GPU.  Both are
+ * process-wide and off by default.
+ *
+ * dsanls_debug_fail_alloc_after(n): n >= 0 lets the next n device
+ * allocations of handles (dsanls_create, set_*, step workspaces) succeed and
+ * makes the one after fail as if the device were out of memory (the call
+ * returns DSANLS_ENOMEM and releases what it had allocated); n < 0 turns the
+ * switch off.  Never fails itself.
+ *
+ * dsanls_debug_tc_wait(wait_ns, starve), on the current device: wait_ns > 0
+ * replaces the 2 s limit of the bounded waits of the tensor-core kernels
+ * (0 restores it); starve = 1 (needs wait_ns > 0) makes the TMA producer of
+ * the tensor-core GEMM issue no copy, so its consumers' waits run out with
+ * nothing in flight: the kernel frees its tensor memory, returns, and the
+ * next synchronising call of the handle reports DSANLS_ETIMEOUT.  EINVAL for
+ * starve outside {0, 1} or starve without a limit; ECUDA if the device
+ * symbols cannot be written.  Synchronous. */
+int dsanls_debug_fail_alloc_after(int64_t n);
+int dsanls_debug_tc_wait(uint64_t wait_ns, int32_t starve);
+
 /* Message of the last failed call on handle h; with h == NULL, of the last
  * failed dsanls_create or stateless primitive on the calling thread ("" if
  * none).  The string stays valid until the next call that fails. */
@@ -315,6 +336,13 @@ int dsanls_batch_rel_error(dsanls_batch_t b, double *out);
 int dsanls_batch_profile(dsanls_batch_t b, double *ms);
 /* Persistent CTAs chosen by the autotuner (0 before the first step). */
 int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas);
+/* BF16 paper order: R_i = (X_i S_i) B_i^T runs on tcgen05 tensor cores (one
+ * persistent launch over (instance, 128-row tile) items, A_i kept on chip).
+ * The tile chosen by the autotuner for it: *chunk = sketch columns per chunk
+ * of a tile (64, 128 or 256; it sets the tile's shared memory and tensor-
+ * memory columns and so its CTAs per SM), *ctas = persistent CTAs; both 0
+ * before the first step or in the other forms. */
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas);
 const char *dsanls_batch_last_error(dsanls_batch_t b);
 void dsanls_batch_destroy(dsanls_batch_t b);
 

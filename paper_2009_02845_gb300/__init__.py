@@ -13,7 +13,7 @@ from ._lib import (  # noqa: F401
     DSANLS, Batch, MLP, DSANLSError, GAUSSIAN, SUBSAMPLE, IDENTITY, RADEMACHER, COUNT, SRHT, PGD, RCD, FP32, BF16, FP8,
     ORDER_PAPER, ORDER_REASSOCIATED,
     STREAM_SKETCH_U, STREAM_SKETCH_V, STREAM_INIT_U, STREAM_INIT_V,
-    lib, lib_path, kernel_launches, PHASES, gram_noalloc, philox_field, gaussian_field, rademacher_field, count_field,
+    lib, lib_path, kernel_launches, PHASES, gram_noalloc, debug_fail_alloc_after, debug_tc_wait, philox_field, gaussian_field, rademacher_field, count_field,
     srht_field, uniform_field,
     subsample_indices,
     EXPORTED_SYMBOLS,

@@ -25,11 +25,11 @@ EXPORTED_SYMBOLS = [
     "dsanls_uniform_field",
     "dsanls_subsample_indices", "dsanls_profile_half_step", "dsanls_kernel_launches", "dsanls_gram_noalloc",
     "dsanls_batch_create", "dsanls_batch_set_options", "dsanls_batch_set_dense", "dsanls_batch_set_factors",
-    "dsanls_batch_step", "dsanls_batch_get_factors", "dsanls_batch_rel_error", "dsanls_batch_tuned_blocks", "dsanls_batch_profile",
+    "dsanls_batch_step", "dsanls_batch_get_factors", "dsanls_batch_rel_error", "dsanls_batch_tuned_blocks", "dsanls_batch_tuned_tile", "dsanls_batch_profile",
     "dsanls_batch_last_error", "dsanls_batch_destroy",
     "dsanls_mlp_create", "dsanls_mlp_param_count", "dsanls_mlp_get_params", "dsanls_mlp_set_params",
     "dsanls_mlp_predict", "dsanls_mlp_train_step", "dsanls_mlp_destroy", "dsanls_set_mlp", "dsanls_mlp_kept",
-    "dsanls_harvest",
+    "dsanls_harvest", "dsanls_debug_fail_alloc_after", "dsanls_debug_tc_wait",
 ]
 NPHASES = 7
 PHASES = ["sketch", "B", "product", "rhs", "gram", "step_size", "update"]
@@ -104,6 +104,7 @@ def lib():
             "dsanls_batch_get_factors": ([vp, i32, vp, vp, i32], ctypes.c_int),
             "dsanls_batch_rel_error": ([vp, vp], ctypes.c_int),
             "dsanls_batch_tuned_blocks": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
+            "dsanls_batch_tuned_tile": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
             "dsanls_batch_profile": ([vp, vp], ctypes.c_int),
             "dsanls_batch_last_error": ([vp], ctypes.c_char_p),
             "dsanls_batch_destroy": ([vp], None),
@@ -118,6 +119,8 @@ def lib():
             "dsanls_set_mlp": ([vp, vp, i32], ctypes.c_int),
             "dsanls_mlp_kept": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
             "dsanls_harvest": ([vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
+            "dsanls_debug_fail_alloc_after": ([i64], ctypes.c_int),
+            "dsanls_debug_tc_wait": ([u64, i32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -158,6 +161,19 @@ def kernel_launches():
     v = ctypes.c_uint64()
     _check(lib().dsanls_kernel_launches(ctypes.byref(v)), "kernel_launches")
     return v.value
+
+
+def debug_fail_alloc_after(n):
+    """Test switch: the next n device allocations of handles succeed, the one
+    after fails as out of memory (n < 0: off)."""
+    _check(lib().dsanls_debug_fail_alloc_after(int(n)), "debug_fail_alloc_after")
+
+
+def debug_tc_wait(wait_ns=0, starve=False):
+    """Test switch of the tensor-core kernels' bounded waits on the current
+    device: a limit of wait_ns (0: the default 2 s) and, with starve, a GEMM
+    producer that issues no copy so the waits run out."""
+    _check(lib().dsanls_debug_tc_wait(int(wait_ns), int(bool(starve))), "debug_tc_wait")
 
 
 def gram_noalloc(B, G=None):
@@ -466,6 +482,13 @@ class Batch:
         v = ctypes.c_int32()
         self._err(lib().dsanls_batch_tuned_blocks(self._h, ctypes.byref(v)), "batch_tuned_blocks")
         return v.value
+
+    def tuned_tile(self):
+        """(chunk, ctas) of the tensor-core product chosen by the autotuner (bf16
+        paper order; (0, 0) otherwise or before the first step)."""
+        c, n = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._err(lib().dsanls_batch_tuned_tile(self._h, ctypes.byref(c), ctypes.byref(n)), "batch_tuned_tile")
+        return c.value, n.value
 
     def close(self):
         if getattr(self, "_h", None):

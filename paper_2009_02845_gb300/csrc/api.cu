@@ -16,6 +16,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -31,6 +32,11 @@ using namespace dsanls;
 
 namespace {
 
+// Allocation-failure test switch (dsanls_debug_fail_alloc_after): when >= 0,
+// the number of handle allocations that still succeed; the next one fails as
+// if the device were out of memory.
+std::atomic<int64_t> g_alloc_budget{-1};
+
 template <typename T>
 void dalloc(T *&p, int64_t count) {
     if (p) {
@@ -38,6 +44,10 @@ void dalloc(T *&p, int64_t count) {
         p = nullptr;
     }
     if (count <= 0) return;
+    for (int64_t b = g_alloc_budget.load(); b >= 0; b = g_alloc_budget.load()) {
+        if (b == 0) throw std::bad_alloc();
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
     cudaError_t e = cudaMalloc((void **)&p, (size_t)count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -102,6 +112,8 @@ struct dsanls_ctx {
     bool sumsq_dirty = false;  // ||M||^2 of new dense data not computed yet (done when needed)
     float *M = nullptr, *MT = nullptr;
     __nv_bfloat16 *Mb = nullptr, *MTb = nullptr;
+    // FP32 form on tensor cores: three-way bf16 splits of M and M^T
+    __nv_bfloat16 *M3[3] = {nullptr, nullptr, nullptr}, *MT3[3] = {nullptr, nullptr, nullptr};
     int64_t nnz = 0;
     int64_t *rp = nullptr, *trp = nullptr;
     int32_t *ci = nullptr, *tci = nullptr;
@@ -133,6 +145,10 @@ struct dsanls_ctx {
     // fp8 reassociated order: P^T in fp32, its E4M3 codes and one scale per row of P^T
     float *Ptf = nullptr, *pscale = nullptr;
     uint8_t *Pq = nullptr;
+    // FP32 form on tensor cores: split parts of S^T (paper order) or of P^T
+    // (reassociated order) and the split-K partials of their products
+    __nv_bfloat16 *St3[3] = {nullptr, nullptr, nullptr}, *Pt3[3] = {nullptr, nullptr, nullptr};
+    float *Spart = nullptr;
     double *G64[2] = {nullptr, nullptr};
     double *scal[2] = {nullptr, nullptr};
     float *Gf = nullptr;
@@ -141,7 +157,7 @@ struct dsanls_ctx {
     int *flag = nullptr;
     double *dscal = nullptr;  // [0] ||M||^2, [1] residual^2, [2] cross, [3..] Gram of U, Gram of V
     uint32_t *bits = nullptr;  // membership bitmap of the sampled set (sparse subsampling)
-    LongRows lr[2];            // chunked long rows of the CSR of M (0) and of M^T (1)
+    SubCsr sub[2];             // sub-CSR of X[:, J] per side (sparse data, subsampling sketch)
     dsanls_mlp_ctx *mlp = nullptr;          // learned warm start (borrowed), or none
     int pg_iters = 0;
     unsigned long long *kept = nullptr;     // rows whose learned point was kept
@@ -220,6 +236,25 @@ void invalidate_graph(dsanls_ctx *h) {
 
 int d_v_of(const dsanls_ctx *h) { return h->opt.d_v > 0 ? h->opt.d_v : h->d; }
 
+// The FP32 form of a dense-sketch product runs on tensor cores from three-way
+// bf16 splits when the rows of both orientations of M are 16-byte multiples
+// (TMA), else on CUDA cores.
+bool fp32_split(const dsanls_ctx *h) {
+    return h->has_dense && h->opt.precision == DSANLS_PREC_FP32 && h->m % 8 == 0 && h->n % 8 == 0;
+}
+
+// Sum of the d largest row lengths of a CSR row pointer (the most entries a
+// sampled set of d of its rows can hold).
+int64_t top_sum(const std::vector<int64_t> &ptr, int64_t d) {
+    std::vector<int64_t> len(ptr.size() > 0 ? ptr.size() - 1 : 0);
+    for (size_t i = 0; i < len.size(); ++i) len[i] = ptr[i + 1] - ptr[i];
+    d = std::min<int64_t>(d, (int64_t)len.size());
+    std::nth_element(len.begin(), len.begin() + d, len.end(), std::greater<int64_t>());
+    int64_t s = 0;
+    for (int64_t i = 0; i < d; ++i) s += len[i];
+    return s;
+}
+
 // (Re)allocate the per-configuration workspaces.
 void prepare(dsanls_ctx *h) {
     const int dv = d_v_of(h);
@@ -256,6 +291,15 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->Ptf, (reas && fp8) ? k * kmax : 0);
     dalloc(h->Pq, (reas && fp8) ? k * kmax : 0);
     dalloc(h->pscale, (reas && fp8) ? 2 * k : 0);  // scales, then the row maxima (scratch)
+    const bool split = gauss && fp32_split(h);
+    for (int a = 0; a < 3; ++a) {
+        dalloc(h->St3[a], (split && !reas) ? std::max(n * h->d, m * dv) : 0);
+        dalloc(h->Pt3[a], (split && reas) ? k * kmax : 0);
+    }
+    dalloc(h->Spart, split ? std::max({tc_split3_part_elems(m, n, h->d), tc_split3_part_elems(n, m, dv),
+                                       tc_skinny_split3_part_elems(m, n, k), tc_skinny_split3_part_elems(n, m, k),
+                                       (int64_t)1})
+                           : 0);
     dalloc(h->W, k * (ident ? std::max(m, n) : dmax));
     dalloc(h->Wpart, (gauss && !bf16) ? (int64_t)MAX_SPLITS * k * dmax : 0);
     dalloc(h->Ytb, ((gauss && bf16) || ident_tc) ? k * std::max(m, n) : 0);
@@ -265,6 +309,15 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->Sq, (gauss && fp8 && !reas) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->bits, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? ceil_div(std::max(m, n), 32) + 1
                     : (srht ? ceil_div(srht_pad(std::max(m, n)), 32) + 1 : 0));
+    if (h->sketch == DSANLS_SKETCH_SUBSAMPLE && h->has_sparse) {
+        // U-half: columns of M (rows of M^T), V-half: rows of M; room for the
+        // longest possible sampled set of each side
+        h->sub[0].reserve(m, h->d, top_sum(h->h_trp, h->d), h->stream());
+        h->sub[1].reserve(n, dv, top_sum(h->h_rp, dv), h->stream());
+    } else {
+        h->sub[0].release();
+        h->sub[1].release();
+    }
     std::copy(key, key + 7, h->cfg_key);
 }
 
@@ -383,6 +436,10 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
                                      h->Rpart2, h->R, h->flag, s);
             } else if (tc) {
                 launch_tc_skinny(Xb, h->Ptb, rows, K, k, h->Rpart2, h->R, h->flag, s);
+            } else if (dense && fp32_split(h)) {
+                // R = X P at binary32 accuracy on tensor cores (six bf16 products of the splits)
+                launch_split3_transpose(h->P, K, k, h->Pt3, s);
+                launch_tc_skinny_split3(side == 0 ? h->M3 : h->MT3, h->Pt3, rows, K, k, h->Spart, h->R, h->flag, s);
             } else if (dense) {
                 GemmArgs g{};
                 g.M = rows; g.N = k; g.K = K;
@@ -403,7 +460,11 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             }
             mark(pe, DSANLS_PHASE_RHS, s);
         } else {
-            if (dense) {
+            if (dense && fp32_split(h)) {
+                // A = X S at binary32 accuracy on tensor cores (six bf16 products of the splits)
+                launch_split3_transpose(h->S, K, dd, h->St3, s);
+                launch_tc_gemm_split3(side == 0 ? h->M3 : h->MT3, h->St3, rows, K, dd, h->Spart, h->A, h->flag, s);
+            } else if (dense) {
                 GemmArgs g{};
                 g.M = rows; g.N = dd; g.K = K;
                 g.A = X; g.lda = K; g.a_kcontig = true;
@@ -438,8 +499,14 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             mark(pe, DSANLS_PHASE_RHS, s);
             launch_sgemm(g, s);
         } else {
+            // X[:, J] gathered from the rows J of the CSR of X^T, then
+            // R = c^2 X[:, J] Y[J, :] row by row
             mark(pe, DSANLS_PHASE_RHS, s);
-            launch_sampled_spmm(xp, xc, xv, rows, h->bits, Y, k, c2, h->R, h->lr[side], s);
+            const int64_t *ytp = side == 0 ? h->trp : h->rp;
+            const int32_t *ytc = side == 0 ? h->tci : h->ci;
+            const float *ytv = side == 0 ? h->tcv : h->cv;
+            launch_subcsr_build(ytp, ytc, ytv, h->J, dd, h->sub[side], s);
+            launch_subcsr_rows(h->sub[side], Y, k, c2, h->R, s);
         }
     } else {  // identity
         mark(pe, DSANLS_PHASE_B, s);
@@ -490,40 +557,6 @@ void outer_iteration(dsanls_ctx *h, cudaStream_t s) {
     launch_increment_t(h->t_dev, 1, s);
 }
 
-void free_long_rows(LongRows &lr) {
-    dfree(lr.rows); dfree(lr.first); dfree(lr.cbeg); dfree(lr.cend); dfree(lr.partial);
-    lr.nlong = lr.nchunks = 0;
-}
-
-// Rows longer than LONG_ROW entries and their chunks (host row pointer).
-void build_long_rows(LongRows &lr, const std::vector<int64_t> &ptr, int k, cudaStream_t s) {
-    free_long_rows(lr);
-    std::vector<int64_t> rows, first(1, 0), cb, ce;
-    for (size_t i = 0; i + 1 < ptr.size(); ++i) {
-        const int64_t len = ptr[i + 1] - ptr[i];
-        if (len <= LONG_ROW) continue;
-        rows.push_back((int64_t)i);
-        for (int64_t e = ptr[i]; e < ptr[i + 1]; e += LONG_ROW) {
-            cb.push_back(e);
-            ce.push_back(std::min(e + LONG_ROW, ptr[i + 1]));
-        }
-        first.push_back((int64_t)cb.size());
-    }
-    if (rows.empty()) return;
-    lr.nlong = (int64_t)rows.size();
-    lr.nchunks = (int64_t)cb.size();
-    dalloc(lr.rows, lr.nlong);
-    dalloc(lr.first, lr.nlong + 1);
-    dalloc(lr.cbeg, lr.nchunks);
-    dalloc(lr.cend, lr.nchunks);
-    dalloc(lr.partial, lr.nchunks * k);
-    DSANLS_CUDA(cudaMemcpyAsync(lr.rows, rows.data(), rows.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    DSANLS_CUDA(cudaMemcpyAsync(lr.first, first.data(), first.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    DSANLS_CUDA(cudaMemcpyAsync(lr.cbeg, cb.data(), cb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    DSANLS_CUDA(cudaMemcpyAsync(lr.cend, ce.data(), ce.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    DSANLS_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
-}
-
 int check_ready(dsanls_ctx *h) {
     if (!h->has_dense && !h->has_sparse) return fail(h, DSANLS_ESTATE, "no data: call dsanls_set_dense or dsanls_set_csr first");
     return DSANLS_OK;
@@ -550,6 +583,14 @@ void make_reduced_copies(dsanls_ctx *h) {
         dalloc(h->MTb, h->m * h->n);
         launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, s);
         launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, s);
+    }
+    if (fp32_split(h) && !h->M3[0]) {
+        for (int a = 0; a < 3; ++a) {
+            dalloc(h->M3[a], h->m * h->n);
+            dalloc(h->MT3[a], h->m * h->n);
+        }
+        launch_split3(h->M, h->m * h->n, h->M3, s);
+        launch_split3(h->MT, h->m * h->n, h->MT3, s);
     }
     if (h->opt.precision == DSANLS_PREC_FP8 && !h->Mq) {
         dalloc(h->Mq, h->m * h->n);
@@ -608,6 +649,7 @@ void prime_kernel_attributes() {
     prime_rng_attributes(max_smem);
     prime_solver_attributes(max_smem);
     prime_tc_attributes(max_smem);
+    batch_prime_tc(max_smem);
     done[dev] = true;
 }
 }  // namespace dsanls
@@ -779,6 +821,16 @@ int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device) 
             dfree(h->Mb);
             dfree(h->MTb);
         }
+        const bool split = fp32_split(h);
+        if (refresh && split && h->M3[0]) {
+            launch_split3(h->M, h->m * h->n, h->M3, s);
+            launch_split3(h->MT, h->m * h->n, h->MT3, s);
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                dfree(h->M3[a]);
+                dfree(h->MT3[a]);
+            }
+        }
         if (refresh && fp8 && h->Mq) {
             launch_quant_rowblocks(h->M, h->m, h->n, h->qscale[0], h->Mq, s);
             launch_quant_rowblocks(h->MT, h->n, h->m, h->qscale[1], h->MTq, s);
@@ -786,7 +838,7 @@ int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device) 
             dfree(h->Mq);
             dfree(h->MTq);
         }
-        const bool had_copies = (bf16 && h->Mb) || (fp8 && h->Mq) || (!bf16 && !fp8);
+        const bool had_copies = (bf16 && h->Mb) || (fp8 && h->Mq) || (!bf16 && !fp8 && (!split || h->M3[0]));
         make_reduced_copies(h);
         // a graph holds the buffer pointers and, with the clamp, the bound by value
         if (!refresh || !had_copies || h->opt.bound_clamp) {
@@ -857,6 +909,10 @@ int dsanls_set_csr(dsanls_t h, const int64_t *rowptr, const int32_t *col, const 
         }
         if (h->has_dense) {
             dfree(h->M); dfree(h->MT); dfree(h->Mb); dfree(h->MTb); dfree(h->Mq); dfree(h->MTq);
+            for (int a = 0; a < 3; ++a) {
+                dfree(h->M3[a]);
+                dfree(h->MT3[a]);
+            }
             h->has_dense = false;
         }
         dalloc(h->rp, m + 1);
@@ -874,7 +930,6 @@ int dsanls_set_csr(dsanls_t h, const int64_t *rowptr, const int32_t *col, const 
             copy_in(h->tcv, tv_src, nnz * sizeof(float), on_device, s);
         }
         h->nnz = nnz;
-        for (int which = 0; which < 2; ++which) build_long_rows(h->lr[which], which == 0 ? h->h_rp : h->h_trp, h->k, s);
         launch_sumsq(h->cv, nnz, h->work, WORK_ELEMS, h->dscal + 0, s);
         h->has_sparse = true;
         invalidate_graph(h);
@@ -1090,6 +1145,23 @@ int dsanls_harvest(dsanls_t h, int32_t side, int32_t iters, float *G, float *mu,
     });
 }
 
+int dsanls_debug_fail_alloc_after(int64_t n) {
+    g_alloc_budget.store(n < 0 ? -1 : n);
+    return DSANLS_OK;
+}
+
+int dsanls_debug_tc_wait(uint64_t wait_ns, int32_t starve) {
+    if (starve != 0 && starve != 1) return DSANLS_EINVAL;
+    if (starve && wait_ns == 0) {
+        record_handleless_error("dsanls_debug_tc_wait: a starved producer needs a short wait limit");
+        return DSANLS_EINVAL;
+    }
+    return guarded(nullptr, [&]() {
+        set_tc_wait_debug(wait_ns, starve);
+        return DSANLS_OK;
+    });
+}
+
 int dsanls_kernel_launches(uint64_t *out) {
     if (!out) return DSANLS_EINVAL;
     *out = launch_count();
@@ -1114,7 +1186,10 @@ void dsanls_destroy(dsanls_t h) {
         dfree(h->S); dfree(h->Sb); dfree(h->J); dfree(h->A); dfree(h->W); dfree(h->Wpart); dfree(h->R);
         dfree(h->Rpart); dfree(h->Ytb); dfree(h->Bpart);
         dfree(h->P); dfree(h->Sn); dfree(h->Bb); dfree(h->Ptb); dfree(h->Ppart); dfree(h->Rpart2);
-        dfree(h->Ptf); dfree(h->Pq); dfree(h->pscale);
+        dfree(h->Ptf); dfree(h->Pq); dfree(h->pscale); dfree(h->Spart);
+        for (int a = 0; a < 3; ++a) {
+            dfree(h->M3[a]); dfree(h->MT3[a]); dfree(h->St3[a]); dfree(h->Pt3[a]);
+        }
         dfree(h->Mq); dfree(h->MTq); dfree(h->Sq); dfree(h->qscale[0]); dfree(h->qscale[1]);
         for (int side = 0; side < 2; ++side) {
             dfree(h->G64[side]);
@@ -1122,8 +1197,8 @@ void dsanls_destroy(dsanls_t h) {
         }
         dfree(h->Gf); dfree(h->work); dfree(h->t_dev); dfree(h->flag); dfree(h->dscal);
         dfree(h->bits); dfree(h->kept);
-        free_long_rows(h->lr[0]);
-        free_long_rows(h->lr[1]);
+        h->sub[0].release();
+        h->sub[1].release();
         if (h->aux_stream) {
             cudaStreamSynchronize(h->aux_stream);
             cudaStreamDestroy(h->aux_stream);

@@ -35,7 +35,8 @@ struct dsanls_batch_ctx {
     uint64_t graph_launches = 0;
     std::vector<char> has_data;
     int64_t data_elems = 0;   // packed M_i and M_i^T
-    bool bf16_stale = true;   // the bf16 copy of data no longer matches it
+    int64_t datap_elems = 0, st_elems = 0;  // padded bf16 data and S^T (tensor-core form)
+    bool bf16_stale = true;   // the bf16 copies of data no longer match it
     std::vector<double> mm;  // ||M_i||^2
     double *work = nullptr;
     double *dres = nullptr;  // residual^2 per instance
@@ -96,10 +97,14 @@ void iteration(dsanls_batch_ctx *b, cudaStream_t s) {
     launch_increment_t(b->g.t_dev, 1, s);
 }
 
-// bf16 form: bring the bf16 copy of the packed data up to date (after set_dense)
+// bf16 form: bring the bf16 copy of the packed data (CUDA-core kernels) or its
+// padded copy (tensor-core product) up to date after set_dense
 void refresh_bf16(dsanls_batch_ctx *b, cudaStream_t s) {
     if (b->g.bf16 && b->bf16_stale) {
-        launch_copy_cast_bf16(b->g.data, b->data_elems, b->g.data_b, s);
+        if (b->g.tc)
+            launch_batch_pad_bf16(b->g, s);
+        else
+            launch_copy_cast_bf16(b->g.data, b->data_elems, b->g.data_b, s);
         b->bf16_stale = false;
     }
 }
@@ -116,7 +121,8 @@ std::string tune_key(const dsanls_batch_ctx *b) {
         shapes.push_back(buf);
     }
     std::sort(shapes.begin(), shapes.end());
-    const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "");
+    const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "") +
+                             (b->g.tc ? "tc" : "");
     std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
     return std::to_string(std::hash<std::string>()(key)) + "/" + form;
@@ -163,6 +169,17 @@ void cache_store(const std::string &key, int value) {
     std::fclose(f);
 }
 
+// A tuned configuration: per-SM persistent CTAs of the CUDA-core kernels, plus
+// (tensor-core form) 1000 x that + the chunk width of the tensor-core product.
+void apply_config(dsanls_batch_ctx *b, int code, int sms) {
+    const int per_sm = code >= 1000 ? code / 1000 : code;
+    b->cfg.persistent_blocks = 152 * per_sm;
+    if (code >= 1000) {
+        b->cfg.tc_nc = code % 1000;
+        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc);
+    }
+}
+
 // Time one full outer iteration for each candidate (factors restored after
 // each trial) and keep the fastest.
 void autotune(dsanls_batch_ctx *b) {
@@ -181,10 +198,21 @@ void autotune(dsanls_batch_ctx *b) {
         DSANLS_CUDA(cudaEventCreate(&e0));
         DSANLS_CUDA(cudaEventCreate(&e1));
         float best = 1e30f;
-        const int candidates[4] = {1, 2, 4, 8};
+        // CUDA-core kernels: persistent CTAs per SM; tensor-core product (bf16 paper
+        // order): the chunk of sketch columns per tile (64, 128 or 256), which sets its
+        // shared memory, tensor-memory columns and CTAs per SM
+        std::vector<int> candidates;
+        if (b->g.tc) {
+            for (int nc : {64, 128, 256})
+                for (int c : {2, 4}) candidates.push_back(c * 1000 + nc);
+        } else {
+            candidates = {1, 2, 4, 8};
+        }
+        int sms = 152;
+        DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
         try {
             for (int c : candidates) {
-                b->cfg.persistent_blocks = 152 * c;
+                apply_config(b, c, sms);
                 iteration(b, s);  // warm
                 DSANLS_CUDA(cudaEventRecord(e0, s));
                 iteration(b, s);
@@ -211,7 +239,9 @@ void autotune(dsanls_batch_ctx *b) {
         bfree(backup);
         cache_store(key, per_sm);
     }
-    b->cfg.persistent_blocks = 152 * per_sm;
+    int sms = 152;
+    DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    apply_config(b, per_sm, sms);
     b->tuned = true;
 }
 
@@ -246,7 +276,8 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
         DSANLS_CUDA(cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking));
         prime_kernel_attributes();
         b->h.resize(count);
-        int64_t offM = 0, offF = 0, offS = 0, offB = 0, offR = 0, offG = 0;
+        int64_t offM = 0, offF = 0, offS = 0, offB = 0, offR = 0, offG = 0, offMp = 0, offSt = 0;
+        auto pad8 = [](int64_t x) { return (x + 7) & ~(int64_t)7; };
         for (int i = 0; i < count; ++i) {
             BatchInst &x = b->h[i];
             std::memset(&x, 0, sizeof x);
@@ -272,7 +303,13 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
             offR += std::max(x.m, x.n) * x.k;
             x.offG = offG;
             offG += (int64_t)x.k * x.k + 4;
+            x.offMp = offMp;
+            offMp += pad8(x.m * pad8(x.n)) + pad8(x.n * pad8(x.m));
+            x.offSt = offSt;
+            offSt += pad8(std::max((int64_t)x.d * pad8(x.n), (int64_t)x.dv * pad8(x.m)));
         }
+        b->datap_elems = offMp;
+        b->st_elems = offSt;
         cudaStream_t s = b->stream();
         BatchDev &g = b->g;
         g.count = count;
@@ -311,6 +348,15 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
             DSANLS_CUDA(cudaMemcpyAsync(g.aritems[side], ai.data(), ai.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaMemcpyAsync(g.uitems[side], ui.data(), ui.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaMemcpyAsync(g.sketch_prefix[side], pre.data(), pre.size() * sizeof(int64_t),
+                                        cudaMemcpyHostToDevice, s));
+            std::vector<int2> ti;
+            std::vector<int64_t> tpre;
+            batch_build_tc_items(b->h, side, ti, tpre);
+            balloc(g.tcitems[side], (int64_t)ti.size());
+            balloc(g.sketch_t_prefix[side], (int64_t)tpre.size());
+            g.ntc[side] = (int)ti.size();
+            DSANLS_CUDA(cudaMemcpyAsync(g.tcitems[side], ti.data(), ti.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaMemcpyAsync(g.sketch_t_prefix[side], tpre.data(), tpre.size() * sizeof(int64_t),
                                         cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
         }
@@ -353,7 +399,13 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
             b->tuned = false;  // the launch geometry is tuned per form
         b->g.order = opt->order;
         b->g.bf16 = opt->precision == DSANLS_PREC_BF16 ? 1 : 0;
-        if (b->g.bf16 && !b->g.data_b) balloc(b->g.data_b, b->data_elems);
+        // bf16 in the paper order runs the right-hand side on tensor cores
+        b->g.tc = (b->g.bf16 && b->g.order == DSANLS_ORDER_PAPER) ? 1 : 0;
+        if (b->g.bf16 && !b->g.tc && !b->g.data_b) balloc(b->g.data_b, b->data_elems);
+        if (b->g.tc && !b->g.data_p) {
+            balloc(b->g.data_p, b->datap_elems);
+            balloc(b->g.St, b->st_elems);
+        }
         b->bf16_stale = true;
         drop_graph(b);
         if (opt->t != b->t_host) {
@@ -512,6 +564,14 @@ int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas) {
     return DSANLS_OK;
 }
 
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas) {
+    if (!b || !chunk || !ctas) return DSANLS_EINVAL;
+    const bool tc = b->tuned && b->g.tc;
+    *chunk = tc ? b->cfg.tc_nc : 0;
+    *ctas = tc ? b->cfg.tc_ctas : 0;
+    return DSANLS_OK;
+}
+
 const char *dsanls_batch_last_error(dsanls_batch_t b) { return b ? b->err.c_str() : "invalid handle"; }
 
 void dsanls_batch_destroy(dsanls_batch_t b) {
@@ -521,8 +581,10 @@ void dsanls_batch_destroy(dsanls_batch_t b) {
     drop_graph(b);
     BatchDev &g = b->g;
     bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.P); bfree(g.G); bfree(g.data_b);
+    bfree(g.data_p); bfree(g.St);
     for (int side = 0; side < 2; ++side) {
         bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]); bfree(g.pitems[side]);
+        bfree(g.tcitems[side]); bfree(g.sketch_t_prefix[side]);
     }
     bfree(g.counters); bfree(g.t_dev); bfree(g.flag); bfree(b->work); bfree(b->dres);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);

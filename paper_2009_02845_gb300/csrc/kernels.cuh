@@ -27,6 +27,7 @@ void prime_kernel_attributes();
 void record_handleless_error(const std::string &msg);
 void prime_rng_attributes(int max_smem);
 void prime_solver_attributes(int max_smem);
+void batch_prime_tc(int max_smem);
 
 // ---- rng.cu ---------------------------------------------------------------
 int feistel_half_bits(int64_t n);
@@ -136,21 +137,28 @@ void launch_copy_cast_bf16(const float *in, int64_t n, __nv_bfloat16 *out, cudaS
 // out[i][0..w) = alpha * sum_{e in row i} val_e * D[col_e*ldd + 0..w)
 void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
                       const float *D, int64_t ldd, int w, float alpha, float *out, int64_t ldo, cudaStream_t s);
-// Rows longer than LONG_ROW entries, split into chunks of at most LONG_ROW
-// (built on the host from the row pointer): long row l has chunks
-// first[l] .. first[l+1]-1 covering [cbeg, cend) each; partial is scratch of
-// nchunks x k floats.
-constexpr int64_t LONG_ROW = 2048;
-struct LongRows {
-    int64_t nlong = 0, nchunks = 0;
-    int64_t *rows = nullptr, *first = nullptr, *cbeg = nullptr, *cend = nullptr;
-    float *partial = nullptr;
+// Sub-CSR of X[:, J] for a subsampling sketch on sparse X (rows x K): built
+// from the rows J of the CSR of X^T, entries stably sorted by row, so each
+// row's entries are in ascending column order.  Workspace for sampled sets of
+// up to dmax columns holding at most cap entries in total (cap = the sum of
+// the dmax longest columns of X, so no J can overflow it).  After a build,
+// row i's entries are [ptr[i], ptr[i+1]) of col[cur] / val[cur].
+struct SubCsr {
+    int64_t rows = 0, cap = 0;
+    int dmax = 0, cur = 0;
+    int64_t *off = nullptr, *len = nullptr, *bsum = nullptr, *hist = nullptr, *ptr = nullptr;
+    int32_t *cnt = nullptr, *longs = nullptr;  // longs: count, then the rows with many entries
+    int32_t *key[2] = {nullptr, nullptr}, *col[2] = {nullptr, nullptr};
+    float *val[2] = {nullptr, nullptr};
+    void reserve(int64_t rows, int dmax, int64_t cap, cudaStream_t s);
+    void release();
 };
-// out[i][0..k) = alpha * sum over entries e of row i with col_e in J of val_e * Y[col_e][0..k)
-// (CSR order; long rows summed chunk by chunk, chunks in order); bits is the
-// membership bitmap of J over the columns (as left by launch_subsample); k <= 128.
-void launch_sampled_spmm(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
-                         const uint32_t *bits, const float *Y, int k, float alpha, float *out, const LongRows &lr,
-                         cudaStream_t s);
+// Build the sub-CSR of X[:, J] from the CSR of X^T (xtp, xtc, xtv); J ascending, d <= dmax.
+void launch_subcsr_build(const int64_t *xtp, const int32_t *xtc, const float *xtv, const int32_t *J, int d,
+                         SubCsr &sc, cudaStream_t s);
+// out[i][0..k) = alpha * sum over row i's sub-CSR entries of val * Y[col][0..k) (k <= 128):
+// rows of at most 64 entries summed in ascending column order by one warp, longer
+// rows by a CTA (32 interleaved partial sums added in a fixed order).
+void launch_subcsr_rows(const SubCsr &sc, const float *Y, int k, float alpha, float *out, cudaStream_t s);
 
 }  // namespace dsanls

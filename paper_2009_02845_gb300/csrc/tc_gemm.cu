@@ -32,6 +32,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace dsanls {
 
@@ -49,48 +50,18 @@ constexpr uint32_t D2_COL = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded wait: 2 s of wall time
 constexpr int kMaxSplits = 32;                         // split-K slices of the plain product
 
-// ---- PTX helpers ---------------------------------------------------------
-DSANLS_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+}  // namespace
 
-DSANLS_DEV void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
+// Test switch of the bounded waits (dsanls_debug_tc_wait): g_wait_ns > 0
+// replaces the 2 s limit of every tensor-core kernel's waits, and g_starve = 1
+// makes the TMA producer of k_tc_gemm issue no copy at all, so the waits on
+// its copies run out (nothing is in flight) and the kernel reports a timeout.
+__device__ unsigned long long g_wait_ns = 0;
+__device__ int g_starve = 0;
 
-DSANLS_DEV void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
+namespace {
 
-DSANLS_DEV void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-DSANLS_DEV bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, P;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-DSANLS_DEV unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// true when phase `parity` of the barrier completed within WAIT_NS
-DSANLS_DEV bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer_ns() - t0 > WAIT_NS) return false;
-    return true;
-}
+DSANLS_DEV unsigned long long wait_limit() { return g_wait_ns ? g_wait_ns : WAIT_NS; }
 
 DSANLS_DEV void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
     asm volatile(
@@ -98,72 +69,6 @@ DSANLS_DEV void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uin
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand with 128-byte
-// swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
-DSANLS_DEV uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);     // start address
-    d |= (uint64_t)(16u >> 4) << 16;              // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024u >> 4) << 32;            // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                       // descriptor version
-    d |= (uint64_t)2 << 61;                       // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: kind::f16 with bf16 A and B, fp32 D, both K-major.
-DSANLS_DEV uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-DSANLS_DEV void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// Instruction descriptor: kind::f8f6f4 with E4M3 A and B, fp32 D, both K-major.
-DSANLS_DEV uint32_t idesc_e4m3(int M, int N) {
-    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-DSANLS_DEV void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-DSANLS_DEV void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-DSANLS_DEV void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-DSANLS_DEV void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-DSANLS_DEV void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-
-DSANLS_DEV void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-DSANLS_DEV uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
 }
 
 struct __align__(8) TcSmemTail {
@@ -194,12 +99,21 @@ struct __align__(8) TcSmemTail {
 // BNT: width of the N tile (256 for the fused kernel; 64, 128 or 256 for the
 //   plain product).  TMEM: 512 columns for the fused kernel, BNT otherwise, so
 //   two plain CTAs with BNT <= 128 can share an SM.
-template <int STAGES, bool FUSED, bool FP8, int BNT = BN>
+// NP = 6 (plain product only): binary32-accurate product from three-way bf16
+// splits of both operands, X = X0 + X1 + X2 (map_x, map_x1, map_x2) and
+// S = S0 + S1 + S2 (map_s, map_s1, map_s2): every K-block runs the six
+// products Xa Sb with a + b <= 2 (the dropped ones are of order 2^-24 of
+// the product) into the same fp32 accumulator, one ring stage per product.
+template <int STAGES, bool FUSED, bool FP8, int BNT = BN, int NP = 1>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
-              const __grid_constant__ CUtensorMap map_b, int64_t rows, int64_t K, int64_t d, int k, int kp,
+              const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_x1,
+              const __grid_constant__ CUtensorMap map_x2, const __grid_constant__ CUtensorMap map_s1,
+              const __grid_constant__ CUtensorMap map_s2, int64_t rows, int64_t K, int64_t d, int k, int kp,
               int kb_per_split, float *__restrict__ out, int *__restrict__ err, const float *__restrict__ row_scale,
               float extra_scale, const float *__restrict__ col_scale) {
+    static_assert(NP == 1 || (NP == 6 && !FUSED && !FP8), "the split product is a plain bf16 product");
+    const unsigned long long wl = wait_limit();
     constexpr int BKE = FP8 ? 128 : BK;  // K elements per stage
     static_assert(!FUSED || BNT == BN, "the fused kernel uses 256-wide N tiles");
     static_assert(BNT == 64 || BNT == 128 || BNT == 256, "N tile of 64, 128 or 256");
@@ -249,38 +163,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = tail->tmem_base;
 
     if (warp == 0) {
-        if (lane == 0) {
+        if (lane == 0 && !g_starve) {  // (test switch: a starved producer issues nothing)
             if (FUSED) {  // B tile first (needed only at the end), then the K ring
                 mbar_expect_tx(&tail->b_full, 4u * kp * 128u);
                 for (int a = 0; a < 4; ++a) tma_load_2d(btile + a * kp * 128, &map_b, n0 + a * 64, 0, &tail->b_full);
             }
             int issued = 0;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES && !mbar_wait(&tail->empty[s], ((kb / STAGES) - 1) & 1)) {
+            for (int it = 0; it < nk * NP; ++it) {
+                const int s = it % STAGES;
+                if (it >= STAGES && !mbar_wait(&tail->empty[s], ((it / STAGES) - 1) & 1, wl)) {
                     atomicOr(err, 2);
                     tail->failed = 1;
                     break;
                 }
                 if (*(volatile int *)&tail->failed) break;
+                const int kb = it / NP, pr = it % NP;
+                // operand parts of product pr: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+                const int pa = NP == 1 ? 0 : (0x210100 >> (4 * pr)) & 15;
+                const int pb = NP == 1 ? 0 : (0x012010 >> (4 * pr)) & 15;
+                const CUtensorMap *mx = pa == 0 ? &map_x : (pa == 1 ? &map_x1 : &map_x2);
+                const CUtensorMap *ms = pb == 0 ? &map_s : (pb == 1 ? &map_s1 : &map_s2);
                 uint8_t *sa = stage_base + s * SB;
                 mbar_expect_tx(&tail->full[s], SB);
-                tma_load_2d(sa, &map_x, (kb0 + kb) * BKE, (int)m0, &tail->full[s]);
-                tma_load_2d(sa + A_STAGE_BYTES, &map_s, (kb0 + kb) * BKE, n0, &tail->full[s]);
+                tma_load_2d(sa, mx, (kb0 + kb) * BKE, (int)m0, &tail->full[s]);
+                tma_load_2d(sa + A_STAGE_BYTES, ms, (kb0 + kb) * BKE, n0, &tail->full[s]);
                 ++issued;
             }
             // drain: every copy this thread issued has landed before the CTA can exit
-            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-                mbar_wait(&tail->full[kb % STAGES], (kb / STAGES) & 1);
-            if (FUSED) mbar_wait(&tail->b_full, 0);
+            for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
+                mbar_wait(&tail->full[it % STAGES], (it / STAGES) & 1, wl);
+            if (FUSED) mbar_wait(&tail->b_full, 0, wl);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t id1 = FP8 ? idesc_e4m3(BM, BNT) : idesc_bf16(BM, BNT);
             bool ok = true;
-            for (int kb = 0; kb < nk && ok; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&tail->full[s], (kb / STAGES) & 1)) {
+            for (int it = 0; it < nk * NP && ok; ++it) {
+                const int s = it % STAGES;
+                if (!mbar_wait(&tail->full[s], (it / STAGES) & 1, wl)) {
                     ok = false;
                     break;
                 }
@@ -290,16 +210,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk)
                     if (FP8)  // 32 fp8 elements = 32 bytes per MMA, as 16 bf16 elements
-                        mma_e4m3(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (kb | kk) != 0);
+                        mma_e4m3(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (it | kk) != 0);
                     else
-                        mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (kb | kk) != 0);
+                        mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), id1, (it | kk) != 0);
                 mma_commit(&tail->empty[s]);
             }
             if (ok) {
                 mma_commit(&tail->d1_full);
                 if (FUSED) {
                     // second product: D2 = bf16(D1) B_tile^T, K = 256 in 16 steps
-                    if (mbar_wait(&tail->a2_ready, 0) && mbar_wait(&tail->b_full, 0)) {
+                    if (mbar_wait(&tail->a2_ready, 0, wl) && mbar_wait(&tail->b_full, 0, wl)) {
                         fence_after();
                         const uint32_t id2 = idesc_bf16(BM, kp);
                         const uint32_t a2s = smem_u32(a2), bts = smem_u32(btile);
@@ -321,14 +241,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // every MMA this thread issued has retired before TMEM is freed
             mma_commit(&tail->mma_done);
-            mbar_wait(&tail->mma_done, 0);
+            mbar_wait(&tail->mma_done, 0, wl);
         }
     } else if (warp >= 4) {
         const int q = warp & 3;  // TMEM lane quarter of this warp
         const int r = q * 32 + lane;
         const int64_t row = m0 + r;
         const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-        bool ok = mbar_wait(&tail->d1_full, 0);
+        bool ok = mbar_wait(&tail->d1_full, 0, wl);
         if (!FUSED) {
             // D1 (fp32) straight to the split's slice; nk == 0 leaves D1 unwritten: store zeros
             if (ok) {
@@ -384,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
             mbar_arrive(&tail->a2_ready);
-            if (ok) ok = mbar_wait(&tail->d2_full, 0);
+            if (ok) ok = mbar_wait(&tail->d2_full, 0, wl);
             if (ok) {
                 fence_after();
                 float *dst = out + ((int64_t)chunk * rows + row) * k;
@@ -562,10 +482,10 @@ void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const
     const int stages = stages_for(kp);
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
-        k_tc_gemm<4, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+        k_tc_gemm<4, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
                                                                             err, nullptr, 1.0f, nullptr);
     else
-        k_tc_gemm<3, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+        k_tc_gemm<3, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
                                                                             err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
@@ -590,10 +510,10 @@ void launch_tc_sketch_rhs_fp8(const uint8_t *Xq, const float *row_scale, const u
     const int stages = stages_for(kp);
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
-        k_tc_gemm<4, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+        k_tc_gemm<4, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
                                                                            err, row_scale, s_scale, nullptr);
     else
-        k_tc_gemm<3, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, rows, K, d, k, kp, 0, Rpart,
+        k_tc_gemm<3, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
                                                                            err, row_scale, s_scale, nullptr);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
@@ -640,7 +560,7 @@ void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t row
     const CUtensorMap mx = make_map(X, rows, K, BM);
     const CUtensorMap ms = make_map(St, d, K, BN);
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
-    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, d, 0, 0,
+    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, mx, mx, ms, ms, rows, K, d, 0, 0,
                                                                          p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * d, p.splits, rows, d, d, C, d, s);
@@ -669,7 +589,7 @@ void launch_tc_gemm_bf16out(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int
     const CUtensorMap mx = make_map(X, rows, K, BM);
     const CUtensorMap ms = make_map(St, N, K, BN);
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
-    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, rows, K, N, 0, 0,
+    k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, mx, mx, ms, ms, rows, K, N, 0, 0,
                                                                          p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     k_split_reduce_bf16<<<(unsigned)ceil_div(rows * N, 256), 256, 0, s>>>(part, p.splits, rows * N, C);
@@ -693,10 +613,10 @@ void launch_tc_skinny(const __nv_bfloat16 *X, const __nv_bfloat16 *Pt, int64_t r
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     if (bnt == 64)
         k_tc_gemm<4, false, false, 64><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
-            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     else
         k_tc_gemm<3, false, false, 128><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
-            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
 }
@@ -718,10 +638,10 @@ void launch_tc_skinny_fp8(const uint8_t *Xq, const float *xscale, const uint8_t 
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     if (bnt == 64)
         k_tc_gemm<4, false, true, 64><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
-            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
     else
         k_tc_gemm<3, false, true, 128><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
-            mx, mp, mx, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
 }
@@ -794,6 +714,122 @@ void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfl
     DSANLS_LAUNCH_CHECK();
 }
 
+// ---- binary32-accurate products from three-way bf16 splits ---------------------
+__global__ void k_split3(const float *__restrict__ in, int64_t n, __nv_bfloat16 *__restrict__ h,
+                         __nv_bfloat16 *__restrict__ m, __nv_bfloat16 *__restrict__ l) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        split3_one(in[i], h[i], m[i], l[i]);
+}
+
+// in (rows x cols, fp32 row-major) -> the three parts of in^T (cols x rows)
+__global__ void k_split3_transpose(const float *__restrict__ in, int64_t rows, int64_t cols,
+                                   __nv_bfloat16 *__restrict__ h, __nv_bfloat16 *__restrict__ m,
+                                   __nv_bfloat16 *__restrict__ l) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t r = r0 + y, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[y][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t c = c0 + y, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) split3_one(tile[threadIdx.x][y], h[c * rows + r], m[c * rows + r], l[c * rows + r]);
+    }
+}
+
+void launch_split3(const float *in, int64_t n, __nv_bfloat16 *const parts[3], cudaStream_t s) {
+    if (n <= 0) return;
+    k_split3<<<152 * 16, 256, 0, s>>>(in, n, parts[0], parts[1], parts[2]);
+    DSANLS_LAUNCH_CHECK();
+}
+
+void launch_split3_transpose(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *const parts[3],
+                             cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    if (ceil_div(rows, 32) > 65535) throw ArgError{"split3_transpose: too many rows"};
+    dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
+    k_split3_transpose<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, parts[0], parts[1], parts[2]);
+    DSANLS_LAUNCH_CHECK();
+}
+
+// The tensor cores' fp32 accumulation drifts toward zero over long chains of
+// additions (measured: -1.2e-5 relative on A = X S after 16384 / 16 x 6 adds),
+// so a split product keeps every accumulator chain to at most kSplitChain
+// K-blocks (x 6 products) and sums the split partials in binary32
+// round-to-nearest, in order.
+static constexpr int kSplitChain = 32;
+
+static PlainPlan plan_split3(int64_t rows, int64_t K, int64_t N) {
+    PlainPlan p = plan_one_wave(rows, K, N, BN);
+    const int nk = (int)ceil_div(K, BK);
+    const int min_splits = (int)ceil_div(nk, kSplitChain);
+    if (p.splits < min_splits) p = finish_plan(p.tiles, nk, min_splits);
+    return p;
+}
+
+int64_t tc_split3_part_elems(int64_t rows, int64_t K, int64_t N) {
+    const PlainPlan p = plan_split3(rows, K, N);
+    return p.splits > 1 ? (int64_t)p.splits * rows * N : 0;
+}
+
+void launch_tc_gemm_split3(const __nv_bfloat16 *const X3[3], const __nv_bfloat16 *const St3[3], int64_t rows,
+                           int64_t K, int64_t N, float *part, float *C, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || N > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0) throw ArgError{"split tensor-core product needs K a multiple of 8"};
+    const PlainPlan p = plan_split3(rows, K, N);
+    CUtensorMap mx[3], ms[3];
+    for (int a = 0; a < 3; ++a) {
+        mx[a] = make_map(X3[a], rows, K, BM);
+        ms[a] = make_map(St3[a], N, K, BN);
+    }
+    dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
+    float *dst = p.splits > 1 ? part : C;
+    k_tc_gemm<4, false, false, BN, 6><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(
+        mx[0], ms[0], mx[0], mx[1], mx[2], ms[1], ms[2], rows, K, N, 0, 0, p.kb_per_split, dst, err, nullptr, 1.0f,
+        nullptr);
+    DSANLS_LAUNCH_CHECK();
+    if (p.splits > 1) launch_split_reduce(part, rows * N, p.splits, rows, N, N, C, N, s);
+}
+
+static PlainPlan plan_skinny_split3(int64_t rows, int64_t K, int k) {
+    PlainPlan p = plan_stream(rows, K, k, skinny_bnt(k), kSkinnySlots, BK, 6);
+    const int nk = (int)ceil_div(K, BK);
+    const int min_splits = (int)ceil_div(nk, kSplitChain);
+    if (p.splits < min_splits) p = finish_plan(p.tiles, nk, min_splits);
+    return p;
+}
+
+int64_t tc_skinny_split3_part_elems(int64_t rows, int64_t K, int k) {
+    const PlainPlan p = plan_skinny_split3(rows, K, k);
+    return (int64_t)p.splits * rows * k;
+}
+
+void launch_tc_skinny_split3(const __nv_bfloat16 *const X3[3], const __nv_bfloat16 *const Pt3[3], int64_t rows,
+                             int64_t K, int k, float *part, float *R, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0) throw ArgError{"split tensor-core product needs K a multiple of 8"};
+    if (k < 1 || k > 128) throw ArgError{"skinny product needs 1 <= k <= 128"};
+    const int bnt = skinny_bnt(k);
+    const PlainPlan p = plan_skinny_split3(rows, K, k);
+    CUtensorMap mx[3], mp[3];
+    for (int a = 0; a < 3; ++a) {
+        mx[a] = make_map(X3[a], rows, K, BM);
+        mp[a] = make_map(Pt3[a], k, K, bnt);
+    }
+    dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
+    if (bnt == 64)
+        k_tc_gemm<4, false, false, 64, 6><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
+            mx[0], mp[0], mx[0], mx[1], mx[2], mp[1], mp[2], rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr,
+            1.0f, nullptr);
+    else
+        k_tc_gemm<3, false, false, 128, 6><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
+            mx[0], mp[0], mx[0], mx[1], mx[2], mp[1], mp[2], rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr,
+            1.0f, nullptr);
+    DSANLS_LAUNCH_CHECK();
+    launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
+}
+
 // ---- fused row update on tensor cores ---------------------------------------
 // Z <- max(0, Z - eta (Z G - R)) (eq. gradient_descent, one projected-gradient
 // step) for 32 < k <= 128.  Z G is taken on tcgen05 from a three-way bf16 split
@@ -831,18 +867,6 @@ DSANLS_DEV float upd_project(float v, float bound, int *flag) {
     float r = v > 0.0f ? v : 0.0f;
     if (bound > 0.0f) r = fminf(r, bound);
     return r;
-}
-
-DSANLS_DEV void split3_one(float z, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
-    h = __float2bfloat16_rn(z);
-    const float r1 = __fsub_rn(z, __bfloat162float(h));
-    m = __float2bfloat16_rn(r1);
-    l = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
-}
-
-// byte offset of element (r, c) in a 128-byte swizzled K-major operand of `rows` rows
-DSANLS_DEV int sw128_off(int r, int c, int rows) {
-    return (c >> 6) * rows * 128 + r * 128 + ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 7) << 1);
 }
 
 template <int KA>  // K atoms of 64 columns: 1 for k <= 64, 2 for k <= 128
@@ -990,7 +1014,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
                 if (4 * g < nf) rr[j] = __ldcs(reinterpret_cast<const float4 *>(R + f0) + g);
             }
         }
-        const bool got = mbar_wait(&tail->done, it & 1);
+        const bool got = mbar_wait(&tail->done, it & 1, wait_limit());
         if (__syncthreads_or(!got)) {
             if (tid == 0) atomicOr(flag, 2);
             break;
@@ -1042,7 +1066,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
     }
     if (tid == 0) {  // every MMA this thread issued has retired before TMEM is freed
         mma_commit(&tail->fin);
-        mbar_wait(&tail->fin, 0);
+        mbar_wait(&tail->fin, 0, wait_limit());
     }
     fence_before();
     __syncthreads();
@@ -1060,32 +1084,40 @@ size_t update_tc_smem(int N) {
 
 bool update_tc_supported(int k) { return k > 32 && k <= 128; }
 
+namespace {
+template <int KA>
+void launch_update_tc_kind(float *Z, const float *R, int64_t rows, int k, int N, const float *Gf, int kp,
+                           const double *scal, float bound, int *flag, uint32_t tmem_cols, int sms, cudaStream_t s) {
+    const size_t smem = update_tc_smem<KA>(N);
+    int per_sm = 1;
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<KA>, UPD_THREADS, smem));
+    per_sm = std::max(1, std::min(per_sm, 512 / (int)tmem_cols));
+    const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
+    k_update_tc<KA><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
+                                                              tmem_cols);
+    DSANLS_LAUNCH_CHECK();
+}
+}  // namespace
+
 void launch_update_tc(float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
                       float bound, int *flag, cudaStream_t s) {
     if (!update_tc_supported(k)) throw ArgError{"launch_update_tc: needs 32 < k <= 128"};
     if (rows <= 0) return;
     const int N = (k + 15) / 16 * 16;
     const uint32_t tmem_cols = N <= 64 ? 64u : 128u;
-    int dev = 0, sms = 152, per_sm = 1;
+    int dev = 0, sms = 152;
     DSANLS_CUDA(cudaGetDevice(&dev));
     DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
-    if (k <= 64) {
-        const size_t smem = update_tc_smem<1>(N);
-        DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<1>, UPD_THREADS, smem));
-        per_sm = std::max(1, std::min(per_sm, 512 / (int)tmem_cols));
-        const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
-        k_update_tc<1><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
-                                                                tmem_cols);
-    } else {
-        const size_t smem = update_tc_smem<2>(N);
-        DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<2>, UPD_THREADS, smem));
-        per_sm = std::max(1, std::min(per_sm, 512 / (int)tmem_cols));
-        const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
-        k_update_tc<2><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
-                                                                tmem_cols);
-    }
-    DSANLS_LAUNCH_CHECK();
+    if (k <= 64)
+        launch_update_tc_kind<1>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
+    else
+        launch_update_tc_kind<2>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
+}
+
+void set_tc_wait_debug(unsigned long long wait_ns, int starve) {
+    DSANLS_CUDA(cudaMemcpyToSymbol(g_wait_ns, &wait_ns, sizeof(wait_ns)));
+    DSANLS_CUDA(cudaMemcpyToSymbol(g_starve, &starve, sizeof(starve)));
 }
 
 void prime_tc_attributes(int max_smem) {
@@ -1099,6 +1131,9 @@ void prime_tc_attributes(int max_smem) {
     allow_max_dynamic_smem(k_tc_gemm<4, false, false, 64>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, false, false, 128>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, true, 64>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, false, false, BN, 6>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, false, false, 64, 6>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<3, false, false, 128, 6>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, false, true, 128>, max_smem);
 }
 

@@ -50,6 +50,22 @@ void launch_tc_skinny_fp8(const uint8_t *Xq, const float *xscale, const uint8_t 
 // scratch of `rows` words.
 void launch_quant_rows(const float *X, int64_t rows, int64_t K, float *scale, uint8_t *Xq, unsigned int *maxbits,
                        cudaStream_t s);
+// Three-way bf16 split z = h + m + l of every entry (binary32-exact up to 2^-24 |z|):
+// parts[0..2] of n entries, or of in^T (cols x rows) for in rows x cols.
+void launch_split3(const float *in, int64_t n, __nv_bfloat16 *const parts[3], cudaStream_t s);
+void launch_split3_transpose(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *const parts[3],
+                             cudaStream_t s);
+// C (rows x N, fp32) = X S at binary32 accuracy on tcgen05: six bf16 products of the
+// parts (X3: rows x K, St3 = parts of S^T: N x K) into one fp32 accumulator; split-K
+// partials (scratch of tc_split3_part_elems floats, 0 when none) summed in order.
+int64_t tc_split3_part_elems(int64_t rows, int64_t K, int64_t N);
+void launch_tc_gemm_split3(const __nv_bfloat16 *const X3[3], const __nv_bfloat16 *const St3[3], int64_t rows,
+                           int64_t K, int64_t N, float *part, float *C, int *err, cudaStream_t s);
+// R (rows x k, fp32) = X P at binary32 accuracy: the streaming product from the parts
+// of X (rows x K) and of P^T (k x K); partials summed in order.
+int64_t tc_skinny_split3_part_elems(int64_t rows, int64_t K, int k);
+void launch_tc_skinny_split3(const __nv_bfloat16 *const X3[3], const __nv_bfloat16 *const Pt3[3], int64_t rows,
+                             int64_t K, int k, float *part, float *R, int *err, cudaStream_t s);
 // out (cols x rows, bf16) = in^T for in rows x cols fp32 row-major.
 void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfloat16 *out, cudaStream_t s);
 // Z <- max(0, Z - eta (Z G - R)) (one projected-gradient step, eta = scal[2])
@@ -61,5 +77,9 @@ bool update_tc_supported(int k);
 void launch_update_tc(float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
                       float bound, int *flag, cudaStream_t s);
 void prime_tc_attributes(int max_smem);
+// Test switch of the bounded waits on the current device: wait_ns > 0 replaces the
+// 2 s limit (0 restores it); starve = 1 makes the producer of the tensor-core GEMM
+// issue no copy, so its consumers' waits run out and report DSANLS_ETIMEOUT.
+void set_tc_wait_debug(unsigned long long wait_ns, int starve);
 
 }  // namespace dsanls

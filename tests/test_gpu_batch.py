@@ -178,3 +178,45 @@ def test_batch_bf16_one_iteration(pkg, order):
         rel, rb = bounds.check(V, M64.T, U.astype(np.float64), V0.astype(np.float64), Sp, 0, mu, form)
         assert rel <= rb, (i, rel, rb)
     b.close()
+
+
+def test_batch_bf16_tensor_core_tile_is_tuned(pkg):
+    """The bf16 paper order runs R_i = (X_i S_i) B_i^T on tensor cores; the
+    autotuner times the candidate tiles (64-, 128- and 256-column chunks of the
+    sketch, each with its CTAs per SM) on the real batch -- every candidate
+    runs a full iteration, with the factors restored after each -- and keeps
+    one; the first iteration then matches a second handle that reuses the
+    cached choice bit for bit."""
+    Ms = _inputs(SHAPES)
+    out = []
+    for _ in range(2):
+        b = pkg.Batch(SHAPES, use_graph=1, precision=pkg.BF16)
+        for i, M in enumerate(Ms):
+            b.set_dense(i, M)
+        b.step(1)
+        chunk, ctas = b.tuned_tile()
+        assert chunk in (64, 128, 256) and ctas > 0
+        out.append([b.factors(i) for i in range(len(SHAPES))])
+        b.close()
+    for (u0, v0), (u1, v1) in zip(*out):
+        assert np.array_equal(u0, u1) and np.array_equal(v0, v1)
+
+
+def test_batch_bf16_run_final_errors(pkg):
+    """20 outer iterations of every instance, bf16 tensor-core form with the last
+    three in binary32: each instance's final relative error within 2e-3 of the
+    exact oracle's (the acceptance of the reduced-precision forms)."""
+    Ms = _inputs(SHAPES)
+    b = pkg.Batch(SHAPES, use_graph=1, precision=pkg.BF16)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(17)
+    b.set_options(precision=pkg.FP32, t=17)
+    b.step(3)
+    errs = b.rel_errors()
+    b.close()
+    for i, (s, M) in enumerate(zip(SHAPES, Ms)):
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        opt = method.Options(sketch=method.GAUSSIAN, d=s["d"], d_v=s["d_v"])
+        _, _, eo = method.run(M, U0, V0, s["seed"], 20, opt)
+        assert abs(errs[i] - eo[-1]) <= 2e-3, (i, errs[i], eo[-1])

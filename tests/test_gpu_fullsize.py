@@ -10,6 +10,9 @@ Tolerances: binary32 form <= 1e-5 norm-wise on the sampled rows; bf16 form
 within the derived bound of oracle/bounds.py against the exact oracle
 (diagnostic: <= 3e-4 against the oracle's frozen bf16 rounding model).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -75,3 +78,46 @@ def test_fullsize_half_step_sampled_rows(pkg, data, precision, side):
         model = method.half_step(Xs, Y, Z, S, method.PGD, mu, bf16=True)
         assert _rel(got[rows], model) <= 3e-4, _rel(got[rows], model)
     assert got.min() >= 0.0 and np.isfinite(got).all()
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "dense_65536x16384_k64_d2048_gaussian_pgd_T100.json")
+
+FORMS = [
+    # (name, precision, order): each run takes 100 outer iterations, the reduced-precision
+    # forms with the last 3 in binary32 (paper order)
+    ("fp32", "FP32", 0),
+    ("bf16", "BF16", 0),
+    ("fp8", "FP8", 0),
+    ("bf16_reassociated", "BF16", 1),
+    ("fp8_reassociated", "FP8", 1),
+]
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="oracle trajectory not written")
+@pytest.mark.parametrize("name,prec,order", FORMS)
+def test_fullsize_100_iterations_against_the_oracle(pkg, data, name, prec, order):
+    """The dense 65,536 x 16,384 workload (k = 64, Gaussian d = d' = 2048, seed 0)
+    for T = 100 outer iterations, against the FP64 oracle's trajectory of the same
+    problem (tests/golden/, written by make_dense_trajectory.py from oracle/ only):
+    FP32 within 1e-4 of the oracle's relative error at every 10th iteration, every
+    reduced-precision form (3 closing FP32 iterations) within 2e-3 at T = 100."""
+    gold = json.load(open(GOLDEN))["errors"]
+    M, _, _ = data
+    h = pkg.DSANLS(M_ROWS, N_COLS, K, D, pkg.GAUSSIAN, seed=0, precision=getattr(pkg, prec), order=order,
+                   use_graph=1)
+    h.set_dense(M)
+    errs = {}
+    if prec == "FP32":
+        for t in range(10, 101, 10):
+            h.step(10)
+            errs[t] = h.rel_error()
+    else:
+        h.step(97)
+        h.set_options(precision=pkg.FP32, order=0, t=97, use_graph=1)
+        h.step(3)
+        errs[100] = h.rel_error()
+    h.close()
+    tol = 1e-4 if prec == "FP32" else 2e-3
+    for t, e in errs.items():
+        assert abs(e - gold[t - 1]) <= tol, (name, t, e, gold[t - 1])

@@ -135,9 +135,18 @@ def test_learned_half_step_matches_oracle(pkg, plain_iters):
     net.close()
 
 
-def test_training_lowers_loss_and_trained_network_gains(pkg):
+def test_training_lowers_loss_and_what_the_network_adds(pkg):
     """Harvest triples from planted training problems (seeds 1-4), train on the
-    GPU, and compare the learned form with the plain method on seed 21."""
+    GPU (the loss must fall), then run seed 21 for 15 outer iterations with:
+    the plain single step; the plain form with 4 projected-gradient steps per
+    half (the correction alone); the learned form with the trained network
+    and 4 correction steps; and the same learned form with all weights zero
+    (x0 = 0: the correction restarted from zero).  The learned forms keep the
+    plain step whenever its proximal objective is lower, so neither may end
+    worse than the plain single step.  Whether the trained network beats the
+    zero-weight network is measured and reported, not assumed: on these
+    well-conditioned planted problems it does not (the correction steps and
+    the restart away from the current row carry the gain)."""
     import torch
     m, n, k, d, hidden = 1024, 512, 16, 128, 128
     net = pkg.MLP(k, hidden, max_rows=4096, max_groups=64, seed=1)
@@ -163,14 +172,19 @@ def test_training_lowers_loss_and_trained_network_gains(pkg):
         x = torch.cat([xs[i][:r] for i, r in zip(pick, rows)])
         losses.append(net.train_step(G, mu, off, b, x, 3e-3))
     assert np.mean(losses[-20:]) < 0.7 * np.mean(losses[:20])
+    zero = pkg.MLP(k, hidden, max_rows=4096, max_groups=64, seed=1)
+    zero.set_params(np.zeros_like(zero.params()))
     errs = {}
-    for learned in (False, True):
+    for name, mlp, inner in (("plain", None, 1), ("plain_4_steps", None, 4), ("trained", net, 1),
+                             ("zero_weights", zero, 1)):
         h, _ = _handle(pkg, m, n, k, d, 21)
-        if learned:
-            h.set_mlp(net, pg_iters=4)
-        h.set_options(t=0)
+        h.set_options(t=0, inner_iters=inner)
+        if mlp is not None:
+            h.set_mlp(mlp, pg_iters=4)
         h.step(15)
-        errs[learned] = h.rel_error()
+        errs[name] = h.rel_error()
         h.close()
-    assert errs[True] < errs[False], errs
+    print("learned form after 15 iterations:", errs)
+    assert errs["trained"] <= errs["plain"] and errs["zero_weights"] <= errs["plain"], errs
     net.close()
+    zero.close()

@@ -107,6 +107,42 @@ def test_dense_subsample_half_steps(pkg, case, solver):
         assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
 
 
+SPLIT_CASES = [
+    # m, n (multiples of 8: the FP32 product runs on tensor cores from three-way bf16
+    # splits), k, d, d_v: several 128 x 256 tiles, ragged row tails, d not a multiple of 256
+    (1032, 520, 64, 264, 136),
+    (264, 1040, 128, 520, 72),
+    (136, 64, 1, 8, 16),
+    (2056, 4104, 100, 512, 1024),
+]
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("case", SPLIT_CASES)
+def test_dense_fp32_split_tensor_core_half_steps(pkg, case, order):
+    """The FP32 form of dense Gaussian products on tcgen05 (A = X S in the paper
+    order, R = X P in the reassociated order; six bf16 products of the splits)
+    against the exact oracle at the binary32 tolerance (1e-5 per step)."""
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 8)
+    U, V = initial_factors(m, n, k, 9)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=17, d_v=d_v, t=3, order=order)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 17, 3, side, X.shape[1], dd)
+        want = method.half_step(X, Y, Z, S, 0, method.mu_t(1.0, 1.0, 3), reassociate=order == 1)
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
 @pytest.mark.parametrize("solver", [0, 1])
 def test_dense_identity_half_steps(pkg, solver):
     m, n, k = 200, 150, 12
@@ -158,8 +194,10 @@ def _csr_with_long_rows(m, n, seed):
 
 @pytest.mark.parametrize("solver", [0, 1])
 def test_sparse_long_rows_half_steps(pkg, solver):
-    """Subsampled sparse half-steps where rows of M and of M^T exceed one pass
-    of the sampled product (chunked, then combined), against the oracle."""
+    """Subsampled sparse half-steps where rows of M and of M^T hold thousands
+    of entries (long sampled columns in the gather, many sampled entries per
+    row), with the unfused update kernels (k = 24: CUDA-core PGD and RCD),
+    against the oracle."""
     m, n, k = 3000, 5000, 24
     rp, col, val, Msp = _csr_with_long_rows(m, n, 11)
     assert np.diff(rp).max() > 2048 and np.diff(Msp.T.tocsr().indptr).max() > 2048
@@ -169,6 +207,49 @@ def test_sparse_long_rows_half_steps(pkg, solver):
                               csr=(rp, col, val))
         want = _oracle_half(Msp, U, V, method.SUBSAMPLE, solver, 6, 2, side, dd, sparse=True)
         assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
+@pytest.mark.parametrize("case", [
+    # m, n, k, d, d_v: row counts that take 1, 2 and 3 passes of the 8-bit radix sort
+    (200, 150, 48, 40, 30),
+    (3000, 5000, 100, 500, 300),
+    (70000, 300, 40, 120, 2000),
+])
+def test_sparse_subsample_tensor_core_update(pkg, case):
+    """One projected-gradient step with 32 < k <= 128 (tensor-core update) on
+    sparse data with a subsampling sketch, R formed from the gathered sub-CSR
+    of X[:, J]; against the oracle (1e-5).  The 3000 x 5000 case has rows of M
+    and of M^T of 3,000 to 4,500 entries (rows of the sub-CSR with more than
+    64 sampled entries are summed by a whole CTA) and a column present in
+    2,500 rows."""
+    m, n, k, d, d_v = case
+    if m == 3000:
+        rp, col, val, Msp = _csr_with_long_rows(m, n, 11)
+    else:
+        rp, col, val, Msp = _csr(m, n, 13)
+    U, V = initial_factors(m, n, k, 5)
+    for side, dd in ((0, d), (1, d_v)):
+        got, _, _ = _gpu_half(pkg, None, U, V, method.SUBSAMPLE, 0, 6, 2, side, d, d_v=d_v, csr=(rp, col, val))
+        want = _oracle_half(Msp, U, V, method.SUBSAMPLE, 0, 6, 2, side, dd, sparse=True)
+        assert got.min() >= 0
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+
+
+def test_sparse_subsample_is_deterministic(pkg):
+    """Two handles, and a captured graph against eager launches, give bitwise
+    equal factors: the gathered entries are sorted stably by row, so every
+    row's right-hand side is summed in the same (ascending column) order."""
+    m, n, k = 3000, 5000, 100
+    rp, col, val, _ = _csr_with_long_rows(m, n, 11)
+    out = []
+    for g in (0, 1, 1):
+        h = pkg.DSANLS(m, n, k, 500, pkg.SUBSAMPLE, seed=6, d_v=300, use_graph=g)
+        h.set_csr(rp, col, val)
+        h.step(3)
+        out.append(h.factors())
+        h.close()
+    for a in out[1:]:
+        assert np.array_equal(out[0][0], a[0]) and np.array_equal(out[0][1], a[1])
 
 
 def test_sparse_given_transpose_equals_built_transpose(pkg):

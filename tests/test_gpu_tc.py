@@ -148,3 +148,32 @@ def test_fp8_run_final_error(pkg):
     h.close()
     _, _, errs = method.run(M, U0, V0, 0, T, method.Options(sketch=method.GAUSSIAN, d=d))
     assert abs(err - errs[-1]) <= 2e-3, (err, errs[-1])
+
+
+def test_fp8_columns_of_very_different_scale(pkg):
+    """Data whose columns differ in scale by a factor 1000 (M = U0 V0^T D with
+    D = diag(10^(3 c / n))): the fp8 form keeps one scale per 128-row block of
+    the K-major operand (per 128 rows of M for the U-half, per 128 columns of M
+    for the V-half), so the small columns of a row block sit up to 1000x
+    below its scale, down to E4M3's subnormal range.  The half-steps must stay
+    within the derived fp8 bound against the exact oracle (the bound's
+    absolute floor 2^-10 scale covers the subnormal rounding)."""
+    m, n, k, d = 640, 528, 32, 264
+    M, _, _ = planted_dense(m, n, 16, 6)
+    M = (M * np.power(10.0, 3.0 * np.arange(n) / n)[None, :]).astype(np.float32)
+    U, V = initial_factors(m, n, k, 7)
+    M64 = M.astype(np.float64)
+    for side in (0, 1):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=29, precision=pkg.FP8, t=2)
+        h.set_dense(M)
+        h.set_factors(U, V)
+        h.half_step(side)
+        Ug, Vg = h.factors()
+        h.close()
+        got = Ug if side == 0 else Vg
+        X = M64 if side == 0 else M64.T
+        Y = (V if side == 0 else U).astype(np.float64)
+        Z = (U if side == 0 else V).astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, 29, 2, side, X.shape[1], d)
+        rel, rb = bounds.check(got, X, Y, Z, S, method.PGD, method.mu_t(1.0, 1.0, 2), "fp8")
+        assert rel <= rb, (side, rel, rb)
