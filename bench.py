@@ -53,7 +53,8 @@ WORKLOADS = {
                                    "(profiling case: M 0.5 GB)"),
     "sparse_text": dict(m=2_000_000, n=500_000, k=100, d=5000, d_v=5000, sketch=1, sparse=True,
                         desc="CSR 2e6 docs x 5e5 terms (lognormal lengths mean 100, Zipf 1.07 ids, "
-                             "log(1+Poisson) values, ~2e8 nnz), k=100, subsampling d=d'=5000, PGD"),
+                             "log(1+Poisson) values, ~2e8 nnz), k=100, subsampling d=d'=5000, PGD "
+                             "(--precision bf16: bf16 factors)"),
     "sparse_text_small": dict(m=200_000, n=50_000, k=100, d=500, d_v=500, sketch=1, sparse=True,
                               desc="CSR 2e5 x 5e4 text-like (~2e7 nnz), k=100, subsampling d=d'=500, PGD"),
     "learned": dict(learned=True, m=65536, n=16384, k=32, d=2048, d_v=2048, sketch=0, eps=0.05, t_max=400,
@@ -364,8 +365,11 @@ def run_ours(args, w):
     if ws > 1:
         dist.init_process_group("nccl")
     prec = {"fp32": pkg.FP32, "bf16": pkg.BF16, "fp8": pkg.FP8}[args.precision]
-    if w.get("sparse") or w["sketch"] == 1 or (w["sketch"] == 2 and prec == pkg.FP8):
-        prec = pkg.FP32  # the tensor-core forms serve dense data with a Gaussian (or, bf16, identity) sketch
+    if (w.get("sparse") and prec != pkg.BF16) or (w["sketch"] == 1 and not w.get("sparse")) or \
+            (w["sketch"] == 2 and prec == pkg.FP8):
+        # the tensor-core forms serve dense data with a dense (or, bf16, identity) sketch;
+        # sparse data runs in FP32 or with bf16 factors (BF16)
+        prec = pkg.FP32
     M = make_inputs(w, rank)
     # all library work and all timing events on one dedicated (non-default) stream
     stream = torch.cuda.Stream()
@@ -460,8 +464,10 @@ def run_ours(args, w):
         bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "sgemm_simt_gather"
         peak_note = "hbm_gbs of %s" % peak_src
     else:
-        # sparse subsampling: the row update reads Z and R and writes Z (12 bytes per entry)
-        bytes_ = [12.0 * m * k, 12.0 * n * k]
+        # sparse subsampling: the row update reads Z and R and writes Z (12 bytes per entry;
+        # 8 with bf16 factors)
+        zb = 8.0 if prec == pkg.BF16 else 12.0
+        bytes_ = [zb * m * k, zb * n * k]
         prod_ms = [p["update"] for p in phases]
         achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
         bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "update"

@@ -122,6 +122,9 @@ struct dsanls_ctx {
 
     // factors
     float *U = nullptr, *V = nullptr;
+    // bf16-factor form (sparse data, subsampling sketch, BF16): the bf16 U16 and
+    // V16 are the factors; U and V are refreshed from them when read
+    __nv_bfloat16 *U16 = nullptr, *V16 = nullptr;
 
     // workspaces (sized by prepare())
     int64_t cfg_key[7] = {-1, -1, -1, -1, -1, -1, -1};
@@ -236,6 +239,18 @@ void invalidate_graph(dsanls_ctx *h) {
 
 int d_v_of(const dsanls_ctx *h) { return h->opt.d_v > 0 ? h->opt.d_v : h->d; }
 
+// BF16 with a subsampling sketch on sparse data: the factors are stored in bf16
+bool bf16_factors(const dsanls_ctx *h) {
+    return h->has_sparse && h->sketch == DSANLS_SKETCH_SUBSAMPLE && h->opt.precision == DSANLS_PREC_BF16;
+}
+
+// binary32 U and V from the bf16 factors (before anything reads U or V)
+void factors_to_f32(dsanls_ctx *h, cudaStream_t s) {
+    if (!h->U16) return;
+    launch_cast_f32(h->U16, h->m * h->k, h->U, s);
+    launch_cast_f32(h->V16, h->n * h->k, h->V, s);
+}
+
 // The FP32 form of a dense-sketch product runs on tensor cores from three-way
 // bf16 splits when the rows of both orientations of M are 16-byte multiples
 // (TMA), else on CUDA cores.
@@ -309,6 +324,18 @@ void prepare(dsanls_ctx *h) {
     dalloc(h->Sq, (gauss && fp8 && !reas) ? std::max(n * h->d, m * dv) : 0);
     dalloc(h->bits, h->sketch == DSANLS_SKETCH_SUBSAMPLE ? ceil_div(std::max(m, n), 32) + 1
                     : (srht ? ceil_div(srht_pad(std::max(m, n)), 32) + 1 : 0));
+    if (bf16_factors(h)) {
+        if (!h->U16) {  // the factors enter the bf16 form rounded to bf16
+            dalloc(h->U16, m * k);
+            dalloc(h->V16, n * k);
+            launch_copy_cast_bf16(h->U, m * k, h->U16, h->stream());
+            launch_copy_cast_bf16(h->V, n * k, h->V16, h->stream());
+        }
+    } else if (h->U16) {  // leaving the bf16 form: the binary32 factors take over
+        factors_to_f32(h, h->stream());
+        dfree(h->U16);
+        dfree(h->V16);
+    }
     if (h->sketch == DSANLS_SKETCH_SUBSAMPLE && h->has_sparse) {
         // U-half: columns of M (rows of M^T), V-half: rows of M; room for the
         // longest possible sampled set of each side
@@ -487,7 +514,11 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         const float c2 = c * c;
         launch_subsample(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, h->J, h->bits, s);
         mark(pe, DSANLS_PHASE_B, s);
-        launch_gather_w(Y, k, h->J, dd, c, h->W, s);
+        const __nv_bfloat16 *Y16 = side == 0 ? h->V16 : h->U16;
+        if (h->U16)
+            launch_gather_w(Y16, k, h->J, dd, c, h->W, s);
+        else
+            launch_gather_w(Y, k, h->J, dd, c, h->W, s);
         mark(pe, DSANLS_PHASE_PRODUCT, s);
         start_gram();
         if (dense) {
@@ -506,7 +537,10 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             const int32_t *ytc = side == 0 ? h->tci : h->ci;
             const float *ytv = side == 0 ? h->tcv : h->cv;
             launch_subcsr_build(ytp, ytc, ytv, h->J, dd, h->sub[side], s);
-            launch_subcsr_rows(h->sub[side], Y, k, c2, h->R, s);
+            if (h->U16)
+                launch_subcsr_rows(h->sub[side], Y16, k, c2, h->R, s);
+            else
+                launch_subcsr_rows(h->sub[side], Y, k, c2, h->R, s);
         }
     } else {  // identity
         mark(pe, DSANLS_PHASE_B, s);
@@ -545,6 +579,8 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         mlp_learned_update(h->mlp->st, Z, h->R, rows, h->G64[side], h->Gf, kp, h->scal[side], h->pg_iters,
                            h->opt.inner_iters, h->kept,
                            h->flag, s);
+    else if (h->U16)  // bf16 factors: one PGD step on tensor cores (checked at set_options)
+        launch_update_tc(side == 0 ? h->U16 : h->V16, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->flag, s);
     else
         launch_update(h->opt.solver, Z, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->opt.inner_iters, h->flag,
                       s);
@@ -753,10 +789,17 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
             (h->has_sparse || !dense_kind(h->sketch) || h->m % 16 || h->n % 16 ||
              h->d % 8 || (opt->d_v > 0 ? opt->d_v : h->d) % 8))
             throw ArgError{"FP8 precision needs dense data, a Gaussian sketch, m and n multiples of 16, d and d_v of 8"};
-        if (opt->precision == DSANLS_PREC_BF16 &&
-            (h->has_sparse || h->sketch == DSANLS_SKETCH_SUBSAMPLE || !tc_supported(h->k)))
-            throw ArgError{"BF16 precision needs dense data and a Gaussian or identity sketch"};
-        if (opt->precision == DSANLS_PREC_BF16) {
+        if (opt->precision == DSANLS_PREC_BF16 && h->sketch == DSANLS_SKETCH_SUBSAMPLE) {
+            // the bf16-factor form of sparse data
+            if (h->has_dense) throw ArgError{"BF16 with a subsampling sketch is the bf16-factor form of sparse data"};
+            if (opt->solver != DSANLS_SOLVER_PGD || opt->inner_iters != 1 || !update_tc_supported(h->k) ||
+                h->mlp || opt->bound_clamp)
+                throw ArgError{"bf16 factors need one PGD step per half, 32 < k <= 128, no network and no bound"};
+        } else if (opt->precision == DSANLS_PREC_BF16 && (h->has_sparse || !tc_supported(h->k))) {
+            throw ArgError{"BF16 precision needs dense data and a Gaussian or identity sketch, or sparse data and a "
+                           "subsampling sketch (bf16 factors)"};
+        }
+        if (opt->precision == DSANLS_PREC_BF16 && h->sketch != DSANLS_SKETCH_SUBSAMPLE) {
             const int dv = opt->d_v > 0 ? opt->d_v : h->d;
             if (h->m % 8 || h->n % 8 || h->d % 8 || dv % 8)
                 throw ArgError{"BF16 precision needs m, n, d and d_v multiples of 8 (16-byte TMA rows)"};
@@ -797,6 +840,8 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
 int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device) {
     if (!h) return DSANLS_EINVAL;
     if (!M || ld < h->n) return fail(h, DSANLS_EINVAL, "M is NULL or ld < n");
+    if (h->opt.precision == DSANLS_PREC_BF16 && h->sketch == DSANLS_SKETCH_SUBSAMPLE)
+        return fail(h, DSANLS_EINVAL, "BF16 with a subsampling sketch is the bf16-factor form of sparse data");
     DeviceGuard dg(h->device);
     return guarded(h, [&]() {
         cudaStream_t s = h->stream();
@@ -857,7 +902,8 @@ int dsanls_set_csr(dsanls_t h, const int64_t *rowptr, const int32_t *col, const 
     if (!rowptr || nnz < 0 || (nnz > 0 && (!col || !val))) return fail(h, DSANLS_EINVAL, "bad CSR pointers");
     if (t_rowptr && (nnz > 0 && (!t_col || !t_val))) return fail(h, DSANLS_EINVAL, "bad transposed CSR pointers");
     if (!t_rowptr && on_device) return fail(h, DSANLS_EINVAL, "device CSR input needs the transposed CSR too");
-    if (h->opt.precision == DSANLS_PREC_BF16) return fail(h, DSANLS_EINVAL, "BF16 precision needs dense data");
+    if (h->opt.precision == DSANLS_PREC_BF16 && h->sketch != DSANLS_SKETCH_SUBSAMPLE)
+        return fail(h, DSANLS_EINVAL, "BF16 precision needs dense data (or a subsampling sketch: bf16 factors)");
     DeviceGuard dg(h->device);
     return guarded(h, [&]() {
         cudaStream_t s = h->stream();
@@ -945,8 +991,13 @@ int dsanls_set_factors(dsanls_t h, const float *U, const float *V, int32_t on_de
     DeviceGuard dg(h->device);
     return guarded(h, [&]() {
         cudaStream_t s = h->stream();
+        if (h->U16 && (!U || !V)) factors_to_f32(h, s);  // the factor not given keeps its bf16 value
         if (U) copy_in(h->U, U, (size_t)h->m * h->k * sizeof(float), on_device, s);
         if (V) copy_in(h->V, V, (size_t)h->n * h->k * sizeof(float), on_device, s);
+        if (h->U16) {  // the bf16 factors take the new values, rounded
+            launch_copy_cast_bf16(h->U, h->m * h->k, h->U16, s);
+            launch_copy_cast_bf16(h->V, h->n * h->k, h->V16, s);
+        }
         DSANLS_CUDA(cudaStreamSynchronize(s));
         return DSANLS_OK;
     });
@@ -1010,6 +1061,7 @@ int dsanls_rel_error(dsanls_t h, double *out) {
     DeviceGuard dg(h->device);
     return guarded(h, [&]() {
         cudaStream_t s = h->stream();
+        factors_to_f32(h, s);
         if (h->has_dense) {
             ensure_sumsq(h);
             launch_dense_residual(h->M, h->n, h->U, h->V, h->m, h->n, h->k, h->work, WORK_ELEMS, h->dscal + 1, s);
@@ -1032,6 +1084,7 @@ int dsanls_get_factors(dsanls_t h, float *U, float *V, int32_t on_device) {
     if (!h) return DSANLS_EINVAL;
     DeviceGuard dg(h->device);
     return guarded(h, [&]() {
+        factors_to_f32(h, h->stream());
         if (int rc = pending_status(h)) return rc;
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         if (U) DSANLS_CUDA(cudaMemcpyAsync(U, h->U, (size_t)h->m * h->k * sizeof(float), kind, h->stream()));
@@ -1092,6 +1145,8 @@ int dsanls_set_mlp(dsanls_t h, dsanls_mlp_t m, int32_t pg_iters) {
     if (m && (m->st.k != h->k || h->k > 32 || m->st.max_rows < std::max(h->m, h->n)))
         return fail(h, DSANLS_EINVAL, "the network's k must equal the handle's (<= 32) and max_rows >= max(m, n)");
     if (m && h->opt.bound_clamp) return fail(h, DSANLS_EINVAL, "the learned form has no bound clamp");
+    if (m && h->opt.precision == DSANLS_PREC_BF16 && h->sketch == DSANLS_SKETCH_SUBSAMPLE)
+        return fail(h, DSANLS_EINVAL, "the learned form has no bf16 factors");
     DeviceGuard dg(h->device);
     return guarded(h, [&]() {
         DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
@@ -1182,7 +1237,7 @@ void dsanls_destroy(dsanls_t h) {
         invalidate_graph(h);
         dfree(h->M); dfree(h->MT); dfree(h->Mb); dfree(h->MTb);
         dfree(h->rp); dfree(h->trp); dfree(h->ci); dfree(h->tci); dfree(h->cv); dfree(h->tcv);
-        dfree(h->U); dfree(h->V);
+        dfree(h->U); dfree(h->V); dfree(h->U16); dfree(h->V16);
         dfree(h->S); dfree(h->Sb); dfree(h->J); dfree(h->A); dfree(h->W); dfree(h->Wpart); dfree(h->R);
         dfree(h->Rpart); dfree(h->Ytb); dfree(h->Bpart);
         dfree(h->P); dfree(h->Sn); dfree(h->Bb); dfree(h->Ptb); dfree(h->Ppart); dfree(h->Rpart2);

@@ -84,12 +84,10 @@ __global__ void kb_sketch(const BatchInst *__restrict__ inst, int count, const i
 
 // ---- B = Y^T S: item = (instance, 64-column tile) --------------------------
 constexpr int BT = 64;
-// STT: S read from the padded bf16 S^T of the tensor-core form (already rounded).
-template <bool BF16, bool STT = false>
+template <bool BF16>
 __global__ void __launch_bounds__(256)
     kb_bmat(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
-            int side, const float *__restrict__ factors, const float *__restrict__ S_all, float *__restrict__ B_all,
-            const __nv_bfloat16 *__restrict__ St_all = nullptr) {
+            int side, const float *__restrict__ factors, const float *__restrict__ S_all, float *__restrict__ B_all) {
     __shared__ float ys[32][33];
     __shared__ float ss[32][BT + 1];
     __shared__ int item_s;
@@ -114,19 +112,9 @@ __global__ void __launch_bounds__(256)
                 const int l = e / 32, c = e % 32;
                 ys[l][c] = (l0 + l < K && c < k) ? op<BF16>(Y[(l0 + l) * k + c]) : 0.0f;
             }
-            if (STT) {
-                const int64_t Kp = (K + 7) & ~(int64_t)7;
-                const __nv_bfloat16 *St = St_all + b.offSt;
-                for (int e = threadIdx.x; e < 32 * BT; e += 256) {
-                    const int jj = e / 32, l = e % 32;
-                    ss[l][jj] = (l0 + l < K && j0 + jj < dd) ? __bfloat162float(St[(int64_t)(j0 + jj) * Kp + l0 + l])
-                                                             : 0.0f;
-                }
-            } else {
-                for (int e = threadIdx.x; e < 32 * BT; e += 256) {
-                    const int l = e / BT, jj = e % BT;
-                    ss[l][jj] = (l0 + l < K && j0 + jj < dd) ? op<BF16>(S[(l0 + l) * dd + j0 + jj]) : 0.0f;
-                }
+            for (int e = threadIdx.x; e < 32 * BT; e += 256) {
+                const int l = e / BT, jj = e % BT;
+                ss[l][jj] = (l0 + l < K && j0 + jj < dd) ? op<BF16>(S[(l0 + l) * dd + j0 + jj]) : 0.0f;
             }
             __syncthreads();
 #pragma unroll 8
@@ -615,11 +603,9 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
     const bool tc = g.tc && g.bf16 && g.order == 0;
     mark(0);
     if (tc) {
-        launch_batch_sketch_t(g, side, cfg.sketch_blocks, s);
+        launch_batch_sketch_t(g, side, s);
         mark(1);
-        kb_bmat<true, true><<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, g.bitems[side], g.nb[side], ctr + 0, side,
-                                                                 g.factors, g.S, g.B, g.St);
-        DSANLS_LAUNCH_CHECK();
+        launch_batch_b_tc(g, side, cfg.tc_b_ctas, ctr + 0, s);
         mark(2);
         launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_ctas, ctr + 1, s);
         mark(3);
@@ -678,9 +664,9 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
 }
 
 void batch_build_tc_items(const std::vector<BatchInst> &h, int side, std::vector<int2> &tcitems,
-                          std::vector<int64_t> &sketch_t_prefix) {
+                          std::vector<int2> &tcbitems) {
     tcitems.clear();
-    sketch_t_prefix.assign(1, 0);
+    tcbitems.clear();
     std::vector<int> order(h.size());
     for (size_t i = 0; i < h.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -690,13 +676,9 @@ void batch_build_tc_items(const std::vector<BatchInst> &h, int side, std::vector
     });
     for (int i : order) {
         const int64_t rows = side == 0 ? h[i].m : h[i].n;
-        for (int t = 0; t < (int)ceil_div(rows, 128); ++t) tcitems.push_back(make_int2(i, t));
-    }
-    for (size_t i = 0; i < h.size(); ++i) {
-        const int64_t K = side == 0 ? h[i].n : h[i].m;
-        const int64_t Kp = (K + 7) & ~(int64_t)7;
         const int dd = side == 0 ? h[i].d : h[i].dv;
-        sketch_t_prefix.push_back(sketch_t_prefix.back() + (Kp / 4) * dd);
+        for (int t = 0; t < (int)ceil_div(rows, 128); ++t) tcitems.push_back(make_int2(i, t));
+        for (int t = 0; t < (int)ceil_div(dd, 128); ++t) tcbitems.push_back(make_int2(i, t));
     }
 }
 

@@ -19,7 +19,7 @@ struct BatchInst {
     int64_t offM, offU, offV, offS, offB, offR, offG;
     // tensor-core form: padded bf16 copy of M_i and M_i^T (rows padded to multiples
     // of 8 elements) and the padded bf16 S_i^T, element offsets (multiples of 8)
-    int64_t offMp, offSt;
+    int64_t offMp, offSt, offYt;  // offYt: padded bf16 Y_i^T (k_i x pad8(K_i)) of the half-step
 };
 
 struct BatchDev {
@@ -32,10 +32,9 @@ struct BatchDev {
     // bf16 paper order on tensor cores: padded bf16 data and S^T, (instance,
     // 128-row tile) items, prefix of the S^T sketch threads
     int tc = 0;
-    __nv_bfloat16 *data_p = nullptr, *St = nullptr;
-    int2 *tcitems[2] = {nullptr, nullptr};
-    int ntc[2] = {0, 0};
-    int64_t *sketch_t_prefix[2] = {nullptr, nullptr};
+    __nv_bfloat16 *data_p = nullptr, *St = nullptr, *Yt = nullptr;
+    int2 *tcitems[2] = {nullptr, nullptr}, *tcbitems[2] = {nullptr, nullptr};  // R items, B items (S^T row tiles)
+    int ntc[2] = {0, 0}, ntcb[2] = {0, 0};
     double *G = nullptr;
     int2 *bitems[2] = {nullptr, nullptr}, *aritems[2] = {nullptr, nullptr}, *uitems[2] = {nullptr, nullptr};
     int nb[2] = {0, 0}, nar[2] = {0, 0}, nu[2] = {0, 0};
@@ -56,6 +55,7 @@ struct BatchLaunch {
     int sketch_blocks = 152 * 8;
     int tc_nc = 128;    // sketch columns per chunk of the tensor-core product (64, 128, 256)
     int tc_ctas = 304;  // persistent CTAs of the tensor-core product
+    int tc_b_ctas = 304;  // persistent CTAs of B = Y^T S on tensor cores
 };
 
 void batch_build_items(const std::vector<BatchInst> &h, int side, std::vector<int2> &bitems,
@@ -65,16 +65,18 @@ void batch_build_items(const std::vector<BatchInst> &h, int side, std::vector<in
 // sketch, B, AR, gram, update.
 void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaStream_t s, cudaEvent_t *ev = nullptr);
 void batch_init_factors(const BatchInst *inst, int count, float *factors, cudaStream_t s);
-// (instance, 128-row tile) items of the tensor-core product, largest first, and
-// the prefix of the S^T sketch threads ((pad8(K_i) / 4) x d_i per instance).
+// (instance, 128-row tile) items of the tensor-core products, largest first: of
+// R_i (rows of X_i) and of B_i (rows of S_i^T, d_i of them).
 void batch_build_tc_items(const std::vector<BatchInst> &h, int side, std::vector<int2> &tcitems,
-                          std::vector<int64_t> &sketch_t_prefix);
+                          std::vector<int2> &tcbitems);
 // batch_tc.cu
 size_t batch_tc_smem(int nc);
 void batch_prime_tc(int max_smem);
 int batch_tc_ctas_per_sm(int nc);
 void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int ctas, int *counter, cudaStream_t s);
-void launch_batch_sketch_t(const BatchDev &g, int side, int blocks, cudaStream_t s);
+void launch_batch_sketch_t(const BatchDev &g, int side, cudaStream_t s);
+// B_i = Y_i^T S_i on tensor cores (padded bf16 Y_i^T first); counter: a cleared queue counter
+void launch_batch_b_tc(const BatchDev &g, int side, int ctas, int *counter, cudaStream_t s);
 void launch_batch_pad_bf16(const BatchDev &g, cudaStream_t s);
 
 }  // namespace dsanls

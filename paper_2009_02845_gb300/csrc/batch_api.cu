@@ -35,7 +35,7 @@ struct dsanls_batch_ctx {
     uint64_t graph_launches = 0;
     std::vector<char> has_data;
     int64_t data_elems = 0;   // packed M_i and M_i^T
-    int64_t datap_elems = 0, st_elems = 0;  // padded bf16 data and S^T (tensor-core form)
+    int64_t datap_elems = 0, st_elems = 0, yt_elems = 0;  // padded bf16 data, S^T, Y^T (tensor-core form)
     bool bf16_stale = true;   // the bf16 copies of data no longer match it
     std::vector<double> mm;  // ||M_i||^2
     double *work = nullptr;
@@ -177,6 +177,7 @@ void apply_config(dsanls_batch_ctx *b, int code, int sms) {
     if (code >= 1000) {
         b->cfg.tc_nc = code % 1000;
         b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc);
+        b->cfg.tc_b_ctas = sms * batch_tc_ctas_per_sm(64);
     }
 }
 
@@ -276,7 +277,7 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
         DSANLS_CUDA(cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking));
         prime_kernel_attributes();
         b->h.resize(count);
-        int64_t offM = 0, offF = 0, offS = 0, offB = 0, offR = 0, offG = 0, offMp = 0, offSt = 0;
+        int64_t offM = 0, offF = 0, offS = 0, offB = 0, offR = 0, offG = 0, offMp = 0, offSt = 0, offYt = 0;
         auto pad8 = [](int64_t x) { return (x + 7) & ~(int64_t)7; };
         for (int i = 0; i < count; ++i) {
             BatchInst &x = b->h[i];
@@ -307,9 +308,12 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
             offMp += pad8(x.m * pad8(x.n)) + pad8(x.n * pad8(x.m));
             x.offSt = offSt;
             offSt += pad8(std::max((int64_t)x.d * pad8(x.n), (int64_t)x.dv * pad8(x.m)));
+            x.offYt = offYt;
+            offYt += pad8((int64_t)x.k * std::max(pad8(x.n), pad8(x.m)));
         }
         b->datap_elems = offMp;
         b->st_elems = offSt;
+        b->yt_elems = offYt;
         cudaStream_t s = b->stream();
         BatchDev &g = b->g;
         g.count = count;
@@ -349,15 +353,14 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
             DSANLS_CUDA(cudaMemcpyAsync(g.uitems[side], ui.data(), ui.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaMemcpyAsync(g.sketch_prefix[side], pre.data(), pre.size() * sizeof(int64_t),
                                         cudaMemcpyHostToDevice, s));
-            std::vector<int2> ti;
-            std::vector<int64_t> tpre;
-            batch_build_tc_items(b->h, side, ti, tpre);
+            std::vector<int2> ti, tb;
+            batch_build_tc_items(b->h, side, ti, tb);
             balloc(g.tcitems[side], (int64_t)ti.size());
-            balloc(g.sketch_t_prefix[side], (int64_t)tpre.size());
+            balloc(g.tcbitems[side], (int64_t)tb.size());
             g.ntc[side] = (int)ti.size();
+            g.ntcb[side] = (int)tb.size();
             DSANLS_CUDA(cudaMemcpyAsync(g.tcitems[side], ti.data(), ti.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-            DSANLS_CUDA(cudaMemcpyAsync(g.sketch_t_prefix[side], tpre.data(), tpre.size() * sizeof(int64_t),
-                                        cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaMemcpyAsync(g.tcbitems[side], tb.data(), tb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
         }
         batch_init_factors(g.inst, count, g.factors, s);
@@ -405,6 +408,7 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
         if (b->g.tc && !b->g.data_p) {
             balloc(b->g.data_p, b->datap_elems);
             balloc(b->g.St, b->st_elems);
+            balloc(b->g.Yt, b->yt_elems);
         }
         b->bf16_stale = true;
         drop_graph(b);
@@ -581,10 +585,10 @@ void dsanls_batch_destroy(dsanls_batch_t b) {
     drop_graph(b);
     BatchDev &g = b->g;
     bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.P); bfree(g.G); bfree(g.data_b);
-    bfree(g.data_p); bfree(g.St);
+    bfree(g.data_p); bfree(g.St); bfree(g.Yt);
     for (int side = 0; side < 2; ++side) {
         bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]); bfree(g.pitems[side]);
-        bfree(g.tcitems[side]); bfree(g.sketch_t_prefix[side]);
+        bfree(g.tcitems[side]); bfree(g.tcbitems[side]);
     }
     bfree(g.counters); bfree(g.t_dev); bfree(g.flag); bfree(b->work); bfree(b->dres);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);

@@ -6,20 +6,25 @@
 // One persistent launch over a work queue of (instance, 128-row tile) items,
 // largest instances first.  A CTA of 256 threads takes an item with atomicAdd
 // and, for each NC-wide chunk of the instance's sketch columns:
-//   * walks K in blocks of 64: all threads copy the X tile (128 x 64) and the
-//     S^T chunk (N x 64, N = the chunk's columns rounded up to 16) from the
-//     padded bf16 copies into one of two shared-memory stages in the 128-byte
-//     swizzled K-major layout (16-byte loads; rows padded to multiples of 8
-//     elements, so any instance shape works), and thread 0 issues four
-//     tcgen05.mma (M = 128, N, K = 16) into the accumulator D1 in tensor
-//     memory and commits to the stage's mbarrier -- the copy of the next
-//     block overlaps the products of this one;
+//   * walks K in blocks of 64 through a ring of TB_STAGES shared-memory
+//     stages: all threads copy the X tile (128 x 64) and the S^T chunk (N x 64,
+//     N = the chunk's columns rounded up to 16) from the padded bf16 copies
+//     with 16-byte cp.async straight into the 128-byte swizzled K-major layout
+//     (rows padded to multiples of 8 elements, so any instance shape works),
+//     TB_STAGES - 1 blocks ahead of the products; thread 0 issues four
+//     tcgen05.mma (M = 128, N, K = 16) per block into the accumulator D1 in
+//     tensor memory and commits to the stage's mbarrier, which frees the stage;
 //   * moves D1 to shared memory as bf16 (the rounding of A where it enters R)
 //     next to the bf16 B chunk (k rows padded to 16 or 32), and thread 0 adds
 //     A_chunk B_chunk^T into the second accumulator D2 (M = 128, N = k).
 // After the last chunk D2 holds R for the tile's rows.  Every wait is
 // bounded (2 s); a wait that gives up sets bit 2 of the error flag, and the
 // CTA stops taking items, retires its MMAs and frees its tensor memory.
+//
+// PLAIN: the same kernel forms B_i = Y_i^T S_i as B_i^T = S_i^T Y_i over
+// (instance, 128-row tile of S_i^T) items -- S_i^T in place of X, the padded
+// bf16 Y_i^T (k_i rows) in place of the S^T chunk -- and writes D1 transposed
+// to B_i (no second product).
 #include <algorithm>
 
 #include "batch.cuh"
@@ -35,13 +40,14 @@ constexpr int TB_BM = 128;
 constexpr int TB_BK = 64;
 constexpr int TB_THREADS = 256;
 constexpr int TB_KP = 32;  // rows of the B tile (k <= 32 padded)
+constexpr int TB_STAGES = 4;
 constexpr unsigned long long TB_WAIT_NS = 2000000000ull;
 
 __host__ __device__ constexpr int tb_stage_bytes(int nc) { return TB_BM * TB_BK * 2 + nc * TB_BK * 2; }
 __host__ __device__ constexpr uint32_t tb_tmem_cols(int nc) { return nc + TB_KP <= 128 ? 128u : (nc + TB_KP <= 256 ? 256u : 512u); }
 
 struct __align__(8) TbTail {
-    uint64_t stage_done[2];
+    uint64_t stage_done[TB_STAGES];
     uint64_t d1_done;
     uint64_t d2_done;
     uint32_t tmem_base;
@@ -49,29 +55,29 @@ struct __align__(8) TbTail {
 };
 
 __host__ __device__ constexpr size_t tb_smem(int nc) {
-    return 1024 + 2 * (size_t)tb_stage_bytes(nc) + (size_t)(nc / 64) * TB_KP * 128 + sizeof(TbTail);
+    return 1024 + TB_STAGES * (size_t)tb_stage_bytes(nc) + (size_t)(nc / 64) * TB_KP * 128 + sizeof(TbTail);
 }
 
 DSANLS_DEV int64_t pad8(int64_t x) { return (x + 7) & ~(int64_t)7; }
 
-template <int NC>
+template <int NC, bool PLAIN>
 __global__ void __launch_bounds__(TB_THREADS)
     kb_ar_tc(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
              int side, const __nv_bfloat16 *__restrict__ data_p, const __nv_bfloat16 *__restrict__ St_all,
-             const float *__restrict__ B_all, float *__restrict__ R_all, int *__restrict__ flag) {
+             const __nv_bfloat16 *__restrict__ Yt_all, float *__restrict__ B_all, float *__restrict__ R_all,
+             int *__restrict__ flag) {
     static_assert(NC == 64 || NC == 128 || NC == 256, "chunk of 64, 128 or 256 columns");
     constexpr int SB = tb_stage_bytes(NC);
     constexpr uint32_t TCOLS = tb_tmem_cols(NC);
     extern __shared__ __align__(1024) uint8_t tb_smem_raw[];
     uint8_t *base = tb_smem_raw + ((1024u - (smem_u32(tb_smem_raw) & 1023u)) & 1023u);
-    uint8_t *stages = base;                    // 2 x (X 16 KB | S^T chunk NC x 128 B); A2 after the K loop
-    uint8_t *btile = base + 2 * SB;            // NC / 64 atoms of TB_KP rows x 128 B
+    uint8_t *stages = base;                    // TB_STAGES x (X 16 KB | S^T chunk NC x 128 B); A2 after the K loop
+    uint8_t *btile = base + TB_STAGES * SB;    // NC / 64 atoms of TB_KP rows x 128 B
     TbTail *tail = reinterpret_cast<TbTail *>(btile + (NC / 64) * TB_KP * 128);
     uint8_t *a2 = stages;                      // 128 x NC bf16 (NC / 64 atoms of 16 KB) <= 2 stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        mbar_init(&tail->stage_done[0], 1);
-        mbar_init(&tail->stage_done[1], 1);
+        for (int st = 0; st < TB_STAGES; ++st) mbar_init(&tail->stage_done[st], 1);
         mbar_init(&tail->d1_done, 1);
         mbar_init(&tail->d2_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -88,7 +94,7 @@ __global__ void __launch_bounds__(TB_THREADS)
     fence_after();
     const uint32_t tmem = tail->tmem_base;
     const uint32_t d2col = (uint32_t)NC;
-    uint32_t git = 0;            // stage uses so far (stage = git & 1)
+    uint32_t git = 0;            // stage loads so far (stage = git % TB_STAGES, its use git / TB_STAGES)
     uint32_t n_d1 = 0, n_d2 = 0;  // completions of the d1 / d2 barriers so far
     bool ok = true;
     while (ok) {
@@ -100,56 +106,70 @@ __global__ void __launch_bounds__(TB_THREADS)
         const BatchInst b = inst[items[it].x];
         const int64_t r0 = (int64_t)items[it].y * TB_BM;
         const int k = b.k, dd = side == 0 ? b.d : b.dv;
-        const int64_t K = side == 0 ? b.n : b.m, rows = side == 0 ? b.m : b.n;
+        const int64_t K = side == 0 ? b.n : b.m;
+        const int64_t rows = PLAIN ? dd : (side == 0 ? b.m : b.n);
         const int64_t Kp = pad8(K);
-        const __nv_bfloat16 *X = data_p + b.offMp + (side == 0 ? 0 : b.m * pad8(b.n));
-        const __nv_bfloat16 *St = St_all + b.offSt;
-        const float *B = B_all + b.offB;
+        // the first operand (rows x Kp) and the second (ncols x Kp, taken NC rows at a time)
+        const __nv_bfloat16 *X = PLAIN ? St_all + b.offSt : data_p + b.offMp + (side == 0 ? 0 : b.m * pad8(b.n));
+        const __nv_bfloat16 *St = PLAIN ? Yt_all + b.offYt : St_all + b.offSt;
+        const int ncols = PLAIN ? k : dd;
+        float *B = B_all + b.offB;
         const int nkb = (int)((Kp + TB_BK - 1) / TB_BK);
-        for (int dc = 0; dc < dd && ok; dc += NC) {
-            const int N = min(NC, (dd - dc + 15) & ~15);
+        for (int dc = 0; dc < ncols && ok; dc += NC) {
+            const int N = min(NC, (ncols - dc + 15) & ~15);
             const uint32_t id1 = idesc_bf16(TB_BM, N);
-            for (int kb = 0; kb < nkb; ++kb, ++git) {
-                const int s = git & 1;
-                uint8_t *sx = stages + s * SB;
+            // copies of block kb into stage (git + kb) % TB_STAGES, after the products of
+            // that stage's previous use (bounded wait) have read it
+            auto load_block = [&](int kb) -> bool {
+                const uint32_t L = git + (uint32_t)kb, st = L % TB_STAGES, use = L / TB_STAGES;
+                if (use >= 1 && !mbar_wait(&tail->stage_done[st], (use - 1) & 1, TB_WAIT_NS)) return false;
+                uint8_t *sx = stages + st * SB;
                 uint8_t *ss = sx + TB_BM * TB_BK * 2;
-                // the stage's previous products have read it
-                if (git >= 2 && !mbar_wait(&tail->stage_done[s], ((git >> 1) - 1) & 1, TB_WAIT_NS)) ok = false;
-                if (__syncthreads_or(!ok)) {
+                const int64_t c0 = (int64_t)kb * TB_BK;
+#pragma unroll
+                for (int q = 0; q < (TB_BM * 8) / TB_THREADS; ++q) {  // X tile: 128 rows x 8 chunks of 8 bf16
+                    const int e = tid + q * TB_THREADS, r = e >> 3, ch = e & 7;
+                    const int64_t col = c0 + 8 * ch;
+                    const bool in = r0 + r < rows && col < Kp;
+                    cp_async16(sx + sw128_off(r, 8 * ch, TB_BM), in ? (const void *)(X + (r0 + r) * Kp + col) : X, in);
+                }
+                for (int e = tid; e < N * 8; e += TB_THREADS) {  // S^T chunk: N rows x 8 chunks
+                    const int j = e >> 3, ch = e & 7;
+                    const int64_t col = c0 + 8 * ch;
+                    const bool in = dc + j < ncols && col < Kp;
+                    cp_async16(ss + sw128_off(j, 8 * ch, NC), in ? (const void *)(St + (int64_t)(dc + j) * Kp + col) : St,
+                               in);
+                }
+                return true;
+            };
+            bool lok = true;
+            for (int p = 0; p < TB_STAGES - 1; ++p) {  // prologue: TB_STAGES - 1 blocks in flight
+                if (p < nkb && lok) lok = load_block(p);
+                cp_async_commit();
+            }
+            for (int kb = 0; kb < nkb; ++kb) {
+                cp_async_wait<TB_STAGES - 2>();  // this thread's copies of block kb have landed
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_before();
+                if (__syncthreads_or(!lok)) {
                     ok = false;
                     break;
                 }
-                const int64_t c0 = (int64_t)kb * TB_BK;
-                // X tile: 128 rows x 8 chunks of 8 bf16
-#pragma unroll
-                for (int q = 0; q < (TB_BM * 8) / TB_THREADS; ++q) {
-                    const int e = tid + q * TB_THREADS, r = e >> 3, ch = e & 7;
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    const int64_t col = c0 + 8 * ch;
-                    if (r0 + r < rows && col < Kp) v = __ldg(reinterpret_cast<const uint4 *>(X + (r0 + r) * Kp + col));
-                    *reinterpret_cast<uint4 *>(sx + sw128_off(r, 8 * ch, TB_BM)) = v;
-                }
-                // S^T chunk: N rows x 8 chunks
-                for (int e = tid; e < N * 8; e += TB_THREADS) {
-                    const int j = e >> 3, ch = e & 7;
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    const int64_t col = c0 + 8 * ch;
-                    if (dc + j < dd && col < Kp)
-                        v = __ldg(reinterpret_cast<const uint4 *>(St + (int64_t)(dc + j) * Kp + col));
-                    *reinterpret_cast<uint4 *>(ss + sw128_off(j, 8 * ch, NC)) = v;
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                fence_before();
-                __syncthreads();
                 if (tid == 0) {
                     fence_after();
-                    const uint32_t ax = smem_u32(sx), bx = smem_u32(ss);
+                    const uint32_t st = (git + (uint32_t)kb) % TB_STAGES;
+                    const uint32_t ax = smem_u32(stages + st * SB), bx = ax + TB_BM * TB_BK * 2;
 #pragma unroll
                     for (int kk = 0; kk < TB_BK / 16; ++kk)
                         mma_bf16(tmem, sw128_desc(ax + kk * 32), sw128_desc(bx + kk * 32), id1, (kb | kk) != 0);
-                    mma_commit(&tail->stage_done[s]);
+                    mma_commit(&tail->stage_done[st]);
                 }
+                const int next = kb + TB_STAGES - 1;
+                if (next < nkb && lok) lok = load_block(next);
+                cp_async_commit();
             }
+            cp_async_wait<0>();
+            git += (uint32_t)nkb;
             if (!ok) break;
             // D1 complete: every product of this chunk has retired (the stages are free)
             if (tid == 0) mma_commit(&tail->d1_done);
@@ -160,6 +180,24 @@ __global__ void __launch_bounds__(TB_THREADS)
                 break;
             }
             fence_after();
+            if (PLAIN) {
+                // B^T rows of the tile from D1: B[c][r0 + r] (warps 0-3, columns < k <= 32)
+                if (warp < 4) {
+                    const int r = warp * 32 + lane;
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+                    tmem_ld_wait();
+                    if (r0 + r < rows) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            if (c < k) B[(int64_t)c * dd + r0 + r] = __uint_as_float(v[c]);
+                    }
+                }
+                fence_before();
+                __syncthreads();
+                fence_after();
+                continue;
+            }
             // A chunk (bf16) over the stages: warp w reads lanes 32 (w % 4).. of columns half (w / 4)
             {
                 const int q4 = warp & 3, half = warp >> 2;
@@ -211,7 +249,7 @@ __global__ void __launch_bounds__(TB_THREADS)
         }
         if (!ok) break;
         // R rows of the tile from D2 (warps 0-3: one TMEM lane = one row)
-        if (warp < 4) {
+        if (!PLAIN && warp < 4) {
             const int r = warp * 32 + lane;
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + d2col, v);
@@ -239,36 +277,44 @@ __global__ void __launch_bounds__(TB_THREADS)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
-// S_i^T (d_i x Kp_i, bf16, columns past K_i zero): one thread per Philox block of
-// four rows of S_i and one column, z * scale as in the binary32 sketch, then rounded.
-__global__ void kb_sketch_t(const BatchInst *__restrict__ inst, int count, const int64_t *__restrict__ prefix,
-                            int side, const int64_t *__restrict__ t_dev, __nv_bfloat16 *__restrict__ St_all) {
-    const int64_t total = prefix[count];
+// S_i^T (d_i x Kp_i, bf16, columns past K_i zero): blockIdx.y = instance, one
+// thread per Philox block of four rows of S_i and one column, z * scale as in
+// the binary32 sketch, then rounded; consecutive threads write consecutive
+// 8-byte groups of a row of S_i^T.
+__global__ void kb_sketch_t(const BatchInst *__restrict__ inst, int side, const int64_t *__restrict__ t_dev,
+                            __nv_bfloat16 *__restrict__ St_all) {
+    const BatchInst b = inst[blockIdx.y];
     const uint64_t t = (uint64_t)*t_dev;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = count;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (prefix[mid] <= idx) lo = mid;
-            else hi = mid;
-        }
-        const BatchInst b = inst[lo];
-        const int64_t local = idx - prefix[lo];
-        const int dd = side == 0 ? b.d : b.dv;
-        const int64_t K = side == 0 ? b.n : b.m, Kp = pad8(K);
-        const int64_t j = local / (Kp >> 2), q = local % (Kp >> 2);
+    const int dd = side == 0 ? b.d : b.dv;
+    const int64_t K = side == 0 ? b.n : b.m, Kp = pad8(K);
+    const uint32_t q4 = (uint32_t)(Kp >> 2), total = q4 * (uint32_t)dd;
+    const float scale = b.scale[side];
+    __nv_bfloat16 *St = St_all + b.offSt;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const uint32_t j = idx / q4, q = idx - j * q4;
         float z[4];
-        gaussian4(b.seed, (uint32_t)side, t, (uint32_t)q, (uint32_t)j, z);
-        const float scale = b.scale[side];
+        gaussian4(b.seed, (uint32_t)side, t, q, j, z);
         __nv_bfloat16 o[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) o[r] = __float2bfloat16_rn(4 * q + r < K ? __fmul_rn(z[r], scale) : 0.0f);
+        for (int r = 0; r < 4; ++r) o[r] = __float2bfloat16_rn(4 * (int64_t)q + r < K ? __fmul_rn(z[r], scale) : 0.0f);
         uint2 w;
         w.x = (uint32_t)__bfloat16_as_ushort(o[0]) | ((uint32_t)__bfloat16_as_ushort(o[1]) << 16);
         w.y = (uint32_t)__bfloat16_as_ushort(o[2]) | ((uint32_t)__bfloat16_as_ushort(o[3]) << 16);
-        *reinterpret_cast<uint2 *>(St_all + b.offSt + j * Kp + 4 * q) = w;
-        (void)dd;
+        *reinterpret_cast<uint2 *>(St + (int64_t)j * Kp + 4 * q) = w;
+    }
+}
+
+// Y_i^T (k_i x pad8(K_i), bf16, columns past K_i zero) of the fixed factor of the
+// half-step (V_i for side 0, U_i for side 1): blockIdx.y = instance, one thread
+// per row l of Y_i (its k_i contiguous values), coalesced writes per column.
+__global__ void kb_yt(const BatchInst *__restrict__ inst, int side, const float *__restrict__ factors,
+                      __nv_bfloat16 *__restrict__ Yt_all) {
+    const BatchInst b = inst[blockIdx.y];
+    const int64_t K = side == 0 ? b.n : b.m, Kp = pad8(K);
+    const float *Y = factors + (side == 0 ? b.offV : b.offU);
+    __nv_bfloat16 *Yt = Yt_all + b.offYt;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < Kp; l += (int64_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < b.k; ++c) Yt[c * Kp + l] = __float2bfloat16_rn(l < K ? Y[l * b.k + c] : 0.0f);
     }
 }
 
@@ -293,15 +339,16 @@ __global__ void kb_pad_bf16(const BatchInst *__restrict__ inst, const float *__r
 size_t batch_tc_smem(int nc) { return tb_smem(nc); }
 
 void batch_prime_tc(int max_smem) {
-    allow_max_dynamic_smem(kb_ar_tc<64>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<128>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<256>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<64, false>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<128, false>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<256, false>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<64, true>, max_smem);
 }
 
 int batch_tc_ctas_per_sm(int nc) {
     int per_sm = 1;
-    const void *f = nc == 64 ? (const void *)kb_ar_tc<64> : (nc == 128 ? (const void *)kb_ar_tc<128>
-                                                                        : (const void *)kb_ar_tc<256>);
+    const void *f = nc == 64 ? (const void *)kb_ar_tc<64, false>
+                             : (nc == 128 ? (const void *)kb_ar_tc<128, false> : (const void *)kb_ar_tc<256, false>);
     DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, TB_THREADS, tb_smem(nc)));
     // tensor memory: 512 columns per SM
     return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(nc))));
@@ -309,19 +356,27 @@ int batch_tc_ctas_per_sm(int nc) {
 
 void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int ctas, int *counter, cudaStream_t s) {
     if (nc == 64)
-        kb_ar_tc<64><<<ctas, TB_THREADS, tb_smem(64), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter, side, g.data_p,
-                                                            g.St, g.B, g.R, g.flag);
+        kb_ar_tc<64, false><<<ctas, TB_THREADS, tb_smem(64), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter, side,
+                                                                   g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     else if (nc == 128)
-        kb_ar_tc<128><<<ctas, TB_THREADS, tb_smem(128), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter, side,
-                                                              g.data_p, g.St, g.B, g.R, g.flag);
+        kb_ar_tc<128, false><<<ctas, TB_THREADS, tb_smem(128), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
+                                                                     side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     else
-        kb_ar_tc<256><<<ctas, TB_THREADS, tb_smem(256), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter, side,
-                                                              g.data_p, g.St, g.B, g.R, g.flag);
+        kb_ar_tc<256, false><<<ctas, TB_THREADS, tb_smem(256), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
+                                                                     side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     DSANLS_LAUNCH_CHECK();
 }
 
-void launch_batch_sketch_t(const BatchDev &g, int side, int blocks, cudaStream_t s) {
-    kb_sketch_t<<<blocks, 256, 0, s>>>(g.inst, g.count, g.sketch_t_prefix[side], side, g.t_dev, g.St);
+void launch_batch_b_tc(const BatchDev &g, int side, int ctas, int *counter, cudaStream_t s) {
+    kb_yt<<<dim3(4, (unsigned)g.count), 256, 0, s>>>(g.inst, side, g.factors, g.Yt);
+    DSANLS_LAUNCH_CHECK();
+    kb_ar_tc<64, true><<<ctas, TB_THREADS, tb_smem(64), s>>>(g.inst, g.tcbitems[side], g.ntcb[side], counter, side,
+                                                              g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
+    DSANLS_LAUNCH_CHECK();
+}
+
+void launch_batch_sketch_t(const BatchDev &g, int side, cudaStream_t s) {
+    kb_sketch_t<<<dim3(16, (unsigned)g.count), 256, 0, s>>>(g.inst, side, g.t_dev, g.St);
     DSANLS_LAUNCH_CHECK();
 }
 

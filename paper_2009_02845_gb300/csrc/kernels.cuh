@@ -19,6 +19,8 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(float v) {
     return __float2bfloat16_rn(v);
 }
+__device__ __forceinline__ float load_as_float(const float *p) { return *p; }
+__device__ __forceinline__ float load_as_float(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
 // Raise the dynamic shared-memory limit of every kernel that needs more than
 // 48 KB once per process (before any graph capture).
@@ -128,10 +130,12 @@ void launch_sparse_combine(const double *mm, const double *cross, const double *
 // out[j*ldo + i] = in[i*ldi + j] (rows x cols -> cols x rows)
 void launch_transpose(const float *in, int64_t ldi, int64_t rows, int64_t cols, float *out, int64_t ldo,
                       cudaStream_t s);
-// W[c][p] = scale * Y[J[p]][c]  (k x d)
-void launch_gather_w(const float *Y, int k, const int32_t *J, int d, float scale, float *W, cudaStream_t s);
+// W[c][p] = scale * Y[J[p]][c]  (k x d), Y binary32 or bf16 (bf16 factors)
+template <typename T>
+void launch_gather_w(const T *Y, int k, const int32_t *J, int d, float scale, float *W, cudaStream_t s);
 // W = Y^T (k x K) for the identity sketch
 void launch_copy_cast_bf16(const float *in, int64_t n, __nv_bfloat16 *out, cudaStream_t s);
+void launch_cast_f32(const __nv_bfloat16 *in, int64_t n, float *out, cudaStream_t s);
 
 // ---- sparse.cu ------------------------------------------------------------
 // out[i][0..w) = alpha * sum_{e in row i} val_e * D[col_e*ldd + 0..w)
@@ -159,6 +163,7 @@ void launch_subcsr_build(const int64_t *xtp, const int32_t *xtc, const float *xt
 // out[i][0..k) = alpha * sum over row i's sub-CSR entries of val * Y[col][0..k) (k <= 128):
 // rows of at most 64 entries summed in ascending column order by one warp, longer
 // rows by a CTA (32 interleaved partial sums added in a fixed order).
-void launch_subcsr_rows(const SubCsr &sc, const float *Y, int k, float alpha, float *out, cudaStream_t s);
+template <typename T>
+void launch_subcsr_rows(const SubCsr &sc, const T *Y, int k, float alpha, float *out, cudaStream_t s);
 
 }  // namespace dsanls

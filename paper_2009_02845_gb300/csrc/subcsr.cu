@@ -232,9 +232,10 @@ __global__ void k_long_rows(const int64_t *__restrict__ ptr, int64_t rows, int32
 }
 
 // out[i][c] = alpha * sum over the row's entries (ascending column) of val * Y[col][c]
+template <typename T>
 __global__ void __launch_bounds__(256)
     k_sub_rows(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const float *__restrict__ val,
-               int64_t rows, const float *__restrict__ Y, int k, float alpha, float *__restrict__ out) {
+               int64_t rows, const T *__restrict__ Y, int k, float alpha, float *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -244,11 +245,11 @@ __global__ void __launch_bounds__(256)
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int64_t e = e0; e < e1; ++e) {
             const float v = val[e];
-            const float *y = Y + (int64_t)col[e] * k;
+            const T *y = Y + (int64_t)col[e] * k;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = lane + 32 * q;
-                if (c < k) acc[q] = __fmaf_rn(v, y[c], acc[q]);
+                if (c < k) acc[q] = __fmaf_rn(v, load_as_float(y + c), acc[q]);
             }
         }
 #pragma unroll
@@ -264,9 +265,10 @@ __global__ void __launch_bounds__(256)
 // flight), then the partial sums are added in warp order.
 constexpr int LONG_WARPS = 32;
 
+template <typename T>
 __global__ void __launch_bounds__(32 * LONG_WARPS)
     k_sub_rows_long(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const float *__restrict__ val,
-                    const int32_t *__restrict__ list, const int32_t *__restrict__ nlong, const float *__restrict__ Y,
+                    const int32_t *__restrict__ list, const int32_t *__restrict__ nlong, const T *__restrict__ Y,
                     int k, float alpha, float *__restrict__ out) {
     __shared__ float part[LONG_WARPS][128];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -278,11 +280,11 @@ __global__ void __launch_bounds__(32 * LONG_WARPS)
 #pragma unroll 4
         for (int64_t e = e0 + warp; e < e1; e += LONG_WARPS) {
             const float v = val[e];
-            const float *y = Y + (int64_t)col[e] * k;
+            const T *y = Y + (int64_t)col[e] * k;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = lane + 32 * q;
-                if (c < k) acc[q] = __fmaf_rn(v, y[c], acc[q]);
+                if (c < k) acc[q] = __fmaf_rn(v, load_as_float(y + c), acc[q]);
             }
         }
 #pragma unroll
@@ -390,15 +392,19 @@ void launch_subcsr_build(const int64_t *xtp, const int32_t *xtc, const float *xt
     DSANLS_LAUNCH_CHECK();
 }
 
-void launch_subcsr_rows(const SubCsr &sc, const float *Y, int k, float alpha, float *out, cudaStream_t s) {
+template <typename T>
+void launch_subcsr_rows(const SubCsr &sc, const T *Y, int k, float alpha, float *out, cudaStream_t s) {
     if (sc.rows <= 0) return;
     int64_t blocks = ceil_div(sc.rows, 8);
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_sub_rows<<<(unsigned)blocks, 256, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.rows, Y, k, alpha, out);
+    k_sub_rows<T><<<(unsigned)blocks, 256, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.rows, Y, k, alpha, out);
     DSANLS_LAUNCH_CHECK();
-    k_sub_rows_long<<<152 * 2, 32 * LONG_WARPS, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.longs + 1, sc.longs, Y, k,
-                                            alpha, out);
+    k_sub_rows_long<T><<<152 * 2, 32 * LONG_WARPS, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.longs + 1,
+                                                           sc.longs, Y, k, alpha, out);
     DSANLS_LAUNCH_CHECK();
 }
+template void launch_subcsr_rows<float>(const SubCsr &, const float *, int, float, float *, cudaStream_t);
+template void launch_subcsr_rows<__nv_bfloat16>(const SubCsr &, const __nv_bfloat16 *, int, float, float *,
+                                                cudaStream_t);
 
 }  // namespace dsanls

@@ -869,11 +869,27 @@ DSANLS_DEV float upd_project(float v, float bound, int *flag) {
     return r;
 }
 
-template <int KA>  // K atoms of 64 columns: 1 for k <= 64, 2 for k <= 128
+// Z of type ZT: binary32, or bf16 for the bf16-factor form -- z is then exactly
+// a bf16 value (z_m = z_l = 0), so only the three products z_h g_j are issued,
+// and the step's binary32 result is rounded to bf16 when it is stored.
+DSANLS_DEV float4 load_z4(const float *Z, int64_t f0, int g) { return __ldcs(reinterpret_cast<const float4 *>(Z + f0) + g); }
+DSANLS_DEV float4 load_z4(const __nv_bfloat16 *Z, int64_t f0, int g) {
+    const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(Z + f0) + g);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+}
+DSANLS_DEV void store_z4(float *Z, int64_t f0, int g, float4 v) { __stcs(reinterpret_cast<float4 *>(Z + f0) + g, v); }
+DSANLS_DEV void store_z4(__nv_bfloat16 *Z, int64_t f0, int g, float4 v) {
+    __stcs(reinterpret_cast<uint2 *>(Z + f0) + g, make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w)));
+}
+
+template <int KA, typename ZT>  // K atoms of 64 columns: 1 for k <= 64, 2 for k <= 128
 __global__ void __launch_bounds__(UPD_THREADS)
-    k_update_tc(float *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k, int N,
+    k_update_tc(ZT *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k, int N,
                 const float *__restrict__ Gf, int kp, const double *__restrict__ scal, float bound,
                 int *__restrict__ flag, uint32_t tmem_cols) {
+    constexpr bool ZBF = sizeof(ZT) == 2;
+    constexpr int ZPARTS = ZBF ? 1 : 3;  // nonzero parts of the split of z
     extern __shared__ uint8_t upd_smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(upd_smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int KC = KA * 64;  // padded K
@@ -933,7 +949,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
 #pragma unroll
             for (int j = 0; j < UPD_UNROLL; ++j) {
                 const int g = tid + j * UPD_THREADS;
-                if (4 * g < nf) zz[j] = __ldcs(reinterpret_cast<const float4 *>(Z + f0) + g);
+                if (4 * g < nf) zz[j] = load_z4(Z, f0, g);
             }
 #pragma unroll
             for (int j = 0; j < UPD_UNROLL; ++j) {
@@ -947,8 +963,10 @@ __global__ void __launch_bounds__(UPD_THREADS)
                     split3_one(zv[e], h, m, l);
                     const int off = sw128_off(r, c, UPD_BM);
                     *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = h;
-                    *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
-                    *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
+                    if (!ZBF) {
+                        *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
+                        *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
+                    }
                     if (++c == k) {
                         c = 0;
                         ++r;
@@ -959,11 +977,13 @@ __global__ void __launch_bounds__(UPD_THREADS)
             for (int f = tid; f < nf; f += UPD_THREADS) {
                 const int r = f / k, c = f - r * k;
                 __nv_bfloat16 h, m, l;
-                split3_one(Z[f0 + f], h, m, l);
+                split3_one(load_as_float(Z + f0 + f), h, m, l);
                 const int off = sw128_off(r, c, UPD_BM);
                 *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = h;
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
+                if (!ZBF) {
+                    *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
+                    *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
+                }
             }
         }
         {
@@ -972,16 +992,12 @@ __global__ void __launch_bounds__(UPD_THREADS)
             for (int e = tid; e < UPD_BM * pc; e += UPD_THREADS) {
                 const int r = e / pc, c = k + (e - r * pc);
                 const int off = sw128_off(r, c, UPD_BM);
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = zero;
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = zero;
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = zero;
+                for (int pt = 0; pt < ZPARTS; ++pt) *reinterpret_cast<__nv_bfloat16 *>(Ap + pt * a_part + off) = zero;
             }
             for (int e = nr * k + tid; e < UPD_BM * k; e += UPD_THREADS) {  // rows past the end
                 const int r = e / k, c = e - r * k;
                 const int off = sw128_off(r, c, UPD_BM);
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = zero;
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = zero;
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = zero;
+                for (int pt = 0; pt < ZPARTS; ++pt) *reinterpret_cast<__nv_bfloat16 *>(Ap + pt * a_part + off) = zero;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -993,7 +1009,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
             const uint32_t a0 = smem_u32(Ap), b0 = smem_u32(Bp);
             uint32_t acc = 0;
 #pragma unroll 1
-            for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < ZPARTS; ++i)
 #pragma unroll 1
                 for (int jp = 0; i + jp < 3; ++jp)
 #pragma unroll 1
@@ -1052,13 +1068,13 @@ __global__ void __launch_bounds__(UPD_THREADS)
                         ++r;
                     }
                 }
-                __stcs(reinterpret_cast<float4 *>(Z + f0) + g, make_float4(zv[0], zv[1], zv[2], zv[3]));
+                store_z4(Z, f0, g, make_float4(zv[0], zv[1], zv[2], zv[3]));
             }
         } else {
             for (int f = tid; f < nf; f += UPD_THREADS) {
                 const int r = f / k, c = f - r * k;
                 const float grad = __fsub_rn(stage[r * lds + c], R[f0 + f]);
-                Z[f0 + f] = upd_project(__fmaf_rn(-eta, grad, Z[f0 + f]), bound, flag);
+                Z[f0 + f] = store_cast<ZT>(upd_project(__fmaf_rn(-eta, grad, load_as_float(Z + f0 + f)), bound, flag));
             }
         }
         // the next tile's split overwrites the staging: every thread is done with it
@@ -1085,22 +1101,23 @@ size_t update_tc_smem(int N) {
 bool update_tc_supported(int k) { return k > 32 && k <= 128; }
 
 namespace {
-template <int KA>
-void launch_update_tc_kind(float *Z, const float *R, int64_t rows, int k, int N, const float *Gf, int kp,
+template <int KA, typename ZT>
+void launch_update_tc_kind(ZT *Z, const float *R, int64_t rows, int k, int N, const float *Gf, int kp,
                            const double *scal, float bound, int *flag, uint32_t tmem_cols, int sms, cudaStream_t s) {
     const size_t smem = update_tc_smem<KA>(N);
     int per_sm = 1;
-    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<KA>, UPD_THREADS, smem));
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<KA, ZT>, UPD_THREADS, smem));
     per_sm = std::max(1, std::min(per_sm, 512 / (int)tmem_cols));
     const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
-    k_update_tc<KA><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
-                                                              tmem_cols);
+    k_update_tc<KA, ZT><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
+                                                                  tmem_cols);
     DSANLS_LAUNCH_CHECK();
 }
 }  // namespace
 
-void launch_update_tc(float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
+template <typename ZT>
+void launch_update_tc(ZT *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
                       float bound, int *flag, cudaStream_t s) {
     if (!update_tc_supported(k)) throw ArgError{"launch_update_tc: needs 32 < k <= 128"};
     if (rows <= 0) return;
@@ -1110,10 +1127,14 @@ void launch_update_tc(float *Z, const float *R, int64_t rows, int k, const float
     DSANLS_CUDA(cudaGetDevice(&dev));
     DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (k <= 64)
-        launch_update_tc_kind<1>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
+        launch_update_tc_kind<1, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
     else
-        launch_update_tc_kind<2>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
+        launch_update_tc_kind<2, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
 }
+template void launch_update_tc<float>(float *, const float *, int64_t, int, const float *, int, const double *, float,
+                                      int *, cudaStream_t);
+template void launch_update_tc<__nv_bfloat16>(__nv_bfloat16 *, const float *, int64_t, int, const float *, int,
+                                              const double *, float, int *, cudaStream_t);
 
 void set_tc_wait_debug(unsigned long long wait_ns, int starve) {
     DSANLS_CUDA(cudaMemcpyToSymbol(g_wait_ns, &wait_ns, sizeof(wait_ns)));
@@ -1121,8 +1142,10 @@ void set_tc_wait_debug(unsigned long long wait_ns, int starve) {
 }
 
 void prime_tc_attributes(int max_smem) {
-    allow_max_dynamic_smem(k_update_tc<1>, max_smem);
-    allow_max_dynamic_smem(k_update_tc<2>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<1, float>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<2, float>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<1, __nv_bfloat16>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<2, __nv_bfloat16>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, true, false>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, true, false>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, false>, max_smem);

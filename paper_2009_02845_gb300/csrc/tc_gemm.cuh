@@ -74,7 +74,10 @@ void launch_transpose_bf16(const float *in, int64_t rows, int64_t cols, __nv_bfl
 // products, accurate to about binary32); entries clamped at `bound` when > 0;
 // NaN/Inf set bit 1 of *flag, a bounded wait that gives up bit 2.
 bool update_tc_supported(int k);
-void launch_update_tc(float *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
+// Z of type float, or bf16 for the bf16-factor form (z exact in bf16: three products;
+// the binary32 step rounded to bf16 when stored).
+template <typename ZT>
+void launch_update_tc(ZT *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
                       float bound, int *flag, cudaStream_t s);
 void prime_tc_attributes(int max_smem);
 // Test switch of the bounded waits on the current device: wait_ns > 0 replaces the

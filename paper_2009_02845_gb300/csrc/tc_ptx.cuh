@@ -136,5 +136,17 @@ DSANLS_DEV int sw128_off(int r, int c, int rows) {
     return (c >> 6) * rows * 128 + r * 128 + ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 7) << 1);
 }
 
+// 16-byte asynchronous global->shared copy (zero-filled when !pred; src must still be
+// a valid address), grouped with commit / wait.
+DSANLS_DEV void cp_async16(void *dst, const void *src, bool pred) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(pred ? 16 : 0)
+                 : "memory");
+}
+DSANLS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+DSANLS_DEV void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 }  // namespace
 }  // namespace dsanls
