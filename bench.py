@@ -378,7 +378,7 @@ def run_ours(args, w):
     solver = {"pgd": pkg.PGD, "rcd": pkg.RCD}[args.solver]
     h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=rank, d_v=w["d_v"], solver=solver,
                    precision=prec, use_graph=1, order=order, alpha=args.alpha, beta=args.beta,
-                   inner_iters=args.inner_iters)
+                   inner_iters=args.inner_iters, regen_sketch=int(args.regen_sketch))
     _set_data(h, M)
 
     for _ in range(args.warmup):
@@ -525,6 +525,7 @@ def run_ours(args, w):
             "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "k": k, "d": d, "d_v": d_v,
                        "precision": {pkg.FP32: "fp32", pkg.BF16: "bf16", pkg.FP8: "fp8"}[prec], "solver": args.solver, "alpha": args.alpha, "beta": args.beta,
                        "inner_iters": args.inner_iters, "graph": True, "replicas": ws,
+                       "sketch_in_gemm": bool(args.regen_sketch),
                        "order": ["paper", "reassociated"][order],
                        "l2": "inputs larger than L2 (M is %.1f GB)" % (_input_bytes(M) / 1e9)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -556,6 +557,8 @@ def main():
                     help="PGD steps per half-step on the proximal row objective (1: the paper's single step)")
     ap.add_argument("--alpha", type=float, default=1.0, help="mu_t = alpha + beta t")
     ap.add_argument("--beta", type=float, default=1.0)
+    ap.add_argument("--regen-sketch", action="store_true",
+                    help="BF16 paper order: draw the Gaussian sketch inside the GEMMs instead of a pre-pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned workload")

@@ -129,6 +129,12 @@ typedef struct dsanls_options {
                               default) is the single step of eq. gradient_descent.
                               1..256; must be 1 with RCD and in the batched form */
     void *stream;          /* cudaStream_t for all work; NULL = the handle's own     */
+    int32_t regen_sketch;  /* BF16, paper order, Gaussian sketch: 1 draws S inside the
+                              tensor-core GEMMs (warps of the GEMM compute each S^T
+                              tile from the Philox field) instead of a sketch pre-pass
+                              read by TMA; bitwise the same results.  Default 0: the
+                              pre-pass, measured faster (the draw costs ~45 ALU ops per
+                              entry and is repeated by every row tile)               */
 } dsanls_options;
 
 typedef struct dsanls_ctx *dsanls_t;

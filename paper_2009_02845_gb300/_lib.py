@@ -55,6 +55,7 @@ class Options(ctypes.Structure):
         ("order", ctypes.c_int32),
         ("inner_iters", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("regen_sketch", ctypes.c_int32),
     ]
 
 

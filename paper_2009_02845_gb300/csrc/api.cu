@@ -399,6 +399,8 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         const bool tc = dense && (h->opt.precision == DSANLS_PREC_BF16 || fp8);
         const bool reas = h->opt.order == DSANLS_ORDER_REASSOCIATED;
         const __nv_bfloat16 *Xb = side == 0 ? h->Mb : h->MTb;
+        // S drawn inside the GEMMs (BF16, paper order, Gaussian): no pre-pass
+        const bool regen = tc && !fp8 && !reas && h->sketch == DSANLS_SKETCH_GAUSSIAN && h->opt.regen_sketch;
         // SRHT: the sampled Hadamard columns J (dd of srht_pad(K), side 0x40 | side)
         const int32_t *hcols = nullptr;
         if (h->sketch == DSANLS_SKETCH_SRHT) {
@@ -409,7 +411,9 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         // CUDA-core form, bf16 S^T (K-major operand) for the tensor-core forms, and
         // for the fp8 form also fp8 S^T of the unit-variance draws; the reassociated
         // bf16 form also keeps bf16 S (d-major operand of P^T = B S^T)
-        if (tc && reas)
+        if (regen)
+            ;
+        else if (tc && reas)
             launch_gaussian_pair(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sn, rade, hcols, 0, s);
         else if (fp8)
             launch_gaussian_dual(h->seed, (uint32_t)side, h->t_dev, K, dd, scale, h->Sb, h->Sq, rade, hcols, s);
@@ -420,7 +424,11 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             launch_gaussian_field<float>(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, scale, false, h->S, rade,
                                          hcols, s);
         mark(pe, DSANLS_PHASE_B, s);
-        if (tc) {
+        if (regen) {
+            launch_transpose_bf16(Y, K, k, h->Ytb, s);
+            launch_tc_gemm_regen(h->Ytb, k, K, dd, h->seed, (uint32_t)side, h->t_dev, scale, h->Bpart, h->W, h->flag,
+                                 s);
+        } else if (tc) {
             // B = Y^T S (k x dd) on tensor cores from bf16 Y^T and S^T, split-K
             launch_transpose_bf16(Y, K, k, h->Ytb, s);
             launch_tc_gemm(h->Ytb, h->Sb, k, K, dd, h->Bpart, h->W, h->flag, s);
@@ -482,6 +490,9 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             if (fp8) {
                 launch_tc_sketch_rhs_fp8(side == 0 ? h->Mq : h->MTq, h->qscale[side], h->Sq, scale, h->W, rows, K, dd,
                                          k, h->Rpart, h->R, h->flag, s);
+            } else if (regen) {
+                launch_tc_sketch_rhs_regen(Xb, h->W, rows, K, dd, k, h->seed, (uint32_t)side, h->t_dev, scale, h->Rpart,
+                                           h->R, h->flag, s);
             } else {
                 launch_tc_sketch_rhs(Xb, h->Sb, h->W, rows, K, dd, k, h->Rpart, h->R, h->flag, s);
             }
@@ -710,6 +721,7 @@ int dsanls_default_options(dsanls_options *opt) {
     opt->order = DSANLS_ORDER_PAPER;
     opt->inner_iters = 1;
     opt->stream = nullptr;
+    opt->regen_sketch = 0;
     return DSANLS_OK;
 }
 
@@ -809,6 +821,7 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
             throw ArgError{"the reassociated order needs a dense sketch (Gaussian, Rademacher, count or SRHT)"};
         if (opt->power_iters < 0 || opt->power_iters > 10000) throw ArgError{"power_iters out of range"};
         if (opt->inner_iters < 1 || opt->inner_iters > 256) throw ArgError{"inner_iters must be in 1..256"};
+        if (opt->regen_sketch != 0 && opt->regen_sketch != 1) throw ArgError{"regen_sketch must be 0 or 1"};
         if (opt->inner_iters > 1 && opt->solver != DSANLS_SOLVER_PGD)
             throw ArgError{"inner_iters > 1 needs the PGD solver"};
         if (!(opt->alpha >= 0.0) || !(opt->beta >= 0.0) || !std::isfinite(opt->alpha) || !std::isfinite(opt->beta))
@@ -821,7 +834,7 @@ int dsanls_set_options(dsanls_t h, const dsanls_options *opt) {
                                 (opt->power_iters != h->opt.power_iters) || (opt->alpha != h->opt.alpha) ||
                                 (opt->beta != h->opt.beta) || (opt->bound_clamp != h->opt.bound_clamp) ||
                                 (opt->use_graph != h->opt.use_graph) || (opt->order != h->opt.order) ||
-                                (opt->inner_iters != h->opt.inner_iters);
+                                (opt->inner_iters != h->opt.inner_iters) || (opt->regen_sketch != h->opt.regen_sketch);
         // finish work queued on the old stream before switching
         DSANLS_CUDA(cudaStreamSynchronize(h->stream()));
         h->opt = *opt;

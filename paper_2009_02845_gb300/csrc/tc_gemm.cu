@@ -104,15 +104,26 @@ struct __align__(8) TcSmemTail {
 // S = S0 + S1 + S2 (map_s, map_s1, map_s2): every K-block runs the six
 // products Xa Sb with a + b <= 2 (the dropped ones are of order 2^-24 of
 // the product) into the same fp32 accumulator, one ring stage per product.
-template <int STAGES, bool FUSED, bool FP8, int BNT = BN, int NP = 1>
+//
+// GEN (bf16, NP = 1, BNT = 256): the second operand is the Gaussian sketch S^T
+// itself, drawn inside the kernel instead of read by TMA -- warps 2-7 (192
+// threads) compute each stage's 256 x 64 tile from the Philox field (key
+// gseed, stream gside, t from gt_dev; entry bf16(z gscale), exactly the values
+// of the sketch pre-pass, so the results are bitwise those of the TMA form),
+// write it in the swizzled layout and arrive on the stage's full barrier
+// beside the X tile's TMA.
+template <int STAGES, bool FUSED, bool FP8, int BNT = BN, int NP = 1, bool GEN = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_s,
               const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_x1,
               const __grid_constant__ CUtensorMap map_x2, const __grid_constant__ CUtensorMap map_s1,
               const __grid_constant__ CUtensorMap map_s2, int64_t rows, int64_t K, int64_t d, int k, int kp,
               int kb_per_split, float *__restrict__ out, int *__restrict__ err, const float *__restrict__ row_scale,
-              float extra_scale, const float *__restrict__ col_scale) {
+              float extra_scale, const float *__restrict__ col_scale, uint64_t gseed, uint32_t gside,
+              const int64_t *__restrict__ gt_dev, float gscale) {
     static_assert(NP == 1 || (NP == 6 && !FUSED && !FP8), "the split product is a plain bf16 product");
+    static_assert(!GEN || (NP == 1 && !FP8 && BNT == BN), "the drawn sketch is a 256-wide bf16 operand");
+    constexpr int NGEN = 6;  // generator warps 2..7
     const unsigned long long wl = wait_limit();
     constexpr int BKE = FP8 ? 128 : BK;  // K elements per stage
     static_assert(!FUSED || BNT == BN, "the fused kernel uses 256-wide N tiles");
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&tail->full[s], 1);
+            mbar_init(&tail->full[s], GEN ? 1 + NGEN : 1);
             mbar_init(&tail->empty[s], 1);
         }
         mbar_init(&tail->b_full, 1);
@@ -184,9 +195,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const CUtensorMap *mx = pa == 0 ? &map_x : (pa == 1 ? &map_x1 : &map_x2);
                 const CUtensorMap *ms = pb == 0 ? &map_s : (pb == 1 ? &map_s1 : &map_s2);
                 uint8_t *sa = stage_base + s * SB;
-                mbar_expect_tx(&tail->full[s], SB);
+                mbar_expect_tx(&tail->full[s], GEN ? A_STAGE_BYTES : SB);
                 tma_load_2d(sa, mx, (kb0 + kb) * BKE, (int)m0, &tail->full[s]);
-                tma_load_2d(sa + A_STAGE_BYTES, ms, (kb0 + kb) * BKE, n0, &tail->full[s]);
+                if (!GEN) tma_load_2d(sa + A_STAGE_BYTES, ms, (kb0 + kb) * BKE, n0, &tail->full[s]);
                 ++issued;
             }
             // drain: every copy this thread issued has landed before the CTA can exit
@@ -243,7 +254,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mma_commit(&tail->mma_done);
             mbar_wait(&tail->mma_done, 0, wl);
         }
-    } else if (warp >= 4) {
+    }
+    if (GEN && warp >= 2) {
+        // draw the sketch tile of every stage: Philox block (row group q of S, column j)
+        // gives rows 4q..4q+3, i.e. four consecutive K elements of row j of S^T
+        const uint64_t t = (uint64_t)*gt_dev;
+        const int gt = (warp - 2) * 32 + lane;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&tail->empty[s], ((kb / STAGES) - 1) & 1, wl)) {
+                if (lane == 0) atomicOr(err, 2);
+                tail->failed = 1;
+                break;
+            }
+            if (*(volatile int *)&tail->failed) break;
+            uint8_t *sb = stage_base + s * SB + A_STAGE_BYTES;
+            const int64_t lbase = (int64_t)(kb0 + kb) * BK;
+            for (int bi = gt; bi < (BK / 4) * BN; bi += NGEN * 32) {
+                const int jl = bi & (BN - 1), ql = bi / BN;
+                const int64_t l0 = lbase + 4 * ql, j = n0 + jl;
+                uint2 w = make_uint2(0u, 0u);
+                if (j < d && l0 < K) {
+                    float z[4];
+                    gaussian4(gseed, gside, t, (uint32_t)(l0 >> 2), (uint32_t)j, z);
+                    float v[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) v[r] = l0 + r < K ? __fmul_rn(z[r], gscale) : 0.0f;
+                    w = make_uint2(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]));
+                }
+                *reinterpret_cast<uint2 *>(sb + sw128_off(jl, 4 * ql, BN)) = w;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tail->full[s]);
+        }
+    }
+    if (warp >= 4) {
         const int q = warp & 3;  // TMEM lane quarter of this warp
         const int r = q * 32 + lane;
         const int64_t row = m0 + r;
@@ -483,10 +529,39 @@ void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
         k_tc_gemm<4, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
-                                                                            err, nullptr, 1.0f, nullptr);
+                                                                            err, nullptr, 1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
     else
         k_tc_gemm<3, true, false><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
-                                                                            err, nullptr, 1.0f, nullptr);
+                                                                            err, nullptr, 1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
+    DSANLS_LAUNCH_CHECK();
+    k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
+    DSANLS_LAUNCH_CHECK();
+}
+
+void launch_tc_sketch_rhs_regen(const __nv_bfloat16 *X, const float *B, int64_t rows, int64_t K, int64_t d, int k,
+                                uint64_t seed, uint32_t side, const int64_t *t_dev, float scale, float *Rpart,
+                                float *R, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || d > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0 || d % 8 != 0) throw ArgError{"tensor-core path needs K and d multiples of 8"};
+    const int kp = kp_of(k);
+    const int nchunks = (int)ceil_div(d, BN);
+    __nv_bfloat16 *Bb = reinterpret_cast<__nv_bfloat16 *>(
+        (reinterpret_cast<uintptr_t>(Rpart + (int64_t)nchunks * rows * k) + 15) & ~(uintptr_t)15);
+    k_to_bf16<<<(unsigned)ceil_div((int64_t)k * d, 256), 256, 0, s>>>(B, (int64_t)k * d, Bb);
+    DSANLS_LAUNCH_CHECK();
+    const CUtensorMap mx = make_map(X, rows, K, BM);
+    const CUtensorMap mb = make_map(Bb, k, d, kp);
+    const int64_t tiles = ceil_div(rows, BM) * nchunks;
+    const int stages = stages_for(kp);
+    const size_t smem = smem_bytes(stages, kp);
+    if (stages == 4)
+        k_tc_gemm<4, true, false, BN, 1, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(
+            mx, mx, mb, mx, mx, mx, mx, rows, K, d, k, kp, 0, Rpart, err, nullptr, 1.0f, nullptr, seed, side, t_dev,
+            scale);
+    else
+        k_tc_gemm<3, true, false, BN, 1, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(
+            mx, mx, mb, mx, mx, mx, mx, rows, K, d, k, kp, 0, Rpart, err, nullptr, 1.0f, nullptr, seed, side, t_dev,
+            scale);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
     DSANLS_LAUNCH_CHECK();
@@ -511,10 +586,10 @@ void launch_tc_sketch_rhs_fp8(const uint8_t *Xq, const float *row_scale, const u
     const size_t smem = smem_bytes(stages, kp);
     if (stages == 4)
         k_tc_gemm<4, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
-                                                                           err, row_scale, s_scale, nullptr);
+                                                                           err, row_scale, s_scale, nullptr, 0ull, 0u, nullptr, 0.0f);
     else
         k_tc_gemm<3, true, true><<<(unsigned)tiles, TC_THREADS, smem, s>>>(mx, ms, mb, mx, mx, ms, ms, rows, K, d, k, kp, 0, Rpart,
-                                                                           err, row_scale, s_scale, nullptr);
+                                                                           err, row_scale, s_scale, nullptr, 0ull, 0u, nullptr, 0.0f);
     DSANLS_LAUNCH_CHECK();
     k_reduce_chunks<<<(unsigned)ceil_div(rows * k, 256), 256, 0, s>>>(Rpart, nchunks, rows, k, R);
     DSANLS_LAUNCH_CHECK();
@@ -561,7 +636,21 @@ void launch_tc_gemm(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int64_t row
     const CUtensorMap ms = make_map(St, d, K, BN);
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, mx, mx, ms, ms, rows, K, d, 0, 0,
-                                                                         p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
+                                                                         p.kb_per_split, part, err, nullptr, 1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
+    DSANLS_LAUNCH_CHECK();
+    launch_split_reduce(part, rows * d, p.splits, rows, d, d, C, d, s);
+}
+
+void launch_tc_gemm_regen(const __nv_bfloat16 *X, int64_t rows, int64_t K, int64_t d, uint64_t seed, uint32_t side,
+                         const int64_t *t_dev, float scale, float *part, float *C, int *err, cudaStream_t s) {
+    if (rows > (1ll << 31) - 1 || K > (1ll << 31) - 1 || d > (1ll << 31) - 1) throw ArgError{"sizes too large"};
+    if (K % 8 != 0 || d % 8 != 0) throw ArgError{"tensor-core path needs K and d multiples of 8"};
+    const PlainPlan p = plan_one_wave(rows, K, d, BN);
+    const CUtensorMap mx = make_map(X, rows, K, BM);
+    dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
+    k_tc_gemm<4, false, false, BN, 1, true><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(
+        mx, mx, mx, mx, mx, mx, mx, rows, K, d, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr, seed, side,
+        t_dev, scale);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * d, p.splits, rows, d, d, C, d, s);
 }
@@ -590,7 +679,7 @@ void launch_tc_gemm_bf16out(const __nv_bfloat16 *X, const __nv_bfloat16 *St, int
     const CUtensorMap ms = make_map(St, N, K, BN);
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     k_tc_gemm<4, false, false><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(mx, ms, mx, mx, mx, ms, ms, rows, K, N, 0, 0,
-                                                                         p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
+                                                                         p.kb_per_split, part, err, nullptr, 1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
     DSANLS_LAUNCH_CHECK();
     k_split_reduce_bf16<<<(unsigned)ceil_div(rows * N, 256), 256, 0, s>>>(part, p.splits, rows * N, C);
     DSANLS_LAUNCH_CHECK();
@@ -613,10 +702,10 @@ void launch_tc_skinny(const __nv_bfloat16 *X, const __nv_bfloat16 *Pt, int64_t r
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     if (bnt == 64)
         k_tc_gemm<4, false, false, 64><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
-            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
     else
         k_tc_gemm<3, false, false, 128><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
-            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr, 1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
 }
@@ -638,10 +727,10 @@ void launch_tc_skinny_fp8(const uint8_t *Xq, const float *xscale, const uint8_t 
     dim3 grid((unsigned)p.tiles, (unsigned)p.splits);
     if (bnt == 64)
         k_tc_gemm<4, false, true, 64><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
-            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale, 0ull, 0u, nullptr, 0.0f);
     else
         k_tc_gemm<3, false, true, 128><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
-            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale);
+            mx, mp, mx, mx, mx, mp, mp, rows, K, k, 0, 0, p.kb_per_split, part, err, xscale, 1.0f, pscale, 0ull, 0u, nullptr, 0.0f);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
 }
@@ -787,7 +876,7 @@ void launch_tc_gemm_split3(const __nv_bfloat16 *const X3[3], const __nv_bfloat16
     float *dst = p.splits > 1 ? part : C;
     k_tc_gemm<4, false, false, BN, 6><<<grid, TC_THREADS, smem_bytes(4, 0), s>>>(
         mx[0], ms[0], mx[0], mx[1], mx[2], ms[1], ms[2], rows, K, N, 0, 0, p.kb_per_split, dst, err, nullptr, 1.0f,
-        nullptr);
+        nullptr, 0ull, 0u, nullptr, 0.0f);
     DSANLS_LAUNCH_CHECK();
     if (p.splits > 1) launch_split_reduce(part, rows * N, p.splits, rows, N, N, C, N, s);
 }
@@ -821,11 +910,11 @@ void launch_tc_skinny_split3(const __nv_bfloat16 *const X3[3], const __nv_bfloat
     if (bnt == 64)
         k_tc_gemm<4, false, false, 64, 6><<<grid, TC_THREADS, smem_bytes(4, 0, 64), s>>>(
             mx[0], mp[0], mx[0], mx[1], mx[2], mp[1], mp[2], rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr,
-            1.0f, nullptr);
+            1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
     else
         k_tc_gemm<3, false, false, 128, 6><<<grid, TC_THREADS, smem_bytes(3, 0, 128), s>>>(
             mx[0], mp[0], mx[0], mx[1], mx[2], mp[1], mp[2], rows, K, k, 0, 0, p.kb_per_split, part, err, nullptr,
-            1.0f, nullptr);
+            1.0f, nullptr, 0ull, 0u, nullptr, 0.0f);
     DSANLS_LAUNCH_CHECK();
     launch_split_reduce(part, rows * k, p.splits, rows, k, k, R, k, s);
 }
@@ -1155,6 +1244,9 @@ void prime_tc_attributes(int max_smem) {
     allow_max_dynamic_smem(k_tc_gemm<3, false, false, 128>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, true, 64>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, false, BN, 6>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, true, false, BN, 1, true>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<3, true, false, BN, 1, true>, max_smem);
+    allow_max_dynamic_smem(k_tc_gemm<4, false, false, BN, 1, true>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, false, 64, 6>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, false, false, 128, 6>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, false, true, 128>, max_smem);

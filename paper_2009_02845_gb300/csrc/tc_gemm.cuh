@@ -16,6 +16,15 @@ int64_t tc_rpart_elems(int64_t rows, int64_t d, int k);
 // bounded wait that gives up sets bit 2 of *err.  K and d must be multiples of 8.
 void launch_tc_sketch_rhs(const __nv_bfloat16 *X, const __nv_bfloat16 *St, const float *B, int64_t rows, int64_t K,
                           int64_t d, int k, float *Rpart, float *R, int *err, cudaStream_t s);
+// The same with the Gaussian sketch drawn inside the GEMM (warps 2-7 compute each
+// S^T tile from the Philox field of (seed, side, t from t_dev), entries bf16(z scale),
+// bitwise the sketch pre-pass's values) instead of read by TMA.
+void launch_tc_sketch_rhs_regen(const __nv_bfloat16 *X, const float *B, int64_t rows, int64_t K, int64_t d, int k,
+                                uint64_t seed, uint32_t side, const int64_t *t_dev, float scale, float *Rpart,
+                                float *R, int *err, cudaStream_t s);
+// C (rows x d, fp32) = X S with the Gaussian S drawn inside the GEMM as above (B = Y^T S).
+void launch_tc_gemm_regen(const __nv_bfloat16 *X, int64_t rows, int64_t K, int64_t d, uint64_t seed, uint32_t side,
+                          const int64_t *t_dev, float scale, float *part, float *C, int *err, cudaStream_t s);
 // The same with X and S^T in fp8 E4M3: X = Xq * row_scale[row / 128], S = Sq * s_scale
 // (K a multiple of 16, d of 8).
 void launch_tc_sketch_rhs_fp8(const uint8_t *Xq, const float *row_scale, const uint8_t *Sq, float s_scale,

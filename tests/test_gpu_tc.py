@@ -177,3 +177,22 @@ def test_fp8_columns_of_very_different_scale(pkg):
         S = method.Sketch(method.GAUSSIAN, 29, 2, side, X.shape[1], d)
         rel, rb = bounds.check(got, X, Y, Z, S, method.PGD, method.mu_t(1.0, 1.0, 2), "fp8")
         assert rel <= rb, (side, rel, rb)
+
+
+@pytest.mark.parametrize("case", [(1000, 808, 10, 104, 96), (640, 520, 64, 520, 264), (136, 200, 32, 2048, 64)])
+def test_sketch_drawn_inside_the_gemm_is_bitwise_the_prepass(pkg, case):
+    """regen_sketch = 1 draws the Gaussian S^T tiles inside the tensor-core GEMMs
+    (B = Y^T S and the fused R = (X S) B^T) from the Philox field instead of
+    reading the sketch pre-pass through TMA: the tiles are the same bf16 values,
+    so three outer iterations give bitwise equal factors."""
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, min(k, 16), 3)
+    out = []
+    for regen in (0, 1):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=31, d_v=d_v, precision=pkg.BF16, regen_sketch=regen,
+                       use_graph=1)
+        h.set_dense(M)
+        h.step(3)
+        out.append(h.factors())
+        h.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
