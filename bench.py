@@ -505,6 +505,19 @@ def run_ours(args, w):
                        "get_factors to host"}
         del Mp
 
+    traj = None
+    if rank == 0 and args.trajectory > 0:
+        ht = pkg.DSANLS(m, n, k, d, w["sketch"], seed=rank, d_v=d_v, solver=solver, precision=prec, use_graph=1,
+                        order=order, alpha=args.alpha, beta=args.beta, inner_iters=args.inner_iters)
+        _set_data(ht, M)
+        every = max(1, args.trajectory // 10)
+        traj = [(0, ht.rel_error())]
+        for it in range(1, args.trajectory + 1):
+            ht.step(1)
+            if it % every == 0 or it == args.trajectory:
+                traj.append((it, ht.rel_error()))
+        ht.close()
+
     tte = None
     if rank == 0 and args.time_to_eps > 0 and w["sketch"] == 0:
         tte = time_to_eps(pkg, torch, M, w, args.time_to_eps, 5, stream)
@@ -532,6 +545,7 @@ def run_ours(args, w):
             "phases_ms": {"U": {k_: round(v_, 4) for k_, v_ in phases[0].items()},
                           "V": {k_: round(v_, 4) for k_, v_ in phases[1].items()}},
             "rel_error_after": err,
+            "rel_error_trajectory": traj,
             "time_to_eps": tte,
         }
         print(json.dumps(line), flush=True)
@@ -562,6 +576,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned workload")
+    ap.add_argument("--trajectory", type=int, default=0,
+                    help="also run T outer iterations on a fresh handle and report the relative error every "
+                         "T/10 iterations (untimed)")
     ap.add_argument("--time-to-eps", type=int, default=100,
                     help="also run T outer iterations of the fp32 and bf16 forms and report time to eps")
     args = ap.parse_args()
