@@ -228,14 +228,72 @@ def oracle_sample(M, w, seed, rows_budget):
 
 
 def _cores():
+    """Host cores this process may run on (what `nproc` prints)."""
     try:
-        from threadpoolctl import threadpool_info
-        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
-        if n:
-            return int(max(n))
+        return len(os.sched_getaffinity(0))
     except Exception:
+        return os.cpu_count() or 1
+
+
+def _openblas_libs():
+    """The OpenBLAS libraries loaded into this process (numpy's and scipy's)."""
+    import ctypes
+    paths = set()
+    try:
+        with open("/proc/self/maps") as f:
+            for line in f:
+                part = line.split()
+                if len(part) >= 6 and "openblas" in part[-1].lower() and part[-1].startswith("/"):
+                    paths.add(part[-1])
+    except OSError:
         pass
-    return os.cpu_count() or 1
+    libs = []
+    for path in sorted(paths):
+        try:
+            libs.append(ctypes.CDLL(path))
+        except OSError:
+            pass
+    return libs
+
+
+_BLAS_PREFIXES = ("scipy_openblas", "openblas")
+_BLAS_SUFFIXES = ("64_", "")
+
+
+def _blas_call(libs, what, *args):
+    out = []
+    for lib in libs:
+        for pre in _BLAS_PREFIXES:
+            for suf in _BLAS_SUFFIXES:
+                fn = getattr(lib, "%s_%s%s" % (pre, what, suf), None)
+                if fn is not None:
+                    out.append(fn(*args))
+                    break
+            else:
+                continue
+            break
+    return out
+
+
+def _blas_threads():
+    n = _blas_call(_openblas_libs(), "get_num_threads")
+    return int(max(n)) if n else None
+
+
+def oracle_single_thread(M, w, seed, rows_budget):
+    """The same bounded oracle sample with the BLAS limited to one thread (the
+    rest of the oracle is single-threaded already); None when no OpenBLAS is
+    loaded to limit."""
+    libs = _openblas_libs()
+    before = _blas_call(libs, "get_num_threads")
+    if not before:
+        return None
+    _blas_call(libs, "set_num_threads", 1)
+    try:
+        v, desc = oracle_sample(M, w, seed, rows_budget)
+    finally:
+        _blas_call(libs, "set_num_threads", int(max(before)))
+    return {"value": v, "unit": UNIT, "cores": 1, "sample": desc}
 
 
 def run_reference(args, w):
@@ -253,13 +311,19 @@ def run_reference(args, w):
         vals.append(v)
     wall = time.perf_counter() - t0
     value = float(statistics.mean(vals))
+    single = oracle_single_thread(M, w, 0, min(rows, 128))
+    # a step is the timed row sample: ms_per_step is its measured wall time, and
+    # value the full iteration's rate extrapolated from it
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "value_source": "extrapolated in rows from the timed sample (ms_per_step is the sample's wall time)",
+        "ms_per_full_iteration": 1000.0 / value,
         "config": {"workload": args.workload, "desc": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"],
                    "d": w["d"], "d_v": w["d_v"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "blas_threads": _blas_threads(),
+                         "kind": "oracle", "sample": desc, "single_thread": single},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }
@@ -526,7 +590,8 @@ def run_ours(args, w):
     if rank == 0 and not args.no_cpu_baseline:
         rows = (20000 if w.get("sparse") else 512) if m > 10000 else m
         v, desc = oracle_sample(M, w, rank, rows)
-        cpu = {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": UNIT, "cores": _cores(), "blas_threads": _blas_threads(), "kind": "oracle",
+               "sample": desc, "single_thread": oracle_single_thread(M, w, rank, min(rows, 128))}
 
     h.close()
     if rank == 0:

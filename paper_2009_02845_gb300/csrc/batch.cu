@@ -607,7 +607,7 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
         mark(1);
         launch_batch_b_tc(g, side, cfg.tc_b_ctas, ctr + 0, s);
         mark(2);
-        launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_ctas, ctr + 1, s);
+        launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_stages, cfg.tc_ctas, ctr + 1, s);
         mark(3);
         kb_gram<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, count, ctr + 2, side, g.B, g.alpha, g.beta,
                                                      g.power_iters, g.t_dev, g.G);

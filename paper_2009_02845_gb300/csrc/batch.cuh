@@ -54,6 +54,7 @@ struct BatchLaunch {
     int persistent_blocks = 152 * 4;
     int sketch_blocks = 152 * 8;
     int tc_nc = 128;    // sketch columns per chunk of the tensor-core product (64, 128, 256)
+    int tc_stages = 4;  // cp.async ring stages of the tensor-core product (3 or 4)
     int tc_ctas = 304;  // persistent CTAs of the tensor-core product
     int tc_b_ctas = 304;  // persistent CTAs of B = Y^T S on tensor cores
 };
@@ -70,10 +71,11 @@ void batch_init_factors(const BatchInst *inst, int count, float *factors, cudaSt
 void batch_build_tc_items(const std::vector<BatchInst> &h, int side, std::vector<int2> &tcitems,
                           std::vector<int2> &tcbitems);
 // batch_tc.cu
-size_t batch_tc_smem(int nc);
+size_t batch_tc_smem(int nc, int stages);
 void batch_prime_tc(int max_smem);
-int batch_tc_ctas_per_sm(int nc);
-void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int ctas, int *counter, cudaStream_t s);
+int batch_tc_ctas_per_sm(int nc, int stages);
+int batch_tc_b_ctas_per_sm();
+void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int stages, int ctas, int *counter, cudaStream_t s);
 void launch_batch_sketch_t(const BatchDev &g, int side, cudaStream_t s);
 // B_i = Y_i^T S_i on tensor cores (padded bf16 Y_i^T first); counter: a cleared queue counter
 void launch_batch_b_tc(const BatchDev &g, int side, int ctas, int *counter, cudaStream_t s);

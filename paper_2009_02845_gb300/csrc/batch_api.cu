@@ -122,7 +122,7 @@ std::string tune_key(const dsanls_batch_ctx *b) {
     }
     std::sort(shapes.begin(), shapes.end());
     const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "") +
-                             (b->g.tc ? "tc" : "");
+                             (b->g.tc ? "tc2" : "");
     std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
     return std::to_string(std::hash<std::string>()(key)) + "/" + form;
@@ -170,14 +170,16 @@ void cache_store(const std::string &key, int value) {
 }
 
 // A tuned configuration: per-SM persistent CTAs of the CUDA-core kernels, plus
-// (tensor-core form) 1000 x that + the chunk width of the tensor-core product.
+// (tensor-core form) 10000 x that + 1000 x the ring stages + the chunk width of
+// the tensor-core product.
 void apply_config(dsanls_batch_ctx *b, int code, int sms) {
-    const int per_sm = code >= 1000 ? code / 1000 : code;
+    const int per_sm = code >= 10000 ? code / 10000 : code;
     b->cfg.persistent_blocks = 152 * per_sm;
-    if (code >= 1000) {
+    if (code >= 10000) {
+        b->cfg.tc_stages = (code / 1000) % 10;
         b->cfg.tc_nc = code % 1000;
-        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc);
-        b->cfg.tc_b_ctas = sms * batch_tc_ctas_per_sm(64);
+        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc, b->cfg.tc_stages);
+        b->cfg.tc_b_ctas = sms * batch_tc_b_ctas_per_sm();
     }
 }
 
@@ -204,8 +206,10 @@ void autotune(dsanls_batch_ctx *b) {
         // shared memory, tensor-memory columns and CTAs per SM
         std::vector<int> candidates;
         if (b->g.tc) {
-            for (int nc : {64, 128, 256})
-                for (int c : {2, 4}) candidates.push_back(c * 1000 + nc);
+            // (chunk, stages): 64/4 and 128/3 fit two CTAs per SM, 128/4 and 256/4 one
+            const int tiles[4][2] = {{64, 4}, {128, 3}, {128, 4}, {256, 4}};
+            for (const auto &tl : tiles)
+                for (int c : {2, 4}) candidates.push_back(c * 10000 + tl[1] * 1000 + tl[0]);
         } else {
             candidates = {1, 2, 4, 8};
         }

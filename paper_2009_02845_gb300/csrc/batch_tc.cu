@@ -40,33 +40,34 @@ constexpr int TB_BM = 128;
 constexpr int TB_BK = 64;
 constexpr int TB_THREADS = 256;
 constexpr int TB_KP = 32;  // rows of the B tile (k <= 32 padded)
-constexpr int TB_STAGES = 4;
+constexpr int TB_MAX_STAGES = 4;
 constexpr unsigned long long TB_WAIT_NS = 2000000000ull;
 
 __host__ __device__ constexpr int tb_stage_bytes(int nc) { return TB_BM * TB_BK * 2 + nc * TB_BK * 2; }
 __host__ __device__ constexpr uint32_t tb_tmem_cols(int nc) { return nc + TB_KP <= 128 ? 128u : (nc + TB_KP <= 256 ? 256u : 512u); }
 
 struct __align__(8) TbTail {
-    uint64_t stage_done[TB_STAGES];
+    uint64_t stage_done[TB_MAX_STAGES];
     uint64_t d1_done;
     uint64_t d2_done;
     uint32_t tmem_base;
     int item;
 };
 
-__host__ __device__ constexpr size_t tb_smem(int nc) {
-    return 1024 + TB_STAGES * (size_t)tb_stage_bytes(nc) + (size_t)(nc / 64) * TB_KP * 128 + sizeof(TbTail);
+__host__ __device__ constexpr size_t tb_smem(int nc, int st) {
+    return 1024 + st * (size_t)tb_stage_bytes(nc) + (size_t)(nc / 64) * TB_KP * 128 + sizeof(TbTail);
 }
 
 DSANLS_DEV int64_t pad8(int64_t x) { return (x + 7) & ~(int64_t)7; }
 
-template <int NC, bool PLAIN>
+template <int NC, bool PLAIN, int TB_STAGES>
 __global__ void __launch_bounds__(TB_THREADS)
     kb_ar_tc(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
              int side, const __nv_bfloat16 *__restrict__ data_p, const __nv_bfloat16 *__restrict__ St_all,
              const __nv_bfloat16 *__restrict__ Yt_all, float *__restrict__ B_all, float *__restrict__ R_all,
              int *__restrict__ flag) {
     static_assert(NC == 64 || NC == 128 || NC == 256, "chunk of 64, 128 or 256 columns");
+    static_assert(TB_STAGES >= 2 && TB_STAGES <= TB_MAX_STAGES, "2 to 4 stages");
     constexpr int SB = tb_stage_bytes(NC);
     constexpr uint32_t TCOLS = tb_tmem_cols(NC);
     extern __shared__ __align__(1024) uint8_t tb_smem_raw[];
@@ -336,42 +337,59 @@ __global__ void kb_pad_bf16(const BatchInst *__restrict__ inst, const float *__r
 
 }  // namespace
 
-size_t batch_tc_smem(int nc) { return tb_smem(nc); }
+size_t batch_tc_smem(int nc, int st) { return tb_smem(nc, st); }
 
 void batch_prime_tc(int max_smem) {
-    allow_max_dynamic_smem(kb_ar_tc<64, false>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<128, false>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<256, false>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<64, true>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<64, false, 4>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<128, false, 4>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<128, false, 3>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<256, false, 4>, max_smem);
+    allow_max_dynamic_smem(kb_ar_tc<64, true, 4>, max_smem);
 }
 
-int batch_tc_ctas_per_sm(int nc) {
+namespace {
+const void *ar_kernel(int nc, int st) {
+    if (nc == 64) return (const void *)kb_ar_tc<64, false, 4>;
+    if (nc == 128) return st == 3 ? (const void *)kb_ar_tc<128, false, 3> : (const void *)kb_ar_tc<128, false, 4>;
+    return (const void *)kb_ar_tc<256, false, 4>;
+}
+}  // namespace
+
+int batch_tc_ctas_per_sm(int nc, int st) {
     int per_sm = 1;
-    const void *f = nc == 64 ? (const void *)kb_ar_tc<64, false>
-                             : (nc == 128 ? (const void *)kb_ar_tc<128, false> : (const void *)kb_ar_tc<256, false>);
-    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, TB_THREADS, tb_smem(nc)));
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ar_kernel(nc, st), TB_THREADS, tb_smem(nc, st)));
     // tensor memory: 512 columns per SM
     return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(nc))));
 }
 
-void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int ctas, int *counter, cudaStream_t s) {
+int batch_tc_b_ctas_per_sm() {
+    int per_sm = 1;
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_ar_tc<64, true, 4>, TB_THREADS,
+                                                              tb_smem(64, 4)));
+    return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(64))));
+}
+
+void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int st, int ctas, int *counter, cudaStream_t s) {
     if (nc == 64)
-        kb_ar_tc<64, false><<<ctas, TB_THREADS, tb_smem(64), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter, side,
-                                                                   g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
+        kb_ar_tc<64, false, 4><<<ctas, TB_THREADS, tb_smem(64, 4), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
+                                                                         side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
+    else if (nc == 128 && st == 3)
+        kb_ar_tc<128, false, 3><<<ctas, TB_THREADS, tb_smem(128, 3), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
+                                                                           side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     else if (nc == 128)
-        kb_ar_tc<128, false><<<ctas, TB_THREADS, tb_smem(128), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
-                                                                     side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
+        kb_ar_tc<128, false, 4><<<ctas, TB_THREADS, tb_smem(128, 4), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
+                                                                           side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     else
-        kb_ar_tc<256, false><<<ctas, TB_THREADS, tb_smem(256), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
-                                                                     side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
+        kb_ar_tc<256, false, 4><<<ctas, TB_THREADS, tb_smem(256, 4), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
+                                                                           side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     DSANLS_LAUNCH_CHECK();
 }
 
 void launch_batch_b_tc(const BatchDev &g, int side, int ctas, int *counter, cudaStream_t s) {
     kb_yt<<<dim3(4, (unsigned)g.count), 256, 0, s>>>(g.inst, side, g.factors, g.Yt);
     DSANLS_LAUNCH_CHECK();
-    kb_ar_tc<64, true><<<ctas, TB_THREADS, tb_smem(64), s>>>(g.inst, g.tcbitems[side], g.ntcb[side], counter, side,
-                                                              g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
+    kb_ar_tc<64, true, 4><<<ctas, TB_THREADS, tb_smem(64, 4), s>>>(g.inst, g.tcbitems[side], g.ntcb[side], counter, side,
+                                                                    g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     DSANLS_LAUNCH_CHECK();
 }
 

@@ -926,23 +926,25 @@ void launch_tc_skinny_split3(const __nv_bfloat16 *const X3[3], const __nv_bfloat
 // z_l = bf16(z - z_h - z_m) (each difference exact in binary32): the six
 // products z_i g_j with i + j <= 2 accumulate in fp32 in TMEM, and the dropped
 // terms are of order 2^-24 |z| |g|, the rounding level of a binary32 product.
-// Persistent: a CTA splits G once into the three B operands (N = k rounded up
-// to 16 rows, K = k rounded up to 64, 128-byte swizzled K-major), then walks
-// 128-row tiles of Z: the CTA's 512 threads split the tile into the three A
-// operands (written from coalesced flat reads of the nr x k contiguous floats,
-// zeros in the padding), thread 0 issues the 6 x (K / 16) MMAs and commits,
-// the accumulator is moved from TMEM into an fp32 staging tile over the A
-// operands, and the step is applied with the exact binary32 z (kept in
-// registers since the split) and r (loaded while the products run), stored in
-// the same coalesced flat order.
+//
+// Persistent, one CTA per SM.  The CTA splits G once into the three B operands
+// in shared memory (N = k rounded up to 16 rows, K = k rounded up to 64,
+// 128-byte swizzled K-major), then walks 128-row tiles of Z.  A tile of Z is
+// nr x k contiguous elements; it arrives in shared memory by one bulk copy,
+// issued two tiles ahead into a double buffer, so the reads of Z are in flight
+// while earlier tiles are computed.  Thread (row, slice) owns one row of the
+// tile and 32 consecutive columns: it reads its z from the buffer, writes the
+// split parts straight into tensor memory as the A operand (row i in lane i),
+// starts its loads of r, and after the MMAs (issued by one thread) reads its 32
+// accumulator columns back, applies the step and stores the row slice of Z.
+// Nothing of the tile passes through shared memory but the z read once.
 namespace {
 
 constexpr int UPD_BM = 128;
-constexpr int UPD_THREADS = 512;
-constexpr int UPD_UNROLL = 8;  // float4 groups per thread: 8 x 512 x 4 = 128 x 128 floats
 
 struct __align__(8) UpdTail {
-    uint64_t done;
+    uint64_t full[2];  // the Z tile in buffer 0 / 1 has landed (bulk copy bytes)
+    uint64_t done;     // the tile's MMAs have retired
     uint64_t fin;
     uint32_t tmem_base;
     uint32_t pad;
@@ -958,38 +960,77 @@ DSANLS_DEV float upd_project(float v, float bound, int *flag) {
     return r;
 }
 
+DSANLS_DEV uint32_t bf16_bits(__nv_bfloat16 v) { return (uint32_t)__bfloat16_as_ushort(v); }
+
 // Z of type ZT: binary32, or bf16 for the bf16-factor form -- z is then exactly
 // a bf16 value (z_m = z_l = 0), so only the three products z_h g_j are issued,
 // and the step's binary32 result is rounded to bf16 when it is stored.
-DSANLS_DEV float4 load_z4(const float *Z, int64_t f0, int g) { return __ldcs(reinterpret_cast<const float4 *>(Z + f0) + g); }
-DSANLS_DEV float4 load_z4(const __nv_bfloat16 *Z, int64_t f0, int g) {
-    const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(Z + f0) + g);
-    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
-                       __uint_as_float(u.y & 0xffff0000u));
+// The 32 elements of a row slice, `n` of them valid (the rest read as 0), from
+// shared or global memory; vectorised when the row start is 16 / 8 bytes aligned.
+DSANLS_DEV void load_slice(const float *p, int n, bool vec, float (&z)[32]) {
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * j < n) v = *reinterpret_cast<const float4 *>(p + 4 * j);
+            z[4 * j] = v.x, z[4 * j + 1] = v.y, z[4 * j + 2] = v.z, z[4 * j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) z[j] = j < n ? p[j] : 0.0f;
+    }
 }
-DSANLS_DEV void store_z4(float *Z, int64_t f0, int g, float4 v) { __stcs(reinterpret_cast<float4 *>(Z + f0) + g, v); }
-DSANLS_DEV void store_z4(__nv_bfloat16 *Z, int64_t f0, int g, float4 v) {
-    __stcs(reinterpret_cast<uint2 *>(Z + f0) + g, make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w)));
+DSANLS_DEV void load_slice(const __nv_bfloat16 *p, int n, bool vec, float (&z)[32]) {
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            uint2 u = make_uint2(0u, 0u);
+            if (4 * j < n) u = *reinterpret_cast<const uint2 *>(p + 4 * j);
+            z[4 * j] = __uint_as_float(u.x << 16), z[4 * j + 1] = __uint_as_float(u.x & 0xffff0000u);
+            z[4 * j + 2] = __uint_as_float(u.y << 16), z[4 * j + 3] = __uint_as_float(u.y & 0xffff0000u);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) z[j] = j < n ? __bfloat162float(p[j]) : 0.0f;
+    }
+}
+DSANLS_DEV void store4(float *p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+DSANLS_DEV void store4(__nv_bfloat16 *p, float a, float b, float c, float d) {
+    *reinterpret_cast<uint2 *>(p) = make_uint2(pack_bf16(a, b), pack_bf16(c, d));
 }
 
-template <int KA, typename ZT>  // K atoms of 64 columns: 1 for k <= 64, 2 for k <= 128
-__global__ void __launch_bounds__(UPD_THREADS)
+template <int KA>  // K atoms of 64 columns: 1 for k <= 64, 2 for k <= 128
+__host__ __device__ constexpr int upd_threads() {
+    return KA * 256;  // 128 rows x (64 KA / 32) column slices
+}
+
+template <int KA, typename ZT>
+__global__ void __launch_bounds__(upd_threads<KA>())
     k_update_tc(ZT *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k, int N,
                 const float *__restrict__ Gf, int kp, const double *__restrict__ scal, float bound,
-                int *__restrict__ flag, uint32_t tmem_cols) {
+                int *__restrict__ flag, uint32_t tmem_cols, int zbuf_bytes, int use_bulk) {
     constexpr bool ZBF = sizeof(ZT) == 2;
     constexpr int ZPARTS = ZBF ? 1 : 3;  // nonzero parts of the split of z
+    constexpr int THREADS = upd_threads<KA>();
+    constexpr int KC = KA * 64;          // padded K
+    constexpr int ACOL = KA * 64;        // TMEM: accumulator in columns [0, N), the A parts from ACOL
     extern __shared__ uint8_t upd_smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(upd_smem_raw) + 1023) & ~uintptr_t(1023));
-    constexpr int KC = KA * 64;  // padded K
-    const int b_part = KA * N * 128, a_part = KA * UPD_BM * 128;
-    uint8_t *Bp = base;               // 3 parts x KA atoms x N rows x 128 B
-    uint8_t *Ap = Bp + 3 * b_part;    // 3 parts x KA atoms x 128 rows x 128 B; the fp32 staging of Z G after the MMAs
-    float *stage = reinterpret_cast<float *>(Ap);
-    const int lds = N + 1;            // staging row stride (odd: conflict-free column writes)
-    UpdTail *tail = reinterpret_cast<UpdTail *>(Ap + 3 * a_part);
+    const int b_part = KA * N * 128;
+    uint8_t *Bp = base;  // 3 parts x KA atoms x N rows x 128 B
+    ZT *zbuf[2] = {reinterpret_cast<ZT *>(Bp + 3 * b_part), reinterpret_cast<ZT *>(Bp + 3 * b_part + zbuf_bytes)};
+    UpdTail *tail = reinterpret_cast<UpdTail *>(Bp + 3 * b_part + 2 * zbuf_bytes);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, cw = warp >> 2;  // TMEM lane quarter and 32-column slice of this warp
+    const int row = 32 * q + lane, c0 = 32 * cw;
+    const int ncol = min(32, k - c0);  // valid columns of the slice (<= 0: padding only)
+    const bool vec = (k & 3) == 0;
+    const size_t es = sizeof(ZT);
     if (tid == 0) {
+        mbar_init(&tail->full[0], 1);
+        mbar_init(&tail->full[1], 1);
         mbar_init(&tail->done, 1);
         mbar_init(&tail->fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1002,7 +1043,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // the three parts of G: B row n, K column c holds G[n][c] (G is symmetric)
-    for (int e = tid; e < N * KC; e += UPD_THREADS) {
+    for (int e = tid; e < N * KC; e += THREADS) {
         const int n = e / KC, c = e % KC;
         const float g = (n < k && c < k) ? Gf[n * kp + c] : 0.0f;
         __nv_bfloat16 h, m, l;
@@ -1017,161 +1058,145 @@ __global__ void __launch_bounds__(UPD_THREADS)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tail->tmem_base;
+    const uint32_t tlane = (uint32_t)(32 * q) << 16;
     const float eta = (float)scal[2];
     const uint32_t idesc = idesc_bf16(UPD_BM, N);
+    const int KS = (k + 15) >> 4;  // K steps of 16 that hold data
     const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
-    const bool vec = (k & 3) == 0;
-    const int q = warp & 3, cw = warp >> 2;  // TMEM lane quarter and 32-column slice of this warp
-    uint32_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int64_t r0 = tile * UPD_BM;
-        const int nr = (int)min((int64_t)UPD_BM, rows - r0);
-        const int64_t f0 = r0 * k;  // the tile is nr * k contiguous floats of Z and of R
-        const int nf = nr * k;
-        // 1. the three A parts: the tile's entries (coalesced flat reads, every load of
-        //    a thread in flight before the first is used), then zeros in the padding
-        //    columns k..KC-1 and in the rows past the end of Z
-        // the tile's z stay in registers for the step (the flat mapping of the
-        // split and of the step is the same), r is loaded while the products run
-        float4 zz[UPD_UNROLL], rr[UPD_UNROLL];
-        if (vec) {
-#pragma unroll
-            for (int j = 0; j < UPD_UNROLL; ++j) {
-                const int g = tid + j * UPD_THREADS;
-                if (4 * g < nf) zz[j] = load_z4(Z, f0, g);
+    // tile j of this CTA and whether it comes by bulk copy (every tile but a
+    // ragged last one whose byte count is not a multiple of 16)
+    auto tile_of = [&](int64_t j) { return (int64_t)blockIdx.x + j * gridDim.x; };
+    auto nrows = [&](int64_t t) { return (int)min((int64_t)UPD_BM, rows - t * UPD_BM); };
+    auto by_bulk = [&](int64_t t) { return use_bulk && (((int64_t)nrows(t) * k * (int64_t)es) & 15) == 0; };
+    uint32_t armed = 0;  // thread 0: buffers with a copy in flight
+    auto issue = [&](int64_t j) {
+        const int64_t t = tile_of(j);
+        if (t >= ntiles || !by_bulk(t)) return;
+        const int b = (int)(j & 1);
+        const uint32_t bytes = (uint32_t)((int64_t)nrows(t) * k * (int64_t)es);
+        mbar_expect_tx(&tail->full[b], bytes);
+        bulk_load(zbuf[b], Z + t * UPD_BM * (int64_t)k, bytes, &tail->full[b]);
+        armed |= 1u << b;
+    };
+    if (tid == 0) {
+        issue(0);
+        issue(1);
+    }
+    uint32_t phase = 0;  // bit b: parity of the next completion of full[b]
+    for (int64_t j = 0;; ++j) {
+        const int64_t tile = tile_of(j);
+        if (tile >= ntiles) break;
+        const int b = (int)(j & 1);
+        const int nr = nrows(tile);
+        const int64_t f0 = tile * UPD_BM * (int64_t)k;
+        const bool rowok = row < nr;
+        const int nv = rowok ? ncol : 0;  // valid entries of this thread's slice
+        // 1. r of the row slice: in flight while z is split and the products run
+        float rv[32];
+        load_slice(R + f0 + (int64_t)row * k + c0, nv, vec, rv);
+        // 2. z of the row slice, from the bulk-copied buffer (or from Z for a ragged
+        //    last tile); the split parts go to tensor memory as the A operand
+        bool ok = true;
+        const bool bulk = by_bulk(tile);
+        if (bulk) {
+            ok = mbar_wait(&tail->full[b], (phase >> b) & 1, wait_limit());
+            if (ok) {
+                phase ^= 1u << b;
+                if (tid == 0) armed &= ~(1u << b);
             }
-#pragma unroll
-            for (int j = 0; j < UPD_UNROLL; ++j) {
-                const int g = tid + j * UPD_THREADS;
-                if (4 * g >= nf) continue;
-                const float zv[4] = {zz[j].x, zz[j].y, zz[j].z, zz[j].w};
-                int r = (4 * g) / k, c = 4 * g - r * k;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    __nv_bfloat16 h, m, l;
-                    split3_one(zv[e], h, m, l);
-                    const int off = sw128_off(r, c, UPD_BM);
-                    *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = h;
-                    if (!ZBF) {
-                        *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
-                        *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
-                    }
-                    if (++c == k) {
-                        c = 0;
-                        ++r;
-                    }
-                }
-            }
+        }
+        float zv[32];
+        if (ok) {
+            const ZT *src = bulk ? zbuf[b] + row * k + c0 : Z + f0 + (int64_t)row * k + c0;
+            load_slice(src, nv, vec, zv);
         } else {
-            for (int f = tid; f < nf; f += UPD_THREADS) {
-                const int r = f / k, c = f - r * k;
-                __nv_bfloat16 h, m, l;
-                split3_one(load_as_float(Z + f0 + f), h, m, l);
-                const int off = sw128_off(r, c, UPD_BM);
-                *reinterpret_cast<__nv_bfloat16 *>(Ap + off) = h;
-                if (!ZBF) {
-                    *reinterpret_cast<__nv_bfloat16 *>(Ap + a_part + off) = m;
-                    *reinterpret_cast<__nv_bfloat16 *>(Ap + 2 * a_part + off) = l;
-                }
-            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) zv[e] = 0.0f;
         }
-        {
-            const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-            const int pc = KC - k;  // padding columns of every row
-            for (int e = tid; e < UPD_BM * pc; e += UPD_THREADS) {
-                const int r = e / pc, c = k + (e - r * pc);
-                const int off = sw128_off(r, c, UPD_BM);
-                for (int pt = 0; pt < ZPARTS; ++pt) *reinterpret_cast<__nv_bfloat16 *>(Ap + pt * a_part + off) = zero;
+        if (ZBF) {  // z is a bf16 value: its split is z itself
+            uint32_t pk[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                pk[e] = (__float_as_uint(zv[2 * e]) >> 16) | (__float_as_uint(zv[2 * e + 1]) & 0xffff0000u);
+            tmem_st16(tmem + tlane + ACOL + cw * 16, pk);
+        } else {
+            uint32_t ph[16], pm[16], pl[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+                split3_one(zv[2 * e], h0, m0, l0);
+                split3_one(zv[2 * e + 1], h1, m1, l1);
+                ph[e] = bf16_bits(h0) | (bf16_bits(h1) << 16);
+                pm[e] = bf16_bits(m0) | (bf16_bits(m1) << 16);
+                pl[e] = bf16_bits(l0) | (bf16_bits(l1) << 16);
             }
-            for (int e = nr * k + tid; e < UPD_BM * k; e += UPD_THREADS) {  // rows past the end
-                const int r = e / k, c = e - r * k;
-                const int off = sw128_off(r, c, UPD_BM);
-                for (int pt = 0; pt < ZPARTS; ++pt) *reinterpret_cast<__nv_bfloat16 *>(Ap + pt * a_part + off) = zero;
-            }
+            tmem_st16(tmem + tlane + ACOL + cw * 16, ph);
+            tmem_st16(tmem + tlane + ACOL + (KC / 2) + cw * 16, pm);
+            tmem_st16(tmem + tlane + ACOL + KC + cw * 16, pl);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tmem_st_wait();
         fence_before();
-        __syncthreads();  // A complete; the previous tile's staging reads are done
+        if (__syncthreads_or(!ok)) {  // A complete in TMEM; the buffer b is read
+            if (tid == 0) atomicOr(flag, 2);
+            break;
+        }
         fence_after();
-        // 2. the six products into TMEM
+        // 3. the products into TMEM; the freed buffer takes tile j + 2
         if (tid == 0) {
-            const uint32_t a0 = smem_u32(Ap), b0 = smem_u32(Bp);
+            issue(j + 2);
+            const uint32_t b0 = smem_u32(Bp);
             uint32_t acc = 0;
 #pragma unroll 1
             for (int i = 0; i < ZPARTS; ++i)
 #pragma unroll 1
                 for (int jp = 0; i + jp < 3; ++jp)
 #pragma unroll 1
-                    for (int ka = 0; ka < KA; ++ka)
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint32_t ad = a0 + i * a_part + ka * UPD_BM * 128 + kk * 32;
-                            const uint32_t bd = b0 + jp * b_part + ka * N * 128 + kk * 32;
-                            mma_bf16(tmem, sw128_desc(ad), sw128_desc(bd), idesc, acc);
-                            acc = 1;
-                        }
+                    for (int ks = 0; ks < KS; ++ks) {
+                        const uint32_t bd = b0 + jp * b_part + (ks >> 2) * N * 128 + (ks & 3) * 32;
+                        mma_bf16_tmem_a(tmem, tmem + ACOL + i * (KC / 2) + ks * 8, sw128_desc(bd), idesc, acc);
+                        acc = 1;
+                    }
             mma_commit(&tail->done);
         }
-        if (vec) {
-#pragma unroll
-            for (int j = 0; j < UPD_UNROLL; ++j) {
-                const int g = tid + j * UPD_THREADS;
-                if (4 * g < nf) rr[j] = __ldcs(reinterpret_cast<const float4 *>(R + f0) + g);
-            }
-        }
-        const bool got = mbar_wait(&tail->done, it & 1, wait_limit());
+        const bool got = mbar_wait(&tail->done, (uint32_t)(j & 1), wait_limit());
         if (__syncthreads_or(!got)) {
             if (tid == 0) atomicOr(flag, 2);
             break;
         }
         fence_after();
-        // 3. Z G from TMEM into the fp32 staging tile (over the A parts, which the
-        //    finished MMAs no longer read): warp (q, cw) moves lanes 32q.. x columns 32cw..
-        if (32 * cw < N) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + 32 * cw, v);
-            tmem_ld_wait();
-            const int r = q * 32 + lane;
+        // 4. the step on the row slice: Z G from the accumulator columns c0.., z
+        //    exact in registers, r loaded at the start of the tile
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (32 * cw + j < N) stage[r * lds + 32 * cw + j] = __uint_as_float(v[j]);
+        for (int hh = 0; hh < 2; ++hh) {
+            uint32_t a[16];
+            tmem_ld16(tmem + tlane + c0 + 16 * hh, a);
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int c = 16 * hh + e;
+                const float grad = __fsub_rn(__uint_as_float(a[e]), rv[c]);
+                zv[c] = upd_project(__fmaf_rn(-eta, grad, zv[c]), bound, flag);
+            }
         }
-        fence_before();
-        __syncthreads();
-        // 4. the step on the tile's nr * k contiguous entries (z still in registers from
-        //    the split, r loaded while the products ran; coalesced stores)
+        ZT *dst = Z + f0 + (int64_t)row * k + c0;
         if (vec) {
 #pragma unroll
-            for (int j = 0; j < UPD_UNROLL; ++j) {
-                const int g = tid + j * UPD_THREADS;
-                if (4 * g >= nf) continue;
-                float zv[4] = {zz[j].x, zz[j].y, zz[j].z, zz[j].w};
-                const float rv[4] = {rr[j].x, rr[j].y, rr[j].z, rr[j].w};
-                int r = (4 * g) / k, c = 4 * g - r * k;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float grad = __fsub_rn(stage[r * lds + c], rv[e]);
-                    zv[e] = upd_project(__fmaf_rn(-eta, grad, zv[e]), bound, flag);
-                    if (++c == k) {
-                        c = 0;
-                        ++r;
-                    }
-                }
-                store_z4(Z, f0, g, make_float4(zv[0], zv[1], zv[2], zv[3]));
-            }
+            for (int e = 0; e < 8; ++e)
+                if (4 * e < nv) store4(dst + 4 * e, zv[4 * e], zv[4 * e + 1], zv[4 * e + 2], zv[4 * e + 3]);
         } else {
-            for (int f = tid; f < nf; f += UPD_THREADS) {
-                const int r = f / k, c = f - r * k;
-                const float grad = __fsub_rn(stage[r * lds + c], R[f0 + f]);
-                Z[f0 + f] = store_cast<ZT>(upd_project(__fmaf_rn(-eta, grad, load_as_float(Z + f0 + f)), bound, flag));
-            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                if (e < nv) dst[e] = store_cast<ZT>(zv[e]);
         }
-        // the next tile's split overwrites the staging: every thread is done with it
-        __syncthreads();
+        // the next tile's tcgen05.st and MMAs come after every thread's loads of
+        // the accumulator (the barrier after the next split orders them)
+        fence_before();
     }
-    if (tid == 0) {  // every MMA this thread issued has retired before TMEM is freed
+    if (tid == 0) {  // every MMA and copy this thread issued has completed before TMEM and the CTA go
         mma_commit(&tail->fin);
         mbar_wait(&tail->fin, 0, wait_limit());
+        for (int b = 0; b < 2; ++b)
+            if (armed & (1u << b)) mbar_wait(&tail->full[b], (phase >> b) & 1, wait_limit());
     }
     fence_before();
     __syncthreads();
@@ -1180,9 +1205,11 @@ __global__ void __launch_bounds__(UPD_THREADS)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+int update_tc_zbuf_bytes(int k, size_t es) { return (int)((UPD_BM * (size_t)k * es + 127) / 128 * 128); }
+
 template <int KA>
-size_t update_tc_smem(int N) {
-    return 1024 + 3 * (size_t)KA * N * 128 + 3 * (size_t)KA * UPD_BM * 128 + sizeof(UpdTail);
+size_t update_tc_smem(int N, int zbuf_bytes) {
+    return 1024 + 3 * (size_t)KA * N * 128 + 2 * (size_t)zbuf_bytes + sizeof(UpdTail);
 }
 
 }  // namespace
@@ -1192,15 +1219,18 @@ bool update_tc_supported(int k) { return k > 32 && k <= 128; }
 namespace {
 template <int KA, typename ZT>
 void launch_update_tc_kind(ZT *Z, const float *R, int64_t rows, int k, int N, const float *Gf, int kp,
-                           const double *scal, float bound, int *flag, uint32_t tmem_cols, int sms, cudaStream_t s) {
-    const size_t smem = update_tc_smem<KA>(N);
-    int per_sm = 1;
-    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tc<KA, ZT>, UPD_THREADS, smem));
-    per_sm = std::max(1, std::min(per_sm, 512 / (int)tmem_cols));
+                           const double *scal, float bound, int *flag, int sms, cudaStream_t s) {
+    constexpr int zparts = sizeof(ZT) == 2 ? 1 : 3;
+    const int need = KA * 64 + zparts * KA * 32;  // accumulator + A parts, TMEM columns
+    uint32_t tmem_cols = 32;
+    while ((int)tmem_cols < need) tmem_cols <<= 1;
+    const int zb = update_tc_zbuf_bytes(k, sizeof(ZT));
+    const size_t smem = update_tc_smem<KA>(N, zb);
+    const int use_bulk = (reinterpret_cast<uintptr_t>(Z) & 15) == 0;
     const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
-    k_update_tc<KA, ZT><<<(unsigned)grid, UPD_THREADS, smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
-                                                                  tmem_cols);
+    const int64_t grid = std::min<int64_t>(ntiles, sms);  // one CTA per SM (shared memory and TMEM)
+    k_update_tc<KA, ZT><<<(unsigned)grid, upd_threads<KA>(), smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
+                                                                        tmem_cols, zb, use_bulk);
     DSANLS_LAUNCH_CHECK();
 }
 }  // namespace
@@ -1211,14 +1241,13 @@ void launch_update_tc(ZT *Z, const float *R, int64_t rows, int k, const float *G
     if (!update_tc_supported(k)) throw ArgError{"launch_update_tc: needs 32 < k <= 128"};
     if (rows <= 0) return;
     const int N = (k + 15) / 16 * 16;
-    const uint32_t tmem_cols = N <= 64 ? 64u : 128u;
     int dev = 0, sms = 152;
     DSANLS_CUDA(cudaGetDevice(&dev));
     DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (k <= 64)
-        launch_update_tc_kind<1, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
+        launch_update_tc_kind<1, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, sms, s);
     else
-        launch_update_tc_kind<2, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, tmem_cols, sms, s);
+        launch_update_tc_kind<2, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, sms, s);
 }
 template void launch_update_tc<float>(float *, const float *, int64_t, int, const float *, int, const double *, float,
                                       int *, cudaStream_t);

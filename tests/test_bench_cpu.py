@@ -29,8 +29,13 @@ def test_reference_arm_json_line():
     assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["higher_is_better"] is True and d["vs_baseline"] is None
     assert d["config"]["workload"] == "small"
-    assert d["value"] > 0 and abs(d["value"] * d["ms_per_step"] / 1000.0 - 1.0) < 1e-6
+    # value: the full iteration's rate extrapolated from the sample; ms_per_step: the
+    # sample's measured wall time (so K steps fit in the run's own clock)
+    assert d["value"] > 0 and abs(d["value"] * d["ms_per_full_iteration"] / 1000.0 - 1.0) < 1e-6
+    assert 0 < d["ms_per_step"] * d["steps"] <= 1000.0 * d["wall_s"] * 1.001
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == d["unit"] and cb["cores"] >= 1
     assert cb["sample"]
+    st = cb["single_thread"]  # one BLAS thread (null only where no OpenBLAS is loaded)
+    assert st is None or (st["cores"] == 1 and st["value"] > 0)
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -143,6 +143,38 @@ def test_dense_fp32_split_tensor_core_half_steps(pkg, case, order):
         assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
 
 
+UPDATE_CASES = [
+    # m, n, k, d, d_v for the tensor-core row update (32 < k <= 128): several 128-row
+    # tiles per CTA (the double-buffered bulk copies of Z), ragged last tiles whose
+    # bytes are not a multiple of 16 (read without the bulk copy), k not a multiple
+    # of 4 (scalar row slices), one and two 64-column K atoms
+    (70001, 300, 99, 64, 64),
+    (40000, 333, 50, 48, 48),
+    (20001, 257, 77, 80, 80),
+    (300, 261, 112, 64, 64),
+    (19457, 130, 128, 40, 40),
+    (60001, 90, 36, 30, 30),
+]
+
+
+@pytest.mark.parametrize("case", UPDATE_CASES)
+def test_tensor_core_update_tiles(pkg, case):
+    """One projected-gradient half-step through the tensor-core row update against
+    the exact oracle, norm-wise and on every 128-row tile (a tile computed wrong
+    would hide in the norm of tens of thousands of rows)."""
+    m, n, k, d, d_v = case
+    M, _, _ = planted_dense(m, n, 16, 12)
+    U, V = initial_factors(m, n, k, 13)
+    M64 = M.astype(np.float64)
+    for side, dd in ((0, d), (1, d_v)):
+        got, _, _ = _gpu_half(pkg, M, U, V, method.SUBSAMPLE, 0, 9, 5, side, d, d_v=d_v)
+        want = _oracle_half(M64, U, V, method.SUBSAMPLE, 0, 9, 5, side, dd)
+        assert _rel(got, want) <= TOL_STEP, (side, _rel(got, want))
+        rows = got.shape[0]
+        worst = max(_rel(got[r:r + 128], want[r:r + 128]) for r in range(0, rows, 128))
+        assert worst <= 4 * TOL_STEP, (side, worst)
+
+
 @pytest.mark.parametrize("solver", [0, 1])
 def test_dense_identity_half_steps(pkg, solver):
     m, n, k = 200, 150, 12

@@ -34,7 +34,14 @@ def _csr(m, n, seed, mean_len):
     return rp, col, val, sp.csr_matrix((val.astype(np.float64), col, rp), shape=(m, n))
 
 
-@pytest.mark.parametrize("case", [(3000, 1200, 48, 300, 400, 20.0), (2000, 5000, 100, 500, 300, 40.0)])
+@pytest.mark.parametrize("case", [
+    (3000, 1200, 48, 300, 400, 20.0),
+    (2000, 5000, 100, 500, 300, 40.0),
+    # several 128-row tiles per CTA, ragged last tiles whose bytes are not a multiple
+    # of 16 (k = 66 also takes the scalar row slices)
+    (70001, 700, 66, 300, 2000, 20.0),
+    (60001, 900, 100, 400, 3000, 20.0),
+])
 def test_bf16_factor_half_steps(pkg, case):
     m, n, k, d, d_v, mean_len = case
     rp, col, val, Msp = _csr(m, n, 7, mean_len)

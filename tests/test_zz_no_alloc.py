@@ -1,5 +1,5 @@
 """The allocation-free Gram entry point (dsanls_gram_noalloc) against the Gram
-the existing handle API computes.
+the existing handle API computes and against the FP64 oracle's.
 
 Some callers cannot let a library allocate device memory (a host framework
 that owns all device memory through its own pool, or a latency-critical loop
@@ -20,6 +20,7 @@ import sys
 import numpy as np
 import pytest
 
+from oracle import method
 from synthdata import initial_factors, planted_dense
 
 pytestmark = pytest.mark.gpu
@@ -61,6 +62,11 @@ def test_noalloc_gram_matches_handle_gram(pkg, m, n, k):
         torch.cuda.synchronize()
         got = G.cpu().numpy()
         assert np.max(np.abs(got - want)) <= TOL * np.max(np.abs(want))
+        # and directly against the FP64 oracle's Gram of the unsketched subproblem
+        # (B = V^T S with S = I; binary32 products are exact in FP64)
+        S = method.Sketch(method.IDENTITY, 0, 0, 0, n, n)
+        _, _, Go, _ = method.sketched_terms(M.astype(np.float64), V.astype(np.float64), S)
+        assert np.max(np.abs(got - Go)) <= TOL * np.max(np.abs(Go))
         # a different problem in between must not leave anything behind
         pkg.gram_noalloc(Bother)
         torch.cuda.synchronize()
