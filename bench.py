@@ -53,10 +53,10 @@ WORKLOADS = {
                                    "(profiling case: M 0.5 GB)"),
     "sparse_text": dict(m=2_000_000, n=500_000, k=100, d=5000, d_v=5000, sketch=1, sparse=True,
                         desc="CSR 2e6 docs x 5e5 terms (lognormal lengths mean 100, Zipf 1.07 ids, "
-                             "log(1+Poisson) values, ~2e8 nnz), k=100, subsampling d=d'=5000, PGD "
+                             "log(1+Poisson) values, ~1.4e8 nnz), k=100, subsampling d=d'=5000, PGD "
                              "(--precision bf16: bf16 factors)"),
     "sparse_text_small": dict(m=200_000, n=50_000, k=100, d=500, d_v=500, sketch=1, sparse=True,
-                              desc="CSR 2e5 x 5e4 text-like (~2e7 nnz), k=100, subsampling d=d'=500, PGD"),
+                              desc="CSR 2e5 x 5e4 text-like (~1.3e7 nnz), k=100, subsampling d=d'=500, PGD"),
     "learned": dict(learned=True, m=65536, n=16384, k=32, d=2048, d_v=2048, sketch=0, eps=0.05, t_max=400,
                     desc="dense 65536x16384 planted (k=32, 70% zero factors), Gaussian d=2048, PGD; network trained "
                          "on ~1e7 triples harvested from seeds 1-20, evaluated on seed 21 to rel. error 0.05"),
