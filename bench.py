@@ -638,6 +638,9 @@ def main():
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--regen-sketch", action="store_true",
                     help="BF16 paper order: draw the Gaussian sketch inside the GEMMs instead of a pre-pass")
+    ap.add_argument("--batch-tile", default="",
+                    help="batched bf16 paper order: pin the tensor-core tile 'chunk,stages,row_tiles' "
+                         "(e.g. 192,3,2) instead of autotuning it")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned workload")
@@ -936,6 +939,8 @@ def run_batch(args, w):
     torch.cuda.set_stream(stream)
     prec = {"fp32": pkg.FP32, "bf16": pkg.BF16}[args.precision]
     b = pkg.Batch(specs, use_graph=1, order=order, precision=prec)
+    if args.batch_tile:
+        b.set_tile(*[int(x) for x in args.batch_tile.split(",")])
     for i, M in enumerate(Ms):
         b.set_dense(i, M)
     for _ in range(args.warmup):

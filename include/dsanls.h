@@ -343,12 +343,20 @@ int dsanls_batch_profile(dsanls_batch_t b, double *ms);
 /* Persistent CTAs chosen by the autotuner (0 before the first step). */
 int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas);
 /* BF16 paper order: R_i = (X_i S_i) B_i^T runs on tcgen05 tensor cores (one
- * persistent launch over (instance, 128-row tile) items, A_i kept on chip).
+ * persistent launch over (instance, row tiles) items, A_i kept on chip).
  * The tile chosen by the autotuner for it: *chunk = sketch columns per chunk
- * of a tile (64, 128 or 256; it sets the tile's shared memory and tensor-
- * memory columns and so its CTAs per SM), *ctas = persistent CTAs; both 0
- * before the first step or in the other forms. */
-int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas);
+ * of a tile (64, 128, 192 or 256; it sets the tile's shared memory and tensor-
+ * memory columns and so its CTAs per SM), *ctas = persistent CTAs, *row_tiles
+ * = 128-row tiles per work item (1, or 2 sharing every copy of the sketch
+ * chunk); all 0 before the first step or in the other forms.  row_tiles may
+ * be NULL. */
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles);
+/* Pin the tile of the tensor-core product instead of letting the autotuner time
+ * the candidates: (chunk, stages, row_tiles) one of (64,4,1) (128,3,1) (128,4,1)
+ * (256,4,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2); (0,0,0) returns to the
+ * autotuner.  Takes effect at the next step (the iteration graph is rebuilt);
+ * other configurations return EINVAL and change nothing. */
+int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles);
 const char *dsanls_batch_last_error(dsanls_batch_t b);
 void dsanls_batch_destroy(dsanls_batch_t b);
 

@@ -25,7 +25,7 @@ EXPORTED_SYMBOLS = [
     "dsanls_uniform_field",
     "dsanls_subsample_indices", "dsanls_profile_half_step", "dsanls_kernel_launches", "dsanls_gram_noalloc",
     "dsanls_batch_create", "dsanls_batch_set_options", "dsanls_batch_set_dense", "dsanls_batch_set_factors",
-    "dsanls_batch_step", "dsanls_batch_get_factors", "dsanls_batch_rel_error", "dsanls_batch_tuned_blocks", "dsanls_batch_tuned_tile", "dsanls_batch_profile",
+    "dsanls_batch_step", "dsanls_batch_get_factors", "dsanls_batch_rel_error", "dsanls_batch_tuned_blocks", "dsanls_batch_tuned_tile", "dsanls_batch_set_tile", "dsanls_batch_profile",
     "dsanls_batch_last_error", "dsanls_batch_destroy",
     "dsanls_mlp_create", "dsanls_mlp_param_count", "dsanls_mlp_get_params", "dsanls_mlp_set_params",
     "dsanls_mlp_predict", "dsanls_mlp_train_step", "dsanls_mlp_destroy", "dsanls_set_mlp", "dsanls_mlp_kept",
@@ -105,7 +105,9 @@ def lib():
             "dsanls_batch_get_factors": ([vp, i32, vp, vp, i32], ctypes.c_int),
             "dsanls_batch_rel_error": ([vp, vp], ctypes.c_int),
             "dsanls_batch_tuned_blocks": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
-            "dsanls_batch_tuned_tile": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+            "dsanls_batch_tuned_tile": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
+                                        ctypes.c_int),
+            "dsanls_batch_set_tile": ([vp, i32, i32, i32], ctypes.c_int),
             "dsanls_batch_profile": ([vp, vp], ctypes.c_int),
             "dsanls_batch_last_error": ([vp], ctypes.c_char_p),
             "dsanls_batch_destroy": ([vp], None),
@@ -484,12 +486,18 @@ class Batch:
         self._err(lib().dsanls_batch_tuned_blocks(self._h, ctypes.byref(v)), "batch_tuned_blocks")
         return v.value
 
+    def set_tile(self, chunk, stages, row_tiles):
+        """Pin the tensor-core tile (bf16 paper order) instead of autotuning it;
+        (0, 0, 0) returns to the autotuner."""
+        self._err(lib().dsanls_batch_set_tile(self._h, int(chunk), int(stages), int(row_tiles)), "batch_set_tile")
+
     def tuned_tile(self):
-        """(chunk, ctas) of the tensor-core product chosen by the autotuner (bf16
-        paper order; (0, 0) otherwise or before the first step)."""
-        c, n = ctypes.c_int32(0), ctypes.c_int32(0)
-        self._err(lib().dsanls_batch_tuned_tile(self._h, ctypes.byref(c), ctypes.byref(n)), "batch_tuned_tile")
-        return c.value, n.value
+        """(chunk, ctas, row tiles per item) of the tensor-core product chosen by the
+        autotuner (bf16 paper order; zeros otherwise or before the first step)."""
+        c, n, r = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        self._err(lib().dsanls_batch_tuned_tile(self._h, ctypes.byref(c), ctypes.byref(n), ctypes.byref(r)),
+                  "batch_tuned_tile")
+        return c.value, n.value, r.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -607,7 +607,7 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
         mark(1);
         launch_batch_b_tc(g, side, cfg.tc_b_ctas, ctr + 0, s);
         mark(2);
-        launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_stages, cfg.tc_ctas, ctr + 1, s);
+        launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_stages, cfg.tc_rt, cfg.tc_ctas, ctr + 1, s);
         mark(3);
         kb_gram<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, count, ctr + 2, side, g.B, g.alpha, g.beta,
                                                      g.power_iters, g.t_dev, g.G);
@@ -664,8 +664,9 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
 }
 
 void batch_build_tc_items(const std::vector<BatchInst> &h, int side, std::vector<int2> &tcitems,
-                          std::vector<int2> &tcbitems) {
+                          std::vector<int2> &tcitems2, std::vector<int2> &tcbitems) {
     tcitems.clear();
+    tcitems2.clear();
     tcbitems.clear();
     std::vector<int> order(h.size());
     for (size_t i = 0; i < h.size(); ++i) order[i] = (int)i;
@@ -678,6 +679,7 @@ void batch_build_tc_items(const std::vector<BatchInst> &h, int side, std::vector
         const int64_t rows = side == 0 ? h[i].m : h[i].n;
         const int dd = side == 0 ? h[i].d : h[i].dv;
         for (int t = 0; t < (int)ceil_div(rows, 128); ++t) tcitems.push_back(make_int2(i, t));
+        for (int t = 0; t < (int)ceil_div(rows, 256); ++t) tcitems2.push_back(make_int2(i, t));
         for (int t = 0; t < (int)ceil_div(dd, 128); ++t) tcbitems.push_back(make_int2(i, t));
     }
 }

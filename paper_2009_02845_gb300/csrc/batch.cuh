@@ -34,7 +34,8 @@ struct BatchDev {
     int tc = 0;
     __nv_bfloat16 *data_p = nullptr, *St = nullptr, *Yt = nullptr;
     int2 *tcitems[2] = {nullptr, nullptr}, *tcbitems[2] = {nullptr, nullptr};  // R items, B items (S^T row tiles)
-    int ntc[2] = {0, 0}, ntcb[2] = {0, 0};
+    int2 *tcitems2[2] = {nullptr, nullptr};  // R items of two row tiles (instance, 256-row pair)
+    int ntc[2] = {0, 0}, ntcb[2] = {0, 0}, ntc2[2] = {0, 0};
     double *G = nullptr;
     int2 *bitems[2] = {nullptr, nullptr}, *aritems[2] = {nullptr, nullptr}, *uitems[2] = {nullptr, nullptr};
     int nb[2] = {0, 0}, nar[2] = {0, 0}, nu[2] = {0, 0};
@@ -53,8 +54,9 @@ struct BatchDev {
 struct BatchLaunch {
     int persistent_blocks = 152 * 4;
     int sketch_blocks = 152 * 8;
-    int tc_nc = 128;    // sketch columns per chunk of the tensor-core product (64, 128, 256)
+    int tc_nc = 128;    // sketch columns per chunk of the tensor-core product (64 to 256)
     int tc_stages = 4;  // cp.async ring stages of the tensor-core product (3 or 4)
+    int tc_rt = 1;      // 128-row tiles per work item of the tensor-core product (1 or 2)
     int tc_ctas = 304;  // persistent CTAs of the tensor-core product
     int tc_b_ctas = 304;  // persistent CTAs of B = Y^T S on tensor cores
 };
@@ -67,15 +69,18 @@ void batch_build_items(const std::vector<BatchInst> &h, int side, std::vector<in
 void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaStream_t s, cudaEvent_t *ev = nullptr);
 void batch_init_factors(const BatchInst *inst, int count, float *factors, cudaStream_t s);
 // (instance, 128-row tile) items of the tensor-core products, largest first: of
-// R_i (rows of X_i) and of B_i (rows of S_i^T, d_i of them).
+// R_i (rows of X_i), of R_i in pairs of tiles (instance, 256-row pair) and of B_i
+// (rows of S_i^T, d_i of them).
 void batch_build_tc_items(const std::vector<BatchInst> &h, int side, std::vector<int2> &tcitems,
-                          std::vector<int2> &tcbitems);
+                          std::vector<int2> &tcitems2, std::vector<int2> &tcbitems);
 // batch_tc.cu
-size_t batch_tc_smem(int nc, int stages);
+size_t batch_tc_smem(int nc, int stages, int rt);
+bool batch_tc_tile_built(int nc, int stages, int rt);
 void batch_prime_tc(int max_smem);
-int batch_tc_ctas_per_sm(int nc, int stages);
+int batch_tc_ctas_per_sm(int nc, int stages, int rt);
 int batch_tc_b_ctas_per_sm();
-void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int stages, int ctas, int *counter, cudaStream_t s);
+void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int stages, int rt, int ctas, int *counter,
+                        cudaStream_t s);
 void launch_batch_sketch_t(const BatchDev &g, int side, cudaStream_t s);
 // B_i = Y_i^T S_i on tensor cores (padded bf16 Y_i^T first); counter: a cleared queue counter
 void launch_batch_b_tc(const BatchDev &g, int side, int ctas, int *counter, cudaStream_t s);

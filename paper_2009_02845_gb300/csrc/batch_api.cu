@@ -28,6 +28,7 @@ struct dsanls_batch_ctx {
     BatchDev g;
     BatchLaunch cfg;
     bool tuned = false;
+    int forced_tile = 0;  // a tile set by dsanls_batch_set_tile (code of apply_config), 0: tune
     dsanls_options opt{};
     int64_t t_host = 0;
     cudaStream_t own_stream = nullptr;
@@ -122,7 +123,7 @@ std::string tune_key(const dsanls_batch_ctx *b) {
     }
     std::sort(shapes.begin(), shapes.end());
     const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "") +
-                             (b->g.tc ? "tc2" : "");
+                             (b->g.tc ? "tc3" : "");
     std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
     return std::to_string(std::hash<std::string>()(key)) + "/" + form;
@@ -170,15 +171,18 @@ void cache_store(const std::string &key, int value) {
 }
 
 // A tuned configuration: per-SM persistent CTAs of the CUDA-core kernels, plus
-// (tensor-core form) 10000 x that + 1000 x the ring stages + the chunk width of
-// the tensor-core product.
+// (tensor-core form) 100000 x that + 10000 x the row tiles per item + 1000 x the
+// ring stages + the chunk width of the tensor-core product.
 void apply_config(dsanls_batch_ctx *b, int code, int sms) {
-    const int per_sm = code >= 10000 ? code / 10000 : code;
+    const int per_sm = code >= 100000 ? code / 100000 : code;
     b->cfg.persistent_blocks = 152 * per_sm;
-    if (code >= 10000) {
+    if (code >= 100000) {
+        b->cfg.tc_rt = (code / 10000) % 10;
         b->cfg.tc_stages = (code / 1000) % 10;
         b->cfg.tc_nc = code % 1000;
-        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc, b->cfg.tc_stages);
+        if (!batch_tc_tile_built(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt))
+            throw ArgError{"tuned tile configuration not built"};
+        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt);
         b->cfg.tc_b_ctas = sms * batch_tc_b_ctas_per_sm();
     }
 }
@@ -186,6 +190,13 @@ void apply_config(dsanls_batch_ctx *b, int code, int sms) {
 // Time one full outer iteration for each candidate (factors restored after
 // each trial) and keep the fastest.
 void autotune(dsanls_batch_ctx *b) {
+    int sms0 = 152;
+    DSANLS_CUDA(cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, b->device));
+    if (b->g.tc && b->forced_tile) {  // the caller's tile, no timing
+        apply_config(b, b->forced_tile, sms0);
+        b->tuned = true;
+        return;
+    }
     const std::string key = tune_key(b);
     int per_sm = 0;
     if (!cache_lookup(key, per_sm)) {
@@ -206,10 +217,12 @@ void autotune(dsanls_batch_ctx *b) {
         // shared memory, tensor-memory columns and CTAs per SM
         std::vector<int> candidates;
         if (b->g.tc) {
-            // (chunk, stages): 64/4 and 128/3 fit two CTAs per SM, 128/4 and 256/4 one
-            const int tiles[4][2] = {{64, 4}, {128, 3}, {128, 4}, {256, 4}};
+            // (chunk, stages, row tiles): with one row tile 64/4 and 128/3 fit two CTAs per
+            // SM, 128/4 and 256/4 one; two row tiles (the sketch chunk shared) run one CTA
+            const int tiles[8][3] = {{64, 4, 1}, {128, 3, 1}, {128, 4, 1}, {256, 4, 1},
+                                     {64, 4, 2}, {128, 3, 2}, {128, 4, 2}, {192, 3, 2}};
             for (const auto &tl : tiles)
-                for (int c : {2, 4}) candidates.push_back(c * 10000 + tl[1] * 1000 + tl[0]);
+                for (int c : {2, 4}) candidates.push_back(c * 100000 + tl[2] * 10000 + tl[1] * 1000 + tl[0]);
         } else {
             candidates = {1, 2, 4, 8};
         }
@@ -357,13 +370,17 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
             DSANLS_CUDA(cudaMemcpyAsync(g.uitems[side], ui.data(), ui.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaMemcpyAsync(g.sketch_prefix[side], pre.data(), pre.size() * sizeof(int64_t),
                                         cudaMemcpyHostToDevice, s));
-            std::vector<int2> ti, tb;
-            batch_build_tc_items(b->h, side, ti, tb);
+            std::vector<int2> ti, ti2, tb;
+            batch_build_tc_items(b->h, side, ti, ti2, tb);
             balloc(g.tcitems[side], (int64_t)ti.size());
+            balloc(g.tcitems2[side], (int64_t)ti2.size());
             balloc(g.tcbitems[side], (int64_t)tb.size());
             g.ntc[side] = (int)ti.size();
+            g.ntc2[side] = (int)ti2.size();
             g.ntcb[side] = (int)tb.size();
             DSANLS_CUDA(cudaMemcpyAsync(g.tcitems[side], ti.data(), ti.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaMemcpyAsync(g.tcitems2[side], ti2.data(), ti2.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                        s));
             DSANLS_CUDA(cudaMemcpyAsync(g.tcbitems[side], tb.data(), tb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
         }
@@ -572,11 +589,27 @@ int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas) {
     return DSANLS_OK;
 }
 
-int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas) {
+int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles) {
+    if (!b) return DSANLS_EINVAL;
+    if (chunk == 0 && stages == 0 && row_tiles == 0) {
+        b->forced_tile = 0;
+    } else {
+        if (!batch_tc_tile_built(chunk, stages, row_tiles))
+            return bfail(b, DSANLS_EINVAL, "no such tile: (64,4,1) (128,3,1) (128,4,1) (256,4,1) (64,4,2) (128,3,2) "
+                                           "(128,4,2) (192,3,2)");
+        b->forced_tile = 2 * 100000 + row_tiles * 10000 + stages * 1000 + chunk;
+    }
+    b->tuned = false;
+    drop_graph(b);
+    return DSANLS_OK;
+}
+
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles) {
     if (!b || !chunk || !ctas) return DSANLS_EINVAL;
     const bool tc = b->tuned && b->g.tc;
     *chunk = tc ? b->cfg.tc_nc : 0;
     *ctas = tc ? b->cfg.tc_ctas : 0;
+    if (row_tiles) *row_tiles = tc ? b->cfg.tc_rt : 0;
     return DSANLS_OK;
 }
 
@@ -592,7 +625,7 @@ void dsanls_batch_destroy(dsanls_batch_t b) {
     bfree(g.data_p); bfree(g.St); bfree(g.Yt);
     for (int side = 0; side < 2; ++side) {
         bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]); bfree(g.pitems[side]);
-        bfree(g.tcitems[side]); bfree(g.tcbitems[side]);
+        bfree(g.tcitems[side]); bfree(g.tcitems2[side]); bfree(g.tcbitems[side]);
     }
     bfree(g.counters); bfree(g.t_dev); bfree(g.flag); bfree(b->work); bfree(b->dres);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);

@@ -3,21 +3,25 @@
 // eq. gradient_descent for every instance of the batch; A_i never leaves the
 // SM).
 //
-// One persistent launch over a work queue of (instance, 128-row tile) items,
-// largest instances first.  A CTA of 256 threads takes an item with atomicAdd
-// and, for each NC-wide chunk of the instance's sketch columns:
+// One persistent launch over a work queue of (instance, RT x 128-row tiles)
+// items, largest instances first.  A CTA of 256 threads takes an item with
+// atomicAdd and, for each NC-wide chunk of the instance's sketch columns:
 //   * walks K in blocks of 64 through a ring of TB_STAGES shared-memory
-//     stages: all threads copy the X tile (128 x 64) and the S^T chunk (N x 64,
+//     stages: all threads copy the RT X tiles (128 x 64) and the S^T chunk (N x 64,
 //     N = the chunk's columns rounded up to 16) from the padded bf16 copies
 //     with 16-byte cp.async straight into the 128-byte swizzled K-major layout
 //     (rows padded to multiples of 8 elements, so any instance shape works),
 //     TB_STAGES - 1 blocks ahead of the products; thread 0 issues four
-//     tcgen05.mma (M = 128, N, K = 16) per block into the accumulator D1 in
-//     tensor memory and commits to the stage's mbarrier, which frees the stage;
-//   * moves D1 to shared memory as bf16 (the rounding of A where it enters R)
-//     next to the bf16 B chunk (k rows padded to 16 or 32), and thread 0 adds
-//     A_chunk B_chunk^T into the second accumulator D2 (M = 128, N = k).
-// After the last chunk D2 holds R for the tile's rows.  Every wait is
+//     tcgen05.mma (M = 128, N, K = 16) per block and row tile into that tile's
+//     accumulator D1 in tensor memory and commits to the stage's mbarrier,
+//     which frees the stage;
+//   * moves each D1 to shared memory as bf16 (the rounding of A where it enters
+//     R) next to the bf16 B chunk (k rows padded to 32), and thread 0 adds
+//     A_chunk B_chunk^T into the tile's second accumulator D2 (M = 128, N = k).
+// After the last chunk D2 holds R for the tiles' rows.  RT = 2 row tiles share
+// every copy of the S^T chunk, which halves the sketch bytes the SMs read per
+// byte of X (they come from L2: the chunk is reused by every tile of the
+// instance); it needs 2 (NC + 32) TMEM columns, so NC <= 192.  Every wait is
 // bounded (2 s); a wait that gives up sets bit 2 of the error flag, and the
 // CTA stops taking items, retires its MMAs and frees its tensor memory.
 //
@@ -43,8 +47,10 @@ constexpr int TB_KP = 32;  // rows of the B tile (k <= 32 padded)
 constexpr int TB_MAX_STAGES = 4;
 constexpr unsigned long long TB_WAIT_NS = 2000000000ull;
 
-__host__ __device__ constexpr int tb_stage_bytes(int nc) { return TB_BM * TB_BK * 2 + nc * TB_BK * 2; }
-__host__ __device__ constexpr uint32_t tb_tmem_cols(int nc) { return nc + TB_KP <= 128 ? 128u : (nc + TB_KP <= 256 ? 256u : 512u); }
+__host__ __device__ constexpr int tb_stage_bytes(int nc, int rt) { return rt * TB_BM * TB_BK * 2 + nc * TB_BK * 2; }
+__host__ __device__ constexpr uint32_t tb_tmem_cols(int nc, int rt) {
+    return rt * (nc + TB_KP) <= 128 ? 128u : (rt * (nc + TB_KP) <= 256 ? 256u : 512u);
+}
 
 struct __align__(8) TbTail {
     uint64_t stage_done[TB_MAX_STAGES];
@@ -54,25 +60,29 @@ struct __align__(8) TbTail {
     int item;
 };
 
-__host__ __device__ constexpr size_t tb_smem(int nc, int st) {
-    return 1024 + st * (size_t)tb_stage_bytes(nc) + (size_t)(nc / 64) * TB_KP * 128 + sizeof(TbTail);
+__host__ __device__ constexpr size_t tb_smem(int nc, int st, int rt) {
+    return 1024 + st * (size_t)tb_stage_bytes(nc, rt) + (size_t)((nc + 63) / 64) * TB_KP * 128 + sizeof(TbTail);
 }
 
 DSANLS_DEV int64_t pad8(int64_t x) { return (x + 7) & ~(int64_t)7; }
 
-template <int NC, bool PLAIN, int TB_STAGES>
+template <int NC, bool PLAIN, int TB_STAGES, int RT>
 __global__ void __launch_bounds__(TB_THREADS)
     kb_ar_tc(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
              int side, const __nv_bfloat16 *__restrict__ data_p, const __nv_bfloat16 *__restrict__ St_all,
              const __nv_bfloat16 *__restrict__ Yt_all, float *__restrict__ B_all, float *__restrict__ R_all,
              int *__restrict__ flag) {
-    static_assert(NC == 64 || NC == 128 || NC == 256, "chunk of 64, 128 or 256 columns");
+    static_assert(NC % 64 == 0 && NC >= 64 && NC <= 256, "chunk of 64 to 256 columns");
     static_assert(TB_STAGES >= 2 && TB_STAGES <= TB_MAX_STAGES, "2 to 4 stages");
-    constexpr int SB = tb_stage_bytes(NC);
-    constexpr uint32_t TCOLS = tb_tmem_cols(NC);
+    static_assert(RT == 1 || (RT == 2 && !PLAIN), "two row tiles only for the right-hand side");
+    static_assert(RT * (NC + TB_KP) <= 512, "tensor memory");
+    constexpr int SB = tb_stage_bytes(NC, RT);
+    constexpr int XB = RT * TB_BM * TB_BK * 2;  // bytes of the X tiles of a stage
+    constexpr uint32_t TCOLS = tb_tmem_cols(NC, RT);
+    static_assert(TB_BM * NC * 2 <= 2 * SB, "the A chunk fits over two stages");
     extern __shared__ __align__(1024) uint8_t tb_smem_raw[];
     uint8_t *base = tb_smem_raw + ((1024u - (smem_u32(tb_smem_raw) & 1023u)) & 1023u);
-    uint8_t *stages = base;                    // TB_STAGES x (X 16 KB | S^T chunk NC x 128 B); A2 after the K loop
+    uint8_t *stages = base;                    // TB_STAGES x (RT X tiles of 16 KB | S^T chunk NC x 128 B); A2 after the K loop
     uint8_t *btile = base + TB_STAGES * SB;    // NC / 64 atoms of TB_KP rows x 128 B
     TbTail *tail = reinterpret_cast<TbTail *>(btile + (NC / 64) * TB_KP * 128);
     uint8_t *a2 = stages;                      // 128 x NC bf16 (NC / 64 atoms of 16 KB) <= 2 stages
@@ -94,7 +104,7 @@ __global__ void __launch_bounds__(TB_THREADS)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tail->tmem_base;
-    const uint32_t d2col = (uint32_t)NC;
+    const uint32_t d2col = (uint32_t)(RT * NC);  // D1 of tile t at t NC, D2 of tile t at RT NC + t TB_KP
     uint32_t git = 0;            // stage loads so far (stage = git % TB_STAGES, its use git / TB_STAGES)
     uint32_t n_d1 = 0, n_d2 = 0;  // completions of the d1 / d2 barriers so far
     bool ok = true;
@@ -105,7 +115,7 @@ __global__ void __launch_bounds__(TB_THREADS)
         __syncthreads();
         if (it >= nitems) break;
         const BatchInst b = inst[items[it].x];
-        const int64_t r0 = (int64_t)items[it].y * TB_BM;
+        const int64_t r0 = (int64_t)items[it].y * (RT * TB_BM);
         const int k = b.k, dd = side == 0 ? b.d : b.dv;
         const int64_t K = side == 0 ? b.n : b.m;
         const int64_t rows = PLAIN ? dd : (side == 0 ? b.m : b.n);
@@ -125,14 +135,15 @@ __global__ void __launch_bounds__(TB_THREADS)
                 const uint32_t L = git + (uint32_t)kb, st = L % TB_STAGES, use = L / TB_STAGES;
                 if (use >= 1 && !mbar_wait(&tail->stage_done[st], (use - 1) & 1, TB_WAIT_NS)) return false;
                 uint8_t *sx = stages + st * SB;
-                uint8_t *ss = sx + TB_BM * TB_BK * 2;
+                uint8_t *ss = sx + XB;
                 const int64_t c0 = (int64_t)kb * TB_BK;
 #pragma unroll
-                for (int q = 0; q < (TB_BM * 8) / TB_THREADS; ++q) {  // X tile: 128 rows x 8 chunks of 8 bf16
-                    const int e = tid + q * TB_THREADS, r = e >> 3, ch = e & 7;
+                for (int q = 0; q < (RT * TB_BM * 8) / TB_THREADS; ++q) {  // X tiles: 128 rows x 8 chunks of 8 bf16
+                    const int e = tid + q * TB_THREADS, r = e >> 3, ch = e & 7;  // r: row of the RT tiles
                     const int64_t col = c0 + 8 * ch;
                     const bool in = r0 + r < rows && col < Kp;
-                    cp_async16(sx + sw128_off(r, 8 * ch, TB_BM), in ? (const void *)(X + (r0 + r) * Kp + col) : X, in);
+                    cp_async16(sx + (r >> 7) * (TB_BM * TB_BK * 2) + sw128_off(r & 127, 8 * ch, TB_BM),
+                               in ? (const void *)(X + (r0 + r) * Kp + col) : X, in);
                 }
                 for (int e = tid; e < N * 8; e += TB_THREADS) {  // S^T chunk: N rows x 8 chunks
                     const int j = e >> 3, ch = e & 7;
@@ -159,10 +170,13 @@ __global__ void __launch_bounds__(TB_THREADS)
                 if (tid == 0) {
                     fence_after();
                     const uint32_t st = (git + (uint32_t)kb) % TB_STAGES;
-                    const uint32_t ax = smem_u32(stages + st * SB), bx = ax + TB_BM * TB_BK * 2;
+                    const uint32_t ax = smem_u32(stages + st * SB), bx = ax + XB;
 #pragma unroll
-                    for (int kk = 0; kk < TB_BK / 16; ++kk)
-                        mma_bf16(tmem, sw128_desc(ax + kk * 32), sw128_desc(bx + kk * 32), id1, (kb | kk) != 0);
+                    for (int t = 0; t < RT; ++t)
+#pragma unroll
+                        for (int kk = 0; kk < TB_BK / 16; ++kk)
+                            mma_bf16(tmem + t * NC, sw128_desc(ax + t * (TB_BM * TB_BK * 2) + kk * 32),
+                                     sw128_desc(bx + kk * 32), id1, (kb | kk) != 0);
                     mma_commit(&tail->stage_done[st]);
                 }
                 const int next = kb + TB_STAGES - 1;
@@ -199,64 +213,67 @@ __global__ void __launch_bounds__(TB_THREADS)
                 fence_after();
                 continue;
             }
-            // A chunk (bf16) over the stages: warp w reads lanes 32 (w % 4).. of columns half (w / 4)
-            {
-                const int q4 = warp & 3, half = warp >> 2;
-                const int r = q4 * 32 + lane;
-                for (int cc = half * 32; cc < N; cc += 64) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + cc, v);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (cc + 8 * j >= N) break;
-                        uint4 w;
-                        w.x = pack_bf16(__uint_as_float(v[8 * j + 0]), __uint_as_float(v[8 * j + 1]));
-                        w.y = pack_bf16(__uint_as_float(v[8 * j + 2]), __uint_as_float(v[8 * j + 3]));
-                        w.z = pack_bf16(__uint_as_float(v[8 * j + 4]), __uint_as_float(v[8 * j + 5]));
-                        w.w = pack_bf16(__uint_as_float(v[8 * j + 6]), __uint_as_float(v[8 * j + 7]));
-                        *reinterpret_cast<uint4 *>(a2 + sw128_off(r, cc + 8 * j, TB_BM)) = w;
-                    }
-                }
-            }
-            // B chunk (bf16): TB_KP rows (zero past k) x N columns
+            // B chunk (bf16): TB_KP rows (zero past k) x N columns, shared by the row tiles
             for (int e = tid; e < TB_KP * N; e += TB_THREADS) {
                 const int c = e / N, j = e - c * N;
                 const float v = (c < k && dc + j < dd) ? B[(int64_t)c * dd + dc + j] : 0.0f;
                 *reinterpret_cast<__nv_bfloat16 *>(btile + sw128_off(c, j, TB_KP)) = __float2bfloat16_rn(v);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                fence_after();
-                const uint32_t id2 = idesc_bf16(TB_BM, TB_KP);
-                const uint32_t as = smem_u32(a2), bs = smem_u32(btile);
-                for (int kk = 0; kk < N / 16; ++kk) {
-                    const uint32_t ad = as + (kk >> 2) * (TB_BM * 128) + (kk & 3) * 32;
-                    const uint32_t bd = bs + (kk >> 2) * (TB_KP * 128) + (kk & 3) * 32;
-                    mma_bf16(tmem + d2col, sw128_desc(ad), sw128_desc(bd), id2, (dc | kk) != 0);
+            for (int t = 0; t < RT && ok; ++t) {
+                // A chunk of tile t (bf16) over the stages: warp w reads lanes 32 (w % 4).. of
+                // columns half (w / 4)
+                {
+                    const int q4 = warp & 3, half = warp >> 2;
+                    const int r = q4 * 32 + lane;
+                    for (int cc = half * 32; cc < N; cc += 64) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + t * NC + cc, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            if (cc + 8 * j >= N) break;
+                            uint4 w;
+                            w.x = pack_bf16(__uint_as_float(v[8 * j + 0]), __uint_as_float(v[8 * j + 1]));
+                            w.y = pack_bf16(__uint_as_float(v[8 * j + 2]), __uint_as_float(v[8 * j + 3]));
+                            w.z = pack_bf16(__uint_as_float(v[8 * j + 4]), __uint_as_float(v[8 * j + 5]));
+                            w.w = pack_bf16(__uint_as_float(v[8 * j + 6]), __uint_as_float(v[8 * j + 7]));
+                            *reinterpret_cast<uint4 *>(a2 + sw128_off(r, cc + 8 * j, TB_BM)) = w;
+                        }
+                    }
                 }
-                mma_commit(&tail->d2_done);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    fence_after();
+                    const uint32_t id2 = idesc_bf16(TB_BM, TB_KP);
+                    const uint32_t as = smem_u32(a2), bs = smem_u32(btile);
+                    for (int kk = 0; kk < N / 16; ++kk) {
+                        const uint32_t ad = as + (kk >> 2) * (TB_BM * 128) + (kk & 3) * 32;
+                        const uint32_t bd = bs + (kk >> 2) * (TB_KP * 128) + (kk & 3) * 32;
+                        mma_bf16(tmem + d2col + t * TB_KP, sw128_desc(ad), sw128_desc(bd), id2, (dc | kk) != 0);
+                    }
+                    mma_commit(&tail->d2_done);
+                }
+                // the next tile or chunk overwrites the A and B tiles: wait for these products
+                if (!mbar_wait(&tail->d2_done, n_d2 & 1, TB_WAIT_NS)) ok = false;
+                ++n_d2;
+                if (__syncthreads_or(!ok)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
             }
-            // the next chunk overwrites the A and B tiles: wait for these products
-            if (!mbar_wait(&tail->d2_done, n_d2 & 1, TB_WAIT_NS)) ok = false;
-            ++n_d2;
-            if (__syncthreads_or(!ok)) {
-                ok = false;
-                break;
-            }
-            fence_after();
         }
         if (!ok) break;
-        // R rows of the tile from D2 (warps 0-3: one TMEM lane = one row)
-        if (!PLAIN && warp < 4) {
-            const int r = warp * 32 + lane;
+        // R rows of the tiles from D2 (warps 0-3 tile 0, warps 4-7 tile 1: one TMEM lane = one row)
+        if (!PLAIN && warp < 4 * RT) {
+            const int t = warp >> 2, r = (warp & 3) * 32 + lane;
             uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + d2col, v);
+            tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + d2col + t * TB_KP, v);
             tmem_ld_wait();
-            if (r0 + r < rows) {
-                float *R = R_all + b.offR + (r0 + r) * k;
+            if (r0 + t * TB_BM + r < rows) {
+                float *R = R_all + b.offR + (r0 + t * TB_BM + r) * k;
 #pragma unroll
                 for (int c = 0; c < TB_KP; ++c)
                     if (c < k) R[c] = __uint_as_float(v[c]);
@@ -337,59 +354,72 @@ __global__ void kb_pad_bf16(const BatchInst *__restrict__ inst, const float *__r
 
 }  // namespace
 
-size_t batch_tc_smem(int nc, int st) { return tb_smem(nc, st); }
-
-void batch_prime_tc(int max_smem) {
-    allow_max_dynamic_smem(kb_ar_tc<64, false, 4>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<128, false, 4>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<128, false, 3>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<256, false, 4>, max_smem);
-    allow_max_dynamic_smem(kb_ar_tc<64, true, 4>, max_smem);
-}
+size_t batch_tc_smem(int nc, int st, int rt) { return tb_smem(nc, st, rt); }
 
 namespace {
-const void *ar_kernel(int nc, int st) {
-    if (nc == 64) return (const void *)kb_ar_tc<64, false, 4>;
-    if (nc == 128) return st == 3 ? (const void *)kb_ar_tc<128, false, 3> : (const void *)kb_ar_tc<128, false, 4>;
-    return (const void *)kb_ar_tc<256, false, 4>;
+// the tile configurations built: (chunk NC, ring stages, row tiles RT)
+struct ArKernel {
+    int nc, st, rt;
+    const void *fn;
+};
+const ArKernel kArKernels[] = {
+    {64, 4, 1, (const void *)kb_ar_tc<64, false, 4, 1>},   {128, 3, 1, (const void *)kb_ar_tc<128, false, 3, 1>},
+    {128, 4, 1, (const void *)kb_ar_tc<128, false, 4, 1>}, {256, 4, 1, (const void *)kb_ar_tc<256, false, 4, 1>},
+    {64, 4, 2, (const void *)kb_ar_tc<64, false, 4, 2>},   {128, 3, 2, (const void *)kb_ar_tc<128, false, 3, 2>},
+    {128, 4, 2, (const void *)kb_ar_tc<128, false, 4, 2>}, {192, 3, 2, (const void *)kb_ar_tc<192, false, 3, 2>},
+};
+const ArKernel &ar_kernel(int nc, int st, int rt) {
+    for (const ArKernel &a : kArKernels)
+        if (a.nc == nc && a.st == st && a.rt == rt) return a;
+    throw ArgError{"batched tensor-core product: no such tile configuration"};
 }
 }  // namespace
 
-int batch_tc_ctas_per_sm(int nc, int st) {
+bool batch_tc_tile_built(int nc, int st, int rt) {
+    for (const ArKernel &a : kArKernels)
+        if (a.nc == nc && a.st == st && a.rt == rt) return true;
+    return false;
+}
+
+void batch_prime_tc(int max_smem) {
+    for (const ArKernel &a : kArKernels) {
+        cudaFuncAttributes fa;
+        DSANLS_CUDA(cudaFuncGetAttributes(&fa, a.fn));
+        DSANLS_CUDA(cudaFuncSetAttribute(a.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_smem - (int)fa.sharedSizeBytes));
+    }
+    allow_max_dynamic_smem(kb_ar_tc<64, true, 4, 1>, max_smem);
+}
+
+int batch_tc_ctas_per_sm(int nc, int st, int rt) {
     int per_sm = 1;
-    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ar_kernel(nc, st), TB_THREADS, tb_smem(nc, st)));
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ar_kernel(nc, st, rt).fn, TB_THREADS,
+                                                              tb_smem(nc, st, rt)));
     // tensor memory: 512 columns per SM
-    return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(nc))));
+    return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(nc, rt))));
 }
 
 int batch_tc_b_ctas_per_sm() {
     int per_sm = 1;
-    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_ar_tc<64, true, 4>, TB_THREADS,
-                                                              tb_smem(64, 4)));
-    return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(64))));
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_ar_tc<64, true, 4, 1>, TB_THREADS,
+                                                              tb_smem(64, 4, 1)));
+    return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(64, 1))));
 }
 
-void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int st, int ctas, int *counter, cudaStream_t s) {
-    if (nc == 64)
-        kb_ar_tc<64, false, 4><<<ctas, TB_THREADS, tb_smem(64, 4), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
-                                                                         side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
-    else if (nc == 128 && st == 3)
-        kb_ar_tc<128, false, 3><<<ctas, TB_THREADS, tb_smem(128, 3), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
-                                                                           side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
-    else if (nc == 128)
-        kb_ar_tc<128, false, 4><<<ctas, TB_THREADS, tb_smem(128, 4), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
-                                                                           side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
-    else
-        kb_ar_tc<256, false, 4><<<ctas, TB_THREADS, tb_smem(256, 4), s>>>(g.inst, g.tcitems[side], g.ntc[side], counter,
-                                                                           side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
-    DSANLS_LAUNCH_CHECK();
+void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int st, int rt, int ctas, int *counter, cudaStream_t s) {
+    const ArKernel &a = ar_kernel(nc, st, rt);
+    const int2 *items = rt == 2 ? g.tcitems2[side] : g.tcitems[side];
+    int nitems = rt == 2 ? g.ntc2[side] : g.ntc[side];
+    void *args[] = {(void *)&g.inst, (void *)&items, (void *)&nitems, (void *)&counter, (void *)&side,
+                    (void *)&g.data_p, (void *)&g.St, (void *)&g.Yt, (void *)&g.B, (void *)&g.R, (void *)&g.flag};
+    DSANLS_CUDA(cudaLaunchKernel(a.fn, dim3((unsigned)ctas), dim3(TB_THREADS), args, tb_smem(nc, st, rt), s));
 }
 
 void launch_batch_b_tc(const BatchDev &g, int side, int ctas, int *counter, cudaStream_t s) {
     kb_yt<<<dim3(4, (unsigned)g.count), 256, 0, s>>>(g.inst, side, g.factors, g.Yt);
     DSANLS_LAUNCH_CHECK();
-    kb_ar_tc<64, true, 4><<<ctas, TB_THREADS, tb_smem(64, 4), s>>>(g.inst, g.tcbitems[side], g.ntcb[side], counter, side,
-                                                                    g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
+    kb_ar_tc<64, true, 4, 1><<<ctas, TB_THREADS, tb_smem(64, 4, 1), s>>>(g.inst, g.tcbitems[side], g.ntcb[side], counter,
+                                                                          side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
     DSANLS_LAUNCH_CHECK();
 }
 

@@ -180,10 +180,51 @@ def test_batch_bf16_one_iteration(pkg, order):
     b.close()
 
 
+TILES = [(64, 4, 1), (128, 3, 1), (128, 4, 1), (256, 4, 1), (64, 4, 2), (128, 3, 2), (128, 4, 2), (192, 3, 2)]
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_batch_bf16_every_tile(pkg, tile):
+    """Each tile of the tensor-core product pinned in turn (chunk of sketch columns,
+    ring stages, one or two 128-row tiles per work item): every instance within the
+    derived bound of the exact oracle.  The shapes give pairs of row tiles whose
+    second tile is ragged or empty (257 and 64 rows) and sketches of several chunks
+    (d' = 512, d = 256)."""
+    Ms = _inputs(SHAPES)
+    b = pkg.Batch(SHAPES, use_graph=1, precision=pkg.BF16)
+    b.set_tile(*tile)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(1)
+    chunk, ctas, row_tiles = b.tuned_tile()
+    assert (chunk, row_tiles) == (tile[0], tile[2]) and ctas > 0
+    mu = method.mu_t(1.0, 1.0, 0)
+    for i, (s, M) in enumerate(zip(SHAPES, Ms)):
+        U, V = b.factors(i)
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        M64 = M.astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, s["seed"], 0, 0, s["n"], s["d"])
+        rel, rb = bounds.check(U, M64, V0.astype(np.float64), U0.astype(np.float64), S, 0, mu, "bf16")
+        assert rel <= rb, (tile, i, rel, rb)
+        Sp = method.Sketch(method.GAUSSIAN, s["seed"], 0, 1, s["m"], s["d_v"])
+        rel, rb = bounds.check(V, M64.T, U.astype(np.float64), V0.astype(np.float64), Sp, 0, mu, "bf16")
+        assert rel <= rb, (tile, i, rel, rb)
+    b.close()
+
+
+def test_batch_set_tile_rejects_unbuilt_tiles(pkg):
+    b = pkg.Batch(SHAPES[:2], precision=pkg.BF16)
+    for bad in [(96, 3, 2), (256, 4, 2), (128, 2, 1), (64, 4, 3)]:
+        with pytest.raises(pkg.DSANLSError):
+            b.set_tile(*bad)
+    b.set_tile(0, 0, 0)  # back to the autotuner
+    b.close()
+
+
 def test_batch_bf16_tensor_core_tile_is_tuned(pkg):
     """The bf16 paper order runs R_i = (X_i S_i) B_i^T on tensor cores; the
-    autotuner times the candidate tiles (64-, 128- and 256-column chunks of the
-    sketch, each with its CTAs per SM) on the real batch -- every candidate
+    autotuner times the candidate tiles (64- to 256-column chunks of the sketch,
+    one or two 128-row tiles per work item, each with its CTAs per SM) on the real batch -- every candidate
     runs a full iteration, with the factors restored after each -- and keeps
     one; the first iteration then matches a second handle that reuses the
     cached choice bit for bit."""
@@ -194,8 +235,8 @@ def test_batch_bf16_tensor_core_tile_is_tuned(pkg):
         for i, M in enumerate(Ms):
             b.set_dense(i, M)
         b.step(1)
-        chunk, ctas = b.tuned_tile()
-        assert chunk in (64, 128, 256) and ctas > 0
+        chunk, ctas, row_tiles = b.tuned_tile()
+        assert (chunk, row_tiles) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (192, 2)) and ctas > 0
         out.append([b.factors(i) for i in range(len(SHAPES))])
         b.close()
     for (u0, v0), (u1, v1) in zip(*out):
