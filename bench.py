@@ -418,6 +418,46 @@ def time_to_eps(pkg, torch, M, w, T, check_every, stream):
     return out
 
 
+def time_to_eps_sparse(pkg, torch, M, w, T, check_every, stream):
+    """Sparse data (subsampling sketch): the FP32 path against the bf16-factor form
+    with its last 3 iterations in FP32, as time_to_eps does for dense data; eps is
+    the FP32 path's error after T iterations + 1e-3."""
+    def trajectory(prec_plan):
+        h = pkg.DSANLS(w["m"], w["n"], w["k"], w["d"], w["sketch"], seed=0, d_v=w["d_v"], solver=pkg.PGD,
+                       precision=prec_plan[0], use_graph=1)
+        h.set_csr(*M)
+        errs, total_ms = [], 0.0
+        for it in range(T):
+            if prec_plan[1] != prec_plan[0] and it == T - 3:
+                h.set_options(precision=prec_plan[1])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            if (it + 1) % check_every == 0 or it == T - 1:
+                errs.append((it + 1, total_ms, h.rel_error()))
+        h.close()
+        return errs
+
+    fp32 = trajectory((pkg.FP32, pkg.FP32))
+    eps = fp32[-1][2] + 1e-3
+    bf16 = trajectory((pkg.BF16, pkg.FP32))
+
+    def first_hit(tr):
+        for it, ms, e in tr:
+            if e <= eps:
+                return {"iters": it, "seconds": ms / 1000.0, "err": e}
+        return None
+
+    a, b = first_hit(fp32), first_hit(bf16)
+    return {"eps": eps, "T": T, "checked_every": check_every,
+            "fp32": {"to_eps": a, "final_err": fp32[-1][2], "seconds_T": fp32[-1][1] / 1000.0},
+            "bf16_factors_closing_fp32": {"to_eps": b, "final_err": bf16[-1][2], "seconds_T": bf16[-1][1] / 1000.0,
+                                          "speedup_time_to_eps": (a["seconds"] / b["seconds"]) if (a and b) else None}}
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -585,6 +625,8 @@ def run_ours(args, w):
     tte = None
     if rank == 0 and args.time_to_eps > 0 and w["sketch"] == 0:
         tte = time_to_eps(pkg, torch, M, w, args.time_to_eps, 5, stream)
+    elif rank == 0 and args.time_to_eps > 0 and w.get("sparse"):
+        tte = time_to_eps_sparse(pkg, torch, M, w, args.time_to_eps, 5, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -242,6 +242,16 @@ int dsanls_kernel_launches(uint64_t *out);
  * symbols cannot be written.  Synchronous. */
 int dsanls_debug_fail_alloc_after(int64_t n);
 int dsanls_debug_tc_wait(uint64_t wait_ns, int32_t starve);
+/* Index checks of the debug build: a library compiled with -DDSANLS_BOUNDS
+ * (paper_2009_02845_gb300.build.build(bounds=True) -> libdsanls_bounds.so)
+ * checks every index it takes from the data -- the columns of a CSR, the row
+ * keys and scatter destinations of the sub-CSR build -- against its array,
+ * skips an access that would leave it and counts it.  out[0] = failed checks
+ * since the last reset, out[1] = site code of the first (101-105: sub-CSR
+ * gather, scatter and right-hand side; 201-202: CSR product), out[2] = its
+ * index; reset = 1 clears them.  Returns 1 in the checking build, 0 in the
+ * normal one (out all 0), EINVAL for a NULL out.  Synchronous. */
+int dsanls_debug_bounds_report(int32_t reset, int64_t *out);
 
 /* Message of the last failed call on handle h; with h == NULL, of the last
  * failed dsanls_create or stateless primitive on the calling thread ("" if

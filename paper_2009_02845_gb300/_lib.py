@@ -29,7 +29,7 @@ EXPORTED_SYMBOLS = [
     "dsanls_batch_last_error", "dsanls_batch_destroy",
     "dsanls_mlp_create", "dsanls_mlp_param_count", "dsanls_mlp_get_params", "dsanls_mlp_set_params",
     "dsanls_mlp_predict", "dsanls_mlp_train_step", "dsanls_mlp_destroy", "dsanls_set_mlp", "dsanls_mlp_kept",
-    "dsanls_harvest", "dsanls_debug_fail_alloc_after", "dsanls_debug_tc_wait",
+    "dsanls_harvest", "dsanls_debug_fail_alloc_after", "dsanls_debug_tc_wait", "dsanls_debug_bounds_report",
 ]
 NPHASES = 7
 PHASES = ["sketch", "B", "product", "rhs", "gram", "step_size", "update"]
@@ -124,6 +124,7 @@ def lib():
             "dsanls_harvest": ([vp, i32, i32, vp, vp, vp, vp], ctypes.c_int),
             "dsanls_debug_fail_alloc_after": ([i64], ctypes.c_int),
             "dsanls_debug_tc_wait": ([u64, i32], ctypes.c_int),
+            "dsanls_debug_bounds_report": ([i32, ctypes.POINTER(i64)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -177,6 +178,24 @@ def debug_tc_wait(wait_ns=0, starve=False):
     device: a limit of wait_ns (0: the default 2 s) and, with starve, a GEMM
     producer that issues no copy so the waits run out."""
     _check(lib().dsanls_debug_tc_wait(int(wait_ns), int(bool(starve))), "debug_tc_wait")
+
+
+def use_bounds_build():
+    """Load libdsanls_bounds.so (the index-checking debug build) instead of
+    libdsanls.so; call before anything else loads the library."""
+    global lib_path
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    lib_path = os.path.join(_PKG, "libdsanls_bounds.so")
+
+
+def debug_bounds_report(reset=False):
+    """(checking build?, failed index checks, site of the first, its index)."""
+    out = (ctypes.c_int64 * 3)()
+    rc = lib().dsanls_debug_bounds_report(int(bool(reset)), out)
+    if rc < 0:
+        _check(rc, "debug_bounds_report")
+    return bool(rc), int(out[0]), int(out[1]), int(out[2])
 
 
 def gram_noalloc(B, G=None):

@@ -1,8 +1,11 @@
 """Build libdsanls.so in-tree with nvcc for sm_103a (GB300).
 
-Usage: python -m paper_2009_02845_gb300.build  (or build() from Python).
+Usage: python -m paper_2009_02845_gb300.build [--bounds]  (or build() from Python).
 Each .cu file compiles in parallel to _build/*.o; the objects link into
-paper_2009_02845_gb300/libdsanls.so.  Rebuilds only what changed.
+paper_2009_02845_gb300/libdsanls.so.  Rebuilds only what changed.  With
+bounds=True the same sources compile with -DDSANLS_BOUNDS (index checks of
+the indices taken from the data; csrc/bounds.cuh) into _build_bounds/ and
+libdsanls_bounds.so, a debug build beside the normal one.
 """
 import concurrent.futures as cf
 import glob
@@ -15,6 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdsanls.so")
+BUILD_BOUNDS = os.path.join(PKG, "_build_bounds")
+LIB_BOUNDS = os.path.join(PKG, "libdsanls_bounds.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I" + os.path.join(ROOT, "include")]
@@ -32,18 +37,20 @@ def _deps_mtime():
     return max(os.path.getmtime(f) for f in files) if files else 0.0
 
 
-def build(verbose=False, force=False):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, force=False, bounds=False):
+    build_dir, lib = (BUILD_BOUNDS, LIB_BOUNDS) if bounds else (BUILD, LIB)
+    flags = NVCC_FLAGS + (["-DDSANLS_BOUNDS"] if bounds else [])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     dep_t = _deps_mtime()
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         if (not force and os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
                 and os.path.getmtime(obj) >= dep_t):
             return obj, None
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             return obj, "%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr)
@@ -57,15 +64,15 @@ def build(verbose=False, force=False):
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     objs = [o for o, _ in results]
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, bounds="--bounds" in sys.argv))

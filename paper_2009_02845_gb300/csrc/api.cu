@@ -483,7 +483,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
                 g.C = h->R; g.ldc = k; g.alpha = 1.0f; g.splits = 1;
                 launch_sgemm(g, s);
             } else {
-                launch_spmm_rows(xp, xc, xv, rows, h->P, k, k, 1.0f, h->R, k, s);
+                launch_spmm_rows(xp, xc, xv, rows, h->P, K, k, k, 1.0f, h->R, k, s);
             }
         } else if (tc) {
             // R = (X S) B^T on tcgen05, X and S in bf16, A never stored
@@ -510,7 +510,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
                 g.C = h->A; g.ldc = dd; g.alpha = 1.0f; g.splits = 1;
                 launch_sgemm(g, s);
             } else {
-                launch_spmm_rows(xp, xc, xv, rows, h->S, dd, dd, 1.0f, h->A, dd, s);
+                launch_spmm_rows(xp, xc, xv, rows, h->S, K, dd, dd, 1.0f, h->A, dd, s);
             }
             mark(pe, DSANLS_PHASE_RHS, s);
             GemmArgs g{};
@@ -549,9 +549,9 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             const float *ytv = side == 0 ? h->tcv : h->cv;
             launch_subcsr_build(ytp, ytc, ytv, h->J, dd, h->sub[side], s);
             if (h->U16)
-                launch_subcsr_rows(h->sub[side], Y16, k, c2, h->R, s);
+                launch_subcsr_rows(h->sub[side], Y16, K, k, c2, h->R, s);
             else
-                launch_subcsr_rows(h->sub[side], Y, k, c2, h->R, s);
+                launch_subcsr_rows(h->sub[side], Y, K, k, c2, h->R, s);
         }
     } else {  // identity
         mark(pe, DSANLS_PHASE_B, s);
@@ -572,7 +572,7 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             g.C = h->R; g.ldc = k; g.alpha = 1.0f; g.splits = 1;
             launch_sgemm(g, s);
         } else {
-            launch_spmm_rows(xp, xc, xv, rows, Y, k, k, 1.0f, h->R, k, s);
+            launch_spmm_rows(xp, xc, xv, rows, Y, K, k, k, 1.0f, h->R, k, s);
         }
     }
     if (forked) {
@@ -1227,6 +1227,23 @@ int dsanls_debug_tc_wait(uint64_t wait_ns, int32_t starve) {
     return guarded(nullptr, [&]() {
         set_tc_wait_debug(wait_ns, starve);
         return DSANLS_OK;
+    });
+}
+
+int dsanls_debug_bounds_report(int32_t reset, int64_t *out) {
+    if (!out) return DSANLS_EINVAL;
+    return guarded(nullptr, [&]() {
+        int64_t a[3], b[3];
+        bounds_report_subcsr(reset, a);
+        bounds_report_sparse(reset, b);
+        out[0] = a[0] + b[0];
+        out[1] = a[0] ? a[1] : b[1];
+        out[2] = a[0] ? a[2] : b[2];
+#ifdef DSANLS_BOUNDS
+        return 1;
+#else
+        return 0;
+#endif
     });
 }
 

@@ -138,9 +138,10 @@ void launch_copy_cast_bf16(const float *in, int64_t n, __nv_bfloat16 *out, cudaS
 void launch_cast_f32(const __nv_bfloat16 *in, int64_t n, float *out, cudaStream_t s);
 
 // ---- sparse.cu ------------------------------------------------------------
-// out[i][0..w) = alpha * sum_{e in row i} val_e * D[col_e*ldd + 0..w)
+// out[i][0..w) = alpha * sum_{e in row i} val_e * D[col_e*ldd + 0..w), D with drows rows
 void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *val, int64_t rows,
-                      const float *D, int64_t ldd, int w, float alpha, float *out, int64_t ldo, cudaStream_t s);
+                      const float *D, int64_t drows, int64_t ldd, int w, float alpha, float *out, int64_t ldo,
+                      cudaStream_t s);
 // Sub-CSR of X[:, J] for a subsampling sketch on sparse X (rows x K): built
 // from the rows J of the CSR of X^T, entries stably sorted by row, so each
 // row's entries are in ascending column order.  Workspace for sampled sets of
@@ -164,6 +165,10 @@ void launch_subcsr_build(const int64_t *xtp, const int32_t *xtc, const float *xt
 // rows of at most 64 entries summed in ascending column order by one warp, longer
 // rows by a CTA (32 interleaved partial sums added in a fixed order).
 template <typename T>
-void launch_subcsr_rows(const SubCsr &sc, const T *Y, int k, float alpha, float *out, cudaStream_t s);
+void launch_subcsr_rows(const SubCsr &sc, const T *Y, int64_t yrows, int k, float alpha, float *out, cudaStream_t s);
+// Failed index checks of the debug build (-DDSANLS_BOUNDS) in subcsr.cu and sparse.cu:
+// out = (count, site of the first, its index), all 0 in the normal build; reset clears them.
+void bounds_report_subcsr(int reset, int64_t out[3]);
+void bounds_report_sparse(int reset, int64_t out[3]);
 
 }  // namespace dsanls

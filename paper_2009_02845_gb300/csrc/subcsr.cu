@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <new>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -130,7 +131,7 @@ __global__ void k_seg_len(const int64_t *__restrict__ xtp, const int32_t *__rest
 __global__ void __launch_bounds__(256)
     k_gather(const int64_t *__restrict__ xtp, const int32_t *__restrict__ xtc, const float *__restrict__ xtv,
              const int32_t *__restrict__ J, const int64_t *__restrict__ off, int d, int32_t *__restrict__ key,
-             int32_t *__restrict__ col, float *__restrict__ val, int32_t *__restrict__ cnt) {
+             int32_t *__restrict__ col, float *__restrict__ val, int32_t *__restrict__ cnt, int64_t cap, int64_t rows) {
     const int64_t total = off[d];
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(256)
         const int32_t j = __ldg(&J[lo]);
         const int64_t src = __ldg(&xtp[j]) + (e - __ldg(&off[lo]));
         const int32_t row = xtc[src];
+        if (!DSANLS_IN(e, cap, 101) || !DSANLS_IN(row, rows, 102)) continue;
         key[e] = row;
         col[e] = j;
         val[e] = xtv[src];
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(RADIX_THREADS)
             for (int w = 0; w < RADIX_WARPS; ++w) s += wcnt[w][threadIdx.x];
             base[threadIdx.x] += s;
         }
-        if (ok) {
+        if (ok && DSANLS_IN(dest, *total_p, 103)) {
             okey[dest] = key[e];
             ocol[dest] = col[e];
             oval[dest] = val[e];
@@ -235,7 +237,7 @@ __global__ void k_long_rows(const int64_t *__restrict__ ptr, int64_t rows, int32
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_sub_rows(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const float *__restrict__ val,
-               int64_t rows, const T *__restrict__ Y, int k, float alpha, float *__restrict__ out) {
+               int64_t rows, const T *__restrict__ Y, int64_t yrows, int k, float alpha, float *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -245,6 +247,7 @@ __global__ void __launch_bounds__(256)
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int64_t e = e0; e < e1; ++e) {
             const float v = val[e];
+            if (!DSANLS_IN(col[e], yrows, 104)) continue;
             const T *y = Y + (int64_t)col[e] * k;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -269,7 +272,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * LONG_WARPS)
     k_sub_rows_long(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const float *__restrict__ val,
                     const int32_t *__restrict__ list, const int32_t *__restrict__ nlong, const T *__restrict__ Y,
-                    int k, float alpha, float *__restrict__ out) {
+                    int64_t yrows, int k, float alpha, float *__restrict__ out) {
     __shared__ float part[LONG_WARPS][128];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = *nlong;
@@ -280,6 +283,7 @@ __global__ void __launch_bounds__(32 * LONG_WARPS)
 #pragma unroll 4
         for (int64_t e = e0 + warp; e < e1; e += LONG_WARPS) {
             const float v = val[e];
+            if (!DSANLS_IN(col[e], yrows, 105)) continue;
             const T *y = Y + (int64_t)col[e] * k;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -369,7 +373,8 @@ void launch_subcsr_build(const int64_t *xtp, const int32_t *xtc, const float *xt
     k_seg_len<<<(unsigned)ceil_div(d, 256), 256, 0, s>>>(xtp, J, d, sc.len);
     DSANLS_LAUNCH_CHECK();
     launch_scan<int64_t>(sc.len, d, sc.bsum, sc.off, s);
-    k_gather<<<152 * 8, 256, 0, s>>>(xtp, xtc, xtv, J, sc.off, d, sc.key[0], sc.col[0], sc.val[0], sc.cnt);
+    k_gather<<<152 * 8, 256, 0, s>>>(xtp, xtc, xtv, J, sc.off, d, sc.key[0], sc.col[0], sc.val[0], sc.cnt, sc.cap,
+                                     sc.rows);
     DSANLS_LAUNCH_CHECK();
     const int64_t *total = sc.off + d;
     const int passes = key_passes(sc.rows);
@@ -393,18 +398,28 @@ void launch_subcsr_build(const int64_t *xtp, const int32_t *xtc, const float *xt
 }
 
 template <typename T>
-void launch_subcsr_rows(const SubCsr &sc, const T *Y, int k, float alpha, float *out, cudaStream_t s) {
+void launch_subcsr_rows(const SubCsr &sc, const T *Y, int64_t yrows, int k, float alpha, float *out, cudaStream_t s) {
     if (sc.rows <= 0) return;
     int64_t blocks = ceil_div(sc.rows, 8);
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_sub_rows<T><<<(unsigned)blocks, 256, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.rows, Y, k, alpha, out);
+    k_sub_rows<T><<<(unsigned)blocks, 256, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.rows, Y, yrows, k, alpha,
+                                                   out);
     DSANLS_LAUNCH_CHECK();
     k_sub_rows_long<T><<<152 * 2, 32 * LONG_WARPS, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.longs + 1,
-                                                           sc.longs, Y, k, alpha, out);
+                                                           sc.longs, Y, yrows, k, alpha, out);
     DSANLS_LAUNCH_CHECK();
 }
-template void launch_subcsr_rows<float>(const SubCsr &, const float *, int, float, float *, cudaStream_t);
-template void launch_subcsr_rows<__nv_bfloat16>(const SubCsr &, const __nv_bfloat16 *, int, float, float *,
+template void launch_subcsr_rows<float>(const SubCsr &, const float *, int64_t, int, float, float *, cudaStream_t);
+template void launch_subcsr_rows<__nv_bfloat16>(const SubCsr &, const __nv_bfloat16 *, int64_t, int, float, float *,
                                                 cudaStream_t);
+
+void bounds_report_subcsr(int reset, int64_t out[3]) {
+#ifdef DSANLS_BOUNDS
+    bounds_read_tu(reset, out);
+#else
+    (void)reset;
+    out[0] = out[1] = out[2] = 0;
+#endif
+}
 
 }  // namespace dsanls
