@@ -363,8 +363,8 @@ int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas);
 int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles);
 /* Pin the tile of the tensor-core product instead of letting the autotuner time
  * the candidates: (chunk, stages, row_tiles) one of (64,4,1) (128,3,1) (128,4,1)
- * (256,4,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2); (0,0,0) returns to the
- * autotuner.  Takes effect at the next step (the iteration graph is rebuilt);
+ * (256,4,1) (64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2) (64,2,2); (0,0,0)
+ * returns to the autotuner.  Takes effect at the next step (the iteration graph is rebuilt);
  * other configurations return EINVAL and change nothing. */
 int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles);
 const char *dsanls_batch_last_error(dsanls_batch_t b);

@@ -866,14 +866,32 @@ int dsanls_set_dense(dsanls_t h, const float *M, int64_t ld, int32_t on_device) 
         const bool refresh = h->has_dense && h->M && h->MT;
         if (!h->M) dalloc(h->M, h->m * h->n);
         if (!h->MT) dalloc(h->MT, h->m * h->n);
-        DSANLS_CUDA(cudaMemcpy2DAsync(h->M, h->n * sizeof(float), M, ld * sizeof(float), h->n * sizeof(float), h->m,
-                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        launch_transpose(h->M, h->n, h->m, h->n, h->MT, h->m, s);
+        const bool bf16 = h->opt.precision == DSANLS_PREC_BF16, fp8 = h->opt.precision == DSANLS_PREC_FP8;
+        const bool cast_b = refresh && bf16 && h->Mb;
+        if (on_device) {
+            DSANLS_CUDA(cudaMemcpy2DAsync(h->M, h->n * sizeof(float), M, ld * sizeof(float), h->n * sizeof(float),
+                                          h->m, cudaMemcpyDeviceToDevice, s));
+            launch_transpose(h->M, h->n, h->m, h->n, h->MT, h->m, s);
+            if (cast_b) launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, s);
+        } else {
+            // host data: copied in chunks of rows (about 256 MB); the transpose (and bf16
+            // copy) of a chunk runs on the second stream while the next chunk is copied
+            const int64_t ch = std::max<int64_t>(1024, ((int64_t)256 << 20) / (h->n * (int64_t)sizeof(float)));
+            for (int64_t r0 = 0; r0 < h->m; r0 += ch) {
+                const int64_t rc = std::min(ch, h->m - r0);
+                DSANLS_CUDA(cudaMemcpy2DAsync(h->M + r0 * h->n, h->n * sizeof(float), M + r0 * ld, ld * sizeof(float),
+                                              h->n * sizeof(float), rc, cudaMemcpyHostToDevice, s));
+                DSANLS_CUDA(cudaEventRecord(h->ev_fork, s));
+                DSANLS_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+                launch_transpose(h->M + r0 * h->n, h->n, rc, h->n, h->MT + r0, h->m, h->aux_stream);
+                if (cast_b) launch_copy_cast_bf16(h->M + r0 * h->n, rc * h->n, h->Mb + r0 * h->n, h->aux_stream);
+            }
+            DSANLS_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
+            DSANLS_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+        }
         h->sumsq_dirty = true;  // ||M||^2 is computed when a relative error or the bound needs it
         h->has_dense = true;
-        const bool bf16 = h->opt.precision == DSANLS_PREC_BF16, fp8 = h->opt.precision == DSANLS_PREC_FP8;
-        if (refresh && bf16 && h->Mb) {
-            launch_copy_cast_bf16(h->M, h->m * h->n, h->Mb, s);
+        if (cast_b) {
             launch_copy_cast_bf16(h->MT, h->m * h->n, h->MTb, s);
         } else {
             dfree(h->Mb);

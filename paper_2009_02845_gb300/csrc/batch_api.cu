@@ -219,8 +219,8 @@ void autotune(dsanls_batch_ctx *b) {
         if (b->g.tc) {
             // (chunk, stages, row tiles): with one row tile 64/4 and 128/3 fit two CTAs per
             // SM, 128/4 and 256/4 one; two row tiles (the sketch chunk shared) run one CTA
-            const int tiles[8][3] = {{64, 4, 1}, {128, 3, 1}, {128, 4, 1}, {256, 4, 1},
-                                     {64, 4, 2}, {128, 3, 2}, {128, 4, 2}, {192, 3, 2}};
+            const int tiles[10][3] = {{64, 4, 1}, {128, 3, 1}, {128, 4, 1}, {256, 4, 1}, {64, 2, 1},
+                                      {64, 4, 2}, {128, 3, 2}, {128, 4, 2}, {192, 3, 2}, {64, 2, 2}};
             for (const auto &tl : tiles)
                 for (int c : {2, 4}) candidates.push_back(c * 100000 + tl[2] * 10000 + tl[1] * 1000 + tl[0]);
         } else {
@@ -595,8 +595,8 @@ int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32
         b->forced_tile = 0;
     } else {
         if (!batch_tc_tile_built(chunk, stages, row_tiles))
-            return bfail(b, DSANLS_EINVAL, "no such tile: (64,4,1) (128,3,1) (128,4,1) (256,4,1) (64,4,2) (128,3,2) "
-                                           "(128,4,2) (192,3,2)");
+            return bfail(b, DSANLS_EINVAL, "no such tile: (64,4,1) (128,3,1) (128,4,1) (256,4,1) (64,2,1) (64,4,2) "
+                                           "(128,3,2) (128,4,2) (192,3,2) (64,2,2)");
         b->forced_tile = 2 * 100000 + row_tiles * 10000 + stages * 1000 + chunk;
     }
     b->tuned = false;

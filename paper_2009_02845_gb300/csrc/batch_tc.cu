@@ -367,6 +367,8 @@ const ArKernel kArKernels[] = {
     {128, 4, 1, (const void *)kb_ar_tc<128, false, 4, 1>}, {256, 4, 1, (const void *)kb_ar_tc<256, false, 4, 1>},
     {64, 4, 2, (const void *)kb_ar_tc<64, false, 4, 2>},   {128, 3, 2, (const void *)kb_ar_tc<128, false, 3, 2>},
     {128, 4, 2, (const void *)kb_ar_tc<128, false, 4, 2>}, {192, 3, 2, (const void *)kb_ar_tc<192, false, 3, 2>},
+    // two-stage rings: small enough for two (RT = 2) or four (RT = 1) CTAs per SM
+    {64, 2, 1, (const void *)kb_ar_tc<64, false, 2, 1>},   {64, 2, 2, (const void *)kb_ar_tc<64, false, 2, 2>},
 };
 const ArKernel &ar_kernel(int nc, int st, int rt) {
     for (const ArKernel &a : kArKernels)

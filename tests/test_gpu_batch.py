@@ -180,7 +180,8 @@ def test_batch_bf16_one_iteration(pkg, order):
     b.close()
 
 
-TILES = [(64, 4, 1), (128, 3, 1), (128, 4, 1), (256, 4, 1), (64, 4, 2), (128, 3, 2), (128, 4, 2), (192, 3, 2)]
+TILES = [(64, 4, 1), (128, 3, 1), (128, 4, 1), (256, 4, 1), (64, 2, 1),
+         (64, 4, 2), (128, 3, 2), (128, 4, 2), (192, 3, 2), (64, 2, 2)]
 
 
 @pytest.mark.parametrize("tile", TILES)
@@ -236,7 +237,7 @@ def test_batch_bf16_tensor_core_tile_is_tuned(pkg):
             b.set_dense(i, M)
         b.step(1)
         chunk, ctas, row_tiles = b.tuned_tile()
-        assert (chunk, row_tiles) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (192, 2)) and ctas > 0
+        assert (chunk, row_tiles) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (192, 2)) and ctas > 0  # noqa
         out.append([b.factors(i) for i in range(len(SHAPES))])
         b.close()
     for (u0, v0), (u1, v1) in zip(*out):

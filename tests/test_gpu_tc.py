@@ -196,3 +196,32 @@ def test_sketch_drawn_inside_the_gemm_is_bitwise_the_prepass(pkg, case):
         out.append(h.factors())
         h.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16", "FP8"])
+def test_set_dense_refill_matches_a_fresh_handle(pkg, prec):
+    """A second set_dense on a handle refills M, its transpose and the reduced-precision
+    copies in place (host data arrives in row chunks, each chunk transposed and cast on
+    a second stream while the next is copied; 20,000 x 4,096 floats make two chunks):
+    the half-steps that follow are bit for bit those of a fresh handle given the same
+    data."""
+    m, n, k, d = 20000, 4096, 16, 64
+    p = getattr(pkg, prec)
+    M1, _, _ = planted_dense(m, n, 8, 31)
+    M2, _, _ = planted_dense(m, n, 8, 32)
+    U, V = initial_factors(m, n, k, 33)
+    out = []
+    for refill in (True, False):
+        h = pkg.DSANLS(m, n, k, d, pkg.GAUSSIAN, seed=4, precision=p, t=1)
+        if refill:
+            h.set_dense(M1)
+            h.step(1)
+            h.set_options(t=1)  # the same sketches as the fresh handle's
+        h.set_dense(M2)
+        h.set_factors(U, V)
+        h.half_step(0)
+        h.half_step(1)
+        out.append(h.factors())
+        h.close()
+    (u0, v0), (u1, v1) = out
+    assert np.array_equal(u0, u1) and np.array_equal(v0, v1)
