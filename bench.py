@@ -568,10 +568,16 @@ def run_ours(args, w):
         bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "sgemm_simt_gather"
         peak_note = "hbm_gbs of %s" % peak_src
     else:
-        # sparse subsampling: the row update reads Z and R and writes Z (12 bytes per entry;
-        # 8 with bf16 factors)
-        zb = 8.0 if prec == pkg.BF16 else 12.0
-        bytes_ = [zb * m * k, zb * n * k]
+        # sparse subsampling: the row update forms the right-hand side of the sampled entries
+        # itself -- it reads and writes Z (8 bytes per element; 4 with bf16 factors), the row
+        # pointers (8 bytes per row) and sampled entries (8 bytes each; nnz d / K expected) of
+        # the sub-CSR and the d sampled rows of the other factor (R only for the few rows of
+        # more than 64 entries, not counted)
+        zb = 4.0 if prec == pkg.BF16 else 8.0
+        es = 2.0 if prec == pkg.BF16 else 4.0
+        nnz = float(len(M[1]))
+        bytes_ = [zb * m * k + 8.0 * m + 8.0 * nnz * d / n + es * d * k,
+                  zb * n * k + 8.0 * n + 8.0 * nnz * d_v / m + es * d_v * k]
         prod_ms = [p["update"] for p in phases]
         achieved = sum(bytes_) / (sum(prod_ms) / 1000.0) / 1e9
         bound, peak, unit, kernel_key = "hbm", peaks["hbm_gbs"], "GB/s", "update"

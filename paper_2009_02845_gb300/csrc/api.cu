@@ -376,6 +376,8 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     const bool dense = h->has_dense;
     int64_t gram_d = dd;
     const int kp = kp_bucket(k);
+    bool fuse_sub = false;  // sparse subsampled data: short rows' R formed in the update
+    float fuse_c2 = 0.0f;
     // after B: the Gram and the step size on the aux stream, in parallel with R
     // (profiling keeps every phase in order on one stream)
     bool forked = false;
@@ -523,6 +525,11 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
     } else if (h->sketch == DSANLS_SKETCH_SUBSAMPLE) {
         const float c = (float)std::sqrt((double)K / (double)dd);
         const float c2 = c * c;
+        // sparse data with one PGD step on tensor cores: the right-hand side of the
+        // short sub-CSR rows is formed inside the update (R is neither written nor read)
+        fuse_sub = !dense && update && !h->mlp && h->opt.solver == DSANLS_SOLVER_PGD && h->opt.inner_iters == 1 &&
+                   update_tc_supported(k);
+        fuse_c2 = c2;
         launch_subsample(h->seed, (uint32_t)side, 0, h->t_dev, K, dd, h->J, h->bits, s);
         mark(pe, DSANLS_PHASE_B, s);
         const __nv_bfloat16 *Y16 = side == 0 ? h->V16 : h->U16;
@@ -548,10 +555,16 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
             const int32_t *ytc = side == 0 ? h->tci : h->ci;
             const float *ytv = side == 0 ? h->tcv : h->cv;
             launch_subcsr_build(ytp, ytc, ytv, h->J, dd, h->sub[side], s);
-            if (h->U16)
+            if (fuse_sub) {  // short rows: formed inside the row update
+                if (h->U16)
+                    launch_subcsr_long_rows(h->sub[side], Y16, K, k, c2, h->R, s);
+                else
+                    launch_subcsr_long_rows(h->sub[side], Y, K, k, c2, h->R, s);
+            } else if (h->U16) {
                 launch_subcsr_rows(h->sub[side], Y16, K, k, c2, h->R, s);
-            else
+            } else {
                 launch_subcsr_rows(h->sub[side], Y, K, k, c2, h->R, s);
+            }
         }
     } else {  // identity
         mark(pe, DSANLS_PHASE_B, s);
@@ -590,6 +603,12 @@ void half_step(dsanls_ctx *h, int side, cudaStream_t s, PhaseEvents *pe = nullpt
         mlp_learned_update(h->mlp->st, Z, h->R, rows, h->G64[side], h->Gf, kp, h->scal[side], h->pg_iters,
                            h->opt.inner_iters, h->kept,
                            h->flag, s);
+    else if (fuse_sub && h->U16)
+        launch_update_tc_subcsr(side == 0 ? h->U16 : h->V16, h->R, h->sub[side], side == 0 ? h->V16 : h->U16, K,
+                                fuse_c2, rows, k, h->Gf, kp, h->scal[side], h->bound, h->flag, s);
+    else if (fuse_sub)
+        launch_update_tc_subcsr(Z, h->R, h->sub[side], Y, K, fuse_c2, rows, k, h->Gf, kp, h->scal[side], h->bound,
+                                h->flag, s);
     else if (h->U16)  // bf16 factors: one PGD step on tensor cores (checked at set_options)
         launch_update_tc(side == 0 ? h->U16 : h->V16, h->R, rows, k, h->Gf, kp, h->scal[side], h->bound, h->flag, s);
     else
@@ -1251,12 +1270,13 @@ int dsanls_debug_tc_wait(uint64_t wait_ns, int32_t starve) {
 int dsanls_debug_bounds_report(int32_t reset, int64_t *out) {
     if (!out) return DSANLS_EINVAL;
     return guarded(nullptr, [&]() {
-        int64_t a[3], b[3];
+        int64_t a[3], b[3], c[3];
         bounds_report_subcsr(reset, a);
         bounds_report_sparse(reset, b);
-        out[0] = a[0] + b[0];
-        out[1] = a[0] ? a[1] : b[1];
-        out[2] = a[0] ? a[2] : b[2];
+        bounds_report_tc(reset, c);
+        out[0] = a[0] + b[0] + c[0];
+        out[1] = a[0] ? a[1] : (b[0] ? b[1] : c[1]);
+        out[2] = a[0] ? a[2] : (b[0] ? b[2] : c[2]);
 #ifdef DSANLS_BOUNDS
         return 1;
 #else

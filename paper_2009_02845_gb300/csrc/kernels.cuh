@@ -148,6 +148,10 @@ void launch_spmm_rows(const int64_t *rowptr, const int32_t *col, const float *va
 // up to dmax columns holding at most cap entries in total (cap = the sum of
 // the dmax longest columns of X, so no J can overflow it).  After a build,
 // row i's entries are [ptr[i], ptr[i+1]) of col[cur] / val[cur].
+// Rows of a sub-CSR with more than this many entries are long: their right-hand
+// side is summed by a whole CTA (launch_subcsr_rows, launch_subcsr_long_rows).
+constexpr int64_t SUB_LONG = 64;
+
 struct SubCsr {
     int64_t rows = 0, cap = 0;
     int dmax = 0, cur = 0;
@@ -166,6 +170,10 @@ void launch_subcsr_build(const int64_t *xtp, const int32_t *xtc, const float *xt
 // rows by a CTA (32 interleaved partial sums added in a fixed order).
 template <typename T>
 void launch_subcsr_rows(const SubCsr &sc, const T *Y, int64_t yrows, int k, float alpha, float *out, cudaStream_t s);
+// only the long rows (more than SUB_LONG entries) of launch_subcsr_rows
+template <typename T>
+void launch_subcsr_long_rows(const SubCsr &sc, const T *Y, int64_t yrows, int k, float alpha, float *out,
+                             cudaStream_t s);
 // Failed index checks of the debug build (-DDSANLS_BOUNDS) in subcsr.cu and sparse.cu:
 // out = (count, site of the first, its index), all 0 in the normal build; reset clears them.
 void bounds_report_subcsr(int reset, int64_t out[3]);

@@ -225,7 +225,6 @@ __global__ void __launch_bounds__(RADIX_THREADS)
 // Rows with more than SUB_LONG sampled entries (popular columns of a skewed
 // matrix gather thousands) are listed by k_long_rows and summed by a whole CTA
 // of 32 warps; the rest by one warp each.
-constexpr int64_t SUB_LONG = 64;
 
 __global__ void k_long_rows(const int64_t *__restrict__ ptr, int64_t rows, int32_t *__restrict__ list,
                             int32_t *__restrict__ nlong) {
@@ -412,6 +411,19 @@ void launch_subcsr_rows(const SubCsr &sc, const T *Y, int64_t yrows, int k, floa
 template void launch_subcsr_rows<float>(const SubCsr &, const float *, int64_t, int, float, float *, cudaStream_t);
 template void launch_subcsr_rows<__nv_bfloat16>(const SubCsr &, const __nv_bfloat16 *, int64_t, int, float, float *,
                                                 cudaStream_t);
+
+template <typename T>
+void launch_subcsr_long_rows(const SubCsr &sc, const T *Y, int64_t yrows, int k, float alpha, float *out,
+                             cudaStream_t s) {
+    if (sc.rows <= 0) return;
+    k_sub_rows_long<T><<<152 * 2, 32 * LONG_WARPS, 0, s>>>(sc.ptr, sc.col[sc.cur], sc.val[sc.cur], sc.longs + 1,
+                                                           sc.longs, Y, yrows, k, alpha, out);
+    DSANLS_LAUNCH_CHECK();
+}
+template void launch_subcsr_long_rows<float>(const SubCsr &, const float *, int64_t, int, float, float *,
+                                             cudaStream_t);
+template void launch_subcsr_long_rows<__nv_bfloat16>(const SubCsr &, const __nv_bfloat16 *, int64_t, int, float,
+                                                     float *, cudaStream_t);
 
 void bounds_report_subcsr(int reset, int64_t out[3]) {
 #ifdef DSANLS_BOUNDS

@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
@@ -994,6 +995,28 @@ DSANLS_DEV void load_slice(const __nv_bfloat16 *p, int n, bool vec, float (&z)[3
         for (int j = 0; j < 32; ++j) z[j] = j < n ? __bfloat162float(p[j]) : 0.0f;
     }
 }
+// Four consecutive elements, `n` of them valid (vectorised as load_slice).
+DSANLS_DEV void load4(const float *p, int n, bool vec, float (&y)[4]) {
+    if (vec) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n >= 4) v = *reinterpret_cast<const float4 *>(p);
+        y[0] = v.x, y[1] = v.y, y[2] = v.z, y[3] = v.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = u < n ? p[u] : 0.0f;
+    }
+}
+DSANLS_DEV void load4(const __nv_bfloat16 *p, int n, bool vec, float (&y)[4]) {
+    if (vec) {
+        uint2 w = make_uint2(0u, 0u);
+        if (n >= 4) w = *reinterpret_cast<const uint2 *>(p);
+        y[0] = __uint_as_float(w.x << 16), y[1] = __uint_as_float(w.x & 0xffff0000u);
+        y[2] = __uint_as_float(w.y << 16), y[3] = __uint_as_float(w.y & 0xffff0000u);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = u < n ? __bfloat162float(p[u]) : 0.0f;
+    }
+}
 DSANLS_DEV void store4(float *p, float a, float b, float c, float d) {
     *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
 }
@@ -1006,11 +1029,26 @@ __host__ __device__ constexpr int upd_threads() {
     return KA * 256;  // 128 rows x (64 KA / 32) column slices
 }
 
-template <int KA, typename ZT>
+// Sparse subsampled data (SPR): the right-hand side of a row of at most SUB_LONG
+// sub-CSR entries is formed in the kernel, r = alpha * sum over the row's entries
+// (ascending) of val * Y[col][.], one fused multiply-add per entry and column --
+// the arithmetic of launch_subcsr_rows bit for bit -- so R is neither written nor
+// read for it; longer rows come precomputed in R (launch_subcsr_long_rows).
+template <typename ZT>
+struct UpdSub {
+    const int64_t *ptr;
+    const int32_t *col;
+    const float *val;
+    const ZT *Y;
+    int64_t yrows;
+    float alpha;
+};
+
+template <int KA, typename ZT, bool SPR>
 __global__ void __launch_bounds__(upd_threads<KA>())
     k_update_tc(ZT *__restrict__ Z, const float *__restrict__ R, int64_t rows, int k, int N,
                 const float *__restrict__ Gf, int kp, const double *__restrict__ scal, float bound,
-                int *__restrict__ flag, uint32_t tmem_cols, int zbuf_bytes, int use_bulk) {
+                int *__restrict__ flag, uint32_t tmem_cols, int zbuf_bytes, int use_bulk, UpdSub<ZT> sub) {
     constexpr bool ZBF = sizeof(ZT) == 2;
     constexpr int ZPARTS = ZBF ? 1 : 3;  // nonzero parts of the split of z
     constexpr int THREADS = upd_threads<KA>();
@@ -1092,8 +1130,15 @@ __global__ void __launch_bounds__(upd_threads<KA>())
         const bool rowok = row < nr;
         const int nv = rowok ? ncol : 0;  // valid entries of this thread's slice
         // 1. r of the row slice: in flight while z is split and the products run
+        //    (SPR: the row's entry range now, r while the products run)
         float rv[32];
-        load_slice(R + f0 + (int64_t)row * k + c0, nv, vec, rv);
+        int64_t e0 = 0, e1 = 0;
+        if (!SPR) {
+            load_slice(R + f0 + (int64_t)row * k + c0, nv, vec, rv);
+        } else if (rowok) {
+            e0 = sub.ptr[tile * UPD_BM + row];
+            e1 = sub.ptr[tile * UPD_BM + row + 1];
+        }
         // 2. z of the row slice, from the bulk-copied buffer (or from Z for a ragged
         //    last tile); the split parts go to tensor memory as the A operand
         bool ok = true;
@@ -1158,6 +1203,29 @@ __global__ void __launch_bounds__(upd_threads<KA>())
                     }
             mma_commit(&tail->done);
         }
+        if (SPR) {
+            if (e1 - e0 > SUB_LONG) {
+                load_slice(R + f0 + (int64_t)row * k + c0, nv, vec, rv);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) rv[c] = 0.0f;
+                for (int64_t e = e0; e < e1; ++e) {
+                    const float v = sub.val[e];
+                    const int32_t yr = sub.col[e];
+                    if (!DSANLS_IN(yr, sub.yrows, 301)) continue;
+                    const ZT *y = sub.Y + (int64_t)yr * k + c0;
+#pragma unroll
+                    for (int q4 = 0; q4 < 8; ++q4) {
+                        float y4[4];
+                        load4(y + 4 * q4, nv - 4 * q4, vec, y4);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) rv[4 * q4 + u] = __fmaf_rn(v, y4[u], rv[4 * q4 + u]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) rv[c] = __fmul_rn(sub.alpha, rv[c]);
+            }
+        }
         const bool got = mbar_wait(&tail->done, (uint32_t)(j & 1), wait_limit());
         if (__syncthreads_or(!got)) {
             if (tid == 0) atomicOr(flag, 2);
@@ -1217,9 +1285,9 @@ size_t update_tc_smem(int N, int zbuf_bytes) {
 bool update_tc_supported(int k) { return k > 32 && k <= 128; }
 
 namespace {
-template <int KA, typename ZT>
+template <int KA, typename ZT, bool SPR>
 void launch_update_tc_kind(ZT *Z, const float *R, int64_t rows, int k, int N, const float *Gf, int kp,
-                           const double *scal, float bound, int *flag, int sms, cudaStream_t s) {
+                           const double *scal, float bound, int *flag, int sms, UpdSub<ZT> sub, cudaStream_t s) {
     constexpr int zparts = sizeof(ZT) == 2 ? 1 : 3;
     const int need = KA * 64 + zparts * KA * 32;  // accumulator + A parts, TMEM columns
     uint32_t tmem_cols = 32;
@@ -1229,15 +1297,14 @@ void launch_update_tc_kind(ZT *Z, const float *R, int64_t rows, int k, int N, co
     const int use_bulk = (reinterpret_cast<uintptr_t>(Z) & 15) == 0;
     const int64_t ntiles = (rows + UPD_BM - 1) / UPD_BM;
     const int64_t grid = std::min<int64_t>(ntiles, sms);  // one CTA per SM (shared memory and TMEM)
-    k_update_tc<KA, ZT><<<(unsigned)grid, upd_threads<KA>(), smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound, flag,
-                                                                        tmem_cols, zb, use_bulk);
+    k_update_tc<KA, ZT, SPR><<<(unsigned)grid, upd_threads<KA>(), smem, s>>>(Z, R, rows, k, N, Gf, kp, scal, bound,
+                                                                             flag, tmem_cols, zb, use_bulk, sub);
     DSANLS_LAUNCH_CHECK();
 }
-}  // namespace
 
-template <typename ZT>
-void launch_update_tc(ZT *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
-                      float bound, int *flag, cudaStream_t s) {
+template <typename ZT, bool SPR>
+void launch_update_tc_any(ZT *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
+                          float bound, int *flag, UpdSub<ZT> sub, cudaStream_t s) {
     if (!update_tc_supported(k)) throw ArgError{"launch_update_tc: needs 32 < k <= 128"};
     if (rows <= 0) return;
     const int N = (k + 15) / 16 * 16;
@@ -1245,14 +1312,45 @@ void launch_update_tc(ZT *Z, const float *R, int64_t rows, int k, const float *G
     DSANLS_CUDA(cudaGetDevice(&dev));
     DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (k <= 64)
-        launch_update_tc_kind<1, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, sms, s);
+        launch_update_tc_kind<1, ZT, SPR>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, sms, sub, s);
     else
-        launch_update_tc_kind<2, ZT>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, sms, s);
+        launch_update_tc_kind<2, ZT, SPR>(Z, R, rows, k, N, Gf, kp, scal, bound, flag, sms, sub, s);
+}
+}  // namespace
+
+template <typename ZT>
+void launch_update_tc(ZT *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
+                      float bound, int *flag, cudaStream_t s) {
+    launch_update_tc_any<ZT, false>(Z, R, rows, k, Gf, kp, scal, bound, flag, UpdSub<ZT>{}, s);
 }
 template void launch_update_tc<float>(float *, const float *, int64_t, int, const float *, int, const double *, float,
                                       int *, cudaStream_t);
 template void launch_update_tc<__nv_bfloat16>(__nv_bfloat16 *, const float *, int64_t, int, const float *, int,
                                               const double *, float, int *, cudaStream_t);
+
+template <typename ZT>
+void launch_update_tc_subcsr(ZT *Z, const float *R, const SubCsr &sc, const ZT *Y, int64_t yrows, float alpha,
+                             int64_t rows, int k, const float *Gf, int kp, const double *scal, float bound, int *flag,
+                             cudaStream_t s) {
+    if (sc.rows != rows) throw ArgError{"launch_update_tc_subcsr: the sub-CSR has other rows"};
+    const UpdSub<ZT> sub{sc.ptr, sc.col[sc.cur], sc.val[sc.cur], Y, yrows, alpha};
+    launch_update_tc_any<ZT, true>(Z, R, rows, k, Gf, kp, scal, bound, flag, sub, s);
+}
+template void launch_update_tc_subcsr<float>(float *, const float *, const SubCsr &, const float *, int64_t, float,
+                                             int64_t, int, const float *, int, const double *, float, int *,
+                                             cudaStream_t);
+template void launch_update_tc_subcsr<__nv_bfloat16>(__nv_bfloat16 *, const float *, const SubCsr &,
+                                                     const __nv_bfloat16 *, int64_t, float, int64_t, int,
+                                                     const float *, int, const double *, float, int *, cudaStream_t);
+
+void bounds_report_tc(int reset, int64_t out[3]) {
+#ifdef DSANLS_BOUNDS
+    bounds_read_tu(reset, out);
+#else
+    (void)reset;
+    out[0] = out[1] = out[2] = 0;
+#endif
+}
 
 void set_tc_wait_debug(unsigned long long wait_ns, int starve) {
     DSANLS_CUDA(cudaMemcpyToSymbol(g_wait_ns, &wait_ns, sizeof(wait_ns)));
@@ -1260,10 +1358,14 @@ void set_tc_wait_debug(unsigned long long wait_ns, int starve) {
 }
 
 void prime_tc_attributes(int max_smem) {
-    allow_max_dynamic_smem(k_update_tc<1, float>, max_smem);
-    allow_max_dynamic_smem(k_update_tc<2, float>, max_smem);
-    allow_max_dynamic_smem(k_update_tc<1, __nv_bfloat16>, max_smem);
-    allow_max_dynamic_smem(k_update_tc<2, __nv_bfloat16>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<1, float, false>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<2, float, false>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<1, __nv_bfloat16, false>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<2, __nv_bfloat16, false>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<1, float, true>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<2, float, true>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<1, __nv_bfloat16, true>, max_smem);
+    allow_max_dynamic_smem(k_update_tc<2, __nv_bfloat16, true>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, true, false>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<3, true, false>, max_smem);
     allow_max_dynamic_smem(k_tc_gemm<4, false, false>, max_smem);

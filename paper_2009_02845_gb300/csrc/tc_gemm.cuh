@@ -88,6 +88,18 @@ bool update_tc_supported(int k);
 template <typename ZT>
 void launch_update_tc(ZT *Z, const float *R, int64_t rows, int k, const float *Gf, int kp, const double *scal,
                       float bound, int *flag, cudaStream_t s);
+struct SubCsr;
+// The same step with the right-hand side of sparse subsampled data formed inside
+// the kernel: r_i = alpha * sum over row i's sub-CSR entries (ascending) of
+// val * Y[col][.] -- the arithmetic of launch_subcsr_rows, bit for bit -- except
+// for rows of more than SUB_LONG entries, whose r the caller has written to R
+// (launch_subcsr_long_rows).  Y (yrows x k) has the type of Z.
+template <typename ZT>
+void launch_update_tc_subcsr(ZT *Z, const float *R, const SubCsr &sc, const ZT *Y, int64_t yrows, float alpha,
+                             int64_t rows, int k, const float *Gf, int kp, const double *scal, float bound, int *flag,
+                             cudaStream_t s);
+// failed index checks of the debug build in tc_gemm.cu (see bounds_report_subcsr)
+void bounds_report_tc(int reset, int64_t out[3]);
 void prime_tc_attributes(int max_smem);
 // Test switch of the bounded waits on the current device: wait_ns > 0 replaces the
 // 2 s limit (0 restores it); starve = 1 makes the producer of the tensor-core GEMM
