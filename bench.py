@@ -687,8 +687,8 @@ def main():
     ap.add_argument("--regen-sketch", action="store_true",
                     help="BF16 paper order: draw the Gaussian sketch inside the GEMMs instead of a pre-pass")
     ap.add_argument("--batch-tile", default="",
-                    help="batched bf16 paper order: pin the tensor-core tile 'chunk,stages,row_tiles' "
-                         "(e.g. 192,3,2) instead of autotuning it")
+                    help="batched bf16 paper order: pin the tensor-core tile 'chunk,stages,row_tiles[,pipeline]' "
+                         "(e.g. 192,3,2; pipeline 0 cp.async ring, 1 TMA ring, 2 overlapped epilogue) instead of autotuning it")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned workload")

@@ -358,15 +358,23 @@ int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas);
  * of a tile (64, 128, 192 or 256; it sets the tile's shared memory and tensor-
  * memory columns and so its CTAs per SM), *ctas = persistent CTAs, *row_tiles
  * = 128-row tiles per work item (1, or 2 sharing every copy of the sketch
- * chunk); all 0 before the first step or in the other forms.  row_tiles may
- * be NULL. */
-int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles);
+ * chunk), *pipeline = how the kernel is organised (0: every thread issues
+ * 16-byte cp.async copies into the operand ring; 1: one thread feeds the ring by
+ * TMA tile copies and another issues the products; 2: as 1 with two row tiles
+ * per item, the ring kept full across chunks and items while warps 4-7 round
+ * each D1 chunk to bf16 in tensor memory and the second product reads it
+ * there); all 0 before the first step or in the other forms.  row_tiles and
+ * pipeline may be NULL. */
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles,
+                            int32_t *pipeline);
 /* Pin the tile of the tensor-core product instead of letting the autotuner time
- * the candidates: (chunk, stages, row_tiles) one of (64,4,1) (128,3,1) (128,4,1)
- * (256,4,1) (64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2) (64,2,2); (0,0,0)
- * returns to the autotuner.  Takes effect at the next step (the iteration graph is rebuilt);
- * other configurations return EINVAL and change nothing. */
-int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles);
+ * the candidates: pipeline 0 or 1 with (chunk, stages, row_tiles) one of (64,4,1)
+ * (128,3,1) (128,4,1) (256,4,1) (64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2)
+ * (64,2,2), or pipeline 2 with (192,3,2) (128,4,2) (64,5,2);
+ * (0,0,0,any) returns to the autotuner.  Takes effect at the next step (the
+ * iteration graph is rebuilt); other configurations return EINVAL and change
+ * nothing. */
+int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles, int32_t pipeline);
 const char *dsanls_batch_last_error(dsanls_batch_t b);
 void dsanls_batch_destroy(dsanls_batch_t b);
 

@@ -105,9 +105,10 @@ def lib():
             "dsanls_batch_get_factors": ([vp, i32, vp, vp, i32], ctypes.c_int),
             "dsanls_batch_rel_error": ([vp, vp], ctypes.c_int),
             "dsanls_batch_tuned_blocks": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
-            "dsanls_batch_tuned_tile": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
+            "dsanls_batch_tuned_tile": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32)],
                                         ctypes.c_int),
-            "dsanls_batch_set_tile": ([vp, i32, i32, i32], ctypes.c_int),
+            "dsanls_batch_set_tile": ([vp, i32, i32, i32, i32], ctypes.c_int),
             "dsanls_batch_profile": ([vp, vp], ctypes.c_int),
             "dsanls_batch_last_error": ([vp], ctypes.c_char_p),
             "dsanls_batch_destroy": ([vp], None),
@@ -505,18 +506,21 @@ class Batch:
         self._err(lib().dsanls_batch_tuned_blocks(self._h, ctypes.byref(v)), "batch_tuned_blocks")
         return v.value
 
-    def set_tile(self, chunk, stages, row_tiles):
+    def set_tile(self, chunk, stages, row_tiles, pipeline=1):
         """Pin the tensor-core tile (bf16 paper order) instead of autotuning it;
-        (0, 0, 0) returns to the autotuner."""
-        self._err(lib().dsanls_batch_set_tile(self._h, int(chunk), int(stages), int(row_tiles)), "batch_set_tile")
+        pipeline 0: cp.async ring, 1: TMA ring, 2: TMA ring with the chunk
+        epilogue overlapped; (0, 0, 0) returns to the autotuner."""
+        self._err(lib().dsanls_batch_set_tile(self._h, int(chunk), int(stages), int(row_tiles), int(pipeline)),
+                  "batch_set_tile")
 
     def tuned_tile(self):
-        """(chunk, ctas, row tiles per item) of the tensor-core product chosen by the
-        autotuner (bf16 paper order; zeros otherwise or before the first step)."""
-        c, n, r = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
-        self._err(lib().dsanls_batch_tuned_tile(self._h, ctypes.byref(c), ctypes.byref(n), ctypes.byref(r)),
-                  "batch_tuned_tile")
-        return c.value, n.value, r.value
+        """(chunk, ctas, row tiles per item, pipeline) of the tensor-core product
+        chosen by the autotuner (bf16 paper order; zeros otherwise or before the
+        first step)."""
+        c, n, r, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        self._err(lib().dsanls_batch_tuned_tile(self._h, ctypes.byref(c), ctypes.byref(n), ctypes.byref(r),
+                                                ctypes.byref(t)), "batch_tuned_tile")
+        return c.value, n.value, r.value, t.value
 
     def close(self):
         if getattr(self, "_h", None):

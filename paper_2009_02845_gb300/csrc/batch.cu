@@ -414,10 +414,19 @@ __global__ void __launch_bounds__(256)
                 ++a;
             }
             const int c = a + rem;
-            double acc = 0.0;
-            for (int j = 0; j < dd; ++j) acc = fma((double)B[(int64_t)a * dd + j], (double)B[(int64_t)c * dd + j], acc);
-            g64[a * 32 + c] = acc;
-            g64[c * 32 + a] = acc;
+            // four interleaved partial sums (j mod 4) keep four FP64 FMAs in flight,
+            // added in a fixed order: the products are exact in FP64
+            const float *Ba = B + (int64_t)a * dd, *Bc = B + (int64_t)c * dd;
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            int j = 0;
+            for (; j + 4 <= dd; j += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma((double)Ba[j + u], (double)Bc[j + u], acc[u]);
+            }
+            for (; j < dd; ++j) acc[j & 3] = fma((double)Ba[j], (double)Bc[j], acc[j & 3]);
+            const double sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+            g64[a * 32 + c] = sum;
+            g64[c * 32 + a] = sum;
         }
         __syncthreads();
         double *G = G_all + b.offG;  // k x k, then lambda, mu, eta
@@ -593,25 +602,50 @@ void batch_build_items(const std::vector<BatchInst> &h, int side, std::vector<in
     }
 }
 
-void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaStream_t s, cudaEvent_t *ev) {
+void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaStream_t s, cudaEvent_t *ev,
+                     const BatchFork *fork) {
     const int count = g.count;
     int *ctr = g.counters + side * 6;
     auto mark = [&](int i) {
         if (ev) DSANLS_CUDA(cudaEventRecord(ev[i], s));
     };
+    if (ev) fork = nullptr;  // the profile times every phase in order on one stream
+    auto launch_gram = [&](cudaStream_t gs) {
+        kb_gram<<<cfg.persistent_blocks, 256, 0, gs>>>(g.inst, count, ctr + 2, side, g.B, g.alpha, g.beta,
+                                                      g.power_iters, g.t_dev, g.G);
+        DSANLS_LAUNCH_CHECK();
+    };
+    // the Gram and step size need only B: with a fork they start on its stream as
+    // soon as B is done and run beside the right-hand side
+    auto fork_gram = [&]() {
+        if (!fork) return;
+        DSANLS_CUDA(cudaEventRecord(fork->b_done[side], s));
+        DSANLS_CUDA(cudaStreamWaitEvent(fork->gram, fork->b_done[side], 0));
+        launch_gram(fork->gram);
+        DSANLS_CUDA(cudaEventRecord(fork->g_done[side], fork->gram));
+    };
+    // before the update: join the forked Gram, or run it here
+    auto join_gram = [&]() {
+        if (fork)
+            DSANLS_CUDA(cudaStreamWaitEvent(s, fork->g_done[side], 0));
+        else
+            launch_gram(s);
+    };
     DSANLS_CUDA(cudaMemsetAsync(ctr, 0, 6 * sizeof(int), s));
     const bool tc = g.tc && g.bf16 && g.order == 0;
     mark(0);
     if (tc) {
-        launch_batch_sketch_t(g, side, s);
+        if (fork && fork->sketch_ahead && side == 1)
+            DSANLS_CUDA(cudaStreamWaitEvent(s, fork->s_done, 0));  // S_1^T drawn during the U-half
+        else
+            launch_batch_sketch_t(g, side, s);
         mark(1);
-        launch_batch_b_tc(g, side, cfg.tc_b_ctas, ctr + 0, s);
+        launch_batch_b_tc(g, side, cfg.tc_tma, cfg.tc_b_ctas, ctr + 0, s);
         mark(2);
-        launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_stages, cfg.tc_rt, cfg.tc_ctas, ctr + 1, s);
+        fork_gram();
+        launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_stages, cfg.tc_rt, cfg.tc_tma, cfg.tc_ctas, ctr + 1, s);
         mark(3);
-        kb_gram<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, count, ctr + 2, side, g.B, g.alpha, g.beta,
-                                                     g.power_iters, g.t_dev, g.G);
-        DSANLS_LAUNCH_CHECK();
+        join_gram();
         mark(4);
         kb_update<<<cfg.persistent_blocks * 2, 128, 0, s>>>(g.inst, g.uitems[side], g.nu[side], ctr + 3, side,
                                                            g.solver, g.factors, g.R, g.G, g.flag);
@@ -630,6 +664,7 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
                                                             g.factors, g.S, g.B);
     DSANLS_LAUNCH_CHECK();
     mark(2);
+    fork_gram();
     const int pb = cfg.persistent_blocks;
     if (g.order == 1) {
         if (g.bf16)
@@ -653,9 +688,7 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
     }
     DSANLS_LAUNCH_CHECK();
     mark(3);
-    kb_gram<<<cfg.persistent_blocks, 256, 0, s>>>(g.inst, count, ctr + 2, side, g.B, g.alpha, g.beta, g.power_iters,
-                                                 g.t_dev, g.G);
-    DSANLS_LAUNCH_CHECK();
+    join_gram();
     mark(4);
     kb_update<<<cfg.persistent_blocks * 2, 128, 0, s>>>(g.inst, g.uitems[side], g.nu[side], ctr + 3, side, g.solver,
                                                        g.factors, g.R, g.G, g.flag);

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -32,6 +33,11 @@ struct dsanls_batch_ctx {
     dsanls_options opt{};
     int64_t t_host = 0;
     cudaStream_t own_stream = nullptr;
+    // forked iteration: the main path on `lead` (highest priority), the Gram and
+    // the V-half sketch on the fork's streams (lower priorities)
+    cudaStream_t lead = nullptr;
+    BatchFork fork;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_launches = 0;
     std::vector<char> has_data;
@@ -92,10 +98,29 @@ void drop_graph(dsanls_batch_ctx *b) {
     b->graph = nullptr;
 }
 
+// One outer iteration on s.  The work forks from s onto the handle's streams
+// and joins back into it, so that everything after it on s (and a graph
+// captured on s) sees the iteration complete: the main path runs on `lead`; the
+// Gram of each half-step starts on fork.gram once B is done and joins before the
+// update; in the tensor-core form the V-half sketch S_1^T (it needs only the
+// seed and t) is drawn on fork.sketch from the start of the iteration and
+// joined before the V-half's B.
 void iteration(dsanls_batch_ctx *b, cudaStream_t s) {
-    batch_half_step(b->g, 0, b->cfg, s);
-    batch_half_step(b->g, 1, b->cfg, s);
-    launch_increment_t(b->g.t_dev, 1, s);
+    BatchFork f = b->fork;
+    cudaStream_t ls = b->lead;
+    f.sketch_ahead = b->g.tc && b->g.bf16 && b->g.order == DSANLS_ORDER_PAPER;
+    DSANLS_CUDA(cudaEventRecord(b->ev_start, s));
+    DSANLS_CUDA(cudaStreamWaitEvent(ls, b->ev_start, 0));
+    if (f.sketch_ahead) {
+        DSANLS_CUDA(cudaStreamWaitEvent(f.sketch, b->ev_start, 0));
+        launch_batch_sketch_t(b->g, 1, f.sketch);
+        DSANLS_CUDA(cudaEventRecord(f.s_done, f.sketch));
+    }
+    batch_half_step(b->g, 0, b->cfg, ls, nullptr, &f);
+    batch_half_step(b->g, 1, b->cfg, ls, nullptr, &f);
+    launch_increment_t(b->g.t_dev, 1, ls);
+    DSANLS_CUDA(cudaEventRecord(b->ev_end, ls));
+    DSANLS_CUDA(cudaStreamWaitEvent(s, b->ev_end, 0));
 }
 
 // bf16 form: bring the bf16 copy of the packed data (CUDA-core kernels) or its
@@ -123,7 +148,7 @@ std::string tune_key(const dsanls_batch_ctx *b) {
     }
     std::sort(shapes.begin(), shapes.end());
     const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "") +
-                             (b->g.tc ? "tc3" : "");
+                             (b->g.tc ? "tc7" : "");
     std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
     return std::to_string(std::hash<std::string>()(key)) + "/" + form;
@@ -171,18 +196,20 @@ void cache_store(const std::string &key, int value) {
 }
 
 // A tuned configuration: per-SM persistent CTAs of the CUDA-core kernels, plus
-// (tensor-core form) 100000 x that + 10000 x the row tiles per item + 1000 x the
-// ring stages + the chunk width of the tensor-core product.
+// (tensor-core form) 1000000 x the loader (1 TMA, 0 cp.async) + 100000 x that +
+// 10000 x the row tiles per item + 1000 x the ring stages + the chunk width of
+// the tensor-core product.
 void apply_config(dsanls_batch_ctx *b, int code, int sms) {
-    const int per_sm = code >= 100000 ? code / 100000 : code;
+    const int per_sm = code >= 100000 ? (code / 100000) % 10 : code;
     b->cfg.persistent_blocks = 152 * per_sm;
     if (code >= 100000) {
+        b->cfg.tc_tma = code / 1000000;
         b->cfg.tc_rt = (code / 10000) % 10;
         b->cfg.tc_stages = (code / 1000) % 10;
         b->cfg.tc_nc = code % 1000;
-        if (!batch_tc_tile_built(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt))
+        if (!batch_tc_tile_built(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt, b->cfg.tc_tma))
             throw ArgError{"tuned tile configuration not built"};
-        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt);
+        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt, b->cfg.tc_tma);
         b->cfg.tc_b_ctas = sms * batch_tc_b_ctas_per_sm();
     }
 }
@@ -222,7 +249,13 @@ void autotune(dsanls_batch_ctx *b) {
             const int tiles[10][3] = {{64, 4, 1}, {128, 3, 1}, {128, 4, 1}, {256, 4, 1}, {64, 2, 1},
                                       {64, 4, 2}, {128, 3, 2}, {128, 4, 2}, {192, 3, 2}, {64, 2, 2}};
             for (const auto &tl : tiles)
-                for (int c : {2, 4}) candidates.push_back(c * 100000 + tl[2] * 10000 + tl[1] * 1000 + tl[0]);
+                for (int tma : {0, 1})
+                    for (int c : {2, 4})
+                        candidates.push_back(tma * 1000000 + c * 100000 + tl[2] * 10000 + tl[1] * 1000 + tl[0]);
+            // the overlapped epilogue (one row tile per item)
+            const int ws_tiles[3][2] = {{192, 3}, {128, 4}, {64, 5}};
+            for (const auto &tl : ws_tiles)
+                for (int c : {2, 4}) candidates.push_back(2 * 1000000 + c * 100000 + 2 * 10000 + tl[1] * 1000 + tl[0]);
         } else {
             candidates = {1, 2, 4, 8};
         }
@@ -292,6 +325,16 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
     const int rc = bguard(b, [&]() {
         DSANLS_CUDA(cudaGetDevice(&b->device));
         DSANLS_CUDA(cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking));
+        {
+            int least = 0, greatest = 0;  // numerically: greatest <= least
+            DSANLS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            DSANLS_CUDA(cudaStreamCreateWithPriority(&b->lead, cudaStreamNonBlocking, greatest));
+            DSANLS_CUDA(cudaStreamCreateWithPriority(&b->fork.gram, cudaStreamNonBlocking, (least + greatest) / 2));
+            DSANLS_CUDA(cudaStreamCreateWithPriority(&b->fork.sketch, cudaStreamNonBlocking, least));
+            for (cudaEvent_t *e : {&b->ev_start, &b->ev_end, &b->fork.b_done[0], &b->fork.b_done[1],
+                                   &b->fork.g_done[0], &b->fork.g_done[1], &b->fork.s_done})
+                DSANLS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        }
         prime_kernel_attributes();
         b->h.resize(count);
         int64_t offM = 0, offF = 0, offS = 0, offB = 0, offR = 0, offG = 0, offMp = 0, offSt = 0, offYt = 0;
@@ -324,7 +367,9 @@ int dsanls_batch_create(int32_t count, const int64_t *m, const int64_t *n, const
             x.offMp = offMp;
             offMp += pad8(x.m * pad8(x.n)) + pad8(x.n * pad8(x.m));
             x.offSt = offSt;
-            offSt += pad8(std::max((int64_t)x.d * pad8(x.n), (int64_t)x.dv * pad8(x.m)));
+            offSt += pad8((int64_t)x.d * pad8(x.n));
+            x.offSt1 = offSt;
+            offSt += pad8((int64_t)x.dv * pad8(x.m));
             x.offYt = offYt;
             offYt += pad8((int64_t)x.k * std::max(pad8(x.n), pad8(x.m)));
         }
@@ -430,6 +475,10 @@ int dsanls_batch_set_options(dsanls_batch_t b, const dsanls_options *opt) {
             balloc(b->g.data_p, b->datap_elems);
             balloc(b->g.St, b->st_elems);
             balloc(b->g.Yt, b->yt_elems);
+            std::vector<CUtensorMap> maps;
+            batch_tc_encode_maps(b->h, b->g, maps);
+            balloc(b->g.tmaps, (int64_t)maps.size());
+            DSANLS_CUDA(cudaMemcpy(b->g.tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
         }
         b->bf16_stale = true;
         drop_graph(b);
@@ -503,7 +552,8 @@ int dsanls_batch_step(dsanls_batch_t b, int32_t outer_iters) {
                 DSANLS_CUDA(cudaStreamEndCapture(s, &gr));
                 b->graph_launches = launch_count() - before;
                 add_launches(0 - b->graph_launches);
-                const cudaError_t e = cudaGraphInstantiate(&b->graph, gr, 0);
+                // the kernel nodes keep the priorities of the streams they were captured on
+                const cudaError_t e = cudaGraphInstantiate(&b->graph, gr, cudaGraphInstantiateFlagUseNodePriority);
                 cudaGraphDestroy(gr);
                 DSANLS_CUDA(e);
             }
@@ -589,27 +639,30 @@ int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas) {
     return DSANLS_OK;
 }
 
-int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles) {
+int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles, int32_t pipeline) {
     if (!b) return DSANLS_EINVAL;
     if (chunk == 0 && stages == 0 && row_tiles == 0) {
         b->forced_tile = 0;
     } else {
-        if (!batch_tc_tile_built(chunk, stages, row_tiles))
-            return bfail(b, DSANLS_EINVAL, "no such tile: (64,4,1) (128,3,1) (128,4,1) (256,4,1) (64,2,1) (64,4,2) "
-                                           "(128,3,2) (128,4,2) (192,3,2) (64,2,2)");
-        b->forced_tile = 2 * 100000 + row_tiles * 10000 + stages * 1000 + chunk;
+        if (!batch_tc_tile_built(chunk, stages, row_tiles, pipeline))
+            return bfail(b, DSANLS_EINVAL, "no such tile: pipeline 0 or 1 with (64,4,1) (128,3,1) (128,4,1) (256,4,1) "
+                                           "(64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2) (64,2,2); pipeline 2 "
+                                           "with (192,3,2) (128,4,2) (64,5,2)");
+        b->forced_tile = pipeline * 1000000 + 2 * 100000 + row_tiles * 10000 + stages * 1000 + chunk;
     }
     b->tuned = false;
     drop_graph(b);
     return DSANLS_OK;
 }
 
-int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles) {
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles,
+                            int32_t *pipeline) {
     if (!b || !chunk || !ctas) return DSANLS_EINVAL;
     const bool tc = b->tuned && b->g.tc;
     *chunk = tc ? b->cfg.tc_nc : 0;
     *ctas = tc ? b->cfg.tc_ctas : 0;
     if (row_tiles) *row_tiles = tc ? b->cfg.tc_rt : 0;
+    if (pipeline) *pipeline = tc ? b->cfg.tc_tma : 0;
     return DSANLS_OK;
 }
 
@@ -622,12 +675,19 @@ void dsanls_batch_destroy(dsanls_batch_t b) {
     drop_graph(b);
     BatchDev &g = b->g;
     bfree(g.inst); bfree(g.data); bfree(g.factors); bfree(g.S); bfree(g.B); bfree(g.R); bfree(g.P); bfree(g.G); bfree(g.data_b);
-    bfree(g.data_p); bfree(g.St); bfree(g.Yt);
+    bfree(g.data_p); bfree(g.St); bfree(g.Yt); bfree(g.tmaps);
     for (int side = 0; side < 2; ++side) {
         bfree(g.bitems[side]); bfree(g.aritems[side]); bfree(g.uitems[side]); bfree(g.sketch_prefix[side]); bfree(g.pitems[side]);
         bfree(g.tcitems[side]); bfree(g.tcitems2[side]); bfree(g.tcbitems[side]);
     }
     bfree(g.counters); bfree(g.t_dev); bfree(g.flag); bfree(b->work); bfree(b->dres);
+    for (cudaStream_t st : {b->lead, b->fork.gram, b->fork.sketch})
+        if (st) cudaStreamSynchronize(st);
+    for (cudaEvent_t e : {b->ev_start, b->ev_end, b->fork.b_done[0], b->fork.b_done[1], b->fork.g_done[0],
+                          b->fork.g_done[1], b->fork.s_done})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : {b->lead, b->fork.gram, b->fork.sketch})
+        if (st) cudaStreamDestroy(st);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
 }

@@ -30,10 +30,12 @@
 // bf16 Y_i^T (k_i rows) in place of the S^T chunk -- and writes D1 transposed
 // to B_i (no second product).
 #include <algorithm>
+#include <vector>
 
 #include "batch.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
 
 namespace dsanls {
@@ -54,10 +56,12 @@ __host__ __device__ constexpr uint32_t tb_tmem_cols(int nc, int rt) {
 
 struct __align__(8) TbTail {
     uint64_t stage_done[TB_MAX_STAGES];
+    uint64_t full[TB_MAX_STAGES];  // TMA: the stage's copies have landed
     uint64_t d1_done;
     uint64_t d2_done;
     uint32_t tmem_base;
     int item;
+    int issued, used;  // TMA ring: K blocks of the chunk copied / consumed
 };
 
 __host__ __device__ constexpr size_t tb_smem(int nc, int st, int rt) {
@@ -66,12 +70,46 @@ __host__ __device__ constexpr size_t tb_smem(int nc, int st, int rt) {
 
 DSANLS_DEV int64_t pad8(int64_t x) { return (x + 7) & ~(int64_t)7; }
 
-template <int NC, bool PLAIN, int TB_STAGES, int RT>
+// The bf16 B chunk of the second product: rows c < 32 (zero past k), columns
+// j < N of B_i[c][dc + j] (zero past d), 128-byte swizzled K-major.  Four warps
+// (w = 0..3) take rows w, w + 4, ...; lane l columns l, l + 32, ...: the loads of a
+// warp are coalesced and all issued before the first store.
+template <int NC>
+struct BChunk {
+    float v[TB_KP / 4][NC / 32];
+};
+template <int NC>
+DSANLS_DEV void bchunk_load(BChunk<NC> &bc, const float *B, int k, int dd, int dc, int N, int w, int lane) {
+#pragma unroll
+    for (int i = 0; i < TB_KP / 4; ++i) {
+        const int c = w + 4 * i;
+#pragma unroll
+        for (int u = 0; u < NC / 32; ++u) {
+            const int j = lane + 32 * u;
+            bc.v[i][u] = (c < k && j < N && dc + j < dd) ? B[(int64_t)c * dd + dc + j] : 0.0f;
+        }
+    }
+}
+template <int NC>
+DSANLS_DEV void bchunk_store(const BChunk<NC> &bc, uint8_t *btile, int N, int w, int lane) {
+#pragma unroll
+    for (int i = 0; i < TB_KP / 4; ++i) {
+        const int c = w + 4 * i;
+#pragma unroll
+        for (int u = 0; u < NC / 32; ++u) {
+            const int j = lane + 32 * u;
+            if (j < N)
+                *reinterpret_cast<__nv_bfloat16 *>(btile + sw128_off(c, j, TB_KP)) = __float2bfloat16_rn(bc.v[i][u]);
+        }
+    }
+}
+
+template <int NC, bool PLAIN, int TB_STAGES, int RT, bool TMA>
 __global__ void __launch_bounds__(TB_THREADS)
     kb_ar_tc(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
              int side, const __nv_bfloat16 *__restrict__ data_p, const __nv_bfloat16 *__restrict__ St_all,
              const __nv_bfloat16 *__restrict__ Yt_all, float *__restrict__ B_all, float *__restrict__ R_all,
-             int *__restrict__ flag) {
+             int *__restrict__ flag, const CUtensorMap *__restrict__ maps, int count) {
     static_assert(NC % 64 == 0 && NC >= 64 && NC <= 256, "chunk of 64 to 256 columns");
     static_assert(TB_STAGES >= 2 && TB_STAGES <= TB_MAX_STAGES, "2 to 4 stages");
     static_assert(RT == 1 || (RT == 2 && !PLAIN), "two row tiles only for the right-hand side");
@@ -88,7 +126,10 @@ __global__ void __launch_bounds__(TB_THREADS)
     uint8_t *a2 = stages;                      // 128 x NC bf16 (NC / 64 atoms of 16 KB) <= 2 stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int st = 0; st < TB_STAGES; ++st) mbar_init(&tail->stage_done[st], 1);
+        for (int st = 0; st < TB_STAGES; ++st) {
+            mbar_init(&tail->stage_done[st], 1);
+            mbar_init(&tail->full[st], 1);
+        }
         mbar_init(&tail->d1_done, 1);
         mbar_init(&tail->d2_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -121,14 +162,98 @@ __global__ void __launch_bounds__(TB_THREADS)
         const int64_t rows = PLAIN ? dd : (side == 0 ? b.m : b.n);
         const int64_t Kp = pad8(K);
         // the first operand (rows x Kp) and the second (ncols x Kp, taken NC rows at a time)
-        const __nv_bfloat16 *X = PLAIN ? St_all + b.offSt : data_p + b.offMp + (side == 0 ? 0 : b.m * pad8(b.n));
-        const __nv_bfloat16 *St = PLAIN ? Yt_all + b.offYt : St_all + b.offSt;
+        const __nv_bfloat16 *X = PLAIN ? St_all + st_off(b, side) : data_p + b.offMp + (side == 0 ? 0 : b.m * pad8(b.n));
+        const __nv_bfloat16 *St = PLAIN ? Yt_all + b.offYt : St_all + st_off(b, side);
         const int ncols = PLAIN ? k : dd;
         float *B = B_all + b.offB;
         const int nkb = (int)((Kp + TB_BK - 1) / TB_BK);
         for (int dc = 0; dc < ncols && ok; dc += NC) {
             const int N = min(NC, (ncols - dc + 15) & ~15);
             const uint32_t id1 = idesc_bf16(TB_BM, N);
+            // the products of K block kb into the D1 of each row tile, from stage st
+            auto issue_mmas = [&](uint32_t st, int kb) {
+                const uint32_t ax = smem_u32(stages + st * SB), bx = ax + XB;
+#pragma unroll
+                for (int t = 0; t < RT; ++t)
+#pragma unroll
+                    for (int kk = 0; kk < TB_BK / 16; ++kk)
+                        mma_bf16(tmem + t * NC, sw128_desc(ax + t * (TB_BM * TB_BK * 2) + kk * 32),
+                                 sw128_desc(bx + kk * 32), id1, (kb | kk) != 0);
+                mma_commit(&tail->stage_done[st]);
+            };
+            if constexpr (TMA) {
+                // Two threads walk K.  Thread 32 (warp 1) feeds the ring: once the
+                // products that last read a stage have retired it refills the stage with
+                // the TMA copies of the next K block (boxes of 64 columns: the X row tiles
+                // of 128 rows and the chunk in boxes of 64 rows; the B form reads S_i^T in
+                // two boxes of 64 rows and Y_i^T in one of 32; out-of-range rows and
+                // columns arrive as zeros).  Thread 0 (warp 0) issues the products of each
+                // block as its copies land and commits them to the stage's barrier.  The
+                // other threads wait at the barrier.
+                const CUtensorMap *mp = maps + ((size_t)side * count + items[it].x) * 3;
+                const CUtensorMap *mx = PLAIN ? mp + 1 : mp;
+                const CUtensorMap *ms = PLAIN ? mp + 2 : mp + 1;
+                const int sbox = PLAIN ? 1 : (N + 63) / 64;
+                const uint32_t bytes = PLAIN ? (uint32_t)(TB_BM * TB_BK * 2 + TB_KP * 128)
+                                             : (uint32_t)(XB + sbox * 64 * TB_BK * 2);
+                if (tid == 32) {
+                    int issued = 0;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint32_t L = git + (uint32_t)kb, st = L % TB_STAGES, use = L / TB_STAGES;
+                        if (use >= 1 && !mbar_wait(&tail->stage_done[st], (use - 1) & 1, TB_WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        uint64_t *fb = &tail->full[st];
+                        uint8_t *sx = stages + st * SB;
+                        uint8_t *ss = sx + XB;
+                        const int x = kb * TB_BK;
+                        mbar_expect_tx(fb, bytes);
+                        if (PLAIN) {
+                            tma_load_2d(sx, mx, x, (int)r0, fb);
+                            tma_load_2d(sx + 64 * TB_BK * 2, mx, x, (int)r0 + 64, fb);
+                            tma_load_2d(ss, ms, x, 0, fb);
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < RT; ++t)
+                                tma_load_2d(sx + t * (TB_BM * TB_BK * 2), mx, x, (int)r0 + t * TB_BM, fb);
+                            for (int q = 0; q < sbox; ++q) tma_load_2d(ss + q * 64 * TB_BK * 2, ms, x, dc + 64 * q, fb);
+                        }
+                        ++issued;
+                    }
+                    tail->issued = issued;
+                } else if (tid == 0) {
+                    int used = 0;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint32_t L = git + (uint32_t)kb, st = L % TB_STAGES, use = L / TB_STAGES;
+                        if (!mbar_wait(&tail->full[st], use & 1, TB_WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        ++used;
+                        fence_after();
+                        issue_mmas(st, kb);
+                    }
+                    tail->used = used;
+                } else if (!PLAIN && warp >= 4) {
+                    // the B chunk while the products run (the previous chunk's second
+                    // products, its last readers, have retired)
+                    BChunk<NC> bc;
+                    bchunk_load<NC>(bc, B, k, dd, dc, N, warp - 4, lane);
+                    bchunk_store<NC>(bc, btile, N, warp - 4, lane);
+                }
+                git += (uint32_t)nkb;
+                if (__syncthreads_or(!ok)) {
+                    // copies still in flight land before the CTA gives up (bounded waits)
+                    if (tid == 0)
+                        for (int u = tail->used; u < tail->issued; ++u) {
+                            const uint32_t L = git - (uint32_t)nkb + (uint32_t)u;
+                            mbar_wait(&tail->full[L % TB_STAGES], (L / TB_STAGES) & 1, TB_WAIT_NS);
+                        }
+                    ok = false;
+                    break;
+                }
+            } else {
             // copies of block kb into stage (git + kb) % TB_STAGES, after the products of
             // that stage's previous use (bounded wait) have read it
             auto load_block = [&](int kb) -> bool {
@@ -169,15 +294,7 @@ __global__ void __launch_bounds__(TB_THREADS)
                 }
                 if (tid == 0) {
                     fence_after();
-                    const uint32_t st = (git + (uint32_t)kb) % TB_STAGES;
-                    const uint32_t ax = smem_u32(stages + st * SB), bx = ax + XB;
-#pragma unroll
-                    for (int t = 0; t < RT; ++t)
-#pragma unroll
-                        for (int kk = 0; kk < TB_BK / 16; ++kk)
-                            mma_bf16(tmem + t * NC, sw128_desc(ax + t * (TB_BM * TB_BK * 2) + kk * 32),
-                                     sw128_desc(bx + kk * 32), id1, (kb | kk) != 0);
-                    mma_commit(&tail->stage_done[st]);
+                    issue_mmas((git + (uint32_t)kb) % TB_STAGES, kb);
                 }
                 const int next = kb + TB_STAGES - 1;
                 if (next < nkb && lok) lok = load_block(next);
@@ -186,6 +303,7 @@ __global__ void __launch_bounds__(TB_THREADS)
             cp_async_wait<0>();
             git += (uint32_t)nkb;
             if (!ok) break;
+            }
             // D1 complete: every product of this chunk has retired (the stages are free)
             if (tid == 0) mma_commit(&tail->d1_done);
             if (!mbar_wait(&tail->d1_done, n_d1 & 1, TB_WAIT_NS)) ok = false;
@@ -214,11 +332,13 @@ __global__ void __launch_bounds__(TB_THREADS)
                 continue;
             }
             // B chunk (bf16): TB_KP rows (zero past k) x N columns, shared by the row tiles
-            for (int e = tid; e < TB_KP * N; e += TB_THREADS) {
-                const int c = e / N, j = e - c * N;
-                const float v = (c < k && dc + j < dd) ? B[(int64_t)c * dd + dc + j] : 0.0f;
-                *reinterpret_cast<__nv_bfloat16 *>(btile + sw128_off(c, j, TB_KP)) = __float2bfloat16_rn(v);
-            }
+            // (the TMA form wrote it during the K loop)
+            if (!TMA)
+                for (int e = tid; e < TB_KP * N; e += TB_THREADS) {
+                    const int c = e / N, j = e - c * N;
+                    const float v = (c < k && dc + j < dd) ? B[(int64_t)c * dd + dc + j] : 0.0f;
+                    *reinterpret_cast<__nv_bfloat16 *>(btile + sw128_off(c, j, TB_KP)) = __float2bfloat16_rn(v);
+                }
             for (int t = 0; t < RT && ok; ++t) {
                 // A chunk of tile t (bf16) over the stages: warp w reads lanes 32 (w % 4).. of
                 // columns half (w / 4)
@@ -295,6 +415,284 @@ __global__ void __launch_bounds__(TB_THREADS)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
+// ---- the right-hand side with the chunk epilogue off the copy path --------------
+// kb_ar_ws: R_i = (X_i S_i) B_i^T over (instance, two 128-row tiles) items with
+// three roles that run at the same time, joined by mbarriers:
+//   * thread 32 (warp 1) feeds a ring of WS_ST stages by TMA (the two X tiles,
+//     128 x 64 each, and the S^T chunk in boxes of 64 rows), refilling a stage once
+//     the products that read it have retired -- across chunk and item boundaries,
+//     so the ring stays full while an epilogue runs;
+//   * thread 0 (warp 0) issues the products: those of chunk g into the tiles' D1
+//     accumulators, then -- once the epilogue has turned D1 into bf16 -- the second
+//     product D2 += A_g B_g^T (M = 128, N = 32 per tile) with A read from tensor
+//     memory, and waits for it before chunk g + 1 overwrites D1;
+//   * warps 4-7 (one TMEM lane, i.e. one row of each tile, per thread) round D1 of
+//     chunk g to bf16 in place (A_g packed two per column in D1's first N/2
+//     columns), write the bf16 B chunk to shared memory, and write the tiles' rows
+//     of R from D2 after the item's last chunk.
+// The items are taken in a fixed stride (item blockIdx.x + q gridDim.x), the same
+// sequence in every role.  Every wait is bounded (2 s) and also gives up when
+// another role has given up; the CTA then lets its copies land and its products
+// retire before it frees its tensor memory, and sets bit 2 of the error flag.
+constexpr int WS_THREADS = 256;
+constexpr int WS_RT = 2;
+
+__host__ __device__ constexpr size_t ws_stage_bytes(int nc) {
+    return (size_t)WS_RT * TB_BM * TB_BK * 2 + (size_t)nc * TB_BK * 2;
+}
+
+struct __align__(8) WsTail {
+    uint64_t full[8], empty[8];
+    uint64_t d1_full, conv, d2s, d2_full, d2_free;
+    uint64_t fin;
+    uint32_t tmem_base;
+    int abort;
+    uint32_t issued, consumed;  // ring blocks copied / consumed
+};
+
+__host__ __device__ constexpr size_t ws_smem(int nc, int st) {
+    // ring | B chunk (32 x nc bf16) | tail, 1024-aligned
+    return 1024 + (size_t)st * ws_stage_bytes(nc) + (size_t)TB_KP * nc * 2 + sizeof(WsTail);
+}
+
+// bounded wait that also gives up once another role has given up
+DSANLS_DEV bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (globaltimer_ns() - t0 > TB_WAIT_NS) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+template <int NC, int WS_ST>
+__global__ void __launch_bounds__(WS_THREADS)
+    kb_ar_ws(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int side,
+             const float *__restrict__ B_all, float *__restrict__ R_all, int *__restrict__ flag,
+             const CUtensorMap *__restrict__ maps, int count) {
+    static_assert(NC % 64 == 0 && NC >= 64 && WS_RT * (NC + TB_KP) <= 512, "D1 and D2 of both tiles in 512 columns");
+    static_assert(WS_ST >= 2 && WS_ST <= 8, "2 to 8 stages");
+    constexpr uint32_t SB = (uint32_t)ws_stage_bytes(NC);
+    constexpr uint32_t XT = TB_BM * TB_BK * 2;  // bytes of one X tile of a stage
+    constexpr uint32_t D2COL = WS_RT * NC;      // D1 of tile t at t NC, D2 of tile t at D2COL + t TB_KP
+    extern __shared__ __align__(1024) uint8_t ws_smem_raw[];
+    uint8_t *base = ws_smem_raw + ((1024u - (smem_u32(ws_smem_raw) & 1023u)) & 1023u);
+    uint8_t *stages = base;
+    uint8_t *btile = base + WS_ST * SB;  // NC / 64 atoms of 32 rows x 128 B
+    WsTail *tail = reinterpret_cast<WsTail *>(btile + TB_KP * NC * 2);
+    volatile int *abort = &tail->abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < WS_ST; ++i) {
+            mbar_init(&tail->full[i], 1);
+            mbar_init(&tail->empty[i], 1);
+        }
+        mbar_init(&tail->d1_full, 1);
+        mbar_init(&tail->conv, 128);
+        mbar_init(&tail->d2s, 1);
+        mbar_init(&tail->d2_full, 1);
+        mbar_init(&tail->d2_free, 128);
+        mbar_init(&tail->fin, 1);
+        tail->abort = 0;
+        tail->issued = 0;
+        tail->consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tail->tmem_base)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tail->tmem_base;
+    if (tid == 32) {
+        // ---- producer: TMA copies into the ring ----
+        uint32_t L = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+            const BatchInst b = inst[items[it].x];
+            const int dd = side == 0 ? b.d : b.dv;
+            const int64_t K = side == 0 ? b.n : b.m, Kp = (K + 7) & ~(int64_t)7;
+            const int nkb = (int)((Kp + TB_BK - 1) / TB_BK);
+            const int r0 = items[it].y * (WS_RT * TB_BM);
+            const CUtensorMap *mx = maps + ((size_t)side * count + items[it].x) * 3;
+            const CUtensorMap *ms = mx + 1;
+            for (int dc = 0; dc < dd && ok; dc += NC) {
+                const int N = min(NC, (dd - dc + 15) & ~15);
+                const int sbox = (N + 63) / 64;
+                const uint32_t bytes = WS_RT * XT + (uint32_t)sbox * 64 * TB_BK * 2;
+                for (int kb = 0; kb < nkb; ++kb, ++L) {
+                    const uint32_t st = L % WS_ST, use = L / WS_ST;
+                    if (use >= 1 && !ws_wait(&tail->empty[st], (use - 1) & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    uint64_t *fb = &tail->full[st];
+                    uint8_t *sx = stages + st * SB;
+                    const int x = kb * TB_BK;
+                    mbar_expect_tx(fb, bytes);
+#pragma unroll
+                    for (int t = 0; t < WS_RT; ++t) tma_load_2d(sx + t * XT, mx, x, r0 + t * TB_BM, fb);
+                    for (int q = 0; q < sbox; ++q)
+                        tma_load_2d(sx + WS_RT * XT + q * 64 * TB_BK * 2, ms, x, dc + 64 * q, fb);
+                    tail->issued = L + 1;
+                }
+            }
+        }
+    } else if (tid == 0) {
+        // ---- products ----
+        const uint32_t id2 = idesc_bf16(TB_BM, TB_KP);
+        uint32_t L = 0;
+        int g = 0, q = 0;  // jobs (chunks) and items so far
+        int pdc = 0, pN = 0, pq = 0;
+        bool plast = false;
+        bool ok = true;
+        // D2 += A_h B_h^T for job h once its epilogue is done (A in D1, packed); the
+        // first chunk of an item overwrites D2 once the previous item's rows are out.
+        // Waits for these products before D1 is written again.
+        auto second = [&](int hg) -> bool {
+            if (!ws_wait(&tail->conv, hg & 1, abort)) return false;
+            if (pdc == 0 && pq >= 1 && !ws_wait(&tail->d2_free, (pq - 1) & 1, abort)) return false;
+            fence_after();
+            const uint32_t bs = smem_u32(btile);
+#pragma unroll
+            for (int t = 0; t < WS_RT; ++t)
+                for (int kk = 0; kk < pN / 16; ++kk) {
+                    const uint32_t bd = bs + (kk >> 2) * (TB_KP * 128) + (kk & 3) * 32;
+                    mma_bf16_tmem_a(tmem + D2COL + t * TB_KP, tmem + t * NC + kk * 8, sw128_desc(bd), id2,
+                                    (pdc | kk) != 0);
+                }
+            mma_commit(&tail->d2s);
+            if (plast) mma_commit(&tail->d2_full);
+            return ws_wait(&tail->d2s, hg & 1, abort);
+        };
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++q) {
+            const BatchInst b = inst[items[it].x];
+            const int dd = side == 0 ? b.d : b.dv;
+            const int64_t K = side == 0 ? b.n : b.m, Kp = (K + 7) & ~(int64_t)7;
+            const int nkb = (int)((Kp + TB_BK - 1) / TB_BK);
+            for (int dc = 0; dc < dd && ok; dc += NC, ++g) {
+                if (g >= 1 && !second(g - 1)) {
+                    ok = false;
+                    break;
+                }
+                const int N = min(NC, (dd - dc + 15) & ~15);
+                const uint32_t id1 = idesc_bf16(TB_BM, N);
+                for (int kb = 0; kb < nkb; ++kb, ++L) {
+                    const uint32_t st = L % WS_ST, use = L / WS_ST;
+                    if (!ws_wait(&tail->full[st], use & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tail->consumed = L + 1;
+                    fence_after();
+                    const uint32_t ax = smem_u32(stages + st * SB), bx = ax + WS_RT * XT;
+#pragma unroll
+                    for (int t = 0; t < WS_RT; ++t)
+#pragma unroll
+                        for (int kk = 0; kk < TB_BK / 16; ++kk)
+                            mma_bf16(tmem + t * NC, sw128_desc(ax + t * XT + kk * 32), sw128_desc(bx + kk * 32), id1,
+                                     (kb | kk) != 0);
+                    mma_commit(&tail->empty[st]);
+                }
+                if (!ok) break;
+                mma_commit(&tail->d1_full);
+                pdc = dc;
+                pN = N;
+                pq = q;
+                plast = dc + NC >= dd;
+            }
+        }
+        if (ok && g >= 1) second(g - 1);
+    } else if (warp >= 4) {
+        // ---- epilogue: D1 -> bf16 A in place, B chunk, and R from D2 ----
+        const int qw = warp & 3, r = qw * 32 + lane;
+        const uint32_t tl = (uint32_t)(qw * 32) << 16;
+        int g = 0, q = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++q) {
+            const BatchInst b = inst[items[it].x];
+            const int k = b.k, dd = side == 0 ? b.d : b.dv;
+            const int64_t rows = side == 0 ? b.m : b.n;
+            const int64_t r0 = (int64_t)items[it].y * (WS_RT * TB_BM);
+            const float *B = B_all + b.offB;
+            for (int dc = 0; dc < dd && ok; dc += NC, ++g) {
+                const int N = min(NC, (dd - dc + 15) & ~15);
+                BChunk<NC> bc;  // in flight while the chunk's products run
+                bchunk_load<NC>(bc, B, k, dd, dc, N, qw, lane);
+                ok = __all_sync(0xffffffffu, ws_wait(&tail->d1_full, g & 1, abort));
+                if (!ok) break;
+                fence_after();
+                // A = bf16(D1), two per column in D1's first N/2 columns: the columns
+                // written for a block of 32 read lie at or below it, already read
+#pragma unroll
+                for (int t = 0; t < WS_RT; ++t)
+                    for (int cc = 0; cc < N; cc += 32) {
+                        uint32_t v[32], w[16];
+                        tmem_ld32(tmem + tl + (uint32_t)(t * NC + cc), v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            w[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+                        tmem_st16(tmem + tl + (uint32_t)(t * NC + cc / 2), w);
+                    }
+                tmem_st_wait();
+                // the B chunk, once the previous chunk's second products have read it
+                if (g >= 1) ok = __all_sync(0xffffffffu, ws_wait(&tail->d2s, (g - 1) & 1, abort));
+                if (!ok) break;
+                bchunk_store<NC>(bc, btile, N, qw, lane);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_before();
+                mbar_arrive(&tail->conv);
+                if (dc + NC >= dd) {  // the item's last chunk: its rows of R from D2
+                    ok = __all_sync(0xffffffffu, ws_wait(&tail->d2_full, q & 1, abort));
+                    if (!ok) break;
+                    fence_after();
+#pragma unroll
+                    for (int t = 0; t < WS_RT; ++t) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + tl + D2COL + t * TB_KP, v);
+                        tmem_ld_wait();
+                        if (r0 + t * TB_BM + r < rows) {
+                            float *R = R_all + b.offR + (r0 + t * TB_BM + r) * k;
+#pragma unroll
+                            for (int c = 0; c < TB_KP; ++c)
+                                if (c < k) R[c] = __uint_as_float(v[c]);
+                        }
+                    }
+                    fence_before();
+                    mbar_arrive(&tail->d2_free);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (tail->abort) {
+            atomicOr(flag, 2);
+            // copies in flight land before the shared memory is given up (bounded)
+            for (uint32_t L = tail->consumed; L < tail->issued; ++L)
+                mbar_wait(&tail->full[L % WS_ST], (L / WS_ST) & 1, TB_WAIT_NS);
+        }
+        // every product this CTA issued has retired before the tensor memory is freed
+        mma_commit(&tail->fin);
+        mbar_wait(&tail->fin, 0, TB_WAIT_NS);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
 // S_i^T (d_i x Kp_i, bf16, columns past K_i zero): blockIdx.y = instance, one
 // thread per Philox block of four rows of S_i and one column, z * scale as in
 // the binary32 sketch, then rounded; consecutive threads write consecutive
@@ -307,7 +705,7 @@ __global__ void kb_sketch_t(const BatchInst *__restrict__ inst, int side, const 
     const int64_t K = side == 0 ? b.n : b.m, Kp = pad8(K);
     const uint32_t q4 = (uint32_t)(Kp >> 2), total = q4 * (uint32_t)dd;
     const float scale = b.scale[side];
-    __nv_bfloat16 *St = St_all + b.offSt;
+    __nv_bfloat16 *St = St_all + st_off(b, side);
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
         const uint32_t j = idx / q4, q = idx - j * q4;
         float z[4];
@@ -357,45 +755,77 @@ __global__ void kb_pad_bf16(const BatchInst *__restrict__ inst, const float *__r
 size_t batch_tc_smem(int nc, int st, int rt) { return tb_smem(nc, st, rt); }
 
 namespace {
-// the tile configurations built: (chunk NC, ring stages, row tiles RT)
+// the tile configurations built: (chunk NC, ring stages, row tiles RT), each with
+// the all-thread cp.async ring and with the single-thread TMA ring
 struct ArKernel {
-    int nc, st, rt;
+    int nc, st, rt, tma;
     const void *fn;
 };
+#define DSANLS_AR(NC, ST, RT)                                                                   \
+    {NC, ST, RT, 0, (const void *)kb_ar_tc<NC, false, ST, RT, false>},                          \
+    {                                                                                           \
+        NC, ST, RT, 1, (const void *)kb_ar_tc<NC, false, ST, RT, true>                          \
+    }
 const ArKernel kArKernels[] = {
-    {64, 4, 1, (const void *)kb_ar_tc<64, false, 4, 1>},   {128, 3, 1, (const void *)kb_ar_tc<128, false, 3, 1>},
-    {128, 4, 1, (const void *)kb_ar_tc<128, false, 4, 1>}, {256, 4, 1, (const void *)kb_ar_tc<256, false, 4, 1>},
-    {64, 4, 2, (const void *)kb_ar_tc<64, false, 4, 2>},   {128, 3, 2, (const void *)kb_ar_tc<128, false, 3, 2>},
-    {128, 4, 2, (const void *)kb_ar_tc<128, false, 4, 2>}, {192, 3, 2, (const void *)kb_ar_tc<192, false, 3, 2>},
+    DSANLS_AR(64, 4, 1), DSANLS_AR(128, 3, 1), DSANLS_AR(128, 4, 1), DSANLS_AR(256, 4, 1),
+    DSANLS_AR(64, 4, 2), DSANLS_AR(128, 3, 2), DSANLS_AR(128, 4, 2), DSANLS_AR(192, 3, 2),
     // two-stage rings: small enough for two (RT = 2) or four (RT = 1) CTAs per SM
-    {64, 2, 1, (const void *)kb_ar_tc<64, false, 2, 1>},   {64, 2, 2, (const void *)kb_ar_tc<64, false, 2, 2>},
+    DSANLS_AR(64, 2, 1), DSANLS_AR(64, 2, 2),
 };
-const ArKernel &ar_kernel(int nc, int st, int rt) {
+#undef DSANLS_AR
+const ArKernel &ar_kernel(int nc, int st, int rt, int tma) {
     for (const ArKernel &a : kArKernels)
-        if (a.nc == nc && a.st == st && a.rt == rt) return a;
+        if (a.nc == nc && a.st == st && a.rt == rt && a.tma == (tma ? 1 : 0)) return a;
     throw ArgError{"batched tensor-core product: no such tile configuration"};
+}
+// the overlapped-epilogue kernels (one 128-row tile per item): (chunk NC, ring stages)
+struct WsKernel {
+    int nc, st;
+    const void *fn;
+};
+const WsKernel kWsKernels[] = {
+    {192, 3, (const void *)kb_ar_ws<192, 3>},
+    {128, 4, (const void *)kb_ar_ws<128, 4>},
+    {64, 5, (const void *)kb_ar_ws<64, 5>},
+};
+const WsKernel *ws_kernel(int nc, int st) {
+    for (const WsKernel &a : kWsKernels)
+        if (a.nc == nc && a.st == st) return &a;
+    return nullptr;
+}
+const void *b_kernel(int tma) {
+    return tma ? (const void *)kb_ar_tc<64, true, 4, 1, true> : (const void *)kb_ar_tc<64, true, 4, 1, false>;
 }
 }  // namespace
 
-bool batch_tc_tile_built(int nc, int st, int rt) {
+bool batch_tc_tile_built(int nc, int st, int rt, int mode) {
+    if (mode == 2) return rt == WS_RT && ws_kernel(nc, st) != nullptr;
+    if (mode != 0 && mode != 1) return false;
     for (const ArKernel &a : kArKernels)
         if (a.nc == nc && a.st == st && a.rt == rt) return true;
     return false;
 }
 
+size_t batch_tc_smem_mode(int nc, int st, int rt, int mode) { return mode == 2 ? ws_smem(nc, st) : tb_smem(nc, st, rt); }
+
 void batch_prime_tc(int max_smem) {
-    for (const ArKernel &a : kArKernels) {
+    std::vector<const void *> fns;
+    for (const ArKernel &a : kArKernels) fns.push_back(a.fn);
+    for (const WsKernel &a : kWsKernels) fns.push_back(a.fn);
+    fns.push_back(b_kernel(0));
+    fns.push_back(b_kernel(1));
+    for (const void *fn : fns) {
         cudaFuncAttributes fa;
-        DSANLS_CUDA(cudaFuncGetAttributes(&fa, a.fn));
-        DSANLS_CUDA(cudaFuncSetAttribute(a.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        DSANLS_CUDA(cudaFuncGetAttributes(&fa, fn));
+        DSANLS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          max_smem - (int)fa.sharedSizeBytes));
     }
-    allow_max_dynamic_smem(kb_ar_tc<64, true, 4, 1>, max_smem);
 }
 
-int batch_tc_ctas_per_sm(int nc, int st, int rt) {
+int batch_tc_ctas_per_sm(int nc, int st, int rt, int mode) {
+    if (mode == 2) return 1;  // all 512 tensor-memory columns
     int per_sm = 1;
-    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ar_kernel(nc, st, rt).fn, TB_THREADS,
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ar_kernel(nc, st, rt, 0).fn, TB_THREADS,
                                                               tb_smem(nc, st, rt)));
     // tensor memory: 512 columns per SM
     return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(nc, rt))));
@@ -403,26 +833,60 @@ int batch_tc_ctas_per_sm(int nc, int st, int rt) {
 
 int batch_tc_b_ctas_per_sm() {
     int per_sm = 1;
-    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_ar_tc<64, true, 4, 1>, TB_THREADS,
-                                                              tb_smem(64, 4, 1)));
+    DSANLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_kernel(0), TB_THREADS, tb_smem(64, 4, 1)));
     return std::max(1, std::min(per_sm, (int)(512u / tb_tmem_cols(64, 1))));
 }
 
-void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int st, int rt, int ctas, int *counter, cudaStream_t s) {
-    const ArKernel &a = ar_kernel(nc, st, rt);
+void batch_tc_encode_maps(const std::vector<BatchInst> &h, const BatchDev &g, std::vector<CUtensorMap> &maps) {
+    const int count = (int)h.size();
+    maps.assign((size_t)6 * count, CUtensorMap{});
+    for (int side = 0; side < 2; ++side)
+        for (int i = 0; i < count; ++i) {
+            const BatchInst &b = h[i];
+            const int64_t K = side == 0 ? b.n : b.m, Kp = (K + 7) & ~(int64_t)7;
+            const int64_t rows = side == 0 ? b.m : b.n, dd = side == 0 ? b.d : b.dv;
+            CUtensorMap *m = maps.data() + ((size_t)side * count + i) * 3;
+            encode_bf16_map(m + 0, g.data_p + b.offMp + (side == 0 ? 0 : b.m * ((b.n + 7) & ~(int64_t)7)), rows, Kp,
+                            TB_BM);
+            encode_bf16_map(m + 1, g.St + st_off(b, side), dd, Kp, 64);
+            encode_bf16_map(m + 2, g.Yt + b.offYt, b.k, Kp, TB_KP);
+        }
+}
+
+void launch_batch_ar_tc(const BatchDev &g, int side, int nc, int st, int rt, int tma, int ctas, int *counter,
+                        cudaStream_t s) {
+    if (tma == 2 && g.tmaps) {
+        const WsKernel *w = ws_kernel(nc, st);
+        if (!w || rt != WS_RT) throw ArgError{"batched tensor-core product: no such overlapped-epilogue tile"};
+        const int2 *items = g.tcitems2[side];
+        int nitems = g.ntc2[side];
+        int count = g.count;
+        void *args[] = {(void *)&g.inst, (void *)&items, (void *)&nitems, (void *)&side, (void *)&g.B,
+                        (void *)&g.R, (void *)&g.flag, (void *)&g.tmaps, (void *)&count};
+        DSANLS_CUDA(cudaLaunchKernel(w->fn, dim3((unsigned)ctas), dim3(WS_THREADS), args, ws_smem(nc, st), s));
+        return;
+    }
+    const ArKernel &a = ar_kernel(nc, st, rt, tma && g.tmaps);
     const int2 *items = rt == 2 ? g.tcitems2[side] : g.tcitems[side];
     int nitems = rt == 2 ? g.ntc2[side] : g.ntc[side];
+    int count = g.count;
     void *args[] = {(void *)&g.inst, (void *)&items, (void *)&nitems, (void *)&counter, (void *)&side,
-                    (void *)&g.data_p, (void *)&g.St, (void *)&g.Yt, (void *)&g.B, (void *)&g.R, (void *)&g.flag};
+                    (void *)&g.data_p, (void *)&g.St, (void *)&g.Yt, (void *)&g.B, (void *)&g.R, (void *)&g.flag,
+                    (void *)&g.tmaps, (void *)&count};
     DSANLS_CUDA(cudaLaunchKernel(a.fn, dim3((unsigned)ctas), dim3(TB_THREADS), args, tb_smem(nc, st, rt), s));
 }
 
-void launch_batch_b_tc(const BatchDev &g, int side, int ctas, int *counter, cudaStream_t s) {
+void launch_batch_b_tc(const BatchDev &g, int side, int tma, int ctas, int *counter, cudaStream_t s) {
     kb_yt<<<dim3(4, (unsigned)g.count), 256, 0, s>>>(g.inst, side, g.factors, g.Yt);
     DSANLS_LAUNCH_CHECK();
-    kb_ar_tc<64, true, 4, 1><<<ctas, TB_THREADS, tb_smem(64, 4, 1), s>>>(g.inst, g.tcbitems[side], g.ntcb[side], counter,
-                                                                          side, g.data_p, g.St, g.Yt, g.B, g.R, g.flag);
-    DSANLS_LAUNCH_CHECK();
+    const int2 *items = g.tcbitems[side];
+    int nitems = g.ntcb[side];
+    int count = g.count;
+    void *args[] = {(void *)&g.inst, (void *)&items, (void *)&nitems, (void *)&counter, (void *)&side,
+                    (void *)&g.data_p, (void *)&g.St, (void *)&g.Yt, (void *)&g.B, (void *)&g.R, (void *)&g.flag,
+                    (void *)&g.tmaps, (void *)&count};
+    DSANLS_CUDA(
+        cudaLaunchKernel(b_kernel(tma && g.tmaps), dim3((unsigned)ctas), dim3(TB_THREADS), args, tb_smem(64, 4, 1), s));
 }
 
 void launch_batch_sketch_t(const BatchDev &g, int side, cudaStream_t s) {

@@ -64,14 +64,6 @@ namespace {
 
 DSANLS_DEV unsigned long long wait_limit() { return g_wait_ns ? g_wait_ns : WAIT_NS; }
 
-DSANLS_DEV void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
 struct __align__(8) TcSmemTail {
     uint64_t full[4];
     uint64_t empty[4];
@@ -503,6 +495,10 @@ int skinny_bnt(int k) { return k <= 64 ? 64 : 128; }
 int stages_for(int kp) { return smem_bytes(4, kp) <= 227 * 1024 ? 4 : 3; }  // opt-in limit of sm_100/sm_103
 
 }  // namespace
+
+void encode_bf16_map(CUtensorMap *out, const void *base, int64_t rows, int64_t cols, int box_rows) {
+    *out = make_map(base, rows, cols, box_rows);
+}
 
 bool tc_supported(int k) { return k >= 1 && k <= 128; }
 

@@ -1,11 +1,17 @@
 // Tensor-core (tcgen05) path of the sketched right-hand side R = (X S) B^T.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace dsanls {
+
+// Tensor map of a 2-D bf16 row-major tensor (rows x cols, cols a multiple of 8,
+// base 16-byte aligned): boxes of 64 columns x box_rows rows, 128-byte swizzle
+// (the K-major operand layout of the tcgen05 kernels), zero fill out of bounds.
+void encode_bf16_map(CUtensorMap *out, const void *base, int64_t rows, int64_t cols, int box_rows);
 
 // True when the tcgen05 path handles rank k.
 bool tc_supported(int k);

@@ -4,6 +4,7 @@
 // Device-only, internal linkage in every file that includes it.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -53,6 +54,17 @@ DSANLS_DEV bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long lim
     while (!mbar_try_wait(bar, parity))
         if (globaltimer_ns() - t0 > limit) return false;
     return true;
+}
+
+// 2-D tiled TMA load of the box at (x, y) (x: innermost, elements) of the tensor
+// map into shared memory; its bytes complete the transaction count of `bar`.
+// The map is in kernel-parameter, constant or global memory.
+DSANLS_DEV void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // Shared-memory matrix descriptor of a K-major operand with 128-byte

@@ -182,23 +182,27 @@ def test_batch_bf16_one_iteration(pkg, order):
 
 TILES = [(64, 4, 1), (128, 3, 1), (128, 4, 1), (256, 4, 1), (64, 2, 1),
          (64, 4, 2), (128, 3, 2), (128, 4, 2), (192, 3, 2), (64, 2, 2)]
+TILES_LOADERS = ([t + (2,) for t in [(192, 3, 2), (128, 4, 2), (64, 5, 2)]] +
+                 [t + (p,) for p in (1, 0) for t in TILES])
 
 
-@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("tile", TILES_LOADERS)
 def test_batch_bf16_every_tile(pkg, tile):
     """Each tile of the tensor-core product pinned in turn (chunk of sketch columns,
-    ring stages, one or two 128-row tiles per work item): every instance within the
-    derived bound of the exact oracle.  The shapes give pairs of row tiles whose
-    second tile is ragged or empty (257 and 64 rows) and sketches of several chunks
-    (d' = 512, d = 256)."""
+    ring stages, one or two 128-row tiles per work item, operand ring fed by TMA or
+    by cp.async, the chunk epilogue off the copy path or not): every instance within the
+    derived bound of the exact oracle.  The
+    shapes give pairs of row tiles whose second tile is ragged or empty (257 and 64
+    rows), sketches of several chunks (d' = 512, d = 256) and K not a multiple of
+    64 (the TMA boxes past K read zeros)."""
     Ms = _inputs(SHAPES)
     b = pkg.Batch(SHAPES, use_graph=1, precision=pkg.BF16)
     b.set_tile(*tile)
     for i, M in enumerate(Ms):
         b.set_dense(i, M)
     b.step(1)
-    chunk, ctas, row_tiles = b.tuned_tile()
-    assert (chunk, row_tiles) == (tile[0], tile[2]) and ctas > 0
+    chunk, ctas, row_tiles, pipeline = b.tuned_tile()
+    assert (chunk, row_tiles, pipeline) == (tile[0], tile[2], tile[3]) and ctas > 0
     mu = method.mu_t(1.0, 1.0, 0)
     for i, (s, M) in enumerate(zip(SHAPES, Ms)):
         U, V = b.factors(i)
@@ -215,7 +219,8 @@ def test_batch_bf16_every_tile(pkg, tile):
 
 def test_batch_set_tile_rejects_unbuilt_tiles(pkg):
     b = pkg.Batch(SHAPES[:2], precision=pkg.BF16)
-    for bad in [(96, 3, 2), (256, 4, 2), (128, 2, 1), (64, 4, 3)]:
+    for bad in [(96, 3, 2, 1), (256, 4, 2, 1), (128, 2, 1, 0), (64, 4, 3, 1), (64, 4, 1, 3), (192, 4, 2, 2),
+                (192, 3, 1, 2)]:
         with pytest.raises(pkg.DSANLSError):
             b.set_tile(*bad)
     b.set_tile(0, 0, 0)  # back to the autotuner
@@ -236,8 +241,9 @@ def test_batch_bf16_tensor_core_tile_is_tuned(pkg):
         for i, M in enumerate(Ms):
             b.set_dense(i, M)
         b.step(1)
-        chunk, ctas, row_tiles = b.tuned_tile()
-        assert (chunk, row_tiles) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (192, 2)) and ctas > 0  # noqa
+        chunk, ctas, row_tiles, pipeline = b.tuned_tile()
+        assert (chunk, row_tiles) in ((64, 1), (128, 1), (192, 1), (256, 1), (64, 2), (128, 2), (192, 2))
+        assert ctas > 0 and pipeline in (0, 1, 2)
         out.append([b.factors(i) for i in range(len(SHAPES))])
         b.close()
     for (u0, v0), (u1, v1) in zip(*out):
