@@ -1054,7 +1054,7 @@ def run_batch(args, w):
             "vs_baseline": None, "dtype": "f32" if prec == pkg.FP32 else "bf16", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "instances": len(specs),
                        "order": ["paper", "reassociated"][order],
-                       "graph": True, "persistent_ctas": b.tuned_blocks(), "tc_tile": b.tuned_tile(),
+                       "graph": True, "persistent_ctas": b.tuned_blocks(), "tc_tile": [b.tuned_tile(0), b.tuned_tile(1)],
                        "l2": "inputs larger than L2 (M_i total %.1f GB)" % (sum(M.nbytes for M in Ms) / 1e9)},
             "instance_iters_per_s": value * len(specs),
             "roofline": roofline,

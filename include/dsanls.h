@@ -353,28 +353,30 @@ int dsanls_batch_profile(dsanls_batch_t b, double *ms);
 /* Persistent CTAs chosen by the autotuner (0 before the first step). */
 int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas);
 /* BF16 paper order: R_i = (X_i S_i) B_i^T runs on tcgen05 tensor cores (one
- * persistent launch over (instance, row tiles) items, A_i kept on chip).
- * The tile chosen by the autotuner for it: *chunk = sketch columns per chunk
- * of a tile (64, 128, 192 or 256; it sets the tile's shared memory and tensor-
- * memory columns and so its CTAs per SM), *ctas = persistent CTAs, *row_tiles
- * = 128-row tiles per work item (1, or 2 sharing every copy of the sketch
- * chunk), *pipeline = how the kernel is organised (0: every thread issues
- * 16-byte cp.async copies into the operand ring; 1: one thread feeds the ring by
- * TMA tile copies and another issues the products; 2: as 1 with two row tiles
- * per item, the ring kept full across chunks and items while warps 4-7 round
- * each D1 chunk to bf16 in tensor memory and the second product reads it
- * there); all 0 before the first step or in the other forms.  row_tiles and
- * pipeline may be NULL. */
-int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles,
+ * persistent launch over (instance, row tiles) items, A_i kept on chip).  Each
+ * half-step (side 0: U, side 1: V) has its own tile, chosen by the autotuner
+ * from the time of that half-step's product: *chunk = sketch columns per chunk
+ * (64, 128, 192 or 256; it sets the tile's shared memory and tensor-memory
+ * columns and so its CTAs per SM), *ctas = persistent CTAs, *row_tiles = 128-row
+ * tiles per work item (1, or 2 sharing every copy of the sketch chunk),
+ * *pipeline = how the kernel is organised (0: every thread issues 16-byte
+ * cp.async copies into the operand ring; 1: one thread feeds the ring by TMA
+ * tile copies and another issues the products; 2: as 1 with two row tiles per
+ * item, the ring kept full across chunks and items while warps 4-7 round each
+ * D1 chunk to bf16 in tensor memory and the second product reads it there); all
+ * 0 before the first step or in the other forms.  row_tiles and pipeline may be
+ * NULL; side must be 0 or 1. */
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t side, int32_t *chunk, int32_t *ctas, int32_t *row_tiles,
                             int32_t *pipeline);
-/* Pin the tile of the tensor-core product instead of letting the autotuner time
- * the candidates: pipeline 0 or 1 with (chunk, stages, row_tiles) one of (64,4,1)
- * (128,3,1) (128,4,1) (256,4,1) (64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2)
- * (64,2,2), or pipeline 2 with (192,3,2) (128,4,2) (64,5,2);
- * (0,0,0,any) returns to the autotuner.  Takes effect at the next step (the
- * iteration graph is rebuilt); other configurations return EINVAL and change
- * nothing. */
-int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles, int32_t pipeline);
+/* Pin the tile of the tensor-core product of one half-step (side 0 or 1) or of
+ * both (side -1) instead of letting the autotuner time the candidates: pipeline
+ * 0 or 1 with (chunk, stages, row_tiles) one of (64,4,1) (128,3,1) (128,4,1)
+ * (256,4,1) (64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2) (64,2,2), or pipeline
+ * 2 with (192,3,2) (128,4,2) (64,5,2); (0,0,0,any) returns that side to the
+ * autotuner.  Takes effect at the next step (the iteration graph is rebuilt);
+ * other configurations return EINVAL and change nothing. */
+int dsanls_batch_set_tile(dsanls_batch_t b, int32_t side, int32_t chunk, int32_t stages, int32_t row_tiles,
+                          int32_t pipeline);
 const char *dsanls_batch_last_error(dsanls_batch_t b);
 void dsanls_batch_destroy(dsanls_batch_t b);
 

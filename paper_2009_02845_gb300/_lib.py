@@ -105,10 +105,10 @@ def lib():
             "dsanls_batch_get_factors": ([vp, i32, vp, vp, i32], ctypes.c_int),
             "dsanls_batch_rel_error": ([vp, vp], ctypes.c_int),
             "dsanls_batch_tuned_blocks": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
-            "dsanls_batch_tuned_tile": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+            "dsanls_batch_tuned_tile": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                          ctypes.POINTER(i32)],
                                         ctypes.c_int),
-            "dsanls_batch_set_tile": ([vp, i32, i32, i32, i32], ctypes.c_int),
+            "dsanls_batch_set_tile": ([vp, i32, i32, i32, i32, i32], ctypes.c_int),
             "dsanls_batch_profile": ([vp, vp], ctypes.c_int),
             "dsanls_batch_last_error": ([vp], ctypes.c_char_p),
             "dsanls_batch_destroy": ([vp], None),
@@ -506,19 +506,20 @@ class Batch:
         self._err(lib().dsanls_batch_tuned_blocks(self._h, ctypes.byref(v)), "batch_tuned_blocks")
         return v.value
 
-    def set_tile(self, chunk, stages, row_tiles, pipeline=1):
-        """Pin the tensor-core tile (bf16 paper order) instead of autotuning it;
-        pipeline 0: cp.async ring, 1: TMA ring, 2: TMA ring with the chunk
-        epilogue overlapped; (0, 0, 0) returns to the autotuner."""
-        self._err(lib().dsanls_batch_set_tile(self._h, int(chunk), int(stages), int(row_tiles), int(pipeline)),
-                  "batch_set_tile")
+    def set_tile(self, chunk, stages, row_tiles, pipeline=1, side=-1):
+        """Pin the tensor-core tile (bf16 paper order) of one half-step (side 0 or
+        1) or both (-1) instead of autotuning it; pipeline 0: cp.async ring, 1: TMA
+        ring, 2: TMA ring with the chunk epilogue off the copy path; (0, 0, 0)
+        returns to the autotuner."""
+        self._err(lib().dsanls_batch_set_tile(self._h, int(side), int(chunk), int(stages), int(row_tiles),
+                                              int(pipeline)), "batch_set_tile")
 
-    def tuned_tile(self):
-        """(chunk, ctas, row tiles per item, pipeline) of the tensor-core product
-        chosen by the autotuner (bf16 paper order; zeros otherwise or before the
-        first step)."""
+    def tuned_tile(self, side=0):
+        """(chunk, ctas, row tiles per item, pipeline) of the tensor-core product of
+        half-step `side` chosen by the autotuner (bf16 paper order; zeros otherwise
+        or before the first step)."""
         c, n, r, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
-        self._err(lib().dsanls_batch_tuned_tile(self._h, ctypes.byref(c), ctypes.byref(n), ctypes.byref(r),
+        self._err(lib().dsanls_batch_tuned_tile(self._h, int(side), ctypes.byref(c), ctypes.byref(n), ctypes.byref(r),
                                                 ctypes.byref(t)), "batch_tuned_tile")
         return c.value, n.value, r.value, t.value
 

@@ -640,10 +640,11 @@ void batch_half_step(const BatchDev &g, int side, const BatchLaunch &cfg, cudaSt
         else
             launch_batch_sketch_t(g, side, s);
         mark(1);
-        launch_batch_b_tc(g, side, cfg.tc_tma, cfg.tc_b_ctas, ctr + 0, s);
+        const TcTile &tt = cfg.tc[side];
+        launch_batch_b_tc(g, side, tt.mode >= 1 ? 1 : 0, cfg.tc_b_ctas, ctr + 0, s);
         mark(2);
         fork_gram();
-        launch_batch_ar_tc(g, side, cfg.tc_nc, cfg.tc_stages, cfg.tc_rt, cfg.tc_tma, cfg.tc_ctas, ctr + 1, s);
+        launch_batch_ar_tc(g, side, tt.nc, tt.stages, tt.rt, tt.mode, tt.ctas, ctr + 1, s);
         mark(3);
         join_gram();
         mark(4);

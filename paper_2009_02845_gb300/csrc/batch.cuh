@@ -58,15 +58,21 @@ struct BatchDev {
     double alpha = 1.0, beta = 1.0;
 };
 
+// Tile of the tensor-core product of one half-step (picked per side: the sketch
+// widths of the two halves differ).
+struct TcTile {
+    int nc = 128;    // sketch columns per chunk of the tensor-core product (64 to 256)
+    int stages = 4;  // ring stages
+    int rt = 1;      // 128-row tiles per work item (1 or 2)
+    int mode = 1;    // 0: cp.async ring (all threads); 1: TMA ring; 2: TMA ring, epilogue off the copy path
+    int ctas = 304;  // persistent CTAs
+};
+
 // Launch geometry picked by the autotuner.
 struct BatchLaunch {
     int persistent_blocks = 152 * 4;
     int sketch_blocks = 152 * 8;
-    int tc_nc = 128;    // sketch columns per chunk of the tensor-core product (64 to 256)
-    int tc_stages = 4;  // cp.async ring stages of the tensor-core product (3 or 4)
-    int tc_rt = 1;      // 128-row tiles per work item of the tensor-core product (1 or 2)
-    int tc_tma = 1;     // operand ring: 0 cp.async (all threads), 1 TMA, 2 TMA with the epilogue overlapped
-    int tc_ctas = 304;  // persistent CTAs of the tensor-core product
+    TcTile tc[2];         // U-half, V-half
     int tc_b_ctas = 304;  // persistent CTAs of B = Y^T S on tensor cores
 };
 

@@ -29,7 +29,7 @@ struct dsanls_batch_ctx {
     BatchDev g;
     BatchLaunch cfg;
     bool tuned = false;
-    int forced_tile = 0;  // a tile set by dsanls_batch_set_tile (code of apply_config), 0: tune
+    int forced_tile[2] = {0, 0};  // per side: a tile set by dsanls_batch_set_tile (code of apply_tile), 0: tune
     dsanls_options opt{};
     int64_t t_host = 0;
     cudaStream_t own_stream = nullptr;
@@ -148,7 +148,7 @@ std::string tune_key(const dsanls_batch_ctx *b) {
     }
     std::sort(shapes.begin(), shapes.end());
     const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "") +
-                             (b->g.tc ? "tc7" : "");
+                             (b->g.tc ? "tc8" : "");
     std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
     return std::to_string(std::hash<std::string>()(key)) + "/" + form;
@@ -195,38 +195,49 @@ void cache_store(const std::string &key, int value) {
     std::fclose(f);
 }
 
-// A tuned configuration: per-SM persistent CTAs of the CUDA-core kernels, plus
-// (tensor-core form) 1000000 x the loader (1 TMA, 0 cp.async) + 100000 x that +
-// 10000 x the row tiles per item + 1000 x the ring stages + the chunk width of
-// the tensor-core product.
-void apply_config(dsanls_batch_ctx *b, int code, int sms) {
-    const int per_sm = code >= 100000 ? (code / 100000) % 10 : code;
-    b->cfg.persistent_blocks = 152 * per_sm;
-    if (code >= 100000) {
-        b->cfg.tc_tma = code / 1000000;
-        b->cfg.tc_rt = (code / 10000) % 10;
-        b->cfg.tc_stages = (code / 1000) % 10;
-        b->cfg.tc_nc = code % 1000;
-        if (!batch_tc_tile_built(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt, b->cfg.tc_tma))
-            throw ArgError{"tuned tile configuration not built"};
-        b->cfg.tc_ctas = sms * batch_tc_ctas_per_sm(b->cfg.tc_nc, b->cfg.tc_stages, b->cfg.tc_rt, b->cfg.tc_tma);
-        b->cfg.tc_b_ctas = sms * batch_tc_b_ctas_per_sm();
-    }
+// A tile of the tensor-core product: 1000000 x the pipeline (0 cp.async ring, 1
+// TMA ring, 2 TMA ring with the epilogue off the copy path) + 10000 x the row
+// tiles per item + 1000 x the ring stages + the chunk width.
+void apply_tile(dsanls_batch_ctx *b, int side, int code, int sms) {
+    TcTile &t = b->cfg.tc[side];
+    t.mode = code / 1000000;
+    t.rt = (code / 10000) % 10;
+    t.stages = (code / 1000) % 10;
+    t.nc = code % 1000;
+    if (!batch_tc_tile_built(t.nc, t.stages, t.rt, t.mode)) throw ArgError{"tuned tile configuration not built"};
+    t.ctas = sms * batch_tc_ctas_per_sm(t.nc, t.stages, t.rt, t.mode);
+    b->cfg.tc_b_ctas = sms * batch_tc_b_ctas_per_sm();
 }
 
-// Time one full outer iteration for each candidate (factors restored after
-// each trial) and keep the fastest.
+// The candidate tiles of the tensor-core product.
+std::vector<int> tile_candidates() {
+    std::vector<int> c;
+    // (chunk, stages, row tiles) of the cp.async and TMA rings
+    const int tiles[10][3] = {{64, 4, 1}, {128, 3, 1}, {128, 4, 1}, {256, 4, 1}, {64, 2, 1},
+                              {64, 4, 2}, {128, 3, 2}, {128, 4, 2}, {192, 3, 2}, {64, 2, 2}};
+    for (const auto &tl : tiles)
+        for (int mode : {0, 1}) c.push_back(mode * 1000000 + tl[2] * 10000 + tl[1] * 1000 + tl[0]);
+    // the ring with the epilogue off the copy path (two row tiles per item)
+    const int ws_tiles[3][2] = {{192, 3}, {128, 4}, {64, 5}};
+    for (const auto &tl : ws_tiles) c.push_back(2 * 1000000 + 2 * 10000 + tl[1] * 1000 + tl[0]);
+    return c;
+}
+
+// Tensor-core form: the tile of each half-step is chosen by the time of its
+// product alone (each candidate's half-step run twice in order, phases timed by
+// events, the second run counted); then the CTAs per SM of the CUDA-core kernels
+// by the time of a full outer iteration.  Other forms: the CTAs per SM by full
+// iterations.  The factors and t are restored after the trials.
 void autotune(dsanls_batch_ctx *b) {
-    int sms0 = 152;
-    DSANLS_CUDA(cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, b->device));
-    if (b->g.tc && b->forced_tile) {  // the caller's tile, no timing
-        apply_config(b, b->forced_tile, sms0);
-        b->tuned = true;
-        return;
-    }
+    int sms = 152;
+    DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     const std::string key = tune_key(b);
-    int per_sm = 0;
-    if (!cache_lookup(key, per_sm)) {
+    int per_sm = 0, code[2] = {0, 0};
+    bool cached = cache_lookup(key + "#p", per_sm);
+    if (b->g.tc)
+        for (int side = 0; side < 2; ++side)
+            cached = cached && (b->forced_tile[side] || cache_lookup(key + "#" + std::to_string(side), code[side]));
+    if (!cached) {
         cudaStream_t s = b->stream();
         int64_t fbytes = 0;
         for (const BatchInst &i : b->h) fbytes = std::max<int64_t>(fbytes, i.offV + i.n * i.k);
@@ -235,35 +246,46 @@ void autotune(dsanls_batch_ctx *b) {
         int64_t t_backup = 0;
         DSANLS_CUDA(cudaMemcpyAsync(&t_backup, b->g.t_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         DSANLS_CUDA(cudaMemcpyAsync(backup, b->g.factors, fbytes * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        cudaEvent_t e0, e1;
-        DSANLS_CUDA(cudaEventCreate(&e0));
-        DSANLS_CUDA(cudaEventCreate(&e1));
-        float best = 1e30f;
-        // CUDA-core kernels: persistent CTAs per SM; tensor-core product (bf16 paper
-        // order): the chunk of sketch columns per tile (64, 128 or 256), which sets its
-        // shared memory, tensor-memory columns and CTAs per SM
-        std::vector<int> candidates;
-        if (b->g.tc) {
-            // (chunk, stages, row tiles): with one row tile 64/4 and 128/3 fit two CTAs per
-            // SM, 128/4 and 256/4 one; two row tiles (the sketch chunk shared) run one CTA
-            const int tiles[10][3] = {{64, 4, 1}, {128, 3, 1}, {128, 4, 1}, {256, 4, 1}, {64, 2, 1},
-                                      {64, 4, 2}, {128, 3, 2}, {128, 4, 2}, {192, 3, 2}, {64, 2, 2}};
-            for (const auto &tl : tiles)
-                for (int tma : {0, 1})
-                    for (int c : {2, 4})
-                        candidates.push_back(tma * 1000000 + c * 100000 + tl[2] * 10000 + tl[1] * 1000 + tl[0]);
-            // the overlapped epilogue (one row tile per item)
-            const int ws_tiles[3][2] = {{192, 3}, {128, 4}, {64, 5}};
-            for (const auto &tl : ws_tiles)
-                for (int c : {2, 4}) candidates.push_back(2 * 1000000 + c * 100000 + 2 * 10000 + tl[1] * 1000 + tl[0]);
-        } else {
-            candidates = {1, 2, 4, 8};
-        }
-        int sms = 152;
-        DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+        cudaEvent_t ev[6] = {};
+        int created = 0;
+        auto restore = [&]() {
+            DSANLS_CUDA(cudaMemcpyAsync(b->g.factors, backup, fbytes * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            DSANLS_CUDA(cudaMemcpyAsync(b->g.t_dev, &t_backup, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            DSANLS_CUDA(cudaStreamSynchronize(s));
+        };
         try {
-            for (int c : candidates) {
-                apply_config(b, c, sms);
+            for (; created < 6; ++created) DSANLS_CUDA(cudaEventCreate(&ev[created]));
+            b->cfg.persistent_blocks = 152 * 2;
+            if (b->g.tc) {
+                const std::vector<int> cand = tile_candidates();
+                for (int side = 0; side < 2; ++side) {
+                    if (b->forced_tile[side]) {
+                        code[side] = b->forced_tile[side];
+                        apply_tile(b, side, code[side], sms);
+                        continue;
+                    }
+                    float best = 1e30f;
+                    for (int c : cand) {
+                        apply_tile(b, side, c, sms);
+                        float ms = 0.0f;
+                        for (int rep = 0; rep < 2; ++rep) {
+                            batch_half_step(b->g, side, b->cfg, s, ev);
+                            DSANLS_CUDA(cudaEventSynchronize(ev[5]));
+                            DSANLS_CUDA(cudaEventElapsedTime(&ms, ev[2], ev[3]));
+                        }
+                        if (ms < best) {
+                            best = ms;
+                            code[side] = c;
+                        }
+                    }
+                    apply_tile(b, side, code[side], sms);
+                    restore();
+                }
+            }
+            cudaEvent_t e0 = ev[0], e1 = ev[1];
+            float best = 1e30f;
+            for (int c : b->g.tc ? std::vector<int>{2, 4} : std::vector<int>{1, 2, 4, 8}) {
+                b->cfg.persistent_blocks = 152 * c;
                 iteration(b, s);  // warm
                 DSANLS_CUDA(cudaEventRecord(e0, s));
                 iteration(b, s);
@@ -275,24 +297,23 @@ void autotune(dsanls_batch_ctx *b) {
                     best = ms;
                     per_sm = c;
                 }
-                DSANLS_CUDA(cudaMemcpyAsync(b->g.factors, backup, fbytes * sizeof(float), cudaMemcpyDeviceToDevice, s));
-                DSANLS_CUDA(cudaMemcpyAsync(b->g.t_dev, &t_backup, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-                DSANLS_CUDA(cudaStreamSynchronize(s));
+                restore();
             }
         } catch (...) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
+            for (int i = 0; i < created; ++i) cudaEventDestroy(ev[i]);
             bfree(backup);
             throw;
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        for (int i = 0; i < created; ++i) cudaEventDestroy(ev[i]);
         bfree(backup);
-        cache_store(key, per_sm);
+        cache_store(key + "#p", per_sm);
+        if (b->g.tc)
+            for (int side = 0; side < 2; ++side)
+                if (!b->forced_tile[side]) cache_store(key + "#" + std::to_string(side), code[side]);
     }
-    int sms = 152;
-    DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    apply_config(b, per_sm, sms);
+    b->cfg.persistent_blocks = 152 * per_sm;
+    if (b->g.tc)
+        for (int side = 0; side < 2; ++side) apply_tile(b, side, b->forced_tile[side] ? b->forced_tile[side] : code[side], sms);
     b->tuned = true;
 }
 
@@ -639,30 +660,34 @@ int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas) {
     return DSANLS_OK;
 }
 
-int dsanls_batch_set_tile(dsanls_batch_t b, int32_t chunk, int32_t stages, int32_t row_tiles, int32_t pipeline) {
+int dsanls_batch_set_tile(dsanls_batch_t b, int32_t side, int32_t chunk, int32_t stages, int32_t row_tiles,
+                          int32_t pipeline) {
     if (!b) return DSANLS_EINVAL;
-    if (chunk == 0 && stages == 0 && row_tiles == 0) {
-        b->forced_tile = 0;
-    } else {
+    if (side < -1 || side > 1) return bfail(b, DSANLS_EINVAL, "side must be 0, 1 or -1 (both)");
+    int code = 0;
+    if (!(chunk == 0 && stages == 0 && row_tiles == 0)) {
         if (!batch_tc_tile_built(chunk, stages, row_tiles, pipeline))
             return bfail(b, DSANLS_EINVAL, "no such tile: pipeline 0 or 1 with (64,4,1) (128,3,1) (128,4,1) (256,4,1) "
                                            "(64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2) (64,2,2); pipeline 2 "
                                            "with (192,3,2) (128,4,2) (64,5,2)");
-        b->forced_tile = pipeline * 1000000 + 2 * 100000 + row_tiles * 10000 + stages * 1000 + chunk;
+        code = pipeline * 1000000 + row_tiles * 10000 + stages * 1000 + chunk;
     }
+    for (int sd = 0; sd < 2; ++sd)
+        if (side == -1 || side == sd) b->forced_tile[sd] = code;
     b->tuned = false;
     drop_graph(b);
     return DSANLS_OK;
 }
 
-int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t *chunk, int32_t *ctas, int32_t *row_tiles,
+int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t side, int32_t *chunk, int32_t *ctas, int32_t *row_tiles,
                             int32_t *pipeline) {
-    if (!b || !chunk || !ctas) return DSANLS_EINVAL;
+    if (!b || !chunk || !ctas || side < 0 || side > 1) return DSANLS_EINVAL;
     const bool tc = b->tuned && b->g.tc;
-    *chunk = tc ? b->cfg.tc_nc : 0;
-    *ctas = tc ? b->cfg.tc_ctas : 0;
-    if (row_tiles) *row_tiles = tc ? b->cfg.tc_rt : 0;
-    if (pipeline) *pipeline = tc ? b->cfg.tc_tma : 0;
+    const TcTile &t = b->cfg.tc[side];
+    *chunk = tc ? t.nc : 0;
+    *ctas = tc ? t.ctas : 0;
+    if (row_tiles) *row_tiles = tc ? t.rt : 0;
+    if (pipeline) *pipeline = tc ? t.mode : 0;
     return DSANLS_OK;
 }
 

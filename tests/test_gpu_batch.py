@@ -186,6 +186,38 @@ TILES_LOADERS = ([t + (2,) for t in [(192, 3, 2), (128, 4, 2), (64, 5, 2)]] +
                  [t + (p,) for p in (1, 0) for t in TILES])
 
 
+def _check_bf16_batch(b, Ms, tag):
+    """Every instance of a bf16 batch after one outer iteration within the derived
+    bound of the exact oracle."""
+    mu = method.mu_t(1.0, 1.0, 0)
+    for i, (s, M) in enumerate(zip(SHAPES, Ms)):
+        U, V = b.factors(i)
+        U0, V0 = method.default_init(s["seed"], s["m"], s["n"], s["k"])
+        M64 = M.astype(np.float64)
+        S = method.Sketch(method.GAUSSIAN, s["seed"], 0, 0, s["n"], s["d"])
+        rel, rb = bounds.check(U, M64, V0.astype(np.float64), U0.astype(np.float64), S, 0, mu, "bf16")
+        assert rel <= rb, (tag, i, rel, rb)
+        Sp = method.Sketch(method.GAUSSIAN, s["seed"], 0, 1, s["m"], s["d_v"])
+        rel, rb = bounds.check(V, M64.T, U.astype(np.float64), V0.astype(np.float64), Sp, 0, mu, "bf16")
+        assert rel <= rb, (tag, i, rel, rb)
+
+
+def test_batch_tile_per_side(pkg):
+    """Each half-step has its own tile: pinned differently for the U- and the
+    V-half, both are reported as pinned and the results stay within the bound."""
+    Ms = _inputs(SHAPES)
+    b = pkg.Batch(SHAPES, use_graph=1, precision=pkg.BF16)
+    b.set_tile(192, 3, 2, 2, side=0)
+    b.set_tile(128, 3, 1, 1, side=1)
+    for i, M in enumerate(Ms):
+        b.set_dense(i, M)
+    b.step(1)
+    assert b.tuned_tile(0)[0::2] == (192, 2) and b.tuned_tile(0)[3] == 2
+    assert b.tuned_tile(1)[0::2] == (128, 1) and b.tuned_tile(1)[3] == 1
+    _check_bf16_batch(b, Ms, "per side")
+    b.close()
+
+
 @pytest.mark.parametrize("tile", TILES_LOADERS)
 def test_batch_bf16_every_tile(pkg, tile):
     """Each tile of the tensor-core product pinned in turn (chunk of sketch columns,
@@ -201,8 +233,9 @@ def test_batch_bf16_every_tile(pkg, tile):
     for i, M in enumerate(Ms):
         b.set_dense(i, M)
     b.step(1)
-    chunk, ctas, row_tiles, pipeline = b.tuned_tile()
-    assert (chunk, row_tiles, pipeline) == (tile[0], tile[2], tile[3]) and ctas > 0
+    for side in (0, 1):
+        chunk, ctas, row_tiles, pipeline = b.tuned_tile(side)
+        assert (chunk, row_tiles, pipeline) == (tile[0], tile[2], tile[3]) and ctas > 0
     mu = method.mu_t(1.0, 1.0, 0)
     for i, (s, M) in enumerate(zip(SHAPES, Ms)):
         U, V = b.factors(i)
@@ -241,9 +274,10 @@ def test_batch_bf16_tensor_core_tile_is_tuned(pkg):
         for i, M in enumerate(Ms):
             b.set_dense(i, M)
         b.step(1)
-        chunk, ctas, row_tiles, pipeline = b.tuned_tile()
-        assert (chunk, row_tiles) in ((64, 1), (128, 1), (192, 1), (256, 1), (64, 2), (128, 2), (192, 2))
-        assert ctas > 0 and pipeline in (0, 1, 2)
+        for side in (0, 1):
+            chunk, ctas, row_tiles, pipeline = b.tuned_tile(side)
+            assert (chunk, row_tiles) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (192, 2))
+            assert ctas > 0 and pipeline in (0, 1, 2)
         out.append([b.factors(i) for i in range(len(SHAPES))])
         b.close()
     for (u0, v0), (u1, v1) in zip(*out):
