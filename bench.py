@@ -688,7 +688,8 @@ def main():
                     help="BF16 paper order: draw the Gaussian sketch inside the GEMMs instead of a pre-pass")
     ap.add_argument("--batch-tile", default="",
                     help="batched bf16 paper order: pin the tensor-core tile 'chunk,stages,row_tiles[,pipeline]' "
-                         "(e.g. 192,3,2; pipeline 0 cp.async ring, 1 TMA ring, 2 overlapped epilogue) instead of autotuning it")
+                         "(e.g. 192,3,2; pipeline 0 cp.async ring, 1 TMA ring, 2 epilogue off the copy path) of both "
+                         "halves, or 'U-tile/V-tile', instead of autotuning it")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned workload")
@@ -988,7 +989,8 @@ def run_batch(args, w):
     prec = {"fp32": pkg.FP32, "bf16": pkg.BF16}[args.precision]
     b = pkg.Batch(specs, use_graph=1, order=order, precision=prec)
     if args.batch_tile:
-        b.set_tile(*[int(x) for x in args.batch_tile.split(",")])
+        for side, spec in enumerate(args.batch_tile.split("/")):  # one tile for both halves, or U/V
+            b.set_tile(*[int(x) for x in spec.split(",")], side=side if "/" in args.batch_tile else -1)
     for i, M in enumerate(Ms):
         b.set_dense(i, M)
     for _ in range(args.warmup):

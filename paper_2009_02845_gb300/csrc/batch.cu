@@ -473,11 +473,68 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---- row update: item = (instance, 128-row tile), one thread per row --------
+// One row's step with k <= KP (columns past k read as zero and are not written):
+// the sums run over KP terms, which leaves them bitwise unchanged (the extra
+// terms are exact zeros added to sums that start at +0).  G comes from shared
+// memory as float4 broadcasts.
+template <int KP>
+DSANLS_DEV void kb_row_step(float *Z, const float *r, int k, int solver, const float (*gs)[32], float eta, float mu,
+                            int *flag) {
+    float z[KP];
+#pragma unroll
+    for (int l = 0; l < KP; ++l) z[l] = l < k ? Z[l] : 0.0f;
+    if (solver == 0) {
+        float acc[KP];
+#pragma unroll
+        for (int c = 0; c < KP; ++c) acc[c] = 0.0f;
+#pragma unroll
+        for (int l = 0; l < KP; ++l)
+#pragma unroll
+            for (int c4 = 0; c4 < KP / 4; ++c4) {
+                const float4 g = *reinterpret_cast<const float4 *>(&gs[l][4 * c4]);
+                acc[4 * c4 + 0] = __fmaf_rn(z[l], g.x, acc[4 * c4 + 0]);
+                acc[4 * c4 + 1] = __fmaf_rn(z[l], g.y, acc[4 * c4 + 1]);
+                acc[4 * c4 + 2] = __fmaf_rn(z[l], g.z, acc[4 * c4 + 2]);
+                acc[4 * c4 + 3] = __fmaf_rn(z[l], g.w, acc[4 * c4 + 3]);
+            }
+#pragma unroll
+        for (int c = 0; c < KP; ++c) {
+            if (c < k) {
+                float v = __fmaf_rn(-eta, __fsub_rn(acc[c], r[c]), z[c]);
+                if (!(fabsf(v) <= 3.402823466e38f)) {
+                    *flag = 1;
+                    v = 0.0f;
+                }
+                Z[c] = v > 0.0f ? v : 0.0f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+            if (j < k) {
+                float tj = __fmaf_rn(mu, z[j], r[j]);
+#pragma unroll
+                for (int l = 0; l < KP; ++l)
+                    if (l != j) tj = __fmaf_rn(-gs[l][j], z[l], tj);
+                float v = __fdiv_rn(tj, __fadd_rn(gs[j][j], mu));
+                if (!(fabsf(v) <= 3.402823466e38f)) {
+                    *flag = 1;
+                    v = 0.0f;
+                }
+                z[j] = v > 0.0f ? v : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < KP; ++l)
+            if (l < k) Z[l] = z[l];
+    }
+}
+
 __global__ void __launch_bounds__(128)
     kb_update(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int *__restrict__ counter,
               int side, int solver, float *__restrict__ factors, const float *__restrict__ R_all,
               const double *__restrict__ G_all, int *__restrict__ flag) {
-    __shared__ float gs[32][33];
+    __shared__ __align__(16) float gs[32][32];
     __shared__ int item_s;
     while (true) {
         if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
@@ -489,61 +546,31 @@ __global__ void __launch_bounds__(128)
         const int k = b.k;
         const int64_t rows = rows_of(b, side);
         const double *G = G_all + b.offG;
-        for (int e = threadIdx.x; e < 32 * 32; e += 128) {
-            const int a = e / 32, c = e % 32;
-            gs[a][c] = (a < k && c < k) ? (float)G[a * k + c] : 0.0f;
+        {
+            double gv[8];  // all eight loads in flight before the first store
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + 128 * u, a = e / 32, c = e % 32;
+                gv[u] = (a < k && c < k) ? G[a * k + c] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + 128 * u;
+                gs[e / 32][e % 32] = (float)gv[u];
+            }
         }
+        const float eta = (float)G[k * k + 2], mu = (float)G[k * k + 1];
         __syncthreads();
         const int64_t row = (int64_t)items[it].y * 128 + threadIdx.x;
         if (row < rows) {
             float *Z = factors + (side == 0 ? b.offU : b.offV) + row * k;
             const float *r = R_all + b.offR + row * k;
-            float z[32];
-#pragma unroll
-            for (int l = 0; l < 32; ++l) z[l] = l < k ? Z[l] : 0.0f;
-            if (solver == 0) {
-                const float eta = (float)G[k * k + 2];
-                float out[32];
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int l = 0; l < 32; ++l) acc = __fmaf_rn(z[l], gs[l][c], acc);
-                    out[c] = 0.0f;
-                    if (c < k) out[c] = __fmaf_rn(-eta, __fsub_rn(acc, r[c]), z[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    if (c < k) {
-                        float v = out[c];
-                        if (!(fabsf(v) <= 3.402823466e38f)) {
-                            *flag = 1;
-                            v = 0.0f;
-                        }
-                        Z[c] = v > 0.0f ? v : 0.0f;
-                    }
-                }
-            } else {
-                const float mu = (float)G[k * k + 1];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (j < k) {
-                        float tj = __fmaf_rn(mu, z[j], r[j]);
-#pragma unroll
-                        for (int l = 0; l < 32; ++l)
-                            if (l != j) tj = __fmaf_rn(-gs[l][j], z[l], tj);
-                        float v = __fdiv_rn(tj, __fadd_rn(gs[j][j], mu));
-                        if (!(fabsf(v) <= 3.402823466e38f)) {
-                            *flag = 1;
-                            v = 0.0f;
-                        }
-                        z[j] = v > 0.0f ? v : 0.0f;
-                    }
-                }
-#pragma unroll
-                for (int l = 0; l < 32; ++l)
-                    if (l < k) Z[l] = z[l];
-            }
+            if (k <= 8)
+                kb_row_step<8>(Z, r, k, solver, gs, eta, mu, flag);
+            else if (k <= 16)
+                kb_row_step<16>(Z, r, k, solver, gs, eta, mu, flag);
+            else
+                kb_row_step<32>(Z, r, k, solver, gs, eta, mu, flag);
         }
         __syncthreads();
     }
