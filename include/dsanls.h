@@ -362,8 +362,9 @@ int dsanls_batch_tuned_blocks(dsanls_batch_t b, int32_t *persistent_ctas);
  * *pipeline = how the kernel is organised (0: every thread issues 16-byte
  * cp.async copies into the operand ring; 1: one thread feeds the ring by TMA
  * tile copies and another issues the products; 2: as 1 with two row tiles per
- * item, the ring kept full across chunks and items while warps 4-7 round each
- * D1 chunk to bf16 in tensor memory and the second product reads it there); all
+ * item, the ring kept full across chunks and items while warps 2-5 round each
+ * D1 chunk to bf16 in tensor memory, the second product reads it there and its
+ * chunk partials are summed in registers, so a chunk may be 256 wide); all
  * 0 before the first step or in the other forms.  row_tiles and pipeline may be
  * NULL; side must be 0 or 1. */
 int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t side, int32_t *chunk, int32_t *ctas, int32_t *row_tiles,
@@ -372,7 +373,7 @@ int dsanls_batch_tuned_tile(dsanls_batch_t b, int32_t side, int32_t *chunk, int3
  * both (side -1) instead of letting the autotuner time the candidates: pipeline
  * 0 or 1 with (chunk, stages, row_tiles) one of (64,4,1) (128,3,1) (128,4,1)
  * (256,4,1) (64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2) (64,2,2), or pipeline
- * 2 with (192,3,2) (128,4,2) (64,5,2); (0,0,0,any) returns that side to the
+ * 2 with (256,3,2) (192,3,2) (128,4,2) (64,5,2); (0,0,0,any) returns that side to the
  * autotuner.  Takes effect at the next step (the iteration graph is rebuilt);
  * other configurations return EINVAL and change nothing. */
 int dsanls_batch_set_tile(dsanls_batch_t b, int32_t side, int32_t chunk, int32_t stages, int32_t row_tiles,

@@ -393,8 +393,7 @@ __global__ void __launch_bounds__(256)
     kb_gram(const BatchInst *__restrict__ inst, int count, int *__restrict__ counter, int side,
             const float *__restrict__ B_all, double alpha, double beta, int iters, const int64_t *__restrict__ t_dev,
             double *__restrict__ G_all) {
-    __shared__ double g64[32 * 32];
-    __shared__ float gs[32][33];
+    __shared__ double g64[32 * 32];  // the Gram only (8 KB), so the kernel fits beside the products' CTAs
     __shared__ float x[32];
     __shared__ int item_s;
     while (true) {
@@ -433,7 +432,6 @@ __global__ void __launch_bounds__(256)
         for (int e = threadIdx.x; e < k * k; e += 256) {
             const int a = e / k, c = e % k;
             G[e] = g64[a * 32 + c];
-            gs[a][c] = (float)g64[a * 32 + c];
         }
         __syncthreads();
         if (threadIdx.x < 32) {  // power iteration, one warp
@@ -443,7 +441,7 @@ __global__ void __launch_bounds__(256)
             for (int itn = 0; itn < iters; ++itn) {
                 float y = 0.0f;
                 if (lane < k)
-                    for (int l = 0; l < k; ++l) y = fmaf(gs[lane][l], x[l], y);
+                    for (int l = 0; l < k; ++l) y = fmaf((float)g64[l * 32 + lane], x[l], y);  // G symmetric
                 float nrm2 = y * y;
                 for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
                 if (nrm2 == 0.0f) break;

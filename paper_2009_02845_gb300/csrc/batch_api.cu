@@ -148,7 +148,7 @@ std::string tune_key(const dsanls_batch_ctx *b) {
     }
     std::sort(shapes.begin(), shapes.end());
     const std::string form = std::string(b->g.bf16 ? "bf16" : "f32") + (b->g.order == 1 ? "r" : "") +
-                             (b->g.tc ? "tc8" : "");
+                             (b->g.tc ? "tc10" : "");
     std::string key = form;
     for (const std::string &sh : shapes) key += ";" + sh;
     return std::to_string(std::hash<std::string>()(key)) + "/" + form;
@@ -218,16 +218,17 @@ std::vector<int> tile_candidates() {
     for (const auto &tl : tiles)
         for (int mode : {0, 1}) c.push_back(mode * 1000000 + tl[2] * 10000 + tl[1] * 1000 + tl[0]);
     // the ring with the epilogue off the copy path (two row tiles per item)
-    const int ws_tiles[3][2] = {{192, 3}, {128, 4}, {64, 5}};
+    const int ws_tiles[4][2] = {{256, 3}, {192, 3}, {128, 4}, {64, 5}};
     for (const auto &tl : ws_tiles) c.push_back(2 * 1000000 + 2 * 10000 + tl[1] * 1000 + tl[0]);
     return c;
 }
 
-// Tensor-core form: the tile of each half-step is chosen by the time of its
-// product alone (each candidate's half-step run twice in order, phases timed by
-// events, the second run counted); then the CTAs per SM of the CUDA-core kernels
-// by the time of a full outer iteration.  Other forms: the CTAs per SM by full
-// iterations.  The factors and t are restored after the trials.
+// Tensor-core form: the tile of each half-step is chosen by the time of a full
+// outer iteration (forked as in a step, so a tile whose shared memory leaves no
+// room for the side streams' kernels pays for it), the other half-step's tile
+// held; then the CTAs per SM of the CUDA-core kernels.  Other forms: the CTAs per
+// SM.  Each candidate runs two iterations, the second timed; the factors and t
+// are restored after the trials.
 void autotune(dsanls_batch_ctx *b) {
     int sms = 152;
     DSANLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -253,26 +254,33 @@ void autotune(dsanls_batch_ctx *b) {
             DSANLS_CUDA(cudaMemcpyAsync(b->g.t_dev, &t_backup, sizeof(int64_t), cudaMemcpyHostToDevice, s));
             DSANLS_CUDA(cudaStreamSynchronize(s));
         };
+        // two forked outer iterations, the second timed (ms)
+        auto time_iteration = [&]() -> float {
+            iteration(b, s);
+            DSANLS_CUDA(cudaEventRecord(ev[0], s));
+            iteration(b, s);
+            DSANLS_CUDA(cudaEventRecord(ev[1], s));
+            DSANLS_CUDA(cudaEventSynchronize(ev[1]));
+            float ms = 0.0f;
+            DSANLS_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+            return ms;
+        };
         try {
             for (; created < 6; ++created) DSANLS_CUDA(cudaEventCreate(&ev[created]));
             b->cfg.persistent_blocks = 152 * 2;
             if (b->g.tc) {
                 const std::vector<int> cand = tile_candidates();
+                const int start = 1 * 1000000 + 2 * 10000 + 3 * 1000 + 192;  // TMA ring, (192, 3, 2)
                 for (int side = 0; side < 2; ++side) {
-                    if (b->forced_tile[side]) {
-                        code[side] = b->forced_tile[side];
-                        apply_tile(b, side, code[side], sms);
-                        continue;
-                    }
+                    code[side] = b->forced_tile[side] ? b->forced_tile[side] : start;
+                    apply_tile(b, side, code[side], sms);
+                }
+                for (int side = 0; side < 2; ++side) {
+                    if (b->forced_tile[side]) continue;
                     float best = 1e30f;
                     for (int c : cand) {
                         apply_tile(b, side, c, sms);
-                        float ms = 0.0f;
-                        for (int rep = 0; rep < 2; ++rep) {
-                            batch_half_step(b->g, side, b->cfg, s, ev);
-                            DSANLS_CUDA(cudaEventSynchronize(ev[5]));
-                            DSANLS_CUDA(cudaEventElapsedTime(&ms, ev[2], ev[3]));
-                        }
+                        const float ms = time_iteration();
                         if (ms < best) {
                             best = ms;
                             code[side] = c;
@@ -282,17 +290,10 @@ void autotune(dsanls_batch_ctx *b) {
                     restore();
                 }
             }
-            cudaEvent_t e0 = ev[0], e1 = ev[1];
             float best = 1e30f;
             for (int c : b->g.tc ? std::vector<int>{2, 4} : std::vector<int>{1, 2, 4, 8}) {
                 b->cfg.persistent_blocks = 152 * c;
-                iteration(b, s);  // warm
-                DSANLS_CUDA(cudaEventRecord(e0, s));
-                iteration(b, s);
-                DSANLS_CUDA(cudaEventRecord(e1, s));
-                DSANLS_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.0f;
-                DSANLS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                const float ms = time_iteration();
                 if (ms < best) {
                     best = ms;
                     per_sm = c;
@@ -669,7 +670,7 @@ int dsanls_batch_set_tile(dsanls_batch_t b, int32_t side, int32_t chunk, int32_t
         if (!batch_tc_tile_built(chunk, stages, row_tiles, pipeline))
             return bfail(b, DSANLS_EINVAL, "no such tile: pipeline 0 or 1 with (64,4,1) (128,3,1) (128,4,1) (256,4,1) "
                                            "(64,2,1) (64,4,2) (128,3,2) (128,4,2) (192,3,2) (64,2,2); pipeline 2 "
-                                           "with (192,3,2) (128,4,2) (64,5,2)");
+                                           "with (256,3,2) (192,3,2) (128,4,2) (64,5,2)");
         code = pipeline * 1000000 + row_tiles * 10000 + stages * 1000 + chunk;
     }
     for (int sd = 0; sd < 2; ++sd)

@@ -424,17 +424,20 @@ __global__ void __launch_bounds__(TB_THREADS)
 //     so the ring stays full while an epilogue runs;
 //   * thread 0 (warp 0) issues the products: those of chunk g into the tiles' D1
 //     accumulators, then -- once the epilogue has turned D1 into bf16 -- the second
-//     product D2 += A_g B_g^T (M = 128, N = 32 per tile) with A read from tensor
-//     memory, and waits for it before chunk g + 1 overwrites D1;
-//   * warps 4-7 (one TMEM lane, i.e. one row of each tile, per thread) round D1 of
+//     product P_g = A_g B_g^T (M = 128, N = 32 per tile) with A read from tensor
+//     memory into D1's free upper half, and waits until the epilogue has read P_g
+//     before chunk g + 1 overwrites D1;
+//   * warps 2-5 (one TMEM lane, i.e. one row of each tile, per thread) round D1 of
 //     chunk g to bf16 in place (A_g packed two per column in D1's first N/2
-//     columns), write the bf16 B chunk to shared memory, and write the tiles' rows
-//     of R from D2 after the item's last chunk.
+//     columns), write the bf16 B chunk to shared memory, add P_g to the rows of R
+//     they hold in registers (fp32, chunk by chunk in order) and write them out
+//     after the item's last chunk.
+// All of tensor memory is D1 (two tiles x NC columns), so a chunk may be 256 wide.
 // The items are taken in a fixed stride (item blockIdx.x + q gridDim.x), the same
 // sequence in every role.  Every wait is bounded (2 s) and also gives up when
 // another role has given up; the CTA then lets its copies land and its products
 // retire before it frees its tensor memory, and sets bit 2 of the error flag.
-constexpr int WS_THREADS = 256;
+constexpr int WS_THREADS = 192;  // six warps: no idle warp holds registers other kernels could use
 constexpr int WS_RT = 2;
 
 __host__ __device__ constexpr size_t ws_stage_bytes(int nc) {
@@ -443,7 +446,7 @@ __host__ __device__ constexpr size_t ws_stage_bytes(int nc) {
 
 struct __align__(8) WsTail {
     uint64_t full[8], empty[8];
-    uint64_t d1_full, conv, d2s, d2_full, d2_free;
+    uint64_t d1_full, conv, d2s, d2_read;
     uint64_t fin;
     uint32_t tmem_base;
     int abort;
@@ -474,11 +477,11 @@ __global__ void __launch_bounds__(WS_THREADS)
     kb_ar_ws(const BatchInst *__restrict__ inst, const int2 *__restrict__ items, int nitems, int side,
              const float *__restrict__ B_all, float *__restrict__ R_all, int *__restrict__ flag,
              const CUtensorMap *__restrict__ maps, int count) {
-    static_assert(NC % 64 == 0 && NC >= 64 && WS_RT * (NC + TB_KP) <= 512, "D1 and D2 of both tiles in 512 columns");
+    static_assert(NC % 64 == 0 && NC >= 64 && WS_RT * NC <= 512, "D1 of both tiles in 512 columns");
     static_assert(WS_ST >= 2 && WS_ST <= 8, "2 to 8 stages");
     constexpr uint32_t SB = (uint32_t)ws_stage_bytes(NC);
     constexpr uint32_t XT = TB_BM * TB_BK * 2;  // bytes of one X tile of a stage
-    constexpr uint32_t D2COL = WS_RT * NC;      // D1 of tile t at t NC, D2 of tile t at D2COL + t TB_KP
+    constexpr uint32_t PCOL = NC / 2;           // D1 of tile t at t NC; P of tile t at t NC + PCOL (after A)
     extern __shared__ __align__(1024) uint8_t ws_smem_raw[];
     uint8_t *base = ws_smem_raw + ((1024u - (smem_u32(ws_smem_raw) & 1023u)) & 1023u);
     uint8_t *stages = base;
@@ -494,8 +497,7 @@ __global__ void __launch_bounds__(WS_THREADS)
         mbar_init(&tail->d1_full, 1);
         mbar_init(&tail->conv, 128);
         mbar_init(&tail->d2s, 1);
-        mbar_init(&tail->d2_full, 1);
-        mbar_init(&tail->d2_free, 128);
+        mbar_init(&tail->d2_read, 128);
         mbar_init(&tail->fin, 1);
         tail->abort = 0;
         tail->issued = 0;
@@ -552,27 +554,22 @@ __global__ void __launch_bounds__(WS_THREADS)
         const uint32_t id2 = idesc_bf16(TB_BM, TB_KP);
         uint32_t L = 0;
         int g = 0, q = 0;  // jobs (chunks) and items so far
-        int pdc = 0, pN = 0, pq = 0;
-        bool plast = false;
+        int pN = 0;
         bool ok = true;
-        // D2 += A_h B_h^T for job h once its epilogue is done (A in D1, packed); the
-        // first chunk of an item overwrites D2 once the previous item's rows are out.
-        // Waits for these products before D1 is written again.
+        // P_h = A_h B_h^T for job h once its epilogue is done (A in D1, packed), then
+        // wait until the epilogue has read P_h: the next chunk writes all of D1
         auto second = [&](int hg) -> bool {
             if (!ws_wait(&tail->conv, hg & 1, abort)) return false;
-            if (pdc == 0 && pq >= 1 && !ws_wait(&tail->d2_free, (pq - 1) & 1, abort)) return false;
             fence_after();
             const uint32_t bs = smem_u32(btile);
 #pragma unroll
             for (int t = 0; t < WS_RT; ++t)
                 for (int kk = 0; kk < pN / 16; ++kk) {
                     const uint32_t bd = bs + (kk >> 2) * (TB_KP * 128) + (kk & 3) * 32;
-                    mma_bf16_tmem_a(tmem + D2COL + t * TB_KP, tmem + t * NC + kk * 8, sw128_desc(bd), id2,
-                                    (pdc | kk) != 0);
+                    mma_bf16_tmem_a(tmem + t * NC + PCOL, tmem + t * NC + kk * 8, sw128_desc(bd), id2, kk != 0);
                 }
             mma_commit(&tail->d2s);
-            if (plast) mma_commit(&tail->d2_full);
-            return ws_wait(&tail->d2s, hg & 1, abort);
+            return ws_wait(&tail->d2_read, hg & 1, abort);
         };
         for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++q) {
             const BatchInst b = inst[items[it].x];
@@ -605,25 +602,24 @@ __global__ void __launch_bounds__(WS_THREADS)
                 }
                 if (!ok) break;
                 mma_commit(&tail->d1_full);
-                pdc = dc;
                 pN = N;
-                pq = q;
-                plast = dc + NC >= dd;
             }
         }
         if (ok && g >= 1) second(g - 1);
-    } else if (warp >= 4) {
-        // ---- epilogue: D1 -> bf16 A in place, B chunk, and R from D2 ----
+    } else if (warp >= 2) {
+        // ---- epilogue (warps 2-5: TMEM lane quarters 2, 3, 0, 1) ----
+        // D1 -> bf16 A in place, B chunk, R = sum of the chunks' P
         const int qw = warp & 3, r = qw * 32 + lane;
         const uint32_t tl = (uint32_t)(qw * 32) << 16;
-        int g = 0, q = 0;
+        int g = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++q) {
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
             const BatchInst b = inst[items[it].x];
             const int k = b.k, dd = side == 0 ? b.d : b.dv;
             const int64_t rows = side == 0 ? b.m : b.n;
             const int64_t r0 = (int64_t)items[it].y * (WS_RT * TB_BM);
             const float *B = B_all + b.offB;
+            float racc[WS_RT][TB_KP];  // the rows of R of this thread, fp32
             for (int dc = 0; dc < dd && ok; dc += NC, ++g) {
                 const int N = min(NC, (dd - dc + 15) & ~15);
                 BChunk<NC> bc;  // in flight while the chunk's products run
@@ -645,31 +641,36 @@ __global__ void __launch_bounds__(WS_THREADS)
                         tmem_st16(tmem + tl + (uint32_t)(t * NC + cc / 2), w);
                     }
                 tmem_st_wait();
-                // the B chunk, once the previous chunk's second products have read it
-                if (g >= 1) ok = __all_sync(0xffffffffu, ws_wait(&tail->d2s, (g - 1) & 1, abort));
-                if (!ok) break;
+                // the B chunk (the previous chunk's second products, its last readers, have
+                // retired: this thread waited for them before reading their result)
                 bchunk_store<NC>(bc, btile, N, qw, lane);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 fence_before();
                 mbar_arrive(&tail->conv);
-                if (dc + NC >= dd) {  // the item's last chunk: its rows of R from D2
-                    ok = __all_sync(0xffffffffu, ws_wait(&tail->d2_full, q & 1, abort));
-                    if (!ok) break;
-                    fence_after();
+                // P of this chunk, added to R in chunk order
+                ok = __all_sync(0xffffffffu, ws_wait(&tail->d2s, g & 1, abort));
+                if (!ok) break;
+                fence_after();
 #pragma unroll
-                    for (int t = 0; t < WS_RT; ++t) {
-                        uint32_t v[32];
-                        tmem_ld32(tmem + tl + D2COL + t * TB_KP, v);
-                        tmem_ld_wait();
+                for (int t = 0; t < WS_RT; ++t) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + tl + (uint32_t)(t * NC) + PCOL, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < TB_KP; ++c)
+                        racc[t][c] = dc == 0 ? __uint_as_float(v[c]) : __fadd_rn(racc[t][c], __uint_as_float(v[c]));
+                }
+                fence_before();
+                mbar_arrive(&tail->d2_read);
+                if (dc + NC >= dd) {  // the item's last chunk: its rows of R
+#pragma unroll
+                    for (int t = 0; t < WS_RT; ++t)
                         if (r0 + t * TB_BM + r < rows) {
                             float *R = R_all + b.offR + (r0 + t * TB_BM + r) * k;
 #pragma unroll
                             for (int c = 0; c < TB_KP; ++c)
-                                if (c < k) R[c] = __uint_as_float(v[c]);
+                                if (c < k) R[c] = racc[t][c];
                         }
-                    }
-                    fence_before();
-                    mbar_arrive(&tail->d2_free);
                 }
             }
         }
@@ -784,6 +785,7 @@ struct WsKernel {
     const void *fn;
 };
 const WsKernel kWsKernels[] = {
+    {256, 3, (const void *)kb_ar_ws<256, 3>},
     {192, 3, (const void *)kb_ar_ws<192, 3>},
     {128, 4, (const void *)kb_ar_ws<128, 4>},
     {64, 5, (const void *)kb_ar_ws<64, 5>},

@@ -182,7 +182,7 @@ def test_batch_bf16_one_iteration(pkg, order):
 
 TILES = [(64, 4, 1), (128, 3, 1), (128, 4, 1), (256, 4, 1), (64, 2, 1),
          (64, 4, 2), (128, 3, 2), (128, 4, 2), (192, 3, 2), (64, 2, 2)]
-TILES_LOADERS = ([t + (2,) for t in [(192, 3, 2), (128, 4, 2), (64, 5, 2)]] +
+TILES_LOADERS = ([t + (2,) for t in [(256, 3, 2), (192, 3, 2), (128, 4, 2), (64, 5, 2)]] +
                  [t + (p,) for p in (1, 0) for t in TILES])
 
 
@@ -276,7 +276,7 @@ def test_batch_bf16_tensor_core_tile_is_tuned(pkg):
         b.step(1)
         for side in (0, 1):
             chunk, ctas, row_tiles, pipeline = b.tuned_tile(side)
-            assert (chunk, row_tiles) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (192, 2))
+            assert (chunk, row_tiles) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (192, 2), (256, 2))
             assert ctas > 0 and pipeline in (0, 1, 2)
         out.append([b.factors(i) for i in range(len(SHAPES))])
         b.close()
