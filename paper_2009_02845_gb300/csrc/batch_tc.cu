@@ -7,14 +7,17 @@
 // items, largest instances first.  A CTA of 256 threads takes an item with
 // atomicAdd and, for each NC-wide chunk of the instance's sketch columns:
 //   * walks K in blocks of 64 through a ring of TB_STAGES shared-memory
-//     stages: all threads copy the RT X tiles (128 x 64) and the S^T chunk (N x 64,
-//     N = the chunk's columns rounded up to 16) from the padded bf16 copies
-//     with 16-byte cp.async straight into the 128-byte swizzled K-major layout
-//     (rows padded to multiples of 8 elements, so any instance shape works),
-//     TB_STAGES - 1 blocks ahead of the products; thread 0 issues four
-//     tcgen05.mma (M = 128, N, K = 16) per block and row tile into that tile's
-//     accumulator D1 in tensor memory and commits to the stage's mbarrier,
-//     which frees the stage;
+//     stages holding the RT X tiles (128 x 64) and the S^T chunk (N x 64, N = the
+//     chunk's columns rounded up to 16) of the padded bf16 copies (rows padded to
+//     multiples of 8 elements, so any instance shape works) in the 128-byte
+//     swizzled K-major layout.  TMA = false: all threads copy them with 16-byte
+//     cp.async, TB_STAGES - 1 blocks ahead, and thread 0 issues the products of a
+//     block after a CTA barrier.  TMA = true: thread 32 copies them with TMA tile
+//     loads as soon as the products that last read the stage have retired,
+//     thread 0 issues the products of each block as its copies land, and warps
+//     4-7 fill the bf16 B chunk meanwhile.  Per block and row tile: four
+//     tcgen05.mma (M = 128, N, K = 16) into that tile's accumulator D1 in tensor
+//     memory, committed to the stage's mbarrier, which frees the stage;
 //   * moves each D1 to shared memory as bf16 (the rounding of A where it enters
 //     R) next to the bf16 B chunk (k rows padded to 32), and thread 0 adds
 //     A_chunk B_chunk^T into the tile's second accumulator D2 (M = 128, N = k).
@@ -254,55 +257,55 @@ __global__ void __launch_bounds__(TB_THREADS)
                     break;
                 }
             } else {
-            // copies of block kb into stage (git + kb) % TB_STAGES, after the products of
-            // that stage's previous use (bounded wait) have read it
-            auto load_block = [&](int kb) -> bool {
-                const uint32_t L = git + (uint32_t)kb, st = L % TB_STAGES, use = L / TB_STAGES;
-                if (use >= 1 && !mbar_wait(&tail->stage_done[st], (use - 1) & 1, TB_WAIT_NS)) return false;
-                uint8_t *sx = stages + st * SB;
-                uint8_t *ss = sx + XB;
-                const int64_t c0 = (int64_t)kb * TB_BK;
+                // copies of block kb into stage (git + kb) % TB_STAGES, after the products of
+                // that stage's previous use (bounded wait) have read it
+                auto load_block = [&](int kb) -> bool {
+                    const uint32_t L = git + (uint32_t)kb, st = L % TB_STAGES, use = L / TB_STAGES;
+                    if (use >= 1 && !mbar_wait(&tail->stage_done[st], (use - 1) & 1, TB_WAIT_NS)) return false;
+                    uint8_t *sx = stages + st * SB;
+                    uint8_t *ss = sx + XB;
+                    const int64_t c0 = (int64_t)kb * TB_BK;
 #pragma unroll
-                for (int q = 0; q < (RT * TB_BM * 8) / TB_THREADS; ++q) {  // X tiles: 128 rows x 8 chunks of 8 bf16
-                    const int e = tid + q * TB_THREADS, r = e >> 3, ch = e & 7;  // r: row of the RT tiles
-                    const int64_t col = c0 + 8 * ch;
-                    const bool in = r0 + r < rows && col < Kp;
-                    cp_async16(sx + (r >> 7) * (TB_BM * TB_BK * 2) + sw128_off(r & 127, 8 * ch, TB_BM),
-                               in ? (const void *)(X + (r0 + r) * Kp + col) : X, in);
+                    for (int q = 0; q < (RT * TB_BM * 8) / TB_THREADS; ++q) {  // X tiles: 128 rows x 8 chunks of 8 bf16
+                        const int e = tid + q * TB_THREADS, r = e >> 3, ch = e & 7;  // r: row of the RT tiles
+                        const int64_t col = c0 + 8 * ch;
+                        const bool in = r0 + r < rows && col < Kp;
+                        cp_async16(sx + (r >> 7) * (TB_BM * TB_BK * 2) + sw128_off(r & 127, 8 * ch, TB_BM),
+                                   in ? (const void *)(X + (r0 + r) * Kp + col) : X, in);
+                    }
+                    for (int e = tid; e < N * 8; e += TB_THREADS) {  // S^T chunk: N rows x 8 chunks
+                        const int j = e >> 3, ch = e & 7;
+                        const int64_t col = c0 + 8 * ch;
+                        const bool in = dc + j < ncols && col < Kp;
+                        cp_async16(ss + sw128_off(j, 8 * ch, NC), in ? (const void *)(St + (int64_t)(dc + j) * Kp + col) : St,
+                                   in);
+                    }
+                    return true;
+                };
+                bool lok = true;
+                for (int p = 0; p < TB_STAGES - 1; ++p) {  // prologue: TB_STAGES - 1 blocks in flight
+                    if (p < nkb && lok) lok = load_block(p);
+                    cp_async_commit();
                 }
-                for (int e = tid; e < N * 8; e += TB_THREADS) {  // S^T chunk: N rows x 8 chunks
-                    const int j = e >> 3, ch = e & 7;
-                    const int64_t col = c0 + 8 * ch;
-                    const bool in = dc + j < ncols && col < Kp;
-                    cp_async16(ss + sw128_off(j, 8 * ch, NC), in ? (const void *)(St + (int64_t)(dc + j) * Kp + col) : St,
-                               in);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    cp_async_wait<TB_STAGES - 2>();  // this thread's copies of block kb have landed
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    fence_before();
+                    if (__syncthreads_or(!lok)) {
+                        ok = false;
+                        break;
+                    }
+                    if (tid == 0) {
+                        fence_after();
+                        issue_mmas((git + (uint32_t)kb) % TB_STAGES, kb);
+                    }
+                    const int next = kb + TB_STAGES - 1;
+                    if (next < nkb && lok) lok = load_block(next);
+                    cp_async_commit();
                 }
-                return true;
-            };
-            bool lok = true;
-            for (int p = 0; p < TB_STAGES - 1; ++p) {  // prologue: TB_STAGES - 1 blocks in flight
-                if (p < nkb && lok) lok = load_block(p);
-                cp_async_commit();
-            }
-            for (int kb = 0; kb < nkb; ++kb) {
-                cp_async_wait<TB_STAGES - 2>();  // this thread's copies of block kb have landed
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                fence_before();
-                if (__syncthreads_or(!lok)) {
-                    ok = false;
-                    break;
-                }
-                if (tid == 0) {
-                    fence_after();
-                    issue_mmas((git + (uint32_t)kb) % TB_STAGES, kb);
-                }
-                const int next = kb + TB_STAGES - 1;
-                if (next < nkb && lok) lok = load_block(next);
-                cp_async_commit();
-            }
-            cp_async_wait<0>();
-            git += (uint32_t)nkb;
-            if (!ok) break;
+                cp_async_wait<0>();
+                git += (uint32_t)nkb;
+                if (!ok) break;
             }
             // D1 complete: every product of this chunk has retired (the stages are free)
             if (tid == 0) mma_commit(&tail->d1_done);
