@@ -556,8 +556,8 @@ __global__ void __launch_bounds__(WS_THREADS)
         // ---- products ----
         const uint32_t id2 = idesc_bf16(TB_BM, TB_KP);
         uint32_t L = 0;
-        int g = 0, q = 0;  // jobs (chunks) and items so far
-        int pN = 0;
+        int g = 0;   // jobs (chunks) so far
+        int pN = 0;  // columns of the previous job's chunk
         bool ok = true;
         // P_h = A_h B_h^T for job h once its epilogue is done (A in D1, packed), then
         // wait until the epilogue has read P_h: the next chunk writes all of D1
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(WS_THREADS)
             mma_commit(&tail->d2s);
             return ws_wait(&tail->d2_read, hg & 1, abort);
         };
-        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++q) {
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
             const BatchInst b = inst[items[it].x];
             const int dd = side == 0 ? b.d : b.dv;
             const int64_t K = side == 0 ? b.n : b.m, Kp = (K + 7) & ~(int64_t)7;
