@@ -49,6 +49,35 @@ def test_binding_symbol_list_matches_header(libpath):
     pkg.lib()
 
 
+def _prototype_arity():
+    """Number of parameters of every dsanls_* prototype in the headers."""
+    arity = {}
+    for hdr in HEADERS:
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"(dsanls_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, re.S):
+            params = m.group(2).strip()
+            arity[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return arity
+
+
+def test_binding_argument_counts_match_the_prototypes(libpath):
+    """Every entry point the binding declares takes as many arguments as its
+    prototype in the header (a changed signature cannot go unnoticed on CPU)."""
+    import paper_2009_02845_gb300._lib as L
+    lib = L.lib()
+    arity = _prototype_arity()
+    assert set(arity) == _declared()
+    checked = 0
+    for name, n in sorted(arity.items()):
+        fn = getattr(lib, name)
+        if fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+        checked += 1
+    assert checked >= 30
+
+
 def test_default_options_without_gpu(libpath):
     import paper_2009_02845_gb300._lib as L
     o = L.Options()
