@@ -936,6 +936,21 @@ def run_compare(args, w):
     }), flush=True)
 
 
+def parse_batch_tile(spec):
+    """--batch-tile: 'chunk,stages,row_tiles[,pipeline]' for both half-steps (side -1),
+    or 'U-tile/V-tile' (sides 0 and 1) -> [(side, (chunk, stages, row_tiles[, pipeline]))]."""
+    parts = spec.split("/")
+    if len(parts) > 2:
+        raise ValueError("--batch-tile: at most two tiles (U/V)")
+    out = []
+    for i, p in enumerate(parts):
+        tile = tuple(int(x) for x in p.split(","))
+        if len(tile) not in (3, 4):
+            raise ValueError("--batch-tile: a tile is chunk,stages,row_tiles[,pipeline]")
+        out.append((i if len(parts) == 2 else -1, tile))
+    return out
+
+
 def _batch_inputs(count):
     from synthdata import batch_specs, planted_dense
     specs = batch_specs(count, 0)
@@ -989,8 +1004,8 @@ def run_batch(args, w):
     prec = {"fp32": pkg.FP32, "bf16": pkg.BF16}[args.precision]
     b = pkg.Batch(specs, use_graph=1, order=order, precision=prec)
     if args.batch_tile:
-        for side, spec in enumerate(args.batch_tile.split("/")):  # one tile for both halves, or U/V
-            b.set_tile(*[int(x) for x in spec.split(",")], side=side if "/" in args.batch_tile else -1)
+        for side, tile in parse_batch_tile(args.batch_tile):
+            b.set_tile(*tile, side=side)
     for i, M in enumerate(Ms):
         b.set_dense(i, M)
     for _ in range(args.warmup):

@@ -7,6 +7,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -39,3 +41,13 @@ def test_reference_arm_json_line():
     st = cb["single_thread"]  # one BLAS thread (null only where no OpenBLAS is loaded)
     assert st is None or (st["cores"] == 1 and st["value"] > 0)
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_batch_tile_spec():
+    """--batch-tile pins one tile for both half-steps or one per half-step."""
+    import bench
+    assert bench.parse_batch_tile("192,3,2") == [(-1, (192, 3, 2))]
+    assert bench.parse_batch_tile("256,3,2,2/192,3,2,1") == [(0, (256, 3, 2, 2)), (1, (192, 3, 2, 1))]
+    for bad in ("192,3", "1,2,3,4,5", "1,2,3/1,2,3/1,2,3", "a,b,c"):
+        with pytest.raises(ValueError):
+            bench.parse_batch_tile(bad)
