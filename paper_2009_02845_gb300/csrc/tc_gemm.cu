@@ -46,7 +46,6 @@ constexpr int TC_THREADS = 256;
 constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KB
 // one stage: the X tile (16 KB) and BNT rows of 128 bytes of the second operand
 __host__ __device__ constexpr int stage_bytes(int bnt) { return A_STAGE_BYTES + bnt * BK * 2; }
-constexpr int STAGE_BYTES = stage_bytes(BN);
 constexpr uint32_t D2_COL = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded wait: 2 s of wall time
 constexpr int kMaxSplits = 32;                         // split-K slices of the plain product
